@@ -1,0 +1,11 @@
+"""FP64 CPU oracle for the staggered-mesh MHD step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain reference that the
+CUDA path is checked against.  Only the test suite, the package smoke check
+and the CPU-baseline leg of the benchmark may import it; the library itself
+never does, and it shares no code with the CUDA sources.
+"""
+from .stagger import (  # noqa: F401
+    Grid, Params, up, dn, ddup, dddn, rhs, rhs_parts, rk3_step, step, courant_dt,
+    diagnostics, step_adjoint, quench, max3, smooth3, ALPHA, BETA,
+)

@@ -1,0 +1,218 @@
+"""Seeded synthetic initial states for the staggered MHD workloads.
+
+This module only evaluates analytic initial conditions at the staggered
+positions of the mesh (cell centres for rho and E, lower cell faces for the
+momenta and the magnetic field).  It contains none of the method's discrete
+arithmetic: no staggered derivative or interpolation, no right-hand side and
+no time step.  Both the FP64 oracle and the CUDA path take their inputs from
+here.
+
+Layout: every field is a float64 array of shape (nz, ny, nx), x fastest.
+Positions (box [0, L) per axis, spacing h = L/n):
+    centre  x_i = (i + 1/2) h        (rho, E)
+    face    x_i = i h                (px, Bx along x; py, By along y; ...)
+The eight prognostic fields are returned in the order
+    r, px, py, pz, E, Bx, By, Bz
+with E the internal energy per unit volume (rho * e).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FIELD_NAMES = ("r", "px", "py", "pz", "E", "Bx", "By", "Bz")
+
+
+@dataclass
+class Workload:
+    """A seeded initial state plus the grid and the physics it is run with."""
+    name: str
+    shape: tuple            # (nx, ny, nz)
+    spacing: tuple          # (dx, dy, dz)
+    fields: list            # 8 float64 arrays, shape (nz, ny, nx)
+    physics: dict = field(default_factory=dict)
+
+
+def _coords(n: int, L: float, face: bool) -> np.ndarray:
+    h = L / n
+    i = np.arange(n, dtype=np.float64)
+    return i * h if face else (i + 0.5) * h
+
+
+def _mesh(shape, lengths, face_axis):
+    """3D coordinate arrays (z, y, x order) with one axis on faces (or none)."""
+    nx, ny, nz = shape
+    Lx, Ly, Lz = lengths
+    x = _coords(nx, Lx, face_axis == 0)
+    y = _coords(ny, Ly, face_axis == 1)
+    z = _coords(nz, Lz, face_axis == 2)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def linear_waves(n: int = 32, seed: int = 1, amp: float = 1e-3,
+                 gamma: float = 5.0 / 3.0, b0: float = 0.5) -> Workload:
+    """Uniform state rho=1, P=1/gamma (c_s = 1), B=(0,0,b0), plus one
+    travelling sound wave and one travelling shear Alfven wave of amplitude
+    ``amp``, each with a wave vector 2*pi*m, m drawn from {-2..2}^3 \\ {0}
+    (for the Alfven wave m_z != 0) by ``numpy.random.default_rng(seed)``."""
+    rng = np.random.default_rng(seed)
+    cand = [(a, b, c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)
+            if (a, b, c) != (0, 0, 0)]
+    ms = np.array(cand[rng.integers(len(cand))], dtype=np.float64)
+    cand_a = [m for m in cand if m[2] != 0]
+    ma = np.array(cand_a[rng.integers(len(cand_a))], dtype=np.float64)
+    phs, pha = rng.uniform(0.0, 2 * math.pi, size=2)
+
+    shape = (n, n, n)
+    L = (1.0, 1.0, 1.0)
+    h = 1.0 / n
+    rho0, P0 = 1.0, 1.0 / gamma
+    cs = math.sqrt(gamma * P0 / rho0)
+    ks = 2 * math.pi * ms
+    khat = ks / np.linalg.norm(ks)
+    ka = 2 * math.pi * ma
+    ez = np.array([0.0, 0.0, 1.0])
+    ea = np.cross(ka, ez)
+    if np.linalg.norm(ea) == 0.0:
+        ea = np.array([1.0, 0.0, 0.0])
+    ea = ea / np.linalg.norm(ea)
+    sgn = 1.0 if ka[2] > 0 else -1.0
+
+    def rho_at(X, Y, Z):
+        return rho0 + amp * np.sin(ks[0] * X + ks[1] * Y + ks[2] * Z + phs)
+
+    def u_at(d, X, Y, Z):
+        snd = amp * cs * khat[d] * np.sin(ks[0] * X + ks[1] * Y + ks[2] * Z + phs)
+        alf = amp * ea[d] * np.sin(ka[0] * X + ka[1] * Y + ka[2] * Z + pha)
+        return snd + alf
+
+    def b_at(d, X, Y, Z):
+        base = b0 if d == 2 else 0.0
+        return base - sgn * math.sqrt(rho0) * amp * ea[d] * np.sin(
+            ka[0] * X + ka[1] * Y + ka[2] * Z + pha)
+
+    Xc, Yc, Zc = _mesh(shape, L, None)
+    r = rho_at(Xc, Yc, Zc)
+    E = (P0 + cs * cs * (r - rho0)) / (gamma - 1.0)
+    mom, mag = [], []
+    for d in range(3):
+        X, Y, Z = _mesh(shape, L, d)
+        mom.append(rho_at(X, Y, Z) * u_at(d, X, Y, Z))
+        mag.append(b_at(d, X, Y, Z))
+    fields = [r, mom[0], mom[1], mom[2], E, mag[0], mag[1], mag[2]]
+    return Workload("linear_waves", shape, (h, h, h), fields,
+                    dict(gamma=gamma, m_sound=ms.tolist(), m_alfven=ma.tolist()))
+
+
+def orszag_tang(nx: int = 1024, ny: int = 1024, nz: int = 1,
+                gamma: float = 5.0 / 3.0) -> Workload:
+    """Orszag-Tang vortex in the unit square (uniform in z):
+    rho = 25/(36 pi), P = 5/(12 pi), u = (-sin 2 pi y, sin 2 pi x, 0),
+    B = B0 (-sin 2 pi y, sin 4 pi x, 0), B0 = 1/sqrt(4 pi)."""
+    shape = (nx, ny, nz)
+    L = (1.0, 1.0, 1.0)
+    rho0 = 25.0 / (36.0 * math.pi)
+    P0 = 5.0 / (12.0 * math.pi)
+    B0 = 1.0 / math.sqrt(4.0 * math.pi)
+    Xc, Yc, Zc = _mesh(shape, L, None)
+    r = np.full(Xc.shape, rho0)
+    E = np.full(Xc.shape, P0 / (gamma - 1.0))
+    X, Y, Z = _mesh(shape, L, 0)
+    px = rho0 * -np.sin(2 * math.pi * Y)
+    Bx = B0 * -np.sin(2 * math.pi * Y)
+    X, Y, Z = _mesh(shape, L, 1)
+    py = rho0 * np.sin(2 * math.pi * X)
+    By = B0 * np.sin(4 * math.pi * X)
+    pz = np.zeros(Xc.shape)
+    Bz = np.zeros(Xc.shape)
+    fields = [r, px, py, pz, E, Bx, By, Bz]
+    return Workload("orszag_tang", shape, (1.0 / nx, 1.0 / ny, 1.0 / nz), fields,
+                    dict(gamma=gamma))
+
+
+def solenoidal_velocity(shape, seed: int, urms: float, kmin: float = 1.0,
+                        kmax: float = 4.0, slope: float = -2.0, device: str = "cpu"):
+    """Gaussian random solenoidal velocity in a periodic unit box with energy
+    spectrum E(k) ~ k^slope for kmin <= |m| <= kmax (m the integer wave
+    vector), sampled at the three face positions and scaled to the given rms
+    speed.  Returns three float64 numpy arrays (ux, uy, uz)."""
+    import torch
+
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    K = int(math.ceil(kmax))
+    m1 = np.arange(-K, K + 1)
+    MZ, MY, MX = np.meshgrid(m1, m1, m1, indexing="ij")
+    kk = np.sqrt(MX ** 2 + MY ** 2 + MZ ** 2)
+    band = (kk >= kmin) & (kk <= kmax)
+    # Each component of every mode a complex Gaussian; amplitude chosen so the
+    # shell energy follows k^slope (shell area ~ k^2).
+    coef = (rng.standard_normal((3,) + MX.shape) + 1j * rng.standard_normal((3,) + MX.shape))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        amp = np.where(band, kk ** ((slope - 2.0) / 2.0), 0.0)
+    coef = coef * amp
+    # Make the field real: c(-m) = conj(c(m)).
+    coef = 0.5 * (coef + np.conj(coef[:, ::-1, ::-1, ::-1]))
+    # Solenoidal projection c <- c - m (m.c)/|m|^2.
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mdotc = (MX * coef[0] + MY * coef[1] + MZ * coef[2]) / np.where(kk > 0, kk ** 2, 1.0)
+    coef = coef - np.stack([MX, MY, MZ]) * mdotc
+
+    comps = []
+    for d, (n_d) in enumerate((nx, ny, nz)):
+        spec = torch.zeros((nz, ny, nx // 2 + 1), dtype=torch.complex128, device=device)
+        # Fill the rfft half-spectrum directly (mx >= 0).
+        sel = band & (MX >= 0)
+        vals = coef[d][sel]
+        mxv, myv, mzv = MX[sel], MY[sel], MZ[sel]
+        # The FFT grid point i sits at i*h, the lower face; along the axes
+        # where this component lives at the centre (i+1/2)h add a half-cell phase.
+        shift = np.zeros(len(vals))
+        for ax, mv, n_ax in ((0, mxv, nx), (1, myv, ny), (2, mzv, nz)):
+            if ax != d:
+                shift = shift + mv * (0.5 / n_ax)
+        phase = np.exp(2j * math.pi * shift)
+        v = vals * phase
+        # irfftn supplies the mx<0 half as the conjugate mirror; the mx=0
+        # plane is Hermitian in (my, mz) by construction, so it is kept as is.
+        zi = torch.as_tensor(np.mod(mzv, nz), device=device)
+        yi = torch.as_tensor(np.mod(myv, ny), device=device)
+        xi = torch.as_tensor(mxv, device=device)
+        spec.index_put_((zi, yi, xi), torch.as_tensor(v, device=device), accumulate=True)
+        u = torch.fft.irfftn(spec, s=(nz, ny, nx)) * (nx * ny * nz)
+        comps.append(u.cpu().numpy())
+    rms = math.sqrt(sum(float((c ** 2).mean()) for c in comps))
+    s = urms / rms
+    return [c * s for c in comps]
+
+
+def turbulence(n: int = 512, seed: int = 3, urms: float = 0.5, b0: float = 0.3,
+               gamma: float = 5.0 / 3.0, device: str = "cpu") -> Workload:
+    """Driven-free compressible MHD turbulence start: rho=1, P=1/gamma
+    (c_s = 1), B=(0,0,b0), Gaussian random solenoidal velocity with
+    E(k) ~ k^-2 for 1 <= |m| <= 4 and rms speed ``urms`` (Mach 0.5)."""
+    shape = (n, n, n)
+    h = 1.0 / n
+    ux, uy, uz = solenoidal_velocity(shape, seed, urms, device=device)
+    r = np.ones((n, n, n))
+    E = np.full((n, n, n), (1.0 / gamma) / (gamma - 1.0))
+    z = np.zeros((n, n, n))
+    Bz = np.full((n, n, n), b0)
+    fields = [r, ux, uy, uz, E, z, z.copy(), Bz]
+    return Workload("turbulence", shape, (h, h, h), fields, dict(gamma=gamma))
+
+
+def orszag_tang_3d(n: int = 128, seed: int = 4, pert: float = 1e-3,
+                   gamma: float = 5.0 / 3.0) -> Workload:
+    """Orszag-Tang fields on an n^3 box (uniform in z) plus a seeded random
+    solenoidal velocity perturbation of rms ``pert`` so every axis matters."""
+    w = orszag_tang(n, n, n, gamma)
+    du = solenoidal_velocity((n, n, n), seed, pert)
+    rho0 = w.fields[0][0, 0, 0]
+    for d in range(3):
+        w.fields[1 + d] = w.fields[1 + d] + rho0 * du[d]
+    w.name = "orszag_tang_3d"
+    return w

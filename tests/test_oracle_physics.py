@@ -1,0 +1,525 @@
+"""Pins of the oracle's right-hand side, time step, Courant limit, diagnostics
+and adjoint against closed forms, invariants and finite differences.
+
+Every check here fixes the oracle by something other than itself:
+- RK3: the amplification of y' = lambda y against exp(z) to third order;
+- uniform state: F = 0 exactly;
+- conservation of mass and momentum, and invariance of the discrete div B,
+  over a nonlinear viscous, quenched step;
+- exact shift symmetry and cyclic-permutation symmetry of the axes;
+- linear sound and Alfven phase speeds against c_s D(th)/h and
+  v_A D(th) I(th)/h, the closed-form symbols of the semi-discrete scheme;
+- constant-viscosity and constant-resistivity decay rates;
+- quench, max3 and smooth3 on inputs with closed-form results;
+- Courant step on uniform flows;
+- the adjoint against central finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.stagger as S
+from oracle.stagger import Grid, Params
+
+DT = torch.float64
+
+
+def D_sym(th):
+    return 2 * (S.DA * math.sin(th / 2) + S.DB * math.sin(3 * th / 2) + S.DC * math.sin(5 * th / 2))
+
+
+def I_sym(th):
+    return 2 * (S.IA * math.cos(th / 2) + S.IB * math.cos(3 * th / 2) + S.IC * math.cos(5 * th / 2))
+
+
+def smooth_field(shape, seed, modes=3):
+    """Sum of a few low-wavenumber sinusoids, amplitude O(1)."""
+    g = torch.Generator().manual_seed(seed)
+    nz, ny, nx = shape
+    z = torch.arange(nz, dtype=DT).reshape(nz, 1, 1) / nz
+    y = torch.arange(ny, dtype=DT).reshape(1, ny, 1) / ny
+    x = torch.arange(nx, dtype=DT).reshape(1, 1, nx) / nx
+    f = torch.zeros(shape, dtype=DT)
+    for _ in range(modes):
+        m = torch.randint(-2, 3, (3,), generator=g).to(DT)
+        ph = float(torch.rand(1, generator=g, dtype=DT)) * 2 * math.pi
+        a = float(torch.randn(1, generator=g, dtype=DT))
+        f = f + a * torch.sin(2 * math.pi * (m[0] * x + m[1] * y + m[2] * z) + ph)
+    return f / modes
+
+
+def random_state(grid: Grid, seed=0, amp_u=0.2, amp_b=0.1, solenoidal=True):
+    shape = (grid.nz, grid.ny, grid.nx)
+    r = 1.0 + 0.1 * smooth_field(shape, seed + 1)
+    E = 0.9 * (1.0 + 0.1 * smooth_field(shape, seed + 2))
+    p = [amp_u * smooth_field(shape, seed + 3 + d) for d in range(3)]
+    if solenoidal:
+        A = [amp_b * grid.dx * 5 * smooth_field(shape, seed + 10 + d) for d in range(3)]
+        Bx = S.ddup(A[2], "y", grid.dy) - S.ddup(A[1], "z", grid.dz)
+        By = S.ddup(A[0], "z", grid.dz) - S.ddup(A[2], "x", grid.dx)
+        Bz = S.ddup(A[1], "x", grid.dx) - S.ddup(A[0], "y", grid.dy)
+        B = [Bx + 0.05, By - 0.02, Bz + 0.3]
+    else:
+        B = [amp_b * smooth_field(shape, seed + 20 + d) for d in range(3)]
+    return [r, p[0], p[1], p[2], E, B[0], B[1], B[2]]
+
+
+VISC = Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=True)
+
+
+# ----------------------------------------------------------------- RK3 -------
+
+def test_rk3_third_order_amplification():
+    for z in (-0.2, -0.05, 0.03, 0.1):
+        y = S.rk3_step([torch.tensor(1.0, dtype=DT)], 1.0, lambda s: [z * s[0]])[0]
+        # Third order: R(z) = e^z - z^4/24 + ..., constants printed to 6 digits.
+        taylor3 = 1 + z + z * z / 2 + z ** 3 / 6
+        assert abs(float(y) - taylor3) < 1e-6 * abs(z)
+        assert abs(float(y) - math.exp(z)) < abs(z) ** 4 / 24 * 1.2 + 1e-6 * abs(z)
+
+
+def test_rk3_linear_system_rotation():
+    # y'' = -y as a 2-vector; one step of size h keeps |y| to O(h^4).
+    h = 0.05
+    y = [torch.tensor(1.0, dtype=DT), torch.tensor(0.0, dtype=DT)]
+    for _ in range(20):
+        y = S.rk3_step(y, h, lambda s: [s[1], -s[0]])
+    t = 20 * h
+    assert abs(float(y[0]) - math.cos(t)) < 1e-5
+    assert abs(float(y[1]) + math.sin(t)) < 1e-5
+
+
+# ---------------------------------------------------------- invariants -------
+
+def test_uniform_state_has_zero_rhs():
+    g = Grid(8, 6, 5, 0.1, 0.2, 0.3)
+    vals = (1.3, 0.2, -0.1, 0.3, 0.9, 0.1, 0.2, 0.5)
+    f = [torch.full((5, 6, 8), v, dtype=DT) for v in vals]
+    for p in (Params(), VISC, Params(nu_const=0.01)):
+        for d in S.rhs(f, g, p):
+            assert float(d.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("p", [Params(), VISC], ids=["ideal", "viscous_quench"])
+def test_conservation_and_divb(p):
+    g = Grid(12, 12, 12, 1 / 12, 1 / 12, 1 / 12)
+    f = random_state(g, seed=5)
+    divb0 = S.ddup(f[5], "x", g.dx) + S.ddup(f[6], "y", g.dy) + S.ddup(f[7], "z", g.dz)
+    assert float(divb0.abs().max()) < 1e-12
+    f1, dt = S.step(f, g, p)
+    assert 0 < dt < 1
+    m0, m1 = float(f[0].sum()), float(f1[0].sum())
+    assert abs(m1 - m0) < 1e-13 * abs(m0)
+    for d in (1, 2, 3):
+        ref = float(f[d].abs().sum())
+        assert abs(float(f1[d].sum()) - float(f[d].sum())) < 1e-13 * ref, d
+    divb1 = S.ddup(f1[5], "x", g.dx) + S.ddup(f1[6], "y", g.dy) + S.ddup(f1[7], "z", g.dz)
+    assert float((divb1 - divb0).abs().max()) < 1e-11
+
+
+def test_divb_change_zero_for_any_b():
+    # Even for a B that is not solenoidal, the curl update leaves div B unchanged.
+    g = Grid(10, 9, 8, 0.1, 0.11, 0.12)
+    f = random_state(g, seed=7, solenoidal=False)
+    F = S.rhs(f, g, VISC)
+    ddiv = S.ddup(F[5], "x", g.dx) + S.ddup(F[6], "y", g.dy) + S.ddup(F[7], "z", g.dz)
+    assert float(ddiv.abs().max()) < 1e-10
+
+
+def test_shift_symmetry_bitwise():
+    g = Grid(9, 8, 7, 0.1, 0.1, 0.1)
+    f = random_state(g, seed=3)
+    F = S.rhs(f, g, VISC)
+    for dim in (0, 1, 2):
+        Fs = S.rhs([torch.roll(x, 2, dims=dim) for x in f], g, VISC)
+        for a, b in zip(Fs, F):
+            assert torch.equal(a, torch.roll(b, 2, dims=dim))
+
+
+@pytest.mark.parametrize("p", [Params(), VISC, Params(nu_const=0.02, nuB=0.5, nuE=0.7)],
+                         ids=["ideal", "rm_quench", "const"])
+def test_cyclic_axis_permutation(p):
+    # Old axes (x, y, z) become new (y, z, x): new x is old z, etc.
+    g = Grid(8, 10, 12, 0.11, 0.09, 0.13)
+    f = random_state(g, seed=11, solenoidal=False)
+    gp = Grid(g.nz, g.nx, g.ny, g.dz, g.dx, g.dy)
+    perm = lambda t: t.permute(1, 2, 0).contiguous()
+    r, px, py, pz, E, Bx, By, Bz = [perm(t) for t in f]
+    fp = [r, pz, px, py, E, Bz, Bx, By]
+    F = [perm(t) for t in S.rhs(f, g, p)]
+    Fp = S.rhs(fp, gp, p)
+    expect = [F[0], F[3], F[1], F[2], F[4], F[7], F[5], F[6]]
+    for a, b in zip(Fp, expect):
+        scale = float(b.abs().max()) + 1e-30
+        assert float((a - b).abs().max()) < 1e-12 * scale
+
+
+def test_quasi_2d_equals_uniform_3d():
+    g2 = Grid(12, 10, 1, 0.1, 0.1, 0.1)
+    g3 = Grid(12, 10, 4, 0.1, 0.1, 0.1)
+    f2 = random_state(g2, seed=2, solenoidal=False)
+    f3 = [t.expand(4, -1, -1).contiguous() for t in f2]
+    F2 = S.rhs(f2, g2, VISC)
+    F3 = S.rhs(f3, g3, VISC)
+    for a, b in zip(F2, F3):
+        assert float((a - b[0:1]).abs().max()) <= 1e-12 * (float(a.abs().max()) + 1e-30)
+
+
+# -------------------------------------------------------- linear waves -------
+
+def _phase(v, k, z):
+    c = (v * np.exp(-1j * k * z)).sum()
+    return np.angle(c)
+
+
+def _evolve(f, g, p, dt, nsteps):
+    for _ in range(nsteps):
+        f, _ = S.step(f, g, p, dt=dt)
+    return f
+
+
+def test_sound_phase_speed():
+    n, m, a = 32, 4, 1e-8
+    g = Grid(1, 1, n, 1.0, 1.0, 1.0 / n)
+    h = g.dz
+    gam = 5.0 / 3.0
+    k = 2 * math.pi * m
+    zc = (np.arange(n) + 0.5) * h
+    zf = np.arange(n) * h
+    rho = 1 + a * np.sin(k * zc)
+    uz = a * np.sin(k * zf)
+    P = 1 / gam + a * np.sin(k * zc)
+    sh = lambda v: torch.tensor(v, dtype=DT).reshape(n, 1, 1)
+    zero = sh(np.zeros(n))
+    f = [sh(rho), zero, zero, sh(uz * 1.0), sh(P / (gam - 1)), zero, zero, zero]
+    omega = D_sym(k * h) / h
+    T, nsteps = 0.1, 125                      # omega T = 2.5 rad < pi
+    f1 = _evolve(f, g, Params(gamma=gam), T / nsteps, nsteps)
+    ph0 = _phase(rho - 1, k, zc)
+    ph1 = _phase(f1[0].reshape(-1).numpy() - 1, k, zc)
+    om = ((ph0 - ph1) % (2 * math.pi)) / T
+    assert abs(om / omega - 1) < 2e-6, (om, omega)
+    assert abs(omega / k - 1) > 1e-5          # the discrete speed differs from c_s
+
+
+def test_alfven_phase_speed():
+    n, m, a = 32, 4, 1e-8
+    g = Grid(1, 1, n, 1.0, 1.0, 1.0 / n)
+    h = g.dz
+    k = 2 * math.pi * m
+    zc = (np.arange(n) + 0.5) * h
+    b0, rho0 = 0.5, 1.0
+    ux = a * np.sin(k * zc)
+    bx = -math.sqrt(rho0) * ux
+    sh = lambda v: torch.tensor(v, dtype=DT).reshape(n, 1, 1)
+    one = sh(np.ones(n))
+    zero = sh(np.zeros(n))
+    f = [one * rho0, sh(rho0 * ux), zero, zero, one * 0.9, sh(bx), zero, one * b0]
+    omega = b0 / math.sqrt(rho0) * D_sym(k * h) * I_sym(k * h) / h
+    T, nsteps = 0.2, 125                      # omega T = 2.5 rad < pi
+    f1 = _evolve(f, g, Params(), T / nsteps, nsteps)
+    om = ((_phase(ux, k, zc) - _phase(f1[1].reshape(-1).numpy(), k, zc)) % (2 * math.pi)) / T
+    assert abs(om / omega - 1) < 2e-6, (om, omega)
+
+
+def test_viscous_shear_decay():
+    n, m, a, nu = 32, 3, 1e-7, 0.01
+    g = Grid(1, n, 1, 1.0, 1.0 / n, 1.0)
+    h = g.dy
+    k = 2 * math.pi * m
+    yc = (np.arange(n) + 0.5) * h
+    sh = lambda v: torch.tensor(v, dtype=DT).reshape(1, n, 1)
+    one = sh(np.ones(n))
+    zero = 0 * one
+    ux = a * np.sin(k * yc)
+    f = [one, sh(ux), zero, zero, one * 0.9, zero, zero, zero]
+    lam = 0.5 * nu * (D_sym(k * h) / h) ** 2
+    T, nsteps = 0.5 / lam, 200
+    f1 = _evolve(f, g, Params(nu_const=nu), T / nsteps, nsteps)
+    ratio = float((f1[1].reshape(-1).numpy() * ux).sum() / (ux * ux).sum())
+    assert abs(ratio / math.exp(-lam * T) - 1) < 2e-6
+
+
+def test_resistive_decay():
+    n, m, a, nu, nuB = 32, 2, 1e-7, 0.01, 0.5
+    g = Grid(1, n, 1, 1.0, 1.0 / n, 1.0)
+    h = g.dy
+    k = 2 * math.pi * m
+    yc = (np.arange(n) + 0.5) * h
+    sh = lambda v: torch.tensor(v, dtype=DT).reshape(1, n, 1)
+    one = sh(np.ones(n))
+    zero = 0 * one
+    bx = a * np.sin(k * yc)
+    f = [one, zero, zero, zero, one * 0.9, sh(bx), zero, zero]
+    lam = nuB * nu * (D_sym(k * h) / h) ** 2
+    T, nsteps = 0.5 / lam, 200
+    f1 = _evolve(f, g, Params(nu_const=nu, nuB=nuB), T / nsteps, nsteps)
+    ratio = float((f1[5].reshape(-1).numpy() * bx).sum() / (bx * bx).sum())
+    assert abs(ratio / math.exp(-lam * T) - 1) < 2e-6
+
+
+def test_energy_diffusion_rate():
+    n, m, a, nu, nuE = 32, 5, 1e-6, 0.02, 0.7
+    g = Grid(n, 1, 1, 1.0 / n, 1.0, 1.0)
+    h = g.dx
+    k = 2 * math.pi * m
+    xc = (np.arange(n) + 0.5) * h
+    sh = lambda v: torch.tensor(v, dtype=DT).reshape(1, 1, n)
+    one = sh(np.ones(n))
+    zero = 0 * one
+    de = a * np.sin(k * xc)
+    f = [one, zero, zero, zero, sh(0.9 + de), zero, zero, zero]
+    F = S.rhs(f, g, Params(nu_const=nu, nuE=nuE))
+    expect = -nuE * nu * (D_sym(k * h) / h) ** 2 * de
+    np.testing.assert_allclose(F[4].reshape(-1).numpy(), expect, rtol=0, atol=1e-8 * np.abs(expect).max())
+
+
+# ---------------------------------------------- quench, max3, smooth3 --------
+
+def test_quench_closed_forms():
+    p = Params(qmax=8.0, qlim=2.0)
+    x = torch.arange(16, dtype=DT).reshape(1, 1, 16)
+    lin = 0.3 + 0.0 * x                      # constant: d2 = 0 -> quenched to 0
+    assert float(S.quench(lin, "x", p).abs().max()) == 0.0
+    alt = torch.where(x % 2 == 0, 1.0, -1.0).to(DT)
+    # |d2| = 4, |T| = 1: q = 4 / (1 + 4/8) = 8/3, factor min(8/3, 2) = 2.
+    assert torch.allclose(S.quench(alt, "x", p), 2.0 * alt)
+    p2 = Params(qmax=8.0, qlim=5.0)
+    assert torch.allclose(S.quench(alt, "x", p2), (8.0 / 3.0) * alt)
+    # Along an axis where T is constant the factor is 0 unless another axis wiggles.
+    t2 = alt.expand(1, 4, 16).contiguous()
+    assert torch.allclose(S.quench(t2, "y", p), torch.zeros_like(t2))
+    assert torch.allclose(S.quench(t2, "xy", p), 2.0 * t2)
+
+
+def test_max3_smooth3_delta():
+    f = torch.zeros(5, 5, 5, dtype=DT)
+    f[2, 2, 2] = 1.0
+    m = f
+    for ax in "xyz":
+        m = S.max3(m, ax)
+    assert float(m.sum()) == 27.0 and float(m[1:4, 1:4, 1:4].min()) == 1.0
+    s = f
+    for ax in "xyz":
+        s = S.smooth3(s, ax)
+    assert float(s.sum()) == pytest.approx(1.0, abs=1e-15)
+    assert float(s[1:4, 1:4, 1:4].min()) == pytest.approx(1 / 27, abs=1e-16)
+
+
+# ---------------------------------------------------------- Courant ----------
+
+def test_courant_uniform_flow():
+    g = Grid(8, 8, 8, 0.1, 0.05, 0.2)
+    gam = 5.0 / 3.0
+    r0, P0 = 2.0, 0.6
+    u = np.array([0.3, -0.4, 0.1])
+    B = np.array([0.0, 0.6, 0.8])
+    f = [torch.full((8, 8, 8), v, dtype=DT) for v in
+         (r0, r0 * u[0], r0 * u[1], r0 * u[2], P0 / (gam - 1), B[0], B[1], B[2])]
+    cs = math.sqrt(gam * P0 / r0)
+    ca = math.sqrt((B ** 2).sum() / r0)
+    bh = B / np.linalg.norm(B)
+    uperp = np.linalg.norm(u - (u @ bh) * bh)
+    q1 = S.rhs(f, g, Params())
+    dt, (tw, tr, td) = S.courant_dt(f, q1, g, Params(gamma=gam))
+    assert tw == pytest.approx(0.4 * 0.05 / (cs + ca + uperp), rel=1e-13)
+    assert tr == math.inf and td == math.inf and dt == tw
+    p = Params(gamma=gam, nu1=0.1, nu3=0.05, nu2=1.0, nuE=1.5, nuB=0.8)
+    q1 = S.rhs(f, g, p)
+    nu = 0.1 * np.linalg.norm(u) + 0.05 * (cs + ca)
+    dt, (tw, tr, td) = S.courant_dt(f, q1, g, p)
+    assert td == pytest.approx(0.7 * 0.05 / (nu * max(1.0, 1.5, 0.8 * 0.2 / 0.05)), rel=1e-12)
+
+
+def test_courant_rate_limit():
+    g = Grid(8, 8, 8, 0.1, 0.1, 0.1)
+    f = [torch.full((8, 8, 8), v, dtype=DT) for v in (1.0, 0, 0, 0, 0.9, 0, 0, 0)]
+    q1 = [torch.zeros(8, 8, 8, dtype=DT) for _ in range(8)]
+    q1[0][3, 3, 3] = -0.5
+    q1[4][1, 1, 1] = 0.9 * 3.0
+    dt, (tw, tr, td) = S.courant_dt(f, q1, g, Params())
+    assert tr == pytest.approx(0.1 / 3.0, rel=1e-14)
+
+
+# ------------------------------------------------------- diagnostics ---------
+
+def test_diagnostics_uniform():
+    g = Grid(4, 4, 4, 0.25, 0.25, 0.25)
+    f = [torch.full((4, 4, 4), v, dtype=DT) for v in (2.0, 0.2, 0.4, 0.0, 1.5, 0.3, 0.0, 0.4)]
+    d = S.diagnostics(f, g, Params())
+    assert d[0] == pytest.approx(128.0) and d[4] == pytest.approx(96.0)
+    assert d[5] == pytest.approx(64 * 0.5 * (0.2 ** 2 + 0.4 ** 2) / 2.0)
+    assert d[6] == pytest.approx(64 * 0.5 * (0.09 + 0.16))
+    assert d[7] == 0.0 and d[9] == 0.0
+
+
+# ----------------------------------------------------------- adjoint ---------
+
+@pytest.mark.parametrize("p", [Params(), VISC], ids=["ideal", "viscous_quench"])
+def test_adjoint_matches_central_differences(p):
+    g = Grid(8, 8, 8, 1 / 8, 1 / 8, 1 / 8)
+    f = random_state(g, seed=21)
+    dt = 2e-3
+    gen = torch.Generator().manual_seed(99)
+    w = [torch.randn(8, 8, 8, generator=gen, dtype=DT) for _ in range(8)]
+    lam = S.step_adjoint(f, dt, w, g, p)
+
+    def loss(state):
+        out, _ = S.step(state, g, p, dt=dt)
+        return sum(float((o * wi).sum()) for o, wi in zip(out, w))
+
+    for d in range(3):
+        v = [torch.randn(8, 8, 8, generator=gen, dtype=DT) for _ in range(8)]
+        scale = [0.1, 0.05, 0.05, 0.05, 0.1, 0.02, 0.02, 0.02]
+        v = [vi * s for vi, s in zip(v, scale)]
+        eps = 1e-6
+        fp = [a + eps * b for a, b in zip(f, v)]
+        fm = [a - eps * b for a, b in zip(f, v)]
+        fd = (loss(fp) - loss(fm)) / (2 * eps)
+        an = sum(float((l * vi).sum()) for l, vi in zip(lam, v))
+        assert abs(fd - an) < 1e-6 * abs(an), (d, fd, an)
+
+
+# ------------------------- instantaneous closed forms, every component -------
+
+def _line_state(n, ax, h, other=4):
+    """Grid with n cells along ax (spacing h) and ``other`` uniform cells
+    along the other axes, plus coordinate arrays at centres and faces."""
+    sizes = {a: (n if a == ax else other) for a in "xyz"}
+    sp = {a: (h if a == ax else 0.37) for a in "xyz"}
+    g = Grid(sizes["x"], sizes["y"], sizes["z"], sp["x"], sp["y"], sp["z"])
+    shape = (g.nz, g.ny, g.nx)
+    idx = torch.arange(n, dtype=DT)
+    view = {"x": (1, 1, n), "y": (1, n, 1), "z": (n, 1, 1)}[ax]
+    c = ((idx + 0.5) * h).reshape(view).expand(shape)
+    f = (idx * h).reshape(view).expand(shape)
+    return g, shape, c, f
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("a", [0, 1, 2])
+def test_shear_and_resistive_rates_all_pairs(d, a):
+    if d == a:
+        pytest.skip("longitudinal case tested separately")
+    n, m, amp, nu, nuB = 24, 3, 1e-9, 0.01, 0.6
+    ax = "xyz"[a]
+    h = 1.0 / n
+    g, shape, xc, _ = _line_state(n, ax, h)
+    k = 2 * math.pi * m
+    wave = amp * torch.sin(k * xc)            # component d lives at the d-face: centre along a
+    one = torch.ones(shape, dtype=DT)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = wave.clone()
+    F = S.rhs(f, g, Params(nu_const=nu, nuB=nuB))
+    lam = 0.5 * nu * (D_sym(k * h) / h) ** 2
+    assert torch.allclose(F[1 + d], -lam * wave, rtol=0, atol=1e-6 * lam * amp)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[5 + d] = wave.clone()
+    F = S.rhs(f, g, Params(nu_const=nu, nuB=nuB))
+    lam = nuB * nu * (D_sym(k * h) / h) ** 2
+    assert torch.allclose(F[5 + d], -lam * wave, rtol=0, atol=1e-6 * lam * amp)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("c1", [0.0, -1.0 / 3.0])
+def test_longitudinal_viscous_rate(d, c1):
+    # amp between the rounding of the O(1) pressure inside T_dd and the O(amp^2)
+    # advection term.
+    n, m, amp, nu = 24, 2, 1e-8, 0.01
+    ax = "xyz"[d]
+    h = 1.0 / n
+    g, shape, _, xf = _line_state(n, ax, h)
+    k = 2 * math.pi * m
+    wave = amp * torch.sin(k * xf)            # u_d on its own face
+    one = torch.ones(shape, dtype=DT)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = wave.clone()
+    F = S.rhs(f, g, Params(nu_const=nu, c1=c1))
+    lam = nu * (1 + c1) * (D_sym(k * h) / h) ** 2
+    assert torch.allclose(F[1 + d], -lam * wave, rtol=0, atol=1e-5 * lam * amp)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_contact_advection(d):
+    # Uniform flow U along axis d, uniform P, small density wave: to first order
+    # d rho/dt = -U D I/h rho'(shifted), d p_d/dt = -U^2 D I^2/h (...), dE/dt = 0.
+    n, m, amp, U = 24, 2, 1e-8, 0.3
+    ax = "xyz"[d]
+    h = 1.0 / n
+    g, shape, xc, xf = _line_state(n, ax, h)
+    k = 2 * math.pi * m
+    th = k * h
+    one = torch.ones(shape, dtype=DT)
+    rho_c = 1.0 + amp * torch.sin(k * xc)
+    rho_f = torch.exp(S.dn(torch.log(rho_c), ax))
+    f = [rho_c, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = rho_f * U
+    F = S.rhs(f, g, Params())
+    DI = D_sym(th) * I_sym(th) / h
+    expect_r = -U * DI * amp * torch.cos(k * xc)
+    assert torch.allclose(F[0], expect_r, rtol=0, atol=1e-6 * U * DI * amp)
+    expect_p = -U * U * DI * I_sym(th) * amp * torch.cos(k * xf)
+    assert torch.allclose(F[1 + d], expect_p, rtol=0, atol=1e-6 * U * U * DI * amp)
+    assert float(F[4].abs().max()) < 1e-6 * U * DI * amp
+
+
+def test_rm_viscosity_value_and_edge_scale():
+    # Compressive 1D flow, only the shock term: nu = nu2 dl_min max(0, -div u).
+    n, m, amp = 24, 2, 1e-3
+    h = 1.0 / n
+    g, shape, xc, xf = _line_state(n, "x", h)
+    k = 2 * math.pi * m
+    one = torch.ones(shape, dtype=DT)
+    ux = amp * torch.sin(k * xf)
+    rx = torch.exp(S.dn(torch.log(one), "x"))
+    f = [one, ux * rx, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    parts = S.rhs_parts(f, g, Params(nu2=1.3))
+    divu = amp * D_sym(k * h) / h * torch.cos(k * xc)
+    expect = 1.3 * g.dl_min * torch.clamp(-divu, min=0.0)
+    assert torch.allclose(parts["nu_raw"], expect, rtol=0, atol=1e-12)
+    # Uniform RM nu from the wave-speed term; shear rate uses max(dx, dy).
+    n = 24
+    gy = Grid(4, n, 1, 2.5 / n, 1.0 / n, 1.0)
+    shape = (1, n, 4)
+    one = torch.ones(shape, dtype=DT)
+    yc = ((torch.arange(n, dtype=DT) + 0.5) / n).reshape(1, n, 1).expand(shape)
+    ky = 2 * math.pi * 3
+    amp = 1e-8
+    wave = amp * torch.sin(ky * yc)
+    P0, B0, gam = 0.6, 0.4, 5.0 / 3.0
+    f = [one, wave.clone(), 0 * one, 0 * one, P0 / (gam - 1) * one, 0 * one, 0 * one, B0 * one]
+    p = Params(nu3=0.05)
+    nu_c = 0.05 * (math.sqrt(gam * P0) + B0)
+    F = S.rhs(f, gy, p)
+    lam = 0.5 * max(gy.dx, gy.dy) * nu_c * (D_sym(ky / n) * n) ** 2
+    assert torch.allclose(F[1], -lam * wave, rtol=0, atol=1e-6 * lam * amp)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("a", [0, 1, 2])
+def test_viscous_and_joule_heating_closed_form(d, a):
+    # Shear wave u_d(x_a): Q_visc = 2 up up(rho nu S_da^2) with S_da = 1/2 dd u_d,
+    # exactly 1/2 rho nu amp^2 (D/h)^2 (1/2 + 1/2 I(2 th) cos(2 k x)); with a
+    # sheared B_d(x_a) instead, Joule heating eta up up(J^2) is twice that with
+    # nu -> eta.  No other term of dE/dt is nonzero for these states.
+    if d == a:
+        pytest.skip("needs a shear")
+    n, m, amp, nu, nuB = 24, 3, 1e-2, 0.01, 0.6
+    ax = "xyz"[a]
+    h = 1.0 / n
+    g, shape, xc, _ = _line_state(n, ax, h)
+    k = 2 * math.pi * m
+    th = k * h
+    one = torch.ones(shape, dtype=DT)
+    shape_fn = 0.5 + 0.5 * I_sym(2 * th) * torch.cos(2 * k * xc)
+    base = amp * amp * (D_sym(th) / h) ** 2
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = amp * torch.sin(k * xc)
+    F = S.rhs(f, g, Params(nu_const=nu, nuB=nuB))
+    assert torch.allclose(F[4], 0.5 * nu * base * shape_fn, rtol=1e-10, atol=1e-14)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[5 + d] = amp * torch.sin(k * xc)
+    F = S.rhs(f, g, Params(nu_const=nu, nuB=nuB))
+    assert torch.allclose(F[4], nuB * nu * base * shape_fn, rtol=1e-10, atol=1e-14)
