@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the staggered-mesh MHD step on GB300.
+
+Workload: compressible MHD turbulence in a periodic 512^3 box (gamma 5/3,
+rho 1, P 1/gamma, B0 = 0.3 z, Gaussian random solenoidal velocity with
+E(k) ~ k^-2 for 1 <= k <= 4 at rms Mach 0.5), Richtmyer-Morton shock
+viscosity, energy diffusion, resistivity and quenching on, FP32 storage and
+arithmetic, Courant time step computed on the device every step.  A "step" is
+one full low-storage RK3 step (three right-hand-side evaluations).
+
+Prints one JSON line.  `value` is zone-updates/s over the whole job with the
+state resident in HBM; `e2e` repeats the measurement through the host-memory
+entry point (copies included); `roofline` reports the dominant kernel's
+algorithmic HBM bytes per launch over its CUDA-event time; `cpu_baseline`
+times the FP64 CPU oracle on a bounded sample of the same workload.
+
+--impl reference times that CPU oracle alone (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per full MHD step (FP32) at 512^3 + % HBM roofline; adjoint step cost"
+UNIT = "zone-updates/s"
+PHYS = dict(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=1)
+STEP_BYTES_PER_ZONE = 288       # minimal HBM bytes per zone per RK3 step (8 FP32 fields, 2N storage)
+CPU_SAMPLE_N = 128              # oracle sample grid (cells per axis)
+CPU_SAMPLE_SECONDS = 12.0       # run oracle steps until this much host time is spent
+CPU_SAMPLE_MAX_STEPS = 30
+REF_N = 96                      # per-step sample grid of the reference (oracle) arm
+
+# Distinct FP32 arrays each fused kernel reads + writes per launch (its
+# algorithmic HBM traffic: every array touched once), for the viscous,
+# quenched workload.  k_div: stage 1 (Courant) reads 25 and writes 8;
+# stages 2 and 3 read 38 (fluxes, state, previous dfdt) and write 16.
+KERNEL_ARRAYS = {"k_lr": 2, "k_vel": 7, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
+                 "k_tau": 22, "k_edge": 31, "k_flux": 44, "k_div": (33 + 54 + 54) / 3.0,
+                 "k_update": 3}
+# DRAM bytes per launch from the ncu capture summarised in profiles/ (None
+# until taken for the current kernels).
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n=CPU_SAMPLE_N, seconds=CPU_SAMPLE_SECONDS, max_steps=CPU_SAMPLE_MAX_STEPS):
+    """FP64 oracle, as it stands, on the host cores: Courant RK3 steps of the
+    same physics and initial-condition recipe on an n^3 box, until `seconds`
+    of host time (at least one step)."""
+    import torch
+
+    import oracle
+    from paper_2405_02483_gb300 import inputs
+    w = inputs.turbulence(n)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    p = oracle.Params(**{k: (bool(v) if k == "do_quench" else v) for k, v in PHYS.items()})
+    f = [torch.tensor(a) for a in w.fields]
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        f, _ = oracle.step(f, g, p)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    t = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / t, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": "%d Courant RK3 steps of the same physics and initial-condition recipe "
+                      "on a %d^3 periodic box (FP64, whole-array torch CPU ops), %.1f s" % (steps, n, t)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    n = REF_N
+    steps_per = 1
+    import oracle
+    from paper_2405_02483_gb300 import inputs
+    w = inputs.turbulence(n)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    p = oracle.Params(**{k: (bool(v) if k == "do_quench" else v) for k, v in PHYS.items()})
+    f = [torch.tensor(a) for a in w.fields]
+    for _ in range(args.warmup):
+        f, _ = oracle.step(f, g, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, _ = oracle.step(f, g, p)
+    t = time.perf_counter() - t0
+    v = n ** 3 * args.steps * steps_per / t
+    sample = ("each step one Courant RK3 step of the 512^3 workload's physics and initial-"
+              "condition recipe on a %d^3 box (FP64 oracle, whole-array torch CPU ops)" % n)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "MHD turbulence, %d^3 sample of the 512^3 workload" % n,
+                      "grid": [n, n, n], "parallelism": "host cores"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2405_02483_gb300 as S
+    from paper_2405_02483_gb300 import inputs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    w = inputs.turbulence(n, device="cuda")
+    refs, dev = S.split_state(w.fields)
+    del w
+    params = S.default_params(ref=refs, **PHYS)
+    sim = S.Sim((n, n, n), (1.0 / n,) * 3, params)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        sim.step(dev, None)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    sim.timing(True)
+    l0 = sim.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(dev, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launches() - l0
+    ktimes = sim.kernel_times()
+    sim.timing(False)
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * n ** 3 * args.steps / (ms * 1e-3)
+
+    # Dominant kernel roofline (algorithmic bytes per launch / mean launch time).
+    peak, peak_kind = peaks()
+    top = max(ktimes.items(), key=lambda kv: kv[1][0])
+    kname, (kms, kcnt) = top
+    kbytes = KERNEL_ARRAYS.get(kname, 0) * 4.0 * n ** 3
+    kavg = kms / kcnt
+    achieved = kbytes / (kavg * 1e-3) / 1e9
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "bytes_per_launch": kbytes, "ms_per_launch": kavg,
+            "traffic": NCU_TRAFFIC.get(kname)}
+    step_gbs = STEP_BYTES_PER_ZONE * (value / ws) / 1e9
+    step_roof = {"bytes_per_zone": STEP_BYTES_PER_ZONE, "achieved": step_gbs, "peak": peak,
+                 "unit": "GB/s", "frac": step_gbs / peak}
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
+                   "share": v[0] / sum(x[0] for x in ktimes.values())}
+               for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])}
+
+    # End to end through the host-memory entry point (copies inside).
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(sim, dev, args.e2e_steps, ws, n)
+
+    out = {"metric": METRIC
+, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "MHD turbulence %d^3, RM viscosity + quench, Courant dt" % n,
+                      "grid": [n, n, n], "l2": "inputs larger than L2 (state %.1f GiB)"
+                      % (8 * 4 * n ** 3 / 2 ** 30),
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+
+    if rank == 0 and not args.no_adjoint:
+        out["adjoint"] = adjoint_cost(S, torch)
+    sim.close()
+    del dev
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(sim, dev, steps, ws, n):
+    """Same metric through stagger_step_host: every step copies the 8 state
+    arrays from pinned host memory to the device, steps, and copies them back."""
+    import torch
+    host = [t.cpu().pin_memory() for t in dev]
+    sim.step_host(host, 1, None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step_host(host, 1, None)
+    te = time.perf_counter() - t0
+    nbytes = 8 * 4 * n ** 3
+    return {"value": ws * n ** 3 * steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
+
+
+def adjoint_cost(S, torch, n=128, reps=3):
+    """Adjoint step cost: the FP32 adjoint of one fixed-dt step (stage
+    recompute and reverse sweep included) over one forward step, on the
+    Orszag-Tang 128^3 workload with the same physics."""
+    from paper_2405_02483_gb300 import inputs
+    w = inputs.orszag_tang_3d(n)
+    refs, dev = S.split_state(w.fields)
+    sim = S.Sim((n, n, n), (1.0 / n,) * 3, S.default_params(ref=refs, **PHYS))
+    dt = sim.courant(dev)[0]
+    lam = [torch.randn_like(t) for t in dev]
+    st = [t.clone() for t in dev]
+    sim.step(st, dt)
+    sim.step_adjoint(dev, dt, lam)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(reps):
+        sim.step(st, dt)
+    e[1].record()
+    for _ in range(reps):
+        sim.step_adjoint(dev, dt, lam)
+    e[2].record()
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1]) / reps
+    adj = e[1].elapsed_time(e[2]) / reps
+    sim.close()
+    return {"workload": "Orszag-Tang 3D %d^3, same physics" % n, "ms_forward_step": fwd,
+            "ms_adjoint_step": adj, "ratio": adj / fwd}
+
+
+if __name__ == "__main__":
+    main()

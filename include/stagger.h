@@ -1,0 +1,177 @@
+/*
+ * stagger.h - C ABI of libstagger, a GB300 (sm_103a) implementation of the
+ * per-timestep right-hand side and low-storage RK3 step of the Stagger Code's
+ * compressible MHD method (Stein, Nordlund, Collet & Trampedach, "The Stagger
+ * Code for Accurate and Efficient, Radiation-Coupled MHD Simulations").
+ *
+ * Mesh and layout (Sect. "Centering"): a periodic nx*ny*nz box.  Every field
+ * is one contiguous array of nx*ny*nz values indexed [k][j][i], x fastest.
+ * rho and E (internal energy per volume, rho*e) sit at cell centres; the
+ * momenta p = rho u and the magnetic field B on the lower cell faces
+ * (px, Bx at (i-1/2, j, k), etc.).
+ *
+ * State: eight fields in the fixed order r, px, py, pz, E, Bx, By, Bz.  Each
+ * is stored as an FP32 DEVIATION from a per-field FP64 constant ref[k]
+ * (stagger_params.ref): the value used in the equations is ref[k] + stored.
+ * Derivatives annihilate constants, so this is exact algebra; it keeps FP32
+ * resolution for small perturbations on large backgrounds.
+ *
+ * Pointers: "device" arrays are caller-owned CUDA device memory of at least
+ * nx*ny*nz floats (4-byte aligned); the library never frees them.  "host"
+ * arrays are caller-owned host memory.  stream is a cudaStream_t passed as
+ * void*; NULL means the legacy default stream.  Unless stated, calls are
+ * asynchronous on that stream and return after enqueueing.
+ *
+ * Errors: every function returns STAGGER_OK (0) or a negative status and
+ * never aborts or throws.  stagger_strerror() names a status.  A context is
+ * not thread-safe: serialise calls that share one.
+ */
+#ifndef STAGGER_H
+#define STAGGER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STAGGER_OK = 0,
+  STAGGER_EINVAL = -1,      /* bad argument (NULL pointer, size, parameter)   */
+  STAGGER_ECUDA = -2,       /* a CUDA runtime call failed                      */
+  STAGGER_ENONFINITE = -3,  /* the state holds NaN/Inf (diagnostics, Courant)  */
+  STAGGER_EOOM = -4,        /* device allocation failed                        */
+  STAGGER_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up         */
+  STAGGER_EUNSUPPORTED = -6 /* feature not built (e.g. precision 64 path)      */
+};
+
+typedef struct stagger_ctx stagger_ctx;  /* opaque, library-owned */
+
+typedef struct {
+  int nx, ny, nz;          /* cells per axis, each >= 1; all axes periodic     */
+  double dx, dy, dz;       /* uniform spacings, > 0                            */
+} stagger_grid;
+
+typedef struct {
+  double gamma;            /* ideal-gas gamma, P = (gamma-1) E (&pde gamma)    */
+  /* Richtmyer & Morton viscosity, eq. (RMnu): nu = nu1|u| + nu3 (c_s + c_A)
+   * + nu2 dl_min max(0, -div u), spread by a 3-cell max and a 3-cell mean,
+   * then nu_ii = dx_i <nu>, nu_ij = max(dx_i, dx_j) exp(interp ln<nu>),
+   * eq. (nuij).  All zero and nu_const == 0 gives ideal MHD.                 */
+  double nu1, nu2, nu3;
+  double nu_const;         /* > 0: constant viscosity nu_ij = nu_const instead */
+  double nuE;              /* energy diffusion factor, eq. (ediffuse)          */
+  double nuB;              /* resistivity eta = nuB * nu (edge), eq. (ohm)     */
+  double c1;               /* bulk term of eq. (itv); 0 typical                */
+  int do_quench;           /* 1: quench stresses and eta J, eq. (quench)       */
+  double qmax, qlim;       /* quench limits (&quench; 8 and 2)                 */
+  int log_interp;          /* 1: rho to faces/edges as exp(interp ln rho)      */
+  double Cdt, Cdtr, Cdtd;  /* Courant factors, eq. (courantcond) (0.4,0.1,0.7)*/
+  double g[3];             /* constant gravity; source rho_face * g            */
+  double ref[8];           /* per-field background added to the stored values */
+} stagger_params;
+
+/* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
+ * nuE = nuB = 1, qmax 8, qlim 2, log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
+ * no gravity, zero references.  Returns STAGGER_EINVAL if p is NULL. */
+int stagger_params_default(stagger_params* p);
+
+/* Create a context for one grid and parameter set on the current CUDA device.
+ * Allocates all device scratch once (about 30 fields of nx*ny*nz floats for
+ * the fused step; more on the first adjoint call).  *out receives the handle.
+ * Errors: EINVAL (bad grid/params/NULL), EOOM, ECUDA. */
+int stagger_create(const stagger_grid* grid, const stagger_params* params,
+                   stagger_ctx** out);
+
+/* Release a context and all its device memory (synchronises the device).
+ * NULL is accepted.  Returns OK or ECUDA. */
+int stagger_destroy(stagger_ctx* ctx);
+
+/* F(f): the eight time derivatives of eqs. (mass), (mom), (ien), (indu)
+ * at the state, written to dfdt (8 device arrays, NOT deviations: the plain
+ * derivative values).  state and dfdt must not overlap.  Async. */
+int stagger_rhs(stagger_ctx* ctx, float* const state[8], float* dfdt[8], void* stream);
+
+/* One full low-storage RK3 step, eqs. (ddt), (tupdate), (tconst), updating
+ * the 8 device arrays of state in place.  dt > 0: that step; dt <= 0: the
+ * Courant step of eq. (courantcond), taken from the state and its stage-1
+ * derivative and held for all three stages (computed on the device; no host
+ * synchronisation).  If dt_used is not NULL it is a HOST pointer: the call
+ * then synchronises the stream and stores the step used.  Async otherwise. */
+int stagger_step(stagger_ctx* ctx, float* state[8], double dt, double* dt_used, void* stream);
+
+/* Run nsteps steps as stagger_step does, with dt <= 0 meaning Courant. */
+int stagger_run(stagger_ctx* ctx, float* state[8], int nsteps, double dt, void* stream);
+
+/* The Courant step of eq. (courantcond) for this state (FP64 reduction on the
+ * device).  Synchronises; *dt_host receives it, limits[3] (may be NULL) the
+ * wave-speed, rate-of-change and diffusion limits (HUGE_VAL when inactive).
+ * Returns ENONFINITE if the state produced a non-finite limit. */
+int stagger_courant(stagger_ctx* ctx, float* const state[8], double* dt_host,
+                    double limits[3], void* stream);
+
+/* FP64 diagnostics of the state (plain sums over cells): out[0..9] =
+ * sum r, sum px, sum py, sum pz, sum E, sum 1/2 p.u (faces), sum 1/2 B^2,
+ * max |div B|, rms div B (div B = sum_i ddup_i B_i at centres), count of
+ * non-finite values.  Values include the refs.  Synchronises.  Returns
+ * ENONFINITE (after filling out) if the count is nonzero. */
+int stagger_diagnostics(stagger_ctx* ctx, float* const state[8], double out[10], void* stream);
+
+/* Adjoint of one fixed-dt step (vector-Jacobian product): given the step's
+ * input state_n (deviations, as passed to stagger_step), its dt > 0 and the
+ * cotangent lam_np1 of the output state, write the cotangent of the input
+ * state to lam_n (8 device arrays, may alias lam_np1).  Recomputes the stage
+ * states, then reverses the RK3 recurrence and the right-hand side.  The
+ * first call allocates the reverse-sweep workspace (about 3 x the number of
+ * graph nodes x nx*ny*nz floats).  Async. */
+int stagger_step_adjoint(stagger_ctx* ctx, float* const state_n[8], double dt,
+                         float* const lam_np1[8], float* lam_n[8], void* stream);
+
+/* Unfused evaluation of the same right-hand side: the equations as a graph
+ * of primitive staggered operations (eqs. (deriv), (interp) and pointwise
+ * arithmetic), one launch per operation.  It is the forward of the adjoint's
+ * reverse sweep and a cross-check of the fused path.  The first call
+ * allocates one array of nx*ny*nz values per graph node (a few hundred).
+ * _f64 variants take FP64 device arrays (deviations, as above) and compute
+ * in FP64.  Async. */
+int stagger_rhs_unfused(stagger_ctx* ctx, float* const state[8], float* dfdt[8], void* stream);
+int stagger_rhs_unfused_f64(stagger_ctx* ctx, double* const state[8], double* dfdt[8],
+                            void* stream);
+/* One fixed-dt (dt > 0) RK3 step through the unfused graph in FP64, in place. */
+int stagger_step_unfused_f64(stagger_ctx* ctx, double* state[8], double dt, void* stream);
+/* stagger_step_adjoint in FP64 (FP64 device arrays). */
+int stagger_step_adjoint_f64(stagger_ctx* ctx, double* const state_n[8], double dt,
+                             double* const lam_np1[8], double* lam_n[8], void* stream);
+
+/* End-to-end step through host memory: copies the 8 HOST arrays (pinned
+ * recommended) to a library-owned device state, runs nsteps steps (dt <= 0:
+ * Courant), and copies the result back into the same host arrays.
+ * Synchronises.  The device copy is allocated on the first call. */
+int stagger_step_host(stagger_ctx* ctx, float* state_host[8], int nsteps, double dt,
+                      void* stream);
+
+/* Per-kernel timing of the fused path with CUDA events recorded on the
+ * launch stream around each launch.  on != 0 enables it (and clears the
+ * totals), 0 disables it.  Returns OK or EINVAL. */
+int stagger_timing(stagger_ctx* ctx, int on);
+
+/* Collect the timing events (synchronises the stream) and report, for up to
+ * max kernel kinds, the kernel name (static string), the summed device time
+ * in milliseconds and the number of timed launches.  Any output array may be
+ * NULL.  Returns the number of kernel kinds (>= 0) or a negative status. */
+int stagger_kernel_times(stagger_ctx* ctx, int max, const char** names, double* total_ms,
+                         long long* launches, void* stream);
+
+/* Number of cells nx*ny*nz of the context's grid (0 for NULL). */
+size_t stagger_cells(const stagger_ctx* ctx);
+
+/* Count of this library's kernels launched on ctx since creation. */
+long long stagger_launch_count(const stagger_ctx* ctx);
+
+/* Short English description of a status code (static storage). */
+const char* stagger_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAGGER_H */

@@ -22,7 +22,8 @@ path by specification only, never by code):
   R6  energy diffusion flux nuE * dn(rho nu_ii) * dd_dn(e);
   R7  resistivity eta on an edge = nuB * nu of that edge;
   R8  quench: one quenched value per stress / eta J component, the factor
-      taken over the directions in which that component is differentiated;
+      taken over the directions in which that component is differentiated,
+      the ratio's |T| taken as the 3-cell max of |T| along each direction;
   R9  Courant step from the stage-1 right-hand side, held for all stages;
   R10 RK constants exactly as printed;
   R13 axes with n = 1 are skipped in dl_min, dl_max, and take dl_min as their
@@ -152,12 +153,15 @@ def smooth3(f, ax):
 
 def quench(T, dirs, p: Params):
     """Quenching of a stress-like component, eq. (quench), reading R8:
-    q = |d2 T| / (|T| + |d2 T|/qmax), T <- T * min(max_d max3_d(q_d), qlim)."""
+    q = |d2 T| / (M + |d2 T|/qmax) with M the 3-cell max of |T| along the
+    same axis, T <- T * min(max_d max3_d(q_d), qlim).  (With the point value
+    |T| the ratio is 0/0 where T vanishes by symmetry on a grid point, and the
+    quenched stress of the neighbours then depends on roundoff.)"""
     fac = None
     for ax in dirs:
         d2 = _s(T, ax, 1) - 2.0 * T + _s(T, ax, -1)
         a2 = torch.abs(d2)
-        q = a2 / (torch.abs(T) + a2 / p.qmax + Q_EPS)
+        q = a2 / (max3(torch.abs(T), ax) + a2 / p.qmax + Q_EPS)
         m = max3(q, ax)
         fac = m if fac is None else torch.maximum(fac, m)
     return T * torch.clamp(fac, max=p.qlim)

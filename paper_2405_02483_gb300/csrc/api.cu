@@ -1,0 +1,383 @@
+// C ABI of libstagger (declared in include/stagger.h).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "fused.cuh"
+#include "graph.cuh"
+
+using namespace stg;
+
+struct stagger_ctx {
+  stagger_grid grid;
+  stagger_params params;
+  Geo geo;
+  Fused fused;
+  GraphDef gdef;
+  GraphExec<float>* g32 = nullptr;
+  GraphExec<double>* g64 = nullptr;
+  float* w32 = nullptr;    // adjoint workspace: f1, f2, q, fbar, qbar (8 each)
+  double* w64 = nullptr;
+  float* host_state = nullptr;  // device copy for stagger_step_host
+  long long extra_launches = 0;
+};
+
+extern "C" {
+
+int stagger_params_default(stagger_params* p) {
+  if (!p) return STAGGER_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->gamma = 5.0 / 3.0;
+  p->nuE = 1.0;
+  p->nuB = 1.0;
+  p->qmax = 8.0;
+  p->qlim = 2.0;
+  p->log_interp = 1;
+  p->Cdt = 0.4;
+  p->Cdtr = 0.1;
+  p->Cdtd = 0.7;
+  return STAGGER_OK;
+}
+
+const char* stagger_strerror(int s) {
+  switch (s) {
+    case STAGGER_OK: return "ok";
+    case STAGGER_EINVAL: return "invalid argument";
+    case STAGGER_ECUDA: return "CUDA runtime error";
+    case STAGGER_ENONFINITE: return "non-finite value in the state";
+    case STAGGER_EOOM: return "device memory allocation failed";
+    case STAGGER_ETIMEOUT: return "bounded device wait timed out";
+    case STAGGER_EUNSUPPORTED: return "unsupported feature";
+    default: return "unknown status";
+  }
+}
+
+static int validate(const stagger_grid* g, const stagger_params* p) {
+  if (!g || !p) return STAGGER_EINVAL;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return STAGGER_EINVAL;
+  if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return STAGGER_EINVAL;
+  long long n = (long long)g->nx * g->ny * g->nz;
+  if (n >= (1LL << 31)) return STAGGER_EINVAL;  // 32-bit cell offsets in the kernels
+  if (!(p->gamma > 1.0)) return STAGGER_EINVAL;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu3 < 0 || p->nu_const < 0 || p->nuE < 0 || p->nuB < 0)
+    return STAGGER_EINVAL;
+  if (p->do_quench && (!(p->qmax > 0) || !(p->qlim > 0))) return STAGGER_EINVAL;
+  if (!(p->Cdt > 0) || !(p->Cdtr > 0) || !(p->Cdtd > 0)) return STAGGER_EINVAL;
+  if (p->ref[0] < 0) return STAGGER_EINVAL;
+  for (int k = 0; k < 8; ++k)
+    if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
+  return STAGGER_OK;
+}
+
+int stagger_create(const stagger_grid* grid, const stagger_params* params, stagger_ctx** out) {
+  if (!out) return STAGGER_EINVAL;
+  *out = nullptr;
+  int rc = validate(grid, params);
+  if (rc) return rc;
+  stagger_ctx* c = new (std::nothrow) stagger_ctx();
+  if (!c) return STAGGER_EOOM;
+  c->grid = *grid;
+  c->params = *params;
+  c->geo = make_geo(grid->nx, grid->ny, grid->nz);
+  rc = fused_init(c->fused, *grid, *params);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  build_rhs_graph(c->gdef, *grid, *params);
+  *out = c;
+  return STAGGER_OK;
+}
+
+int stagger_destroy(stagger_ctx* c) {
+  if (!c) return STAGGER_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  fused_release(c->fused);
+  if (c->g32) { c->g32->release(); delete c->g32; }
+  if (c->g64) { c->g64->release(); delete c->g64; }
+  if (c->w32) cudaFree(c->w32);
+  if (c->w64) cudaFree(c->w64);
+  if (c->host_state) cudaFree(c->host_state);
+  delete c;
+  return e == cudaSuccess ? STAGGER_OK : STAGGER_ECUDA;
+}
+
+size_t stagger_cells(const stagger_ctx* c) { return c ? (size_t)c->geo.n : 0; }
+
+long long stagger_launch_count(const stagger_ctx* c) {
+  if (!c) return 0;
+  long long n = c->fused.launches + c->extra_launches;
+  if (c->g32) n += c->g32->launches;
+  if (c->g64) n += c->g64->launches;
+  return n;
+}
+
+static bool ptrs_ok(void* const* a) {
+  if (!a) return false;
+  for (int k = 0; k < 8; ++k)
+    if (!a[k]) return false;
+  return true;
+}
+
+int stagger_rhs(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
+  return fused_rhs(c->fused, state, dfdt, (cudaStream_t)stream);
+}
+
+int stagger_step(stagger_ctx* c, float* state[8], double dt, double* dt_used, void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !(dt == dt)) return STAGGER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = fused_step(c->fused, state, dt, s);
+  if (rc) return rc;
+  if (dt_used) {
+    double h;
+    STG_CUDA_OK(cudaMemcpyAsync(&h, c->fused.dt_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    STG_CUDA_OK(cudaStreamSynchronize(s));
+    *dt_used = h;
+  }
+  return STAGGER_OK;
+}
+
+int stagger_run(stagger_ctx* c, float* state[8], int nsteps, double dt, void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || nsteps < 0 || !(dt == dt)) return STAGGER_EINVAL;
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = fused_step(c->fused, state, dt, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
+  return STAGGER_OK;
+}
+
+int stagger_timing(stagger_ctx* c, int on) {
+  if (!c) return STAGGER_EINVAL;
+  if (on && !c->fused.timing)
+    for (int i = 0; i < K_COUNT; ++i) { c->fused.kt_ms[i] = 0; c->fused.kt_n[i] = 0; }
+  fused_timing(c->fused, on ? 1 : 0);
+  return STAGGER_OK;
+}
+
+int stagger_kernel_times(stagger_ctx* c, int max, const char** names, double* total_ms,
+                         long long* launches, void* stream) {
+  if (!c || max < 0) return STAGGER_EINVAL;
+  int rc = fused_collect(c->fused, (cudaStream_t)stream);
+  if (rc) return rc;
+  for (int i = 0; i < K_COUNT && i < max; ++i) {
+    if (names) names[i] = KNAMES[i];
+    if (total_ms) total_ms[i] = c->fused.kt_ms[i];
+    if (launches) launches[i] = c->fused.kt_n[i];
+  }
+  return K_COUNT;
+}
+
+int stagger_courant(stagger_ctx* c, float* const state[8], double* dt_host, double limits[3],
+                    void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !dt_host) return STAGGER_EINVAL;
+  return fused_courant(c->fused, state, limits, dt_host, (cudaStream_t)stream);
+}
+
+int stagger_diagnostics(stagger_ctx* c, float* const state[8], double out[10], void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !out) return STAGGER_EINVAL;
+  return fused_diagnostics(c->fused, state, c->params, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Unfused graph path and the adjoint step.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lin2(T* o, const T* x, double a, const T* y, double b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = (T)a * x[i] + (T)b * y[i];
+}
+template <typename T>
+__global__ void k_copy(T* o, const T* x, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = x[i];
+}
+
+template <typename T> GraphExec<T>*& graph_of(stagger_ctx* c);
+template <> GraphExec<float>*& graph_of<float>(stagger_ctx* c) { return c->g32; }
+template <> GraphExec<double>*& graph_of<double>(stagger_ctx* c) { return c->g64; }
+template <typename T> T*& work_of(stagger_ctx* c);
+template <> float*& work_of<float>(stagger_ctx* c) { return c->w32; }
+template <> double*& work_of<double>(stagger_ctx* c) { return c->w64; }
+
+template <typename T>
+static int ensure_graph(stagger_ctx* c, bool grads) {
+  GraphExec<T>*& G = graph_of<T>(c);
+  if (G && (!grads || G->grads)) return STAGGER_OK;
+  if (!G) {
+    G = new (std::nothrow) GraphExec<T>();
+    if (!G) return STAGGER_EOOM;
+  }
+  return G->init(c->gdef, c->geo, grads);
+}
+
+template <typename T>
+static int ensure_work(stagger_ctx* c) {
+  T*& w = work_of<T>(c);
+  if (w) return STAGGER_OK;
+  if (cudaMalloc(&w, sizeof(T) * 40 * (size_t)c->geo.n) != cudaSuccess) {
+    w = nullptr;
+    return STAGGER_EOOM;
+  }
+  return STAGGER_OK;
+}
+
+template <typename T>
+static void lin2(stagger_ctx* c, T* o, const T* x, double a, const T* y, double b, cudaStream_t s) {
+  long long n = c->geo.n;
+  k_lin2<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, a, y, b, n);
+  ++c->extra_launches;
+}
+
+template <typename T>
+static int graph_rhs(stagger_ctx* c, T* const f[8], T* out[8], cudaStream_t s) {
+  int rc = ensure_graph<T>(c, false);
+  if (rc) return rc;
+  GraphExec<T>* G = graph_of<T>(c);
+  rc = G->forward(f, s);
+  if (rc) return rc;
+  long long n = c->geo.n;
+  for (int k = 0; k < 8; ++k) {
+    k_copy<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out[k], G->output(k), n);
+    ++c->extra_launches;
+  }
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+// One fixed-dt RK3 step through the graph, in place on f.
+template <typename T>
+static int graph_step(stagger_ctx* c, T* f[8], double dt, cudaStream_t s) {
+  int rc = ensure_graph<T>(c, false);
+  if (rc) return rc;
+  rc = ensure_work<T>(c);
+  if (rc) return rc;
+  GraphExec<T>* G = graph_of<T>(c);
+  T* w = work_of<T>(c);
+  const long long n = c->geo.n;
+  T* q[8];
+  for (int k = 0; k < 8; ++k) q[k] = w + (size_t)k * n;
+  for (int st = 0; st < 3; ++st) {
+    rc = G->forward(f, s);
+    if (rc) return rc;
+    for (int k = 0; k < 8; ++k) {
+      if (st == 0) lin2<T>(c, q[k], G->output(k), 1.0, G->output(k), 0.0, s);
+      else lin2<T>(c, q[k], q[k], RK_ALPHA[st], G->output(k), 1.0, s);
+      lin2<T>(c, f[k], f[k], 1.0, q[k], RK_BETA[st] * dt, s);
+    }
+  }
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+// Adjoint of one fixed-dt step (see stagger_step_adjoint).
+template <typename T>
+static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* const lam_in[8],
+                              T* lam_out[8], cudaStream_t s) {
+  int rc = ensure_graph<T>(c, true);
+  if (rc) return rc;
+  rc = ensure_work<T>(c);
+  if (rc) return rc;
+  GraphExec<T>* G = graph_of<T>(c);
+  T* w = work_of<T>(c);
+  const long long n = c->geo.n;
+  T *f1[8], *f2[8], *q[8], *fb[8], *qb[8];
+  for (int k = 0; k < 8; ++k) {
+    f1[k] = w + (size_t)(0 + k) * n;
+    f2[k] = w + (size_t)(8 + k) * n;
+    q[k] = w + (size_t)(16 + k) * n;
+    fb[k] = w + (size_t)(24 + k) * n;
+    qb[k] = w + (size_t)(32 + k) * n;
+  }
+  const double *A = RK_ALPHA, *B = RK_BETA;
+  // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)).
+  if ((rc = G->forward(f0, s))) return rc;
+  for (int k = 0; k < 8; ++k) {
+    lin2<T>(c, q[k], G->output(k), 1.0, G->output(k), 0.0, s);
+    lin2<T>(c, f1[k], f0[k], 1.0, q[k], B[0] * dt, s);
+  }
+  if ((rc = G->forward(f1, s))) return rc;
+  for (int k = 0; k < 8; ++k) {
+    lin2<T>(c, q[k], q[k], A[1], G->output(k), 1.0, s);
+    lin2<T>(c, f2[k], f1[k], 1.0, q[k], B[1] * dt, s);
+  }
+  // Reverse sweep: fbar_3 = lam; qbar_3 = beta_3 dt fbar.
+  for (int k = 0; k < 8; ++k) {
+    lin2<T>(c, fb[k], lam_in[k], 1.0, lam_in[k], 0.0, s);
+    lin2<T>(c, qb[k], fb[k], B[2] * dt, fb[k], 0.0, s);
+  }
+  T* const* stages[3] = {f0, f1, f2};
+  for (int st = 2; st >= 0; --st) {
+    if ((rc = G->forward(stages[st], s))) return rc;
+    if ((rc = G->backward(qb, fb, s))) return rc;     // fbar += J(f_st)^T qbar
+    if (st > 0)                                         // qbar_{st} = alpha qbar + beta dt fbar
+      for (int k = 0; k < 8; ++k) lin2<T>(c, qb[k], qb[k], A[st], fb[k], B[st - 1] * dt, s);
+  }
+  for (int k = 0; k < 8; ++k) lin2<T>(c, lam_out[k], fb[k], 1.0, fb[k], 0.0, s);
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+extern "C" {
+
+int stagger_step_adjoint(stagger_ctx* c, float* const state_n[8], double dt,
+                         float* const lam_np1[8], float* lam_n[8], void* stream) {
+  if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
+      !ptrs_ok((void* const*)lam_n) || !(dt > 0))
+    return STAGGER_EINVAL;
+  return graph_step_adjoint<float>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
+}
+
+int stagger_rhs_unfused(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
+  return graph_rhs<float>(c, state, dfdt, (cudaStream_t)stream);
+}
+
+int stagger_rhs_unfused_f64(stagger_ctx* c, double* const state[8], double* dfdt[8],
+                            void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
+  return graph_rhs<double>(c, state, dfdt, (cudaStream_t)stream);
+}
+
+int stagger_step_unfused_f64(stagger_ctx* c, double* state[8], double dt, void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !(dt > 0)) return STAGGER_EINVAL;
+  return graph_step<double>(c, state, dt, (cudaStream_t)stream);
+}
+
+int stagger_step_adjoint_f64(stagger_ctx* c, double* const state_n[8], double dt,
+                             double* const lam_np1[8], double* lam_n[8], void* stream) {
+  if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
+      !ptrs_ok((void* const*)lam_n) || !(dt > 0))
+    return STAGGER_EINVAL;
+  return graph_step_adjoint<double>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
+}
+
+int stagger_step_host(stagger_ctx* c, float* state_host[8], int nsteps, double dt, void* stream) {
+  if (!c || !ptrs_ok((void* const*)state_host) || nsteps < 0 || !(dt == dt)) return STAGGER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)c->geo.n;
+  if (!c->host_state) {
+    if (cudaMalloc(&c->host_state, sizeof(float) * 8 * n) != cudaSuccess) {
+      c->host_state = nullptr;
+      return STAGGER_EOOM;
+    }
+  }
+  float* d[8];
+  for (int k = 0; k < 8; ++k) {
+    d[k] = c->host_state + k * n;
+    STG_CUDA_OK(cudaMemcpyAsync(d[k], state_host[k], sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = fused_step(c->fused, d, dt, s);
+    if (rc) return rc;
+  }
+  for (int k = 0; k < 8; ++k)
+    STG_CUDA_OK(cudaMemcpyAsync(state_host[k], d[k], sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  return STAGGER_OK;
+}
+
+}  // extern "C"

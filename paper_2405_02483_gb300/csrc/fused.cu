@@ -1,0 +1,343 @@
+// Fused FP32 forward path: one RK stage is eight launches, each a star
+// stencil of reach <= 3 cells per axis over one or a few fields, with the
+// intermediate fluxes kept in HBM between launches:
+//   lr      ln(rho/r0)                                   (pointwise)
+//   vel     u = p / rho_face                              (Sect. "Centering")
+//   nu_raw  Richtmyer-Morton nu, eq. (RMnu)               (viscous runs)
+//   nu_max  3x3x3 max;  nu_smooth  3x3x3 mean, ln<nu>      (Sect. "Richtmyer & Morton")
+//   tau     stresses eq. (itv), eta J, J                  (edges, centres)
+//   edge    quench eq. (quench), E = -u x B + eta J eq. (ohm), heating densities
+//   flux    momentum, Lorentz and energy fluxes, -P div u + Q
+//   div     divergences -> F(f), eqs. (mass) (mom) (ien) (indu), then the
+//           low-storage update eqs. (ddt), (tupdate)
+#include <math.h>
+
+#include <vector>
+
+#include "fused_kernels.cuh"
+
+namespace stg {
+
+// ================================================================ host =====
+
+const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_nu_raw", "k_nu_max", "k_nu_smooth",
+                                     "k_tau", "k_edge", "k_flux", "k_div", "k_update",
+                                     "k_courant", "k_diag", "k_misc"};
+
+static cudaEvent_t ev_get(Fused& F) {
+  if (!F.pool.empty()) {
+    cudaEvent_t e = F.pool.back();
+    F.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch bracket: count the launch and, when timing, record an event pair
+// around it on the launch stream.
+#define TIMED(kid, stmt)                                          \
+  do {                                                            \
+    cudaEvent_t e0_ = nullptr;                                    \
+    if (F.timing) { e0_ = ev_get(F); cudaEventRecord(e0_, s); }   \
+    stmt;                                                         \
+    if (F.timing) {                                               \
+      cudaEvent_t e1_ = ev_get(F);                                \
+      cudaEventRecord(e1_, s);                                    \
+      F.pending.push_back({(kid), {e0_, e1_}});                   \
+    }                                                             \
+    ++F.launches;                                                 \
+  } while (0)
+
+void fused_timing(Fused& F, int on) { F.timing = on; }
+
+int fused_collect(Fused& F, cudaStream_t s) {
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  for (auto& pe : F.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      F.kt_ms[pe.first] += ms;
+      F.kt_n[pe.first] += 1;
+    }
+    F.pool.push_back(pe.second.first);
+    F.pool.push_back(pe.second.second);
+  }
+  F.pending.clear();
+  return STAGGER_OK;
+}
+
+static dim3 grid3(const Geo& g) {
+  return dim3((unsigned)((g.nx + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY), (unsigned)g.nz);
+}
+static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
+
+int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
+  F.geo = make_geo(gr.nx, gr.ny, gr.nz);
+  F.launches = 0;
+  F.timing = 0;
+  for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
+  KPar& k = F.kp;
+  const double h[3] = {gr.dx, gr.dy, gr.dz};
+  const int nn[3] = {gr.nx, gr.ny, gr.nz};
+  double dlmin = 1e300;
+  int any = 0;
+  for (int a = 0; a < 3; ++a)
+    if (nn[a] > 1) { dlmin = fmin(dlmin, h[a]); any = 1; }
+  if (!any) dlmin = fmin(h[0], fmin(h[1], h[2]));
+  double sp[3];
+  for (int a = 0; a < 3; ++a) {
+    k.ih[a] = (float)(1.0 / h[a]);
+    sp[a] = nn[a] > 1 ? h[a] : dlmin;
+    k.sp[a] = (float)sp[a];
+  }
+  k.spp[0] = (float)fmax(sp[1], sp[2]);
+  k.spp[1] = (float)fmax(sp[2], sp[0]);
+  k.spp[2] = (float)fmax(sp[0], sp[1]);
+  k.r0 = (float)p.ref[0];
+  k.E0 = (float)p.ref[4];
+  k.r0pos = p.ref[0] > 0;
+  k.e0 = p.ref[0] > 0 ? (float)(p.ref[4] / p.ref[0]) : 0.f;
+  for (int d = 0; d < 3; ++d) {
+    k.pref[d] = (float)p.ref[1 + d];
+    k.Bref[d] = (float)p.ref[5 + d];
+    k.g[d] = (float)p.g[d];
+  }
+  k.gamma = (float)p.gamma;
+  k.gm1 = (float)(p.gamma - 1.0);
+  k.visc = (p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0) ? 1 : 0;
+  k.rm = k.visc && !(p.nu_const > 0);
+  k.nu1 = (float)p.nu1;
+  k.nu2dl = (float)(p.nu2 * dlmin);
+  k.nu3 = (float)p.nu3;
+  k.nu_const = (float)p.nu_const;
+  k.nuE = (float)p.nuE;
+  k.nuB = (float)p.nuB;
+  k.c1 = (float)p.c1;
+  k.inv_qmax = (float)(1.0 / p.qmax);
+  k.qlim = (float)p.qlim;
+  k.log_interp = p.log_interp ? 1 : 0;
+  k.do_quench = p.do_quench ? 1 : 0;
+  double dlmax = 0;
+  for (int a = 0; a < 3; ++a)
+    if (nn[a] > 1 || !any) dlmax = fmax(dlmax, h[a]);
+  F.cdt = p.Cdt;
+  F.cdtr = p.Cdtr;
+  F.cdtd = p.Cdtd;
+  F.dlmin = dlmin;
+  F.dfac = fmax(1.0, fmax(p.nuE, p.nuB * dlmax / dlmin));
+
+  const size_t bytes = sizeof(float) * (size_t)F.geo.n;
+  for (int i = 0; i < F_COUNT; ++i) F.fld[i] = nullptr;
+  for (int c = 0; c < 8; ++c) F.q[c] = F.ping[c] = F.pong[c] = nullptr;
+  F.dt_dev = nullptr;
+  F.red = nullptr;
+  // Which intermediate fields this parameter set needs.
+  std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
+                           F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
+                           F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT};
+  if (k.log_interp) need.push_back(F_LR);
+  if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU}) need.push_back(f);
+  if (k.visc)
+    for (int f : {F_TXX, F_TYY, F_TZZ, F_TXY, F_TYZ, F_TZX, F_RX, F_RY, F_RZ, F_WC, F_WX, F_WY, F_WZ})
+      need.push_back(f);
+  if (k.visc && k.do_quench)
+    for (int f : {F_QXX, F_QYY, F_QZZ, F_QXY, F_QYZ, F_QZX}) need.push_back(f);
+  for (int f : need)
+    if (cudaMalloc(&F.fld[f], bytes) != cudaSuccess) { F.fld[f] = nullptr; fused_release(F); return STAGGER_EOOM; }
+  for (int c = 0; c < 8; ++c) {
+    if (cudaMalloc(&F.q[c], bytes) != cudaSuccess || cudaMalloc(&F.ping[c], bytes) != cudaSuccess ||
+        cudaMalloc(&F.pong[c], bytes) != cudaSuccess) {
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+  }
+  dim3 gg = grid3(F.geo);
+  F.red_blocks = (int)(gg.x * gg.y * gg.z);
+  if (cudaMalloc(&F.dt_dev, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc(&F.red, sizeof(double) * 10 * (size_t)F.red_blocks) != cudaSuccess) {
+    fused_release(F);
+    return STAGGER_EOOM;
+  }
+  return STAGGER_OK;
+}
+
+void fused_release(Fused& F) {
+  for (auto& pe : F.pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+  F.pending.clear();
+  for (auto e : F.pool) cudaEventDestroy(e);
+  F.pool.clear();
+  for (int i = 0; i < F_COUNT; ++i) { if (F.fld[i]) cudaFree(F.fld[i]); F.fld[i] = nullptr; }
+  for (int c = 0; c < 8; ++c) {
+    if (F.q[c]) cudaFree(F.q[c]);
+    if (F.ping[c]) cudaFree(F.ping[c]);
+    if (F.pong[c]) cudaFree(F.pong[c]);
+    F.q[c] = F.ping[c] = F.pong[c] = nullptr;
+  }
+  if (F.dt_dev) cudaFree(F.dt_dev);
+  if (F.red) cudaFree(F.red);
+  F.dt_dev = nullptr;
+  F.red = nullptr;
+}
+
+// Everything up to (not including) the divergence kernel: primitives,
+// viscosity, stresses, edge fields and fluxes of state f.
+static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
+  const Geo& g = F.geo;
+  const KPar& k = F.kp;
+  float** d = F.fld;
+  dim3 gg = grid3(g), bb(BX, BY);
+  const float* ls = k.log_interp ? d[F_LR] : f[0];
+  if (k.log_interp) TIMED(K_LR, (k_lr<<<nb1(g.n), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
+  TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ], k, g)));
+  if (k.rm) {
+    TIMED(K_NU_RAW, (k_nu_raw<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6],
+                                                 f[7], d[F_NV], k, g)));
+    TIMED(K_NU_MAX, (k_nu_max<<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
+    TIMED(K_NU_SMOOTH, (k_nu_smooth<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
+  }
+  TIMED(K_TAU, (k_tau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], ls, d[F_NU], d[F_LNU], f[5], f[6], f[7],
+                          d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
+                          d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], k, g)));
+  TIMED(K_EDGE, (k_edge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
+                           d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
+                           f[5], f[6], f[7], d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
+                           d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC], d[F_WX], d[F_WY],
+                           d[F_WZ], k, g)));
+  const bool qn = k.visc && k.do_quench;
+  FluxIn fi = {f[1], f[2], f[3], f[0], f[4], f[5], f[6], f[7], ls, d[F_UX], d[F_UY], d[F_UZ],
+               qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],
+               qn ? d[F_QXY] : d[F_TXY], qn ? d[F_QYZ] : d[F_TYZ], qn ? d[F_QZX] : d[F_TZX],
+               d[F_JX], d[F_JY], d[F_JZ], d[F_NU], d[F_WC], d[F_WX], d[F_WY], d[F_WZ]};
+  FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
+                d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
+                d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT]};
+  TIMED(K_FLUX, (k_flux<<<gg, bb, 0, s>>>(fi, fo, k, g)));
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+static DivIn div_in(Fused& F, float* const f[8]) {
+  float** d = F.fld;
+  DivIn di;
+  di.px = f[1]; di.py = f[2]; di.pz = f[3];
+  di.mxx = d[F_MXX]; di.myy = d[F_MYY]; di.mzz = d[F_MZZ]; di.mxy = d[F_MXY]; di.myx = d[F_MYX];
+  di.mxz = d[F_MXZ]; di.mzx = d[F_MZX]; di.myz = d[F_MYZ]; di.mzy = d[F_MZY];
+  di.lx1 = d[F_LX1]; di.lx2 = d[F_LX2]; di.ly1 = d[F_LY1]; di.ly2 = d[F_LY2];
+  di.lz1 = d[F_LZ1]; di.lz2 = d[F_LZ2];
+  di.gx = d[F_GX]; di.gy = d[F_GY]; di.gz = d[F_GZ]; di.qt = d[F_QT];
+  di.Ex = d[F_EX]; di.Ey = d[F_EY]; di.Ez = d[F_EZ];
+  di.ls = F.kp.log_interp ? d[F_LR] : f[0];
+  for (int c = 0; c < 8; ++c) di.f[c] = f[c];
+  return di;
+}
+
+static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
+                      float beta, int mode, cudaStream_t s) {
+  DivIn di = div_in(F, f);
+  dim3 gg = grid3(F.geo), bb(BX, BY);
+  float* oo[8];
+  for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
+  TIMED(K_DIV, (k_div<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], oo[0],
+                                        oo[1], oo[2], oo[3], oo[4], oo[5], oo[6], oo[7], alpha,
+                                        beta, F.dt_dev, mode, F.kp, F.geo)));
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s) {
+  int st = pre_div(F, f, s);
+  if (st) return st;
+  return launch_div(F, f, out, nullptr, 0.f, 0.f, 0, s);
+}
+
+static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s) {
+  // Uses the primitives and <nu> that pre_div left for this state and q = F(f).
+  const Geo& g = F.geo;
+  const KPar& k = F.kp;
+  dim3 gg = grid3(g), bb(BX, BY);
+  TIMED(K_COURANT, (k_courant_part<<<gg, bb, 0, s>>>(F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0],
+                                                     f[4], f[5], f[6], f[7], F.q[0], F.q[4],
+                                                     F.fld[F_NU], F.red, k, g)));
+  return STAGGER_OK;
+}
+
+int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
+  float* A[8];
+  float* B[8];
+  float* C[8];
+  for (int c = 0; c < 8; ++c) { A[c] = f[c]; B[c] = F.ping[c]; C[c] = F.pong[c]; }
+  float* const* st_in[3] = {A, B, C};
+  float* const* st_out[3] = {B, C, A};
+  for (int stg = 0; stg < 3; ++stg) {
+    int rc = pre_div(F, st_in[stg], s);
+    if (rc) return rc;
+    float alpha = (float)RK_ALPHA[stg], beta = (float)RK_BETA[stg];
+    if (stg == 0 && dt <= 0) {
+      // Courant step from the state and its stage-1 derivative, then update.
+      rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0.f, 0, s);
+      if (rc) return rc;
+      courant_to_dev(F, st_in[0], s);
+      TIMED(K_COURANT, (k_courant_final<<<1, 256, 0, s>>>(F.red, F.red_blocks, F.dt_dev, F.cdt,
+                                                          F.cdtr, F.cdtd, F.dlmin, F.dfac,
+                                                          F.kp.rm)));
+      for (int c = 0; c < 8; ++c)
+        TIMED(K_UPDATE, (k_update<<<nb1(F.geo.n), 256, 0, s>>>(st_in[0][c], F.q[c], st_out[0][c],
+                                                               beta, F.dt_dev, F.geo.n)));
+      STG_CUDA_OK(cudaGetLastError());
+      continue;
+    }
+    if (stg == 0 && dt > 0) {
+      TIMED(K_MISC, (k_set_dt<<<1, 1, 0, s>>>(F.dt_dev, dt)));
+    }
+    rc = launch_div(F, st_in[stg], F.q, const_cast<float**>(st_out[stg]), alpha, beta, 1, s);
+    if (rc) return rc;
+  }
+  return STAGGER_OK;
+}
+
+int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s) {
+  int rc = pre_div(F, f, s);
+  if (rc) return rc;
+  rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s);
+  if (rc) return rc;
+  courant_to_dev(F, f, s);
+  TIMED(K_COURANT, (k_courant_final<<<1, 256, 0, s>>>(F.red, F.red_blocks, F.dt_dev, F.cdt,
+                                                      F.cdtr, F.cdtd, F.dlmin, F.dfac, F.kp.rm)));
+  double h[4];
+  STG_CUDA_OK(cudaMemcpyAsync(h, F.dt_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  *dt = h[0];
+  if (lim) { lim[0] = h[1]; lim[1] = h[2]; lim[2] = h[3]; }
+  if (!(h[0] == h[0]) || h[0] <= 0) return STAGGER_ENONFINITE;
+  return STAGGER_OK;
+}
+
+int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
+                      cudaStream_t s) {
+  dim3 gg = grid3(F.geo), bb(BX, BY);
+  TIMED(K_DIAG, (k_diag_part<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7],
+                                               F.red, F.kp, F.geo)));
+  STG_CUDA_OK(cudaGetLastError());
+  std::vector<double> h((size_t)F.red_blocks * 10);
+  STG_CUDA_OK(cudaMemcpyAsync(h.data(), F.red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < F.red_blocks; ++b)
+    for (int c = 0; c < 10; ++c)
+      acc[c] = c == 7 ? fmax(acc[c], h[10 * b + c]) : acc[c] + h[10 * b + c];
+  const double N = (double)F.geo.n;
+  out[0] = acc[0] + p.ref[0] * N;
+  out[1] = acc[1] + p.ref[1] * N;
+  out[2] = acc[2] + p.ref[2] * N;
+  out[3] = acc[3] + p.ref[3] * N;
+  out[4] = acc[4] + p.ref[4] * N;
+  out[5] = acc[5];
+  out[6] = acc[6];
+  out[7] = acc[7];
+  out[8] = sqrt(acc[8] / N);
+  out[9] = acc[9];
+  return acc[9] > 0 ? STAGGER_ENONFINITE : STAGGER_OK;
+}
+
+}  // namespace stg

@@ -1,0 +1,81 @@
+// Fused FP32 stage kernels of the MHD right-hand side and the RK3 update.
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace stg {
+
+// Scalar parameters in the precision of the kernels.
+struct KPar {
+  float ih[3];          // 1/dx, 1/dy, 1/dz
+  float r0, E0, e0;     // reference density, energy, e0 = E0/r0
+  float pref[3], Bref[3];
+  float gamma, gm1;
+  int visc, rm;         // any viscosity; Richtmyer-Morton (else constant)
+  float nu1, nu2dl, nu3, nu_const;
+  float sp[3];          // diffusion length per axis
+  float spp[3];         // max(sp) of edge pairs: [yz (Ex), zx (Ey), xy (Ez)]
+  float nuE, nuB, c1, inv_qmax, qlim;
+  int log_interp, do_quench, r0pos;
+  float g[3];
+};
+
+// Fields of the fused path, one contiguous device array each.
+enum Fld {
+  F_LR = 0, F_UX, F_UY, F_UZ,                       // ln(rho/r0) (or rho'), face velocities
+  F_NV, F_NM, F_NU, F_LNU,                          // raw, max, smoothed nu, ln<nu>
+  F_TXX, F_TYY, F_TZZ, F_TXY, F_TYZ, F_TZX,         // stress tau
+  F_RX, F_RY, F_RZ, F_JX, F_JY, F_JZ,               // eta J and J
+  F_QXX, F_QYY, F_QZZ, F_QXY, F_QYZ, F_QZX,         // quenched tau
+  F_EX, F_EY, F_EZ,                                 // total electric field (edges)
+  F_WC, F_WX, F_WY, F_WZ,                           // heating densities (centre, edges)
+  F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,  // momentum fluxes
+  F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2,         // Lorentz products
+  F_GX, F_GY, F_GZ, F_QT,                           // energy fluxes, -P div u + Q
+  F_COUNT
+};
+
+// Kernel identities for per-kernel timing.
+enum KId { K_LR = 0, K_VEL, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_TAU, K_EDGE, K_FLUX, K_DIV,
+           K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
+extern const char* const KNAMES[K_COUNT];
+
+struct Fused {
+  Geo geo;
+  KPar kp;
+  float* fld[F_COUNT];
+  float* q[8];          // dfdt (2N storage)
+  float* ping[8];       // stage state buffers
+  float* pong[8];
+  double cdt, cdtr, cdtd, dlmin, dfac;  // Courant factors, dl_min, diffusion factor
+  double* dt_dev;       // device step and the three limits
+  double* red;          // reduction partials
+  int red_blocks;
+  long long launches;
+  // Optional per-kernel timing with CUDA events on the launch stream.
+  int timing;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> pool;
+  double kt_ms[K_COUNT];
+  long long kt_n[K_COUNT];
+};
+
+int fused_init(Fused& F, const stagger_grid& g, const stagger_params& p);
+void fused_release(Fused& F);
+// F(f) into out[8] (plain derivatives).
+int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s);
+// One RK3 step in place on f.  dt > 0 fixed, else Courant (device-side).
+int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s);
+// Courant limits (t_wave, t_rate, t_diff) and dt for state f, synchronising.
+int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s);
+// Per-kernel timing: on/off, and collect (synchronises the stream).
+void fused_timing(Fused& F, int on);
+int fused_collect(Fused& F, cudaStream_t s);
+// FP64 diagnostics, synchronising.
+int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
+                      cudaStream_t s);
+
+}  // namespace stg

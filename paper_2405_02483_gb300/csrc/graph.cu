@@ -1,0 +1,442 @@
+// Op-graph engine (see graph.cuh): forward and transpose kernels of every
+// primitive, the right-hand-side graph of the MHD equations, and the executor.
+#include <math.h>
+
+#include <algorithm>
+
+#include "graph.cuh"
+
+namespace stg {
+
+// ---------------------------------------------------------------------------
+// Periodic neighbour along an axis (index of cell idx shifted by o).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long nbr(long long idx, int axis, int o, const Geo& g) {
+  if (axis == 0) {
+    int i = (int)(idx % g.nx);
+    return idx - i + wrap(i + o, g.nx);
+  } else if (axis == 1) {
+    int j = (int)((idx / g.sy) % g.ny);
+    return idx + (long long)(wrap(j + o, g.ny) - j) * g.sy;
+  }
+  int k = (int)(idx / g.sz);
+  return idx + (long long)(wrap(k + o, g.nz) - k) * g.sz;
+}
+
+// Stencil value at idx: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
+// are eq. (deriv) to i+1/2 and i-1/2, divided by the spacing h.
+template <typename T>
+__device__ __forceinline__ T stencil_at(const T* f, long long idx, int axis, int kind, T h,
+                                        const Geo& g) {
+  const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
+  const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
+  T m3 = f[nbr(idx, axis, -3, g)], m2 = f[nbr(idx, axis, -2, g)], m1 = f[nbr(idx, axis, -1, g)];
+  T z0 = f[idx], p1 = f[nbr(idx, axis, 1, g)], p2 = f[nbr(idx, axis, 2, g)],
+    p3 = f[nbr(idx, axis, 3, g)];
+  switch (kind) {
+    case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
+    case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
+    case ST_DDUP: return (DA * (p1 - z0) + DB * (p2 - m1) + DC * (p3 - m2)) / h;
+    default: return (DA * (z0 - m1) + DB * (p1 - m2) + DC * (p2 - m3)) / h;
+  }
+}
+
+template <typename T>
+__global__ void g_forward(GNode nd, const T* A, const T* B, T* out, Geo g) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.n) return;
+  T r;
+  switch (nd.op) {
+    case G_STENCIL: r = stencil_at(A, idx, nd.axis, nd.sk, (T)nd.c0, g); break;
+    case G_SHIFT: r = A[nbr(idx, nd.axis, nd.sk, g)]; break;
+    case G_ADD: r = A[idx] + B[idx]; break;
+    case G_SUB: r = A[idx] - B[idx]; break;
+    case G_MUL: r = A[idx] * B[idx]; break;
+    case G_DIV: r = A[idx] / B[idx]; break;
+    case G_MAX: r = A[idx] >= B[idx] ? A[idx] : B[idx]; break;
+    case G_EXP: r = exp(A[idx]); break;
+    case G_LOG: r = log(A[idx]); break;
+    case G_LOG1P: r = log1p(A[idx]); break;
+    case G_SQRT: r = sqrt(A[idx]); break;
+    case G_ABS: r = fabs(A[idx]); break;
+    case G_AXPB: r = (T)nd.c0 * A[idx] + (T)nd.c1; break;
+    case G_CLAMPMIN: r = A[idx] < (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
+    case G_CLAMPMAX: r = A[idx] > (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
+    default: r = (T)nd.c0; break;  // G_CONST
+  }
+  out[idx] = r;
+}
+
+// Transpose kernels.  Pointwise rules follow the usual subgradient choices:
+// |x|' = sign(x) with sign(0) = 0; clamp passes the gradient where the bound
+// holds with equality; max(a, b) splits it evenly on ties.
+template <typename T>
+__global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+                           T* gA, T* gB, Geo g) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.n) return;
+  if (nd.op == G_STENCIL) {
+    // Gather form of the transpose: up^T = dn, dn^T = up, ddup^T = -dddn,
+    // dddn^T = -ddup (periodic summation by parts).
+    int kind = nd.sk;
+    int tk = kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
+    T v = stencil_at(gout, idx, nd.axis, tk, (T)nd.c0, g);
+    if (kind == ST_DDUP || kind == ST_DDDN) v = -v;
+    gA[idx] += v;
+    return;
+  }
+  if (nd.op == G_SHIFT) {
+    gA[idx] += gout[nbr(idx, nd.axis, -nd.sk, g)];
+    return;
+  }
+  T gg = gout[idx];
+  switch (nd.op) {
+    case G_ADD: gA[idx] += gg; gB[idx] += gg; break;
+    case G_SUB: gA[idx] += gg; gB[idx] -= gg; break;
+    case G_MUL: {
+      T a = A[idx], b = B[idx];
+      gA[idx] += gg * b;
+      gB[idx] += gg * a;
+      break;
+    }
+    case G_DIV: {
+      T a = A[idx], b = B[idx];
+      gA[idx] += gg / b;
+      gB[idx] += -gg * a / (b * b);
+      break;
+    }
+    case G_MAX: {
+      T a = A[idx], b = B[idx];
+      T ga = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
+      T gb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
+      gA[idx] += ga;
+      gB[idx] += gb;
+      break;
+    }
+    case G_EXP: gA[idx] += gg * out[idx]; break;
+    case G_LOG: gA[idx] += gg / A[idx]; break;
+    case G_LOG1P: gA[idx] += gg / ((T)1 + A[idx]); break;
+    case G_SQRT: gA[idx] += gg / ((T)2 * out[idx]); break;
+    case G_ABS: {
+      T a = A[idx];
+      gA[idx] += a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0);
+      break;
+    }
+    case G_AXPB: gA[idx] += (T)nd.c0 * gg; break;
+    case G_CLAMPMIN: if (A[idx] >= (T)nd.c0) gA[idx] += gg; break;
+    case G_CLAMPMAX: if (A[idx] <= (T)nd.c0) gA[idx] += gg; break;
+    default: break;
+  }
+}
+
+template <typename T>
+__global__ void g_add_into(T* dst, const T* src, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
+// ---------------------------------------------------------------------------
+// The right-hand side, eqs. (mass), (mom), (itv), (ien), (vdiss), (indu),
+// (ohm), written on the stored deviations f' (full value ref + f').
+// ---------------------------------------------------------------------------
+void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& p) {
+  G.nodes.clear();
+  const int X = 0, Y = 1, Z = 2;
+  const double h[3] = {gr.dx, gr.dy, gr.dz};
+  const int nn[3] = {gr.nx, gr.ny, gr.nz};
+  double dlmin = 1e300, any = 0;
+  for (int a = 0; a < 3; ++a)
+    if (nn[a] > 1) { dlmin = std::min(dlmin, h[a]); any = 1; }
+  if (!any) dlmin = std::min(h[0], std::min(h[1], h[2]));
+  double sp[3];
+  for (int a = 0; a < 3; ++a) sp[a] = nn[a] > 1 ? h[a] : dlmin;
+
+  auto ddup = [&](int a, int ax) { return G.st(ST_DDUP, a, ax, h[ax]); };
+  auto dddn = [&](int a, int ax) { return G.st(ST_DDDN, a, ax, h[ax]); };
+  auto up = [&](int a, int ax) { return G.up(a, ax); };
+  auto dn = [&](int a, int ax) { return G.dn(a, ax); };
+  auto full = [&](int a, double ref) { return ref != 0.0 ? G.axpb(a, 1.0, ref) : a; };
+  auto neg = [&](int a) { return G.axpb(a, -1.0, 0.0); };
+
+  int fin[8];
+  for (int k = 0; k < 8; ++k) fin[k] = G.input(k);
+  const double r0 = p.ref[0], E0 = p.ref[4];
+  int rd = fin[0], Ed = fin[4];
+  int r = full(rd, r0), E = full(Ed, E0);
+  int pf[3], B[3], Bd[3];
+  for (int d = 0; d < 3; ++d) {
+    pf[d] = full(fin[1 + d], p.ref[1 + d]);
+    Bd[d] = fin[5 + d];
+    B[d] = full(Bd[d], p.ref[5 + d]);
+  }
+
+  // Primitives; faces and edges by log interpolation of rho (do_loginterp).
+  // lr = ln(rho / r0) keeps FP32 resolution of small density deviations.
+  int lr = -1;
+  auto dens = [&](int t) {  // density from an interpolated lr (or rho') value
+    if (p.log_interp) return r0 > 0 ? G.axpb(G.ex(t), r0, 0.0) : G.ex(t);
+    return full(t, r0);
+  };
+  if (p.log_interp) lr = r0 > 0 ? G.lg1p(G.axpb(rd, 1.0 / r0, 0.0)) : G.lg(r);
+  int lsrc = p.log_interp ? lr : rd;
+  int rf[3], u[3];
+  for (int d = 0; d < 3; ++d) {
+    rf[d] = dens(dn(lsrc, d));
+    u[d] = G.div(pf[d], rf[d]);
+  }
+  const double gm1 = p.gamma - 1.0;
+  int Pd = G.axpb(Ed, gm1, 0.0);
+  int P = G.axpb(Ed, gm1, gm1 * E0);
+  int e = G.div(E, r);
+  // e - e0 with e0 = E0/r0: (E' - e0 r') / r, its derivatives equal those of e.
+  int ed = r0 > 0 ? G.div(G.sub(Ed, G.axpb(rd, E0 / r0, 0.0)), r) : e;
+  int divu = G.add(G.add(ddup(u[X], X), ddup(u[Y], Y)), ddup(u[Z], Z));
+
+  // Current J = curl B on edges (mu = 1).
+  int Jx = G.sub(dddn(Bd[Z], Y), dddn(Bd[Y], Z));
+  int Jy = G.sub(dddn(Bd[X], Z), dddn(Bd[Z], X));
+  int Jz = G.sub(dddn(Bd[Y], X), dddn(Bd[X], Y));
+
+  // Ideal E = -u x B, eq. (ohm).
+  int Ex = neg(G.sub(G.mul(dn(u[Y], Z), dn(B[Z], Y)), G.mul(dn(u[Z], Y), dn(B[Y], Z))));
+  int Ey = neg(G.sub(G.mul(dn(u[Z], X), dn(B[X], Z)), G.mul(dn(u[X], Z), dn(B[Z], X))));
+  int Ez = neg(G.sub(G.mul(dn(u[X], Y), dn(B[Y], X)), G.mul(dn(u[Y], X), dn(B[X], Y))));
+
+  const bool visc = p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0;
+  int Q = -1, txx = -1, tyy = -1, tzz = -1, txy = -1, tyz = -1, tzx = -1;
+  int ediff[3] = {-1, -1, -1};
+  if (visc) {
+    int nxx, nyy, nzz, nxy, nyz, nzx;
+    if (p.nu_const > 0) {
+      nxx = nyy = nzz = nxy = nyz = nzx = G.cnst(p.nu_const);
+    } else {
+      // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u).
+      int ucx = up(u[X], X), ucy = up(u[Y], Y), ucz = up(u[Z], Z);
+      int uc2 = G.add(G.add(G.mul(ucx, ucx), G.mul(ucy, ucy)), G.mul(ucz, ucz));
+      int bcx = up(B[X], X), bcy = up(B[Y], Y), bcz = up(B[Z], Z);
+      int B2 = G.add(G.add(G.mul(bcx, bcx), G.mul(bcy, bcy)), G.mul(bcz, bcz));
+      int nu = -1;
+      auto acc = [&](int t) { nu = nu < 0 ? t : G.add(nu, t); };
+      if (p.nu1 > 0) acc(G.axpb(G.sq(uc2), p.nu1, 0.0));
+      if (p.nu3 > 0) {
+        int cs = G.sq(G.div(G.axpb(P, p.gamma, 0.0), r));
+        int ca = G.sq(G.div(B2, r));
+        acc(G.axpb(G.add(cs, ca), p.nu3, 0.0));
+      }
+      if (p.nu2 > 0) acc(G.axpb(G.cmin(neg(divu), 0.0), p.nu2 * dlmin, 0.0));
+      // <nu>_{max smooth}: 3-cell max along x, y, z, then 3-cell mean.
+      for (int ax = 0; ax < 3; ++ax) nu = G.maxi(G.maxi(G.shift(nu, ax, -1), nu), G.shift(nu, ax, 1));
+      for (int ax = 0; ax < 3; ++ax)
+        nu = G.axpb(G.add(G.add(G.shift(nu, ax, -1), nu), G.shift(nu, ax, 1)), 1.0 / 3.0, 0.0);
+      int lnu = G.lg(G.cmin(nu, 1e-30));
+      nxx = G.axpb(nu, sp[X], 0.0);
+      nyy = G.axpb(nu, sp[Y], 0.0);
+      nzz = G.axpb(nu, sp[Z], 0.0);
+      nxy = G.axpb(G.ex(dn(dn(lnu, X), Y)), std::max(sp[X], sp[Y]), 0.0);
+      nyz = G.axpb(G.ex(dn(dn(lnu, Y), Z)), std::max(sp[Y], sp[Z]), 0.0);
+      nzx = G.axpb(G.ex(dn(dn(lnu, Z), X)), std::max(sp[Z], sp[X]), 0.0);
+    }
+    int rxy = dens(dn(dn(lsrc, X), Y));
+    int ryz = dens(dn(dn(lsrc, Y), Z));
+    int rzx = dens(dn(dn(lsrc, Z), X));
+    // Strain and stress, eq. (itv).
+    int Sxx = ddup(u[X], X), Syy = ddup(u[Y], Y), Szz = ddup(u[Z], Z);
+    int Sxy = G.axpb(G.add(dddn(u[X], Y), dddn(u[Y], X)), 0.5, 0.0);
+    int Syz = G.axpb(G.add(dddn(u[Y], Z), dddn(u[Z], Y)), 0.5, 0.0);
+    int Szx = G.axpb(G.add(dddn(u[Z], X), dddn(u[X], Z)), 0.5, 0.0);
+    auto diag = [&](int nii, int S) {
+      int s = p.c1 != 0.0 ? G.add(S, G.axpb(divu, p.c1, 0.0)) : S;
+      return G.mul(G.mul(r, nii), s);
+    };
+    txx = diag(nxx, Sxx);
+    tyy = diag(nyy, Syy);
+    tzz = diag(nzz, Szz);
+    txy = G.mul(G.mul(rxy, nxy), Sxy);
+    tyz = G.mul(G.mul(ryz, nyz), Syz);
+    tzx = G.mul(G.mul(rzx, nzx), Szx);
+    // Resistive field eta J with eta = nuB * nu of the edge.
+    int Rx = G.mul(G.axpb(nyz, p.nuB, 0.0), Jx);
+    int Ry = G.mul(G.axpb(nzx, p.nuB, 0.0), Jy);
+    int Rz = G.mul(G.axpb(nxy, p.nuB, 0.0), Jz);
+    if (p.do_quench) {
+      // eq. (quench): one factor per component, over its differentiation axes;
+      // |T| in the ratio is the 3-cell max of |T| along the axis.
+      auto quench = [&](int T, int a0, int a1) {
+        int fac = -1;
+        for (int t = 0; t < 2; ++t) {
+          int ax = t == 0 ? a0 : a1;
+          if (ax < 0) continue;
+          int d2 = G.add(G.sub(G.shift(T, ax, 1), G.axpb(T, 2.0, 0.0)), G.shift(T, ax, -1));
+          int a2 = G.ab(d2);
+          int aT = G.ab(T);
+          int M = G.maxi(G.maxi(G.shift(aT, ax, -1), aT), G.shift(aT, ax, 1));
+          int q = G.div(a2, G.axpb(G.add(M, G.axpb(a2, 1.0 / p.qmax, 0.0)), 1.0, 1e-30));
+          int m = G.maxi(G.maxi(G.shift(q, ax, -1), q), G.shift(q, ax, 1));
+          fac = fac < 0 ? m : G.maxi(fac, m);
+        }
+        return G.mul(T, G.cmax(fac, p.qlim));
+      };
+      txx = quench(txx, X, -1);
+      tyy = quench(tyy, Y, -1);
+      tzz = quench(tzz, Z, -1);
+      txy = quench(txy, X, Y);
+      tyz = quench(tyz, Y, Z);
+      tzx = quench(tzx, Z, X);
+      Rx = quench(Rx, Y, Z);
+      Ry = quench(Ry, Z, X);
+      Rz = quench(Rz, X, Y);
+    }
+    Ex = G.add(Ex, Rx);
+    Ey = G.add(Ey, Ry);
+    Ez = G.add(Ez, Rz);
+    // eq. (vdiss) and Joule heating.
+    int Qv = G.add(G.add(G.mul(txx, Sxx), G.mul(tyy, Syy)), G.mul(tzz, Szz));
+    int off = G.add(G.add(up(up(G.mul(txy, Sxy), X), Y), up(up(G.mul(tyz, Syz), Y), Z)),
+                    up(up(G.mul(tzx, Szx), Z), X));
+    Qv = G.add(Qv, G.axpb(off, 2.0, 0.0));
+    int Qj = G.add(G.add(up(up(G.mul(Rx, Jx), Y), Z), up(up(G.mul(Ry, Jy), Z), X)),
+                   up(up(G.mul(Rz, Jz), X), Y));
+    Q = G.add(Qv, Qj);
+    // eq. (ediffuse): nuE ddup(dn(rho nu_ii) dddn e).
+    int nii[3] = {nxx, nyy, nzz};
+    for (int d = 0; d < 3; ++d)
+      ediff[d] = G.axpb(ddup(G.mul(dn(G.mul(r, nii[d]), d), dddn(ed, d)), d), p.nuE, 0.0);
+  }
+
+  // eq. (mass)
+  int d_r = neg(G.add(G.add(ddup(pf[X], X), ddup(pf[Y], Y)), ddup(pf[Z], Z)));
+
+  // eq. (mom): momentum flux components minus the (quenched) stress.
+  auto minus_tau = [&](int flux, int tau) { return tau >= 0 ? G.sub(flux, tau) : flux; };
+  auto Tdiag = [&](int d, int tau) {
+    return minus_tau(G.add(G.mul(up(pf[d], d), up(u[d], d)), Pd), tau);
+  };
+  auto Toff = [&](int d, int a, int tau) {  // p_d carried along axis a
+    return minus_tau(G.mul(dn(pf[d], a), dn(u[a], d)), tau);
+  };
+  auto grav = [&](int t, int d) {
+    return p.g[d] != 0.0 ? G.add(t, G.axpb(rf[d], p.g[d], 0.0)) : t;
+  };
+  int d_px = neg(dddn(Tdiag(X, txx), X));
+  d_px = G.sub(d_px, ddup(Toff(X, Y, txy), Y));
+  d_px = G.sub(d_px, ddup(Toff(X, Z, tzx), Z));
+  d_px = G.add(d_px, up(G.mul(Jy, dn(B[Z], X)), Z));
+  d_px = grav(G.sub(d_px, up(G.mul(Jz, dn(B[Y], X)), Y)), X);
+
+  int d_py = neg(ddup(Toff(Y, X, txy), X));
+  d_py = G.sub(d_py, dddn(Tdiag(Y, tyy), Y));
+  d_py = G.sub(d_py, ddup(Toff(Y, Z, tyz), Z));
+  d_py = G.add(d_py, up(G.mul(Jz, dn(B[X], Y)), X));
+  d_py = grav(G.sub(d_py, up(G.mul(Jx, dn(B[Z], Y)), Z)), Y);
+
+  int d_pz = neg(ddup(Toff(Z, X, tzx), X));
+  d_pz = G.sub(d_pz, ddup(Toff(Z, Y, tyz), Y));
+  d_pz = G.sub(d_pz, dddn(Tdiag(Z, tzz), Z));
+  d_pz = G.add(d_pz, up(G.mul(Jx, dn(B[Y], Z)), Y));
+  d_pz = grav(G.sub(d_pz, up(G.mul(Jy, dn(B[X], Z)), X)), Z);
+
+  // eq. (ien)
+  int adv = G.add(G.add(ddup(G.mul(pf[X], dn(e, X)), X), ddup(G.mul(pf[Y], dn(e, Y)), Y)),
+                  ddup(G.mul(pf[Z], dn(e, Z)), Z));
+  int d_E = G.sub(neg(adv), G.mul(P, divu));
+  if (Q >= 0) {
+    d_E = G.add(d_E, Q);
+    for (int d = 0; d < 3; ++d) d_E = G.add(d_E, ediff[d]);
+  }
+
+  // eq. (indu): dB/dt = -curl E.
+  int d_Bx = neg(G.sub(ddup(Ez, Y), ddup(Ey, Z)));
+  int d_By = neg(G.sub(ddup(Ex, Z), ddup(Ez, X)));
+  int d_Bz = neg(G.sub(ddup(Ey, X), ddup(Ex, Y)));
+
+  int outs[8] = {d_r, d_px, d_py, d_pz, d_E, d_Bx, d_By, d_Bz};
+  for (int k = 0; k < 8; ++k) G.out[k] = outs[k];
+}
+
+// ---------------------------------------------------------------------------
+// Executor
+// ---------------------------------------------------------------------------
+template <typename T>
+int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
+  release();
+  def = d;
+  geo = g;
+  size_t nn = def.nodes.size();
+  size_t nval = 0;
+  for (auto& nd : def.nodes)
+    if (nd.op != G_INPUT) ++nval;
+  if (cudaMalloc(&vals, sizeof(T) * nval * g.n) != cudaSuccess) { vals = nullptr; return STAGGER_EOOM; }
+  if (with_grads) {
+    if (cudaMalloc(&grads, sizeof(T) * nn * g.n) != cudaSuccess) {
+      grads = nullptr;
+      release();
+      return STAGGER_EOOM;
+    }
+  }
+  ptr.assign(nn, nullptr);
+  size_t v = 0;
+  for (size_t i = 0; i < nn; ++i)
+    if (def.nodes[i].op != G_INPUT) ptr[i] = vals + (v++) * g.n;
+  return STAGGER_OK;
+}
+
+template <typename T>
+void GraphExec<T>::release() {
+  if (vals) cudaFree(vals);
+  if (grads) cudaFree(grads);
+  vals = grads = nullptr;
+  ptr.clear();
+}
+
+static inline unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T>
+int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
+  for (size_t i = 0; i < def.nodes.size(); ++i)
+    if (def.nodes[i].op == G_INPUT) ptr[i] = in[def.nodes[i].sk];
+  const int bs = 256;
+  for (size_t i = 0; i < def.nodes.size(); ++i) {
+    const GNode& nd = def.nodes[i];
+    if (nd.op == G_INPUT) continue;
+    const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
+    const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
+    g_forward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], geo);
+    ++launches;
+  }
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+template <typename T>
+int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
+  if (!grads) return STAGGER_EINVAL;
+  const size_t nn = def.nodes.size();
+  STG_CUDA_OK(cudaMemsetAsync(grads, 0, sizeof(T) * nn * geo.n, s));
+  const int bs = 256;
+  for (int k = 0; k < 8; ++k) {
+    g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(grads + (size_t)def.out[k] * geo.n, seed[k], geo.n);
+    ++launches;
+  }
+  for (long long i = (long long)nn - 1; i >= 0; --i) {
+    const GNode& nd = def.nodes[i];
+    if (nd.op == G_INPUT || nd.op == G_CONST) continue;
+    const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
+    const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
+    T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
+    T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
+    g_backward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n,
+                                                     gA, gB, geo);
+    ++launches;
+  }
+  for (int k = 0; k < 8; ++k) {
+    g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(gin[k], grads + (size_t)def.in[k] * geo.n, geo.n);
+    ++launches;
+  }
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+template struct GraphExec<float>;
+template struct GraphExec<double>;
+
+}  // namespace stg

@@ -1,0 +1,84 @@
+// Op graph of the MHD right-hand side: the equations written as a DAG of
+// primitive staggered operations (6th-order derivatives, 5th-order
+// interpolations, shifts, pointwise arithmetic).  Each primitive has a forward
+// CUDA kernel and a hand-written transpose (vector-Jacobian) kernel, so the
+// graph gives an unfused forward and, swept in reverse, the adjoint.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace stg {
+
+enum GOp {
+  G_INPUT = 0, G_STENCIL, G_SHIFT, G_ADD, G_SUB, G_MUL, G_DIV, G_MAX,
+  G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST
+};
+enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
+
+struct GNode {
+  int op;       // GOp
+  int a, b;     // input node ids (-1 if unused)
+  int axis;     // 0 = x, 1 = y, 2 = z (stencil / shift)
+  int sk;       // GStencil kind, or shift distance
+  double c0, c1;  // scalars: spacing h (derivative), a*x+b, clamp bound, const
+};
+
+// Precision-independent description of the graph.
+struct GraphDef {
+  std::vector<GNode> nodes;
+  int in[8];    // input node per state field (stored deviation)
+  int out[8];   // output node per time derivative
+
+  int push(int op, int a, int b, int axis, int sk, double c0, double c1) {
+    GNode n{op, a, b, axis, sk, c0, c1};
+    nodes.push_back(n);
+    return (int)nodes.size() - 1;
+  }
+  int input(int k) { return in[k] = push(G_INPUT, -1, -1, 0, k, 0, 0); }
+  int st(int kind, int a, int axis, double h) { return push(G_STENCIL, a, -1, axis, kind, h, 0); }
+  int up(int a, int ax) { return st(ST_UP, a, ax, 1.0); }
+  int dn(int a, int ax) { return st(ST_DN, a, ax, 1.0); }
+  int shift(int a, int ax, int s) { return push(G_SHIFT, a, -1, ax, s, 0, 0); }
+  int add(int a, int b) { return push(G_ADD, a, b, 0, 0, 0, 0); }
+  int sub(int a, int b) { return push(G_SUB, a, b, 0, 0, 0, 0); }
+  int mul(int a, int b) { return push(G_MUL, a, b, 0, 0, 0, 0); }
+  int div(int a, int b) { return push(G_DIV, a, b, 0, 0, 0, 0); }
+  int maxi(int a, int b) { return push(G_MAX, a, b, 0, 0, 0, 0); }
+  int ex(int a) { return push(G_EXP, a, -1, 0, 0, 0, 0); }
+  int lg(int a) { return push(G_LOG, a, -1, 0, 0, 0, 0); }
+  int lg1p(int a) { return push(G_LOG1P, a, -1, 0, 0, 0, 0); }
+  int sq(int a) { return push(G_SQRT, a, -1, 0, 0, 0, 0); }
+  int ab(int a) { return push(G_ABS, a, -1, 0, 0, 0, 0); }
+  int axpb(int a, double s, double t) { return push(G_AXPB, a, -1, 0, 0, s, t); }
+  int cmin(int a, double c) { return push(G_CLAMPMIN, a, -1, 0, 0, c, 0); }
+  int cmax(int a, double c) { return push(G_CLAMPMAX, a, -1, 0, 0, c, 0); }
+  int cnst(double c) { return push(G_CONST, -1, -1, 0, 0, c, 0); }
+};
+
+// Build the right-hand-side graph for a grid and parameter set.
+void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p);
+
+// Device executor for one precision.  Holds one value and one gradient array
+// of n cells per node (inputs point at caller memory and need none).
+template <typename T>
+struct GraphExec {
+  GraphDef def;
+  Geo geo;
+  T* vals = nullptr;     // node values (non-input nodes)
+  T* grads = nullptr;    // node gradients (all nodes)
+  std::vector<T*> ptr;   // value pointer per node
+  long long launches = 0;
+
+  int init(const GraphDef& d, const Geo& g, bool with_grads);
+  void release();
+  // Evaluate every node; inputs are the 8 stored deviation arrays.
+  int forward(T* const in[8], cudaStream_t s);
+  // Reverse sweep: seed the 8 output gradients, accumulate into gin[8]
+  // (+=).  forward() must have run on the same inputs.
+  int backward(T* const seed[8], T* gin[8], cudaStream_t s);
+  T* output(int k) { return ptr[def.out[k]]; }
+};
+
+}  // namespace stg

@@ -134,11 +134,13 @@ def orszag_tang(nx: int = 1024, ny: int = 1024, nz: int = 1,
 
 
 def solenoidal_velocity(shape, seed: int, urms: float, kmin: float = 1.0,
-                        kmax: float = 4.0, slope: float = -2.0, device: str = "cpu"):
-    """Gaussian random solenoidal velocity in a periodic unit box with energy
-    spectrum E(k) ~ k^slope for kmin <= |m| <= kmax (m the integer wave
-    vector), sampled at the three face positions and scaled to the given rms
-    speed.  Returns three float64 numpy arrays (ux, uy, uz)."""
+                        kmax: float = 4.0, slope: float = -2.0, device: str = "cpu",
+                        solenoidal: bool = True):
+    """Gaussian random velocity in a periodic unit box with energy spectrum
+    E(k) ~ k^slope for kmin <= |m| <= kmax (m the integer wave vector),
+    projected onto its divergence-free part unless ``solenoidal`` is False,
+    sampled at the three face positions and scaled to the given rms speed.
+    Returns three float64 numpy arrays (ux, uy, uz)."""
     import torch
 
     nx, ny, nz = shape
@@ -157,9 +159,10 @@ def solenoidal_velocity(shape, seed: int, urms: float, kmin: float = 1.0,
     # Make the field real: c(-m) = conj(c(m)).
     coef = 0.5 * (coef + np.conj(coef[:, ::-1, ::-1, ::-1]))
     # Solenoidal projection c <- c - m (m.c)/|m|^2.
-    with np.errstate(divide="ignore", invalid="ignore"):
-        mdotc = (MX * coef[0] + MY * coef[1] + MZ * coef[2]) / np.where(kk > 0, kk ** 2, 1.0)
-    coef = coef - np.stack([MX, MY, MZ]) * mdotc
+    if solenoidal:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            mdotc = (MX * coef[0] + MY * coef[1] + MZ * coef[2]) / np.where(kk > 0, kk ** 2, 1.0)
+        coef = coef - np.stack([MX, MY, MZ]) * mdotc
 
     comps = []
     for d, (n_d) in enumerate((nx, ny, nz)):
@@ -208,9 +211,10 @@ def turbulence(n: int = 512, seed: int = 3, urms: float = 0.5, b0: float = 0.3,
 def orszag_tang_3d(n: int = 128, seed: int = 4, pert: float = 1e-3,
                    gamma: float = 5.0 / 3.0) -> Workload:
     """Orszag-Tang fields on an n^3 box (uniform in z) plus a seeded random
-    solenoidal velocity perturbation of rms ``pert`` so every axis matters."""
+    velocity perturbation of rms ``pert`` (with a compressive part, so that
+    div u is not zero and every axis matters)."""
     w = orszag_tang(n, n, n, gamma)
-    du = solenoidal_velocity((n, n, n), seed, pert)
+    du = solenoidal_velocity((n, n, n), seed, pert, solenoidal=False)
     rho0 = w.fields[0][0, 0, 0]
     for d in range(3):
         w.fields[1 + d] = w.fields[1 + d] + rho0 * du[d]

@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every function include/stagger.h
+declares; argument validation rejects bad input before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "stagger.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(stagger_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2405_02483_gb300 as S
+    return S
+
+
+def test_every_declared_symbol_is_exported(S):
+    names = _declared()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(S.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {n for n, _, _ in S.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_params_default_matches_namelists(S):
+    p = S.default_params()
+    assert p.gamma == pytest.approx(5 / 3)
+    assert (p.Cdt, p.Cdtr, p.Cdtd) == (0.4, 0.1, 0.7)
+    assert (p.qmax, p.qlim, p.log_interp) == (8.0, 2.0, 1)
+    assert (p.nu1, p.nu2, p.nu3, p.nu_const) == (0.0, 0.0, 0.0, 0.0)
+    assert S.lib.stagger_params_default(None) == S.EINVAL
+
+
+def test_create_rejects_bad_arguments_without_gpu(S):
+    h = ctypes.c_void_p()
+    p = S.default_params()
+    bad_grids = [S.Grid(0, 8, 8, 1, 1, 1), S.Grid(8, 8, 8, 0, 1, 1), S.Grid(8, -1, 8, 1, 1, 1),
+                 S.Grid(2048, 2048, 1024, 1, 1, 1)]
+    for g in bad_grids:
+        assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)) == S.EINVAL
+    g = S.Grid(8, 8, 8, 0.1, 0.1, 0.1)
+    for field, val in [("gamma", 1.0), ("nu1", -1.0), ("Cdt", 0.0)]:
+        q = S.default_params(**{field: val})
+        assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL
+    q = S.default_params(do_quench=1, qmax=0.0)
+    assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL
+    assert S.lib.stagger_create(None, ctypes.byref(p), ctypes.byref(h)) == S.EINVAL
+    assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(p), None) == S.EINVAL
+
+
+def test_null_context_calls_are_rejected(S):
+    nul = S.P8F()
+    assert S.lib.stagger_rhs(None, nul, nul, None) == S.EINVAL
+    assert S.lib.stagger_step(None, nul, 0.1, None, None) == S.EINVAL
+    assert S.lib.stagger_step_adjoint(None, nul, 0.1, nul, nul, None) == S.EINVAL
+    assert S.lib.stagger_destroy(None) == S.OK
+    assert S.lib.stagger_cells(None) == 0
+    assert S.lib.stagger_strerror(S.ENONFINITE).decode() == "non-finite value in the state"
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "stagger_copy", os.path.join(ROOT, "paper_2405_02483_gb300", "__init__.py"),
+        submodule_search_locations=[])
+    mod = importlib.util.module_from_spec(spec)
+    monkeypatch.setattr(os.path, "exists", lambda p: False if p.endswith("libstagger.so") else True)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)

@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Error measures (FP32 GPU vs FP64 oracle, per field, max norm):
+  err_range = max|f_gpu - f_ora| / (max f_ora - min f_ora)   (state fields)
+  err_scale = max|F_gpu - F_ora| / S_c                        (time derivatives)
+with S_c = max(max|F_c|, 1e-3 * max_c' max|F_c'|): the derivative of a field
+whose equation nearly cancels (continuity of a solenoidal flow) is compared on
+the scale of the other terms of the same right-hand side, since FP32 rounds
+each term, not their sum.
+
+Tolerances: the smooth linear-wave workload (32^3) must meet err_range <= 1e-5
+after one step and <= 1e-4 after 50 steps.  The viscous, quenched workloads
+(Orszag-Tang, random solenoidal flows) use the error relative to the magnitude
+of the field's group (rho; momentum vector; E; B vector) of 1e-5 per step,
+because a field's range there can lie below its FP32 resolution (the density
+of an incompressible flow, a component that starts at zero).
+
+Adjoint: FP64 GPU vs FP64 oracle to 1e-10 (max norm); FP32 GPU vs FP64 oracle
+to 1e-4 in relative L2 (the quench and max operations switch branch where
+FP32 and FP64 round differently, so a few cells differ by more).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_02483_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+VISC_KW = dict(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=1)
+VISC_O = oracle.Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=True)
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2405_02483_gb300 as S
+    return S
+
+
+def err_range(got, ora):
+    out = []
+    for g, o in zip(got, ora):
+        o = np.asarray(o)
+        rng = float(o.max() - o.min())
+        out.append(float(np.abs(g - o).max()) / (rng if rng > 0 else 1.0))
+    return out
+
+
+def err_max(got, ora):
+    return [float(np.abs(g - np.asarray(o)).max()) / max(float(np.abs(np.asarray(o)).max()), 1e-30)
+            for g, o in zip(got, ora)]
+
+
+def err_group(got, ora):
+    """Error of each field relative to the magnitude of its group: rho, the
+    momentum vector, E, the magnetic vector (a component that starts at zero
+    is judged on the scale of its vector)."""
+    groups = [[0], [1, 2, 3], [4], [5, 6, 7]]
+    out = [0.0] * 8
+    for gidx in groups:
+        sc = max(float(np.abs(np.asarray(ora[i])).max()) for i in gidx)
+        for i in gidx:
+            out[i] = float(np.abs(got[i] - np.asarray(ora[i])).max()) / max(sc, 1e-30)
+    return out
+
+
+def err_l2(got, ora):
+    return [float(np.linalg.norm(g - np.asarray(o)) / max(np.linalg.norm(np.asarray(o)), 1e-300))
+            for g, o in zip(got, ora)]
+
+
+def err_scale(got, ora):
+    mx = [float(np.abs(np.asarray(o)).max()) for o in ora]
+    top = max(mx)
+    return [float(np.abs(g - np.asarray(o)).max()) / max(m, 1e-3 * top, 1e-30)
+            for g, o, m in zip(got, ora, mx)]
+
+
+def ragged_state(shape, seed=7):
+    ux, uy, uz = inputs.solenoidal_velocity(shape, seed, 0.3)
+    a = inputs.solenoidal_velocity(shape, seed + 1, 1.0)
+    b = inputs.solenoidal_velocity(shape, seed + 2, 1.0)
+    c = inputs.solenoidal_velocity(shape, seed + 3, 1.0)
+    f = [1 + 0.05 * a[0], ux + 0.02 * c[0], uy, uz, 0.9 + 0.05 * a[1],
+         0.1 * b[0], 0.1 * b[1] + 0.05, 0.1 * b[2] + 0.3]
+    nx, ny, nz = shape
+    return inputs.Workload("ragged", shape, (1.0 / nx, 1.1 / ny, 0.9 / nz), f)
+
+
+def make(S, w, kw, refs=None):
+    refs, dev = S.split_state(w.fields, refs)
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **kw))
+    return sim, refs, dev
+
+
+def oracle_params(kw):
+    d = dict(kw)
+    if "do_quench" in d:
+        d["do_quench"] = bool(d["do_quench"])
+    if "log_interp" in d:
+        d["log_interp"] = bool(d["log_interp"])
+    if "g" in d:
+        d["g"] = tuple(d["g"])
+    return oracle.Params(**d)
+
+
+CASES = {
+    "waves32_ideal": (lambda: inputs.linear_waves(32), {}),
+    "ot3d24_visc_quench": (lambda: inputs.orszag_tang_3d(24), VISC_KW),
+    "ot2d_64x64x1_visc_quench": (lambda: inputs.orszag_tang(64, 64, 1), VISC_KW),
+    "ragged37x29x11_visc_quench": (lambda: ragged_state((37, 29, 11)), VISC_KW),
+    "ragged_const_nu_c1_gravity_nolog": (
+        lambda: ragged_state((33, 20, 9)),
+        dict(nu_const=0.002, c1=-1.0 / 3.0, nuE=0.5, nuB=0.7, g=(0.0, 0.0, -1.0), log_interp=0)),
+    "degenerate_1x1x40_visc": (lambda: inputs.linear_waves(40), None),
+}
+
+
+def _case(name):
+    mk, kw = CASES[name]
+    w = mk()
+    if name.startswith("degenerate"):
+        # a 1D column: x and y of size 1
+        w = inputs.Workload("col", (1, 1, 40), (1.0, 1.0, 1.0 / 40),
+                            [f[:, :1, :1].copy() for f in w.fields])
+        kw = VISC_KW
+    return w, kw
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_matches_oracle(S, name):
+    w, kw = _case(name)
+    sim, refs, dev = make(S, w, kw)
+    F = sim.rhs(dev)
+    Fu = sim.rhs_unfused(dev)
+    torch.cuda.synchronize()
+    g = oracle.Grid(*w.shape, *w.spacing)
+    Fo = [t.numpy() for t in oracle.rhs([torch.tensor(a) for a in w.fields], g, oracle_params(kw))]
+    e = err_scale([t.double().cpu().numpy() for t in F], Fo)
+    eu = err_scale([t.double().cpu().numpy() for t in Fu], Fo)
+    assert max(e) < 2e-4, (name, e)
+    assert max(eu) < 2e-4, (name, eu)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_fp64_unfused_matches_oracle_to_roundoff(S, name):
+    w, kw = _case(name)
+    sim, refs, _ = make(S, w, kw)
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
+    F = sim.rhs_unfused_f64(d64)
+    torch.cuda.synchronize()
+    g = oracle.Grid(*w.shape, *w.spacing)
+    Fo = [t.numpy() for t in oracle.rhs([torch.tensor(a) for a in w.fields], g, oracle_params(kw))]
+    e = err_scale([t.cpu().numpy() for t in F], Fo)
+    assert max(e) < 1e-10, (name, e)
+    sim.close()
+
+
+def test_linear_waves_one_and_fifty_steps(S):
+    """Spec tolerance on the smooth problem: 1e-5 of range after one
+    step, 1e-4 after 50, with the Courant step of each path."""
+    w = inputs.linear_waves(32)
+    sim, refs, dev = make(S, w, {})
+    g = oracle.Grid(*w.shape, *w.spacing)
+    fo = [torch.tensor(a) for a in w.fields]
+    dts = []
+    for n in range(50):
+        dts.append(sim.step(dev, None, want_dt=True))
+        fo, dto = oracle.step(fo, g, oracle.Params())
+        assert abs(dts[-1] / dto - 1) < 1e-5
+        if n == 0:
+            e1 = err_range(S.join_state(dev, refs), [t.numpy() for t in fo])
+            assert max(e1) <= 1e-5, e1
+    e50 = err_range(S.join_state(dev, refs), [t.numpy() for t in fo])
+    assert max(e50) <= 1e-4, e50
+    sim.close()
+
+
+@pytest.mark.parametrize("name,nsteps", [("ot3d24_visc_quench", 3), ("ot2d_64x64x1_visc_quench", 10),
+                                         ("ragged37x29x11_visc_quench", 3),
+                                         ("ragged_const_nu_c1_gravity_nolog", 3)])
+def test_viscous_steps(S, name, nsteps):
+    w, kw = _case(name)
+    sim, refs, dev = make(S, w, kw)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle_params(kw)
+    fo = [torch.tensor(a) for a in w.fields]
+    for _ in range(nsteps):
+        dt = sim.step(dev, None, want_dt=True)
+        fo, dto = oracle.step(fo, g, po, dt=dt)
+    e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
+    assert max(e) < 1e-5 * nsteps, (name, e)
+    sim.close()
+
+
+def test_courant_and_diagnostics(S):
+    w, kw = _case("ragged37x29x11_visc_quench")
+    sim, refs, dev = make(S, w, kw)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle_params(kw)
+    f64 = [torch.tensor(a) for a in w.fields]
+    dt, lim = sim.courant(dev)
+    dto, limo = oracle.courant_dt(f64, oracle.rhs(f64, g, po), g, po)
+    assert dt == pytest.approx(dto, rel=1e-5)
+    for a, b in zip(lim, limo):
+        assert a == pytest.approx(b, rel=1e-4)
+    d = sim.diagnostics(dev)
+    do = oracle.diagnostics(f64, g, po)
+    for i in (0, 4, 5, 6):
+        assert d[i] == pytest.approx(do[i], rel=1e-6)
+    for i in (1, 2, 3):
+        assert abs(d[i] - do[i]) < 1e-6 * float(np.abs(w.fields[i]).sum())
+    assert d[7] == pytest.approx(do[7], rel=1e-3) and d[8] == pytest.approx(do[8], rel=1e-3)
+    assert d[9] == 0
+    sim.close()
+
+
+def test_diagnostics_report_nonfinite(S):
+    w = inputs.linear_waves(16)
+    sim, refs, dev = make(S, w, {})
+    dev[4][3, 2, 1] = float("nan")
+    out = sim.diagnostics(dev, check=False)
+    assert out[9] == 1
+    with pytest.raises(S.StaggerError) as ei:
+        sim.diagnostics(dev)
+    assert ei.value.status == S.ENONFINITE
+    sim.close()
+
+
+def test_conservation_and_divb_on_gpu(S):
+    w = inputs.orszag_tang_3d(32)
+    sim, refs, dev = make(S, w, VISC_KW)
+    d0 = sim.diagnostics(dev)
+    for _ in range(5):
+        sim.step(dev, None)
+    d1 = sim.diagnostics(dev)
+    # FP64 sums of FP32 fields: the telescoping flux sums cancel up to FP32
+    # rounding of each cell's update (about sqrt(N) * 1e-7 * |dt F|).
+    assert abs(d1[0] - d0[0]) < 1e-9 * d0[0]
+    for i in (1, 2, 3):
+        assert abs(d1[i] - d0[i]) < 1e-4
+    # div B starts at zero (B depends on one other coordinate per component)
+    # and the curl update keeps it at FP32 roundoff of B / h (|B| / h ~ 9).
+    assert d0[7] == 0.0 and d1[7] < 1e-3
+    sim.close()
+
+
+def test_step_host_equals_device_step(S):
+    w = inputs.linear_waves(16)
+    sim, refs, dev = make(S, w, {})
+    host = [t.cpu().pin_memory() for t in dev]
+    sim.step(dev, 1e-3)
+    sim.step_host(host, 1, 1e-3)
+    for a, b in zip(dev, host):
+        assert torch.equal(a.cpu(), b)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", ["waves16_ideal", "ot3d12_visc_quench"])
+def test_adjoint_matches_oracle(S, name):
+    if name == "waves16_ideal":
+        w, kw = inputs.linear_waves(16), {}
+    else:
+        w, kw = inputs.orszag_tang_3d(12), VISC_KW
+    sim, refs, dev = make(S, w, kw)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle_params(kw)
+    f64 = [torch.tensor(a) for a in w.fields]
+    dt = 2e-3
+    gen = torch.Generator().manual_seed(0)
+    lam = [torch.randn(t.shape, generator=gen, dtype=torch.float64) for t in f64]
+    ref = [t.numpy() for t in oracle.step_adjoint(f64, dt, lam, g, po)]
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
+    out64 = sim.step_adjoint_f64(d64, dt, [l.cuda() for l in lam])
+    out32 = sim.step_adjoint(dev, dt, [l.float().cuda() for l in lam])
+    torch.cuda.synchronize()
+    e64 = err_max([t.cpu().numpy() for t in out64], ref)
+    e32 = err_l2([t.double().cpu().numpy() for t in out32], ref)
+    assert max(e64) < 1e-10, e64
+    assert max(e32) < 1e-4, e32
+    sim.close()
+
+
+def test_adjoint_dot_product_and_fd_fp64(S):
+    """J^T w against FP64 central differences of the GPU's own FP64 step, on a
+    compressible state (div u != 0, so max(0, -div u) is away from its kink)."""
+    w = ragged_state((14, 12, 10))
+    sim, refs, _ = make(S, w, VISC_KW)
+    base = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
+    dt = 2e-3
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    wv = [torch.randn(t.shape, generator=gen, dtype=torch.float64, device="cuda") for t in base]
+    lam = sim.step_adjoint_f64(base, dt, wv)
+
+    def loss(state):
+        s = [t.clone() for t in state]
+        sim.step_unfused_f64(s, dt)
+        return sum(float((a * b).sum()) for a, b in zip(s, wv))
+
+    for d in range(3):
+        v = [1e-2 * torch.randn(t.shape, generator=gen, dtype=torch.float64, device="cuda") for t in base]
+        eps = 1e-6
+        fd = (loss([a + eps * b for a, b in zip(base, v)]) - loss([a - eps * b for a, b in zip(base, v)])) / (2 * eps)
+        an = sum(float((l * b).sum()) for l, b in zip(lam, v))
+        assert abs(fd - an) < 1e-6 * abs(an), (fd, an)
+    sim.close()
+
+
+def test_rollout_gradient_matches_oracle(S):
+    from paper_2405_02483_gb300.rollout import rollout
+    w = inputs.orszag_tang_3d(12)
+    sim, refs, dev = make(S, w, VISC_KW)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    dts = [2e-3] * 5
+    x = [t.clone().requires_grad_(True) for t in dev]
+    y = rollout(sim, x, dts, k=2)
+    loss = 0.5 * sum((t * t).sum() for t in y[1:4])
+    loss.backward()
+    xo = [torch.tensor(a, requires_grad=True) for a in w.fields]
+    cur = xo
+    for dt in dts:
+        cur = oracle.rk3_step(cur, dt, lambda s: oracle.rhs(s, g, VISC_O))
+    lo = 0.5 * sum((t * t).sum() for t in cur[1:4])
+    go = torch.autograd.grad(lo, xo)
+    e = err_l2([t.grad.double().cpu().numpy() for t in x], [t.numpy() for t in go])
+    assert max(e) < 1e-3, e
+    sim.close()
