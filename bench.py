@@ -47,9 +47,10 @@ REF_N = 96                      # per-step sample grid of the reference (oracle)
 KERNEL_ARRAYS = {"k_lr": 2, "k_vel": 7, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
                  "k_tau": 22, "k_edge": 31, "k_flux": 44, "k_div": (33 + 54 + 54) / 3.0,
                  "k_update": 3}
-# DRAM bytes per launch from the ncu capture summarised in profiles/ (None
-# until taken for the current kernels).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per cell per launch from the ncu capture
+# summarised in profiles/k_edge_turbulence192_fused_v1.md (192^3 capture;
+# traffic grows with the cells).  Only kernels unchanged since their capture.
+NCU_TRAFFIC_PER_CELL = {"k_edge": 854.8e6 / 192 ** 3}
 
 
 def peaks():
@@ -257,7 +258,8 @@ def main():
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "bytes_per_launch": kbytes, "ms_per_launch": kavg,
-            "traffic": NCU_TRAFFIC.get(kname)}
+            "traffic": (NCU_TRAFFIC_PER_CELL[kname] * n ** 3
+                        if kname in NCU_TRAFFIC_PER_CELL else None)}
     step_gbs = STEP_BYTES_PER_ZONE * (value / ws) / 1e9
     step_roof = {"bytes_per_zone": STEP_BYTES_PER_ZONE, "achieved": step_gbs, "peak": peak,
                  "unit": "GB/s", "frac": step_gbs / peak}
