@@ -162,6 +162,26 @@ int stagger_timing(stagger_ctx* ctx, int on);
 int stagger_kernel_times(stagger_ctx* ctx, int max, const char** names, double* total_ms,
                          long long* launches, void* stream);
 
+/* Diagnostics without any allocation (the paper has no counterpart; this is
+ * a library convenience).  Same outputs, status and synchronisation as
+ * stagger_diagnostics, but it takes the grid and parameters directly instead
+ * of a context and allocates nothing: no cudaMalloc, no cudaFree, no host heap.
+ * Its scratch is a fixed 5 MiB array in the library's device image, which
+ * every GPU that loads the library keeps until the process exits.  It is for
+ * callers that cannot allocate: an application whose memory pool already
+ * owns the device's memory, a monitoring tool that must not change the
+ * footprint of the run it inspects, or code that has no context (creating
+ * one allocates tens of arrays of the grid's size).
+ * Limit: at most 65536 thread blocks of 32 x 8 cells, i.e.
+ * ceil(nx/32) * ceil(ny/8) * nz <= 65536 (for example 256^3); larger grids
+ * return STAGGER_EINVAL.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (two streams, two host threads) race, so
+ * serialise them.  Each call overwrites every scratch entry it reads. */
+int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagger_params* params,
+                                float* const state[8], double out[10], void* stream);
+
 /* Number of cells nx*ny*nz of the context's grid (0 for NULL). */
 size_t stagger_cells(const stagger_ctx* ctx);
 

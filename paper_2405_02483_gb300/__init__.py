@@ -65,6 +65,8 @@ SIGNATURES = [
     ("stagger_kernel_times", ctypes.c_int, [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_longlong), VP]),
+    ("stagger_diagnostics_noalloc", ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Params),
+                                                   P8F, ctypes.POINTER(ctypes.c_double), VP]),
     ("stagger_cells", ctypes.c_size_t, [VP]),
     ("stagger_launch_count", ctypes.c_longlong, [VP]),
     ("stagger_strerror", ctypes.c_char_p, [ctypes.c_int]),

@@ -11,6 +11,7 @@
 //   div     divergences -> F(f), eqs. (mass) (mom) (ien) (indu), then the
 //           low-storage update eqs. (ddt), (tupdate)
 #include <math.h>
+#include <string.h>
 
 #include <vector>
 
@@ -341,3 +342,103 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
 }
 
 }  // namespace stg
+
+// ===================================================== no-allocation entry ====
+// stagger_diagnostics_noalloc: the diagnostics reduction with its scratch (the
+// per-block FP64 partials and the ten final sums) in a fixed file-scope device
+// array instead of memory from cudaMalloc.  The array is part of this
+// library's device image, so every GPU that loads the library holds it until
+// the process exits.  Limit: grids of at most NOALLOC_MAX_BLOCKS thread blocks
+// of 32 x 8 cells (16,777,216 cells, e.g. 256^3).
+
+namespace stg {
+
+#define NOALLOC_MAX_BLOCKS 65536
+#define NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 10 + 16];
+
+// Device address of g_noalloc_scratch per device, taken once per device by
+// cudaGetSymbolAddress (in host code the symbol names a host-side stand-in,
+// not device memory).
+static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Sum (max for entry 7) of the nb per-block partials into out[0..9], in a
+// fixed order per thread and a fixed tree, so repeated calls agree bitwise.
+__global__ void k_diag_final(const double* part, int nb, double* out) {
+  __shared__ double sm[10][256];
+  int tid = threadIdx.x;
+  double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = tid; b < nb; b += blockDim.x)
+    for (int c = 0; c < 10; ++c)
+      v[c] = c == 7 ? fmax(v[c], part[10 * b + c]) : v[c] + part[10 * b + c];
+  for (int c = 0; c < 10; ++c) sm[c][tid] = v[c];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s)
+      for (int c = 0; c < 10; ++c)
+        sm[c][tid] = c == 7 ? fmax(sm[c][tid], sm[c][tid + s]) : sm[c][tid] + sm[c][tid + s];
+    __syncthreads();
+  }
+  if (tid < 10) out[tid] = sm[tid][0];
+}
+
+}  // namespace stg
+
+extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagger_params* p,
+                                           float* const state[8], double out[10],
+                                           void* stream) {
+  using namespace stg;
+  if (!grid || !p || !state || !out) return STAGGER_EINVAL;
+  for (int c = 0; c < 8; ++c)
+    if (!state[c]) return STAGGER_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return STAGGER_EINVAL;
+  if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || p->ref[0] < 0) return STAGGER_EINVAL;
+  const long long nb = (long long)((grid->nx + BX - 1) / BX) * ((grid->ny + BY - 1) / BY) * grid->nz;
+  if (nb > NOALLOC_MAX_BLOCKS) return STAGGER_EINVAL;  // grid larger than the fixed scratch
+
+  int dev = 0;
+  STG_CUDA_OK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return STAGGER_EUNSUPPORTED;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    STG_CUDA_OK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (double*)ptr;
+  }
+  double* part = g_noalloc_ptr[dev];
+  double* fin = part + (size_t)NOALLOC_MAX_BLOCKS * 10;
+
+  // The kernel parameters the reduction reads (spacings, references, density
+  // interpolation), from the caller's grid and parameters.
+  KPar k;
+  memset(&k, 0, sizeof(k));
+  k.ih[0] = (float)(1.0 / grid->dx);
+  k.ih[1] = (float)(1.0 / grid->dy);
+  k.ih[2] = (float)(1.0 / grid->dz);
+  k.r0 = (float)p->ref[0];
+  k.r0pos = p->ref[0] > 0;
+  for (int d = 0; d < 3; ++d) {
+    k.pref[d] = (float)p->ref[1 + d];
+    k.Bref[d] = (float)p->ref[5 + d];
+  }
+  k.log_interp = p->log_interp ? 1 : 0;
+  Geo g = make_geo(grid->nx, grid->ny, grid->nz);
+  cudaStream_t s = (cudaStream_t)stream;
+  dim3 gg = grid3(g), bb(BX, BY);
+  // Each block writes all ten of its partials, so nothing carries over from
+  // an earlier call.
+  k_diag_part<<<gg, bb, 0, s>>>(state[0], state[1], state[2], state[3], state[4], state[5],
+                                state[6], state[7], part, k, g);
+  k_diag_final<<<1, 256, 0, s>>>(part, (int)nb, fin);
+  STG_CUDA_OK(cudaGetLastError());
+  double h[10];
+  STG_CUDA_OK(cudaMemcpyAsync(h, fin, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  const double N = (double)g.n;
+  for (int c = 0; c < 5; ++c) out[c] = h[c] + p->ref[c] * N;
+  out[5] = h[5];
+  out[6] = h[6];
+  out[7] = h[7];
+  out[8] = sqrt(h[8] / N);
+  out[9] = h[9];
+  return h[9] > 0 ? STAGGER_ENONFINITE : STAGGER_OK;
+}
