@@ -12,7 +12,8 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libstagger.so")
+# STAGGER_LIB selects another build of the library (e.g. an A/B variant).
+LIB_PATH = os.environ.get("STAGGER_LIB") or os.path.join(PKG, "libstagger.so")
 
 OK, EINVAL, ECUDA, ENONFINITE, EOOM, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("r", "px", "py", "pz", "E", "Bx", "By", "Bz")

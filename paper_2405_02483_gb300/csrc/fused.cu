@@ -69,7 +69,8 @@ int fused_collect(Fused& F, cudaStream_t s) {
 }
 
 static dim3 grid3(const Geo& g) {
-  return dim3((unsigned)((g.nx + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY), (unsigned)g.nz);
+  return dim3((unsigned)((g.nx + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY),
+              (unsigned)((g.nz + BZ - 1) / BZ));
 }
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
 
@@ -78,6 +79,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.launches = 0;
   F.timing = 0;
   for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
+
   KPar& k = F.kp;
   const double h[3] = {gr.dx, gr.dy, gr.dz};
   const int nn[3] = {gr.nx, gr.ny, gr.nz};
@@ -187,7 +189,7 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
   const Geo& g = F.geo;
   const KPar& k = F.kp;
   float** d = F.fld;
-  dim3 gg = grid3(g), bb(BX, BY);
+  dim3 gg = grid3(g), bb(BX, BY, BZ);
   const float* ls = k.log_interp ? d[F_LR] : f[0];
   if (k.log_interp) TIMED(K_LR, (k_lr<<<nb1(g.n), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
   TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ], k, g)));
@@ -236,7 +238,7 @@ static DivIn div_in(Fused& F, float* const f[8]) {
 static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
                       float beta, int mode, cudaStream_t s) {
   DivIn di = div_in(F, f);
-  dim3 gg = grid3(F.geo), bb(BX, BY);
+  dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
   float* oo[8];
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
   TIMED(K_DIV, (k_div<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], oo[0],
@@ -256,7 +258,7 @@ static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s) {
   // Uses the primitives and <nu> that pre_div left for this state and q = F(f).
   const Geo& g = F.geo;
   const KPar& k = F.kp;
-  dim3 gg = grid3(g), bb(BX, BY);
+  dim3 gg = grid3(g), bb(BX, BY, BZ);
   TIMED(K_COURANT, (k_courant_part<<<gg, bb, 0, s>>>(F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0],
                                                      f[4], f[5], f[6], f[7], F.q[0], F.q[4],
                                                      F.fld[F_NU], F.red, k, g)));
@@ -282,9 +284,18 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
       TIMED(K_COURANT, (k_courant_final<<<1, 256, 0, s>>>(F.red, F.red_blocks, F.dt_dev, F.cdt,
                                                           F.cdtr, F.cdtd, F.dlmin, F.dfac,
                                                           F.kp.rm)));
-      for (int c = 0; c < 8; ++c)
-        TIMED(K_UPDATE, (k_update<<<nb1(F.geo.n), 256, 0, s>>>(st_in[0][c], F.q[c], st_out[0][c],
-                                                               beta, F.dt_dev, F.geo.n)));
+      Upd8 u;
+      int vec = (F.geo.n % 4) == 0;
+      for (int c = 0; c < 8; ++c) {
+        u.f[c] = st_in[0][c];
+        u.q[c] = F.q[c];
+        u.o[c] = st_out[0][c];
+        vec &= (((uintptr_t)u.f[c] | (uintptr_t)u.q[c] | (uintptr_t)u.o[c]) & 15) == 0;
+      }
+      const long long work = vec ? F.geo.n / 4 : F.geo.n;
+      unsigned bx = (unsigned)((work + 255) / 256);
+      if (bx > 2048) bx = 2048;
+      TIMED(K_UPDATE, (k_update8<<<dim3(bx, 8), 256, 0, s>>>(u, beta, F.dt_dev, F.geo.n, vec)));
       STG_CUDA_OK(cudaGetLastError());
       continue;
     }
@@ -316,7 +327,7 @@ int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaSt
 
 int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
                       cudaStream_t s) {
-  dim3 gg = grid3(F.geo), bb(BX, BY);
+  dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
   TIMED(K_DIAG, (k_diag_part<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7],
                                                F.red, F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
@@ -393,7 +404,8 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
     if (!state[c]) return STAGGER_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return STAGGER_EINVAL;
   if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || p->ref[0] < 0) return STAGGER_EINVAL;
-  const long long nb = (long long)((grid->nx + BX - 1) / BX) * ((grid->ny + BY - 1) / BY) * grid->nz;
+  const long long nb = (long long)((grid->nx + BX - 1) / BX) * ((grid->ny + BY - 1) / BY) *
+                       ((grid->nz + BZ - 1) / BZ);
   if (nb > NOALLOC_MAX_BLOCKS) return STAGGER_EINVAL;  // grid larger than the fixed scratch
 
   int dev = 0;
@@ -423,7 +435,7 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
   k.log_interp = p->log_interp ? 1 : 0;
   Geo g = make_geo(grid->nx, grid->ny, grid->nz);
   cudaStream_t s = (cudaStream_t)stream;
-  dim3 gg = grid3(g), bb(BX, BY);
+  dim3 gg = grid3(g), bb(BX, BY, BZ);
   // Each block writes all ten of its partials, so nothing carries over from
   // an earlier call.
   k_diag_part<<<gg, bb, 0, s>>>(state[0], state[1], state[2], state[3], state[4], state[5],

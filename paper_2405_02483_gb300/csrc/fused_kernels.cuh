@@ -5,10 +5,23 @@
 
 #include "fused.cuh"
 
+// Minimum resident blocks per SM requested from the register allocator.
+#ifndef STG_MINB
+#define STG_MINB 4
+#endif
+
 namespace stg {
 
+// Thread block of the per-cell kernels: BX x BY x BZ cells.
+#ifndef BX
 #define BX 32
-#define BY 8
+#endif
+#ifndef BY
+#define BY 2
+#endif
+#ifndef BZ
+#define BZ 4
+#endif
 
 #define IA_ 0.5859375f
 #define IB_ (-0.09765625f)
@@ -34,8 +47,8 @@ struct Nb {
 __device__ __forceinline__ bool make_nb(Nb& n, const Geo& g) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return false;
+  int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= g.nx || j >= g.ny || k >= g.nz) return false;
 #pragma unroll
   for (int o = -3; o <= 3; ++o) {
     n.x[o + 3] = wrap(i + o, g.nx);
@@ -79,7 +92,7 @@ __global__ void k_lr(const float* __restrict__ rd, float* __restrict__ lr, KPar 
 }
 
 // ------------------------------------------------------------- velocity ----
-__global__ void __launch_bounds__(256) k_vel(const float* __restrict__ ls,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(const float* __restrict__ ls,
                                              const float* __restrict__ px,
                                              const float* __restrict__ py,
                                              const float* __restrict__ pz, float* __restrict__ ux,
@@ -94,7 +107,7 @@ __global__ void __launch_bounds__(256) k_vel(const float* __restrict__ ls,
 
 // ---------------------------------------------------------- viscosity ------
 // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u), centred.
-__global__ void __launch_bounds__(256) k_nu_raw(const float* __restrict__ ux,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_raw(const float* __restrict__ ux,
                                                 const float* __restrict__ uy,
                                                 const float* __restrict__ uz,
                                                 const float* __restrict__ rd,
@@ -123,7 +136,7 @@ __global__ void __launch_bounds__(256) k_nu_raw(const float* __restrict__ ux,
 }
 
 // 3-cell max along x, y and z: the maximum over the 3x3x3 neighbourhood.
-__global__ void __launch_bounds__(256) k_nu_max(const float* __restrict__ a,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_max(const float* __restrict__ a,
                                                 float* __restrict__ b, Geo g) {
   Nb n;
   if (!make_nb(n, g)) return;
@@ -138,7 +151,7 @@ __global__ void __launch_bounds__(256) k_nu_max(const float* __restrict__ a,
 }
 
 // 3-cell mean along x, y and z (the 3x3x3 mean) and its logarithm.
-__global__ void __launch_bounds__(256) k_nu_smooth(const float* __restrict__ a,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_smooth(const float* __restrict__ a,
                                                    float* __restrict__ nu,
                                                    float* __restrict__ lnu, Geo g) {
   Nb n;
@@ -175,7 +188,7 @@ __device__ __forceinline__ float dn2(const float* __restrict__ f, const Nb& n, i
 }
 
 // Strain, stress (eq. (itv)), J = curl B and eta J on edges, eq. (ohm).
-__global__ void __launch_bounds__(256) k_tau(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ ls, const float* __restrict__ nu,
     const float* __restrict__ lnu, const float* __restrict__ bx, const float* __restrict__ by,
@@ -248,7 +261,7 @@ __device__ __forceinline__ float quench1(const float* __restrict__ T, const Nb& 
 
 // Quenched stresses, total E on edges and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
-__global__ void __launch_bounds__(256) k_edge(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
     const float* __restrict__ Rx, const float* __restrict__ Ry, const float* __restrict__ Rz,
@@ -336,7 +349,7 @@ __device__ __forceinline__ float up2(const float* __restrict__ f, const Nb& n, i
   return s_up(inner);
 }
 
-__global__ void __launch_bounds__(256) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
   Nb n;
   if (!make_nb(n, g)) return;
   const float* pr[3] = {in.px, in.py, in.pz};
@@ -427,7 +440,7 @@ struct DivIn {
 
 // F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q.
 // mode 0: write F to q only; 1: also update with dt from *dtp.
-__global__ void __launch_bounds__(256) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
                                              float* q4, float* q5, float* q6, float* q7,
                                              float* o0, float* o1, float* o2, float* o3,
                                              float* o4, float* o5, float* o6, float* o7,
@@ -478,6 +491,31 @@ __global__ void __launch_bounds__(256) k_div(DivIn in, float* q0, float* q1, flo
 
 __global__ void k_set_dt(double* dtp, double dt) { dtp[0] = dt; }
 
+// f_out = f + beta dt q for the 8 fields in one launch (blockIdx.y = field),
+// 16-byte vectors when every array is 16-byte aligned and n % 4 == 0.
+struct Upd8 {
+  const float* f[8];
+  const float* q[8];
+  float* o[8];
+};
+__global__ void k_update8(Upd8 u, float beta, const double* dtp, long long n, int vec) {
+  const int c = blockIdx.y;
+  const float bdt = (float)((double)beta * dtp[0]);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const float4* f = reinterpret_cast<const float4*>(u.f[c]);
+    const float4* q = reinterpret_cast<const float4*>(u.q[c]);
+    float4* o = reinterpret_cast<float4*>(u.o[c]);
+    for (; i < n / 4; i += stride) {
+      float4 a = __ldg(f + i), b = __ldg(q + i);
+      o[i] = make_float4(a.x + bdt * b.x, a.y + bdt * b.y, a.z + bdt * b.z, a.w + bdt * b.w);
+    }
+  } else {
+    for (; i < n; i += stride) u.o[c][i] = __ldg(u.f[c] + i) + bdt * __ldg(u.q[c] + i);
+  }
+}
+
 // f_out = f + beta dt q (stage-1 update once the Courant step is known).
 __global__ void k_update(const float* __restrict__ f, const float* __restrict__ q,
                          float* __restrict__ o, float beta, const double* dtp, long long n) {
@@ -489,15 +527,15 @@ __global__ void k_update(const float* __restrict__ f, const float* __restrict__ 
 // -------------------------------------------------------------- Courant ----
 // Per-cell wave speed c_s + c_A + |u_perp|, rate max(|dr/dt|/r, |dE/dt|/E)
 // and <nu>; block maxima to part[3*block + {0,1,2}] (as doubles).
-__global__ void __launch_bounds__(256) k_courant_part(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_courant_part(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ Ed, const float* __restrict__ bx,
     const float* __restrict__ by, const float* __restrict__ bz, const float* __restrict__ qr,
     const float* __restrict__ qE, const float* __restrict__ nu, double* part, KPar k, Geo g) {
-  __shared__ float sm[3][256];
+  __shared__ float sm[3][BX * BY * BZ];
   Nb n;
   float w = 0.f, rate = 0.f, nuv = 0.f;
-  int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   if (make_nb(n, g)) {
     float ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
     float bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
@@ -522,7 +560,7 @@ __global__ void __launch_bounds__(256) k_courant_part(
   sm[1][tid] = rate;
   sm[2][tid] = nuv;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = BX * BY * BZ / 2; s > 0; s >>= 1) {
     if (tid < s)
       for (int c = 0; c < 3; ++c) sm[c][tid] = fmaxf(sm[c][tid], sm[c][tid + s]);
     __syncthreads();
@@ -566,14 +604,14 @@ __global__ void k_courant_final(const double* part, int nb, double* dt_out, doub
 // ---------------------------------------------------------- diagnostics ----
 // Per-block FP64 partials: sum r', px', py', pz', E', kinetic, magnetic,
 // max |div B|, sum (div B)^2, non-finite count.
-__global__ void __launch_bounds__(256) k_diag_part(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
     const float* __restrict__ rd, const float* __restrict__ px, const float* __restrict__ py,
     const float* __restrict__ pz, const float* __restrict__ Ed, const float* __restrict__ bx,
     const float* __restrict__ by, const float* __restrict__ bz, double* part, KPar k, Geo g) {
-  __shared__ double sm[10][256];
+  __shared__ double sm[10][BX * BY * BZ];
   Nb n;
   double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   if (make_nb(n, g)) {
     const float* pr[3] = {px, py, pz};
     const float* bb[3] = {bx, by, bz};
@@ -609,7 +647,7 @@ __global__ void __launch_bounds__(256) k_diag_part(
   }
   for (int c = 0; c < 10; ++c) sm[c][tid] = v[c];
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = BX * BY * BZ / 2; s > 0; s >>= 1) {
     if (tid < s)
       for (int c = 0; c < 10; ++c)
         sm[c][tid] = c == 7 ? fmax(sm[c][tid], sm[c][tid + s]) : sm[c][tid] + sm[c][tid + s];
