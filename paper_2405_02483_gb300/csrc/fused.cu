@@ -22,8 +22,8 @@ namespace stg {
 // ================================================================ host =====
 
 const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_nu_raw", "k_nu_max", "k_nu_smooth",
-                                     "k_tau", "k_edge", "k_flux", "k_div", "k_update",
-                                     "k_courant", "k_diag", "k_misc"};
+                                     "k_nu_faces", "k_tau", "k_edge", "k_flux", "k_div",
+                                     "k_update", "k_courant", "k_diag", "k_misc"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -140,9 +140,10 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
                            F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
                            F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT};
   if (k.log_interp) need.push_back(F_LR);
-  if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU}) need.push_back(f);
+  if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
   if (k.visc)
-    for (int f : {F_TXX, F_TYY, F_TZZ, F_TXY, F_TYZ, F_TZX, F_RX, F_RY, F_RZ, F_WC, F_WX, F_WY, F_WZ})
+    for (int f : {F_TXX, F_TYY, F_TZZ, F_TXY, F_TYZ, F_TZX, F_RX, F_RY, F_RZ, F_WC, F_WX, F_WY, F_WZ,
+                  F_LFX, F_LFY, F_LFZ})
       need.push_back(f);
   if (k.visc && k.do_quench)
     for (int f : {F_QXX, F_QYY, F_QZZ, F_QXY, F_QYZ, F_QZX}) need.push_back(f);
@@ -192,14 +193,18 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
   dim3 gg = grid3(g), bb(BX, BY, BZ);
   const float* ls = k.log_interp ? d[F_LR] : f[0];
   if (k.log_interp) TIMED(K_LR, (k_lr<<<nb1(g.n), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
-  TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ], k, g)));
+  TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
+                                        d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
     TIMED(K_NU_RAW, (k_nu_raw<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6],
                                                  f[7], d[F_NV], k, g)));
     TIMED(K_NU_MAX, (k_nu_max<<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
     TIMED(K_NU_SMOOTH, (k_nu_smooth<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
+    TIMED(K_NU_FACES, (k_nu_faces<<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
-  TIMED(K_TAU, (k_tau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], ls, d[F_NU], d[F_LNU], f[5], f[6], f[7],
+  TIMED(K_TAU, (k_tau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
+                                        d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
+                                        f[6], f[7],
                           d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
                           d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], k, g)));
   TIMED(K_EDGE, (k_edge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],

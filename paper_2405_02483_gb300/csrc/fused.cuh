@@ -35,12 +35,14 @@ enum Fld {
   F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,  // momentum fluxes
   F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2,         // Lorentz products
   F_GX, F_GY, F_GZ, F_QT,                           // energy fluxes, -P div u + Q
+  F_LFX, F_LFY, F_LFZ,                              // ln(rho/r0) interpolated to the faces
+  F_LNX, F_LNY, F_LNZ,                              // ln<nu> interpolated to the faces
   F_COUNT
 };
 
 // Kernel identities for per-kernel timing.
-enum KId { K_LR = 0, K_VEL, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_TAU, K_EDGE, K_FLUX, K_DIV,
-           K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
+enum KId { K_LR = 0, K_VEL, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE, K_FLUX,
+           K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {

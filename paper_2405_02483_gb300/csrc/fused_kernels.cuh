@@ -92,17 +92,24 @@ __global__ void k_lr(const float* __restrict__ rd, float* __restrict__ lr, KPar 
 }
 
 // ------------------------------------------------------------- velocity ----
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(const float* __restrict__ ls,
-                                             const float* __restrict__ px,
-                                             const float* __restrict__ py,
-                                             const float* __restrict__ pz, float* __restrict__ ux,
-                                             float* __restrict__ uy, float* __restrict__ uz,
-                                             KPar k, Geo g) {
+// u_d = p_d / rho_face with rho_face = dens(dn_d ls); the face values dn_d ls
+// are also stored (lf, may be null) for the edge densities of the stresses.
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(
+    const float* __restrict__ ls, const float* __restrict__ px, const float* __restrict__ py,
+    const float* __restrict__ pz, float* __restrict__ ux, float* __restrict__ uy,
+    float* __restrict__ uz, float* __restrict__ lfx, float* __restrict__ lfy,
+    float* __restrict__ lfz, KPar k, Geo g) {
   Nb n;
   if (!make_nb(n, g)) return;
-  ux[n.c] = (LDG(px, n.c) + k.pref[0]) / dens(s_dn(AX(ls, 0)), k);
-  uy[n.c] = (LDG(py, n.c) + k.pref[1]) / dens(s_dn(AX(ls, 1)), k);
-  uz[n.c] = (LDG(pz, n.c) + k.pref[2]) / dens(s_dn(AX(ls, 2)), k);
+  const float lx = s_dn(AX(ls, 0)), ly = s_dn(AX(ls, 1)), lz = s_dn(AX(ls, 2));
+  ux[n.c] = (LDG(px, n.c) + k.pref[0]) / dens(lx, k);
+  uy[n.c] = (LDG(py, n.c) + k.pref[1]) / dens(ly, k);
+  uz[n.c] = (LDG(pz, n.c) + k.pref[2]) / dens(lz, k);
+  if (lfx) {
+    lfx[n.c] = lx;
+    lfy[n.c] = ly;
+    lfz[n.c] = lz;
+  }
 }
 
 // ---------------------------------------------------------- viscosity ------
@@ -172,26 +179,25 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_smooth(const floa
   lnu[n.c] = logf(fmaxf(v, 1e-30f));
 }
 
-// -------------------------------------------------------------- stress -----
-// Interpolation to an edge: dn along a then b of field f at the thread's cell.
-__device__ __forceinline__ float dn2(const float* __restrict__ f, const Nb& n, int a, int b) {
-  auto inner = [&](int oa) {
-    auto v = [&](int ob) {
-      int dx = (a == 0 ? oa : 0) + (b == 0 ? ob : 0);
-      int dy = (a == 1 ? oa : 0) + (b == 1 ? ob : 0);
-      int dz = (a == 2 ? oa : 0) + (b == 2 ? ob : 0);
-      return LDG(f, n.at(dx, dy, dz));
-    };
-    return s_dn(v);
-  };
-  return s_dn(inner);
+// ln<nu> interpolated to the three faces (first half of the edge values).
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_faces(
+    const float* __restrict__ lnu, float* __restrict__ lx, float* __restrict__ ly,
+    float* __restrict__ lz, Geo g) {
+  Nb n;
+  if (!make_nb(n, g)) return;
+  lx[n.c] = s_dn(AX(lnu, 0));
+  ly[n.c] = s_dn(AX(lnu, 1));
+  lz[n.c] = s_dn(AX(lnu, 2));
 }
 
+// -------------------------------------------------------------- stress -----
 // Strain, stress (eq. (itv)), J = curl B and eta J on edges, eq. (ohm).
 __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
-    const float* __restrict__ rd, const float* __restrict__ ls, const float* __restrict__ nu,
-    const float* __restrict__ lnu, const float* __restrict__ bx, const float* __restrict__ by,
+    const float* __restrict__ rd, const float* __restrict__ lfx, const float* __restrict__ lfy,
+    const float* __restrict__ lfz, const float* __restrict__ nu, const float* __restrict__ lnx,
+    const float* __restrict__ lny, const float* __restrict__ lnz,
+    const float* __restrict__ bx, const float* __restrict__ by,
     const float* __restrict__ bz, float* __restrict__ txx, float* __restrict__ tyy,
     float* __restrict__ tzz, float* __restrict__ txy, float* __restrict__ tyz,
     float* __restrict__ tzx, float* __restrict__ Rx, float* __restrict__ Ry,
@@ -217,11 +223,13 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
   txx[n.c] = (r * nxx) * (sxx + k.c1 * divu);
   tyy[n.c] = (r * nyy) * (syy + k.c1 * divu);
   tzz[n.c] = (r * nzz) * (szz + k.c1 * divu);
-  float nyz = k.rm ? k.spp[0] * expf(dn2(lnu, n, 1, 2)) : k.nu_const;
-  float nzx = k.rm ? k.spp[1] * expf(dn2(lnu, n, 2, 0)) : k.nu_const;
-  float nxy = k.rm ? k.spp[2] * expf(dn2(lnu, n, 0, 1)) : k.nu_const;
-  float ryz = dens(dn2(ls, n, 1, 2), k), rzx = dens(dn2(ls, n, 2, 0), k),
-        rxy = dens(dn2(ls, n, 0, 1), k);
+  // Edge values: the second interpolation of the face values (Ex edge from
+  // the y faces along z, Ey from the z faces along x, Ez from the x faces along y).
+  float nyz = k.rm ? k.spp[0] * expf(s_dn(AX(lny, 2))) : k.nu_const;
+  float nzx = k.rm ? k.spp[1] * expf(s_dn(AX(lnz, 0))) : k.nu_const;
+  float nxy = k.rm ? k.spp[2] * expf(s_dn(AX(lnx, 1))) : k.nu_const;
+  float ryz = dens(s_dn(AX(lfy, 2)), k), rzx = dens(s_dn(AX(lfz, 0)), k),
+        rxy = dens(s_dn(AX(lfx, 1)), k);
   float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
   float syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
   float szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
