@@ -207,11 +207,13 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
                                         f[6], f[7],
                           d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
                           d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], k, g)));
-  TIMED(K_EDGE, (k_edge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
-                           d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
-                           f[5], f[6], f[7], d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
-                           d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC], d[F_WX], d[F_WY],
-                           d[F_WZ], k, g)));
+  if (k.visc)
+    TIMED(K_EDGE, (k_edge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
+                                            d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
+                                            d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
+                                            d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
+                                            d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC],
+                                            d[F_WX], d[F_WY], d[F_WZ], k, g)));
   const bool qn = k.visc && k.do_quench;
   FluxIn fi = {f[1], f[2], f[3], f[0], f[4], f[5], f[6], f[7], ls, d[F_UX], d[F_UY], d[F_UZ],
                qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],
@@ -219,7 +221,7 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
                d[F_JX], d[F_JY], d[F_JZ], d[F_NU], d[F_WC], d[F_WX], d[F_WY], d[F_WZ]};
   FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
-                d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT]};
+                d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
   TIMED(K_FLUX, (k_flux<<<gg, bb, 0, s>>>(fi, fo, k, g)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;

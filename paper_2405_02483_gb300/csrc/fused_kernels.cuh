@@ -267,15 +267,16 @@ __device__ __forceinline__ float quench1(const float* __restrict__ T, const Nb& 
   return LDG(T, n.c) * fminf(fac, k.qlim);
 }
 
-// Quenched stresses, total E on edges and the heating densities
+// Quenched stresses, the quenched resistive field eta J (left in the E arrays,
+// where k_flux adds -u x B) and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
+// Viscous runs only.
 __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
     const float* __restrict__ Rx, const float* __restrict__ Ry, const float* __restrict__ Rz,
     const float* __restrict__ Jx, const float* __restrict__ Jy, const float* __restrict__ Jz,
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
-    const float* __restrict__ bx, const float* __restrict__ by, const float* __restrict__ bz,
     float* __restrict__ qxx, float* __restrict__ qyy, float* __restrict__ qzz,
     float* __restrict__ qxy, float* __restrict__ qyz, float* __restrict__ qzx,
     float* __restrict__ Ex, float* __restrict__ Ey, float* __restrict__ Ez,
@@ -283,20 +284,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_edge(
     float* __restrict__ wz, KPar k, Geo g) {
   Nb n;
   if (!make_nb(n, g)) return;
-  const float* B0 = k.Bref;
-  // Ideal part -u x B at the three edges.
-  float ex = -((s_dn(AX(uy, 2)) * (s_dn(AX(bz, 1)) + B0[2])) -
-               (s_dn(AX(uz, 1)) * (s_dn(AX(by, 2)) + B0[1])));
-  float ey = -((s_dn(AX(uz, 0)) * (s_dn(AX(bx, 2)) + B0[0])) -
-               (s_dn(AX(ux, 2)) * (s_dn(AX(bz, 0)) + B0[2])));
-  float ez = -((s_dn(AX(ux, 1)) * (s_dn(AX(by, 0)) + B0[1])) -
-               (s_dn(AX(uy, 0)) * (s_dn(AX(bx, 1)) + B0[0])));
-  if (!k.visc) {
-    Ex[n.c] = ex;
-    Ey[n.c] = ey;
-    Ez[n.c] = ez;
-    return;
-  }
   float txx_, tyy_, tzz_, txy_, tyz_, tzx_, rx_, ry_, rz_;
   if (k.do_quench) {
     txx_ = quench1(txx, n, 0, -1, k);
@@ -319,9 +306,9 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_edge(
     txy_ = LDG(txy, n.c); tyz_ = LDG(tyz, n.c); tzx_ = LDG(tzx, n.c);
     rx_ = LDG(Rx, n.c); ry_ = LDG(Ry, n.c); rz_ = LDG(Rz, n.c);
   }
-  Ex[n.c] = ex + rx_;
-  Ey[n.c] = ey + ry_;
-  Ez[n.c] = ez + rz_;
+  Ex[n.c] = rx_;
+  Ey[n.c] = ry_;
+  Ez[n.c] = rz_;
   const float* ih = k.ih;
   float sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
   float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
@@ -341,6 +328,7 @@ struct FluxIn {
 struct FluxOut {
   float *mxx, *myy, *mzz, *mxy, *myx, *mxz, *mzx, *myz, *mzy;
   float *lx1, *lx2, *ly1, *ly2, *lz1, *lz2, *gx, *gy, *gz, *qt;
+  float *ex, *ey, *ez;   // in: eta J (viscous runs); out: E = -u x B + eta J
 };
 
 // 2D interpolation up along a then b (edge -> centre) of f at the cell.
@@ -362,7 +350,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, Flux
   if (!make_nb(n, g)) return;
   const float* pr[3] = {in.px, in.py, in.pz};
   const float* uu[3] = {in.ux, in.uy, in.uz};
-  const float* bb[3] = {in.bx, in.by, in.bz};
   const float* qd[3] = {in.qxx, in.qyy, in.qzz};
   float* md[3] = {out.mxx, out.myy, out.mzz};
   const float Pd = k.gm1 * LDG(in.Ed, n.c);
@@ -375,31 +362,43 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, Flux
     if (k.visc) v -= LDG(qd[d], n.c);
     md[d][n.c] = v;
   }
+  // The twelve edge interpolations of u and B, shared by the off-diagonal
+  // momentum fluxes, the Lorentz products and -u x B.
+  const float* B0 = k.Bref;
+  const float uy_z = s_dn(AX(in.uy, 2)), uz_y = s_dn(AX(in.uz, 1));   // Ex edge
+  const float bz_y = s_dn(AX(in.bz, 1)) + B0[2], by_z = s_dn(AX(in.by, 2)) + B0[1];
+  const float uz_x = s_dn(AX(in.uz, 0)), ux_z = s_dn(AX(in.ux, 2));   // Ey edge
+  const float bx_z = s_dn(AX(in.bx, 2)) + B0[0], bz_x = s_dn(AX(in.bz, 0)) + B0[2];
+  const float ux_y = s_dn(AX(in.ux, 1)), uy_x = s_dn(AX(in.uy, 0));   // Ez edge
+  const float by_x = s_dn(AX(in.by, 0)) + B0[1], bx_y = s_dn(AX(in.bx, 1)) + B0[0];
   // Off-diagonal: p_d carried along axis a, at the (d, a) edge.
-  auto off = [&](int d, int a, const float* tau) {
+  auto off = [&](int d, int a, float ua, const float* tau) {
     const float* pp = pr[d];
-    const float* ua = uu[a];
-    float v = (s_dn(AX(pp, a)) + k.pref[d]) * s_dn(AX(ua, d));
+    float v = (s_dn(AX(pp, a)) + k.pref[d]) * ua;
     if (k.visc) v -= LDG(tau, n.c);
     return v;
   };
-  out.mxy[n.c] = off(0, 1, in.qxy);
-  out.myx[n.c] = off(1, 0, in.qxy);
-  out.mxz[n.c] = off(0, 2, in.qzx);
-  out.mzx[n.c] = off(2, 0, in.qzx);
-  out.myz[n.c] = off(1, 2, in.qyz);
-  out.mzy[n.c] = off(2, 1, in.qyz);
+  out.mxy[n.c] = off(0, 1, uy_x, in.qxy);
+  out.myx[n.c] = off(1, 0, ux_y, in.qxy);
+  out.mxz[n.c] = off(0, 2, uz_x, in.qzx);
+  out.mzx[n.c] = off(2, 0, ux_z, in.qzx);
+  out.myz[n.c] = off(1, 2, uz_y, in.qyz);
+  out.mzy[n.c] = off(2, 1, uy_z, in.qyz);
   // Lorentz force pieces J_a dn_d(B_b) on edges.
-  auto bdn = [&](int b, int d) {
-    const float* f = bb[b];
-    return s_dn(AX(f, d)) + k.Bref[b];
-  };
-  out.lx1[n.c] = LDG(in.Jy, n.c) * bdn(2, 0);
-  out.lx2[n.c] = LDG(in.Jz, n.c) * bdn(1, 0);
-  out.ly1[n.c] = LDG(in.Jz, n.c) * bdn(0, 1);
-  out.ly2[n.c] = LDG(in.Jx, n.c) * bdn(2, 1);
-  out.lz1[n.c] = LDG(in.Jx, n.c) * bdn(1, 2);
-  out.lz2[n.c] = LDG(in.Jy, n.c) * bdn(0, 2);
+  const float jx = LDG(in.Jx, n.c), jy = LDG(in.Jy, n.c), jz = LDG(in.Jz, n.c);
+  out.lx1[n.c] = jy * bz_x;
+  out.lx2[n.c] = jz * by_x;
+  out.ly1[n.c] = jz * bx_y;
+  out.ly2[n.c] = jx * bz_y;
+  out.lz1[n.c] = jx * by_z;
+  out.lz2[n.c] = jy * bx_z;
+  // E = -u x B (eq. ohm) plus the quenched eta J left by k_edge.
+  const float ex = -((uy_z * bz_y) - (uz_y * by_z));
+  const float ey = -((uz_x * bx_z) - (ux_z * bz_x));
+  const float ez = -((ux_y * by_x) - (uy_x * bx_y));
+  out.ex[n.c] = k.visc ? ex + out.ex[n.c] : ex;
+  out.ey[n.c] = k.visc ? ey + out.ey[n.c] : ey;
+  out.ez[n.c] = k.visc ? ez + out.ez[n.c] : ez;
   // Energy fluxes p_d dn(e) - nuE dn(rho nu_dd) dddn(e) at faces.
   float* go[3] = {out.gx, out.gy, out.gz};
   const float* rd = in.rd;
