@@ -48,10 +48,11 @@ REF_N = 96                      # per-step sample grid of the reference (oracle)
 KERNEL_ARRAYS = {"k_lr": 2, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
                  "k_nu_faces": 4, "k_tau": 26, "k_edge": 28, "k_flux": 50,
                  "k_div": (33 + 54 + 54) / 3.0, "k_update": 24}
-# DRAM bytes (read + write) per cell per launch from the ncu capture
-# summarised in profiles/k_edge_turbulence192_fused_v1.md (192^3 capture;
-# traffic grows with the cells).  Only kernels unchanged since their capture.
-NCU_TRAFFIC_PER_CELL = {"k_edge": 854.8e6 / 192 ** 3}
+# DRAM bytes (read + write) per cell per launch from the ncu captures
+# summarised in profiles/k_flux_turbulence192.md and
+# profiles/k_edge_turbulence192.md (192^3 captures; traffic grows with the
+# cells).  Only kernels unchanged since their capture.
+NCU_TRAFFIC_PER_CELL = {"k_flux": 1400.1e6 / 192 ** 3, "k_edge": 763.3e6 / 192 ** 3}
 
 
 def peaks():
