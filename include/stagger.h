@@ -69,11 +69,17 @@ typedef struct {
   double Cdt, Cdtr, Cdtd;  /* Courant factors, eq. (courantcond) (0.4,0.1,0.7)*/
   double g[3];             /* constant gravity; source rho_face * g            */
   double ref[8];           /* per-field background added to the stored values */
+  /* Newtonian cooling, eqs. (NewtonCool), (rhocool): dE/dt gains
+   * -rho (e - e_cool) / t_cool * f(rho), e = E/rho, with f = 1 (cool_cut 0),
+   * (rho/rho_cool)^2 / (1 + (rho/rho_cool)^2) (1, low-density cutoff) or
+   * 1 / (1 + (rho/rho_cool)^2) (2, high-density cutoff).  t_cool = 0: off. */
+  double t_cool, e_cool, rho_cool;
+  int cool_cut;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
  * nuE = nuB = 1, qmax 8, qlim 2, log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
- * no gravity, zero references.  Returns STAGGER_EINVAL if p is NULL. */
+ * no gravity, zero references, no cooling (rho_cool 1).  Returns STAGGER_EINVAL if p is NULL. */
 int stagger_params_default(stagger_params* p);
 
 /* Create a context for one grid and parameter set on the current CUDA device.

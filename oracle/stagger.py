@@ -27,7 +27,9 @@ path by specification only, never by code):
   R9  Courant step from the stage-1 right-hand side, held for all stages;
   R10 RK constants exactly as printed;
   R13 axes with n = 1 are skipped in dl_min, dl_max, and take dl_min as their
-      diffusion length.
+      diffusion length;
+  R16 Newtonian cooling enters the energy-per-volume equation as
+      -rho (e - e_cool)/t_cool (e relaxes to e_cool on t_cool).
 """
 from __future__ import annotations
 
@@ -103,6 +105,10 @@ class Params:
     Cdtr: float = 0.1
     Cdtd: float = 0.7
     g: tuple = (0.0, 0.0, 0.0)
+    t_cool: float = 0.0      # Newtonian cooling time (0: off), Sect. "Newtonian Cooling"
+    e_cool: float = 0.0
+    rho_cool: float = 1.0
+    cool_cut: int = 0        # 0 none, 1 low-density cutoff, 2 high-density cutoff
 
     def visc_on(self):
         return self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
@@ -305,6 +311,14 @@ def rhs_parts(f, g: Grid, p: Params):
     d_E = (-(ddup(px * dn(e, "x"), "x", hx) + ddup(py * dn(e, "y"), "y", hy)
              + ddup(pz * dn(e, "z"), "z", hz))
            - P * divu + Q + ediff[0] + ediff[1] + ediff[2])
+    if p.t_cool > 0:
+        # eq. (NewtonCool), per unit volume (reading R16): -rho (e - e_cool)/t_cool,
+        # times the density cutoff of eq. (rhocool).
+        qn = -(E - r * p.e_cool) / p.t_cool
+        if p.cool_cut:
+            x2 = (r / p.rho_cool) ** 2
+            qn = qn * ((x2 if p.cool_cut == 1 else 1.0) / (1.0 + x2))
+        d_E = d_E + qn
 
     # eq. (indu): dB/dt = -curl E.
     d_Bx = -(ddup(Ez, "y", hy) - ddup(Ey, "z", hz))

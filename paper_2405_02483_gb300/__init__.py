@@ -38,7 +38,9 @@ class Params(ctypes.Structure):
                 ("do_quench", ctypes.c_int), ("qmax", ctypes.c_double),
                 ("qlim", ctypes.c_double), ("log_interp", ctypes.c_int),
                 ("Cdt", ctypes.c_double), ("Cdtr", ctypes.c_double), ("Cdtd", ctypes.c_double),
-                ("g", ctypes.c_double * 3), ("ref", ctypes.c_double * 8)]
+                ("g", ctypes.c_double * 3), ("ref", ctypes.c_double * 8),
+                ("t_cool", ctypes.c_double), ("e_cool", ctypes.c_double),
+                ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int)]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

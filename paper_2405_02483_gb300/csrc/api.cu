@@ -37,6 +37,7 @@ int stagger_params_default(stagger_params* p) {
   p->Cdt = 0.4;
   p->Cdtr = 0.1;
   p->Cdtd = 0.7;
+  p->rho_cool = 1.0;
   return STAGGER_OK;
 }
 
@@ -65,6 +66,8 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (p->do_quench && (!(p->qmax > 0) || !(p->qlim > 0))) return STAGGER_EINVAL;
   if (!(p->Cdt > 0) || !(p->Cdtr > 0) || !(p->Cdtd > 0)) return STAGGER_EINVAL;
   if (p->ref[0] < 0) return STAGGER_EINVAL;
+  if (!(p->t_cool >= 0) || !isfinite(p->e_cool)) return STAGGER_EINVAL;
+  if (p->cool_cut < 0 || p->cool_cut > 2 || (p->cool_cut && !(p->rho_cool > 0))) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
   return STAGGER_OK;

@@ -121,6 +121,10 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.qlim = (float)p.qlim;
   k.log_interp = p.log_interp ? 1 : 0;
   k.do_quench = p.do_quench ? 1 : 0;
+  k.inv_tcool = p.t_cool > 0 ? (float)(1.0 / p.t_cool) : 0.f;
+  k.e_cool = (float)p.e_cool;
+  k.inv_rho_cool = p.cool_cut ? (float)(1.0 / p.rho_cool) : 0.f;
+  k.cool_cut = p.cool_cut;
   double dlmax = 0;
   for (int a = 0; a < 3; ++a)
     if (nn[a] > 1 || !any) dlmax = fmax(dlmax, h[a]);

@@ -21,6 +21,8 @@ struct KPar {
   float nuE, nuB, c1, inv_qmax, qlim;
   int log_interp, do_quench, r0pos;
   float g[3];
+  float inv_tcool, e_cool, inv_rho_cool;   // Newtonian cooling (inv_tcool 0: off)
+  int cool_cut;
 };
 
 // Fields of the fused path, one contiguous device array each.

@@ -434,6 +434,17 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, Flux
     float Q = LDG(in.wc, n.c) + ((up2(in.wz, n, 0, 1) + up2(in.wx, n, 1, 2)) + up2(in.wy, n, 2, 0));
     qt += Q;
   }
+  if (k.inv_tcool > 0.f) {
+    // Newtonian cooling, eq. (NewtonCool), per volume: -rho (e - e_cool) / t_cool,
+    // times the density cutoff of eq. (rhocool).
+    const float r = LDG(in.rd, n.c) + k.r0;
+    float qn = -((LDG(Ed, n.c) + k.E0) - r * k.e_cool) * k.inv_tcool;
+    if (k.cool_cut) {
+      const float x = r * k.inv_rho_cool, x2 = x * x;
+      qn *= (k.cool_cut == 1 ? x2 : 1.f) / (1.f + x2);
+    }
+    qt += qn;
+  }
   out.qt[n.c] = qt;
 }
 

@@ -343,6 +343,18 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     d_E = G.add(d_E, Q);
     for (int d = 0; d < 3; ++d) d_E = G.add(d_E, ediff[d]);
   }
+  if (p.t_cool > 0) {
+    // Newtonian cooling, eqs. (NewtonCool), (rhocool): -rho (e - e_cool) / t_cool * f(rho).
+    int qn = G.axpb(G.sub(E, G.axpb(r, p.e_cool, 0.0)), -1.0 / p.t_cool, 0.0);
+    if (p.cool_cut) {
+      int x = G.axpb(r, 1.0 / p.rho_cool, 0.0);
+      int x2 = G.mul(x, x);
+      int den = G.axpb(x2, 1.0, 1.0);
+      int fac = p.cool_cut == 1 ? G.div(x2, den) : G.div(G.cnst(1.0), den);
+      qn = G.mul(qn, fac);
+    }
+    d_E = G.add(d_E, qn);
+  }
 
   // eq. (indu): dB/dt = -curl E.
   int d_Bx = neg(G.sub(ddup(Ez, Y), ddup(Ey, Z)));

@@ -523,3 +523,36 @@ def test_viscous_and_joule_heating_closed_form(d, a):
     f[5 + d] = amp * torch.sin(k * xc)
     F = S.rhs(f, g, Params(nu_const=nu, nuB=nuB))
     assert torch.allclose(F[4], nuB * nu * base * shape_fn, rtol=1e-10, atol=1e-14)
+
+
+# ------------------------------------------------------ Newtonian cooling ----
+
+def test_newtonian_cooling_relaxation():
+    # Uniform gas at rest: only the cooling term acts; E - rho e_cool decays as
+    # exp(-t / t_cool) (RK3 error O(z^4) per step, printed constants 4e-7).
+    g = Grid(6, 5, 4, 0.1, 0.1, 0.1)
+    rho, e0, ecool, tc = 1.3, 0.9, 0.5, 0.2
+    f = [torch.full((4, 5, 6), v, dtype=DT) for v in (rho, 0, 0, 0, rho * e0, 0, 0, 0)]
+    p = Params(t_cool=tc, e_cool=ecool)
+    dt, n = 0.002, 100
+    for _ in range(n):
+        f, _ = S.step(f, g, p, dt=dt)
+    expect = rho * ecool + rho * (e0 - ecool) * math.exp(-n * dt / tc)
+    assert float(f[4][0, 0, 0]) == pytest.approx(expect, rel=1e-6)
+    for k in (0, 1, 2, 3, 5, 6, 7):
+        assert float(f[k].abs().max() - abs(float(f[k][0, 0, 0]))) == 0.0   # stays uniform
+    assert float(f[0][0, 0, 0]) == rho
+
+
+@pytest.mark.parametrize("cut,ratio,factor", [(1, 1.0, 0.5), (1, 2.0, 0.8), (2, 1.0, 0.5),
+                                              (2, 2.0, 0.2), (0, 2.0, 1.0)])
+def test_newtonian_cooling_density_cutoffs(cut, ratio, factor):
+    # eq. (rhocool): low cutoff x^2/(1+x^2), high cutoff 1/(1+x^2), x = rho/rho_cool.
+    g = Grid(4, 4, 4, 0.1, 0.1, 0.1)
+    rc, e0, ecool, tc = 0.7, 0.9, 0.3, 0.5
+    rho = ratio * rc
+    f = [torch.full((4, 4, 4), v, dtype=DT) for v in (rho, 0, 0, 0, rho * e0, 0, 0, 0)]
+    F = S.rhs(f, g, Params(t_cool=tc, e_cool=ecool, rho_cool=rc, cool_cut=cut))
+    assert float(F[4][1, 2, 3]) == pytest.approx(-rho * (e0 - ecool) / tc * factor, rel=1e-14)
+    for k in (0, 1, 2, 3, 5, 6, 7):
+        assert float(F[k].abs().max()) == 0.0
