@@ -63,6 +63,23 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(ms, device="cpu"):
+    """The slowest rank's time: every rank's result is divided by it, so the
+    job's throughput is the work of all ranks over the longest wall time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_rank, steps, ms_max, world):
+    """Whole-job zone-updates/s: replicas are independent (weak scaling)."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -243,12 +260,9 @@ def main():
     ktimes = sim.kernel_times()
     sim.timing(False)
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")
     ms_step = ms / args.steps
-    value = ws * n ** 3 * args.steps / (ms * 1e-3)
+    value = job_value(n ** 3, args.steps, ms, ws)
 
     # Dominant kernel roofline (algorithmic bytes per launch / mean launch time).
     peak, peak_kind = peaks()

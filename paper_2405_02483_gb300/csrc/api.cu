@@ -276,6 +276,23 @@ static int graph_step(stagger_ctx* c, T* f[8], double dt, cudaStream_t s) {
   return STAGGER_OK;
 }
 
+// F(f) into out[8] for the stage recompute of the adjoint.
+template <typename T>
+static int stage_rhs(stagger_ctx* c, GraphExec<T>* G, T* const f[8], T* out[8], cudaStream_t s);
+template <>
+int stage_rhs<float>(stagger_ctx* c, GraphExec<float>*, float* const f[8], float* out[8],
+                     cudaStream_t s) {
+  return fused_rhs(c->fused, f, out, s);
+}
+template <>
+int stage_rhs<double>(stagger_ctx* c, GraphExec<double>* G, double* const f[8], double* out[8],
+                      cudaStream_t s) {
+  int rc = G->forward(f, s);
+  if (rc) return rc;
+  for (int k = 0; k < 8; ++k) lin2<double>(c, out[k], G->output(k), 1.0, G->output(k), 0.0, s);
+  return STAGGER_OK;
+}
+
 // Adjoint of one fixed-dt step (see stagger_step_adjoint).
 template <typename T>
 static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* const lam_in[8],
@@ -296,15 +313,16 @@ static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* cons
     qb[k] = w + (size_t)(32 + k) * n;
   }
   const double *A = RK_ALPHA, *B = RK_BETA;
-  // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)).
-  if ((rc = G->forward(f0, s))) return rc;
+  // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)); the FP32
+  // path takes F from the fused kernels, FP64 from the graph.
+  if ((rc = stage_rhs<T>(c, G, f0, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
-    lin2<T>(c, q[k], G->output(k), 1.0, G->output(k), 0.0, s);
+    lin2<T>(c, q[k], fb[k], 1.0, fb[k], 0.0, s);
     lin2<T>(c, f1[k], f0[k], 1.0, q[k], B[0] * dt, s);
   }
-  if ((rc = G->forward(f1, s))) return rc;
+  if ((rc = stage_rhs<T>(c, G, f1, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
-    lin2<T>(c, q[k], q[k], A[1], G->output(k), 1.0, s);
+    lin2<T>(c, q[k], q[k], A[1], fb[k], 1.0, s);
     lin2<T>(c, f2[k], f1[k], 1.0, q[k], B[1] * dt, s);
   }
   // Reverse sweep: fbar_3 = lam; qbar_3 = beta_3 dt fbar.

@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
 
 // eq. (quench): T <- T min(max over the axes a0, a1 of max3(q), qlim),
 // q = |d2 T| / (M + |d2 T| / qmax), M the 3-cell max of |T| along the axis.
-__device__ __forceinline__ float quench1(const float* __restrict__ T, const Nb& n, int a0, int a1,
+template <class N>
+__device__ __forceinline__ float quench1(const float* __restrict__ T, const N& n, int a0, int a1,
                                          const KPar& k) {
   float fac = -1.f;
 #pragma unroll
@@ -332,7 +333,8 @@ struct FluxOut {
 };
 
 // 2D interpolation up along a then b (edge -> centre) of f at the cell.
-__device__ __forceinline__ float up2(const float* __restrict__ f, const Nb& n, int a, int b) {
+template <class N>
+__device__ __forceinline__ float up2(const float* __restrict__ f, const N& n, int a, int b) {
   auto inner = [&](int oa) {
     auto v = [&](int ob) {
       int dx = (a == 0 ? oa : 0) + (b == 0 ? ob : 0);
@@ -345,9 +347,9 @@ __device__ __forceinline__ float up2(const float* __restrict__ f, const Nb& n, i
   return s_up(inner);
 }
 
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
+template <class N>
+__device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const FluxOut& out,
+                                          const KPar& k) {
   const float* pr[3] = {in.px, in.py, in.pz};
   const float* uu[3] = {in.ux, in.uy, in.uz};
   const float* qd[3] = {in.qxx, in.qyy, in.qzz};
@@ -446,6 +448,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, Flux
     qt += qn;
   }
   out.qt[n.c] = qt;
+}
+
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
+  Nb n;
+  if (!make_nb(n, g)) return;
+  flux_cell(n, in, out, k);
 }
 
 // ----------------------------------------------------------- divergence ----
