@@ -5,9 +5,14 @@
 
 #include "fused.cuh"
 
-// Minimum resident blocks per SM requested from the register allocator.
+// Minimum resident blocks per SM requested from the register allocator
+// (measured per kernel at 512^3: 4 for the wide flux/stress/divergence
+// kernels, 8 where the tighter register budget was faster).
 #ifndef STG_MINB
 #define STG_MINB 4
+#endif
+#ifndef STG_MINB_HI
+#define STG_MINB_HI 8
 #endif
 
 namespace stg {
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(
 
 // ---------------------------------------------------------- viscosity ------
 // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u), centred.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_raw(const float* __restrict__ ux,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_raw(const float* __restrict__ ux,
                                                 const float* __restrict__ uy,
                                                 const float* __restrict__ uz,
                                                 const float* __restrict__ rd,
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_max(const float* 
 }
 
 // 3-cell mean along x, y and z (the 3x3x3 mean) and its logarithm.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_smooth(const float* __restrict__ a,
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_smooth(const float* __restrict__ a,
                                                    float* __restrict__ nu,
                                                    float* __restrict__ lnu, Geo g) {
   Nb n;
@@ -272,7 +277,7 @@ __device__ __forceinline__ float quench1(const float* __restrict__ T, const N& n
 // where k_flux adds -u x B) and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
 // Viscous runs only.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_edge(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
     const float* __restrict__ Rx, const float* __restrict__ Ry, const float* __restrict__ Rz,
@@ -553,7 +558,7 @@ __global__ void k_update(const float* __restrict__ f, const float* __restrict__ 
 // -------------------------------------------------------------- Courant ----
 // Per-cell wave speed c_s + c_A + |u_perp|, rate max(|dr/dt|/r, |dE/dt|/E)
 // and <nu>; block maxima to part[3*block + {0,1,2}] (as doubles).
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_courant_part(
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_courant_part(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ Ed, const float* __restrict__ bx,
     const float* __restrict__ by, const float* __restrict__ bz, const float* __restrict__ qr,
