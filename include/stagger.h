@@ -75,6 +75,11 @@ typedef struct {
    * 1 / (1 + (rho/rho_cool)^2) (2, high-density cutoff).  t_cool = 0: off. */
   double t_cool, e_cool, rho_cool;
   int cool_cut;
+  /* Smagorinsky viscosity, eq. (nusmag): dl_min * csmag * [2 (sum S_ii^2 -
+   * (div u)^2 / 3 + sum_{i != j} S_ij^2)]^(1/2) is added to the Richtmyer &
+   * Morton nu before its 3-cell max and mean, so nu_ii gains the
+   * dx_i dl_min <...> form of eq. (nuij2).  0: off. */
+  double csmag;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,

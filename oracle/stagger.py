@@ -29,7 +29,9 @@ path by specification only, never by code):
   R13 axes with n = 1 are skipped in dl_min, dl_max, and take dl_min as their
       diffusion length;
   R16 Newtonian cooling enters the energy-per-volume equation as
-      -rho (e - e_cool)/t_cool (e relaxes to e_cool on t_cool).
+      -rho (e - e_cool)/t_cool (e relaxes to e_cool on t_cool);
+  R17 Smagorinsky: dl_min * Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2
+      joins the Richtmyer-Morton nu before the max and the mean.
 """
 from __future__ import annotations
 
@@ -109,9 +111,11 @@ class Params:
     e_cool: float = 0.0
     rho_cool: float = 1.0
     cool_cut: int = 0        # 0 none, 1 low-density cutoff, 2 high-density cutoff
+    csmag: float = 0.0       # Smagorinsky constant, eq. (nusmag) (0: off)
 
     def visc_on(self):
-        return self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
+        return (self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
+                or self.csmag > 0)
 
 
 # --------------------------------------------------------------------------
@@ -226,6 +230,18 @@ def rhs_parts(f, g: Grid, p: Params):
             ca = torch.sqrt(B2 / r)
             nu = (p.nu1 * torch.sqrt(uc2) + p.nu3 * (cs + ca)
                   + p.nu2 * g.dl_min * torch.clamp(-divu, min=0.0))
+            if p.csmag > 0:
+                # eq. (nusmag), reading R17: the rate |S| times dl_min joins the
+                # velocity-like nu, with Sum_ij over i != j and the off-diagonal
+                # squares centred from the edges.
+                sxx, syy, szz = ddup(ux, "x", hx), ddup(uy, "y", hy), ddup(uz, "z", hz)
+                sxy = 0.5 * (dddn(ux, "y", hy) + dddn(uy, "x", hx))
+                syz = 0.5 * (dddn(uy, "z", hz) + dddn(uz, "y", hy))
+                szx = 0.5 * (dddn(uz, "x", hx) + dddn(ux, "z", hz))
+                s2 = (sxx * sxx + syy * syy + szz * szz - divu * divu / 3.0
+                      + 2.0 * (up(up(sxy * sxy, "x"), "y") + up(up(syz * syz, "y"), "z")
+                               + up(up(szx * szx, "z"), "x")))
+                nu = nu + p.csmag * g.dl_min * torch.sqrt(2.0 * torch.clamp(s2, min=0.0))
             out["nu_raw"] = nu
             # <nu>_{max smooth} (R5).
             for ax in "xyz":

@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
                 ("Cdt", ctypes.c_double), ("Cdtr", ctypes.c_double), ("Cdtd", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("ref", ctypes.c_double * 8),
                 ("t_cool", ctypes.c_double), ("e_cool", ctypes.c_double),
-                ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int)]
+                ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int),
+                ("csmag", ctypes.c_double)]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

@@ -61,7 +61,8 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   long long n = (long long)g->nx * g->ny * g->nz;
   if (n >= (1LL << 31)) return STAGGER_EINVAL;  // 32-bit cell offsets in the kernels
   if (!(p->gamma > 1.0)) return STAGGER_EINVAL;
-  if (p->nu1 < 0 || p->nu2 < 0 || p->nu3 < 0 || p->nu_const < 0 || p->nuE < 0 || p->nuB < 0)
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu3 < 0 || p->nu_const < 0 || p->nuE < 0 || p->nuB < 0 ||
+      p->csmag < 0)
     return STAGGER_EINVAL;
   if (p->do_quench && (!(p->qmax > 0) || !(p->qlim > 0))) return STAGGER_EINVAL;
   if (!(p->Cdt > 0) || !(p->Cdtr > 0) || !(p->Cdtd > 0)) return STAGGER_EINVAL;

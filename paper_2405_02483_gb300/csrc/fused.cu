@@ -21,9 +21,9 @@ namespace stg {
 
 // ================================================================ host =====
 
-const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_nu_raw", "k_nu_max", "k_nu_smooth",
-                                     "k_nu_faces", "k_tau", "k_edge", "k_flux", "k_div",
-                                     "k_update", "k_courant", "k_diag", "k_misc"};
+const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
+                                     "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
+                                     "k_div", "k_update", "k_courant", "k_diag", "k_misc"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -108,7 +108,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   }
   k.gamma = (float)p.gamma;
   k.gm1 = (float)(p.gamma - 1.0);
-  k.visc = (p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0) ? 1 : 0;
+  k.visc = (p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0 || p.csmag > 0) ? 1 : 0;
+  k.csmag_dl = (float)(p.csmag * dlmin);
   k.rm = k.visc && !(p.nu_const > 0);
   k.nu1 = (float)p.nu1;
   k.nu2dl = (float)(p.nu2 * dlmin);
@@ -145,6 +146,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
                            F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT};
   if (k.log_interp) need.push_back(F_LR);
   if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
+  if (k.csmag_dl > 0.f) for (int f : {F_SQXY, F_SQYZ, F_SQZX}) need.push_back(f);
   if (k.visc)
     for (int f : {F_TXX, F_TYY, F_TZZ, F_TXY, F_TYZ, F_TZX, F_RX, F_RY, F_RZ, F_WC, F_WX, F_WY, F_WZ,
                   F_LFX, F_LFY, F_LFZ})
@@ -200,8 +202,17 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
   TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
-    TIMED(K_NU_RAW, (k_nu_raw<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6],
-                                                 f[7], d[F_NV], k, g)));
+    if (k.csmag_dl > 0.f)
+      TIMED(K_STRAIN2, (k_strain2<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], d[F_SQXY], d[F_SQYZ],
+                                                    d[F_SQZX], k, g)));
+    if (k.csmag_dl > 0.f)
+      TIMED(K_NU_RAW, (k_nu_raw<true><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
+                                                         f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
+                                                         d[F_SQZX], d[F_NV], k, g)));
+    else
+      TIMED(K_NU_RAW, (k_nu_raw<false><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
+                                                          f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
+                                                          d[F_SQZX], d[F_NV], k, g)));
     TIMED(K_NU_MAX, (k_nu_max<<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
     TIMED(K_NU_SMOOTH, (k_nu_smooth<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
     TIMED(K_NU_FACES, (k_nu_faces<<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));

@@ -23,6 +23,7 @@ struct KPar {
   float g[3];
   float inv_tcool, e_cool, inv_rho_cool;   // Newtonian cooling (inv_tcool 0: off)
   int cool_cut;
+  float csmag_dl;       // Smagorinsky constant times dl_min (0: off)
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -39,12 +40,13 @@ enum Fld {
   F_GX, F_GY, F_GZ, F_QT,                           // energy fluxes, -P div u + Q
   F_LFX, F_LFY, F_LFZ,                              // ln(rho/r0) interpolated to the faces
   F_LNX, F_LNY, F_LNZ,                              // ln<nu> interpolated to the faces
+  F_SQXY, F_SQYZ, F_SQZX,                           // squared off-diagonal strain (edges)
   F_COUNT
 };
 
 // Kernel identities for per-kernel timing.
-enum KId { K_LR = 0, K_VEL, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE, K_FLUX,
-           K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
+enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {

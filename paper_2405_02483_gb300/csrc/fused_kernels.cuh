@@ -117,9 +117,42 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(
   }
 }
 
+// 2D interpolation up along a then b (edge -> centre) of f at the cell.
+template <class N>
+__device__ __forceinline__ float up2(const float* __restrict__ f, const N& n, int a, int b) {
+  auto inner = [&](int oa) {
+    auto v = [&](int ob) {
+      int dx = (a == 0 ? oa : 0) + (b == 0 ? ob : 0);
+      int dy = (a == 1 ? oa : 0) + (b == 1 ? ob : 0);
+      int dz = (a == 2 ? oa : 0) + (b == 2 ? ob : 0);
+      return LDG(f, n.at(dx, dy, dz));
+    };
+    return s_up(v);
+  };
+  return s_up(inner);
+}
+
 // ---------------------------------------------------------- viscosity ------
+// Squared off-diagonal strain on the edges (Smagorinsky runs):
+// S_xy^2 (Ez), S_yz^2 (Ex), S_zx^2 (Ey), S_ij = (dd_j u_i + dd_i u_j) / 2.
+__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_strain2(
+    const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
+    float* __restrict__ sxy2, float* __restrict__ syz2, float* __restrict__ szx2, KPar k, Geo g) {
+  Nb n;
+  if (!make_nb(n, g)) return;
+  const float* ih = k.ih;
+  float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
+  float syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
+  float szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  sxy2[n.c] = sxy * sxy;
+  syz2[n.c] = syz * syz;
+  szx2[n.c] = szx * szx;
+}
+
 // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u), centred.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_raw(const float* __restrict__ ux,
+template <bool SMAG>
+__global__ void __launch_bounds__(BX * BY * BZ, SMAG ? STG_MINB : STG_MINB_HI) k_nu_raw(
+    const float* __restrict__ ux,
                                                 const float* __restrict__ uy,
                                                 const float* __restrict__ uz,
                                                 const float* __restrict__ rd,
@@ -127,11 +160,16 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_raw(const floa
                                                 const float* __restrict__ bx,
                                                 const float* __restrict__ by,
                                                 const float* __restrict__ bz,
+                                                const float* __restrict__ sqxy,
+                                                const float* __restrict__ sqyz,
+                                                const float* __restrict__ sqzx,
                                                 float* __restrict__ nv, KPar k, Geo g) {
   Nb n;
   if (!make_nb(n, g)) return;
   float ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
-  float divu = s_du(AX(ux, 0), k.ih[0]) + s_du(AX(uy, 1), k.ih[1]) + s_du(AX(uz, 2), k.ih[2]);
+  const float sxx = s_du(AX(ux, 0), k.ih[0]), syy = s_du(AX(uy, 1), k.ih[1]),
+              szz = s_du(AX(uz, 2), k.ih[2]);
+  float divu = sxx + syy + szz;
   float nu = 0.f;
   if (k.nu1 > 0.f) nu = k.nu1 * sqrtf(ucx * ucx + ucy * ucy + ucz * ucz);
   if (k.nu3 > 0.f) {
@@ -144,6 +182,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_raw(const floa
     nu += k.nu3 * (cs + ca);
   }
   if (k.nu2dl > 0.f) nu += k.nu2dl * fmaxf(-divu, 0.f);
+  if (SMAG) {
+    // eq. (nusmag): dl_min Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2.
+    float s2 = ((sxx * sxx + syy * syy) + szz * szz) - divu * divu * (1.f / 3.f);
+    s2 += 2.f * ((up2(sqxy, n, 0, 1) + up2(sqyz, n, 1, 2)) + up2(sqzx, n, 2, 0));
+    nu += k.csmag_dl * sqrtf(2.f * fmaxf(s2, 0.f));
+  }
   nv[n.c] = nu;
 }
 
@@ -337,20 +381,6 @@ struct FluxOut {
   float *ex, *ey, *ez;   // in: eta J (viscous runs); out: E = -u x B + eta J
 };
 
-// 2D interpolation up along a then b (edge -> centre) of f at the cell.
-template <class N>
-__device__ __forceinline__ float up2(const float* __restrict__ f, const N& n, int a, int b) {
-  auto inner = [&](int oa) {
-    auto v = [&](int ob) {
-      int dx = (a == 0 ? oa : 0) + (b == 0 ? ob : 0);
-      int dy = (a == 1 ? oa : 0) + (b == 1 ? ob : 0);
-      int dz = (a == 2 ? oa : 0) + (b == 2 ? ob : 0);
-      return LDG(f, n.at(dx, dy, dz));
-    };
-    return s_up(v);
-  };
-  return s_up(inner);
-}
 
 template <class N>
 __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const FluxOut& out,

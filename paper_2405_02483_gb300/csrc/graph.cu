@@ -202,7 +202,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   int Ey = neg(G.sub(G.mul(dn(u[Z], X), dn(B[X], Z)), G.mul(dn(u[X], Z), dn(B[Z], X))));
   int Ez = neg(G.sub(G.mul(dn(u[X], Y), dn(B[Y], X)), G.mul(dn(u[Y], X), dn(B[X], Y))));
 
-  const bool visc = p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0;
+  const bool visc = p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0 || p.csmag > 0;
   int Q = -1, txx = -1, tyy = -1, tzz = -1, txy = -1, tyz = -1, tzx = -1;
   int ediff[3] = {-1, -1, -1};
   if (visc) {
@@ -224,6 +224,19 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
         acc(G.axpb(G.add(cs, ca), p.nu3, 0.0));
       }
       if (p.nu2 > 0) acc(G.axpb(G.cmin(neg(divu), 0.0), p.nu2 * dlmin, 0.0));
+      if (p.csmag > 0) {
+        // eq. (nusmag): dl_min Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2.
+        int sxx = ddup(u[X], X), syy = ddup(u[Y], Y), szz = ddup(u[Z], Z);
+        int sxy = G.axpb(G.add(dddn(u[X], Y), dddn(u[Y], X)), 0.5, 0.0);
+        int syz = G.axpb(G.add(dddn(u[Y], Z), dddn(u[Z], Y)), 0.5, 0.0);
+        int szx = G.axpb(G.add(dddn(u[Z], X), dddn(u[X], Z)), 0.5, 0.0);
+        int dia = G.add(G.add(G.mul(sxx, sxx), G.mul(syy, syy)), G.mul(szz, szz));
+        dia = G.sub(dia, G.axpb(G.mul(divu, divu), 1.0 / 3.0, 0.0));
+        int offd = G.add(G.add(up(up(G.mul(sxy, sxy), X), Y), up(up(G.mul(syz, syz), Y), Z)),
+                         up(up(G.mul(szx, szx), Z), X));
+        int s2 = G.add(dia, G.axpb(offd, 2.0, 0.0));
+        acc(G.axpb(G.sq(G.axpb(G.cmin(s2, 0.0), 2.0, 0.0)), p.csmag * dlmin, 0.0));
+      }
       // <nu>_{max smooth}: 3-cell max along x, y, z, then 3-cell mean.
       for (int ax = 0; ax < 3; ++ax) nu = G.maxi(G.maxi(G.shift(nu, ax, -1), nu), G.shift(nu, ax, 1));
       for (int ax = 0; ax < 3; ++ax)

@@ -122,6 +122,10 @@ CASES = {
     "ragged_visc_cooling_lowcut": (
         lambda: ragged_state((29, 18, 13)),
         dict(VISC_KW, t_cool=0.05, e_cool=0.7, rho_cool=1.02, cool_cut=1)),
+    "ragged_smagorinsky_rm_quench": (
+        lambda: ragged_state((26, 21, 10)), dict(VISC_KW, csmag=0.15)),
+    "ragged_smagorinsky_only": (
+        lambda: ragged_state((19, 23, 12)), dict(csmag=0.2, nuE=0.8, nuB=0.9)),
     "ragged_ideal_cooling_highcut": (
         lambda: ragged_state((21, 16, 12)), dict(t_cool=0.1, e_cool=0.8, rho_cool=0.98, cool_cut=2)),
 }
@@ -191,7 +195,8 @@ def test_linear_waves_one_and_fifty_steps(S):
 @pytest.mark.parametrize("name,nsteps", [("ot3d24_visc_quench", 3), ("ot2d_64x64x1_visc_quench", 10),
                                          ("ragged37x29x11_visc_quench", 3),
                                          ("ragged_const_nu_c1_gravity_nolog", 3),
-                                         ("ragged_visc_cooling_lowcut", 3)])
+                                         ("ragged_visc_cooling_lowcut", 3),
+                                         ("ragged_smagorinsky_rm_quench", 3)])
 def test_viscous_steps(S, name, nsteps):
     w, kw = _case(name)
     sim, refs, dev = make(S, w, kw)

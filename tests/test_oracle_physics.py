@@ -556,3 +556,52 @@ def test_newtonian_cooling_density_cutoffs(cut, ratio, factor):
     assert float(F[4][1, 2, 3]) == pytest.approx(-rho * (e0 - ecool) / tc * factor, rel=1e-14)
     for k in (0, 1, 2, 3, 5, 6, 7):
         assert float(F[k].abs().max()) == 0.0
+
+
+# -------------------------------------------------------------- Smagorinsky --
+
+def test_smagorinsky_shear_closed_form():
+    # u_x(y) = a sin(k y): S_xy = 1/2 dddn_y u_x on Ez edges; the centred
+    # square is (a D/2h)^2 (1 + I(2 th) cos 2ky)/2, so eq. (nusmag) gives
+    # nu = C dl_min [ (a D/h)^2 (1 + I(2 th) cos 2ky) / 2 ]^1/2.
+    n, m, a, C = 24, 3, 0.3, 0.17
+    h = 1.0 / n
+    g = Grid(4, n, 1, 0.37, h, 0.5)
+    shape = (1, n, 4)
+    yc = ((torch.arange(n, dtype=DT) + 0.5) * h).reshape(1, n, 1).expand(shape)
+    k = 2 * math.pi * m
+    th = k * h
+    one = torch.ones(shape, dtype=DT)
+    f = [one, a * torch.sin(k * yc), 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    nu = S.rhs_parts(f, g, Params(csmag=C))["nu_raw"]
+    expect = C * g.dl_min * torch.sqrt(0.5 * (a * D_sym(th) / h) ** 2 * (1 + I_sym(2 * th) * torch.cos(2 * k * yc)))
+    assert torch.allclose(nu, expect, rtol=1e-12, atol=1e-14)
+
+
+def test_smagorinsky_dilatation_closed_form():
+    # u_x(x) = a sin(k x): S_xx = div u, so S_ii^2 - (div u)^2/3 = 2/3 S_xx^2 and
+    # nu = C dl_min (4/3)^1/2 |S_xx|.
+    n, m, a, C = 24, 2, 0.2, 0.12
+    h = 1.0 / n
+    g = Grid(n, 4, 4, h, 0.3, 0.3)
+    shape = (4, 4, n)
+    xf = (torch.arange(n, dtype=DT) * h).reshape(1, 1, n).expand(shape)
+    xc = xf + 0.5 * h
+    k = 2 * math.pi * m
+    one = torch.ones(shape, dtype=DT)
+    f = [one, a * torch.sin(k * xf), 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    nu = S.rhs_parts(f, g, Params(csmag=C))["nu_raw"]
+    sxx = a * D_sym(k * h) / h * torch.cos(k * xc)
+    assert torch.allclose(nu, C * g.dl_min * math.sqrt(4.0 / 3.0) * sxx.abs(), rtol=1e-12, atol=1e-14)
+
+
+SMAG = Params(nu3=0.02, csmag=0.15, do_quench=True, t_cool=0.3, e_cool=0.8)
+
+
+def test_smagorinsky_cooling_symmetry_and_conservation():
+    test_cyclic_axis_permutation(SMAG)
+    test_conservation_and_divb(SMAG)
+    g = Grid(8, 6, 5, 0.1, 0.2, 0.3)
+    vals = (1.3, 0.2, -0.1, 0.3, 1.3 * 0.8, 0.1, 0.2, 0.5)
+    fu = [torch.full((5, 6, 8), v, dtype=DT) for v in vals]
+    assert all(float(d.abs().max()) == 0.0 for d in S.rhs(fu, g, SMAG))
