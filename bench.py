@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--scalar-cells", action="store_true",
+                    help="one cell per thread in the fused kernels (default: four x-cells)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -231,7 +233,7 @@ def main():
     w = inputs.turbulence(n, device="cuda")
     refs, dev = S.split_state(w.fields)
     del w
-    params = S.default_params(ref=refs, **PHYS)
+    params = S.default_params(ref=refs, scalar_cells=int(args.scalar_cells), **PHYS)
     sim = S.Sim((n, n, n), (1.0 / n,) * 3, params)
     stream = torch.cuda.current_stream()
 

@@ -80,6 +80,12 @@ typedef struct {
    * Morton nu before its 3-cell max and mean, so nu_ii gains the
    * dx_i dl_min <...> form of eq. (nuij2).  0: off. */
   double csmag;
+  /* Thread mapping of the fused FP32 kernels (no effect on the results beyond
+   * rounding order).  0 (default): four consecutive x-cells per thread with
+   * 16-byte loads and stores wherever nx % 4 == 0 and every array of the call
+   * is 16-byte aligned, one cell per thread otherwise; 1: one cell per thread
+   * everywhere.  Other values: STAGGER_EINVAL. */
+  int scalar_cells;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,

@@ -69,6 +69,7 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (p->ref[0] < 0) return STAGGER_EINVAL;
   if (!(p->t_cool >= 0) || !isfinite(p->e_cool)) return STAGGER_EINVAL;
   if (p->cool_cut < 0 || p->cool_cut > 2 || (p->cool_cut && !(p->rho_cool > 0))) return STAGGER_EINVAL;
+  if (p->scalar_cells < 0 || p->scalar_cells > 1) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
   return STAGGER_OK;

@@ -74,8 +74,22 @@ static dim3 grid3(const Geo& g) {
 }
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
 
+// Grid of the per-cell kernels for cell type N (N::W consecutive x-cells per thread).
+template <class N> static dim3 grid_cells(const Geo& g) {
+  return dim3((unsigned)((g.nx + BX * N::W - 1) / (BX * N::W)), (unsigned)((g.ny + BY - 1) / BY),
+              (unsigned)((g.nz + BZ - 1) / BZ));
+}
+
+// Four-cell threads need 16-byte aligned arrays (the workspace always is).
+static bool aligned16(float* const* a, int n) {
+  uintptr_t u = 0;
+  for (int i = 0; i < n; ++i) u |= (uintptr_t)a[i];
+  return (u & 15) == 0;
+}
+
 int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.geo = make_geo(gr.nx, gr.ny, gr.nz);
+  F.cells4 = (gr.nx % 4) == 0 && !p.scalar_cells;
   F.launches = 0;
   F.timing = 0;
   for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
@@ -140,6 +154,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   for (int c = 0; c < 8; ++c) F.q[c] = F.ping[c] = F.pong[c] = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
+  F.cmax = nullptr;
   // Which intermediate fields this parameter set needs.
   std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
                            F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
@@ -164,6 +179,11 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   }
   dim3 gg = grid3(F.geo);
   F.red_blocks = (int)(gg.x * gg.y * gg.z);
+  if (cudaMalloc(&F.cmax, sizeof(unsigned) * 4) != cudaSuccess ||
+      cudaMemset(F.cmax, 0, sizeof(unsigned) * 4) != cudaSuccess) {
+    fused_release(F);
+    return STAGGER_EOOM;
+  }
   if (cudaMalloc(&F.dt_dev, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc(&F.red, sizeof(double) * 10 * (size_t)F.red_blocks) != cudaSuccess) {
     fused_release(F);
@@ -186,44 +206,47 @@ void fused_release(Fused& F) {
   }
   if (F.dt_dev) cudaFree(F.dt_dev);
   if (F.red) cudaFree(F.red);
+  if (F.cmax) cudaFree(F.cmax);
+  F.cmax = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
 
 // Everything up to (not including) the divergence kernel: primitives,
 // viscosity, stresses, edge fields and fluxes of state f.
-static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
+template <class N>
+static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
   const Geo& g = F.geo;
   const KPar& k = F.kp;
   float** d = F.fld;
-  dim3 gg = grid3(g), bb(BX, BY, BZ);
+  const dim3 gg = grid_cells<N>(g), bb(BX, BY, BZ);
   const float* ls = k.log_interp ? d[F_LR] : f[0];
-  if (k.log_interp) TIMED(K_LR, (k_lr<<<nb1(g.n), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
-  TIMED(K_VEL, (k_vel<<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
+  if (k.log_interp) TIMED(K_LR, (k_lr<N><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
+  TIMED(K_VEL, (k_vel<N><<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
     if (k.csmag_dl > 0.f)
-      TIMED(K_STRAIN2, (k_strain2<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], d[F_SQXY], d[F_SQYZ],
+      TIMED(K_STRAIN2, (k_strain2<N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], d[F_SQXY], d[F_SQYZ],
                                                     d[F_SQZX], k, g)));
     if (k.csmag_dl > 0.f)
-      TIMED(K_NU_RAW, (k_nu_raw<true><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
+      TIMED(K_NU_RAW, (k_nu_raw<true, N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
                                                          f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
                                                          d[F_SQZX], d[F_NV], k, g)));
     else
-      TIMED(K_NU_RAW, (k_nu_raw<false><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
+      TIMED(K_NU_RAW, (k_nu_raw<false, N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
                                                           f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
                                                           d[F_SQZX], d[F_NV], k, g)));
-    TIMED(K_NU_MAX, (k_nu_max<<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
-    TIMED(K_NU_SMOOTH, (k_nu_smooth<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
-    TIMED(K_NU_FACES, (k_nu_faces<<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
+    TIMED(K_NU_MAX, (k_nu_max<N><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
+    TIMED(K_NU_SMOOTH, (k_nu_smooth<N><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
+    TIMED(K_NU_FACES, (k_nu_faces<N><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
-  TIMED(K_TAU, (k_tau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
+  TIMED(K_TAU, (k_tau<N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
                                         d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
                                         f[6], f[7],
                           d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
                           d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], k, g)));
   if (k.visc)
-    TIMED(K_EDGE, (k_edge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
+    TIMED(K_EDGE, (k_edge<N><<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
                                             d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
                                             d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
                                             d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
@@ -237,9 +260,13 @@ static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
   FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
                 d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
-  TIMED(K_FLUX, (k_flux<<<gg, bb, 0, s>>>(fi, fo, k, g)));
+  TIMED(K_FLUX, (k_flux<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
+}
+
+static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
+  return F.cells4 && aligned16(f, 8) ? pre_div_t<Nb4>(F, f, s) : pre_div_t<Nb>(F, f, s);
 }
 
 static DivIn div_in(Fused& F, float* const f[8]) {
@@ -260,10 +287,12 @@ static DivIn div_in(Fused& F, float* const f[8]) {
 static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
                       float beta, int mode, cudaStream_t s) {
   DivIn di = div_in(F, f);
-  dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
   float* oo[8];
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
-  TIMED(K_DIV, (k_div<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], oo[0],
+  const bool v4 = F.cells4 && aligned16(f, 8) && aligned16(q, 8) && aligned16(oo, 8);
+  const dim3 gg = v4 ? grid_cells<Nb4>(F.geo) : grid_cells<Nb>(F.geo), bb(BX, BY, BZ);
+  auto kern = v4 ? k_div<Nb4> : k_div<Nb>;
+  TIMED(K_DIV, (kern<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], oo[0],
                                         oo[1], oo[2], oo[3], oo[4], oo[5], oo[6], oo[7], alpha,
                                         beta, F.dt_dev, mode, F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
@@ -280,10 +309,17 @@ static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s) {
   // Uses the primitives and <nu> that pre_div left for this state and q = F(f).
   const Geo& g = F.geo;
   const KPar& k = F.kp;
-  dim3 gg = grid3(g), bb(BX, BY, BZ);
-  TIMED(K_COURANT, (k_courant_part<<<gg, bb, 0, s>>>(F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0],
-                                                     f[4], f[5], f[6], f[7], F.q[0], F.q[4],
-                                                     F.fld[F_NU], F.red, k, g)));
+  const dim3 bb(BX, BY, BZ);
+  if (F.cells4 && aligned16(f, 8))
+    TIMED(K_COURANT, (k_courant_part<Nb4><<<grid_cells<Nb4>(g), bb, 0, s>>>(
+                         F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0], f[4], f[5], f[6], f[7],
+                         F.q[0], F.q[4], F.fld[F_NU], F.cmax, k, g)));
+  else
+    TIMED(K_COURANT, (k_courant_part<Nb><<<grid_cells<Nb>(g), bb, 0, s>>>(
+                         F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0], f[4], f[5], f[6], f[7],
+                         F.q[0], F.q[4], F.fld[F_NU], F.cmax, k, g)));
+  TIMED(K_COURANT, (k_courant_final<<<1, 32, 0, s>>>(F.cmax, F.dt_dev, F.cdt, F.cdtr, F.cdtd,
+                                                     F.dlmin, F.dfac, F.kp.rm)));
   return STAGGER_OK;
 }
 
@@ -303,9 +339,6 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
       rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0.f, 0, s);
       if (rc) return rc;
       courant_to_dev(F, st_in[0], s);
-      TIMED(K_COURANT, (k_courant_final<<<1, 256, 0, s>>>(F.red, F.red_blocks, F.dt_dev, F.cdt,
-                                                          F.cdtr, F.cdtd, F.dlmin, F.dfac,
-                                                          F.kp.rm)));
       Upd8 u;
       int vec = (F.geo.n % 4) == 0;
       for (int c = 0; c < 8; ++c) {
@@ -336,8 +369,6 @@ int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaSt
   rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s);
   if (rc) return rc;
   courant_to_dev(F, f, s);
-  TIMED(K_COURANT, (k_courant_final<<<1, 256, 0, s>>>(F.red, F.red_blocks, F.dt_dev, F.cdt,
-                                                      F.cdtr, F.cdtd, F.dlmin, F.dfac, F.kp.rm)));
   double h[4];
   STG_CUDA_OK(cudaMemcpyAsync(h, F.dt_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
   STG_CUDA_OK(cudaStreamSynchronize(s));

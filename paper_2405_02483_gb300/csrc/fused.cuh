@@ -58,8 +58,10 @@ struct Fused {
   float* pong[8];
   double cdt, cdtr, cdtd, dlmin, dfac;  // Courant factors, dl_min, diffusion factor
   double* dt_dev;       // device step and the three limits
-  double* red;          // reduction partials
+  double* red;          // reduction partials (diagnostics)
+  unsigned* cmax;       // Courant maxima as float bits, cleared by each final pass
   int red_blocks;
+  int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   long long launches;
   // Optional per-kernel timing with CUDA events on the launch stream.
   int timing;

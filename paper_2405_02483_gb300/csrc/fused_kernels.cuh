@@ -14,6 +14,17 @@
 #ifndef STG_MINB_HI
 #define STG_MINB_HI 8
 #endif
+// Four-cell threads (Nb4) hold four times the live values of a one-cell
+// thread: 2 blocks per SM (128 registers) by default, 3 (80 registers) or 4
+// (64) where that measured faster at 512^3.
+#ifndef STG_MINB4
+#define STG_MINB4 2
+#endif
+#ifndef STG_MINB4_HI
+#define STG_MINB4_HI 3
+#endif
+#define STG_LB(N, minb) __launch_bounds__(BX * BY * BZ, (N::W == 4 ? STG_MINB4 : (minb)))
+#define STG_LB_HI(N, minb) __launch_bounds__(BX * BY * BZ, (N::W == 4 ? STG_MINB4_HI : (minb)))
 
 namespace stg {
 
@@ -35,8 +46,79 @@ namespace stg {
 #define DB_ (-0.065104166666666667f)
 #define DC_ 0.0046875f
 
+// Four consecutive x-cells of one thread, element-wise arithmetic.  The
+// per-cell kernels are templates over the cell type (Nb: one cell, Nb4: four
+// cells) and write their arithmetic once on the value type N::T.
+struct F4 {
+  float v[4];
+  F4() = default;
+  __device__ __forceinline__ F4(float s) { v[0] = v[1] = v[2] = v[3] = s; }
+  __device__ __forceinline__ F4(float a, float b, float c, float d) {
+    v[0] = a; v[1] = b; v[2] = c; v[3] = d;
+  }
+};
+#define STG_F4_BIN(op)                                                        \
+  __device__ __forceinline__ F4 operator op(const F4& a, const F4& b) {       \
+    return F4(a.v[0] op b.v[0], a.v[1] op b.v[1], a.v[2] op b.v[2], a.v[3] op b.v[3]); \
+  }
+STG_F4_BIN(+)
+STG_F4_BIN(-)
+STG_F4_BIN(*)
+STG_F4_BIN(/)
+#undef STG_F4_BIN
+__device__ __forceinline__ F4 operator-(const F4& a) { return F4(-a.v[0], -a.v[1], -a.v[2], -a.v[3]); }
+__device__ __forceinline__ F4& operator+=(F4& a, const F4& b) { return a = a + b; }
+__device__ __forceinline__ F4& operator-=(F4& a, const F4& b) { return a = a - b; }
+__device__ __forceinline__ F4& operator*=(F4& a, const F4& b) { return a = a * b; }
+// The float versions stay visible next to the F4 overloads below.
+using ::expf;
+using ::fabsf;
+using ::fmaxf;
+using ::fminf;
+using ::log1pf;
+using ::logf;
+using ::sqrtf;
+#define STG_F4_FN1(fn)                                                        \
+  __device__ __forceinline__ F4 fn(const F4& a) {                             \
+    return F4(::fn(a.v[0]), ::fn(a.v[1]), ::fn(a.v[2]), ::fn(a.v[3]));        \
+  }
+#define STG_F4_FN2(fn)                                                        \
+  __device__ __forceinline__ F4 fn(const F4& a, const F4& b) {                \
+    return F4(::fn(a.v[0], b.v[0]), ::fn(a.v[1], b.v[1]), ::fn(a.v[2], b.v[2]), \
+              ::fn(a.v[3], b.v[3]));                                          \
+  }
+STG_F4_FN1(fabsf)
+STG_F4_FN1(sqrtf)
+STG_F4_FN1(expf)
+STG_F4_FN1(logf)
+STG_F4_FN1(log1pf)
+STG_F4_FN2(fmaxf)
+STG_F4_FN2(fminf)
+#undef STG_F4_FN1
+#undef STG_F4_FN2
+
+// Quotient through the special-function reciprocal (__fdividef, within 2 ulp)
+// for divisors that are a density or a quench denominator (>= 1e-30): both
+// stay far inside the [2^-126, 2^126] range where that intrinsic is accurate.
+#ifndef STG_FASTDIV
+#define STG_FASTDIV 1
+#endif
+__device__ __forceinline__ float fdiv(float a, float b) {
+#if STG_FASTDIV
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+__device__ __forceinline__ F4 fdiv(const F4& a, const F4& b) {
+  return F4(fdiv(a.v[0], b.v[0]), fdiv(a.v[1], b.v[1]), fdiv(a.v[2], b.v[2]),
+            fdiv(a.v[3], b.v[3]));
+}
+
 // Periodic neighbour offsets of one cell, offsets -3..3 per axis.
 struct Nb {
+  using T = float;
+  static constexpr int W = 1;
   int c;
   int x[7];
   int y[7];
@@ -47,6 +129,21 @@ struct Nb {
   __device__ __forceinline__ int ax(int axis, int o) const {
     return axis == 0 ? at(o, 0, 0) : axis == 1 ? at(0, o, 0) : at(0, 0, o);
   }
+  __device__ __forceinline__ bool init(const Geo& g);
+  // Loads through the read-only path (arrays not written by the launch).
+  __device__ __forceinline__ float ld(const float* __restrict__ p) const { return __ldg(p + c); }
+  __device__ __forceinline__ float ldat(const float* __restrict__ p, int dx, int dy, int dz) const {
+    return __ldg(p + at(dx, dy, dz));
+  }
+  __device__ __forceinline__ float lda(const float* __restrict__ p, int axis, int o) const {
+    return __ldg(p + ax(axis, o));
+  }
+  // Plain load of the cell's own element of an array the launch rewrites.
+  __device__ __forceinline__ float ldw(const float* p) const { return p[c]; }
+  __device__ __forceinline__ void st(float* p, float v) const { p[c] = v; }
+  // W consecutive elements at p (element-wise kernels).
+  static __device__ __forceinline__ float ldp(const float* __restrict__ p) { return __ldg(p); }
+  static __device__ __forceinline__ void stp(float* p, float v) { *p = v; }
 };
 
 __device__ __forceinline__ bool make_nb(Nb& n, const Geo& g) {
@@ -63,69 +160,132 @@ __device__ __forceinline__ bool make_nb(Nb& n, const Geo& g) {
   n.c = n.z[3] + n.y[3] + n.x[3];
   return true;
 }
+__device__ __forceinline__ bool Nb::init(const Geo& g) { return make_nb(*this, g); }
+
+// Four consecutive x-cells i0..i0+3 (i0 a multiple of 4; requires nx % 4 == 0
+// and 16-byte aligned arrays): every tap is one 16-byte load, and the x taps
+// are register shifts of the aligned 4-cell chunks left, at and right of i0.
+struct Nb4 {
+  using T = F4;
+  static constexpr int W = 4;
+  int c;        // offset of cell i0
+  int x0, xl, xr;   // x of the chunk at, left of and right of i0 (periodic)
+  int y[7];
+  int z[7];
+  __device__ __forceinline__ bool init(const Geo& g) {
+    int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return false;
+    x0 = i;
+    xl = wrap(i - 4, g.nx);
+    xr = wrap(i + 4, g.nx);
+#pragma unroll
+    for (int o = -3; o <= 3; ++o) {
+      y[o + 3] = wrap(j + o, g.ny) * (int)g.sy;
+      z[o + 3] = wrap(k + o, g.nz) * (int)g.sz;
+    }
+    c = z[3] + y[3] + x0;
+    return true;
+  }
+  static __device__ __forceinline__ F4 v4(float4 a) { return F4(a.x, a.y, a.z, a.w); }
+  static __device__ __forceinline__ F4 row(const float* __restrict__ p, int off) {
+    return v4(__ldg(reinterpret_cast<const float4*>(p + off)));
+  }
+  // Elements s..s+3 of the 8-cell window (a, b), s in 1..3.
+  static __device__ __forceinline__ F4 shift(const F4& a, const F4& b, int s) {
+    return s == 1 ? F4(a.v[1], a.v[2], a.v[3], b.v[0])
+         : s == 2 ? F4(a.v[2], a.v[3], b.v[0], b.v[1])
+                  : F4(a.v[3], b.v[0], b.v[1], b.v[2]);
+  }
+  __device__ __forceinline__ F4 ld(const float* __restrict__ p) const { return row(p, c); }
+  __device__ __forceinline__ F4 ldat(const float* __restrict__ p, int dx, int dy, int dz) const {
+    const int r = z[dz + 3] + y[dy + 3];
+    if (dx == 0) return row(p, r + x0);
+    if (dx < 0) return shift(row(p, r + xl), row(p, r + x0), 4 + dx);
+    return shift(row(p, r + x0), row(p, r + xr), dx);
+  }
+  __device__ __forceinline__ F4 lda(const float* __restrict__ p, int axis, int o) const {
+    return axis == 0 ? ldat(p, o, 0, 0) : axis == 1 ? ldat(p, 0, o, 0) : ldat(p, 0, 0, o);
+  }
+  __device__ __forceinline__ F4 ldw(const float* p) const {
+    return v4(*reinterpret_cast<const float4*>(p + c));
+  }
+  __device__ __forceinline__ void st(float* p, const F4& v) const { stp(p + c, v); }
+  static __device__ __forceinline__ F4 ldp(const float* __restrict__ p) { return row(p, 0); }
+  static __device__ __forceinline__ void stp(float* p, const F4& v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+  }
+};
 
 // eq. (interp) to i+1/2 / i-1/2 and eq. (deriv) to i+1/2 / i-1/2, on a
 // functor v(o) giving the operand at offset o along the stencil axis.
-template <class V> __device__ __forceinline__ float s_up(V v) {
+template <class V> __device__ __forceinline__ auto s_up(V v) -> decltype(v(0)) {
   return IA_ * (v(0) + v(1)) + IB_ * (v(-1) + v(2)) + IC_ * (v(-2) + v(3));
 }
-template <class V> __device__ __forceinline__ float s_dn(V v) {
+template <class V> __device__ __forceinline__ auto s_dn(V v) -> decltype(v(0)) {
   return IA_ * (v(-1) + v(0)) + IB_ * (v(-2) + v(1)) + IC_ * (v(-3) + v(2));
 }
-template <class V> __device__ __forceinline__ float s_du(V v, float ih) {
+template <class V> __device__ __forceinline__ auto s_du(V v, float ih) -> decltype(v(0)) {
   return (DA_ * (v(1) - v(0)) + DB_ * (v(2) - v(-1)) + DC_ * (v(3) - v(-2))) * ih;
 }
-template <class V> __device__ __forceinline__ float s_dd(V v, float ih) {
+template <class V> __device__ __forceinline__ auto s_dd(V v, float ih) -> decltype(v(0)) {
   return (DA_ * (v(0) - v(-1)) + DB_ * (v(1) - v(-2)) + DC_ * (v(2) - v(-3))) * ih;
 }
 
 #define LDG(p, i) __ldg((p) + (i))
-// Operand functors along one axis of a field at the thread's cell.
-#define AX(fp, axis) [&](int o) { return LDG(fp, n.ax(axis, o)); }
+// Operand functors along one axis of a field at the thread's cell(s).
+#define AX(fp, axis) [&](int o) { return n.lda(fp, axis, o); }
 
-__device__ __forceinline__ float dens(float t, const KPar& k) {
+template <class T> __device__ __forceinline__ T dens(T t, const KPar& k) {
   if (k.log_interp) return k.r0pos ? k.r0 * expf(t) : expf(t);
   return k.r0 + t;
 }
 
 // ----------------------------------------------------------------- lr ------
+// ln(rho / r0) = log1p(rho' / r0) of the stored deviation (ln rho if r0 = 0),
+// N::W consecutive cells per thread (n a multiple of N::W).
+template <class N>
 __global__ void k_lr(const float* __restrict__ rd, float* __restrict__ lr, KPar k, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  using T = typename N::T;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * N::W;
   if (i >= n) return;
-  float r = rd[i];
-  lr[i] = k.r0pos ? log1pf(r / k.r0) : logf(r);
+  const T r = N::ldp(rd + i);
+  N::stp(lr + i, k.r0pos ? log1pf(r / k.r0) : logf(r));
 }
 
 // ------------------------------------------------------------- velocity ----
 // u_d = p_d / rho_face with rho_face = dens(dn_d ls); the face values dn_d ls
 // are also stored (lf, may be null) for the edge densities of the stresses.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_vel(
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_vel(
     const float* __restrict__ ls, const float* __restrict__ px, const float* __restrict__ py,
     const float* __restrict__ pz, float* __restrict__ ux, float* __restrict__ uy,
     float* __restrict__ uz, float* __restrict__ lfx, float* __restrict__ lfy,
     float* __restrict__ lfz, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  const float lx = s_dn(AX(ls, 0)), ly = s_dn(AX(ls, 1)), lz = s_dn(AX(ls, 2));
-  ux[n.c] = (LDG(px, n.c) + k.pref[0]) / dens(lx, k);
-  uy[n.c] = (LDG(py, n.c) + k.pref[1]) / dens(ly, k);
-  uz[n.c] = (LDG(pz, n.c) + k.pref[2]) / dens(lz, k);
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  const T lx = s_dn(AX(ls, 0)), ly = s_dn(AX(ls, 1)), lz = s_dn(AX(ls, 2));
+  n.st(ux, fdiv(n.ld(px) + k.pref[0], dens(lx, k)));
+  n.st(uy, fdiv(n.ld(py) + k.pref[1], dens(ly, k)));
+  n.st(uz, fdiv(n.ld(pz) + k.pref[2], dens(lz, k)));
   if (lfx) {
-    lfx[n.c] = lx;
-    lfy[n.c] = ly;
-    lfz[n.c] = lz;
+    n.st(lfx, lx);
+    n.st(lfy, ly);
+    n.st(lfz, lz);
   }
 }
 
 // 2D interpolation up along a then b (edge -> centre) of f at the cell.
 template <class N>
-__device__ __forceinline__ float up2(const float* __restrict__ f, const N& n, int a, int b) {
+__device__ __forceinline__ typename N::T up2(const float* __restrict__ f, const N& n, int a, int b) {
   auto inner = [&](int oa) {
     auto v = [&](int ob) {
       int dx = (a == 0 ? oa : 0) + (b == 0 ? ob : 0);
       int dy = (a == 1 ? oa : 0) + (b == 1 ? ob : 0);
       int dz = (a == 2 ? oa : 0) + (b == 2 ? ob : 0);
-      return LDG(f, n.at(dx, dy, dz));
+      return n.ldat(f, dx, dy, dz);
     };
     return s_up(v);
   };
@@ -135,23 +295,26 @@ __device__ __forceinline__ float up2(const float* __restrict__ f, const N& n, in
 // ---------------------------------------------------------- viscosity ------
 // Squared off-diagonal strain on the edges (Smagorinsky runs):
 // S_xy^2 (Ez), S_yz^2 (Ex), S_zx^2 (Ey), S_ij = (dd_j u_i + dd_i u_j) / 2.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_strain2(
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_strain2(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     float* __restrict__ sxy2, float* __restrict__ syz2, float* __restrict__ szx2, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
   const float* ih = k.ih;
-  float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  float syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  float szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
-  sxy2[n.c] = sxy * sxy;
-  syz2[n.c] = syz * syz;
-  szx2[n.c] = szx * szx;
+  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
+  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
+  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  n.st(sxy2, sxy * sxy);
+  n.st(syz2, syz * syz);
+  n.st(szx2, szx * szx);
 }
 
 // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u), centred.
-template <bool SMAG>
-__global__ void __launch_bounds__(BX * BY * BZ, SMAG ? STG_MINB : STG_MINB_HI) k_nu_raw(
+template <bool SMAG, class N>
+__global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : STG_MINB)
+                                                          : (SMAG ? STG_MINB : STG_MINB_HI)) k_nu_raw(
     const float* __restrict__ ux,
                                                 const float* __restrict__ uy,
                                                 const float* __restrict__ uz,
@@ -164,84 +327,92 @@ __global__ void __launch_bounds__(BX * BY * BZ, SMAG ? STG_MINB : STG_MINB_HI) k
                                                 const float* __restrict__ sqyz,
                                                 const float* __restrict__ sqzx,
                                                 float* __restrict__ nv, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  float ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
-  const float sxx = s_du(AX(ux, 0), k.ih[0]), syy = s_du(AX(uy, 1), k.ih[1]),
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
+  const T sxx = s_du(AX(ux, 0), k.ih[0]), syy = s_du(AX(uy, 1), k.ih[1]),
               szz = s_du(AX(uz, 2), k.ih[2]);
-  float divu = sxx + syy + szz;
-  float nu = 0.f;
+  T divu = sxx + syy + szz;
+  T nu = 0.f;
   if (k.nu1 > 0.f) nu = k.nu1 * sqrtf(ucx * ucx + ucy * ucy + ucz * ucz);
   if (k.nu3 > 0.f) {
-    float bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
+    T bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
           bcz = s_up(AX(bz, 2)) + k.Bref[2];
-    float r = LDG(rd, n.c) + k.r0;
-    float P = k.gm1 * (LDG(Ed, n.c) + k.E0);
-    float cs = sqrtf(k.gamma * P / r);
-    float ca = sqrtf((bcx * bcx + bcy * bcy + bcz * bcz) / r);
+    T r = n.ld(rd) + k.r0;
+    T P = k.gm1 * (n.ld(Ed) + k.E0);
+    T cs = sqrtf(k.gamma * P / r);
+    T ca = sqrtf((bcx * bcx + bcy * bcy + bcz * bcz) / r);
     nu += k.nu3 * (cs + ca);
   }
   if (k.nu2dl > 0.f) nu += k.nu2dl * fmaxf(-divu, 0.f);
   if (SMAG) {
     // eq. (nusmag): dl_min Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2.
-    float s2 = ((sxx * sxx + syy * syy) + szz * szz) - divu * divu * (1.f / 3.f);
+    T s2 = ((sxx * sxx + syy * syy) + szz * szz) - divu * divu * (1.f / 3.f);
     s2 += 2.f * ((up2(sqxy, n, 0, 1) + up2(sqyz, n, 1, 2)) + up2(sqzx, n, 2, 0));
     nu += k.csmag_dl * sqrtf(2.f * fmaxf(s2, 0.f));
   }
-  nv[n.c] = nu;
+  n.st(nv, nu);
 }
 
 // 3-cell max along x, y and z: the maximum over the 3x3x3 neighbourhood.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_max(const float* __restrict__ a,
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_nu_max(const float* __restrict__ a,
                                                 float* __restrict__ b, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  float m = -INFINITY;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  T m = -INFINITY;
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) m = fmaxf(m, LDG(a, n.at(dx, dy, dz)));
-  b[n.c] = m;
+      for (int dx = -1; dx <= 1; ++dx) m = fmaxf(m, n.ldat(a, dx, dy, dz));
+  n.st(b, m);
 }
 
 // 3-cell mean along x, y and z (the 3x3x3 mean) and its logarithm.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_nu_smooth(const float* __restrict__ a,
+template <class N>
+__global__ void STG_LB(N, STG_MINB_HI) k_nu_smooth(const float* __restrict__ a,
                                                    float* __restrict__ nu,
                                                    float* __restrict__ lnu, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  float sz = 0.f;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  T sz = 0.f;
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz) {
-    float sy = 0.f;
+    T sy = 0.f;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
-      float sx = LDG(a, n.at(-1, dy, dz)) + LDG(a, n.at(0, dy, dz)) + LDG(a, n.at(1, dy, dz));
+      T sx = n.ldat(a, -1, dy, dz) + n.ldat(a, 0, dy, dz) + n.ldat(a, 1, dy, dz);
       sy += sx;
     }
     sz += sy;
   }
-  float v = sz * (1.f / 27.f);
-  nu[n.c] = v;
-  lnu[n.c] = logf(fmaxf(v, 1e-30f));
+  T v = sz * (1.f / 27.f);
+  n.st(nu, v);
+  n.st(lnu, logf(fmaxf(v, 1e-30f)));
 }
 
 // ln<nu> interpolated to the three faces (first half of the edge values).
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_nu_faces(
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_nu_faces(
     const float* __restrict__ lnu, float* __restrict__ lx, float* __restrict__ ly,
     float* __restrict__ lz, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  lx[n.c] = s_dn(AX(lnu, 0));
-  ly[n.c] = s_dn(AX(lnu, 1));
-  lz[n.c] = s_dn(AX(lnu, 2));
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  n.st(lx, s_dn(AX(lnu, 0)));
+  n.st(ly, s_dn(AX(lnu, 1)));
+  n.st(lz, s_dn(AX(lnu, 2)));
 }
 
 // -------------------------------------------------------------- stress -----
 // Strain, stress (eq. (itv)), J = curl B and eta J on edges, eq. (ohm).
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
+template <class N>
+__global__ void STG_LB_HI(N, STG_MINB) k_tau(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ lfx, const float* __restrict__ lfy,
     const float* __restrict__ lfz, const float* __restrict__ nu, const float* __restrict__ lnx,
@@ -252,76 +423,79 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_tau(
     float* __restrict__ tzx, float* __restrict__ Rx, float* __restrict__ Ry,
     float* __restrict__ Rz, float* __restrict__ Jx, float* __restrict__ Jy,
     float* __restrict__ Jz, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
   const float* ih = k.ih;
-  float jx = s_dd(AX(bz, 1), ih[1]) - s_dd(AX(by, 2), ih[2]);
-  float jy = s_dd(AX(bx, 2), ih[2]) - s_dd(AX(bz, 0), ih[0]);
-  float jz = s_dd(AX(by, 0), ih[0]) - s_dd(AX(bx, 1), ih[1]);
-  Jx[n.c] = jx;
-  Jy[n.c] = jy;
-  Jz[n.c] = jz;
+  T jx = s_dd(AX(bz, 1), ih[1]) - s_dd(AX(by, 2), ih[2]);
+  T jy = s_dd(AX(bx, 2), ih[2]) - s_dd(AX(bz, 0), ih[0]);
+  T jz = s_dd(AX(by, 0), ih[0]) - s_dd(AX(bx, 1), ih[1]);
+  n.st(Jx, jx);
+  n.st(Jy, jy);
+  n.st(Jz, jz);
   if (!k.visc) return;
-  float sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
-  float divu = (sxx + syy) + szz;
-  float r = LDG(rd, n.c) + k.r0;
-  float nuc = k.rm ? LDG(nu, n.c) : 0.f;
-  float nxx = k.rm ? k.sp[0] * nuc : k.nu_const;
-  float nyy = k.rm ? k.sp[1] * nuc : k.nu_const;
-  float nzz = k.rm ? k.sp[2] * nuc : k.nu_const;
-  txx[n.c] = (r * nxx) * (sxx + k.c1 * divu);
-  tyy[n.c] = (r * nyy) * (syy + k.c1 * divu);
-  tzz[n.c] = (r * nzz) * (szz + k.c1 * divu);
+  T sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
+  T divu = (sxx + syy) + szz;
+  T r = n.ld(rd) + k.r0;
+  T nuc = k.rm ? n.ld(nu) : 0.f;
+  T nxx = k.rm ? k.sp[0] * nuc : k.nu_const;
+  T nyy = k.rm ? k.sp[1] * nuc : k.nu_const;
+  T nzz = k.rm ? k.sp[2] * nuc : k.nu_const;
+  n.st(txx, (r * nxx) * (sxx + k.c1 * divu));
+  n.st(tyy, (r * nyy) * (syy + k.c1 * divu));
+  n.st(tzz, (r * nzz) * (szz + k.c1 * divu));
   // Edge values: the second interpolation of the face values (Ex edge from
   // the y faces along z, Ey from the z faces along x, Ez from the x faces along y).
-  float nyz = k.rm ? k.spp[0] * expf(s_dn(AX(lny, 2))) : k.nu_const;
-  float nzx = k.rm ? k.spp[1] * expf(s_dn(AX(lnz, 0))) : k.nu_const;
-  float nxy = k.rm ? k.spp[2] * expf(s_dn(AX(lnx, 1))) : k.nu_const;
-  float ryz = dens(s_dn(AX(lfy, 2)), k), rzx = dens(s_dn(AX(lfz, 0)), k),
+  T nyz = k.rm ? k.spp[0] * expf(s_dn(AX(lny, 2))) : k.nu_const;
+  T nzx = k.rm ? k.spp[1] * expf(s_dn(AX(lnz, 0))) : k.nu_const;
+  T nxy = k.rm ? k.spp[2] * expf(s_dn(AX(lnx, 1))) : k.nu_const;
+  T ryz = dens(s_dn(AX(lfy, 2)), k), rzx = dens(s_dn(AX(lfz, 0)), k),
         rxy = dens(s_dn(AX(lfx, 1)), k);
-  float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  float syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  float szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
-  txy[n.c] = (rxy * nxy) * sxy;
-  tyz[n.c] = (ryz * nyz) * syz;
-  tzx[n.c] = (rzx * nzx) * szx;
-  Rx[n.c] = (k.nuB * nyz) * jx;
-  Ry[n.c] = (k.nuB * nzx) * jy;
-  Rz[n.c] = (k.nuB * nxy) * jz;
+  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
+  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
+  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  n.st(txy, (rxy * nxy) * sxy);
+  n.st(tyz, (ryz * nyz) * syz);
+  n.st(tzx, (rzx * nzx) * szx);
+  n.st(Rx, (k.nuB * nyz) * jx);
+  n.st(Ry, (k.nuB * nzx) * jy);
+  n.st(Rz, (k.nuB * nxy) * jz);
 }
 
 // eq. (quench): T <- T min(max over the axes a0, a1 of max3(q), qlim),
 // q = |d2 T| / (M + |d2 T| / qmax), M the 3-cell max of |T| along the axis.
 template <class N>
-__device__ __forceinline__ float quench1(const float* __restrict__ T, const N& n, int a0, int a1,
-                                         const KPar& k) {
-  float fac = -1.f;
+__device__ __forceinline__ typename N::T quench1(const float* __restrict__ f, const N& n, int a0,
+                                                 int a1, const KPar& k) {
+  using T = typename N::T;
+  T fac = -1.f;
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
     int a = t == 0 ? a0 : a1;
     if (a < 0) continue;
-    float v[5];
+    T v[5];
 #pragma unroll
-    for (int o = -2; o <= 2; ++o) v[o + 2] = LDG(T, n.ax(a, o));
-    float m = -1.f;
+    for (int o = -2; o <= 2; ++o) v[o + 2] = n.lda(f, a, o);
+    T m = -1.f;
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
-      float d2 = (v[o + 2] - 2.f * v[o + 1]) + v[o];
-      float a2 = fabsf(d2);
-      float M = fmaxf(fmaxf(fabsf(v[o]), fabsf(v[o + 1])), fabsf(v[o + 2]));
-      float q = a2 / ((M + a2 * k.inv_qmax) + 1e-30f);
+      T d2 = (v[o + 2] - 2.f * v[o + 1]) + v[o];
+      T a2 = fabsf(d2);
+      T M = fmaxf(fmaxf(fabsf(v[o]), fabsf(v[o + 1])), fabsf(v[o + 2]));
+      T q = fdiv(a2, (M + a2 * k.inv_qmax) + 1e-30f);
       m = fmaxf(m, q);
     }
     fac = fmaxf(fac, m);
   }
-  return LDG(T, n.c) * fminf(fac, k.qlim);
+  return n.ld(f) * fminf(fac, T(k.qlim));
 }
 
 // Quenched stresses, the quenched resistive field eta J (left in the E arrays,
 // where k_flux adds -u x B) and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
 // Viscous runs only.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_edge(
+template <class N>
+__global__ void STG_LB(N, STG_MINB_HI) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
     const float* __restrict__ Rx, const float* __restrict__ Ry, const float* __restrict__ Rz,
@@ -332,9 +506,10 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_edge(
     float* __restrict__ Ex, float* __restrict__ Ey, float* __restrict__ Ez,
     float* __restrict__ wc, float* __restrict__ wx, float* __restrict__ wy,
     float* __restrict__ wz, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
-  float txx_, tyy_, tzz_, txy_, tyz_, tzx_, rx_, ry_, rz_;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  T txx_, tyy_, tzz_, txy_, tyz_, tzx_, rx_, ry_, rz_;
   if (k.do_quench) {
     txx_ = quench1(txx, n, 0, -1, k);
     tyy_ = quench1(tyy, n, 1, -1, k);
@@ -345,29 +520,29 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_edge(
     rx_ = quench1(Rx, n, 1, 2, k);
     ry_ = quench1(Ry, n, 2, 0, k);
     rz_ = quench1(Rz, n, 0, 1, k);
-    qxx[n.c] = txx_;
-    qyy[n.c] = tyy_;
-    qzz[n.c] = tzz_;
-    qxy[n.c] = txy_;
-    qyz[n.c] = tyz_;
-    qzx[n.c] = tzx_;
+    n.st(qxx, txx_);
+    n.st(qyy, tyy_);
+    n.st(qzz, tzz_);
+    n.st(qxy, txy_);
+    n.st(qyz, tyz_);
+    n.st(qzx, tzx_);
   } else {
-    txx_ = LDG(txx, n.c); tyy_ = LDG(tyy, n.c); tzz_ = LDG(tzz, n.c);
-    txy_ = LDG(txy, n.c); tyz_ = LDG(tyz, n.c); tzx_ = LDG(tzx, n.c);
-    rx_ = LDG(Rx, n.c); ry_ = LDG(Ry, n.c); rz_ = LDG(Rz, n.c);
+    txx_ = n.ld(txx); tyy_ = n.ld(tyy); tzz_ = n.ld(tzz);
+    txy_ = n.ld(txy); tyz_ = n.ld(tyz); tzx_ = n.ld(tzx);
+    rx_ = n.ld(Rx); ry_ = n.ld(Ry); rz_ = n.ld(Rz);
   }
-  Ex[n.c] = rx_;
-  Ey[n.c] = ry_;
-  Ez[n.c] = rz_;
+  n.st(Ex, rx_);
+  n.st(Ey, ry_);
+  n.st(Ez, rz_);
   const float* ih = k.ih;
-  float sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
-  float sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  float syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  float szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
-  wc[n.c] = (txx_ * sxx + tyy_ * syy) + tzz_ * szz;
-  wx[n.c] = 2.f * (tyz_ * syz) + rx_ * LDG(Jx, n.c);
-  wy[n.c] = 2.f * (tzx_ * szx) + ry_ * LDG(Jy, n.c);
-  wz[n.c] = 2.f * (txy_ * sxy) + rz_ * LDG(Jz, n.c);
+  T sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
+  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
+  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
+  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  n.st(wc, (txx_ * sxx + tyy_ * syy) + tzz_ * szz);
+  n.st(wx, 2.f * (tyz_ * syz) + rx_ * n.ld(Jx));
+  n.st(wy, 2.f * (tzx_ * szx) + ry_ * n.ld(Jy));
+  n.st(wz, 2.f * (txy_ * sxy) + rz_ * n.ld(Jz));
 }
 
 // ---------------------------------------------------------------- flux -----
@@ -385,109 +560,114 @@ struct FluxOut {
 template <class N>
 __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const FluxOut& out,
                                           const KPar& k) {
+  using T = typename N::T;
   const float* pr[3] = {in.px, in.py, in.pz};
   const float* uu[3] = {in.ux, in.uy, in.uz};
   const float* qd[3] = {in.qxx, in.qyy, in.qzz};
   float* md[3] = {out.mxx, out.myy, out.mzz};
-  const float Pd = k.gm1 * LDG(in.Ed, n.c);
+  const T Pd = k.gm1 * n.ld(in.Ed);
   // Diagonal momentum flux at centres: up(p_d) up(u_d) + P - tau_dd.
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float* pp = pr[d];
     const float* up_ = uu[d];
-    float v = (s_up(AX(pp, d)) + k.pref[d]) * s_up(AX(up_, d)) + Pd;
-    if (k.visc) v -= LDG(qd[d], n.c);
-    md[d][n.c] = v;
+    T v = (s_up(AX(pp, d)) + k.pref[d]) * s_up(AX(up_, d)) + Pd;
+    if (k.visc) v -= n.ld(qd[d]);
+    n.st(md[d], v);
   }
-  // The twelve edge interpolations of u and B, shared by the off-diagonal
-  // momentum fluxes, the Lorentz products and -u x B.
+  // Per edge, the four interpolations of u and B shared by its two
+  // off-diagonal momentum fluxes, its two Lorentz products J_a dn(B_b) and
+  // E = -u x B (eq. ohm) plus the quenched eta J left by k_edge.  One edge at a
+  // time keeps four of the twelve values live.
   const float* B0 = k.Bref;
-  const float uy_z = s_dn(AX(in.uy, 2)), uz_y = s_dn(AX(in.uz, 1));   // Ex edge
-  const float bz_y = s_dn(AX(in.bz, 1)) + B0[2], by_z = s_dn(AX(in.by, 2)) + B0[1];
-  const float uz_x = s_dn(AX(in.uz, 0)), ux_z = s_dn(AX(in.ux, 2));   // Ey edge
-  const float bx_z = s_dn(AX(in.bx, 2)) + B0[0], bz_x = s_dn(AX(in.bz, 0)) + B0[2];
-  const float ux_y = s_dn(AX(in.ux, 1)), uy_x = s_dn(AX(in.uy, 0));   // Ez edge
-  const float by_x = s_dn(AX(in.by, 0)) + B0[1], bx_y = s_dn(AX(in.bx, 1)) + B0[0];
   // Off-diagonal: p_d carried along axis a, at the (d, a) edge.
-  auto off = [&](int d, int a, float ua, const float* tau) {
+  auto off = [&](int d, int a, T ua, const float* tau) {
     const float* pp = pr[d];
-    float v = (s_dn(AX(pp, a)) + k.pref[d]) * ua;
-    if (k.visc) v -= LDG(tau, n.c);
+    T v = (s_dn(AX(pp, a)) + k.pref[d]) * ua;
+    if (k.visc) v -= n.ld(tau);
     return v;
   };
-  out.mxy[n.c] = off(0, 1, uy_x, in.qxy);
-  out.myx[n.c] = off(1, 0, ux_y, in.qxy);
-  out.mxz[n.c] = off(0, 2, uz_x, in.qzx);
-  out.mzx[n.c] = off(2, 0, ux_z, in.qzx);
-  out.myz[n.c] = off(1, 2, uz_y, in.qyz);
-  out.mzy[n.c] = off(2, 1, uy_z, in.qyz);
-  // Lorentz force pieces J_a dn_d(B_b) on edges.
-  const float jx = LDG(in.Jx, n.c), jy = LDG(in.Jy, n.c), jz = LDG(in.Jz, n.c);
-  out.lx1[n.c] = jy * bz_x;
-  out.lx2[n.c] = jz * by_x;
-  out.ly1[n.c] = jz * bx_y;
-  out.ly2[n.c] = jx * bz_y;
-  out.lz1[n.c] = jx * by_z;
-  out.lz2[n.c] = jy * bx_z;
-  // E = -u x B (eq. ohm) plus the quenched eta J left by k_edge.
-  const float ex = -((uy_z * bz_y) - (uz_y * by_z));
-  const float ey = -((uz_x * bx_z) - (ux_z * bz_x));
-  const float ez = -((ux_y * by_x) - (uy_x * bx_y));
-  out.ex[n.c] = k.visc ? ex + out.ex[n.c] : ex;
-  out.ey[n.c] = k.visc ? ey + out.ey[n.c] : ey;
-  out.ez[n.c] = k.visc ? ez + out.ez[n.c] : ez;
+  {  // Ex edge (i, j-1/2, k-1/2)
+    const T uy_z = s_dn(AX(in.uy, 2)), uz_y = s_dn(AX(in.uz, 1));
+    const T bz_y = s_dn(AX(in.bz, 1)) + B0[2], by_z = s_dn(AX(in.by, 2)) + B0[1];
+    n.st(out.myz, off(1, 2, uz_y, in.qyz));
+    n.st(out.mzy, off(2, 1, uy_z, in.qyz));
+    const T jx = n.ld(in.Jx);
+    n.st(out.ly2, jx * bz_y);
+    n.st(out.lz1, jx * by_z);
+    const T ex = -((uy_z * bz_y) - (uz_y * by_z));
+    n.st(out.ex, k.visc ? ex + n.ldw(out.ex) : ex);
+  }
+  {  // Ey edge (i-1/2, j, k-1/2)
+    const T uz_x = s_dn(AX(in.uz, 0)), ux_z = s_dn(AX(in.ux, 2));
+    const T bx_z = s_dn(AX(in.bx, 2)) + B0[0], bz_x = s_dn(AX(in.bz, 0)) + B0[2];
+    n.st(out.mxz, off(0, 2, uz_x, in.qzx));
+    n.st(out.mzx, off(2, 0, ux_z, in.qzx));
+    const T jy = n.ld(in.Jy);
+    n.st(out.lx1, jy * bz_x);
+    n.st(out.lz2, jy * bx_z);
+    const T ey = -((uz_x * bx_z) - (ux_z * bz_x));
+    n.st(out.ey, k.visc ? ey + n.ldw(out.ey) : ey);
+  }
+  {  // Ez edge (i-1/2, j-1/2, k)
+    const T ux_y = s_dn(AX(in.ux, 1)), uy_x = s_dn(AX(in.uy, 0));
+    const T by_x = s_dn(AX(in.by, 0)) + B0[1], bx_y = s_dn(AX(in.bx, 1)) + B0[0];
+    n.st(out.mxy, off(0, 1, uy_x, in.qxy));
+    n.st(out.myx, off(1, 0, ux_y, in.qxy));
+    const T jz = n.ld(in.Jz);
+    n.st(out.lx2, jz * by_x);
+    n.st(out.ly1, jz * bx_y);
+    const T ez = -((ux_y * by_x) - (uy_x * bx_y));
+    n.st(out.ez, k.visc ? ez + n.ldw(out.ez) : ez);
+  }
   // Energy fluxes p_d dn(e) - nuE dn(rho nu_dd) dddn(e) at faces.
   float* go[3] = {out.gx, out.gy, out.gz};
   const float* rd = in.rd;
   const float* Ed = in.Ed;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    auto e_at = [&](int o) {
-      int i = n.ax(d, o);
-      return (LDG(Ed, i) + k.E0) / (LDG(rd, i) + k.r0);
-    };
-    float v = (LDG(pr[d], n.c) + k.pref[d]) * s_dn(e_at);
+    auto e_at = [&](int o) { return fdiv(n.lda(Ed, d, o) + k.E0, n.lda(rd, d, o) + k.r0); };
+    T v = (n.ld(pr[d]) + k.pref[d]) * s_dn(e_at);
     if (k.visc) {
       auto ed_at = [&](int o) {
-        int i = n.ax(d, o);
-        float r = LDG(rd, i) + k.r0;
-        return (LDG(Ed, i) - k.e0 * LDG(rd, i)) / r;
+        const T rdo = n.lda(rd, d, o);
+        return fdiv(n.lda(Ed, d, o) - k.e0 * rdo, rdo + k.r0);
       };
       auto rn_at = [&](int o) {
-        int i = n.ax(d, o);
-        float r = LDG(rd, i) + k.r0;
-        return r * (k.rm ? k.sp[d] * LDG(in.nu, i) : k.nu_const);
+        const T r = n.lda(rd, d, o) + k.r0;
+        return r * (k.rm ? k.sp[d] * n.lda(in.nu, d, o) : T(k.nu_const));
       };
       v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, k.ih[d]));
     }
-    go[d][n.c] = v;
+    n.st(go[d], v);
   }
   // -P div u + Q, Q = w_c + up up of the edge heating densities.
-  float divu = (s_du(AX(in.ux, 0), k.ih[0]) + s_du(AX(in.uy, 1), k.ih[1])) +
+  T divu = (s_du(AX(in.ux, 0), k.ih[0]) + s_du(AX(in.uy, 1), k.ih[1])) +
                s_du(AX(in.uz, 2), k.ih[2]);
-  float P = k.gm1 * (LDG(Ed, n.c) + k.E0);
-  float qt = -P * divu;
+  T P = k.gm1 * (n.ld(Ed) + k.E0);
+  T qt = -P * divu;
   if (k.visc) {
-    float Q = LDG(in.wc, n.c) + ((up2(in.wz, n, 0, 1) + up2(in.wx, n, 1, 2)) + up2(in.wy, n, 2, 0));
+    T Q = n.ld(in.wc) + ((up2(in.wz, n, 0, 1) + up2(in.wx, n, 1, 2)) + up2(in.wy, n, 2, 0));
     qt += Q;
   }
   if (k.inv_tcool > 0.f) {
     // Newtonian cooling, eq. (NewtonCool), per volume: -rho (e - e_cool) / t_cool,
     // times the density cutoff of eq. (rhocool).
-    const float r = LDG(in.rd, n.c) + k.r0;
-    float qn = -((LDG(Ed, n.c) + k.E0) - r * k.e_cool) * k.inv_tcool;
+    const T r = n.ld(in.rd) + k.r0;
+    T qn = -((n.ld(Ed) + k.E0) - r * k.e_cool) * k.inv_tcool;
     if (k.cool_cut) {
-      const float x = r * k.inv_rho_cool, x2 = x * x;
+      const T x = r * k.inv_rho_cool, x2 = x * x;
       qn *= (k.cool_cut == 1 ? x2 : 1.f) / (1.f + x2);
     }
     qt += qn;
   }
-  out.qt[n.c] = qt;
+  n.st(out.qt, qt);
 }
 
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
+template <class N>
+__global__ void STG_LB_HI(N, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
+  N n;
+  if (!n.init(g)) return;
   flux_cell(n, in, out, k);
 }
 
@@ -501,18 +681,20 @@ struct DivIn {
 
 // F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q.
 // mode 0: write F to q only; 1: also update with dt from *dtp.
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
                                              float* q4, float* q5, float* q6, float* q7,
                                              float* o0, float* o1, float* o2, float* o3,
                                              float* o4, float* o5, float* o6, float* o7,
                                              float alpha, float beta, const double* dtp,
                                              int mode, KPar k, Geo g) {
-  Nb n;
-  if (!make_nb(n, g)) return;
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
   const float* ih = k.ih;
-  float F[8];
+  T F[8];
   F[0] = -((s_du(AX(in.px, 0), ih[0]) + s_du(AX(in.py, 1), ih[1])) + s_du(AX(in.pz, 2), ih[2]));
-  float t;
+  T t;
   t = -s_dd(AX(in.mxx, 0), ih[0]);
   t -= s_du(AX(in.mxy, 1), ih[1]);
   t -= s_du(AX(in.mxz, 2), ih[2]);
@@ -535,7 +717,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_div(DivIn in, float*
   if (k.g[2] != 0.f) t += dens(s_dn(AX(in.ls, 2)), k) * k.g[2];
   F[3] = t;
   F[4] = -((s_du(AX(in.gx, 0), ih[0]) + s_du(AX(in.gy, 1), ih[1])) + s_du(AX(in.gz, 2), ih[2])) +
-         LDG(in.qt, n.c);
+         n.ld(in.qt);
   F[5] = -(s_du(AX(in.Ez, 1), ih[1]) - s_du(AX(in.Ey, 2), ih[2]));
   F[6] = -(s_du(AX(in.Ex, 2), ih[2]) - s_du(AX(in.Ez, 0), ih[0]));
   F[7] = -(s_du(AX(in.Ey, 0), ih[0]) - s_du(AX(in.Ex, 1), ih[1]));
@@ -544,9 +726,9 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_div(DivIn in, float*
   float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float qq = alpha != 0.f ? alpha * qs[c][n.c] + F[c] : F[c];
-    qs[c][n.c] = qq;
-    if (mode) os[c][n.c] = LDG(in.f[c], n.c) + bdt * qq;
+    T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F[c] : F[c];
+    n.st(qs[c], qq);
+    if (mode) n.st(os[c], n.ld(in.f[c]) + bdt * qq);
   }
 }
 
@@ -586,80 +768,87 @@ __global__ void k_update(const float* __restrict__ f, const float* __restrict__ 
 }
 
 // -------------------------------------------------------------- Courant ----
+// Non-negative maxima kept as the bits of a float: for x >= 0 (and +inf) the
+// unsigned order of the bit patterns is the numeric order.  NaN maps to +inf
+// (it must win the maximum) and anything below +0, -0 included, to +0.
+__device__ __forceinline__ unsigned max_bits(float v) {
+  if (!(v == v)) v = INFINITY;
+  return __float_as_uint(v > 0.f ? v : 0.f);
+}
+__device__ __forceinline__ unsigned max_bits(const F4& v) {
+  return max(max(max_bits(v.v[0]), max_bits(v.v[1])), max(max_bits(v.v[2]), max_bits(v.v[3])));
+}
+// |u_perp|^2 = u^2 - (u.B)^2 / B^2, and u^2 where B = 0.
+__device__ __forceinline__ float uperp2(float u2, float ub, float B2) {
+  return B2 > 0.f ? u2 - ub * ub / B2 : u2;
+}
+__device__ __forceinline__ F4 uperp2(const F4& u2, const F4& ub, const F4& B2) {
+  return F4(uperp2(u2.v[0], ub.v[0], B2.v[0]), uperp2(u2.v[1], ub.v[1], B2.v[1]),
+            uperp2(u2.v[2], ub.v[2], B2.v[2]), uperp2(u2.v[3], ub.v[3], B2.v[3]));
+}
+
 // Per-cell wave speed c_s + c_A + |u_perp|, rate max(|dr/dt|/r, |dE/dt|/E)
-// and <nu>; block maxima to part[3*block + {0,1,2}] (as doubles).
-__global__ void __launch_bounds__(BX * BY * BZ, STG_MINB_HI) k_courant_part(
+// and <nu>; their maxima over the mesh into cmax[0..2] (float bits, atomic).
+template <class N>
+__global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? STG_MINB : STG_MINB_HI) k_courant_part(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ Ed, const float* __restrict__ bx,
     const float* __restrict__ by, const float* __restrict__ bz, const float* __restrict__ qr,
-    const float* __restrict__ qE, const float* __restrict__ nu, double* part, KPar k, Geo g) {
-  __shared__ float sm[3][BX * BY * BZ];
-  Nb n;
-  float w = 0.f, rate = 0.f, nuv = 0.f;
-  int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
-  if (make_nb(n, g)) {
-    float ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
-    float bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
-          bcz = s_up(AX(bz, 2)) + k.Bref[2];
-    float r = LDG(rd, n.c) + k.r0;
-    float E = LDG(Ed, n.c) + k.E0;
-    float cs = sqrtf(k.gamma * (k.gm1 * E) / r);
-    float B2 = bcx * bcx + bcy * bcy + bcz * bcz;
-    float ca = sqrtf(B2 / r);
-    float u2 = ucx * ucx + ucy * ucy + ucz * ucz;
-    float ub = ucx * bcx + ucy * bcy + ucz * bcz;
-    float up2 = B2 > 0.f ? u2 - ub * ub / B2 : u2;
-    w = cs + ca + sqrtf(fmaxf(up2, 0.f));
-    rate = fmaxf(fabsf(LDG(qr, n.c)) / r, fabsf(LDG(qE, n.c)) / E);
-    if (k.visc) nuv = k.rm ? LDG(nu, n.c) : k.nu_const;
-    // A NaN anywhere must survive the max: map it to +inf.
-    if (!(w == w)) w = INFINITY;
-    if (!(rate == rate)) rate = INFINITY;
-    if (!(nuv == nuv)) nuv = INFINITY;
+    const float* __restrict__ qE, const float* __restrict__ nu, unsigned* cmax, KPar k, Geo g) {
+  using T = typename N::T;
+  __shared__ unsigned sm[3][BX * BY * BZ / 32];
+  N n;
+  unsigned m[3] = {0u, 0u, 0u};
+  if (n.init(g)) {
+    T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
+    T bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
+      bcz = s_up(AX(bz, 2)) + k.Bref[2];
+    T r = n.ld(rd) + k.r0;
+    T E = n.ld(Ed) + k.E0;
+    T cs = sqrtf(k.gamma * (k.gm1 * E) / r);
+    T B2 = bcx * bcx + bcy * bcy + bcz * bcz;
+    T ca = sqrtf(B2 / r);
+    T u2 = ucx * ucx + ucy * ucy + ucz * ucz;
+    T ub = ucx * bcx + ucy * bcy + ucz * bcz;
+    T w = cs + ca + sqrtf(fmaxf(uperp2(u2, ub, B2), T(0.f)));
+    T rate = fmaxf(fabsf(n.ld(qr)) / r, fabsf(n.ld(qE)) / E);
+    m[0] = max_bits(w);
+    m[1] = max_bits(rate);
+    if (k.visc) m[2] = max_bits(k.rm ? n.ld(nu) : T(k.nu_const));
   }
-  sm[0][tid] = w;
-  sm[1][tid] = rate;
-  sm[2][tid] = nuv;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m[c] = max(m[c], __shfl_xor_sync(0xffffffffu, m[c], o));
+  if ((tid & 31) == 0)
+    for (int c = 0; c < 3; ++c) sm[c][tid >> 5] = m[c];
   __syncthreads();
-  for (int s = BX * BY * BZ / 2; s > 0; s >>= 1) {
-    if (tid < s)
-      for (int c = 0; c < 3; ++c) sm[c][tid] = fmaxf(sm[c][tid], sm[c][tid + s]);
-    __syncthreads();
-  }
-  if (tid == 0) {
-    int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    for (int c = 0; c < 3; ++c) part[3 * b + c] = (double)sm[c][0];
+  if (tid < 3) {
+    unsigned v = 0u;
+    for (int wi = 0; wi < BX * BY * BZ / 32; ++wi) v = max(v, sm[tid][wi]);
+    atomicMax(cmax + tid, v);
   }
 }
 
-// Final FP64 reduction: dt = min(Cdt dl/wmax, Cdtr/ratemax, Cdtd dl/(numax f)).
-__global__ void k_courant_final(const double* part, int nb, double* dt_out, double cdt,
-                                double cdtr, double cdtd, double dlmin, double dfac,
-                                int nu_is_velocity) {
-  __shared__ double sm[3][256];
-  int tid = threadIdx.x;
-  double m[3] = {0, 0, 0};
-  for (int b = tid; b < nb; b += blockDim.x)
-    for (int c = 0; c < 3; ++c) m[c] = fmax(m[c], part[3 * b + c]);
-  for (int c = 0; c < 3; ++c) sm[c][tid] = m[c];
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (tid < s)
-      for (int c = 0; c < 3; ++c) sm[c][tid] = fmax(sm[c][tid], sm[c][tid + s]);
-    __syncthreads();
-  }
-  if (tid == 0) {
-    double wmax = sm[0][0], rmax = sm[1][0], nmax = sm[2][0];
-    double tw = wmax > 0 ? cdt * dlmin / wmax : HUGE_VAL;
-    double tr = rmax > 0 ? cdtr / rmax : HUGE_VAL;
-    double nv = nu_is_velocity ? nmax : nmax / dlmin;
-    double td = nv > 0 ? cdtd * dlmin / (nv * dfac) : HUGE_VAL;
-    double dt = fmin(tw, fmin(tr, td));
-    dt_out[0] = dt;
-    dt_out[1] = tw;
-    dt_out[2] = tr;
-    dt_out[3] = td;
-  }
+// dt = min(Cdt dl/wmax, Cdtr/ratemax, Cdtd dl/(numax f)) in FP64 from the
+// three maxima, which it then clears for the next reduction.
+__global__ void k_courant_final(unsigned* cmax, double* dt_out, double cdt, double cdtr,
+                                double cdtd, double dlmin, double dfac, int nu_is_velocity) {
+  if (threadIdx.x != 0) return;
+  const double wmax = (double)__uint_as_float(cmax[0]);
+  const double rmax = (double)__uint_as_float(cmax[1]);
+  const double nmax = (double)__uint_as_float(cmax[2]);
+  cmax[0] = cmax[1] = cmax[2] = 0u;
+  double tw = wmax > 0 ? cdt * dlmin / wmax : HUGE_VAL;
+  double tr = rmax > 0 ? cdtr / rmax : HUGE_VAL;
+  double nv = nu_is_velocity ? nmax : nmax / dlmin;
+  double td = nv > 0 ? cdtd * dlmin / (nv * dfac) : HUGE_VAL;
+  double dt = fmin(tw, fmin(tr, td));
+  dt_out[0] = dt;
+  dt_out[1] = tw;
+  dt_out[2] = tr;
+  dt_out[3] = td;
 }
 
 // ---------------------------------------------------------- diagnostics ----

@@ -83,10 +83,12 @@ def err_scale(got, ora):
 
 
 def ragged_state(shape, seed=7):
-    ux, uy, uz = inputs.solenoidal_velocity(shape, seed, 0.3)
-    a = inputs.solenoidal_velocity(shape, seed + 1, 1.0)
-    b = inputs.solenoidal_velocity(shape, seed + 2, 1.0)
-    c = inputs.solenoidal_velocity(shape, seed + 3, 1.0)
+    # The spectral band must fit the x half-spectrum (|m_x| <= nx / 2).
+    km = dict(kmax=min(4.0, float(shape[0] // 2)))
+    ux, uy, uz = inputs.solenoidal_velocity(shape, seed, 0.3, **km)
+    a = inputs.solenoidal_velocity(shape, seed + 1, 1.0, **km)
+    b = inputs.solenoidal_velocity(shape, seed + 2, 1.0, **km)
+    c = inputs.solenoidal_velocity(shape, seed + 3, 1.0, **km)
     f = [1 + 0.05 * a[0], ux + 0.02 * c[0], uy, uz, 0.9 + 0.05 * a[1],
          0.1 * b[0], 0.1 * b[1] + 0.05, 0.1 * b[2] + 0.3]
     nx, ny, nz = shape
@@ -169,6 +171,76 @@ def test_rhs_fp64_unfused_matches_oracle_to_roundoff(S, name):
     Fo = [t.numpy() for t in oracle.rhs([torch.tensor(a) for a in w.fields], g, oracle_params(kw))]
     e = err_scale([t.cpu().numpy() for t in F], Fo)
     assert max(e) < 1e-10, (name, e)
+    sim.close()
+
+
+# Four consecutive x-cells per thread (16-byte loads and stores) run wherever
+# nx % 4 == 0 and every array is 16-byte aligned.  These shapes put that
+# mapping on the physics of the ragged cases: nx = 4 (the chunks left and
+# right of a thread's cells wrap onto the same one), nx = 8, a partial block in
+# x (28, 36 cells of the 128 a block covers) and two blocks with a tail (140).
+VEC_CASES = {
+    "vec36_visc_cooling_lowcut": (
+        (36, 18, 13), dict(VISC_KW, t_cool=0.05, e_cool=0.7, rho_cool=1.02, cool_cut=1)),
+    "vec28_smagorinsky_rm_quench": ((28, 21, 10), dict(VISC_KW, csmag=0.15)),
+    "vec140_visc_quench": ((140, 9, 7), VISC_KW),
+    "vec4_const_nu_c1_gravity_nolog": (
+        (4, 20, 9),
+        dict(nu_const=0.002, c1=-1.0 / 3.0, nuE=0.5, nuB=0.7, g=(0.0, 0.0, -1.0), log_interp=0)),
+    "vec8_ideal_cooling_highcut": (
+        (8, 16, 12), dict(t_cool=0.1, e_cool=0.8, rho_cool=0.98, cool_cut=2)),
+}
+
+
+@pytest.mark.parametrize("name", list(VEC_CASES))
+def test_four_cell_threads_match_one_cell_threads_and_oracle(S, name):
+    shape, kw = VEC_CASES[name]
+    w = ragged_state(shape)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    Fo = [t.numpy() for t in oracle.rhs([torch.tensor(a) for a in w.fields], g, oracle_params(kw))]
+    got = {}
+    for sc in (0, 1):
+        sim, refs, dev = make(S, w, dict(kw, scalar_cells=sc))
+        got[sc] = [t.double().cpu().numpy() for t in sim.rhs(dev)]
+        sim.close()
+    e4, e1 = err_scale(got[0], Fo), err_scale(got[1], Fo)
+    assert max(e4) < 2e-4 and max(e1) < 2e-4, (name, e4, e1)
+    # Both mappings do the same FP32 operations per cell; only the compiler's
+    # multiply-add contraction may differ.
+    d = err_scale(got[0], got[1])
+    assert max(d) < 2e-5, (name, d)
+
+
+@pytest.mark.parametrize("name", ["vec28_smagorinsky_rm_quench", "vec36_visc_cooling_lowcut"])
+def test_four_cell_threads_steps(S, name):
+    shape, kw = VEC_CASES[name]
+    w = ragged_state(shape)
+    sim, refs, dev = make(S, w, kw)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle_params(kw)
+    fo = [torch.tensor(a) for a in w.fields]
+    for _ in range(3):
+        dt = sim.step(dev, None, want_dt=True)
+        fo, dto = oracle.step(fo, g, po, dt=dt)
+        assert abs(dt / dto - 1) < 1e-4, (dt, dto)
+    e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
+    assert max(e) < 3e-5, (name, e)
+    sim.close()
+
+
+def test_unaligned_state_views(S):
+    """State arrays that start 4 bytes into their storage take the one-cell
+    mapping and give the same derivatives."""
+    w = ragged_state((36, 18, 13))
+    sim, refs, dev = make(S, w, VISC_KW)
+    F = [t.double().cpu().numpy() for t in sim.rhs(dev)]
+    bufs = [torch.empty(t.numel() + 1, dtype=torch.float32, device="cuda") for t in dev]
+    dv = [b[1:].view(t.shape) for b, t in zip(bufs, dev)]
+    for a, t in zip(dv, dev):
+        a.copy_(t)
+    assert all(a.data_ptr() % 16 != 0 for a in dv)
+    F2 = [t.double().cpu().numpy() for t in sim.rhs(dv)]
+    assert max(err_scale(F2, F)) < 2e-5
     sim.close()
 
 
