@@ -42,17 +42,21 @@ REF_N = 96                      # per-step sample grid of the reference (oracle)
 
 # Distinct FP32 arrays each fused kernel reads + writes per launch (its
 # algorithmic HBM traffic: every array touched once), for the viscous,
-# quenched workload.  k_div: stage 1 (Courant) reads 25 and writes 8;
-# stages 2 and 3 read 38 (fluxes, state, previous dfdt) and write 16;
-# k_update is the stage-1 update of all 8 fields (f, dfdt in; f out).
+# quenched workload.  k_div: per stage, over its three launches (momentum;
+# mass and energy; induction; their arrays are disjoint): stage 1 (Courant)
+# reads 25 and writes 8; stages 2 and 3 read 38 (fluxes, state, previous
+# dfdt) and write 16; k_update is the stage-1 update of all 8 fields (f, dfdt
+# in; f out).
 KERNEL_ARRAYS = {"k_lr": 2, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
                  "k_nu_faces": 4, "k_tau": 26, "k_edge": 28, "k_flux": 50,
                  "k_div": (33 + 54 + 54) / 3.0, "k_update": 24}
-# DRAM bytes (read + write) per cell per launch from the ncu captures
-# summarised in profiles/k_flux_turbulence192.md and
-# profiles/k_edge_turbulence192.md (192^3 captures; traffic grows with the
-# cells).  Only kernels unchanged since their capture.
-NCU_TRAFFIC_PER_CELL = {"k_flux": 1399.2e6 / 192 ** 3, "k_edge": 1123.8e6 / 192 ** 3}
+# DRAM bytes (read + write) per cell per launch from one ncu capture of each
+# kernel on the same workload at 192^3 (traffic grows with the cells).  Only
+# kernels unchanged since their capture.
+NCU_TRAFFIC_PER_CELL = {"k_flux": 1667.3e6 / 192 ** 3, "k_edge": 761.9e6 / 192 ** 3,
+                        "k_tau": 707.4e6 / 192 ** 3}
+# Launches that together form one unit of KERNEL_ARRAYS.
+LAUNCHES_PER_UNIT = {"k_div": 3}
 
 
 def peaks():
@@ -271,7 +275,7 @@ def main():
     top = max(ktimes.items(), key=lambda kv: kv[1][0])
     kname, (kms, kcnt) = top
     kbytes = KERNEL_ARRAYS.get(kname, 0) * 4.0 * n ** 3
-    kavg = kms / kcnt
+    kavg = kms / kcnt * LAUNCHES_PER_UNIT.get(kname, 1)
     achieved = kbytes / (kavg * 1e-3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,

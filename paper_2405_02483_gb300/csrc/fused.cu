@@ -291,10 +291,17 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
   const bool v4 = F.cells4 && aligned16(f, 8) && aligned16(q, 8) && aligned16(oo, 8);
   const dim3 gg = v4 ? grid_cells<Nb4>(F.geo) : grid_cells<Nb>(F.geo), bb(BX, BY, BZ);
-  auto kern = v4 ? k_div<Nb4> : k_div<Nb>;
-  TIMED(K_DIV, (kern<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], oo[0],
-                                        oo[1], oo[2], oo[3], oo[4], oo[5], oo[6], oo[7], alpha,
-                                        beta, F.dt_dev, mode, F.kp, F.geo)));
+  // Momentum; mass and energy; induction (disjoint inputs, one kernel each).
+  const int nk = 3;
+  void (*kern[3])(DivIn, float*, float*, float*, float*, float*, float*, float*, float*, float*,
+                  float*, float*, float*, float*, float*, float*, float*, float, float,
+                  const double*, int, KPar, Geo) = {
+      v4 ? k_div<Nb4, 0x0E> : k_div<Nb, 0x0E>, v4 ? k_div<Nb4, 0x11> : k_div<Nb, 0x11>,
+      v4 ? k_div<Nb4, 0xE0> : k_div<Nb, 0xE0>};
+  for (int i = 0; i < nk; ++i)
+    TIMED(K_DIV, (kern[i]<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
+                                            oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6],
+                                            oo[7], alpha, beta, F.dt_dev, mode, F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }

@@ -25,6 +25,7 @@
 #endif
 #define STG_LB(N, minb) __launch_bounds__(BX * BY * BZ, (N::W == 4 ? STG_MINB4 : (minb)))
 #define STG_LB_HI(N, minb) __launch_bounds__(BX * BY * BZ, (N::W == 4 ? STG_MINB4_HI : (minb)))
+#define STG_LB_4(N, minb) __launch_bounds__(BX * BY * BZ, (N::W == 4 ? 4 : (minb)))
 
 namespace stg {
 
@@ -679,57 +680,66 @@ struct DivIn {
   const float* f[8];   // stage input (deviations), for the update
 };
 
-// F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q.
-// mode 0: write F to q only; 1: also update with dt from *dtp.
-template <class N>
-__global__ void STG_LB(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
-                                             float* q4, float* q5, float* q6, float* q7,
-                                             float* o0, float* o1, float* o2, float* o3,
-                                             float* o4, float* o5, float* o6, float* o7,
-                                             float alpha, float beta, const double* dtp,
-                                             int mode, KPar k, Geo g) {
+// F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q, for the
+// fields in the bit mask M (bit c: field c), each stored as soon as it is
+// formed.  mode 0: write F to q only; 1: also update with dt from *dtp.
+// Launched as three kernels (momentum; mass and energy; induction), whose
+// inputs are disjoint, at 4 blocks per SM: fewer live registers per launch.
+template <class N, int M>
+__global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
+                                          float* q4, float* q5, float* q6, float* q7,
+                                          float* o0, float* o1, float* o2, float* o3,
+                                          float* o4, float* o5, float* o6, float* o7,
+                                          float alpha, float beta, const double* dtp,
+                                          int mode, KPar k, Geo g) {
   N n;
   if (!n.init(g)) return;
   using T = typename N::T;
   const float* ih = k.ih;
-  T F[8];
-  F[0] = -((s_du(AX(in.px, 0), ih[0]) + s_du(AX(in.py, 1), ih[1])) + s_du(AX(in.pz, 2), ih[2]));
-  T t;
-  t = -s_dd(AX(in.mxx, 0), ih[0]);
-  t -= s_du(AX(in.mxy, 1), ih[1]);
-  t -= s_du(AX(in.mxz, 2), ih[2]);
-  t += s_up(AX(in.lx1, 2));
-  t -= s_up(AX(in.lx2, 1));
-  if (k.g[0] != 0.f) t += dens(s_dn(AX(in.ls, 0)), k) * k.g[0];
-  F[1] = t;
-  t = -s_du(AX(in.myx, 0), ih[0]);
-  t -= s_dd(AX(in.myy, 1), ih[1]);
-  t -= s_du(AX(in.myz, 2), ih[2]);
-  t += s_up(AX(in.ly1, 0));
-  t -= s_up(AX(in.ly2, 2));
-  if (k.g[1] != 0.f) t += dens(s_dn(AX(in.ls, 1)), k) * k.g[1];
-  F[2] = t;
-  t = -s_du(AX(in.mzx, 0), ih[0]);
-  t -= s_du(AX(in.mzy, 1), ih[1]);
-  t -= s_dd(AX(in.mzz, 2), ih[2]);
-  t += s_up(AX(in.lz1, 1));
-  t -= s_up(AX(in.lz2, 0));
-  if (k.g[2] != 0.f) t += dens(s_dn(AX(in.ls, 2)), k) * k.g[2];
-  F[3] = t;
-  F[4] = -((s_du(AX(in.gx, 0), ih[0]) + s_du(AX(in.gy, 1), ih[1])) + s_du(AX(in.gz, 2), ih[2])) +
-         n.ld(in.qt);
-  F[5] = -(s_du(AX(in.Ez, 1), ih[1]) - s_du(AX(in.Ey, 2), ih[2]));
-  F[6] = -(s_du(AX(in.Ex, 2), ih[2]) - s_du(AX(in.Ez, 0), ih[0]));
-  F[7] = -(s_du(AX(in.Ey, 0), ih[0]) - s_du(AX(in.Ex, 1), ih[1]));
   float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
   float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
-  float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F[c] : F[c];
+  const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
+  auto fin = [&](int c, const T& F) {
+    const T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F : F;
     n.st(qs[c], qq);
     if (mode) n.st(os[c], n.ld(in.f[c]) + bdt * qq);
+  };
+  if (M & 1)   // eq. (mass)
+    fin(0, -((s_du(AX(in.px, 0), ih[0]) + s_du(AX(in.py, 1), ih[1])) + s_du(AX(in.pz, 2), ih[2])));
+  if (M & 2) {   // eq. (mom), x
+    T t = -s_dd(AX(in.mxx, 0), ih[0]);
+    t -= s_du(AX(in.mxy, 1), ih[1]);
+    t -= s_du(AX(in.mxz, 2), ih[2]);
+    t += s_up(AX(in.lx1, 2));
+    t -= s_up(AX(in.lx2, 1));
+    if (k.g[0] != 0.f) t += dens(s_dn(AX(in.ls, 0)), k) * k.g[0];
+    fin(1, t);
   }
+  if (M & 4) {   // eq. (mom), y
+    T t = -s_du(AX(in.myx, 0), ih[0]);
+    t -= s_dd(AX(in.myy, 1), ih[1]);
+    t -= s_du(AX(in.myz, 2), ih[2]);
+    t += s_up(AX(in.ly1, 0));
+    t -= s_up(AX(in.ly2, 2));
+    if (k.g[1] != 0.f) t += dens(s_dn(AX(in.ls, 1)), k) * k.g[1];
+    fin(2, t);
+  }
+  if (M & 8) {   // eq. (mom), z
+    T t = -s_du(AX(in.mzx, 0), ih[0]);
+    t -= s_du(AX(in.mzy, 1), ih[1]);
+    t -= s_dd(AX(in.mzz, 2), ih[2]);
+    t += s_up(AX(in.lz1, 1));
+    t -= s_up(AX(in.lz2, 0));
+    if (k.g[2] != 0.f) t += dens(s_dn(AX(in.ls, 2)), k) * k.g[2];
+    fin(3, t);
+  }
+  if (M & 16)   // eq. (ien)
+    fin(4, -((s_du(AX(in.gx, 0), ih[0]) + s_du(AX(in.gy, 1), ih[1])) + s_du(AX(in.gz, 2), ih[2])) +
+               n.ld(in.qt));
+  // eq. (indu): dB/dt = -curl E
+  if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), ih[1]) - s_du(AX(in.Ey, 2), ih[2])));
+  if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), ih[2]) - s_du(AX(in.Ez, 0), ih[0])));
+  if (M & 128) fin(7, -(s_du(AX(in.Ey, 0), ih[0]) - s_du(AX(in.Ex, 1), ih[1])));
 }
 
 __global__ void k_set_dt(double* dtp, double dt) { dtp[0] = dt; }
