@@ -31,7 +31,14 @@ path by specification only, never by code):
   R16 Newtonian cooling enters the energy-per-volume equation as
       -rho (e - e_cool)/t_cool (e relaxes to e_cool on t_cool);
   R17 Smagorinsky: dl_min * Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2
-      joins the Richtmyer-Morton nu before the max and the mean.
+      joins the Richtmyer-Morton nu before the max and the mean;
+  R18 the second-order switch of the viscous stress (Sect. "Equations",
+      do_2nddiv): the flag of axis a at index (i, j, k) is set where
+      |D2_a ln rho| or |D2_a ln e| of the cell with that index exceeds
+      d2lnr_lim (D2_a f = f(+1) - 2 f + f(-1) along a); every derivative along
+      a in the strain of eq. (itv), in its c1 div u term and in the viscous
+      heating built from that strain is then the two-point difference
+      (f(i+1) - f(i))/h or (f(i) - f(i-1))/h instead of eq. (deriv).
 """
 from __future__ import annotations
 
@@ -112,6 +119,8 @@ class Params:
     rho_cool: float = 1.0
     cool_cut: int = 0        # 0 none, 1 low-density cutoff, 2 high-density cutoff
     csmag: float = 0.0       # Smagorinsky constant, eq. (nusmag) (0: off)
+    do_2nddiv: bool = False  # second-order stress derivatives where ln rho, ln e kink (R18)
+    d2lnr_lim: float = 0.3
 
     def visc_on(self):
         return (self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
@@ -149,6 +158,30 @@ def dddn(f, ax, h):
     """6th-order derivative at i-1/2 (downward variant of eq. (deriv))."""
     return (DA * (f - _s(f, ax, -1)) + DB * (_s(f, ax, 1) - _s(f, ax, -2))
             + DC * (_s(f, ax, 2) - _s(f, ax, -3))) / h
+
+
+def ddup2(f, ax, h):
+    """Second-order derivative at i+1/2: the two-point difference (R18)."""
+    return (_s(f, ax, 1) - f) / h
+
+
+def dddn2(f, ax, h):
+    """Second-order derivative at i-1/2: the two-point difference (R18)."""
+    return (f - _s(f, ax, -1)) / h
+
+
+def d2_flags(r, E, lim):
+    """Second-order switch of the viscous stress (Sect. "Equations",
+    do_2nddiv with d2lnr_lim), reading R18: per axis, True where the second
+    difference of ln rho or of ln e (e = E/rho) along that axis exceeds lim in
+    magnitude, at the cell with the same index."""
+    lr, le = torch.log(r), torch.log(E / r)
+    flags = {}
+    for ax in "xyz":
+        d2r = _s(lr, ax, 1) - 2.0 * lr + _s(lr, ax, -1)
+        d2e = _s(le, ax, 1) - 2.0 * le + _s(le, ax, -1)
+        flags[ax] = (torch.abs(d2r) > lim) | (torch.abs(d2e) > lim)
+    return flags
 
 
 def max3(f, ax):
@@ -264,14 +297,32 @@ def rhs_parts(f, g: Grid, p: Params):
             rzx = torch.exp(dn(dn(lr, "z"), "x"))
         else:
             rxy, ryz, rzx = dn(dn(r, "x"), "y"), dn(dn(r, "y"), "z"), dn(dn(r, "z"), "x")
-        # Strain, eq. (itv).
-        Sxx, Syy, Szz = ddup(ux, "x", hx), ddup(uy, "y", hy), ddup(uz, "z", hz)
-        Sxy = 0.5 * (dddn(ux, "y", hy) + dddn(uy, "x", hx))
-        Syz = 0.5 * (dddn(uy, "z", hz) + dddn(uz, "y", hy))
-        Szx = 0.5 * (dddn(uz, "x", hx) + dddn(ux, "z", hz))
-        txx = r * nxx * (Sxx + p.c1 * divu)
-        tyy = r * nyy * (Syy + p.c1 * divu)
-        tzz = r * nzz * (Szz + p.c1 * divu)
+        # Strain, eq. (itv); with the second-order switch (R18) each derivative
+        # along an axis takes the two-point difference where that axis is flagged.
+        if p.do_2nddiv:
+            fl = d2_flags(r, E, p.d2lnr_lim)
+            out["d2flags"] = fl
+            h = {"x": hx, "y": hy, "z": hz}
+
+            def dup(f, ax):
+                return torch.where(fl[ax], ddup2(f, ax, h[ax]), ddup(f, ax, h[ax]))
+
+            def ddn(f, ax):
+                return torch.where(fl[ax], dddn2(f, ax, h[ax]), dddn(f, ax, h[ax]))
+        else:
+            def dup(f, ax):
+                return ddup(f, ax, {"x": hx, "y": hy, "z": hz}[ax])
+
+            def ddn(f, ax):
+                return dddn(f, ax, {"x": hx, "y": hy, "z": hz}[ax])
+        Sxx, Syy, Szz = dup(ux, "x"), dup(uy, "y"), dup(uz, "z")
+        Sxy = 0.5 * (ddn(ux, "y") + ddn(uy, "x"))
+        Syz = 0.5 * (ddn(uy, "z") + ddn(uz, "y"))
+        Szx = 0.5 * (ddn(uz, "x") + ddn(ux, "z"))
+        divs = Sxx + Syy + Szz if p.do_2nddiv else divu
+        txx = r * nxx * (Sxx + p.c1 * divs)
+        tyy = r * nyy * (Syy + p.c1 * divs)
+        tzz = r * nzz * (Szz + p.c1 * divs)
         txy = rxy * nxy * Sxy
         tyz = ryz * nyz * Syz
         tzx = rzx * nzx * Szx

@@ -605,3 +605,132 @@ def test_smagorinsky_cooling_symmetry_and_conservation():
     vals = (1.3, 0.2, -0.1, 0.3, 1.3 * 0.8, 0.1, 0.2, 0.5)
     fu = [torch.full((5, 6, 8), v, dtype=DT) for v in vals]
     assert all(float(d.abs().max()) == 0.0 for d in S.rhs(fu, g, SMAG))
+
+
+# ------------- second-order switch of the viscous stress (R18, do_2nddiv) ------
+
+def _two_point_symbol(th):
+    """Fourier symbol of the two-point staggered difference times h: 2 sin(th/2)."""
+    return 2 * math.sin(th / 2)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("c1", [0.0, -1.0 / 3.0])
+def test_second_order_switch_longitudinal_rate(d, c1):
+    # Every axis flagged (a negative limit): S_dd and the c1 div u term are the
+    # two-point difference, symbol 2 sin(th/2)/h, and the stress divergence
+    # keeps eq. (deriv), symbol D(th)/h; u_d = a sin(k x) then changes at
+    # -nu (1 + c1) (2 sin(th/2)/h) (D(th)/h) u_d.  A limit no |D2 ln| reaches
+    # gives back the sixth-order rate.
+    n, m, amp, nu = 24, 3, 1e-8, 0.01
+    ax = "xyz"[d]
+    h = 1.0 / n
+    g, shape, _, xf = _line_state(n, ax, h)
+    k = 2 * math.pi * m
+    th = k * h
+    wave = amp * torch.sin(k * xf)
+    one = torch.ones(shape, dtype=DT)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = wave.clone()
+    F2 = S.rhs(f, g, Params(nu_const=nu, c1=c1, do_2nddiv=True, d2lnr_lim=-1.0))
+    lam2 = nu * (1 + c1) * (_two_point_symbol(th) / h) * (D_sym(th) / h)
+    assert torch.allclose(F2[1 + d], -lam2 * wave, rtol=0, atol=1e-5 * lam2 * amp)
+    F6 = S.rhs(f, g, Params(nu_const=nu, c1=c1, do_2nddiv=True, d2lnr_lim=1e30))
+    lam6 = nu * (1 + c1) * (D_sym(th) / h) ** 2
+    assert torch.allclose(F6[1 + d], -lam6 * wave, rtol=0, atol=1e-5 * lam6 * amp)
+
+
+@pytest.mark.parametrize("d,a", [(0, 1), (1, 2), (2, 0), (1, 0)])
+def test_second_order_switch_shear_heating(d, a):
+    # u_d = amp sin(k x_a), everything flagged: S_da = (1/2) two-point
+    # difference along a, so the viscous heating 2 up up(tau_da S_da) with
+    # tau_da = nu S_da (rho = 1, constant nu) is nu (amp 2 sin(th/2)/h)^2 / 2
+    # times the centred (1 + I(2 th) cos 2 k x_a) / 2.
+    n, m, amp, nu = 24, 2, 0.3, 0.02
+    axd, axa = "xyz"[d], "xyz"[a]
+    h = 1.0 / n
+    g, shape, xc, xf = _line_state(n, axa, h)
+    k = 2 * math.pi * m
+    th = k * h
+    one = torch.ones(shape, dtype=DT)
+    f = [one, 0 * one, 0 * one, 0 * one, 0.9 * one, 0 * one, 0 * one, 0 * one]
+    f[1 + d] = amp * torch.sin(k * xc)       # u_d sits at the centre coordinate along a != d
+    Qv = S.rhs_parts(f, g, Params(nu_const=nu, do_2nddiv=True, d2lnr_lim=-1.0))["Qv"]
+    s = amp * _two_point_symbol(th) / h / 2
+    expect = 2 * nu * s * s * 0.5 * (1 + I_sym(2 * th) * torch.cos(2 * k * xc))
+    assert torch.allclose(Qv, expect, rtol=1e-12, atol=1e-14)
+
+
+def _kink_state(n=16, jump=0.5, where="rho"):
+    """ln rho (or ln e) steps by ``jump`` between x-index 7 and 8 of a periodic
+    16 x 5 x 3 box (and back between 15 and 0); everything else uniform."""
+    g = Grid(n, 5, 3, 1.0 / n, 0.2, 0.3)
+    shape = (3, 5, n)
+    step = torch.zeros(n, dtype=DT)
+    step[n // 2:] = jump
+    step = step.reshape(1, 1, n).expand(shape)
+    one = torch.ones(shape, dtype=DT)
+    if where == "rho":
+        r, e = torch.exp(step), 0.9 * one
+    else:
+        r, e = 1.3 * one, 0.9 * torch.exp(step)
+    return g, shape, [r, 0 * one, 0 * one, 0 * one, r * e, 0 * one, 0 * one, 0 * one]
+
+
+@pytest.mark.parametrize("where", ["rho", "e"])
+def test_second_order_flags_at_a_kink(where):
+    # |D2 ln| = 0.5 on the two cells either side of each step (x = 7, 8 and, by
+    # periodicity, 15, 0) and 0 elsewhere, for a kink in ln rho or in ln e.
+    g, shape, f = _kink_state(where=where)
+    fl = S.d2_flags(f[0], f[4], 0.3)
+    expect = torch.zeros(shape, dtype=torch.bool)
+    expect[..., [0, 7, 8, 15]] = True
+    assert torch.equal(fl["x"], expect)
+    assert not fl["y"].any() and not fl["z"].any()
+    assert not S.d2_flags(f[0], f[4], 0.6)["x"].any()
+
+
+def test_second_order_switch_selects_per_axis():
+    # With the kink along x only, the x-derivative of u_y in S_xy takes the
+    # two-point form exactly on the x-flagged cells, and the y-derivative of u_x
+    # never does: tau_xy and tau_xx follow the all-flagged result there and the
+    # unflagged one elsewhere, value for value.
+    g, shape, f = _kink_state()
+    k = 2 * math.pi * 2
+    xc = ((torch.arange(16, dtype=DT) + 0.5) / 16).reshape(1, 1, 16).expand(shape)
+    yc = ((torch.arange(5, dtype=DT) + 0.5) * 0.2).reshape(1, 5, 1).expand(shape)
+    base = dict(nu_const=0.01, c1=0.0)
+    flagged = S.d2_flags(f[0], f[4], 0.3)["x"]
+
+    def tau(fs, **kw):
+        P = S.rhs_parts(fs, g, Params(**base, **kw))
+        return P["txy"], P["txx"]
+
+    # u_y varying along x: flag x governs dddn_x(u_y).
+    fy = list(f)
+    fy[2] = f[0] * 0.2 * torch.sin(k * xc)
+    t_sw, _ = tau(fy, do_2nddiv=True, d2lnr_lim=0.3)
+    t_all, _ = tau(fy, do_2nddiv=True, d2lnr_lim=-1.0)
+    t_off, _ = tau(fy)
+    assert torch.equal(t_sw, torch.where(flagged, t_all, t_off))
+    assert not torch.equal(t_all, t_off)
+    # u_x varying along y: the y-derivative is never flagged.
+    fx = list(f)
+    fx[1] = 0.2 * torch.sin(2 * math.pi * yc)
+    t_sw, _ = tau(fx, do_2nddiv=True, d2lnr_lim=0.3)
+    t_off, _ = tau(fx)
+    assert torch.equal(t_sw, t_off)
+    # u_x varying along x: S_xx switches on the x-flagged cells.
+    fxx = list(f)
+    fxx[1] = 0.2 * torch.sin(k * xc)
+    _, s_sw = tau(fxx, do_2nddiv=True, d2lnr_lim=0.3)
+    _, s_all = tau(fxx, do_2nddiv=True, d2lnr_lim=-1.0)
+    _, s_off = tau(fxx)
+    assert torch.equal(s_sw, torch.where(flagged, s_all, s_off))
+
+
+def test_second_order_switch_conservation():
+    P2 = Params(nu1=0.03, nu2=0.5, nu3=0.03, do_quench=True, c1=-1.0 / 3.0,
+                do_2nddiv=True, d2lnr_lim=0.02)
+    test_conservation_and_divb(P2)
+    test_cyclic_axis_permutation(P2)
