@@ -86,11 +86,20 @@ typedef struct {
    * is 16-byte aligned, one cell per thread otherwise; 1: one cell per thread
    * everywhere.  Other values: STAGGER_EINVAL. */
   int scalar_cells;
+  /* Second-order switch of the viscous stress (Sect. Equations, do_2nddiv):
+   * where |D2_a ln rho| or |D2_a ln e| of a cell exceeds d2lnr_lim (D2_a f =
+   * f(+1) - 2 f + f(-1) along axis a), every derivative along a in the strain
+   * of eq. (itv), in its c1 div u term and in the viscous heating built from it
+   * is the two-point difference instead of eq. (deriv).  0: off (default);
+   * d2lnr_lim defaults to 0.3 (a negative limit flags every cell). */
+  int do_2nddiv;
+  double d2lnr_lim;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
  * nuE = nuB = 1, qmax 8, qlim 2, log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
- * no gravity, zero references, no cooling (rho_cool 1).  Returns STAGGER_EINVAL if p is NULL. */
+ * no gravity, zero references, no cooling (rho_cool 1), no second-order switch
+ * (d2lnr_lim 0.3).  Returns STAGGER_EINVAL if p is NULL. */
 int stagger_params_default(stagger_params* p);
 
 /* Create a context for one grid and parameter set on the current CUDA device.

@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("g", ctypes.c_double * 3), ("ref", ctypes.c_double * 8),
                 ("t_cool", ctypes.c_double), ("e_cool", ctypes.c_double),
                 ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int),
-                ("csmag", ctypes.c_double), ("scalar_cells", ctypes.c_int)]
+                ("csmag", ctypes.c_double), ("scalar_cells", ctypes.c_int),
+                ("do_2nddiv", ctypes.c_int), ("d2lnr_lim", ctypes.c_double)]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

@@ -38,6 +38,7 @@ int stagger_params_default(stagger_params* p) {
   p->Cdtr = 0.1;
   p->Cdtd = 0.7;
   p->rho_cool = 1.0;
+  p->d2lnr_lim = 0.3;
   return STAGGER_OK;
 }
 
@@ -70,6 +71,7 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (!(p->t_cool >= 0) || !isfinite(p->e_cool)) return STAGGER_EINVAL;
   if (p->cool_cut < 0 || p->cool_cut > 2 || (p->cool_cut && !(p->rho_cool > 0))) return STAGGER_EINVAL;
   if (p->scalar_cells < 0 || p->scalar_cells > 1) return STAGGER_EINVAL;
+  if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
   return STAGGER_OK;

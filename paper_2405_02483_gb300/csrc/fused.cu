@@ -23,7 +23,8 @@ namespace stg {
 
 const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
-                                     "k_div", "k_update", "k_courant", "k_diag", "k_misc"};
+                                     "k_div", "k_update", "k_courant", "k_diag", "k_misc",
+                                     "k_d2flag"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -124,6 +125,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.gm1 = (float)(p.gamma - 1.0);
   k.visc = (p.nu_const > 0 || p.nu1 > 0 || p.nu2 > 0 || p.nu3 > 0 || p.csmag > 0) ? 1 : 0;
   k.csmag_dl = (float)(p.csmag * dlmin);
+  k.d2div = p.do_2nddiv && k.visc;
+  k.d2lim = (float)p.d2lnr_lim;
   k.rm = k.visc && !(p.nu_const > 0);
   k.nu1 = (float)p.nu1;
   k.nu2dl = (float)(p.nu2 * dlmin);
@@ -155,6 +158,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.dt_dev = nullptr;
   F.red = nullptr;
   F.cmax = nullptr;
+  F.d2flag = nullptr;
   // Which intermediate fields this parameter set needs.
   std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
                            F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
@@ -179,6 +183,11 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   }
   dim3 gg = grid3(F.geo);
   F.red_blocks = (int)(gg.x * gg.y * gg.z);
+  if (k.d2div && cudaMalloc(&F.d2flag, (size_t)F.geo.n) != cudaSuccess) {
+    F.d2flag = nullptr;
+    fused_release(F);
+    return STAGGER_EOOM;
+  }
   if (cudaMalloc(&F.cmax, sizeof(unsigned) * 4) != cudaSuccess ||
       cudaMemset(F.cmax, 0, sizeof(unsigned) * 4) != cudaSuccess) {
     fused_release(F);
@@ -208,6 +217,8 @@ void fused_release(Fused& F) {
   if (F.red) cudaFree(F.red);
   if (F.cmax) cudaFree(F.cmax);
   F.cmax = nullptr;
+  if (F.d2flag) cudaFree(F.d2flag);
+  F.d2flag = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -240,18 +251,22 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
     TIMED(K_NU_SMOOTH, (k_nu_smooth<N><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
     TIMED(K_NU_FACES, (k_nu_faces<N><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
-  TIMED(K_TAU, (k_tau<N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
-                                        d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
-                                        f[6], f[7],
-                          d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ], d[F_TZX], d[F_RX],
-                          d[F_RY], d[F_RZ], d[F_JX], d[F_JY], d[F_JZ], k, g)));
+  if (k.d2div)
+    TIMED(K_D2FLAG, (k_d2flag<N><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
+  auto ktau = k.d2div ? k_tau<N, true> : k_tau<N, false>;
+  TIMED(K_TAU, (ktau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
+                                       d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
+                                       f[6], f[7], d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY],
+                                       d[F_TYZ], d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
+                                       d[F_JY], d[F_JZ], F.d2flag, k, g)));
+  auto kedge = k.d2div ? k_edge<N, true> : k_edge<N, false>;
   if (k.visc)
-    TIMED(K_EDGE, (k_edge<N><<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
-                                            d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
-                                            d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
-                                            d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
-                                            d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC],
-                                            d[F_WX], d[F_WY], d[F_WZ], k, g)));
+    TIMED(K_EDGE, (kedge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
+                                           d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
+                                           d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
+                                           d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
+                                           d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC],
+                                           d[F_WX], d[F_WY], d[F_WZ], F.d2flag, k, g)));
   const bool qn = k.visc && k.do_quench;
   FluxIn fi = {f[1], f[2], f[3], f[0], f[4], f[5], f[6], f[7], ls, d[F_UX], d[F_UY], d[F_UZ],
                qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],

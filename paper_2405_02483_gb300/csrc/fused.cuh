@@ -24,6 +24,8 @@ struct KPar {
   float inv_tcool, e_cool, inv_rho_cool;   // Newtonian cooling (inv_tcool 0: off)
   int cool_cut;
   float csmag_dl;       // Smagorinsky constant times dl_min (0: off)
+  int d2div;            // second-order switch of the stress derivatives
+  float d2lim;          // its limit on |D2 ln rho|, |D2 ln e|
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -46,7 +48,7 @@ enum Fld {
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
-           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_COUNT };
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {
@@ -60,6 +62,7 @@ struct Fused {
   double* dt_dev;       // device step and the three limits
   double* red;          // reduction partials (diagnostics)
   unsigned* cmax;       // Courant maxima as float bits, cleared by each final pass
+  unsigned char* d2flag;  // second-order switch flags per cell (bit = axis), or null
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   long long launches;

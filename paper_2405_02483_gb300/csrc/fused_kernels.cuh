@@ -145,6 +145,19 @@ struct Nb {
   // W consecutive elements at p (element-wise kernels).
   static __device__ __forceinline__ float ldp(const float* __restrict__ p) { return __ldg(p); }
   static __device__ __forceinline__ void stp(float* p, float v) { *p = v; }
+  // Per-cell switch flags (one byte per cell, bit a for axis a).
+  __device__ __forceinline__ unsigned ldflag(const unsigned char* __restrict__ p) const {
+    return __ldg(p + c);
+  }
+  __device__ __forceinline__ void stflag(unsigned char* p, unsigned f) const {
+    p[c] = (unsigned char)f;
+  }
+  static __device__ __forceinline__ unsigned bits(float v, float lim, int a) {
+    return v > lim ? (1u << a) : 0u;
+  }
+  static __device__ __forceinline__ float sel(unsigned fl, int a, float x, float y) {
+    return ((fl >> a) & 1u) ? x : y;
+  }
 };
 
 __device__ __forceinline__ bool make_nb(Nb& n, const Geo& g) {
@@ -216,6 +229,21 @@ struct Nb4 {
   static __device__ __forceinline__ F4 ldp(const float* __restrict__ p) { return row(p, 0); }
   static __device__ __forceinline__ void stp(float* p, const F4& v) {
     *reinterpret_cast<float4*>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+  }
+  // Per-cell switch flags: the four cells' bytes as one word (byte l, cell i0+l).
+  __device__ __forceinline__ unsigned ldflag(const unsigned char* __restrict__ p) const {
+    return __ldg(reinterpret_cast<const unsigned*>(p + c));
+  }
+  __device__ __forceinline__ void stflag(unsigned char* p, unsigned f) const {
+    *reinterpret_cast<unsigned*>(p + c) = f;
+  }
+  static __device__ __forceinline__ unsigned bits(const F4& v, float lim, int a) {
+    return (v.v[0] > lim ? 1u << a : 0u) | (v.v[1] > lim ? 1u << (8 + a) : 0u) |
+           (v.v[2] > lim ? 1u << (16 + a) : 0u) | (v.v[3] > lim ? 1u << (24 + a) : 0u);
+  }
+  static __device__ __forceinline__ F4 sel(unsigned fl, int a, const F4& x, const F4& y) {
+    return F4(((fl >> a) & 1u) ? x.v[0] : y.v[0], ((fl >> (8 + a)) & 1u) ? x.v[1] : y.v[1],
+              ((fl >> (16 + a)) & 1u) ? x.v[2] : y.v[2], ((fl >> (24 + a)) & 1u) ? x.v[3] : y.v[3]);
   }
 };
 
@@ -410,9 +438,83 @@ __global__ void STG_LB(N, STG_MINB) k_nu_faces(
   n.st(lz, s_dn(AX(lnu, 2)));
 }
 
+// ------------------------------------------------ second-order switch -----
+// Bit a of a cell's flag is set where |D2_a ln rho| or |D2_a ln e| exceeds
+// d2lim (D2_a f = f(+1) - 2 f + f(-1) along axis a; Sect. Equations,
+// do_2nddiv).  The logarithms are those of the stored deviations relative to
+// their references, log1p(r'/r0) and log1p(E'/E0) (ln e = ln E - ln rho); the
+// constant offsets cancel in D2.
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_d2flag(const float* __restrict__ rd,
+                                             const float* __restrict__ Ed,
+                                             unsigned char* __restrict__ flag, KPar k, Geo g) {
+  N n;
+  if (!n.init(g)) return;
+  using T = typename N::T;
+  auto lnr = [&](const T& r) { return k.r0pos ? log1pf(r / k.r0) : logf(r); };
+  auto lnE = [&](const T& E) { return k.E0 > 0.f ? log1pf(E / k.E0) : logf(E); };
+  unsigned fl = 0u;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T lrm = lnr(n.lda(rd, a, -1)), lrc = lnr(n.lda(rd, a, 0)), lrp = lnr(n.lda(rd, a, 1));
+    const T lem = lnE(n.lda(Ed, a, -1)) - lrm, lec = lnE(n.lda(Ed, a, 0)) - lrc,
+            lep = lnE(n.lda(Ed, a, 1)) - lrp;
+    const T d2r = fabsf((lrp - 2.f * lrc) + lrm), d2e = fabsf((lep - 2.f * lec) + lem);
+    fl |= N::bits(fmaxf(d2r, d2e), k.d2lim, a);
+  }
+  n.stflag(flag, fl);
+}
+
+// Two-point staggered differences to i+1/2 and i-1/2.
+template <class V> __device__ __forceinline__ auto s_du2(V v, float ih) -> decltype(v(0)) {
+  return (v(1) - v(0)) * ih;
+}
+template <class V> __device__ __forceinline__ auto s_dd2(V v, float ih) -> decltype(v(0)) {
+  return (v(0) - v(-1)) * ih;
+}
+
+// Strain of eq. (itv) from the face velocities: S_xx, S_yy, S_zz at centres
+// (strain_diag) and S_xy, S_yz, S_zx on the Ez, Ex, Ey edges (strain_off).
+// With the second-order switch compiled in (D2), a derivative along an axis
+// whose bit is set in the cell's flags fl is the two-point difference.
+template <class T> struct Strain3 { T a, b, c; };
+template <bool D2, class N>
+__device__ __forceinline__ Strain3<typename N::T> strain_diag(
+    const N& n, const float* __restrict__ ux, const float* __restrict__ uy,
+    const float* __restrict__ uz, unsigned fl, const KPar& k) {
+  const float* ih = k.ih;
+  Strain3<typename N::T> S{s_du(AX(ux, 0), ih[0]), s_du(AX(uy, 1), ih[1]), s_du(AX(uz, 2), ih[2])};
+  if (D2) {
+    S.a = N::sel(fl, 0, s_du2(AX(ux, 0), ih[0]), S.a);
+    S.b = N::sel(fl, 1, s_du2(AX(uy, 1), ih[1]), S.b);
+    S.c = N::sel(fl, 2, s_du2(AX(uz, 2), ih[2]), S.c);
+  }
+  return S;
+}
+template <bool D2, class N>
+__device__ __forceinline__ Strain3<typename N::T> strain_off(
+    const N& n, const float* __restrict__ ux, const float* __restrict__ uy,
+    const float* __restrict__ uz, unsigned fl, const KPar& k) {
+  using T = typename N::T;
+  const float* ih = k.ih;
+  // (d_a1 f1 + d_a2 f2) / 2, one pair at a time.
+  auto pair = [&](const float* f1, int a1, const float* f2, int a2) {
+    T d1 = s_dd(AX(f1, a1), ih[a1]), d2 = s_dd(AX(f2, a2), ih[a2]);
+    if (D2) {
+      d1 = N::sel(fl, a1, s_dd2(AX(f1, a1), ih[a1]), d1);
+      d2 = N::sel(fl, a2, s_dd2(AX(f2, a2), ih[a2]), d2);
+    }
+    return 0.5f * (d1 + d2);
+  };
+  const T xy = pair(ux, 1, uy, 0);
+  const T yz = pair(uy, 2, uz, 1);
+  const T zx = pair(uz, 0, ux, 2);
+  return Strain3<T>{xy, yz, zx};
+}
+
 // -------------------------------------------------------------- stress -----
 // Strain, stress (eq. (itv)), J = curl B and eta J on edges, eq. (ohm).
-template <class N>
+template <class N, bool D2>
 __global__ void STG_LB_HI(N, STG_MINB) k_tau(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     const float* __restrict__ rd, const float* __restrict__ lfx, const float* __restrict__ lfy,
@@ -423,7 +525,7 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
     float* __restrict__ tzz, float* __restrict__ txy, float* __restrict__ tyz,
     float* __restrict__ tzx, float* __restrict__ Rx, float* __restrict__ Ry,
     float* __restrict__ Rz, float* __restrict__ Jx, float* __restrict__ Jy,
-    float* __restrict__ Jz, KPar k, Geo g) {
+    float* __restrict__ Jz, const unsigned char* __restrict__ flag, KPar k, Geo g) {
   N n;
   if (!n.init(g)) return;
   using T = typename N::T;
@@ -435,7 +537,9 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
   n.st(Jy, jy);
   n.st(Jz, jz);
   if (!k.visc) return;
-  T sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
+  const unsigned fl = D2 ? n.ldflag(flag) : 0u;
+  const Strain3<T> Sd = strain_diag<D2>(n, ux, uy, uz, fl, k);
+  const T sxx = Sd.a, syy = Sd.b, szz = Sd.c;
   T divu = (sxx + syy) + szz;
   T r = n.ld(rd) + k.r0;
   T nuc = k.rm ? n.ld(nu) : 0.f;
@@ -452,9 +556,8 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
   T nxy = k.rm ? k.spp[2] * expf(s_dn(AX(lnx, 1))) : k.nu_const;
   T ryz = dens(s_dn(AX(lfy, 2)), k), rzx = dens(s_dn(AX(lfz, 0)), k),
         rxy = dens(s_dn(AX(lfx, 1)), k);
-  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  const Strain3<T> So = strain_off<D2>(n, ux, uy, uz, fl, k);
+  const T sxy = So.a, syz = So.b, szx = So.c;
   n.st(txy, (rxy * nxy) * sxy);
   n.st(tyz, (ryz * nyz) * syz);
   n.st(tzx, (rzx * nzx) * szx);
@@ -495,7 +598,7 @@ __device__ __forceinline__ typename N::T quench1(const float* __restrict__ f, co
 // where k_flux adds -u x B) and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
 // Viscous runs only.
-template <class N>
+template <class N, bool D2>
 __global__ void STG_LB(N, STG_MINB_HI) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
@@ -506,7 +609,7 @@ __global__ void STG_LB(N, STG_MINB_HI) k_edge(
     float* __restrict__ qxy, float* __restrict__ qyz, float* __restrict__ qzx,
     float* __restrict__ Ex, float* __restrict__ Ey, float* __restrict__ Ez,
     float* __restrict__ wc, float* __restrict__ wx, float* __restrict__ wy,
-    float* __restrict__ wz, KPar k, Geo g) {
+    float* __restrict__ wz, const unsigned char* __restrict__ flag, KPar k, Geo g) {
   N n;
   if (!n.init(g)) return;
   using T = typename N::T;
@@ -535,11 +638,10 @@ __global__ void STG_LB(N, STG_MINB_HI) k_edge(
   n.st(Ex, rx_);
   n.st(Ey, ry_);
   n.st(Ez, rz_);
-  const float* ih = k.ih;
-  T sxx = s_du(AX(ux, 0), ih[0]), syy = s_du(AX(uy, 1), ih[1]), szz = s_du(AX(uz, 2), ih[2]);
-  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  const unsigned fl = D2 ? n.ldflag(flag) : 0u;
+  const Strain3<T> Sd = strain_diag<D2>(n, ux, uy, uz, fl, k);
+  const Strain3<T> So = strain_off<D2>(n, ux, uy, uz, fl, k);
+  const T sxx = Sd.a, syy = Sd.b, szz = Sd.c, sxy = So.a, syz = So.b, szx = So.c;
   n.st(wc, (txx_ * sxx + tyy_ * syy) + tzz_ * szz);
   n.st(wx, 2.f * (tyz_ * syz) + rx_ * n.ld(Jx));
   n.st(wy, 2.f * (tzx_ * szx) + ry_ * n.ld(Jy));

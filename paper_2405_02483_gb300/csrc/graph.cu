@@ -62,6 +62,7 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, Geo g) {
     case G_AXPB: r = (T)nd.c0 * A[idx] + (T)nd.c1; break;
     case G_CLAMPMIN: r = A[idx] < (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_CLAMPMAX: r = A[idx] > (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
+    case G_STEP: r = A[idx] > (T)nd.c0 ? (T)1 : (T)0; break;
     default: r = (T)nd.c0; break;  // G_CONST
   }
   out[idx] = r;
@@ -125,7 +126,7 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
     case G_AXPB: gA[idx] += (T)nd.c0 * gg; break;
     case G_CLAMPMIN: if (A[idx] >= (T)nd.c0) gA[idx] += gg; break;
     case G_CLAMPMAX: if (A[idx] <= (T)nd.c0) gA[idx] += gg; break;
-    default: break;
+    default: break;   // G_STEP (piecewise constant), G_CONST, G_INPUT
   }
 }
 
@@ -252,13 +253,38 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     int rxy = dens(dn(dn(lsrc, X), Y));
     int ryz = dens(dn(dn(lsrc, Y), Z));
     int rzx = dens(dn(dn(lsrc, Z), X));
-    // Strain and stress, eq. (itv).
-    int Sxx = ddup(u[X], X), Syy = ddup(u[Y], Y), Szz = ddup(u[Z], Z);
-    int Sxy = G.axpb(G.add(dddn(u[X], Y), dddn(u[Y], X)), 0.5, 0.0);
-    int Syz = G.axpb(G.add(dddn(u[Y], Z), dddn(u[Z], Y)), 0.5, 0.0);
-    int Szx = G.axpb(G.add(dddn(u[Z], X), dddn(u[X], Z)), 0.5, 0.0);
+    // Strain and stress, eq. (itv).  With the second-order switch
+    // (do_2nddiv), a derivative along an axis flagged at the output's index
+    // (|D2 ln rho| or |D2 ln e| of that cell above d2lnr_lim) is the two-point
+    // difference: d6 + flag (d2 - d6).
+    int flag[3] = {-1, -1, -1};
+    if (p.do_2nddiv) {
+      int lrr = G.lg(r), lee = G.lg(e);
+      auto d2abs = [&](int f, int ax) {
+        return G.ab(G.add(G.sub(G.shift(f, ax, 1), G.axpb(f, 2.0, 0.0)), G.shift(f, ax, -1)));
+      };
+      for (int a = 0; a < 3; ++a)
+        flag[a] = G.stepf(G.maxi(d2abs(lrr, a), d2abs(lee, a)), p.d2lnr_lim);
+    }
+    auto sdup = [&](int f, int ax) {
+      int d6 = ddup(f, ax);
+      if (!p.do_2nddiv) return d6;
+      int d2 = G.axpb(G.sub(G.shift(f, ax, 1), f), 1.0 / h[ax], 0.0);
+      return G.add(d6, G.mul(flag[ax], G.sub(d2, d6)));
+    };
+    auto sddn = [&](int f, int ax) {
+      int d6 = dddn(f, ax);
+      if (!p.do_2nddiv) return d6;
+      int d2 = G.axpb(G.sub(f, G.shift(f, ax, -1)), 1.0 / h[ax], 0.0);
+      return G.add(d6, G.mul(flag[ax], G.sub(d2, d6)));
+    };
+    int Sxx = sdup(u[X], X), Syy = sdup(u[Y], Y), Szz = sdup(u[Z], Z);
+    int Sxy = G.axpb(G.add(sddn(u[X], Y), sddn(u[Y], X)), 0.5, 0.0);
+    int Syz = G.axpb(G.add(sddn(u[Y], Z), sddn(u[Z], Y)), 0.5, 0.0);
+    int Szx = G.axpb(G.add(sddn(u[Z], X), sddn(u[X], Z)), 0.5, 0.0);
+    const int divs = p.do_2nddiv ? G.add(G.add(Sxx, Syy), Szz) : divu;
     auto diag = [&](int nii, int S) {
-      int s = p.c1 != 0.0 ? G.add(S, G.axpb(divu, p.c1, 0.0)) : S;
+      int s = p.c1 != 0.0 ? G.add(S, G.axpb(divs, p.c1, 0.0)) : S;
       return G.mul(G.mul(r, nii), s);
     };
     txx = diag(nxx, Sxx);

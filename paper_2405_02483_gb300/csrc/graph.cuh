@@ -13,7 +13,8 @@ namespace stg {
 
 enum GOp {
   G_INPUT = 0, G_STENCIL, G_SHIFT, G_ADD, G_SUB, G_MUL, G_DIV, G_MAX,
-  G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST
+  G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST,
+  G_STEP   // 1 where a > c0, else 0 (a switch: no gradient)
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -55,6 +56,7 @@ struct GraphDef {
   int cmin(int a, double c) { return push(G_CLAMPMIN, a, -1, 0, 0, c, 0); }
   int cmax(int a, double c) { return push(G_CLAMPMAX, a, -1, 0, 0, c, 0); }
   int cnst(double c) { return push(G_CONST, -1, -1, 0, 0, c, 0); }
+  int stepf(int a, double c) { return push(G_STEP, a, -1, 0, 0, c, 0); }
 };
 
 // Build the right-hand-side graph for a grid and parameter set.
