@@ -38,7 +38,15 @@ path by specification only, never by code):
       d2lnr_lim (D2_a f = f(+1) - 2 f + f(-1) along a); every derivative along
       a in the strain of eq. (itv), in its c1 div u term and in the viscous
       heating built from that strain is then the two-point difference
-      (f(i+1) - f(i))/h or (f(i) - f(i-1))/h instead of eq. (deriv).
+      (f(i+1) - f(i))/h or (f(i) - f(i-1))/h instead of eq. (deriv);
+  R19 a stretched vertical mesh (Sect. "Derivatives", the mesh file of
+      Sect. "Input and output"): z-derivatives are the index-space stencils
+      divided by dz/dk at the centre of the derivative (the cell centre after
+      ddup, the lower face after dddn); interpolations stay in index space;
+      the diffusion length of z is the local spacing (faces for the Ex, Ey
+      edges); dl_min in eq. (RMnu), eq. (nusmag) and the Courant limits is
+      the local smallest cell size, and the limits are minima over cells;
+      dl_min and dl_max of the anisotropy factor are those of the mesh.
 """
 from __future__ import annotations
 
@@ -71,6 +79,10 @@ class Grid:
     dx: float
     dy: float
     dz: float
+    # Stretched vertical mesh (reading R19): dz/dk at the cell centres k and at
+    # the lower faces k-1/2 (nz values each), or None for a uniform z.
+    zc: tuple = None
+    zf: tuple = None
 
     def n(self, ax):
         return {"x": self.nx, "y": self.ny, "z": self.nz}[ax]
@@ -78,20 +90,78 @@ class Grid:
     def h(self, ax):
         return {"x": self.dx, "y": self.dy, "z": self.dz}[ax]
 
+    @property
+    def stretched(self):
+        return self.zc is not None
+
+    def _zt(self, v):
+        return torch.tensor(v, dtype=DT).reshape(self.nz, 1, 1)
+
+    def hc(self, ax):
+        """Spacing at cell centres along ax: the divisor of a derivative whose
+        output sits at a centre along ax (ddup of a face quantity)."""
+        return self._zt(self.zc) if ax == "z" and self.stretched else self.h(ax)
+
+    def hf(self, ax):
+        """Spacing at the lower faces along ax: the divisor of a derivative
+        whose output sits on a face along ax (dddn of a centred quantity)."""
+        return self._zt(self.zf) if ax == "z" and self.stretched else self.h(ax)
+
     def active(self):
         return [a for a in "xyz" if self.n(a) > 1] or ["x", "y", "z"]
 
+    def _cell_sizes(self, ax):
+        return list(self.zc) if ax == "z" and self.stretched else [self.h(ax)]
+
     @property
     def dl_min(self):
-        return min(self.h(a) for a in self.active())
+        return min(min(self._cell_sizes(a)) for a in self.active())
 
     @property
     def dl_max(self):
-        return max(self.h(a) for a in self.active())
+        return max(max(self._cell_sizes(a)) for a in self.active())
+
+    def dlmin_c(self):
+        """Local dl_min at the cell centres: the smallest active cell size
+        (a tensor over z on a stretched mesh)."""
+        out = None
+        for a in self.active():
+            out = self.hc(a) if out is None else _vmin(out, self.hc(a))
+        return out
 
     def spacing(self, ax):
-        """Diffusion length scale of an axis (R13)."""
+        """Diffusion length scale of an axis (R13) on a uniform mesh."""
         return self.h(ax) if self.n(ax) > 1 else self.dl_min
+
+    def spacing_c(self, ax):
+        """Diffusion length of an axis at cell centres (R13, R19)."""
+        return self.hc(ax) if self.n(ax) > 1 else self.dl_min
+
+    def spacing_f(self, ax):
+        """Diffusion length of an axis on its lower faces (R13, R19)."""
+        return self.hf(ax) if self.n(ax) > 1 else self.dl_min
+
+    def weights(self):
+        """Volume weights of centred and z-face cells for the sums of the
+        diagnostics: spacing over mean spacing along a stretched z, else 1."""
+        if not self.stretched:
+            return 1.0, 1.0
+        hbar = sum(self.zc) / self.nz
+        return self._zt(self.zc) / hbar, self._zt(self.zf) / hbar
+
+
+def _vmax(a, b):
+    """Maximum of two lengths, each a number or a tensor over z."""
+    if torch.is_tensor(a) or torch.is_tensor(b):
+        return torch.maximum(torch.as_tensor(a, dtype=DT), torch.as_tensor(b, dtype=DT))
+    return max(a, b)
+
+
+def _vmin(a, b):
+    """Minimum of two lengths, each a number or a tensor over z."""
+    if torch.is_tensor(a) or torch.is_tensor(b):
+        return torch.minimum(torch.as_tensor(a, dtype=DT), torch.as_tensor(b, dtype=DT))
+    return min(a, b)
 
 
 @dataclass
@@ -148,26 +218,46 @@ def dn(f, ax):
             + IC * (_s(f, ax, -3) + _s(f, ax, 2)))
 
 
+class Spacing:
+    """The spacings of one axis at its cell centres (c) and lower faces (f),
+    each a number or a tensor over z (R19).  ddup divides by c, dddn by f: in
+    this code ddup always takes a face quantity to the centres and dddn a
+    centred one to the faces, and the paper's Jacobian is the inverse spacing
+    at the centre of the derivative (Sect. "Derivatives")."""
+
+    def __init__(self, c, f):
+        self.c, self.f = c, f
+
+
+def _hc(h):
+    return h.c if isinstance(h, Spacing) else h
+
+
+def _hf(h):
+    return h.f if isinstance(h, Spacing) else h
+
+
 def ddup(f, ax, h):
-    """6th-order derivative at i+1/2, eq. (deriv)."""
+    """6th-order derivative at i+1/2, eq. (deriv): the index-space stencil
+    over the spacing h (a number, a tensor over z, or a Spacing)."""
     return (DA * (_s(f, ax, 1) - f) + DB * (_s(f, ax, 2) - _s(f, ax, -1))
-            + DC * (_s(f, ax, 3) - _s(f, ax, -2))) / h
+            + DC * (_s(f, ax, 3) - _s(f, ax, -2))) / _hc(h)
 
 
 def dddn(f, ax, h):
     """6th-order derivative at i-1/2 (downward variant of eq. (deriv))."""
     return (DA * (f - _s(f, ax, -1)) + DB * (_s(f, ax, 1) - _s(f, ax, -2))
-            + DC * (_s(f, ax, 2) - _s(f, ax, -3))) / h
+            + DC * (_s(f, ax, 2) - _s(f, ax, -3))) / _hf(h)
 
 
 def ddup2(f, ax, h):
     """Second-order derivative at i+1/2: the two-point difference (R18)."""
-    return (_s(f, ax, 1) - f) / h
+    return (_s(f, ax, 1) - f) / _hc(h)
 
 
 def dddn2(f, ax, h):
     """Second-order derivative at i-1/2: the two-point difference (R18)."""
-    return (f - _s(f, ax, -1)) / h
+    return (f - _s(f, ax, -1)) / _hf(h)
 
 
 def d2_flags(r, E, lim):
@@ -218,7 +308,7 @@ def rhs_parts(f, g: Grid, p: Params):
     """Right-hand side of the eight prognostic equations and the intermediate
     fields it is built from.  Returns a dict; keys d_r ... d_Bz hold F(f)."""
     r, px, py, pz, E, Bx, By, Bz = f
-    hx, hy, hz = g.dx, g.dy, g.dz
+    hx, hy, hz = (Spacing(g.hc(a), g.hf(a)) for a in "xyz")
     out = {}
 
     # Pointwise primitives (Sect. "Centering"); faces by log interpolation (R4).
@@ -250,9 +340,13 @@ def rhs_parts(f, g: Grid, p: Params):
     txx = tyy = tzz = txy = tyz = tzx = zero
     ediff = [zero, zero, zero]
     if p.visc_on():
-        Sx, Sy, Sz = g.spacing("x"), g.spacing("y"), g.spacing("z")
+        # Diffusion lengths (R13) at the centres and, for the edges on z faces,
+        # at the faces (a stretched z, R19).
+        Sx, Sy, Sz = g.spacing_c("x"), g.spacing_c("y"), g.spacing_c("z")
+        Sfx, Sfy, Sfz = g.spacing_f("x"), g.spacing_f("y"), g.spacing_f("z")
+        dlc = g.dlmin_c()
         if p.nu_const > 0:
-            nuc = torch.full_like(r, p.nu_const / g.dl_min)
+            nuc = torch.zeros_like(r) + p.nu_const / dlc
             nxx = nyy = nzz = torch.full_like(r, p.nu_const)
             nxy = nyz = nzx = torch.full_like(r, p.nu_const)
         else:
@@ -262,7 +356,7 @@ def rhs_parts(f, g: Grid, p: Params):
             cs = torch.sqrt(p.gamma * P / r)
             ca = torch.sqrt(B2 / r)
             nu = (p.nu1 * torch.sqrt(uc2) + p.nu3 * (cs + ca)
-                  + p.nu2 * g.dl_min * torch.clamp(-divu, min=0.0))
+                  + p.nu2 * dlc * torch.clamp(-divu, min=0.0))
             if p.csmag > 0:
                 # eq. (nusmag), reading R17: the rate |S| times dl_min joins the
                 # velocity-like nu, with Sum_ij over i != j and the off-diagonal
@@ -274,7 +368,7 @@ def rhs_parts(f, g: Grid, p: Params):
                 s2 = (sxx * sxx + syy * syy + szz * szz - divu * divu / 3.0
                       + 2.0 * (up(up(sxy * sxy, "x"), "y") + up(up(syz * syz, "y"), "z")
                                + up(up(szx * szx, "z"), "x")))
-                nu = nu + p.csmag * g.dl_min * torch.sqrt(2.0 * torch.clamp(s2, min=0.0))
+                nu = nu + p.csmag * dlc * torch.sqrt(2.0 * torch.clamp(s2, min=0.0))
             out["nu_raw"] = nu
             # <nu>_{max smooth} (R5).
             for ax in "xyz":
@@ -286,9 +380,9 @@ def rhs_parts(f, g: Grid, p: Params):
             # eq. (nuij): diagonal on centres, off-diagonal by log interpolation.
             lnu = torch.log(torch.clamp(nuc, min=NU_FLOOR))
             nxx, nyy, nzz = Sx * nuc, Sy * nuc, Sz * nuc
-            nxy = max(Sx, Sy) * torch.exp(dn(dn(lnu, "x"), "y"))
-            nyz = max(Sy, Sz) * torch.exp(dn(dn(lnu, "y"), "z"))
-            nzx = max(Sz, Sx) * torch.exp(dn(dn(lnu, "z"), "x"))
+            nxy = _vmax(Sx, Sy) * torch.exp(dn(dn(lnu, "x"), "y"))      # Ez edge: z centre
+            nyz = _vmax(Sfy, Sfz) * torch.exp(dn(dn(lnu, "y"), "z"))    # Ex edge: z face
+            nzx = _vmax(Sfz, Sfx) * torch.exp(dn(dn(lnu, "z"), "x"))    # Ey edge: z face
         out["nu"] = nuc
         # Edge densities (R4).
         if p.log_interp:
@@ -443,8 +537,16 @@ def courant_dt(f, q1, g: Grid, p: Params, nu=None):
     uperp2 = torch.where(B2 > 0, u2 - ub * ub / torch.where(B2 > 0, B2, 1.0), u2)
     uperp = torch.sqrt(torch.clamp(uperp2, min=0.0))
     inf = math.inf
-    wmax = float(torch.max(cs + ca + uperp))
-    t_wave = p.Cdt * g.dl_min / wmax if wmax > 0 else inf
+    # With a stretched z (R19) the limits are minima over the cells of their
+    # local values, dl the cell's smallest active size.
+    dlc = g.dlmin_c()
+    w = cs + ca + uperp
+    if g.stretched:
+        wr = float(torch.max(w / dlc))
+        t_wave = p.Cdt / wr if wr > 0 else inf
+    else:
+        wmax = float(torch.max(w))
+        t_wave = p.Cdt * g.dl_min / wmax if wmax > 0 else inf
     rate = torch.maximum(torch.abs(q1[0]) / r, torch.abs(q1[4]) / E)
     rmax = float(torch.max(rate))
     t_rate = p.Cdtr / rmax if rmax > 0 else inf
@@ -452,8 +554,13 @@ def courant_dt(f, q1, g: Grid, p: Params, nu=None):
     if p.visc_on():
         if nu is None:
             nu = rhs_parts(f, g, p)["nu"]
-        dmax = float(torch.max(nu)) * max(1.0, p.nuE, p.nuB * g.dl_max / g.dl_min)
-        t_diff = p.Cdtd * g.dl_min / dmax if dmax > 0 else inf
+        dfac = max(1.0, p.nuE, p.nuB * g.dl_max / g.dl_min)
+        if g.stretched:
+            dr = float(torch.max(nu / dlc)) * dfac
+            t_diff = p.Cdtd / dr if dr > 0 else inf
+        else:
+            dmax = float(torch.max(nu)) * dfac
+            t_diff = p.Cdtd * g.dl_min / dmax if dmax > 0 else inf
     return min(t_wave, t_rate, t_diff), (t_wave, t_rate, t_diff)
 
 
@@ -485,17 +592,22 @@ def step_adjoint(f, dt, lam, g: Grid, p: Params):
 def diagnostics(f, g: Grid, p: Params):
     """[sum r, sum px, sum py, sum pz, sum E, kinetic, magnetic, max|divB|,
     rms divB, non-finite count] with kinetic = sum 1/2 p.u over faces and
-    magnetic = sum 1/2 B^2 over faces (plain sums over cells)."""
+    magnetic = sum 1/2 B^2 over faces: plain sums over cells, each term
+    weighted by its cell's z size over the mean one on a stretched z (R19),
+    z-face quantities by the face spacing; these are the totals the discrete
+    equations conserve."""
     r, px, py, pz, E, Bx, By, Bz = [fi.to(DT) for fi in f]
     if p.log_interp:
         lr = torch.log(r)
         rx, ry, rz = torch.exp(dn(lr, "x")), torch.exp(dn(lr, "y")), torch.exp(dn(lr, "z"))
     else:
         rx, ry, rz = dn(r, "x"), dn(r, "y"), dn(r, "z")
-    kin = 0.5 * (px * px / rx + py * py / ry + pz * pz / rz).sum()
-    mag = 0.5 * (Bx * Bx + By * By + Bz * Bz).sum()
-    divb = ddup(Bx, "x", g.dx) + ddup(By, "y", g.dy) + ddup(Bz, "z", g.dz)
+    wc, wf = g.weights()
+    kin = 0.5 * ((px * px / rx + py * py / ry) * wc + pz * pz / rz * wf).sum()
+    mag = 0.5 * ((Bx * Bx + By * By) * wc + Bz * Bz * wf).sum()
+    divb = ddup(Bx, "x", g.hc("x")) + ddup(By, "y", g.hc("y")) + ddup(Bz, "z", g.hc("z"))
     nonfinite = sum(int((~torch.isfinite(fi)).sum()) for fi in (r, px, py, pz, E, Bx, By, Bz))
-    return [float(r.sum()), float(px.sum()), float(py.sum()), float(pz.sum()), float(E.sum()),
+    return [float((r * wc).sum()), float((px * wc).sum()), float((py * wc).sum()),
+            float((pz * wf).sum()), float((E * wc).sum()),
             float(kin), float(mag), float(divb.abs().max()), float(divb.pow(2).mean().sqrt()),
             float(nonfinite)]

@@ -734,3 +734,129 @@ def test_second_order_switch_conservation():
                 do_2nddiv=True, d2lnr_lim=0.02)
     test_conservation_and_divb(P2)
     test_cyclic_axis_permutation(P2)
+
+
+# --------------------- stretched vertical mesh (R19) --------------------------
+
+def _stretched_grid(nx, ny, nz, A=0.4, hbar=None, dx=0.3, dy=0.25):
+    """Periodic stretched z: z(xi) = hbar (xi + A sin(th xi) / th), th = 2 pi / nz,
+    so dz/dk = hbar (1 + A cos(th xi)) at centres (xi = k + 1/2) and faces (xi = k)."""
+    hbar = hbar if hbar is not None else 1.0 / nz
+    th = 2 * math.pi / nz
+    zc = tuple(hbar * (1 + A * math.cos(th * (k + 0.5))) for k in range(nz))
+    zf = tuple(hbar * (1 + A * math.cos(th * k)) for k in range(nz))
+    zpos = lambda xi: hbar * (xi + A * math.sin(th * xi) / th)
+    return Grid(nx, ny, nz, dx, dy, hbar, zc=zc, zf=zf), zpos
+
+
+def test_stretched_mesh_with_constant_spacing_is_the_uniform_grid():
+    g = Grid(7, 6, 8, 0.3, 0.25, 0.125)
+    gs = Grid(7, 6, 8, 0.3, 0.25, 0.125, zc=(0.125,) * 8, zf=(0.125,) * 8)
+    f = random_state(g, seed=5)
+    p = Params(nu1=0.03, nu2=0.5, nu3=0.03, do_quench=True, csmag=0.1, c1=-1.0 / 3.0)
+    a, b = S.rhs(f, g, p), S.rhs(f, gs, p)
+    assert all(torch.allclose(x, y, rtol=1e-13, atol=1e-13 * float(x.abs().max())) for x, y in zip(a, b))
+    q = S.rhs(f, g, p)
+    assert abs(S.courant_dt(f, q, g, p)[0] / S.courant_dt(f, q, gs, p)[0] - 1) < 1e-13
+    da, db = S.diagnostics(f, g, p), S.diagnostics(f, gs, p)
+    assert all(abs(x - y) <= 1e-12 * max(abs(x), 1.0) for x, y in zip(da, db))
+
+
+def _stretched_errors(n, m=2):
+    """Errors of ddup (faces -> centres) and dddn (centres -> faces) of
+    sin(2 pi m z / L) on the stretched mesh, against the exact derivative."""
+    g, zpos = _stretched_grid(4, 4, n)
+    L = n * g.dz
+    k = 2 * math.pi * m / L
+    shape = (n, 4, 4)
+    zf = torch.tensor([zpos(i) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    zc = torch.tensor([zpos(i + 0.5) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    h = S.Spacing(g.hc("z"), g.hf("z"))
+    e_up = float((S.ddup(torch.sin(k * zf), "z", h) - k * torch.cos(k * zc)).abs().max())
+    e_dn = float((S.dddn(torch.sin(k * zc), "z", h) - k * torch.cos(k * zf)).abs().max())
+    return e_up / k, e_dn / k
+
+
+def test_stretched_derivatives_converge_at_sixth_order():
+    # The stencil acts in index space on a smooth function of xi and the
+    # Jacobian is exact at the derivative's centre, so the error falls as
+    # (1/n)^6: a Jacobian taken half a cell off would leave a first-order error.
+    e32, e64 = _stretched_errors(32), _stretched_errors(64)
+    for a, b in zip(e32, e64):
+        assert a / b > 40, (a, b)
+    assert max(e64) < 1e-6
+
+
+def _stretched_rhs_errors(n, nu=0.01, c1=-1.0 / 3.0):
+    # rho = 1, P uniform and small, u_z = amp sin(k z): d rho/dt = -d(pz)/dz, and the
+    # constant-viscosity term of d pz/dt is nu (1 + c1) d2 u_z / dz2.
+    g, zpos = _stretched_grid(4, 4, n)
+    L = n * g.dz
+    k = 2 * math.pi / L
+    shape = (n, 4, 4)
+    zf = torch.tensor([zpos(i) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    zc = torch.tensor([zpos(i + 0.5) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    # A small pressure keeps its rounding inside T_zz below the viscous stress.
+    amp = 1e-6
+    one = torch.ones(shape, dtype=DT)
+    f = [one, 0 * one, 0 * one, amp * torch.sin(k * zf), 1e-7 * one, 0 * one, 0 * one, 0 * one]
+    F0 = S.rhs(f, g, Params(nu_const=nu, c1=c1))
+    Fi = S.rhs(f, g, Params())
+    e_mass = float((F0[0] + amp * k * torch.cos(k * zc)).abs().max()) / (amp * k)
+    lam = nu * (1 + c1) * k * k
+    e_visc = float(((F0[3] - Fi[3]) + lam * amp * torch.sin(k * zf)).abs().max()) / (lam * amp)
+    return e_mass, e_visc
+
+
+def test_stretched_rhs_converges_at_sixth_order():
+    e32, e64 = _stretched_rhs_errors(32), _stretched_rhs_errors(64)
+    for a, b in zip(e32, e64):
+        assert a / b > 30, (a, b)
+
+
+def test_stretched_viscosity_lengths():
+    # Uniform rho, P, B and u = 0 except a tiny u_y(z), u_x(z): <nu> = nu3 (c_s + c_A)
+    # everywhere; nu_zz carries dz/dk at the centre and the Ex, Ey edges on z
+    # faces carry max(dy, dz/dk at the face) and max(dz/dk at the face, dx).
+    n = 16
+    g, zpos = _stretched_grid(4, 4, n, A=0.5, dx=0.01, dy=0.01)
+    shape = (n, 4, 4)
+    one = torch.ones(shape, dtype=DT)
+    zc = torch.tensor([zpos(i + 0.5) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    zf = torch.tensor([zpos(i) for i in range(n)], dtype=DT).reshape(n, 1, 1).expand(shape)
+    gam, Pv, Bz = 5.0 / 3.0, 0.6, 0.3
+    L = n * g.dz
+    f = [one, 1e-9 * torch.sin(2 * math.pi * zc / L), 1e-9 * torch.cos(2 * math.pi * zc / L),
+         1e-9 * torch.sin(2 * math.pi * zf / L), Pv / (gam - 1) * one, 0 * one, 0 * one, Bz * one]
+    nu3 = 0.05
+    P = S.rhs_parts(f, g, Params(nu3=nu3))
+    nu0 = nu3 * (math.sqrt(gam * Pv) + Bz)
+    assert torch.allclose(P["nu"], nu0 * one, rtol=1e-8)
+    hc, hf = g.hc("z").expand(shape), g.hf("z").expand(shape)
+    Szz = S.ddup(f[3], "z", S.Spacing(g.hc("z"), g.hf("z")))
+    assert torch.allclose(P["tzz"], (nu0 * hc) * Szz, rtol=1e-7, atol=1e-20)
+    ux_z = S.dddn(f[1], "z", S.Spacing(g.hc("z"), g.hf("z")))
+    assert torch.allclose(P["tzx"], (nu0 * hf) * 0.5 * ux_z, rtol=1e-7, atol=1e-20)
+
+
+def test_stretched_conservation_divb_and_courant():
+    g, _ = _stretched_grid(6, 5, 12, A=0.45)
+    f = random_state(g, seed=9)
+    p = Params(nu1=0.03, nu2=0.5, nu3=0.03, do_quench=True)
+    F = S.rhs(f, g, p)
+    wc, wf = g.weights()
+    # The weighted mass and momentum totals the diagnostics report do not
+    # change (E = rho e has the sources -P div u + Q of eq. (ien)).
+    for i, w in ((0, wc), (1, wc), (2, wc), (3, wf)):
+        tot = float((F[i] * w).sum())
+        assert abs(tot) < 1e-11 * float((F[i].abs() * w).sum()), (i, tot)
+    # -curl E keeps div B: the divergence of dB/dt vanishes with the same Jacobians.
+    hx, hy, hz = (S.Spacing(g.hc(a), g.hf(a)) for a in "xyz")
+    ddb = S.ddup(F[5], "x", hx) + S.ddup(F[6], "y", hy) + S.ddup(F[7], "z", hz)
+    assert float(ddb.abs().max()) < 1e-10 * float(F[5].abs().max() / g.dl_min)
+    # Uniform state, min dz/dk below dx and dy: the wave limit is Cdt min(dz/dk) / w.
+    u = [torch.full((12, 5, 6), v, dtype=DT) for v in (1.0, 0.0, 0.0, 0.0, 0.9, 0.0, 0.0, 0.0)]
+    q = S.rhs(u, g, Params())
+    dt, (tw, tr, td) = S.courant_dt(u, q, g, Params())
+    cs = math.sqrt(5.0 / 3.0 * (2.0 / 3.0) * 0.9)
+    assert abs(tw - 0.4 * min(g.zc) / cs) < 1e-14
