@@ -94,6 +94,17 @@ typedef struct {
    * d2lnr_lim defaults to 0.3 (a negative limit flags every cell). */
   int do_2nddiv;
   double d2lnr_lim;
+  /* Stretched vertical mesh (Sect. Derivatives; the mesh file of Sect. Input
+   * and output): dz/dk at the cell centres (zc) and at the lower faces (zf),
+   * nz positive values each, host arrays the caller owns, read (copied) by
+   * stagger_create only.  z-derivatives are the index-space stencils times
+   * 1/zc at centres and 1/zf at faces; the z diffusion length, dl_min of
+   * eqs. (RMnu) and (nusmag) and the Courant limits use the local spacing;
+   * diagnostics weight each cell by its spacing over the mean.  Both NULL
+   * (default): uniform z of spacing grid.dz.  Needs nz > 1; one NULL and one
+   * not, or a non-positive value: STAGGER_EINVAL. */
+  const double* zc;
+  const double* zf;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
@@ -198,9 +209,10 @@ int stagger_kernel_times(stagger_ctx* ctx, int max, const char** names, double* 
  * owns the device's memory, a monitoring tool that must not change the
  * footprint of the run it inspects, or code that has no context (creating
  * one allocates tens of arrays of the grid's size).
- * Limit: at most 65536 thread blocks of 32 x 8 cells, i.e.
- * ceil(nx/32) * ceil(ny/8) * nz <= 65536 (for example 256^3); larger grids
- * return STAGGER_EINVAL.  The first call on each device looks up the array's
+ * Limit: at most 65536 thread blocks of 32 x 2 x 4 cells, i.e.
+ * ceil(nx/32) * ceil(ny/2) * ceil(nz/4) <= 65536 (for example 256^3); larger
+ * grids return STAGGER_EINVAL.  A stretched z (params->zc, zf) needs its mesh
+ * on the device and returns STAGGER_EUNSUPPORTED.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  All calls share the one array:
  * calls that overlap on the GPU (two streams, two host threads) race, so

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("t_cool", ctypes.c_double), ("e_cool", ctypes.c_double),
                 ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int),
                 ("csmag", ctypes.c_double), ("scalar_cells", ctypes.c_int),
-                ("do_2nddiv", ctypes.c_int), ("d2lnr_lim", ctypes.c_double)]
+                ("do_2nddiv", ctypes.c_int), ("d2lnr_lim", ctypes.c_double),
+                ("zc", ctypes.POINTER(ctypes.c_double)), ("zf", ctypes.POINTER(ctypes.c_double))]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8
@@ -111,6 +112,12 @@ def default_params(**kw) -> Params:
             p.g = (ctypes.c_double * 3)(*v)
         elif k == "ref":
             p.ref = (ctypes.c_double * 8)(*v)
+        elif k in ("zc", "zf"):
+            # Stretched z mesh: dz/dk at centres / lower faces (nz values each);
+            # the array lives as long as the Params object.
+            arr = (ctypes.c_double * len(v))(*[float(x) for x in v])
+            setattr(p, k, ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)))
+            setattr(p, "_" + k, arr)
         else:
             setattr(p, k, v)
     return p

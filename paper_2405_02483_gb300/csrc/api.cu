@@ -74,6 +74,13 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
+  if ((p->zc == nullptr) != (p->zf == nullptr)) return STAGGER_EINVAL;
+  if (p->zc) {
+    if (g->nz < 2) return STAGGER_EINVAL;
+    for (int k = 0; k < g->nz; ++k)
+      if (!(p->zc[k] > 0) || !(p->zf[k] > 0) || !isfinite(p->zc[k]) || !isfinite(p->zf[k]))
+        return STAGGER_EINVAL;
+  }
   return STAGGER_OK;
 }
 
@@ -93,6 +100,9 @@ int stagger_create(const stagger_grid* grid, const stagger_params* params, stagg
     return rc;
   }
   build_rhs_graph(c->gdef, *grid, *params);
+  // The mesh arrays are the caller's and were read above (the fused path and
+  // the graph keep their own copies): drop the pointers.
+  c->params.zc = c->params.zf = nullptr;
   *out = c;
   return STAGGER_OK;
 }

@@ -98,10 +98,24 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   KPar& k = F.kp;
   const double h[3] = {gr.dx, gr.dy, gr.dz};
   const int nn[3] = {gr.nx, gr.ny, gr.nz};
-  double dlmin = 1e300;
+  // A stretched z (R19) takes its smallest and largest cell into the mesh's
+  // dl_min and dl_max.
+  const bool zs = p.zc != nullptr;
+  double zcmin = 1e300, zcmax = 0, zcsum = 0, zfsum = 0;
+  for (int kk = 0; zs && kk < gr.nz; ++kk) {
+    zcmin = fmin(zcmin, p.zc[kk]);
+    zcmax = fmax(zcmax, p.zc[kk]);
+    zcsum += p.zc[kk];
+    zfsum += p.zf[kk];
+  }
+  double dlmin = 1e300, dlxy = 1e300;
   int any = 0;
   for (int a = 0; a < 3; ++a)
-    if (nn[a] > 1) { dlmin = fmin(dlmin, h[a]); any = 1; }
+    if (nn[a] > 1) {
+      dlmin = fmin(dlmin, (a == 2 && zs) ? zcmin : h[a]);
+      if (a < 2) dlxy = fmin(dlxy, h[a]);
+      any = 1;
+    }
   if (!any) dlmin = fmin(h[0], fmin(h[1], h[2]));
   double sp[3];
   for (int a = 0; a < 3; ++a) {
@@ -145,7 +159,15 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.cool_cut = p.cool_cut;
   double dlmax = 0;
   for (int a = 0; a < 3; ++a)
-    if (nn[a] > 1 || !any) dlmax = fmax(dlmax, h[a]);
+    if (nn[a] > 1 || !any) dlmax = fmax(dlmax, (a == 2 && zs) ? zcmax : h[a]);
+  k.dlmin = (float)dlmin;
+  k.dlxy = (float)fmin(dlxy, 1e30);
+  k.nu2 = (float)p.nu2;
+  k.csmag = (float)p.csmag;
+  k.izbar = zs ? gr.nz / zcsum : 1.0;
+  k.hzc = k.hzf = k.jzc = k.jzf = nullptr;
+  F.zs = zs ? 1 : 0;
+  F.wsum_f = zs ? (double)gr.nx * gr.ny * zfsum * k.izbar : (double)F.geo.n;
   F.cdt = p.Cdt;
   F.cdtr = p.Cdtr;
   F.cdtd = p.Cdtd;
@@ -159,6 +181,31 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.red = nullptr;
   F.cmax = nullptr;
   F.d2flag = nullptr;
+  F.mesh = nullptr;
+  if (zs) {
+    // dz/dk at centres and faces and their inverses, as four arrays of nz.
+    std::vector<float> m((size_t)4 * gr.nz);
+    for (int kk = 0; kk < gr.nz; ++kk) {
+      m[kk] = (float)p.zc[kk];
+      m[gr.nz + kk] = (float)p.zf[kk];
+      m[2 * gr.nz + kk] = (float)(1.0 / p.zc[kk]);
+      m[3 * gr.nz + kk] = (float)(1.0 / p.zf[kk]);
+    }
+    if (cudaMalloc(&F.mesh, sizeof(float) * m.size()) != cudaSuccess) {
+      F.mesh = nullptr;
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+    if (cudaMemcpy(F.mesh, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      fused_release(F);
+      return STAGGER_ECUDA;
+    }
+    k.hzc = F.mesh;
+    k.hzf = F.mesh + gr.nz;
+    k.jzc = F.mesh + 2 * gr.nz;
+    k.jzf = F.mesh + 3 * gr.nz;
+  }
   // Which intermediate fields this parameter set needs.
   std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
                            F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
@@ -219,6 +266,8 @@ void fused_release(Fused& F) {
   F.cmax = nullptr;
   if (F.d2flag) cudaFree(F.d2flag);
   F.d2flag = nullptr;
+  if (F.mesh) cudaFree(F.mesh);
+  F.mesh = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -231,9 +280,10 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
   const KPar& k = F.kp;
   float** d = F.fld;
   const dim3 gg = grid_cells<N>(g), bb(BX, BY, BZ);
+  using NB = typename N::Base;   // kernels without derivatives or lengths
   const float* ls = k.log_interp ? d[F_LR] : f[0];
-  if (k.log_interp) TIMED(K_LR, (k_lr<N><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
-  TIMED(K_VEL, (k_vel<N><<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
+  if (k.log_interp) TIMED(K_LR, (k_lr<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
+  TIMED(K_VEL, (k_vel<NB><<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
     if (k.csmag_dl > 0.f)
@@ -247,12 +297,12 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
       TIMED(K_NU_RAW, (k_nu_raw<false, N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
                                                           f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
                                                           d[F_SQZX], d[F_NV], k, g)));
-    TIMED(K_NU_MAX, (k_nu_max<N><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
-    TIMED(K_NU_SMOOTH, (k_nu_smooth<N><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
-    TIMED(K_NU_FACES, (k_nu_faces<N><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
+    TIMED(K_NU_MAX, (k_nu_max<NB><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
+    TIMED(K_NU_SMOOTH, (k_nu_smooth<NB><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
+    TIMED(K_NU_FACES, (k_nu_faces<NB><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
   if (k.d2div)
-    TIMED(K_D2FLAG, (k_d2flag<N><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
+    TIMED(K_D2FLAG, (k_d2flag<NB><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
   auto ktau = k.d2div ? k_tau<N, true> : k_tau<N, false>;
   TIMED(K_TAU, (ktau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
                                        d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
@@ -281,7 +331,9 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
 }
 
 static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
-  return F.cells4 && aligned16(f, 8) ? pre_div_t<Nb4>(F, f, s) : pre_div_t<Nb>(F, f, s);
+  const bool v4 = F.cells4 && aligned16(f, 8);
+  if (F.zs) return v4 ? pre_div_t<Nb4Z>(F, f, s) : pre_div_t<NbZ>(F, f, s);
+  return v4 ? pre_div_t<Nb4>(F, f, s) : pre_div_t<Nb>(F, f, s);
 }
 
 static DivIn div_in(Fused& F, float* const f[8]) {
@@ -308,11 +360,19 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   const dim3 gg = v4 ? grid_cells<Nb4>(F.geo) : grid_cells<Nb>(F.geo), bb(BX, BY, BZ);
   // Momentum; mass and energy; induction (disjoint inputs, one kernel each).
   const int nk = 3;
-  void (*kern[3])(DivIn, float*, float*, float*, float*, float*, float*, float*, float*, float*,
-                  float*, float*, float*, float*, float*, float*, float*, float, float,
-                  const double*, int, KPar, Geo) = {
-      v4 ? k_div<Nb4, 0x0E> : k_div<Nb, 0x0E>, v4 ? k_div<Nb4, 0x11> : k_div<Nb, 0x11>,
-      v4 ? k_div<Nb4, 0xE0> : k_div<Nb, 0xE0>};
+  typedef void (*DivK)(DivIn, float*, float*, float*, float*, float*, float*, float*, float*,
+                       float*, float*, float*, float*, float*, float*, float*, float*, float,
+                       float, const double*, int, KPar, Geo);
+  DivK kern[3];
+  if (F.zs) {
+    kern[0] = v4 ? k_div<Nb4Z, 0x0E> : k_div<NbZ, 0x0E>;
+    kern[1] = v4 ? k_div<Nb4Z, 0x11> : k_div<NbZ, 0x11>;
+    kern[2] = v4 ? k_div<Nb4Z, 0xE0> : k_div<NbZ, 0xE0>;
+  } else {
+    kern[0] = v4 ? k_div<Nb4, 0x0E> : k_div<Nb, 0x0E>;
+    kern[1] = v4 ? k_div<Nb4, 0x11> : k_div<Nb, 0x11>;
+    kern[2] = v4 ? k_div<Nb4, 0xE0> : k_div<Nb, 0xE0>;
+  }
   for (int i = 0; i < nk; ++i)
     TIMED(K_DIV, (kern[i]<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
                                             oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6],
@@ -327,21 +387,26 @@ int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s) {
   return launch_div(F, f, out, nullptr, 0.f, 0.f, 0, s);
 }
 
+template <class N>
+static void courant_part(Fused& F, float* const f[8], cudaStream_t s) {
+  TIMED(K_COURANT, (k_courant_part<N><<<grid_cells<N>(F.geo), dim3(BX, BY, BZ), 0, s>>>(
+                       F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0], f[4], f[5], f[6], f[7],
+                       F.q[0], F.q[4], F.fld[F_NU], F.cmax, F.kp, F.geo)));
+}
+
 static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s) {
   // Uses the primitives and <nu> that pre_div left for this state and q = F(f).
-  const Geo& g = F.geo;
-  const KPar& k = F.kp;
-  const dim3 bb(BX, BY, BZ);
-  if (F.cells4 && aligned16(f, 8))
-    TIMED(K_COURANT, (k_courant_part<Nb4><<<grid_cells<Nb4>(g), bb, 0, s>>>(
-                         F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0], f[4], f[5], f[6], f[7],
-                         F.q[0], F.q[4], F.fld[F_NU], F.cmax, k, g)));
-  else
-    TIMED(K_COURANT, (k_courant_part<Nb><<<grid_cells<Nb>(g), bb, 0, s>>>(
-                         F.fld[F_UX], F.fld[F_UY], F.fld[F_UZ], f[0], f[4], f[5], f[6], f[7],
-                         F.q[0], F.q[4], F.fld[F_NU], F.cmax, k, g)));
+  const bool v4 = F.cells4 && aligned16(f, 8);
+  if (F.zs) {
+    if (v4) courant_part<Nb4Z>(F, f, s); else courant_part<NbZ>(F, f, s);
+  } else {
+    if (v4) courant_part<Nb4>(F, f, s); else courant_part<Nb>(F, f, s);
+  }
+  // A stretched z reduces w / dl and nu / dl per cell: the final pass then
+  // takes dl = 1 and a velocity-like nu.
   TIMED(K_COURANT, (k_courant_final<<<1, 32, 0, s>>>(F.cmax, F.dt_dev, F.cdt, F.cdtr, F.cdtd,
-                                                     F.dlmin, F.dfac, F.kp.rm)));
+                                                     F.zs ? 1.0 : F.dlmin, F.dfac,
+                                                     F.zs ? 1 : F.kp.rm)));
   return STAGGER_OK;
 }
 
@@ -403,8 +468,9 @@ int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaSt
 int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
                       cudaStream_t s) {
   dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
-  TIMED(K_DIAG, (k_diag_part<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7],
-                                               F.red, F.kp, F.geo)));
+  auto kdiag = F.zs ? k_diag_part<NbZ> : k_diag_part<Nb>;
+  TIMED(K_DIAG, (kdiag<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], F.red,
+                                         F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
   std::vector<double> h((size_t)F.red_blocks * 10);
   STG_CUDA_OK(cudaMemcpyAsync(h.data(), F.red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
@@ -417,7 +483,7 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
   out[0] = acc[0] + p.ref[0] * N;
   out[1] = acc[1] + p.ref[1] * N;
   out[2] = acc[2] + p.ref[2] * N;
-  out[3] = acc[3] + p.ref[3] * N;
+  out[3] = acc[3] + p.ref[3] * F.wsum_f;   // z-face weights on a stretched z
   out[4] = acc[4] + p.ref[4] * N;
   out[5] = acc[5];
   out[6] = acc[6];
@@ -479,6 +545,8 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
     if (!state[c]) return STAGGER_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return STAGGER_EINVAL;
   if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || p->ref[0] < 0) return STAGGER_EINVAL;
+  // A stretched z needs its mesh on the device, which this entry cannot allocate.
+  if (p->zc || p->zf) return STAGGER_EUNSUPPORTED;
   const long long nb = (long long)((grid->nx + BX - 1) / BX) * ((grid->ny + BY - 1) / BY) *
                        ((grid->nz + BZ - 1) / BZ);
   if (nb > NOALLOC_MAX_BLOCKS) return STAGGER_EINVAL;  // grid larger than the fixed scratch
@@ -513,7 +581,7 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
   dim3 gg = grid3(g), bb(BX, BY, BZ);
   // Each block writes all ten of its partials, so nothing carries over from
   // an earlier call.
-  k_diag_part<<<gg, bb, 0, s>>>(state[0], state[1], state[2], state[3], state[4], state[5],
+  k_diag_part<Nb><<<gg, bb, 0, s>>>(state[0], state[1], state[2], state[3], state[4], state[5],
                                 state[6], state[7], part, k, g);
   k_diag_final<<<1, 256, 0, s>>>(part, (int)nb, fin);
   STG_CUDA_OK(cudaGetLastError());

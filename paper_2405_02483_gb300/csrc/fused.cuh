@@ -26,6 +26,13 @@ struct KPar {
   float csmag_dl;       // Smagorinsky constant times dl_min (0: off)
   int d2div;            // second-order switch of the stress derivatives
   float d2lim;          // its limit on |D2 ln rho|, |D2 ln e|
+  float dlmin;          // dl_min of the mesh
+  // Stretched z mesh (null when uniform): dz/dk at centres and lower faces
+  // and their inverses (nz values each), the smallest active x, y spacing, and
+  // the raw coefficients that multiply the local dl_min there.
+  const float *hzc, *hzf, *jzc, *jzf;
+  float dlxy, nu2, csmag;
+  double izbar;         // 1 / mean dz/dk (diagnostic weights)
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -63,6 +70,9 @@ struct Fused {
   double* red;          // reduction partials (diagnostics)
   unsigned* cmax;       // Courant maxima as float bits, cleared by each final pass
   unsigned char* d2flag;  // second-order switch flags per cell (bit = axis), or null
+  int zs;               // stretched z mesh
+  float* mesh;          // its dz/dk and inverses on the device (4 nz floats), or null
+  double wsum_f;        // sum of the z-face weights of the diagnostics (n when uniform)
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   long long launches;

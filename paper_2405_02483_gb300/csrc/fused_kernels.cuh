@@ -119,8 +119,10 @@ __device__ __forceinline__ F4 fdiv(const F4& a, const F4& b) {
 // Periodic neighbour offsets of one cell, offsets -3..3 per axis.
 struct Nb {
   using T = float;
+  using Base = Nb;
   static constexpr int W = 1;
   int c;
+  int kz;       // z index of the cell
   int x[7];
   int y[7];
   int z[7];
@@ -131,6 +133,17 @@ struct Nb {
     return axis == 0 ? at(o, 0, 0) : axis == 1 ? at(0, o, 0) : at(0, 0, o);
   }
   __device__ __forceinline__ bool init(const Geo& g);
+  // Uniform mesh: the inverse spacings of derivatives whose output sits at a
+  // centre (ju) or a face (jd) along axis a, the z diffusion lengths at the
+  // centre, the face and a z tap, and the local dl_min (unused when uniform).
+  static constexpr bool ZS = false;
+  __device__ __forceinline__ bool init(const Geo& g, const KPar&) { return init(g); }
+  __device__ __forceinline__ float ju(int a, const KPar& k) const { return k.ih[a]; }
+  __device__ __forceinline__ float jd(int a, const KPar& k) const { return k.ih[a]; }
+  __device__ __forceinline__ float hzc(const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float hzf(const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float hzc_at(int, const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float dlc(const KPar& k) const { return k.dlmin; }
   // Loads through the read-only path (arrays not written by the launch).
   __device__ __forceinline__ float ld(const float* __restrict__ p) const { return __ldg(p + c); }
   __device__ __forceinline__ float ldat(const float* __restrict__ p, int dx, int dy, int dz) const {
@@ -172,6 +185,7 @@ __device__ __forceinline__ bool make_nb(Nb& n, const Geo& g) {
     n.z[o + 3] = wrap(k + o, g.nz) * (int)g.sz;
   }
   n.c = n.z[3] + n.y[3] + n.x[3];
+  n.kz = k;
   return true;
 }
 __device__ __forceinline__ bool Nb::init(const Geo& g) { return make_nb(*this, g); }
@@ -181,8 +195,10 @@ __device__ __forceinline__ bool Nb::init(const Geo& g) { return make_nb(*this, g
 // are register shifts of the aligned 4-cell chunks left, at and right of i0.
 struct Nb4 {
   using T = F4;
+  using Base = Nb4;
   static constexpr int W = 4;
   int c;        // offset of cell i0
+  int kz;       // z index of the cells
   int x0, xl, xr;   // x of the chunk at, left of and right of i0 (periodic)
   int y[7];
   int z[7];
@@ -200,8 +216,21 @@ struct Nb4 {
       z[o + 3] = wrap(k + o, g.nz) * (int)g.sz;
     }
     c = z[3] + y[3] + x0;
+    kz = k;
     return true;
   }
+  // Uniform mesh: the inverse spacings of derivatives whose output sits at a
+  // centre (ju) or a face (jd) along axis a, the z diffusion lengths at the
+  // centre, the face and a z tap, and the local dl_min (unused when uniform).
+  static constexpr bool ZS = false;
+  __device__ __forceinline__ bool init(const Geo& g, const KPar&) { return init(g); }
+  __device__ __forceinline__ float ju(int a, const KPar& k) const { return k.ih[a]; }
+  __device__ __forceinline__ float jd(int a, const KPar& k) const { return k.ih[a]; }
+  __device__ __forceinline__ float hzc(const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float hzf(const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float hzc_at(int, const KPar& k) const { return k.sp[2]; }
+  __device__ __forceinline__ float dlc(const KPar& k) const { return k.dlmin; }
+
   static __device__ __forceinline__ F4 v4(float4 a) { return F4(a.x, a.y, a.z, a.w); }
   static __device__ __forceinline__ F4 row(const float* __restrict__ p, int off) {
     return v4(__ldg(reinterpret_cast<const float4*>(p + off)));
@@ -246,6 +275,36 @@ struct Nb4 {
               ((fl >> (16 + a)) & 1u) ? x.v[2] : y.v[2], ((fl >> (24 + a)) & 1u) ? x.v[3] : y.v[3]);
   }
 };
+
+// A cell type on a stretched z mesh (Sect. Derivatives, reading R19): the
+// cell's dz/dk at its centre and lower face, whose inverses are the
+// Jacobians of z-derivatives that land there, and its smallest cell size.
+template <class B>
+struct ZCell : B {
+  using Base = B;
+  static constexpr bool ZS = true;
+  float jc, jf, hc, hf;
+  int nzm;
+  __device__ __forceinline__ bool init(const Geo& g, const KPar& k) {
+    if (!B::init(g)) return false;
+    nzm = g.nz;
+    hc = __ldg(k.hzc + this->kz);
+    hf = __ldg(k.hzf + this->kz);
+    jc = __ldg(k.jzc + this->kz);
+    jf = __ldg(k.jzf + this->kz);
+    return true;
+  }
+  __device__ __forceinline__ float ju(int a, const KPar& k) const { return a == 2 ? jc : k.ih[a]; }
+  __device__ __forceinline__ float jd(int a, const KPar& k) const { return a == 2 ? jf : k.ih[a]; }
+  __device__ __forceinline__ float hzc(const KPar&) const { return hc; }
+  __device__ __forceinline__ float hzf(const KPar&) const { return hf; }
+  __device__ __forceinline__ float hzc_at(int o, const KPar& k) const {
+    return o == 0 ? hc : __ldg(k.hzc + wrap(this->kz + o, nzm));
+  }
+  __device__ __forceinline__ float dlc(const KPar& k) const { return fminf(k.dlxy, hc); }
+};
+using NbZ = ZCell<Nb>;
+using Nb4Z = ZCell<Nb4>;
 
 // eq. (interp) to i+1/2 / i-1/2 and eq. (deriv) to i+1/2 / i-1/2, on a
 // functor v(o) giving the operand at offset o along the stencil axis.
@@ -293,7 +352,7 @@ __global__ void STG_LB(N, STG_MINB) k_vel(
     float* __restrict__ uz, float* __restrict__ lfx, float* __restrict__ lfy,
     float* __restrict__ lfz, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
   const T lx = s_dn(AX(ls, 0)), ly = s_dn(AX(ls, 1)), lz = s_dn(AX(ls, 2));
   n.st(ux, fdiv(n.ld(px) + k.pref[0], dens(lx, k)));
@@ -329,12 +388,11 @@ __global__ void STG_LB(N, STG_MINB) k_strain2(
     const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
     float* __restrict__ sxy2, float* __restrict__ syz2, float* __restrict__ szx2, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
-  const float* ih = k.ih;
-  T sxy = 0.5f * (s_dd(AX(ux, 1), ih[1]) + s_dd(AX(uy, 0), ih[0]));
-  T syz = 0.5f * (s_dd(AX(uy, 2), ih[2]) + s_dd(AX(uz, 1), ih[1]));
-  T szx = 0.5f * (s_dd(AX(uz, 0), ih[0]) + s_dd(AX(ux, 2), ih[2]));
+  T sxy = 0.5f * (s_dd(AX(ux, 1), n.jd(1, k)) + s_dd(AX(uy, 0), n.jd(0, k)));
+  T syz = 0.5f * (s_dd(AX(uy, 2), n.jd(2, k)) + s_dd(AX(uz, 1), n.jd(1, k)));
+  T szx = 0.5f * (s_dd(AX(uz, 0), n.jd(0, k)) + s_dd(AX(ux, 2), n.jd(2, k)));
   n.st(sxy2, sxy * sxy);
   n.st(syz2, syz * syz);
   n.st(szx2, szx * szx);
@@ -357,11 +415,11 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : 
                                                 const float* __restrict__ sqzx,
                                                 float* __restrict__ nv, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
   T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
-  const T sxx = s_du(AX(ux, 0), k.ih[0]), syy = s_du(AX(uy, 1), k.ih[1]),
-              szz = s_du(AX(uz, 2), k.ih[2]);
+  const T sxx = s_du(AX(ux, 0), n.ju(0, k)), syy = s_du(AX(uy, 1), n.ju(1, k)),
+              szz = s_du(AX(uz, 2), n.ju(2, k));
   T divu = sxx + syy + szz;
   T nu = 0.f;
   if (k.nu1 > 0.f) nu = k.nu1 * sqrtf(ucx * ucx + ucy * ucy + ucz * ucz);
@@ -374,12 +432,14 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : 
     T ca = sqrtf((bcx * bcx + bcy * bcy + bcz * bcz) / r);
     nu += k.nu3 * (cs + ca);
   }
-  if (k.nu2dl > 0.f) nu += k.nu2dl * fmaxf(-divu, 0.f);
+  // dl_min: of the mesh, or of the cell on a stretched z (R19).
+  const float nu2dl = N::ZS ? k.nu2 * n.dlc(k) : k.nu2dl;
+  if (k.nu2dl > 0.f) nu += nu2dl * fmaxf(-divu, 0.f);
   if (SMAG) {
     // eq. (nusmag): dl_min Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2.
     T s2 = ((sxx * sxx + syy * syy) + szz * szz) - divu * divu * (1.f / 3.f);
     s2 += 2.f * ((up2(sqxy, n, 0, 1) + up2(sqyz, n, 1, 2)) + up2(sqzx, n, 2, 0));
-    nu += k.csmag_dl * sqrtf(2.f * fmaxf(s2, 0.f));
+    nu += (N::ZS ? k.csmag * n.dlc(k) : k.csmag_dl) * sqrtf(2.f * fmaxf(s2, 0.f));
   }
   n.st(nv, nu);
 }
@@ -449,7 +509,7 @@ __global__ void STG_LB(N, STG_MINB) k_d2flag(const float* __restrict__ rd,
                                              const float* __restrict__ Ed,
                                              unsigned char* __restrict__ flag, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
   auto lnr = [&](const T& r) { return k.r0pos ? log1pf(r / k.r0) : logf(r); };
   auto lnE = [&](const T& E) { return k.E0 > 0.f ? log1pf(E / k.E0) : logf(E); };
@@ -482,12 +542,11 @@ template <bool D2, class N>
 __device__ __forceinline__ Strain3<typename N::T> strain_diag(
     const N& n, const float* __restrict__ ux, const float* __restrict__ uy,
     const float* __restrict__ uz, unsigned fl, const KPar& k) {
-  const float* ih = k.ih;
-  Strain3<typename N::T> S{s_du(AX(ux, 0), ih[0]), s_du(AX(uy, 1), ih[1]), s_du(AX(uz, 2), ih[2])};
+  Strain3<typename N::T> S{s_du(AX(ux, 0), n.ju(0, k)), s_du(AX(uy, 1), n.ju(1, k)), s_du(AX(uz, 2), n.ju(2, k))};
   if (D2) {
-    S.a = N::sel(fl, 0, s_du2(AX(ux, 0), ih[0]), S.a);
-    S.b = N::sel(fl, 1, s_du2(AX(uy, 1), ih[1]), S.b);
-    S.c = N::sel(fl, 2, s_du2(AX(uz, 2), ih[2]), S.c);
+    S.a = N::sel(fl, 0, s_du2(AX(ux, 0), n.ju(0, k)), S.a);
+    S.b = N::sel(fl, 1, s_du2(AX(uy, 1), n.ju(1, k)), S.b);
+    S.c = N::sel(fl, 2, s_du2(AX(uz, 2), n.ju(2, k)), S.c);
   }
   return S;
 }
@@ -496,13 +555,12 @@ __device__ __forceinline__ Strain3<typename N::T> strain_off(
     const N& n, const float* __restrict__ ux, const float* __restrict__ uy,
     const float* __restrict__ uz, unsigned fl, const KPar& k) {
   using T = typename N::T;
-  const float* ih = k.ih;
   // (d_a1 f1 + d_a2 f2) / 2, one pair at a time.
   auto pair = [&](const float* f1, int a1, const float* f2, int a2) {
-    T d1 = s_dd(AX(f1, a1), ih[a1]), d2 = s_dd(AX(f2, a2), ih[a2]);
+    T d1 = s_dd(AX(f1, a1), n.jd(a1, k)), d2 = s_dd(AX(f2, a2), n.jd(a2, k));
     if (D2) {
-      d1 = N::sel(fl, a1, s_dd2(AX(f1, a1), ih[a1]), d1);
-      d2 = N::sel(fl, a2, s_dd2(AX(f2, a2), ih[a2]), d2);
+      d1 = N::sel(fl, a1, s_dd2(AX(f1, a1), n.jd(a1, k)), d1);
+      d2 = N::sel(fl, a2, s_dd2(AX(f2, a2), n.jd(a2, k)), d2);
     }
     return 0.5f * (d1 + d2);
   };
@@ -527,12 +585,11 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
     float* __restrict__ Rz, float* __restrict__ Jx, float* __restrict__ Jy,
     float* __restrict__ Jz, const unsigned char* __restrict__ flag, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
-  const float* ih = k.ih;
-  T jx = s_dd(AX(bz, 1), ih[1]) - s_dd(AX(by, 2), ih[2]);
-  T jy = s_dd(AX(bx, 2), ih[2]) - s_dd(AX(bz, 0), ih[0]);
-  T jz = s_dd(AX(by, 0), ih[0]) - s_dd(AX(bx, 1), ih[1]);
+  T jx = s_dd(AX(bz, 1), n.jd(1, k)) - s_dd(AX(by, 2), n.jd(2, k));
+  T jy = s_dd(AX(bx, 2), n.jd(2, k)) - s_dd(AX(bz, 0), n.jd(0, k));
+  T jz = s_dd(AX(by, 0), n.jd(0, k)) - s_dd(AX(bx, 1), n.jd(1, k));
   n.st(Jx, jx);
   n.st(Jy, jy);
   n.st(Jz, jz);
@@ -545,14 +602,17 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
   T nuc = k.rm ? n.ld(nu) : 0.f;
   T nxx = k.rm ? k.sp[0] * nuc : k.nu_const;
   T nyy = k.rm ? k.sp[1] * nuc : k.nu_const;
-  T nzz = k.rm ? k.sp[2] * nuc : k.nu_const;
+  T nzz = k.rm ? n.hzc(k) * nuc : k.nu_const;
   n.st(txx, (r * nxx) * (sxx + k.c1 * divu));
   n.st(tyy, (r * nyy) * (syy + k.c1 * divu));
   n.st(tzz, (r * nzz) * (szz + k.c1 * divu));
   // Edge values: the second interpolation of the face values (Ex edge from
   // the y faces along z, Ey from the z faces along x, Ez from the x faces along y).
-  T nyz = k.rm ? k.spp[0] * expf(s_dn(AX(lny, 2))) : k.nu_const;
-  T nzx = k.rm ? k.spp[1] * expf(s_dn(AX(lnz, 0))) : k.nu_const;
+  // The Ex and Ey edges sit on z faces (their z length at the face, R19).
+  const float spp0 = N::ZS ? fmaxf(k.sp[1], n.hzf(k)) : k.spp[0];
+  const float spp1 = N::ZS ? fmaxf(n.hzf(k), k.sp[0]) : k.spp[1];
+  T nyz = k.rm ? spp0 * expf(s_dn(AX(lny, 2))) : k.nu_const;
+  T nzx = k.rm ? spp1 * expf(s_dn(AX(lnz, 0))) : k.nu_const;
   T nxy = k.rm ? k.spp[2] * expf(s_dn(AX(lnx, 1))) : k.nu_const;
   T ryz = dens(s_dn(AX(lfy, 2)), k), rzx = dens(s_dn(AX(lfz, 0)), k),
         rxy = dens(s_dn(AX(lfx, 1)), k);
@@ -611,7 +671,7 @@ __global__ void STG_LB(N, STG_MINB_HI) k_edge(
     float* __restrict__ wc, float* __restrict__ wx, float* __restrict__ wy,
     float* __restrict__ wz, const unsigned char* __restrict__ flag, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
   T txx_, tyy_, tzz_, txy_, tyz_, tzx_, rx_, ry_, rz_;
   if (k.do_quench) {
@@ -738,15 +798,16 @@ __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const Fl
       };
       auto rn_at = [&](int o) {
         const T r = n.lda(rd, d, o) + k.r0;
-        return r * (k.rm ? k.sp[d] * n.lda(in.nu, d, o) : T(k.nu_const));
+        const float sp = (N::ZS && d == 2) ? n.hzc_at(o, k) : k.sp[d];
+        return r * (k.rm ? sp * n.lda(in.nu, d, o) : T(k.nu_const));
       };
-      v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, k.ih[d]));
+      v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, n.jd(d, k)));
     }
     n.st(go[d], v);
   }
   // -P div u + Q, Q = w_c + up up of the edge heating densities.
-  T divu = (s_du(AX(in.ux, 0), k.ih[0]) + s_du(AX(in.uy, 1), k.ih[1])) +
-               s_du(AX(in.uz, 2), k.ih[2]);
+  T divu = (s_du(AX(in.ux, 0), n.ju(0, k)) + s_du(AX(in.uy, 1), n.ju(1, k))) +
+               s_du(AX(in.uz, 2), n.ju(2, k));
   T P = k.gm1 * (n.ld(Ed) + k.E0);
   T qt = -P * divu;
   if (k.visc) {
@@ -770,7 +831,7 @@ __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const Fl
 template <class N>
 __global__ void STG_LB_HI(N, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   flux_cell(n, in, out, k);
 }
 
@@ -795,9 +856,8 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
                                           float alpha, float beta, const double* dtp,
                                           int mode, KPar k, Geo g) {
   N n;
-  if (!n.init(g)) return;
+  if (!n.init(g, k)) return;
   using T = typename N::T;
-  const float* ih = k.ih;
   float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
   float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
   const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
@@ -807,41 +867,41 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
     if (mode) n.st(os[c], n.ld(in.f[c]) + bdt * qq);
   };
   if (M & 1)   // eq. (mass)
-    fin(0, -((s_du(AX(in.px, 0), ih[0]) + s_du(AX(in.py, 1), ih[1])) + s_du(AX(in.pz, 2), ih[2])));
+    fin(0, -((s_du(AX(in.px, 0), n.ju(0, k)) + s_du(AX(in.py, 1), n.ju(1, k))) + s_du(AX(in.pz, 2), n.ju(2, k))));
   if (M & 2) {   // eq. (mom), x
-    T t = -s_dd(AX(in.mxx, 0), ih[0]);
-    t -= s_du(AX(in.mxy, 1), ih[1]);
-    t -= s_du(AX(in.mxz, 2), ih[2]);
+    T t = -s_dd(AX(in.mxx, 0), n.jd(0, k));
+    t -= s_du(AX(in.mxy, 1), n.ju(1, k));
+    t -= s_du(AX(in.mxz, 2), n.ju(2, k));
     t += s_up(AX(in.lx1, 2));
     t -= s_up(AX(in.lx2, 1));
     if (k.g[0] != 0.f) t += dens(s_dn(AX(in.ls, 0)), k) * k.g[0];
     fin(1, t);
   }
   if (M & 4) {   // eq. (mom), y
-    T t = -s_du(AX(in.myx, 0), ih[0]);
-    t -= s_dd(AX(in.myy, 1), ih[1]);
-    t -= s_du(AX(in.myz, 2), ih[2]);
+    T t = -s_du(AX(in.myx, 0), n.ju(0, k));
+    t -= s_dd(AX(in.myy, 1), n.jd(1, k));
+    t -= s_du(AX(in.myz, 2), n.ju(2, k));
     t += s_up(AX(in.ly1, 0));
     t -= s_up(AX(in.ly2, 2));
     if (k.g[1] != 0.f) t += dens(s_dn(AX(in.ls, 1)), k) * k.g[1];
     fin(2, t);
   }
   if (M & 8) {   // eq. (mom), z
-    T t = -s_du(AX(in.mzx, 0), ih[0]);
-    t -= s_du(AX(in.mzy, 1), ih[1]);
-    t -= s_dd(AX(in.mzz, 2), ih[2]);
+    T t = -s_du(AX(in.mzx, 0), n.ju(0, k));
+    t -= s_du(AX(in.mzy, 1), n.ju(1, k));
+    t -= s_dd(AX(in.mzz, 2), n.jd(2, k));
     t += s_up(AX(in.lz1, 1));
     t -= s_up(AX(in.lz2, 0));
     if (k.g[2] != 0.f) t += dens(s_dn(AX(in.ls, 2)), k) * k.g[2];
     fin(3, t);
   }
   if (M & 16)   // eq. (ien)
-    fin(4, -((s_du(AX(in.gx, 0), ih[0]) + s_du(AX(in.gy, 1), ih[1])) + s_du(AX(in.gz, 2), ih[2])) +
+    fin(4, -((s_du(AX(in.gx, 0), n.ju(0, k)) + s_du(AX(in.gy, 1), n.ju(1, k))) + s_du(AX(in.gz, 2), n.ju(2, k))) +
                n.ld(in.qt));
   // eq. (indu): dB/dt = -curl E
-  if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), ih[1]) - s_du(AX(in.Ey, 2), ih[2])));
-  if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), ih[2]) - s_du(AX(in.Ez, 0), ih[0])));
-  if (M & 128) fin(7, -(s_du(AX(in.Ey, 0), ih[0]) - s_du(AX(in.Ex, 1), ih[1])));
+  if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k))));
+  if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), n.ju(2, k)) - s_du(AX(in.Ez, 0), n.ju(0, k))));
+  if (M & 128) fin(7, -(s_du(AX(in.Ey, 0), n.ju(0, k)) - s_du(AX(in.Ex, 1), n.ju(1, k))));
 }
 
 __global__ void k_set_dt(double* dtp, double dt) { dtp[0] = dt; }
@@ -911,7 +971,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? STG_MINB : STG_MINB_
   __shared__ unsigned sm[3][BX * BY * BZ / 32];
   N n;
   unsigned m[3] = {0u, 0u, 0u};
-  if (n.init(g)) {
+  if (n.init(g, k)) {
     T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
     T bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
       bcz = s_up(AX(bz, 2)) + k.Bref[2];
@@ -924,9 +984,19 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? STG_MINB : STG_MINB_
     T ub = ucx * bcx + ucy * bcy + ucz * bcz;
     T w = cs + ca + sqrtf(fmaxf(uperp2(u2, ub, B2), T(0.f)));
     T rate = fmaxf(fabsf(n.ld(qr)) / r, fabsf(n.ld(qE)) / E);
-    m[0] = max_bits(w);
-    m[1] = max_bits(rate);
-    if (k.visc) m[2] = max_bits(k.rm ? n.ld(nu) : T(k.nu_const));
+    if (N::ZS) {
+      // Stretched z (R19): the limits are minima over cells of the local
+      // values, so reduce w / dl and nu / dl (nu_const / dl^2) with dl the
+      // cell's smallest size; the final pass then takes dl = 1.
+      const float idl = 1.f / n.dlc(k);
+      m[0] = max_bits(w * idl);
+      m[1] = max_bits(rate);
+      if (k.visc) m[2] = max_bits(k.rm ? n.ld(nu) * idl : T(k.nu_const * idl * idl));
+    } else {
+      m[0] = max_bits(w);
+      m[1] = max_bits(rate);
+      if (k.visc) m[2] = max_bits(k.rm ? n.ld(nu) : T(k.nu_const));
+    }
   }
   const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
 #pragma unroll
@@ -966,26 +1036,32 @@ __global__ void k_courant_final(unsigned* cmax, double* dt_out, double cdt, doub
 // ---------------------------------------------------------- diagnostics ----
 // Per-block FP64 partials: sum r', px', py', pz', E', kinetic, magnetic,
 // max |div B|, sum (div B)^2, non-finite count.
+// On a stretched z (R19) every term is weighted by its cell's z size over the
+// mean one (the face spacing for the z-face quantities pz, Bz and their
+// energies), the totals the discrete equations conserve.
+template <class N>
 __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
     const float* __restrict__ rd, const float* __restrict__ px, const float* __restrict__ py,
     const float* __restrict__ pz, const float* __restrict__ Ed, const float* __restrict__ bx,
     const float* __restrict__ by, const float* __restrict__ bz, double* part, KPar k, Geo g) {
   __shared__ double sm[10][BX * BY * BZ];
-  Nb n;
+  N n;
   double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
-  if (make_nb(n, g)) {
+  if (n.init(g, k)) {
+    const double wc = N::ZS ? (double)n.hzc(k) * k.izbar : 1.0;
+    const double wf = N::ZS ? (double)n.hzf(k) * k.izbar : 1.0;
     const float* pr[3] = {px, py, pz};
     const float* bb[3] = {bx, by, bz};
     float vals[8] = {LDG(rd, n.c), LDG(px, n.c), LDG(py, n.c), LDG(pz, n.c),
                      LDG(Ed, n.c), LDG(bx, n.c), LDG(by, n.c), LDG(bz, n.c)};
     int bad = 0;
     for (int c = 0; c < 8; ++c) bad += isfinite(vals[c]) ? 0 : 1;
-    v[0] = vals[0];
-    v[1] = vals[1];
-    v[2] = vals[2];
-    v[3] = vals[3];
-    v[4] = vals[4];
+    v[0] = vals[0] * wc;
+    v[1] = vals[1] * wc;
+    v[2] = vals[2] * wc;
+    v[3] = vals[3] * wf;
+    v[4] = vals[4] * wc;
     double kin = 0, mag = 0, divb = 0;
     for (int d = 0; d < 3; ++d) {
       auto lsv = [&](int o) {
@@ -995,11 +1071,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
       };
       double rf = (double)dens(s_dn(lsv), k);
       double p = (double)LDG(pr[d], n.c) + k.pref[d];
-      kin += 0.5 * p * p / rf;
+      const double w = d == 2 ? wf : wc;
+      kin += 0.5 * p * p / rf * w;
       double b = (double)LDG(bb[d], n.c) + k.Bref[d];
-      mag += 0.5 * b * b;
+      mag += 0.5 * b * b * w;
       const float* bp = bb[d];
-      divb += (double)s_du(AX(bp, d), k.ih[d]);
+      divb += (double)s_du(AX(bp, d), n.ju(d, k));
     }
     v[5] = kin;
     v[6] = mag;

@@ -42,7 +42,7 @@ __device__ __forceinline__ T stencil_at(const T* f, long long idx, int axis, int
 }
 
 template <typename T>
-__global__ void g_forward(GNode nd, const T* A, const T* B, T* out, Geo g) {
+__global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mesh, Geo g) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.n) return;
   T r;
@@ -63,6 +63,7 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, Geo g) {
     case G_CLAMPMIN: r = A[idx] < (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_CLAMPMAX: r = A[idx] > (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_STEP: r = A[idx] > (T)nd.c0 ? (T)1 : (T)0; break;
+    case G_ZFIELD: r = mesh[(long long)nd.sk * g.nz + idx / g.sz]; break;
     default: r = (T)nd.c0; break;  // G_CONST
   }
   out[idx] = r;
@@ -126,7 +127,7 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
     case G_AXPB: gA[idx] += (T)nd.c0 * gg; break;
     case G_CLAMPMIN: if (A[idx] >= (T)nd.c0) gA[idx] += gg; break;
     case G_CLAMPMAX: if (A[idx] <= (T)nd.c0) gA[idx] += gg; break;
-    default: break;   // G_STEP (piecewise constant), G_CONST, G_INPUT
+    default: break;   // G_STEP (piecewise constant), G_ZFIELD, G_CONST, G_INPUT
   }
 }
 
@@ -145,15 +146,50 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   const int X = 0, Y = 1, Z = 2;
   const double h[3] = {gr.dx, gr.dy, gr.dz};
   const int nn[3] = {gr.nx, gr.ny, gr.nz};
+  // A stretched z (R19): the mesh's dl_min takes its smallest z cell; z
+  // derivatives are index-space stencils times 1/dz at the output (centre
+  // after ddup, face after dddn); lengths and dl_min are local there.
+  const bool zs = p.zc != nullptr;
+  double zcmin = 1e300, dlxy = 1e300;
+  for (int k = 0; zs && k < gr.nz; ++k) zcmin = std::min(zcmin, p.zc[k]);
   double dlmin = 1e300, any = 0;
   for (int a = 0; a < 3; ++a)
-    if (nn[a] > 1) { dlmin = std::min(dlmin, h[a]); any = 1; }
+    if (nn[a] > 1) {
+      dlmin = std::min(dlmin, (a == 2 && zs) ? zcmin : h[a]);
+      if (a < 2) dlxy = std::min(dlxy, h[a]);
+      any = 1;
+    }
   if (!any) dlmin = std::min(h[0], std::min(h[1], h[2]));
   double sp[3];
   for (int a = 0; a < 3; ++a) sp[a] = nn[a] > 1 ? h[a] : dlmin;
-
-  auto ddup = [&](int a, int ax) { return G.st(ST_DDUP, a, ax, h[ax]); };
-  auto dddn = [&](int a, int ax) { return G.st(ST_DDDN, a, ax, h[ax]); };
+  G.mesh.clear();
+  int JC = -1, JF = -1, HC = -1, HF = -1, DLC = -1;
+  if (zs) {
+    const int nz = gr.nz;
+    G.mesh.resize((size_t)5 * nz);
+    for (int k = 0; k < nz; ++k) {
+      G.mesh[k] = 1.0 / p.zc[k];
+      G.mesh[nz + k] = 1.0 / p.zf[k];
+      G.mesh[2 * nz + k] = p.zc[k];
+      G.mesh[3 * nz + k] = p.zf[k];
+      G.mesh[4 * nz + k] = std::min(dlxy, p.zc[k]);
+    }
+    JC = G.zfield(0);
+    JF = G.zfield(1);
+    HC = G.zfield(2);
+    HF = G.zfield(3);
+    DLC = G.zfield(4);
+  }
+  auto ddup = [&](int a, int ax) {
+    return (zs && ax == 2) ? G.mul(G.st(ST_DDUP, a, ax, 1.0), JC) : G.st(ST_DDUP, a, ax, h[ax]);
+  };
+  auto dddn = [&](int a, int ax) {
+    return (zs && ax == 2) ? G.mul(G.st(ST_DDDN, a, ax, 1.0), JF) : G.st(ST_DDDN, a, ax, h[ax]);
+  };
+  // x * (local dl_min) and x * c * length: a constant on a uniform mesh.
+  auto times_dl = [&](int a, double c) {
+    return zs ? G.mul(G.axpb(a, c, 0.0), DLC) : G.axpb(a, c * dlmin, 0.0);
+  };
   auto up = [&](int a, int ax) { return G.up(a, ax); };
   auto dn = [&](int a, int ax) { return G.dn(a, ax); };
   auto full = [&](int a, double ref) { return ref != 0.0 ? G.axpb(a, 1.0, ref) : a; };
@@ -224,7 +260,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
         int ca = G.sq(G.div(B2, r));
         acc(G.axpb(G.add(cs, ca), p.nu3, 0.0));
       }
-      if (p.nu2 > 0) acc(G.axpb(G.cmin(neg(divu), 0.0), p.nu2 * dlmin, 0.0));
+      if (p.nu2 > 0) acc(times_dl(G.cmin(neg(divu), 0.0), p.nu2));
       if (p.csmag > 0) {
         // eq. (nusmag): dl_min Csmag [2 (S_ii^2 - (div u)^2/3 + S_ij^2, i != j)]^1/2.
         int sxx = ddup(u[X], X), syy = ddup(u[Y], Y), szz = ddup(u[Z], Z);
@@ -236,7 +272,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
         int offd = G.add(G.add(up(up(G.mul(sxy, sxy), X), Y), up(up(G.mul(syz, syz), Y), Z)),
                          up(up(G.mul(szx, szx), Z), X));
         int s2 = G.add(dia, G.axpb(offd, 2.0, 0.0));
-        acc(G.axpb(G.sq(G.axpb(G.cmin(s2, 0.0), 2.0, 0.0)), p.csmag * dlmin, 0.0));
+        acc(times_dl(G.sq(G.axpb(G.cmin(s2, 0.0), 2.0, 0.0)), p.csmag));
       }
       // <nu>_{max smooth}: 3-cell max along x, y, z, then 3-cell mean.
       for (int ax = 0; ax < 3; ++ax) nu = G.maxi(G.maxi(G.shift(nu, ax, -1), nu), G.shift(nu, ax, 1));
@@ -245,10 +281,16 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
       int lnu = G.lg(G.cmin(nu, 1e-30));
       nxx = G.axpb(nu, sp[X], 0.0);
       nyy = G.axpb(nu, sp[Y], 0.0);
-      nzz = G.axpb(nu, sp[Z], 0.0);
       nxy = G.axpb(G.ex(dn(dn(lnu, X), Y)), std::max(sp[X], sp[Y]), 0.0);
-      nyz = G.axpb(G.ex(dn(dn(lnu, Y), Z)), std::max(sp[Y], sp[Z]), 0.0);
-      nzx = G.axpb(G.ex(dn(dn(lnu, Z), X)), std::max(sp[Z], sp[X]), 0.0);
+      if (zs) {   // z length at the centre; the Ex, Ey edges sit on z faces
+        nzz = G.mul(nu, HC);
+        nyz = G.mul(G.ex(dn(dn(lnu, Y), Z)), G.maxi(G.cnst(sp[Y]), HF));
+        nzx = G.mul(G.ex(dn(dn(lnu, Z), X)), G.maxi(HF, G.cnst(sp[X])));
+      } else {
+        nzz = G.axpb(nu, sp[Z], 0.0);
+        nyz = G.axpb(G.ex(dn(dn(lnu, Y), Z)), std::max(sp[Y], sp[Z]), 0.0);
+        nzx = G.axpb(G.ex(dn(dn(lnu, Z), X)), std::max(sp[Z], sp[X]), 0.0);
+      }
     }
     int rxy = dens(dn(dn(lsrc, X), Y));
     int ryz = dens(dn(dn(lsrc, Y), Z));
@@ -269,13 +311,15 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     auto sdup = [&](int f, int ax) {
       int d6 = ddup(f, ax);
       if (!p.do_2nddiv) return d6;
-      int d2 = G.axpb(G.sub(G.shift(f, ax, 1), f), 1.0 / h[ax], 0.0);
+      int df = G.sub(G.shift(f, ax, 1), f);
+      int d2 = (zs && ax == 2) ? G.mul(df, JC) : G.axpb(df, 1.0 / h[ax], 0.0);
       return G.add(d6, G.mul(flag[ax], G.sub(d2, d6)));
     };
     auto sddn = [&](int f, int ax) {
       int d6 = dddn(f, ax);
       if (!p.do_2nddiv) return d6;
-      int d2 = G.axpb(G.sub(f, G.shift(f, ax, -1)), 1.0 / h[ax], 0.0);
+      int df = G.sub(f, G.shift(f, ax, -1));
+      int d2 = (zs && ax == 2) ? G.mul(df, JF) : G.axpb(df, 1.0 / h[ax], 0.0);
       return G.add(d6, G.mul(flag[ax], G.sub(d2, d6)));
     };
     int Sxx = sdup(u[X], X), Syy = sdup(u[Y], Y), Szz = sdup(u[Z], Z);
@@ -417,6 +461,18 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
   for (auto& nd : def.nodes)
     if (nd.op != G_INPUT) ++nval;
   if (cudaMalloc(&vals, sizeof(T) * nval * g.n) != cudaSuccess) { vals = nullptr; return STAGGER_EOOM; }
+  if (!def.mesh.empty()) {
+    std::vector<T> m(def.mesh.begin(), def.mesh.end());
+    if (cudaMalloc(&mesh, sizeof(T) * m.size()) != cudaSuccess) {
+      mesh = nullptr;
+      release();
+      return STAGGER_EOOM;
+    }
+    if (cudaMemcpy(mesh, m.data(), sizeof(T) * m.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      release();
+      return STAGGER_ECUDA;
+    }
+  }
   if (with_grads) {
     if (cudaMalloc(&grads, sizeof(T) * nn * g.n) != cudaSuccess) {
       grads = nullptr;
@@ -435,7 +491,8 @@ template <typename T>
 void GraphExec<T>::release() {
   if (vals) cudaFree(vals);
   if (grads) cudaFree(grads);
-  vals = grads = nullptr;
+  if (mesh) cudaFree(mesh);
+  vals = grads = mesh = nullptr;
   ptr.clear();
 }
 
@@ -451,7 +508,7 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
     if (nd.op == G_INPUT) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
-    g_forward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], geo);
+    g_forward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], mesh, geo);
     ++launches;
   }
   STG_CUDA_OK(cudaGetLastError());
@@ -470,7 +527,7 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   }
   for (long long i = (long long)nn - 1; i >= 0; --i) {
     const GNode& nd = def.nodes[i];
-    if (nd.op == G_INPUT || nd.op == G_CONST) continue;
+    if (nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;

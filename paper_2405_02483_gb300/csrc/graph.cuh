@@ -14,7 +14,8 @@ namespace stg {
 enum GOp {
   G_INPUT = 0, G_STENCIL, G_SHIFT, G_ADD, G_SUB, G_MUL, G_DIV, G_MAX,
   G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST,
-  G_STEP   // 1 where a > c0, else 0 (a switch: no gradient)
+  G_STEP,  // 1 where a > c0, else 0 (a switch: no gradient)
+  G_ZFIELD // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -57,6 +58,9 @@ struct GraphDef {
   int cmax(int a, double c) { return push(G_CLAMPMAX, a, -1, 0, 0, c, 0); }
   int cnst(double c) { return push(G_CONST, -1, -1, 0, 0, c, 0); }
   int stepf(int a, double c) { return push(G_STEP, a, -1, 0, 0, c, 0); }
+  int zfield(int which) { return push(G_ZFIELD, -1, -1, 2, which, 0, 0); }
+  // Stretched z mesh: the five arrays of G_ZFIELD, nz values each (empty when uniform).
+  std::vector<double> mesh;
 };
 
 // Build the right-hand-side graph for a grid and parameter set.
@@ -69,6 +73,7 @@ struct GraphExec {
   GraphDef def;
   Geo geo;
   T* vals = nullptr;     // node values (non-input nodes)
+  T* mesh = nullptr;     // the mesh arrays of G_ZFIELD on the device, or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
   long long launches = 0;

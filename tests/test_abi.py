@@ -57,6 +57,30 @@ def test_create_rejects_bad_arguments_without_gpu(S):
     assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(p), None) == S.EINVAL
 
 
+def test_mesh_and_switch_parameters_are_validated_without_gpu(S):
+    h = ctypes.c_void_p()
+    g = S.Grid(8, 8, 6, 0.1, 0.1, 0.1)
+    good = [0.1] * 6
+    cases = [dict(zc=good),                                  # zf missing
+             dict(zc=good, zf=good[:5] + [0.0]),             # a non-positive spacing
+             dict(zc=good[:5] + [float("nan")], zf=good),    # not finite
+             dict(do_2nddiv=2), dict(do_2nddiv=1, d2lnr_lim=float("inf")),
+             dict(scalar_cells=2)]
+    for kw in cases:
+        q = S.default_params(**kw)
+        assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL, kw
+    g1 = S.Grid(8, 8, 1, 0.1, 0.1, 0.1)                      # a stretched z needs nz > 1
+    q = S.default_params(zc=[0.1], zf=[0.1])
+    assert S.lib.stagger_create(ctypes.byref(g1), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL
+    # The allocation-free diagnostics cannot hold a mesh on the device.
+    q = S.default_params(zc=good, zf=good)
+    fake = S.P8F(*[ctypes.cast(ctypes.c_void_p(16 * (i + 1)), ctypes.POINTER(ctypes.c_float))
+                   for i in range(8)])
+    out = (ctypes.c_double * 10)()
+    assert S.lib.stagger_diagnostics_noalloc(ctypes.byref(g), ctypes.byref(q), fake, out,
+                                             None) == S.EUNSUPPORTED
+
+
 def test_null_context_calls_are_rejected(S):
     nul = S.P8F()
     assert S.lib.stagger_rhs(None, nul, nul, None) == S.EINVAL
