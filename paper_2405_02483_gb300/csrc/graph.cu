@@ -9,30 +9,45 @@
 namespace stg {
 
 // ---------------------------------------------------------------------------
-// Periodic neighbour along an axis (index of cell idx shifted by o).
+// A cell of a graph launch: 3-D grid of GB x GBY x GBZ thread blocks, so the
+// cell's (i, j, k) come from the launch and a periodic neighbour needs no
+// division.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long nbr(long long idx, int axis, int o, const Geo& g) {
-  if (axis == 0) {
-    int i = (int)(idx % g.nx);
-    return idx - i + wrap(i + o, g.nx);
-  } else if (axis == 1) {
-    int j = (int)((idx / g.sy) % g.ny);
-    return idx + (long long)(wrap(j + o, g.ny) - j) * g.sy;
-  }
-  int k = (int)(idx / g.sz);
-  return idx + (long long)(wrap(k + o, g.nz) - k) * g.sz;
+#define GBX 32
+#define GBY 2
+#define GBZ 4
+
+struct GCell {
+  int i, j, k;
+  long long idx;
+};
+
+__device__ __forceinline__ bool gcell(GCell& c, const Geo& g) {
+  c.i = blockIdx.x * blockDim.x + threadIdx.x;
+  c.j = blockIdx.y * blockDim.y + threadIdx.y;
+  c.k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (c.i >= g.nx || c.j >= g.ny || c.k >= g.nz) return false;
+  c.idx = (long long)c.k * g.sz + (long long)c.j * g.sy + c.i;
+  return true;
 }
 
-// Stencil value at idx: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
+// Periodic neighbour of cell c along an axis (shifted by o).
+__device__ __forceinline__ long long nbr(const GCell& c, int axis, int o, const Geo& g) {
+  if (axis == 0) return c.idx + (wrap(c.i + o, g.nx) - c.i);
+  if (axis == 1) return c.idx + (long long)(wrap(c.j + o, g.ny) - c.j) * g.sy;
+  return c.idx + (long long)(wrap(c.k + o, g.nz) - c.k) * g.sz;
+}
+
+// Stencil value at c: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
 // are eq. (deriv) to i+1/2 and i-1/2, divided by the spacing h.
 template <typename T>
-__device__ __forceinline__ T stencil_at(const T* f, long long idx, int axis, int kind, T h,
+__device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, int kind, T h,
                                         const Geo& g) {
   const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
   const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
-  T m3 = f[nbr(idx, axis, -3, g)], m2 = f[nbr(idx, axis, -2, g)], m1 = f[nbr(idx, axis, -1, g)];
-  T z0 = f[idx], p1 = f[nbr(idx, axis, 1, g)], p2 = f[nbr(idx, axis, 2, g)],
-    p3 = f[nbr(idx, axis, 3, g)];
+  T m3 = f[nbr(c, axis, -3, g)], m2 = f[nbr(c, axis, -2, g)], m1 = f[nbr(c, axis, -1, g)];
+  T z0 = f[c.idx], p1 = f[nbr(c, axis, 1, g)], p2 = f[nbr(c, axis, 2, g)],
+    p3 = f[nbr(c, axis, 3, g)];
   switch (kind) {
     case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
     case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
@@ -43,12 +58,13 @@ __device__ __forceinline__ T stencil_at(const T* f, long long idx, int axis, int
 
 template <typename T>
 __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mesh, Geo g) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.n) return;
+  GCell c;
+  if (!gcell(c, g)) return;
+  const long long idx = c.idx;
   T r;
   switch (nd.op) {
-    case G_STENCIL: r = stencil_at(A, idx, nd.axis, nd.sk, (T)nd.c0, g); break;
-    case G_SHIFT: r = A[nbr(idx, nd.axis, nd.sk, g)]; break;
+    case G_STENCIL: r = stencil_at(A, c, nd.axis, nd.sk, (T)nd.c0, g); break;
+    case G_SHIFT: r = A[nbr(c, nd.axis, nd.sk, g)]; break;
     case G_ADD: r = A[idx] + B[idx]; break;
     case G_SUB: r = A[idx] - B[idx]; break;
     case G_MUL: r = A[idx] * B[idx]; break;
@@ -63,7 +79,7 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mes
     case G_CLAMPMIN: r = A[idx] < (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_CLAMPMAX: r = A[idx] > (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_STEP: r = A[idx] > (T)nd.c0 ? (T)1 : (T)0; break;
-    case G_ZFIELD: r = mesh[(long long)nd.sk * g.nz + idx / g.sz]; break;
+    case G_ZFIELD: r = mesh[(long long)nd.sk * g.nz + c.k]; break;
     default: r = (T)nd.c0; break;  // G_CONST
   }
   out[idx] = r;
@@ -75,20 +91,21 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mes
 template <typename T>
 __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const T* gout,
                            T* gA, T* gB, Geo g) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.n) return;
+  GCell c;
+  if (!gcell(c, g)) return;
+  const long long idx = c.idx;
   if (nd.op == G_STENCIL) {
     // Gather form of the transpose: up^T = dn, dn^T = up, ddup^T = -dddn,
     // dddn^T = -ddup (periodic summation by parts).
     int kind = nd.sk;
     int tk = kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
-    T v = stencil_at(gout, idx, nd.axis, tk, (T)nd.c0, g);
+    T v = stencil_at(gout, c, nd.axis, tk, (T)nd.c0, g);
     if (kind == ST_DDUP || kind == ST_DDDN) v = -v;
     gA[idx] += v;
     return;
   }
   if (nd.op == G_SHIFT) {
-    gA[idx] += gout[nbr(idx, nd.axis, -nd.sk, g)];
+    gA[idx] += gout[nbr(c, nd.axis, -nd.sk, g)];
     return;
   }
   T gg = gout[idx];
@@ -497,18 +514,22 @@ void GraphExec<T>::release() {
 }
 
 static inline unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+static inline dim3 ggrid(const Geo& g) {
+  return dim3((unsigned)((g.nx + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),
+              (unsigned)((g.nz + GBZ - 1) / GBZ));
+}
 
 template <typename T>
 int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
   for (size_t i = 0; i < def.nodes.size(); ++i)
     if (def.nodes[i].op == G_INPUT) ptr[i] = in[def.nodes[i].sk];
-  const int bs = 256;
+  const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
   for (size_t i = 0; i < def.nodes.size(); ++i) {
     const GNode& nd = def.nodes[i];
     if (nd.op == G_INPUT) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
-    g_forward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], mesh, geo);
+    g_forward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], mesh, geo);
     ++launches;
   }
   STG_CUDA_OK(cudaGetLastError());
@@ -521,6 +542,7 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   const size_t nn = def.nodes.size();
   STG_CUDA_OK(cudaMemsetAsync(grads, 0, sizeof(T) * nn * geo.n, s));
   const int bs = 256;
+  const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
   for (int k = 0; k < 8; ++k) {
     g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(grads + (size_t)def.out[k] * geo.n, seed[k], geo.n);
     ++launches;
@@ -532,8 +554,7 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
     T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
-    g_backward<T><<<nblocks(geo.n, bs), bs, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n,
-                                                     gA, gB, geo);
+    g_backward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA, gB, geo);
     ++launches;
   }
   for (int k = 0; k < 8; ++k) {
