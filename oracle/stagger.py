@@ -39,6 +39,12 @@ path by specification only, never by code):
       a in the strain of eq. (itv), in its c1 div u term and in the viscous
       heating built from that strain is then the two-point difference
       (f(i+1) - f(i))/h or (f(i) - f(i-1))/h instead of eq. (deriv);
+  R20 chromospheric cooling, eq. (ChromoCool): <e> is the mean of e over the
+      horizontal plane (constant z, the vertical axis here) of the cell, of
+      the state the right-hand side is evaluated on; rho_bot a parameter;
+  R21 coronal thin cooling, eq. (CoronaCool): an energy loss with
+      T = Tunit (gamma - 1) e (the paper's T ~ (gamma - 1) e, scaled to kelvin)
+      and a prefactor L0 in code units supplied by the caller;
   R19 a stretched vertical mesh (Sect. "Derivatives", the mesh file of
       Sect. "Input and output"): z-derivatives are the index-space stencils
       divided by dz/dk at the centre of the derivative (the cell centre after
@@ -191,6 +197,10 @@ class Params:
     csmag: float = 0.0       # Smagorinsky constant, eq. (nusmag) (0: off)
     do_2nddiv: bool = False  # second-order stress derivatives where ln rho, ln e kink (R18)
     d2lnr_lim: float = 0.3
+    t_chromo: float = 0.0    # chromospheric cooling time, eq. (ChromoCool) (0: off), R20
+    rho_bot: float = 1.0
+    cor_L0: float = 0.0      # coronal thin cooling prefactor in code units (0: off), R21
+    cor_Tunit: float = 1.0   # kelvin per code unit of (gamma - 1) e
 
     def visc_on(self):
         return (self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
@@ -480,6 +490,17 @@ def rhs_parts(f, g: Grid, p: Params):
             x2 = (r / p.rho_cool) ** 2
             qn = qn * ((x2 if p.cool_cut == 1 else 1.0) / (1.0 + x2))
         d_E = d_E + qn
+    if p.t_chromo > 0:
+        # eq. (ChromoCool), reading R20: -rho (rho/rho_bot)^(5/3) (e - <e>)/t_cool,
+        # <e> the mean of e over the horizontal plane (constant z) of the cell.
+        emean = e.mean(dim=(1, 2), keepdim=True)
+        d_E = d_E - r * (r / p.rho_bot) ** (5.0 / 3.0) * (e - emean) / p.t_chromo
+    if p.cor_L0 > 0:
+        # eq. (CoronaCool), reading R21: the loss L0 T^(-1/2) rho^2 exp(-(T/10^4 K)^2)
+        # with T = Tunit (gamma - 1) e in kelvin; L0 carries the paper's constant,
+        # the atomic mass and the code units.
+        T = p.cor_Tunit * (p.gamma - 1.0) * e
+        d_E = d_E - p.cor_L0 * r * r * torch.exp(-(T / 1e4) ** 2) / torch.sqrt(T)
 
     # eq. (indu): dB/dt = -curl E.
     d_Bx = -(ddup(Ez, "y", hy) - ddup(Ey, "z", hz))

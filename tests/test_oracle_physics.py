@@ -860,3 +860,51 @@ def test_stretched_conservation_divb_and_courant():
     dt, (tw, tr, td) = S.courant_dt(u, q, g, Params())
     cs = math.sqrt(5.0 / 3.0 * (2.0 / 3.0) * 0.9)
     assert abs(tw - 0.4 * min(g.zc) / cs) < 1e-14
+
+
+# ------------------- chromospheric and coronal cooling (R20, R21) -------------
+
+def _cool_state(nx=12, ny=6, nz=5, a=0.05, rho=1.3):
+    g = Grid(nx, ny, nz, 1.0 / nx, 0.2, 0.3)
+    shape = (nz, ny, nx)
+    xc = ((torch.arange(nx, dtype=DT) + 0.5) / nx).reshape(1, 1, nx).expand(shape)
+    zc = torch.arange(nz, dtype=DT).reshape(nz, 1, 1).expand(shape)
+    one = torch.ones(shape, dtype=DT)
+    e = 0.9 + 0.1 * zc + a * torch.cos(2 * math.pi * xc)     # plane mean 0.9 + 0.1 z
+    return g, xc, [rho * one, 0 * one, 0 * one, 0 * one, rho * e, 0 * one, 0 * one, 0 * one]
+
+
+def test_chromospheric_cooling_closed_form():
+    # e = e0(z) + a cos(2 pi x): the plane mean is e0(z), so the loss is
+    # rho (rho/rho_bot)^(5/3) a cos(2 pi x) / t_cool; rho = 1.3, rho_bot = 0.65,
+    # so rho (rho/rho_bot)^(5/3) = 1.3 * 2^(5/3) = 4.127...
+    t, a = 0.2, 0.05
+    g, xc, f = _cool_state(a=a)
+    F0 = S.rhs(f, g, Params())
+    F1 = S.rhs(f, g, Params(t_chromo=t, rho_bot=0.65))
+    expect = -1.3 * 3.1748021039363987 * a * torch.cos(2 * math.pi * xc) / t
+    assert torch.allclose(F1[4] - F0[4], expect, rtol=1e-12, atol=1e-12)
+    # A purely vertical profile of e is not cooled.
+    g, xc, f = _cool_state(a=0.0)
+    assert float((S.rhs(f, g, Params(t_chromo=t))[4] - S.rhs(f, g, Params())[4]).abs().max()) < 1e-13
+
+
+def test_coronal_cooling_values():
+    # T = Tunit (gamma - 1) e; with Tunit (gamma-1) e = 10^4 K the loss is
+    # L0 rho^2 e^-1 / 100, and at 2 10^4 K it is L0 rho^2 e^-4 / (100 sqrt 2).
+    g = Grid(4, 3, 2, 0.25, 0.3, 0.5)
+    one = torch.ones((2, 3, 4), dtype=DT)
+    e = 1.5                                      # (gamma - 1) e = 1
+    L0, rho = 2.0, 3.0
+    f = [rho * one, 0 * one, 0 * one, 0 * one, rho * e * one, 0 * one, 0 * one, 0 * one]
+    F0 = S.rhs(f, g, Params())
+    F1 = S.rhs(f, g, Params(cor_L0=L0, cor_Tunit=1e4))
+    assert torch.allclose(F1[4] - F0[4], -0.06621829 * one, rtol=1e-6)
+    F2 = S.rhs(f, g, Params(cor_L0=L0, cor_Tunit=2e4))
+    assert torch.allclose(F2[4] - F0[4], -2.3312002e-3 * one, rtol=1e-6)
+
+
+def test_chromospheric_and_coronal_cooling_conserve_mass_momentum_divb():
+    P = Params(nu3=0.02, do_quench=True, t_chromo=0.3, rho_bot=0.9, cor_L0=0.5, cor_Tunit=5e3)
+    test_conservation_and_divb(P)
+    test_cyclic_axis_permutation(Params(nu3=0.02, cor_L0=0.5, cor_Tunit=5e3))
