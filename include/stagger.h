@@ -105,12 +105,22 @@ typedef struct {
    * not, or a non-positive value: STAGGER_EINVAL. */
   const double* zc;
   const double* zf;
+  /* Chromospheric cooling, eq. (ChromoCool): dE/dt gains
+   * -rho (rho/rho_bot)^(5/3) (e - <e>) / t_chromo, <e> the mean of e = E/rho
+   * over the horizontal plane (constant z) of the cell.  t_chromo = 0: off. */
+  double t_chromo, rho_bot;
+  /* Coronal optically thin cooling, eq. (CoronaCool): dE/dt loses
+   * cor_L0 T^(-1/2) rho^2 exp(-(T / 10^4 K)^2) with T = cor_Tunit (gamma-1) e in
+   * kelvin.  cor_L0 (the paper's constant over the squared atomic mass, in
+   * code units) and cor_Tunit (kelvin per code unit) come from the caller's
+   * unit system.  cor_L0 = 0: off. */
+  double cor_L0, cor_Tunit;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
  * nuE = nuB = 1, qmax 8, qlim 2, log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
- * no gravity, zero references, no cooling (rho_cool 1), no second-order switch
- * (d2lnr_lim 0.3).  Returns STAGGER_EINVAL if p is NULL. */
+ * no gravity, zero references, no cooling (rho_cool 1, rho_bot 1, cor_Tunit 1),
+ * no second-order switch (d2lnr_lim 0.3), uniform z.  Returns STAGGER_EINVAL if p is NULL. */
 int stagger_params_default(stagger_params* p);
 
 /* Create a context for one grid and parameter set on the current CUDA device.

@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
                 ("rho_cool", ctypes.c_double), ("cool_cut", ctypes.c_int),
                 ("csmag", ctypes.c_double), ("scalar_cells", ctypes.c_int),
                 ("do_2nddiv", ctypes.c_int), ("d2lnr_lim", ctypes.c_double),
-                ("zc", ctypes.POINTER(ctypes.c_double)), ("zf", ctypes.POINTER(ctypes.c_double))]
+                ("zc", ctypes.POINTER(ctypes.c_double)), ("zf", ctypes.POINTER(ctypes.c_double)),
+                ("t_chromo", ctypes.c_double), ("rho_bot", ctypes.c_double),
+                ("cor_L0", ctypes.c_double), ("cor_Tunit", ctypes.c_double)]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

@@ -39,6 +39,8 @@ int stagger_params_default(stagger_params* p) {
   p->Cdtd = 0.7;
   p->rho_cool = 1.0;
   p->d2lnr_lim = 0.3;
+  p->rho_bot = 1.0;
+  p->cor_Tunit = 1.0;
   return STAGGER_OK;
 }
 
@@ -74,6 +76,11 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
+  if (!(p->t_chromo >= 0) || (p->t_chromo > 0 && !(p->rho_bot > 0))) return STAGGER_EINVAL;
+  if (!(p->cor_L0 >= 0) || (p->cor_L0 > 0 && !(p->cor_Tunit > 0))) return STAGGER_EINVAL;
+  if (!isfinite(p->t_chromo) || !isfinite(p->cor_L0) || !isfinite(p->rho_bot) ||
+      !isfinite(p->cor_Tunit))
+    return STAGGER_EINVAL;
   if ((p->zc == nullptr) != (p->zf == nullptr)) return STAGGER_EINVAL;
   if (p->zc) {
     if (g->nz < 2) return STAGGER_EINVAL;

@@ -13,6 +13,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fused_kernels.cuh"
@@ -24,7 +25,7 @@ namespace stg {
 const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
-                                     "k_d2flag"};
+                                     "k_d2flag", "k_cool2"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -166,6 +167,11 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.csmag = (float)p.csmag;
   k.izbar = zs ? gr.nz / zcsum : 1.0;
   k.hzc = k.hzf = k.jzc = k.jzf = nullptr;
+  k.inv_tchromo = p.t_chromo > 0 ? (float)(1.0 / p.t_chromo) : 0.f;
+  k.inv_rhobot = p.t_chromo > 0 ? (float)(1.0 / p.rho_bot) : 0.f;
+  k.emean = nullptr;
+  k.corL0 = (float)p.cor_L0;
+  k.corTu = (float)p.cor_Tunit;
   F.zs = zs ? 1 : 0;
   F.wsum_f = zs ? (double)gr.nx * gr.ny * zfsum * k.izbar : (double)F.geo.n;
   F.cdt = p.Cdt;
@@ -182,6 +188,20 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.cmax = nullptr;
   F.d2flag = nullptr;
   F.mesh = nullptr;
+  F.plane = nullptr;
+  F.plane_nb = 0;
+  if (p.t_chromo > 0) {
+    // Plane means of e for the chromospheric cooling: nz means, then the
+    // per-block parts of the fixed-order reduction.
+    const long long m = (long long)gr.nx * gr.ny;
+    F.plane_nb = (int)std::max(1LL, std::min(64LL, (m + 1023) / 1024));
+    if (cudaMalloc(&F.plane, sizeof(double) * (size_t)gr.nz * (1 + F.plane_nb)) != cudaSuccess) {
+      F.plane = nullptr;
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+    k.emean = F.plane;
+  }
   if (zs) {
     // dz/dk at centres and faces and their inverses, as four arrays of nz.
     std::vector<float> m((size_t)4 * gr.nz);
@@ -268,6 +288,8 @@ void fused_release(Fused& F) {
   F.d2flag = nullptr;
   if (F.mesh) cudaFree(F.mesh);
   F.mesh = nullptr;
+  if (F.plane) cudaFree(F.plane);
+  F.plane = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -301,6 +323,12 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
     TIMED(K_NU_SMOOTH, (k_nu_smooth<NB><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
     TIMED(K_NU_FACES, (k_nu_faces<NB><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
+  if (k.inv_tchromo > 0.f) {
+    TIMED(K_COOL2, (k_plane_part<<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
+                       f[0], f[4], F.plane + g.nz, k, g)));
+    TIMED(K_COOL2, (k_plane_final<<<(g.nz + 63) / 64, 64, 0, s>>>(F.plane + g.nz, F.plane_nb,
+                                                                   F.plane, g)));
+  }
   if (k.d2div)
     TIMED(K_D2FLAG, (k_d2flag<NB><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
   auto ktau = k.d2div ? k_tau<N, true> : k_tau<N, false>;
@@ -326,6 +354,8 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
                 d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
   TIMED(K_FLUX, (k_flux<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
+  if (k.inv_tchromo > 0.f || k.corL0 > 0.f)
+    TIMED(K_COOL2, (k_cool2<NB><<<gg, bb, 0, s>>>(f[0], f[4], d[F_QT], k, g)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }

@@ -33,6 +33,9 @@ struct KPar {
   const float *hzc, *hzf, *jzc, *jzf;
   float dlxy, nu2, csmag;
   double izbar;         // 1 / mean dz/dk (diagnostic weights)
+  float inv_tchromo, inv_rhobot;   // chromospheric cooling (0: off)
+  const double* emean;  // plane means of e - e0, one per z (chromospheric cooling)
+  float corL0, corTu;   // coronal thin cooling (corL0 0: off)
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -55,7 +58,7 @@ enum Fld {
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
-           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COUNT };
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {
@@ -73,6 +76,8 @@ struct Fused {
   int zs;               // stretched z mesh
   float* mesh;          // its dz/dk and inverses on the device (4 nz floats), or null
   double wsum_f;        // sum of the z-face weights of the diagnostics (n when uniform)
+  double* plane;        // plane means (nz) then per-block parts (nz * plane_nb), or null
+  int plane_nb;
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   long long launches;

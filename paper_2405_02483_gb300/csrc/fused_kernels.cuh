@@ -79,6 +79,8 @@ using ::fminf;
 using ::log1pf;
 using ::logf;
 using ::sqrtf;
+using ::cbrtf;
+using ::rsqrtf;
 #define STG_F4_FN1(fn)                                                        \
   __device__ __forceinline__ F4 fn(const F4& a) {                             \
     return F4(::fn(a.v[0]), ::fn(a.v[1]), ::fn(a.v[2]), ::fn(a.v[3]));        \
@@ -93,6 +95,8 @@ STG_F4_FN1(sqrtf)
 STG_F4_FN1(expf)
 STG_F4_FN1(logf)
 STG_F4_FN1(log1pf)
+STG_F4_FN1(cbrtf)
+STG_F4_FN1(rsqrtf)
 STG_F4_FN2(fmaxf)
 STG_F4_FN2(fminf)
 #undef STG_F4_FN1
@@ -835,6 +839,35 @@ __global__ void STG_LB_HI(N, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Ge
   flux_cell(n, in, out, k);
 }
 
+// Chromospheric cooling, eq. (ChromoCool), and coronal thin cooling, eq.
+// (CoronaCool), added to -P div u + Q after k_flux (runs only when one is on):
+//   -rho (rho/rho_bot)^(5/3) (e - <e>)/t_chromo, <e> the plane mean (taken on
+//   e - e0 = (E' - e0 r')/r, where e0 cancels);
+//   -L0 T^(-1/2) rho^2 exp(-(T/1e4 K)^2), T = Tunit (gamma - 1) e.
+template <class N>
+__global__ void STG_LB(N, STG_MINB) k_cool2(const float* __restrict__ rd,
+                                            const float* __restrict__ Ed, float* qtp, KPar k,
+                                            Geo g) {
+  N n;
+  if (!n.init(g, k)) return;
+  using T = typename N::T;
+  const T rdv = n.ld(rd), Edv = n.ld(Ed);
+  const T r = rdv + k.r0;
+  T qt = n.ldw(qtp);
+  if (k.inv_tchromo > 0.f) {
+    const T ed = fdiv(Edv - k.e0 * rdv, r);
+    const T x = r * k.inv_rhobot;
+    const T x53 = x * cbrtf(x) * cbrtf(x);
+    qt -= (r * x53) * ((ed - (float)k.emean[n.kz]) * k.inv_tchromo);
+  }
+  if (k.corL0 > 0.f) {
+    const T Tk = (k.corTu * k.gm1) * fdiv(Edv + k.E0, r);
+    const T t4 = Tk * 1e-4f;
+    qt -= (k.corL0 * (r * r)) * (expf(-(t4 * t4)) * rsqrtf(Tk));
+  }
+  n.st(qtp, qt);
+}
+
 // ----------------------------------------------------------- divergence ----
 struct DivIn {
   const float *px, *py, *pz;
@@ -937,6 +970,38 @@ __global__ void k_update(const float* __restrict__ f, const float* __restrict__ 
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   o[i] = f[i] + (float)((double)beta * dtp[0]) * q[i];
+}
+
+// -------------------------------------------------------- plane means -----
+// Mean over each horizontal plane (constant z) of e - e0 = (E' - e0 r')/r, in
+// FP64 with a fixed summation order: part[k * nb + b] is block b's sum over
+// its strided share of plane k; k_plane_final sums the nb parts of a plane.
+__global__ void k_plane_part(const float* __restrict__ rd, const float* __restrict__ Ed,
+                             double* part, KPar k, Geo g) {
+  __shared__ double sm[256];
+  const int kz = blockIdx.y, nb = gridDim.x;
+  const long long m = (long long)g.nx * g.ny;
+  const float* r = rd + (long long)kz * g.sz;
+  const float* E = Ed + (long long)kz * g.sz;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)nb * blockDim.x)
+    acc += (double)((E[i] - k.e0 * r[i]) / (r[i] + k.r0));
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)kz * nb + blockIdx.x] = sm[0];
+}
+
+__global__ void k_plane_final(const double* part, int nb, double* mean, Geo g) {
+  const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kz >= g.nz) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(long long)kz * nb + b];
+  mean[kz] = s / ((double)g.nx * g.ny);
 }
 
 // -------------------------------------------------------------- Courant ----

@@ -148,6 +148,33 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
   }
 }
 
+// Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed
+// order; the broadcast writes (or, for the transpose, adds) sum / (nx ny).
+// The mean is linear and symmetric, so its transpose is the same mean.
+template <typename T>
+__global__ void g_plane_sum(const T* A, T* psum, Geo g) {
+  __shared__ T sm[256];
+  const int kz = blockIdx.x;
+  const long long m = (long long)g.nx * g.ny;
+  T acc = 0;
+  for (long long i = threadIdx.x; i < m; i += blockDim.x) acc += A[(long long)kz * g.sz + i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) psum[kz] = sm[0];
+}
+
+template <typename T>
+__global__ void g_plane_bcast(const T* psum, T* out, int add, Geo g) {
+  GCell c;
+  if (!gcell(c, g)) return;
+  const T v = psum[c.k] / (T)((double)g.nx * g.ny);
+  out[c.idx] = add ? out[c.idx] + v : v;
+}
+
 template <typename T>
 __global__ void g_add_into(T* dst, const T* src, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,6 +482,22 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     }
     d_E = G.add(d_E, qn);
   }
+  if (p.t_chromo > 0) {
+    // Chromospheric cooling, eq. (ChromoCool): -rho (rho/rho_bot)^(5/3) (e - <e>)/t,
+    // <e> the horizontal-plane mean, taken on e - e0 (e0 cancels).
+    int x53 = G.ex(G.axpb(G.lg(G.axpb(r, 1.0 / p.rho_bot, 0.0)), 5.0 / 3.0, 0.0));
+    int de = G.sub(ed, G.pmean(ed));
+    d_E = G.sub(d_E, G.mul(G.mul(r, x53), G.axpb(de, 1.0 / p.t_chromo, 0.0)));
+  }
+  if (p.cor_L0 > 0) {
+    // Coronal thin cooling, eq. (CoronaCool): L0 T^(-1/2) rho^2 exp(-(T/1e4 K)^2),
+    // T = Tunit (gamma - 1) e.
+    int Tk = G.axpb(e, p.cor_Tunit * (p.gamma - 1.0), 0.0);
+    int t4 = G.axpb(Tk, 1e-4, 0.0);
+    int lam = G.mul(G.axpb(G.mul(r, r), p.cor_L0, 0.0),
+                    G.div(G.ex(G.axpb(G.mul(t4, t4), -1.0, 0.0)), G.sq(Tk)));
+    d_E = G.sub(d_E, lam);
+  }
 
   // eq. (indu): dB/dt = -curl E.
   int d_Bx = neg(G.sub(ddup(Ez, Y), ddup(Ey, Z)));
@@ -478,6 +521,13 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
   for (auto& nd : def.nodes)
     if (nd.op != G_INPUT) ++nval;
   if (cudaMalloc(&vals, sizeof(T) * nval * g.n) != cudaSuccess) { vals = nullptr; return STAGGER_EOOM; }
+  bool has_pmean = false;
+  for (auto& nd : def.nodes) has_pmean |= nd.op == G_PMEAN;
+  if (has_pmean && cudaMalloc(&psum, sizeof(T) * g.nz) != cudaSuccess) {
+    psum = nullptr;
+    release();
+    return STAGGER_EOOM;
+  }
   if (!def.mesh.empty()) {
     std::vector<T> m(def.mesh.begin(), def.mesh.end());
     if (cudaMalloc(&mesh, sizeof(T) * m.size()) != cudaSuccess) {
@@ -509,7 +559,8 @@ void GraphExec<T>::release() {
   if (vals) cudaFree(vals);
   if (grads) cudaFree(grads);
   if (mesh) cudaFree(mesh);
-  vals = grads = mesh = nullptr;
+  if (psum) cudaFree(psum);
+  vals = grads = mesh = psum = nullptr;
   ptr.clear();
 }
 
@@ -529,6 +580,12 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
     if (nd.op == G_INPUT) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
+    if (nd.op == G_PMEAN) {
+      g_plane_sum<T><<<geo.nz, 256, 0, s>>>(A, psum, geo);
+      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, ptr[i], 0, geo);
+      launches += 2;
+      continue;
+    }
     g_forward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], mesh, geo);
     ++launches;
   }
@@ -554,6 +611,12 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
     T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
+    if (nd.op == G_PMEAN) {
+      g_plane_sum<T><<<geo.nz, 256, 0, s>>>(grads + (size_t)i * geo.n, psum, geo);
+      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, gA, 1, geo);
+      launches += 2;
+      continue;
+    }
     g_backward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA, gB, geo);
     ++launches;
   }

@@ -15,7 +15,8 @@ enum GOp {
   G_INPUT = 0, G_STENCIL, G_SHIFT, G_ADD, G_SUB, G_MUL, G_DIV, G_MAX,
   G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST,
   G_STEP,  // 1 where a > c0, else 0 (a switch: no gradient)
-  G_ZFIELD // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
+  G_ZFIELD, // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
+  G_PMEAN   // mean of a over the horizontal plane (constant z) of each cell
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -59,6 +60,7 @@ struct GraphDef {
   int cnst(double c) { return push(G_CONST, -1, -1, 0, 0, c, 0); }
   int stepf(int a, double c) { return push(G_STEP, a, -1, 0, 0, c, 0); }
   int zfield(int which) { return push(G_ZFIELD, -1, -1, 2, which, 0, 0); }
+  int pmean(int a) { return push(G_PMEAN, a, -1, 0, 0, 0, 0); }
   // Stretched z mesh: the five arrays of G_ZFIELD, nz values each (empty when uniform).
   std::vector<double> mesh;
 };
@@ -74,6 +76,7 @@ struct GraphExec {
   Geo geo;
   T* vals = nullptr;     // node values (non-input nodes)
   T* mesh = nullptr;     // the mesh arrays of G_ZFIELD on the device, or null
+  T* psum = nullptr;     // per-plane sums of G_PMEAN (nz), or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
   long long launches = 0;
