@@ -53,7 +53,7 @@ KERNEL_ARRAYS = {"k_lr": 2, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smo
 # DRAM bytes (read + write) per cell per launch from one ncu capture of each
 # kernel on the same workload at 192^3 (traffic grows with the cells).  Only
 # kernels unchanged since their capture.
-NCU_TRAFFIC_PER_CELL = {"k_flux": 1667.3e6 / 192 ** 3, "k_edge": 761.9e6 / 192 ** 3,
+NCU_TRAFFIC_PER_CELL = {"k_flux": 1669.8e6 / 192 ** 3, "k_edge": 762.2e6 / 192 ** 3,
                         "k_tau": 707.4e6 / 192 ** 3}
 # Launches that together form one unit of KERNEL_ARRAYS.
 LAUNCHES_PER_UNIT = {"k_div": 3}
