@@ -42,14 +42,16 @@ enum {
   STAGGER_ENONFINITE = -3,  /* the state holds NaN/Inf (diagnostics, Courant)  */
   STAGGER_EOOM = -4,        /* device allocation failed                        */
   STAGGER_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up         */
-  STAGGER_EUNSUPPORTED = -6 /* feature not built (e.g. precision 64 path)      */
+  STAGGER_EUNSUPPORTED = -6 /* not available on this entry (e.g. a stretched
+                             * mesh in stagger_diagnostics_noalloc)         */
 };
 
 typedef struct stagger_ctx stagger_ctx;  /* opaque, library-owned */
 
 typedef struct {
   int nx, ny, nz;          /* cells per axis, each >= 1; all axes periodic     */
-  double dx, dy, dz;       /* uniform spacings, > 0                            */
+  double dx, dy, dz;       /* uniform spacings, > 0 (dz is that of a uniform z;
+                            * stagger_params.zc/zf give a stretched one)      */
 } stagger_grid;
 
 typedef struct {

@@ -90,62 +90,58 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mes
 // holds with equality; max(a, b) splits it evenly on ties.
 template <typename T>
 __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const T* gout,
-                           T* gA, T* gB, Geo g) {
+                           T* gA, T* gB, int wA, int wB, Geo g) {
   GCell c;
   if (!gcell(c, g)) return;
   const long long idx = c.idx;
+  T ca = 0, cb = 0;   // contributions to the gradients of a and b
   if (nd.op == G_STENCIL) {
     // Gather form of the transpose: up^T = dn, dn^T = up, ddup^T = -dddn,
     // dddn^T = -ddup (periodic summation by parts).
     int kind = nd.sk;
     int tk = kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
     T v = stencil_at(gout, c, nd.axis, tk, (T)nd.c0, g);
-    if (kind == ST_DDUP || kind == ST_DDDN) v = -v;
-    gA[idx] += v;
-    return;
+    ca = (kind == ST_DDUP || kind == ST_DDDN) ? -v : v;
+  } else if (nd.op == G_SHIFT) {
+    ca = gout[nbr(c, nd.axis, -nd.sk, g)];
+  } else {
+    const T gg = gout[idx];
+    switch (nd.op) {
+      case G_ADD: ca = gg; cb = gg; break;
+      case G_SUB: ca = gg; cb = -gg; break;
+      case G_MUL: ca = gg * B[idx]; cb = gg * A[idx]; break;
+      case G_DIV: {
+        T a = A[idx], b = B[idx];
+        ca = gg / b;
+        cb = -gg * a / (b * b);
+        break;
+      }
+      case G_MAX: {
+        T a = A[idx], b = B[idx];
+        ca = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
+        cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
+        break;
+      }
+      case G_EXP: ca = gg * out[idx]; break;
+      case G_LOG: ca = gg / A[idx]; break;
+      case G_LOG1P: ca = gg / ((T)1 + A[idx]); break;
+      case G_SQRT: ca = gg / ((T)2 * out[idx]); break;
+      case G_ABS: {
+        T a = A[idx];
+        ca = a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0);
+        break;
+      }
+      case G_AXPB: ca = (T)nd.c0 * gg; break;
+      case G_CLAMPMIN: ca = A[idx] >= (T)nd.c0 ? gg : (T)0; break;
+      case G_CLAMPMAX: ca = A[idx] <= (T)nd.c0 ? gg : (T)0; break;
+      default: break;
+    }
   }
-  if (nd.op == G_SHIFT) {
-    gA[idx] += gout[nbr(c, nd.axis, -nd.sk, g)];
-    return;
-  }
-  T gg = gout[idx];
-  switch (nd.op) {
-    case G_ADD: gA[idx] += gg; gB[idx] += gg; break;
-    case G_SUB: gA[idx] += gg; gB[idx] -= gg; break;
-    case G_MUL: {
-      T a = A[idx], b = B[idx];
-      gA[idx] += gg * b;
-      gB[idx] += gg * a;
-      break;
-    }
-    case G_DIV: {
-      T a = A[idx], b = B[idx];
-      gA[idx] += gg / b;
-      gB[idx] += -gg * a / (b * b);
-      break;
-    }
-    case G_MAX: {
-      T a = A[idx], b = B[idx];
-      T ga = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
-      T gb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
-      gA[idx] += ga;
-      gB[idx] += gb;
-      break;
-    }
-    case G_EXP: gA[idx] += gg * out[idx]; break;
-    case G_LOG: gA[idx] += gg / A[idx]; break;
-    case G_LOG1P: gA[idx] += gg / ((T)1 + A[idx]); break;
-    case G_SQRT: gA[idx] += gg / ((T)2 * out[idx]); break;
-    case G_ABS: {
-      T a = A[idx];
-      gA[idx] += a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0);
-      break;
-    }
-    case G_AXPB: gA[idx] += (T)nd.c0 * gg; break;
-    case G_CLAMPMIN: if (A[idx] >= (T)nd.c0) gA[idx] += gg; break;
-    case G_CLAMPMAX: if (A[idx] <= (T)nd.c0) gA[idx] += gg; break;
-    default: break;   // G_STEP (piecewise constant), G_ZFIELD, G_CONST, G_INPUT
-  }
+  // The first contribution a gradient receives in the reverse sweep writes
+  // it (wA, wB); later ones accumulate.  a and b may be the same node: a's
+  // update happens first in this thread.
+  if (gA) gA[idx] = wA ? ca : gA[idx] + ca;
+  if (gB) gB[idx] = wB ? cb : gB[idx] + cb;
 }
 
 // Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed
@@ -547,6 +543,23 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
       return STAGGER_EOOM;
     }
   }
+  // Reverse-sweep bookkeeping: which nodes receive a gradient, and which
+  // consumer slot gives each node its first contribution (in reverse order).
+  hasg.assign(nn, 0);
+  wa.assign(nn, 0);
+  wb.assign(nn, 0);
+  {
+    std::vector<char> seen(nn, 0);
+    for (int k = 0; k < 8; ++k) seen[def.out[k]] = hasg[def.out[k]] = 1;
+    for (long long i = (long long)nn - 1; i >= 0; --i) {
+      const GNode& nd = def.nodes[i];
+      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
+          nd.op == G_STEP)
+        continue;
+      if (nd.a >= 0) { wa[i] = !seen[nd.a]; seen[nd.a] = hasg[nd.a] = 1; }
+      if (nd.b >= 0) { wb[i] = !seen[nd.b]; seen[nd.b] = hasg[nd.b] = 1; }
+    }
+  }
   ptr.assign(nn, nullptr);
   size_t v = 0;
   for (size_t i = 0; i < nn; ++i)
@@ -597,30 +610,33 @@ template <typename T>
 int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   if (!grads) return STAGGER_EINVAL;
   const size_t nn = def.nodes.size();
-  STG_CUDA_OK(cudaMemsetAsync(grads, 0, sizeof(T) * nn * geo.n, s));
   const int bs = 256;
   const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
-  for (int k = 0; k < 8; ++k) {
-    g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(grads + (size_t)def.out[k] * geo.n, seed[k], geo.n);
-    ++launches;
-  }
+  // Seeds are the first contribution to the outputs' gradients: copy them.
+  for (int k = 0; k < 8; ++k)
+    STG_CUDA_OK(cudaMemcpyAsync(grads + (size_t)def.out[k] * geo.n, seed[k],
+                                sizeof(T) * geo.n, cudaMemcpyDeviceToDevice, s));
   for (long long i = (long long)nn - 1; i >= 0; --i) {
     const GNode& nd = def.nodes[i];
-    if (nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP) continue;
+    if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
+        nd.op == G_STEP)
+      continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
     T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
     if (nd.op == G_PMEAN) {
       g_plane_sum<T><<<geo.nz, 256, 0, s>>>(grads + (size_t)i * geo.n, psum, geo);
-      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, gA, 1, geo);
+      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, gA, wa[i] ? 0 : 1, geo);
       launches += 2;
       continue;
     }
-    g_backward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA, gB, geo);
+    g_backward<T><<<gg, gb, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA, gB, wa[i],
+                                    wb[i], geo);
     ++launches;
   }
   for (int k = 0; k < 8; ++k) {
+    if (!hasg[def.in[k]]) continue;   // the outputs do not depend on this input
     g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(gin[k], grads + (size_t)def.in[k] * geo.n, geo.n);
     ++launches;
   }

@@ -79,6 +79,9 @@ struct GraphExec {
   T* psum = nullptr;     // per-plane sums of G_PMEAN (nz), or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
+  // Reverse sweep: node receives a gradient; its a / b slot writes (rather
+  // than accumulates into) the input's gradient.
+  std::vector<char> hasg, wa, wb;
   long long launches = 0;
 
   int init(const GraphDef& d, const Geo& g, bool with_grads);
