@@ -964,13 +964,6 @@ __global__ void k_update8(Upd8 u, float beta, const double* dtp, long long n, in
   }
 }
 
-// f_out = f + beta dt q (stage-1 update once the Courant step is known).
-__global__ void k_update(const float* __restrict__ f, const float* __restrict__ q,
-                         float* __restrict__ o, float beta, const double* dtp, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  o[i] = f[i] + (float)((double)beta * dtp[0]) * q[i];
-}
 
 // -------------------------------------------------------- plane means -----
 // Mean over each horizontal plane (constant z) of e - e0 = (E' - e0 r')/r, in

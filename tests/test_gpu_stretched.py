@@ -118,3 +118,38 @@ def test_stretched_adjoint_fp64(S):
     e64 = err_max([t.cpu().numpy() for t in out64], ref)
     sim.close()
     assert max(e64) < 1e-10, e64
+
+
+def test_all_options_together(S):
+    """Stretched z, second-order switch, Smagorinsky with RM and the quench,
+    Newtonian, chromospheric and coronal cooling, gravity and the bulk term in
+    one parameter set, on four-cell threads: RHS (FP32, FP64) and three steps
+    against the oracle."""
+    import test_gpu_second_order as T2
+    shape = (20, 12, 10)
+    w = T2.sharp_state(shape)
+    lim, gap = T2.gap_limit(w.fields)
+    assert gap > 1e-5
+    zc, zf = mesh(shape[2], w.spacing[2])
+    kw = dict(VISC_KW, csmag=0.12, c1=-1.0 / 3.0, do_2nddiv=1, d2lnr_lim=float(lim),
+              t_cool=0.2, e_cool=0.8, rho_cool=1.1, cool_cut=1, t_chromo=0.08, rho_bot=0.9,
+              cor_L0=1.0, cor_Tunit=8e3, g=(0.0, 0.0, -0.5))
+    g = oracle.Grid(*shape, *w.spacing, zc=zc, zf=zf)
+    refs, dev = S.split_state(w.fields)
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, zc=zc, zf=zf, **kw))
+    f64 = [torch.tensor(a) for a in w.fields]
+    po = oracle_params(kw)
+    Fo = [t.numpy() for t in oracle.rhs(f64, g, po)]
+    F = [t.double().cpu().numpy() for t in sim.rhs(dev)]
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
+    F64 = [t.cpu().numpy() for t in sim.rhs_unfused_f64(d64)]
+    assert max(err_scale(F, Fo)) < 2e-4, err_scale(F, Fo)
+    assert max(err_scale(F64, Fo)) < 1e-10, err_scale(F64, Fo)
+    fo = f64
+    for _ in range(3):
+        dt = sim.step(dev, None, want_dt=True)
+        fo, dto = oracle.step(fo, g, po, dt=dt)
+        assert abs(dt / dto - 1) < 1e-4, (dt, dto)
+    e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
+    sim.close()
+    assert max(e) < 3e-5, e
