@@ -100,3 +100,55 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(os.path, "exists", lambda p: False if p.endswith("libstagger.so") else True)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def _build_c_user(tmp_path):
+    """Compile and link the plain C user of the library (tests/c_abi_step.c)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pkg = os.path.join(ROOT, "paper_2405_02483_gb300")
+    exe = str(tmp_path / "c_abi_step")
+    cmd = [cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c_abi_step.c"), "-o", exe, "-L", pkg, "-lstagger",
+           "-Wl,-rpath," + pkg, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_plain_c_program_compiles_and_links(tmp_path):
+    """The header is plain C99 and the library links without Python."""
+    _build_c_user(tmp_path)
+
+
+@pytest.mark.gpu
+def test_plain_c_program_matches_the_binding(tmp_path):
+    import subprocess
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2405_02483_gb300 as S
+    exe = _build_c_user(tmp_path)
+    out = str(tmp_path / "state.bin")
+    r = subprocess.run([exe, out], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.stdout, r.stderr)
+    got = np.fromfile(out, dtype=np.float32).reshape(8, 16, 16, 16)
+    # The same state and steps through the Python binding.
+    n, tau = 16, 2 * np.pi
+    x = ((np.arange(n) + 0.5) / n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = [0.02 * np.sin(tau * X) * np.cos(tau * Z), 0.1 * np.sin(tau * Y), 0.1 * np.sin(tau * Z),
+         0.1 * np.sin(tau * X), 0.01 * np.cos(tau * Y), 0.05 * np.cos(tau * Z),
+         0.05 * np.cos(tau * X), 0 * X]
+    host = [torch.tensor(a.astype(np.float32)).contiguous() for a in f]
+    ref = [1.0, 0, 0, 0, 0.9, 0, 0, 0.3]
+    p = S.default_params(ref=ref, nu1=0.04, nu2=1.0, nu3=0.04, do_quench=1)
+    sim = S.Sim((n, n, n), (1.0 / n,) * 3, p)
+    sim.step_host(host, 2, 1e-3)
+    sim.close()
+    for c in range(8):
+        assert np.array_equal(got[c], host[c].numpy()), c
