@@ -21,6 +21,13 @@ struct stagger_ctx {
   double* w64 = nullptr;
   float* host_state = nullptr;  // device copy for stagger_step_host
   long long extra_launches = 0;
+  // The adjoint step as a captured CUDA graph per precision (0 FP32, 1 FP64):
+  // state 0 not tried, 1 captured, -1 capture unavailable (direct launches).
+  int adj_state[2] = {0, 0};
+  cudaGraphExec_t adj_exec[2] = {nullptr, nullptr};
+  long long adj_launches[2] = {0, 0};
+  cudaStream_t cap = nullptr;
+  double* dtp = nullptr;   // the step dt on the device (read by the captured graph)
 };
 
 extern "C" {
@@ -123,6 +130,10 @@ int stagger_destroy(stagger_ctx* c) {
   if (c->w32) cudaFree(c->w32);
   if (c->w64) cudaFree(c->w64);
   if (c->host_state) cudaFree(c->host_state);
+  for (int i = 0; i < 2; ++i)
+    if (c->adj_exec[i]) cudaGraphExecDestroy(c->adj_exec[i]);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->dtp) cudaFree(c->dtp);
   delete c;
   return e == cudaSuccess ? STAGGER_OK : STAGGER_ECUDA;
 }
@@ -214,6 +225,15 @@ __global__ void k_lin2(T* o, const T* x, double a, const T* y, double b, long lo
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = (T)a * x[i] + (T)b * y[i];
 }
+// o = a x + (bB * dt) y with dt read on the device (the adjoint's graph
+// replays with any dt).
+template <typename T>
+__global__ void k_lin2d(T* o, const T* x, double a, const T* y, double bB, const double* dtp,
+                        long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = (T)a * x[i] + (T)(bB * dtp[0]) * y[i];
+}
+__global__ void k_set_scalar(double* p, double v) { p[0] = v; }
 template <typename T>
 __global__ void k_copy(T* o, const T* x, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,7 +262,9 @@ template <typename T>
 static int ensure_work(stagger_ctx* c) {
   T*& w = work_of<T>(c);
   if (w) return STAGGER_OK;
-  if (cudaMalloc(&w, sizeof(T) * 40 * (size_t)c->geo.n) != cudaSuccess) {
+  // f1, f2, q, fbar, qbar, and the fixed state, cotangent-in and cotangent-out
+  // buffers of the captured adjoint (8 arrays each).
+  if (cudaMalloc(&w, sizeof(T) * 64 * (size_t)c->geo.n) != cudaSuccess) {
     w = nullptr;
     return STAGGER_EOOM;
   }
@@ -253,6 +275,13 @@ template <typename T>
 static void lin2(stagger_ctx* c, T* o, const T* x, double a, const T* y, double b, cudaStream_t s) {
   long long n = c->geo.n;
   k_lin2<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, a, y, b, n);
+  ++c->extra_launches;
+}
+template <typename T>
+static void lin2d(stagger_ctx* c, T* o, const T* x, double a, const T* y, double bB,
+                  cudaStream_t s) {
+  long long n = c->geo.n;
+  k_lin2d<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, a, y, bB, c->dtp, n);
   ++c->extra_launches;
 }
 
@@ -315,13 +344,11 @@ int stage_rhs<double>(stagger_ctx* c, GraphExec<double>* G, double* const f[8], 
 }
 
 // Adjoint of one fixed-dt step (see stagger_step_adjoint).
+// The adjoint of one step on its workspace, with dt read from c->dtp: the
+// body that the adjoint replays as a captured CUDA graph (see below).
 template <typename T>
-static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* const lam_in[8],
-                              T* lam_out[8], cudaStream_t s) {
-  int rc = ensure_graph<T>(c, true);
-  if (rc) return rc;
-  rc = ensure_work<T>(c);
-  if (rc) return rc;
+static int adjoint_body(stagger_ctx* c, T* const f0[8], T* const lam_in[8], T* lam_out[8],
+                        cudaStream_t s) {
   GraphExec<T>* G = graph_of<T>(c);
   T* w = work_of<T>(c);
   const long long n = c->geo.n;
@@ -334,32 +361,95 @@ static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* cons
     qb[k] = w + (size_t)(32 + k) * n;
   }
   const double *A = RK_ALPHA, *B = RK_BETA;
+  int rc;
   // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)); the FP32
   // path takes F from the fused kernels, FP64 from the graph.
   if ((rc = stage_rhs<T>(c, G, f0, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, q[k], fb[k], 1.0, fb[k], 0.0, s);
-    lin2<T>(c, f1[k], f0[k], 1.0, q[k], B[0] * dt, s);
+    lin2d<T>(c, f1[k], f0[k], 1.0, q[k], B[0], s);
   }
   if ((rc = stage_rhs<T>(c, G, f1, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, q[k], q[k], A[1], fb[k], 1.0, s);
-    lin2<T>(c, f2[k], f1[k], 1.0, q[k], B[1] * dt, s);
+    lin2d<T>(c, f2[k], f1[k], 1.0, q[k], B[1], s);
   }
   // Reverse sweep: fbar_3 = lam; qbar_3 = beta_3 dt fbar.
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, fb[k], lam_in[k], 1.0, lam_in[k], 0.0, s);
-    lin2<T>(c, qb[k], fb[k], B[2] * dt, fb[k], 0.0, s);
+    lin2d<T>(c, qb[k], fb[k], 0.0, fb[k], B[2], s);
   }
   T* const* stages[3] = {f0, f1, f2};
   for (int st = 2; st >= 0; --st) {
     if ((rc = G->forward(stages[st], s))) return rc;
     if ((rc = G->backward(qb, fb, s))) return rc;     // fbar += J(f_st)^T qbar
     if (st > 0)                                         // qbar_{st} = alpha qbar + beta dt fbar
-      for (int k = 0; k < 8; ++k) lin2<T>(c, qb[k], qb[k], A[st], fb[k], B[st - 1] * dt, s);
+      for (int k = 0; k < 8; ++k) lin2d<T>(c, qb[k], qb[k], A[st], fb[k], B[st - 1], s);
   }
   for (int k = 0; k < 8; ++k) lin2<T>(c, lam_out[k], fb[k], 1.0, fb[k], 0.0, s);
   STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+// Adjoint of one fixed-dt step (see stagger_step_adjoint).  The first call
+// captures adjoint_body on fixed workspace buffers into a CUDA graph (about
+// 4000 launches); every call copies the state and cotangent in, replays the
+// graph on the caller's stream, and copies the result out.  If capture is not
+// available the body is launched directly (the same kernels).
+template <typename T>
+static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* const lam_in[8],
+                              T* lam_out[8], cudaStream_t s) {
+  int rc = ensure_graph<T>(c, true);
+  if (rc) return rc;
+  rc = ensure_work<T>(c);
+  if (rc) return rc;
+  if (!c->dtp && cudaMalloc(&c->dtp, sizeof(double)) != cudaSuccess) {
+    c->dtp = nullptr;
+    return STAGGER_EOOM;
+  }
+  k_set_scalar<<<1, 1, 0, s>>>(c->dtp, dt);
+  ++c->extra_launches;
+  const int pi = sizeof(T) == sizeof(float) ? 0 : 1;
+  const long long n = c->geo.n;
+  T* w = work_of<T>(c);
+  T *f0c[8], *lin[8], *lout[8];
+  for (int k = 0; k < 8; ++k) {
+    f0c[k] = w + (size_t)(40 + k) * n;
+    lin[k] = w + (size_t)(48 + k) * n;
+    lout[k] = w + (size_t)(56 + k) * n;
+  }
+  if (c->adj_state[pi] == 0) {
+    c->adj_state[pi] = -1;
+    if (c->cap || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess) {
+      const int timing = c->fused.timing;
+      c->fused.timing = 0;   // no event records inside the graph
+      const long long before = stagger_launch_count(c);
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const int brc = adjoint_body<T>(c, f0c, lin, lout, c->cap);
+        const cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+        if (brc == STAGGER_OK && ec == cudaSuccess && graph &&
+            cudaGraphInstantiate(&c->adj_exec[pi], graph, 0) == cudaSuccess)
+          c->adj_state[pi] = 1;
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();   // a failed capture leaves no sticky error
+      // Captured launches have not run: count them per replay instead.
+      c->adj_launches[pi] = stagger_launch_count(c) - before;
+      c->extra_launches -= c->adj_launches[pi];
+      c->fused.timing = timing;
+    }
+  }
+  if (c->adj_state[pi] != 1) return adjoint_body<T>(c, f0, lam_in, lam_out, s);
+  const size_t bytes = sizeof(T) * (size_t)n;
+  for (int k = 0; k < 8; ++k) {
+    STG_CUDA_OK(cudaMemcpyAsync(f0c[k], f0[k], bytes, cudaMemcpyDeviceToDevice, s));
+    STG_CUDA_OK(cudaMemcpyAsync(lin[k], lam_in[k], bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  STG_CUDA_OK(cudaGraphLaunch(c->adj_exec[pi], s));
+  c->extra_launches += c->adj_launches[pi];
+  for (int k = 0; k < 8; ++k)
+    STG_CUDA_OK(cudaMemcpyAsync(lam_out[k], lout[k], bytes, cudaMemcpyDeviceToDevice, s));
   return STAGGER_OK;
 }
 
