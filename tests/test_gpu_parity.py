@@ -422,3 +422,32 @@ def test_rollout_gradient_matches_oracle(S):
     e = err_l2([t.grad.double().cpu().numpy() for t in x], [t.numpy() for t in go])
     assert max(e) < 1e-3, e
     sim.close()
+
+
+def test_run_equals_repeated_steps_and_kernel_timing(S):
+    """stagger_run(n) is n stagger_step calls (bitwise, Courant dt on the
+    device), and per-kernel timing reports every stage kernel with the launch
+    counts of the schedule: per step 3 stages of k_vel, k_tau, k_edge, k_flux,
+    three k_div launches each, one Courant pass (part and final) and one
+    stage-1 update."""
+    w, kw = _case("ot3d24_visc_quench")
+    sim, refs, dev = make(S, w, kw)
+    dev2 = [t.clone() for t in dev]
+    for _ in range(3):
+        sim.step(dev)
+    sim.run(dev2, 3)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(dev, dev2))
+    sim.timing(True)
+    sim.step(dev)
+    sim.step(dev)
+    kt = sim.kernel_times()
+    sim.timing(False)
+    sim.close()
+    counts = {k: v[1] for k, v in kt.items()}
+    for name in ("k_vel", "k_tau", "k_edge", "k_flux", "k_nu_raw", "k_nu_max", "k_nu_smooth",
+                 "k_nu_faces"):
+        assert counts.get(name) == 6, (name, counts)
+    assert counts.get("k_div") == 18, counts
+    assert counts.get("k_courant") == 4 and counts.get("k_update") == 2, counts
+    assert all(v[0] > 0 for v in kt.values())
