@@ -56,6 +56,126 @@ __device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Quench, eq. (quench) with reading R8, as one node: out = T min(fac, qlim),
+// fac = the max over the node's axes of max3 along the axis of
+// q = |D2 T| / ((M + |D2 T| / qmax) + 1e-30), D2 T = T(+1) - 2 T + T(-1) and
+// M = max3 |T|.  Its transpose follows the rules of the primitive nodes it
+// stands for: a max splits the gradient evenly on a tie (pairwise, the inner
+// pair first), |x|' = sign x with sign 0 = 0, the clamp passes the gradient
+// where fac <= qlim.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void max_w(T a, T b, T& wa, T& wb) {
+  wa = a > b ? (T)1 : (a == b ? (T)0.5 : (T)0);
+  wb = b > a ? (T)1 : (a == b ? (T)0.5 : (T)0);
+}
+template <typename T>
+__device__ __forceinline__ T sgn(T a) {
+  return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
+}
+
+// q at z = c + s e_ax, and (dq) its derivatives with respect to T at z-1, z,
+// z+1 (through D2 T and through M).
+template <typename T>
+__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, const Geo& g,
+                                  T* dq) {
+  const T vm = A[nbr(c, ax, s - 1, g)], v0 = A[nbr(c, ax, s, g)], vp = A[nbr(c, ax, s + 1, g)];
+  const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
+  const T am = fabs(vm), a0 = fabs(v0), ap = fabs(vp);
+  const T inner = am >= a0 ? am : a0;
+  const T M = inner >= ap ? inner : ap;
+  const T den = (M + a2 * iq) + (T)1e-30;
+  const T q = a2 / den;
+  if (dq) {
+    T wim, wi0, woi, wop;
+    max_w(am, a0, wim, wi0);
+    max_w(inner, ap, woi, wop);
+    const T dq_da2 = (T)1 / den + iq * (-a2 / (den * den));
+    const T dq_dM = -a2 / (den * den);
+    const T sd = sgn(d2);
+    dq[0] = dq_da2 * sd + dq_dM * (woi * wim) * sgn(vm);
+    dq[1] = dq_da2 * sd * (T)-2 + dq_dM * (woi * wi0) * sgn(v0);
+    dq[2] = dq_da2 * sd + dq_dM * wop * sgn(vp);
+  }
+  return q;
+}
+
+// fac at c, and (when wq) the weights of the three q of each axis in fac:
+// wq[3 t + p + 1] for axis t and position p.
+template <typename T>
+__device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int a1, T iq,
+                                        const Geo& g, T* wq) {
+  T m[2] = {0, 0}, w[2][3];
+  for (int t = 0; t < 2; ++t) {
+    const int ax = t == 0 ? a0 : a1;
+    if (ax < 0) continue;
+    const T qm = q_at(A, c, ax, -1, iq, g, (T*)nullptr), q0 = q_at(A, c, ax, 0, iq, g, (T*)nullptr),
+            qp = q_at(A, c, ax, 1, iq, g, (T*)nullptr);
+    const T inner = qm >= q0 ? qm : q0;
+    m[t] = inner >= qp ? inner : qp;
+    T wim, wi0, woi, wop;
+    max_w(qm, q0, wim, wi0);
+    max_w(inner, qp, woi, wop);
+    w[t][0] = woi * wim;
+    w[t][1] = woi * wi0;
+    w[t][2] = wop;
+  }
+  T fac = m[0], wf0 = 1, wf1 = 0;
+  if (a1 >= 0) {
+    fac = m[0] >= m[1] ? m[0] : m[1];
+    max_w(m[0], m[1], wf0, wf1);
+  }
+  if (wq)
+    for (int p = 0; p < 3; ++p) {
+      wq[p] = wf0 * w[0][p];
+      wq[3 + p] = a1 >= 0 ? wf1 * w[1][p] : (T)0;
+    }
+  return fac;
+}
+
+// Transpose, first pass (per output cell y): S0 = gbar C (the product's own
+// term) and S[1 + 3 t + p + 1] = gbar T dC/dfac dfac/dq, the cotangent each
+// q of axis t at position p receives from y.
+template <typename T>
+__global__ void g_quench_b1(GNode nd, const T* A, const T* gout, T* S, Geo g) {
+  GCell c;
+  if (!gcell(c, g)) return;
+  const T iq = (T)1 / (T)nd.c0, qlim = (T)nd.c1;
+  T wq[6];
+  const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, g, wq);
+  const T gg = gout[c.idx];
+  const T C = fac > qlim ? qlim : fac;
+  const T dC = fac <= qlim ? (T)1 : (T)0;
+  const T base = gg * A[c.idx] * dC;
+  S[c.idx] = gg * C;
+  for (int j = 0; j < 6; ++j) S[(long long)(1 + j) * g.n + c.idx] = base * wq[j];
+}
+
+// Transpose, second pass (per input cell x): Tbar(x) = S0(x) + the sum over
+// the axes and the three q positions z = x + r e_a whose stencils hold x of
+// qbar(z) dq(z)/dT(x), qbar(z) = sum_p S[.. p](z - p e_a).
+template <typename T>
+__global__ void g_quench_b3(GNode nd, const T* A, const T* S, T* gA, int wA, Geo g) {
+  GCell c;
+  if (!gcell(c, g)) return;
+  const T iq = (T)1 / (T)nd.c0;
+  T acc = S[c.idx];
+  for (int t = 0; t < 2; ++t) {
+    const int ax = t == 0 ? nd.axis : nd.sk;
+    if (ax < 0) continue;
+    for (int r = -1; r <= 1; ++r) {
+      T qbar = 0;
+      for (int p = -1; p <= 1; ++p)
+        qbar += S[(long long)(1 + 3 * t + p + 1) * g.n + nbr(c, ax, r - p, g)];
+      T dq[3];
+      q_at(A, c, ax, r, iq, g, dq);
+      acc += qbar * dq[1 - r];
+    }
+  }
+  gA[c.idx] = wA ? acc : gA[c.idx] + acc;
+}
+
 template <typename T>
 __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mesh, Geo g) {
   GCell c;
@@ -80,6 +200,11 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, T* out, const T* mes
     case G_CLAMPMAX: r = A[idx] > (T)nd.c0 ? (T)nd.c0 : A[idx]; break;
     case G_STEP: r = A[idx] > (T)nd.c0 ? (T)1 : (T)0; break;
     case G_ZFIELD: r = mesh[(long long)nd.sk * g.nz + c.k]; break;
+    case G_QUENCH: {
+      const T fac = quench_fac(A, c, nd.axis, nd.sk, (T)1 / (T)nd.c0, g, (T*)nullptr);
+      r = A[idx] * (fac > (T)nd.c1 ? (T)nd.c1 : fac);
+      break;
+    }
     default: r = (T)nd.c0; break;  // G_CONST
   }
   out[idx] = r;
@@ -384,21 +509,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     if (p.do_quench) {
       // eq. (quench): one factor per component, over its differentiation axes;
       // |T| in the ratio is the 3-cell max of |T| along the axis.
-      auto quench = [&](int T, int a0, int a1) {
-        int fac = -1;
-        for (int t = 0; t < 2; ++t) {
-          int ax = t == 0 ? a0 : a1;
-          if (ax < 0) continue;
-          int d2 = G.add(G.sub(G.shift(T, ax, 1), G.axpb(T, 2.0, 0.0)), G.shift(T, ax, -1));
-          int a2 = G.ab(d2);
-          int aT = G.ab(T);
-          int M = G.maxi(G.maxi(G.shift(aT, ax, -1), aT), G.shift(aT, ax, 1));
-          int q = G.div(a2, G.axpb(G.add(M, G.axpb(a2, 1.0 / p.qmax, 0.0)), 1.0, 1e-30));
-          int m = G.maxi(G.maxi(G.shift(q, ax, -1), q), G.shift(q, ax, 1));
-          fac = fac < 0 ? m : G.maxi(fac, m);
-        }
-        return G.mul(T, G.cmax(fac, p.qlim));
-      };
+      auto quench = [&](int T, int a0, int a1) { return G.quench(T, a0, a1, p.qmax, p.qlim); };
       txx = quench(txx, X, -1);
       tyy = quench(tyy, Y, -1);
       tzz = quench(tzz, Z, -1);
@@ -517,8 +628,17 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
   for (auto& nd : def.nodes)
     if (nd.op != G_INPUT) ++nval;
   if (cudaMalloc(&vals, sizeof(T) * nval * g.n) != cudaSuccess) { vals = nullptr; return STAGGER_EOOM; }
-  bool has_pmean = false;
-  for (auto& nd : def.nodes) has_pmean |= nd.op == G_PMEAN;
+  bool has_pmean = false, has_quench = false;
+  for (auto& nd : def.nodes) {
+    has_pmean |= nd.op == G_PMEAN;
+    has_quench |= nd.op == G_QUENCH;
+  }
+  if (has_quench && with_grads &&
+      cudaMalloc(&qscr, sizeof(T) * 7 * (size_t)g.n) != cudaSuccess) {
+    qscr = nullptr;
+    release();
+    return STAGGER_EOOM;
+  }
   if (has_pmean && cudaMalloc(&psum, sizeof(T) * g.nz) != cudaSuccess) {
     psum = nullptr;
     release();
@@ -573,7 +693,8 @@ void GraphExec<T>::release() {
   if (grads) cudaFree(grads);
   if (mesh) cudaFree(mesh);
   if (psum) cudaFree(psum);
-  vals = grads = mesh = psum = nullptr;
+  if (qscr) cudaFree(qscr);
+  vals = grads = mesh = psum = qscr = nullptr;
   ptr.clear();
 }
 
@@ -628,6 +749,12 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
     if (nd.op == G_PMEAN) {
       g_plane_sum<T><<<geo.nz, 256, 0, s>>>(grads + (size_t)i * geo.n, psum, geo);
       g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, gA, wa[i] ? 0 : 1, geo);
+      launches += 2;
+      continue;
+    }
+    if (nd.op == G_QUENCH) {
+      g_quench_b1<T><<<gg, gb, 0, s>>>(nd, A, grads + (size_t)i * geo.n, qscr, geo);
+      g_quench_b3<T><<<gg, gb, 0, s>>>(nd, A, qscr, gA, wa[i], geo);
       launches += 2;
       continue;
     }

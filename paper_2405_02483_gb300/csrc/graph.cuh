@@ -16,7 +16,8 @@ enum GOp {
   G_EXP, G_LOG, G_LOG1P, G_SQRT, G_ABS, G_AXPB, G_CLAMPMIN, G_CLAMPMAX, G_CONST,
   G_STEP,  // 1 where a > c0, else 0 (a switch: no gradient)
   G_ZFIELD, // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
-  G_PMEAN   // mean of a over the horizontal plane (constant z) of each cell
+  G_PMEAN,  // mean of a over the horizontal plane (constant z) of each cell
+  G_QUENCH  // eq. (quench) of a over axes axis and sk (-1: one axis); c0 qmax, c1 qlim
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -61,6 +62,9 @@ struct GraphDef {
   int stepf(int a, double c) { return push(G_STEP, a, -1, 0, 0, c, 0); }
   int zfield(int which) { return push(G_ZFIELD, -1, -1, 2, which, 0, 0); }
   int pmean(int a) { return push(G_PMEAN, a, -1, 0, 0, 0, 0); }
+  int quench(int a, int a0, int a1, double qmax, double qlim) {
+    return push(G_QUENCH, a, -1, a0, a1, qmax, qlim);
+  }
   // Stretched z mesh: the five arrays of G_ZFIELD, nz values each (empty when uniform).
   std::vector<double> mesh;
 };
@@ -77,6 +81,7 @@ struct GraphExec {
   T* vals = nullptr;     // node values (non-input nodes)
   T* mesh = nullptr;     // the mesh arrays of G_ZFIELD on the device, or null
   T* psum = nullptr;     // per-plane sums of G_PMEAN (nz), or null
+  T* qscr = nullptr;     // 7 arrays of scratch for the G_QUENCH transpose, or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
   // Reverse sweep: node receives a gradient; its a / b slot writes (rather
