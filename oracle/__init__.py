@@ -7,5 +7,6 @@ never does, and it shares no code with the CUDA sources.
 """
 from .stagger import (  # noqa: F401
     Grid, Params, up, dn, ddup, dddn, rhs, rhs_parts, rk3_step, step, courant_dt,
+    courant_fields, courant_limits,
     diagnostics, step_adjoint, quench, max3, smooth3, ALPHA, BETA,
 )

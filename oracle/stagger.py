@@ -537,10 +537,12 @@ def rk3_step(f, dt, F):
     return f
 
 
-def courant_dt(f, q1, g: Grid, p: Params, nu=None):
-    """eq. (courantcond), reading R9: the smallest of the wave-speed,
-    rate-of-change and diffusion limits, from the state and its stage-1
-    derivative.  Returns (dt, (t_wave, t_rate, t_diff))."""
+def courant_fields(f, q1, g: Grid, p: Params, nu=None):
+    """Per-cell quantities of eq. (courantcond), reading R9: the fastest
+    signal speed w = c_s + c_A + |u_perp| at the centre, the relative rate of
+    change max(|d rho/dt| / rho, |dE/dt| / E) from the stage-1 derivative q1,
+    and the cell-centred viscosity nu (None when no viscosity is on).  The
+    limits are reductions of these over the cells (courant_limits)."""
     r, px, py, pz, E, Bx, By, Bz = f
     if p.log_interp:
         lr = torch.log(r)
@@ -557,24 +559,36 @@ def courant_dt(f, q1, g: Grid, p: Params, nu=None):
     ub = ucx * bcx + ucy * bcy + ucz * bcz
     uperp2 = torch.where(B2 > 0, u2 - ub * ub / torch.where(B2 > 0, B2, 1.0), u2)
     uperp = torch.sqrt(torch.clamp(uperp2, min=0.0))
-    inf = math.inf
-    # With a stretched z (R19) the limits are minima over the cells of their
-    # local values, dl the cell's smallest active size.
-    dlc = g.dlmin_c()
     w = cs + ca + uperp
+    rate = torch.maximum(torch.abs(q1[0]) / r, torch.abs(q1[4]) / E)
+    if p.visc_on():
+        if nu is None:
+            nu = rhs_parts(f, g, p)["nu"]
+    else:
+        nu = None
+    return w, rate, nu
+
+
+def courant_limits(w, rate, nu, g: Grid, p: Params, dlc=None):
+    """eq. (courantcond), reading R9: the wave-speed, rate-of-change and
+    diffusion limits from the per-cell fields of courant_fields, taken over
+    any set of cells (the maxima are all that matter on a uniform mesh).
+    With a stretched z (R19) the limits are minima over the cells of their
+    local values, dl the cell's smallest active size (dlc, per cell, default
+    the whole grid's).  Returns (dt, (t_wave, t_rate, t_diff))."""
+    inf = math.inf
+    if g.stretched and dlc is None:
+        dlc = g.dlmin_c()
     if g.stretched:
         wr = float(torch.max(w / dlc))
         t_wave = p.Cdt / wr if wr > 0 else inf
     else:
         wmax = float(torch.max(w))
         t_wave = p.Cdt * g.dl_min / wmax if wmax > 0 else inf
-    rate = torch.maximum(torch.abs(q1[0]) / r, torch.abs(q1[4]) / E)
     rmax = float(torch.max(rate))
     t_rate = p.Cdtr / rmax if rmax > 0 else inf
     t_diff = inf
-    if p.visc_on():
-        if nu is None:
-            nu = rhs_parts(f, g, p)["nu"]
+    if nu is not None:
         dfac = max(1.0, p.nuE, p.nuB * g.dl_max / g.dl_min)
         if g.stretched:
             dr = float(torch.max(nu / dlc)) * dfac
@@ -583,6 +597,14 @@ def courant_dt(f, q1, g: Grid, p: Params, nu=None):
             dmax = float(torch.max(nu)) * dfac
             t_diff = p.Cdtd * g.dl_min / dmax if dmax > 0 else inf
     return min(t_wave, t_rate, t_diff), (t_wave, t_rate, t_diff)
+
+
+def courant_dt(f, q1, g: Grid, p: Params, nu=None):
+    """eq. (courantcond), reading R9: the smallest of the wave-speed,
+    rate-of-change and diffusion limits, from the state and its stage-1
+    derivative.  Returns (dt, (t_wave, t_rate, t_diff))."""
+    w, rate, nu = courant_fields(f, q1, g, p, nu)
+    return courant_limits(w, rate, nu, g, p)
 
 
 def step(f, g: Grid, p: Params, dt=None):

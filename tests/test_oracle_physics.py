@@ -908,3 +908,51 @@ def test_chromospheric_and_coronal_cooling_conserve_mass_momentum_divb():
     P = Params(nu3=0.02, do_quench=True, t_chromo=0.3, rho_bot=0.9, cor_L0=0.5, cor_Tunit=5e3)
     test_conservation_and_divb(P)
     test_cyclic_axis_permutation(Params(nu3=0.02, cor_L0=0.5, cor_Tunit=5e3))
+
+
+RHS_REACH = 14
+
+
+@pytest.mark.parametrize("seed", [5, 11])
+def test_rhs_and_courant_fields_reach(seed):
+    """Locality of the right-hand side with RM viscosity and the quench: a
+    change of any field in one cell changes the derivative (and the Courant
+    fields w, rate, nu) only in cells at most RHS_REACH away along each axis
+    (derivative 3 + interpolation 3 + strain 3 + max3 1 + smooth3 1 + stress
+    divergence 3), and the wave speed w only within 5 (the face density
+    reaches cells -3..+2 of the face, the centring faces -2..+3 of the
+    cell).  The full-size parity
+    tests rely on this to evaluate the oracle on a patch of a larger box."""
+    from paper_2405_02483_gb300 import inputs
+    n = 2 * RHS_REACH + 6
+    w = inputs.turbulence(n, seed=seed)
+    gen = torch.Generator().manual_seed(seed)
+    f = [torch.tensor(a) * (1 + 0.02 * torch.randn(n, n, n, generator=gen, dtype=DT))
+         for a in w.fields]
+    f[5] = f[5] + 0.05 * torch.randn(n, n, n, generator=gen, dtype=DT)
+    g = Grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n)
+    p = Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=True)
+
+    def outputs(state):
+        P = S.rhs_parts(state, g, p)
+        q = [P[k] for k in ("d_r", "d_px", "d_py", "d_pz", "d_E", "d_Bx", "d_By", "d_Bz")]
+        wv, rate, nu = S.courant_fields(state, q, g, p, nu=P["nu"])
+        return q + [rate, nu], wv
+
+    base, wbase = outputs(f)
+    c = n // 2
+    seen, seen_w = 0, 0
+    for fld in range(8):
+        f2 = [t.clone() for t in f]
+        f2[fld][c, c, c] += 1e-3 * (1 + abs(float(f2[fld][c, c, c])))
+        got, wgot = outputs(f2)
+        for a, b in zip(got, base):
+            idx = ((a - b) != 0).nonzero()
+            if len(idx):
+                seen = max(seen, int((idx - c).abs().max()))
+        idx = ((wgot - wbase) != 0).nonzero()
+        if len(idx):
+            seen_w = max(seen_w, int((idx - c).abs().max()))
+    assert seen <= RHS_REACH, seen
+    assert seen >= RHS_REACH - 2, seen            # the perturbation did travel
+    assert seen_w <= 5, seen_w
