@@ -1,0 +1,287 @@
+"""Parity at the full size of the benchmark workload: MHD turbulence on a
+periodic 512^3 box with RM viscosity and the quench, four-cell threads and the
+Courant step reduced on the device, built exactly as bench.py builds it and
+taken through the benchmark's three warm-up steps first.
+
+The oracle cannot take the whole box in seconds, so it is run on patches: the
+right-hand side of a cell depends only on cells at most RHS_REACH away along
+each axis (pinned on the CPU by test_rhs_and_courant_fields_reach), so the
+oracle evaluated on a patch that holds a block of cells and a halo of HALO
+cells around it is exact on the block, although it treats the patch as
+periodic.  One RK3 step reaches three times as far.
+
+- right-hand side: blocks at the periodic corners (wrapping through index 0),
+  at the last cells, the centre and seeded places, element by element against
+  the oracle;
+- every cell: four-cell and one-cell threads agree over the whole box;
+- Courant limits: the oracle's wave-speed, rate and diffusion limits over
+  blocks centred on the peaks of cheap estimates of those fields (the
+  estimates only place the blocks; the expected values are the oracle's)
+  equal the device's limits over the whole box, which cannot exceed them;
+- one Courant step: blocks against the oracle's RK3 step with the device's
+  dt on patches with a halo of three reaches; mass and momentum sums
+  conserved and div B kept at FP32 roundoff over the whole box.
+
+Tolerance of a time derivative F_c (FP32 device vs FP64 oracle):
+    |F_dev - F_ora| <= 2e-4 S_c + K delta_c,   K = 10,
+with S_c the scale of the small-grid tests (max |F_c|, floored at 1e-3 of the
+largest derivative) and delta_c the FP32 floor of the equation at this state:
+the largest change of the oracle's F_c when every input value is multiplied
+by 1 + u xi (u = 2^-24 the FP32 unit roundoff, xi uniform in [-1, 1]).  The
+floor matters where an equation's terms cancel: on this smooth flow (|k| <= 4
+on 512 cells) the continuity and energy equations are sums of flux
+derivatives that nearly cancel, and FP32 rounds each flux, so the rounding of
+a flux, divided by h, is what remains (an FP32 evaluation of the oracle's own
+formulas shows errors of the same size).  The step error is judged on the state, as in the small-grid tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+from paper_2405_02483_gb300 import inputs
+from test_gpu_parity import oracle_params
+from test_oracle_physics import RHS_REACH
+
+pytestmark = pytest.mark.gpu
+
+N = 512
+WARMUP = 3
+HALO = RHS_REACH + 2
+K_FLOOR = 10.0
+U32 = 2.0 ** -24
+KEYS = ("d_r", "d_px", "d_py", "d_pz", "d_E", "d_Bx", "d_By", "d_Bz")
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def big():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2405_02483_gb300 as S
+    w = inputs.turbulence(N, device="cuda")
+    refs, dev = S.split_state(w.fields)
+    del w
+    sim = S.Sim((N, N, N), (1.0 / N,) * 3, S.default_params(ref=refs, scalar_cells=0, **bench.PHYS))
+    for _ in range(WARMUP):
+        sim.step(dev, None)
+    F = sim.rhs(dev)
+    torch.cuda.synchronize()
+    yield dict(S=S, sim=sim, refs=refs, dev=dev, F=F, po=oracle_params(bench.PHYS))
+    sim.close()
+
+
+def wrap_index(lo, size, device):
+    return [torch.arange(lo[a], lo[a] + size, device=device) % N for a in range(3)]
+
+
+def take(arrs, lo, size, refs=None):
+    """FP64 CPU copies of cells lo + [0, size) per axis (lo = (x, y, z)),
+    wrapped periodically; plus refs when given (the full field values)."""
+    ix, iy, iz = wrap_index(lo, size, arrs[0].device)
+    out = []
+    for c, t in enumerate(arrs):
+        v = t.index_select(0, iz).index_select(1, iy).index_select(2, ix).double().cpu()
+        out.append(v + refs[c] if refs is not None else v)
+    return out
+
+
+def oracle_patch(f, po, seed=None):
+    """Oracle right-hand side and Courant fields on a patch (periodic); with a
+    seed also |F(f (1 + u xi)) - F(f)| per field, xi uniform in [-1, 1]."""
+    n = f[0].shape[0]
+    g = oracle.Grid(n, n, n, 1.0 / N, 1.0 / N, 1.0 / N)
+    P = oracle.rhs_parts(f, g, po)
+    q = [P[k] for k in KEYS]
+    w, rate, nu = oracle.courant_fields(f, q, g, po, nu=P["nu"])
+    if seed is None:
+        return q, (w, rate, nu)
+    gen = torch.Generator().manual_seed(seed)
+    fp = [a * (1.0 + U32 * (2.0 * torch.rand(a.shape, generator=gen, dtype=a.dtype) - 1.0))
+          for a in f]
+    qp = oracle.rhs(fp, g, po)
+    return q, (w, rate, nu), [(a - b).abs() for a, b in zip(qp, q)]
+
+
+def interior(t, halo, size):
+    return t[halo:halo + size, halo:halo + size, halo:halo + size]
+
+
+def rhs_block_starts():
+    gen = np.random.default_rng(2405)
+    starts = [(N - 8, N - 8, N - 8),            # wraps through 0 on every axis
+              (0, 0, 0), (N - 16, N - 16, N - 16), (N // 2 - 8,) * 3,
+              (N - 8, 3, N // 2)]
+    starts += [tuple(int(v) for v in gen.integers(0, N, 3)) for _ in range(4)]
+    return starts
+
+
+def peaks(x, k=4, sep=8):
+    """The k largest local maxima of x (periodic; a local maximum is the
+    largest value within sep cells along each axis), as (x, y, z) cells."""
+    m = x.clone()
+    for ax in range(3):
+        src = m.clone()
+        for s in range(1, sep + 1):
+            m = torch.maximum(m, torch.roll(src, s, ax))
+            m = torch.maximum(m, torch.roll(src, -s, ax))
+    vals = torch.where(x >= m, x, torch.full_like(x, -float("inf"))).flatten()
+    idx = torch.topk(vals, k).indices.cpu().numpy()
+    kz, rem = np.divmod(idx, N * N)
+    ky, kx = np.divmod(rem, N)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(kx, ky, kz)]
+
+
+def estimates(dev, refs, F, phys):
+    """Cheap FP32 estimates (two-point centring and differences) of the wave
+    speed c_s + c_A + |u_perp|, the RM viscosity and the relative rate of
+    change, used only to choose where the oracle looks."""
+    full = [t + float(r) for t, r in zip(dev, refs)]
+    r, E = full[0], full[4]
+    uc = [0.5 * (full[1 + a] + torch.roll(full[1 + a], -1, 2 - a)) / r for a in range(3)]
+    bc = [0.5 * (full[5 + a] + torch.roll(full[5 + a], -1, 2 - a)) for a in range(3)]
+    cs = torch.sqrt(GAMMA * (GAMMA - 1.0) * E / r)
+    b2 = sum(b * b for b in bc)
+    ca = torch.sqrt(b2 / r)
+    u2 = sum(u * u for u in uc)
+    ub = sum(u * b for u, b in zip(uc, bc))
+    uperp = torch.sqrt(torch.clamp(u2 - ub * ub / torch.clamp(b2, min=1e-30), min=0.0))
+    div = sum((torch.roll(full[1 + a], -1, 2 - a) - full[1 + a]) for a in range(3)) * N
+    nu = (phys["nu1"] * torch.sqrt(u2) + phys["nu3"] * (cs + ca)
+          + phys["nu2"] / N * torch.clamp(-div, min=0.0))
+    rate = torch.maximum(F[0].abs() / r, F[4].abs() / E)
+    return cs + ca + uperp, nu, rate
+
+
+@pytest.fixture(scope="module")
+def blocks(big):
+    """Device and oracle right-hand sides on the blocks, the scales S_c and
+    the FP32 floors delta_c."""
+    B = 16
+    got, ora, sens = [[] for _ in KEYS], [[] for _ in KEYS], [[] for _ in KEYS]
+    for b, lo in enumerate(rhs_block_starts()):
+        f = take(big["dev"], tuple(v - HALO for v in lo), B + 2 * HALO, big["refs"])
+        q, _, dq = oracle_patch(f, big["po"], seed=100 + b)
+        Fg = take(big["F"], lo, B)
+        for c in range(8):
+            got[c].append(Fg[c].numpy().ravel())
+            ora[c].append(interior(q[c], HALO, B).numpy().ravel())
+            sens[c].append(interior(dq[c], HALO, B).numpy().ravel())
+    got = [np.concatenate(a) for a in got]
+    ora = [np.concatenate(a) for a in ora]
+    mx = [float(np.abs(o).max()) for o in ora]
+    scale = [max(m, 1e-3 * max(mx)) for m in mx]
+    delta = [float(np.concatenate(a).max()) for a in sens]
+    return dict(got=got, ora=ora, scale=scale, delta=delta)
+
+
+def test_fullsize_rhs_blocks(blocks):
+    got, ora, scale, delta = blocks["got"], blocks["ora"], blocks["scale"], blocks["delta"]
+    for c in range(8):
+        err = float(np.abs(got[c] - ora[c]).max())
+        allowed = 2e-4 * scale[c] + K_FLOOR * delta[c]
+        assert err <= allowed, (KEYS[c], err, scale[c], delta[c])
+    # the floor is the FP32 rounding, far below the terms of a flux equation
+    assert max(delta[c] / scale[c] for c in (1, 2, 3, 5, 6, 7)) < 1e-4, (delta, scale)
+    # the blocks hold a flow, not a uniform state
+    assert min(float(np.abs(o).max()) for o in ora[1:4]) > 0.1
+
+
+def test_fullsize_four_and_one_cell_threads_agree_everywhere(big, blocks):
+    """Every cell: the two thread mappings differ only by the contraction of
+    multiply-adds, within 2e-5 of the scale plus the FP32 floor (the floor is
+    measured on the blocks; the flow is statistically the same everywhere)."""
+    S = big["S"]
+    sim1 = S.Sim((N, N, N), (1.0 / N,) * 3,
+                 S.default_params(ref=big["refs"], scalar_cells=1, **bench.PHYS))
+    F1 = sim1.rhs(big["dev"])
+    torch.cuda.synchronize()
+    sim1.close()
+    F = big["F"]
+    for c in range(8):
+        assert bool(torch.isfinite(F[c]).all())
+        d = float((F1[c] - F[c]).abs().max())
+        allowed = 2e-5 * blocks["scale"][c] + K_FLOOR * blocks["delta"][c]
+        assert d <= allowed, (KEYS[c], d, blocks["scale"][c], blocks["delta"][c])
+    del F1
+
+
+def test_fullsize_courant_limits(big):
+    dev, refs, F, po = big["dev"], big["refs"], big["F"], big["po"]
+    dt, lim = big["sim"].courant(dev)
+    assert dt == min(lim)
+    wave, nu, rate = estimates(dev, refs, F, bench.PHYS)
+    centres = peaks(wave) + peaks(nu) + peaks(rate)
+    del wave, nu, rate
+    B = 8
+    cells = [[], [], []]
+    drate = 0.0
+    starts = [tuple(v - B // 2 for v in c) for c in centres] + rhs_block_starts()[:2]
+    for b, lo in enumerate(starts):
+        f = take(dev, tuple(v - HALO for v in lo), B + 2 * HALO, refs)
+        _, fields, dq = oracle_patch(f, po, seed=200 + b)
+        for i in range(3):
+            cells[i].append(interior(fields[i], HALO, B).flatten())
+        # FP32 floor of the rate max(|F_r| / r, |F_E| / E)
+        fr = [interior(t, HALO, B) for t in (f[0], f[4], dq[0], dq[4])]
+        drate = max(drate, float(torch.maximum(fr[2] / fr[0], fr[3] / fr[1]).max()))
+    g = oracle.Grid(N, N, N, 1.0 / N, 1.0 / N, 1.0 / N)
+    dto, limo = oracle.courant_limits(*[torch.cat(c) for c in cells], g, po)
+    # The device reduces over every cell, the oracle over the blocks only; the
+    # blocks hold each field's peak (by the estimates, whose peaks include the
+    # device's own largest rate), so the limits agree to FP32 rounding.  The
+    # rate is a ratio of right-hand sides: its maxima agree to the tolerance
+    # of F_r and F_E.
+    assert lim[0] == pytest.approx(limo[0], rel=1e-5), (lim, limo)
+    assert lim[2] == pytest.approx(limo[2], rel=1e-5), (lim, limo)
+    rmax, rmax_o = po.Cdtr / lim[1], po.Cdtr / limo[1]
+    assert abs(rmax - rmax_o) <= 3e-4 * rmax_o + K_FLOOR * drate, (rmax, rmax_o, drate)
+    # The step is the smallest limit; when the rate does not decide it, the
+    # oracle's dt equals the device's to FP32 rounding.
+    if min(lim) != lim[1] and min(limo) != limo[1]:
+        assert dt == pytest.approx(dto, rel=1e-5)
+    else:
+        assert dt == pytest.approx(dto, rel=3e-4 + K_FLOOR * drate / rmax_o)
+
+
+def test_fullsize_step_blocks_and_invariants(big):
+    S, refs, po = big["S"], big["refs"], big["po"]
+    st = [t.clone() for t in big["dev"]]
+    sim = big["sim"]
+    B, H = 8, 3 * RHS_REACH + 2
+    starts = [(N - 4, N - 4, N - 4), (N // 2 - 4,) * 3, (N - 4, 100, 300)]
+    before = [take(st, tuple(v - H for v in lo), B + 2 * H, refs) for lo in starts]
+    d0 = sim.diagnostics(st)
+    dt_c, _ = sim.courant(st)
+    dt = sim.step(st, None, want_dt=True)
+    assert dt == dt_c
+    d1 = sim.diagnostics(st)
+    got, ora = [[] for _ in KEYS], [[] for _ in KEYS]
+    for lo, f in zip(starts, before):
+        n = f[0].shape[0]
+        g = oracle.Grid(n, n, n, 1.0 / N, 1.0 / N, 1.0 / N)
+        fo, _ = oracle.step(f, g, po, dt=dt)
+        after = take(st, lo, B, refs)
+        for c in range(8):
+            got[c].append(after[c].numpy().ravel())
+            ora[c].append(interior(fo[c], H, B).numpy().ravel())
+    got = [np.concatenate(a) for a in got]
+    ora = [np.concatenate(a) for a in ora]
+    # error relative to the magnitude of the field's group (rho; momentum; E;
+    # B), as in the small-grid step tests
+    groups = [[0], [1, 2, 3], [4], [5, 6, 7]]
+    for gi in groups:
+        sc = max(float(np.abs(ora[i]).max()) for i in gi)
+        for i in gi:
+            e = float(np.abs(got[i] - ora[i]).max()) / sc
+            assert e < 1e-5, (KEYS[i], e)
+    # Whole box: the FP64 sums of the FP32 fields.  Mass and momentum change
+    # only by the FP32 rounding of each cell's update (a random walk, far
+    # below 1e-9 of the sums); div B starts at FP32 roundoff and stays there.
+    assert abs(d1[0] - d0[0]) < 1e-9 * d0[0]
+    for i in (1, 2, 3):
+        assert abs(d1[i] - d0[i]) < 1e-9 * float(st[i].double().abs().sum())
+    bdev = max(float(t.abs().max()) for t in st[5:8])
+    assert d1[7] < 1e-4 * bdev * N, (d1[7], bdev)
+    del st
