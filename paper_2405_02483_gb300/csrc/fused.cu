@@ -22,10 +22,10 @@ namespace stg {
 
 // ================================================================ host =====
 
-const char* const KNAMES[K_COUNT] = {"k_lr", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
+const char* const KNAMES[K_COUNT] = {"k_lr_ed", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
-                                     "k_d2flag", "k_cool2"};
+                                     "k_d2flag", "k_cool2", "k_flux_e"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -131,6 +131,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.E0 = (float)p.ref[4];
   k.r0pos = p.ref[0] > 0;
   k.e0 = p.ref[0] > 0 ? (float)(p.ref[4] / p.ref[0]) : 0.f;
+  k.Ec = (float)(p.ref[4] - (double)k.e0 * p.ref[0]);
   for (int d = 0; d < 3; ++d) {
     k.pref[d] = (float)p.ref[1 + d];
     k.Bref[d] = (float)p.ref[5 + d];
@@ -230,6 +231,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
                            F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
                            F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT};
+  need.push_back(F_ED);
   if (k.log_interp) need.push_back(F_LR);
   if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
   if (k.csmag_dl > 0.f) for (int f : {F_SQXY, F_SQYZ, F_SQZX}) need.push_back(f);
@@ -304,7 +306,8 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
   const dim3 gg = grid_cells<N>(g), bb(BX, BY, BZ);
   using NB = typename N::Base;   // kernels without derivatives or lengths
   const float* ls = k.log_interp ? d[F_LR] : f[0];
-  if (k.log_interp) TIMED(K_LR, (k_lr<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], d[F_LR], k, g.n)));
+  TIMED(K_LR, (k_lr_ed<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], f[4], k.log_interp ? d[F_LR] : nullptr,
+                                                       d[F_ED], k, g.n)));
   TIMED(K_VEL, (k_vel<NB><<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
@@ -349,11 +352,13 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
   FluxIn fi = {f[1], f[2], f[3], f[0], f[4], f[5], f[6], f[7], ls, d[F_UX], d[F_UY], d[F_UZ],
                qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],
                qn ? d[F_QXY] : d[F_TXY], qn ? d[F_QYZ] : d[F_TYZ], qn ? d[F_QZX] : d[F_TZX],
-               d[F_JX], d[F_JY], d[F_JZ], d[F_NU], d[F_WC], d[F_WX], d[F_WY], d[F_WZ]};
+               d[F_JX], d[F_JY], d[F_JZ], d[F_NU], d[F_WC], d[F_WX], d[F_WY], d[F_WZ],
+               d[F_ED]};
   FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
                 d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
   TIMED(K_FLUX, (k_flux<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
+  TIMED(K_FLUX_E, (k_flux_e<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
   if (k.inv_tchromo > 0.f || k.corL0 > 0.f)
     TIMED(K_COOL2, (k_cool2<NB><<<gg, bb, 0, s>>>(f[0], f[4], d[F_QT], k, g)));
   STG_CUDA_OK(cudaGetLastError());

@@ -12,6 +12,7 @@ namespace stg {
 struct KPar {
   float ih[3];          // 1/dx, 1/dy, 1/dz
   float r0, E0, e0;     // reference density, energy, e0 = E0/r0
+  float Ec;             // E0 - e0 r0 (E0 when r0 = 0), so that e - e0 = (E' + Ec - e0 r') / (r' + r0)
   float pref[3], Bref[3];
   float gamma, gm1;
   int visc, rm;         // any viscosity; Richtmyer-Morton (else constant)
@@ -53,12 +54,13 @@ enum Fld {
   F_LFX, F_LFY, F_LFZ,                              // ln(rho/r0) interpolated to the faces
   F_LNX, F_LNY, F_LNZ,                              // ln<nu> interpolated to the faces
   F_SQXY, F_SQYZ, F_SQZX,                           // squared off-diagonal strain (edges)
+  F_ED,                                             // e - e0 at centres
   F_COUNT
 };
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
-           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_COUNT };
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {

@@ -337,13 +337,18 @@ template <class T> __device__ __forceinline__ T dens(T t, const KPar& k) {
 // ----------------------------------------------------------------- lr ------
 // ln(rho / r0) = log1p(rho' / r0) of the stored deviation (ln rho if r0 = 0),
 // N::W consecutive cells per thread (n a multiple of N::W).
+// Also the specific internal energy's deviation e - e0 = (E' + Ec - e0 r') /
+// (r' + r0) (Ec = E0 - e0 r0), whose taps the energy fluxes interpolate and
+// differentiate; ln rho only when lr is not null (log interpolation).
 template <class N>
-__global__ void k_lr(const float* __restrict__ rd, float* __restrict__ lr, KPar k, long long n) {
+__global__ void k_lr_ed(const float* __restrict__ rd, const float* __restrict__ Ed,
+                        float* __restrict__ lr, float* __restrict__ ed, KPar k, long long n) {
   using T = typename N::T;
   const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * N::W;
   if (i >= n) return;
   const T r = N::ldp(rd + i);
-  N::stp(lr + i, k.r0pos ? log1pf(r / k.r0) : logf(r));
+  if (lr) N::stp(lr + i, k.r0pos ? log1pf(r / k.r0) : logf(r));
+  N::stp(ed + i, fdiv((N::ldp(Ed + i) + k.Ec) - k.e0 * r, r + k.r0));
 }
 
 // ------------------------------------------------------------- velocity ----
@@ -716,6 +721,7 @@ __global__ void STG_LB(N, STG_MINB_HI) k_edge(
 struct FluxIn {
   const float *px, *py, *pz, *rd, *Ed, *bx, *by, *bz, *ls, *ux, *uy, *uz;
   const float *qxx, *qyy, *qzz, *qxy, *qyz, *qzx, *Jx, *Jy, *Jz, *nu, *wc, *wx, *wy, *wz;
+  const float* ed;   // e - e0 at centres
 };
 struct FluxOut {
   float *mxx, *myy, *mzz, *mxy, *myx, *mxz, *mzx, *myz, *mzy;
@@ -724,9 +730,11 @@ struct FluxOut {
 };
 
 
+// Momentum and induction fluxes: the diagonal and off-diagonal momentum
+// fluxes, the Lorentz products and E = -u x B + eta J.
 template <class N>
-__device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const FluxOut& out,
-                                          const KPar& k) {
+__device__ __forceinline__ void flux_mom_cell(const N& n, const FluxIn& in, const FluxOut& out,
+                                              const KPar& k) {
   using T = typename N::T;
   const float* pr[3] = {in.px, in.py, in.pz};
   const float* uu[3] = {in.ux, in.uy, in.uz};
@@ -787,19 +795,24 @@ __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const Fl
     const T ez = -((ux_y * by_x) - (uy_x * bx_y));
     n.st(out.ez, k.visc ? ez + n.ldw(out.ez) : ez);
   }
-  // Energy fluxes p_d dn(e) - nuE dn(rho nu_dd) dddn(e) at faces.
+}
+
+// Energy fluxes p_d dn(e) - nuE dn(rho nu_dd) dddn(e) at faces, and the
+// source -P div u + Q (+ Newtonian cooling).
+template <class N>
+__device__ __forceinline__ void flux_energy_cell(const N& n, const FluxIn& in,
+                                                 const FluxOut& out, const KPar& k) {
+  using T = typename N::T;
+  const float* pr[3] = {in.px, in.py, in.pz};
   float* go[3] = {out.gx, out.gy, out.gz};
   const float* rd = in.rd;
   const float* Ed = in.Ed;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    auto e_at = [&](int o) { return fdiv(n.lda(Ed, d, o) + k.E0, n.lda(rd, d, o) + k.r0); };
-    T v = (n.ld(pr[d]) + k.pref[d]) * s_dn(e_at);
+    // e = e0 + (e - e0): the interpolation weights sum to one.
+    auto ed_at = [&](int o) { return n.lda(in.ed, d, o); };
+    T v = (n.ld(pr[d]) + k.pref[d]) * (s_dn(ed_at) + k.e0);
     if (k.visc) {
-      auto ed_at = [&](int o) {
-        const T rdo = n.lda(rd, d, o);
-        return fdiv(n.lda(Ed, d, o) - k.e0 * rdo, rdo + k.r0);
-      };
       auto rn_at = [&](int o) {
         const T r = n.lda(rd, d, o) + k.r0;
         const float sp = (N::ZS && d == 2) ? n.hzc_at(o, k) : k.sp[d];
@@ -832,17 +845,26 @@ __device__ __forceinline__ void flux_cell(const N& n, const FluxIn& in, const Fl
   n.st(out.qt, qt);
 }
 
+// Two launches with disjoint outputs; they share only the momenta, the
+// velocities and E as inputs, and each keeps its live values in registers.
 template <class N>
 __global__ void STG_LB_HI(N, STG_MINB) k_flux(FluxIn in, FluxOut out, KPar k, Geo g) {
   N n;
   if (!n.init(g, k)) return;
-  flux_cell(n, in, out, k);
+  flux_mom_cell(n, in, out, k);
+}
+
+template <class N>
+__global__ void STG_LB_HI(N, STG_MINB) k_flux_e(FluxIn in, FluxOut out, KPar k, Geo g) {
+  N n;
+  if (!n.init(g, k)) return;
+  flux_energy_cell(n, in, out, k);
 }
 
 // Chromospheric cooling, eq. (ChromoCool), and coronal thin cooling, eq.
 // (CoronaCool), added to -P div u + Q after k_flux (runs only when one is on):
 //   -rho (rho/rho_bot)^(5/3) (e - <e>)/t_chromo, <e> the plane mean (taken on
-//   e - e0 = (E' - e0 r')/r, where e0 cancels);
+//   e - e0 = (E' + Ec - e0 r')/r, where e0 cancels);
 //   -L0 T^(-1/2) rho^2 exp(-(T/1e4 K)^2), T = Tunit (gamma - 1) e.
 template <class N>
 __global__ void STG_LB(N, STG_MINB) k_cool2(const float* __restrict__ rd,
@@ -855,7 +877,7 @@ __global__ void STG_LB(N, STG_MINB) k_cool2(const float* __restrict__ rd,
   const T r = rdv + k.r0;
   T qt = n.ldw(qtp);
   if (k.inv_tchromo > 0.f) {
-    const T ed = fdiv(Edv - k.e0 * rdv, r);
+    const T ed = fdiv((Edv + k.Ec) - k.e0 * rdv, r);
     const T x = r * k.inv_rhobot;
     const T x53 = x * cbrtf(x) * cbrtf(x);
     qt -= (r * x53) * ((ed - (float)k.emean[n.kz]) * k.inv_tchromo);
@@ -966,7 +988,7 @@ __global__ void k_update8(Upd8 u, float beta, const double* dtp, long long n, in
 
 
 // -------------------------------------------------------- plane means -----
-// Mean over each horizontal plane (constant z) of e - e0 = (E' - e0 r')/r, in
+// Mean over each horizontal plane (constant z) of e - e0 = (E' + Ec - e0 r')/r, in
 // FP64 with a fixed summation order: part[k * nb + b] is block b's sum over
 // its strided share of plane k; k_plane_final sums the nb parts of a plane.
 __global__ void k_plane_part(const float* __restrict__ rd, const float* __restrict__ Ed,
@@ -979,7 +1001,7 @@ __global__ void k_plane_part(const float* __restrict__ rd, const float* __restri
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)nb * blockDim.x)
-    acc += (double)((E[i] - k.e0 * r[i]) / (r[i] + k.r0));
+    acc += (double)(((E[i] + k.Ec) - k.e0 * r[i]) / (r[i] + k.r0));
   sm[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {

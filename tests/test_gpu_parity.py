@@ -428,7 +428,7 @@ def test_run_equals_repeated_steps_and_kernel_timing(S):
     """stagger_run(n) is n stagger_step calls (bitwise, Courant dt on the
     device), and per-kernel timing reports every stage kernel with the launch
     counts of the schedule: per step 3 stages of k_vel, k_tau, k_edge, k_flux,
-    three k_div launches each, one Courant pass (part and final) and one
+    k_flux_e, three k_div launches each, one Courant pass (part and final) and one
     stage-1 update."""
     w, kw = _case("ot3d24_visc_quench")
     sim, refs, dev = make(S, w, kw)
@@ -445,9 +445,39 @@ def test_run_equals_repeated_steps_and_kernel_timing(S):
     sim.timing(False)
     sim.close()
     counts = {k: v[1] for k, v in kt.items()}
-    for name in ("k_vel", "k_tau", "k_edge", "k_flux", "k_nu_raw", "k_nu_max", "k_nu_smooth",
-                 "k_nu_faces"):
+    for name in ("k_vel", "k_tau", "k_edge", "k_flux", "k_flux_e", "k_nu_raw", "k_nu_max",
+                 "k_nu_smooth", "k_nu_faces"):
         assert counts.get(name) == 6, (name, counts)
     assert counts.get("k_div") == 18, counts
     assert counts.get("k_courant") == 4 and counts.get("k_update") == 2, counts
     assert all(v[0] > 0 for v in kt.values())
+
+
+@pytest.mark.parametrize("sc", [0, 1])
+def test_zero_density_reference_with_energy_reference(S, sc):
+    """ref rho = 0 (the stored density is the full value) with ref E != 0: e - e0
+    is then (E' + E0) / rho (no e0), in the energy fluxes, the heat diffusion
+    and the chromospheric plane mean.  RHS (fused, unfused) and three Courant
+    steps against the oracle, with viscosity, the quench and chromospheric
+    cooling on."""
+    w = ragged_state((20, 12, 10))
+    kw = dict(VISC_KW, t_chromo=0.05, rho_bot=0.9, scalar_cells=sc)
+    a = [np.asarray(x) for x in w.fields]
+    refs = [0.0, 0.0, 0.0, 0.0, float(a[4].mean()), 0.0, 0.0, 0.0]
+    sim, refs, dev = make(S, w, kw, refs=refs)
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle_params({k: v for k, v in kw.items() if k != "scalar_cells"})
+    f64 = [torch.tensor(x) for x in w.fields]
+    Fo = [t.numpy() for t in oracle.rhs(f64, g, po)]
+    F = [t.double().cpu().numpy() for t in sim.rhs(dev)]
+    Fu = [t.double().cpu().numpy() for t in sim.rhs_unfused(dev)]
+    assert max(err_scale(F, Fo)) < 2e-4, err_scale(F, Fo)
+    assert max(err_scale(Fu, Fo)) < 2e-4, err_scale(Fu, Fo)
+    fo = f64
+    for _ in range(3):
+        dt = sim.step(dev, None, want_dt=True)
+        fo, dto = oracle.step(fo, g, po, dt=dt)
+        assert abs(dt / dto - 1) < 1e-4, (dt, dto)
+    e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
+    sim.close()
+    assert max(e) < 3e-5, e
