@@ -299,7 +299,7 @@ void fused_release(Fused& F) {
 // Everything up to (not including) the divergence kernel: primitives,
 // viscosity, stresses, edge fields and fluxes of state f.
 template <class N>
-static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
+static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   const Geo& g = F.geo;
   const KPar& k = F.kp;
   float** d = F.fld;
@@ -314,16 +314,16 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
     if (k.csmag_dl > 0.f)
       TIMED(K_STRAIN2, (k_strain2<N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], d[F_SQXY], d[F_SQYZ],
                                                     d[F_SQZX], k, g)));
-    if (k.csmag_dl > 0.f)
-      TIMED(K_NU_RAW, (k_nu_raw<true, N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
-                                                         f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
-                                                         d[F_SQZX], d[F_NV], k, g)));
-    else
-      TIMED(K_NU_RAW, (k_nu_raw<false, N><<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4],
-                                                          f[5], f[6], f[7], d[F_SQXY], d[F_SQYZ],
-                                                          d[F_SQZX], d[F_NV], k, g)));
+    // cfl: this stage's derivative sets the Courant step, and the wave-speed
+    // and <nu> maxima are taken here (cmax[0], cmax[2]).
+    auto knu = k.csmag_dl > 0.f ? (cfl ? k_nu_raw<true, true, N> : k_nu_raw<true, false, N>)
+                                : (cfl ? k_nu_raw<false, true, N> : k_nu_raw<false, false, N>);
+    TIMED(K_NU_RAW, (knu<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6], f[7],
+                                           d[F_SQXY], d[F_SQYZ], d[F_SQZX], d[F_NV],
+                                           cfl ? F.cmax : nullptr, k, g)));
     TIMED(K_NU_MAX, (k_nu_max<NB><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
-    TIMED(K_NU_SMOOTH, (k_nu_smooth<NB><<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], g)));
+    auto ksm = cfl ? k_nu_smooth<NB, true> : k_nu_smooth<NB, false>;
+    TIMED(K_NU_SMOOTH, (ksm<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], F.cmax + 2, g)));
     TIMED(K_NU_FACES, (k_nu_faces<NB><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
   if (k.inv_tchromo > 0.f) {
@@ -365,10 +365,15 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s) {
   return STAGGER_OK;
 }
 
-static int pre_div(Fused& F, float* const f[8], cudaStream_t s) {
+// The Courant maxima are taken inside the stage kernels (wave speed in
+// k_nu_raw, <nu> in k_nu_smooth, rate in the mass and energy k_div) when RM
+// viscosity runs on a uniform mesh; otherwise by k_courant_part.
+static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs; }
+
+static int pre_div(Fused& F, float* const f[8], cudaStream_t s, bool cfl = false) {
   const bool v4 = F.cells4 && aligned16(f, 8);
-  if (F.zs) return v4 ? pre_div_t<Nb4Z>(F, f, s) : pre_div_t<NbZ>(F, f, s);
-  return v4 ? pre_div_t<Nb4>(F, f, s) : pre_div_t<Nb>(F, f, s);
+  if (F.zs) return v4 ? pre_div_t<Nb4Z>(F, f, s, false) : pre_div_t<NbZ>(F, f, s, false);
+  return v4 ? pre_div_t<Nb4>(F, f, s, cfl) : pre_div_t<Nb>(F, f, s, cfl);
 }
 
 static DivIn div_in(Fused& F, float* const f[8]) {
@@ -387,7 +392,7 @@ static DivIn div_in(Fused& F, float* const f[8]) {
 }
 
 static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
-                      float beta, int mode, cudaStream_t s) {
+                      float beta, int mode, cudaStream_t s, bool cfl = false) {
   DivIn di = div_in(F, f);
   float* oo[8];
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
@@ -397,21 +402,25 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   const int nk = 3;
   typedef void (*DivK)(DivIn, float*, float*, float*, float*, float*, float*, float*, float*,
                        float*, float*, float*, float*, float*, float*, float*, float*, float,
-                       float, const double*, int, KPar, Geo);
+                       float, const double*, int, unsigned*, KPar, Geo);
   DivK kern[3];
   if (F.zs) {
-    kern[0] = v4 ? k_div<Nb4Z, 0x0E> : k_div<NbZ, 0x0E>;
-    kern[1] = v4 ? k_div<Nb4Z, 0x11> : k_div<NbZ, 0x11>;
-    kern[2] = v4 ? k_div<Nb4Z, 0xE0> : k_div<NbZ, 0xE0>;
+    kern[0] = v4 ? k_div<Nb4Z, 0x0E, false> : k_div<NbZ, 0x0E, false>;
+    kern[1] = v4 ? k_div<Nb4Z, 0x11, false> : k_div<NbZ, 0x11, false>;
+    kern[2] = v4 ? k_div<Nb4Z, 0xE0, false> : k_div<NbZ, 0xE0, false>;
   } else {
-    kern[0] = v4 ? k_div<Nb4, 0x0E> : k_div<Nb, 0x0E>;
-    kern[1] = v4 ? k_div<Nb4, 0x11> : k_div<Nb, 0x11>;
-    kern[2] = v4 ? k_div<Nb4, 0xE0> : k_div<Nb, 0xE0>;
+    kern[0] = v4 ? k_div<Nb4, 0x0E, false> : k_div<Nb, 0x0E, false>;
+    if (cfl)   // and the rate maximum (cmax[1])
+      kern[1] = v4 ? k_div<Nb4, 0x11, true> : k_div<Nb, 0x11, true>;
+    else
+      kern[1] = v4 ? k_div<Nb4, 0x11, false> : k_div<Nb, 0x11, false>;
+    kern[2] = v4 ? k_div<Nb4, 0xE0, false> : k_div<Nb, 0xE0, false>;
   }
   for (int i = 0; i < nk; ++i)
     TIMED(K_DIV, (kern[i]<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
                                             oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6],
-                                            oo[7], alpha, beta, F.dt_dev, mode, F.kp, F.geo)));
+                                            oo[7], alpha, beta, F.dt_dev, mode, F.cmax + 1,
+                                            F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -429,10 +438,12 @@ static void courant_part(Fused& F, float* const f[8], cudaStream_t s) {
                        F.q[0], F.q[4], F.fld[F_NU], F.cmax, F.kp, F.geo)));
 }
 
-static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s) {
-  // Uses the primitives and <nu> that pre_div left for this state and q = F(f).
+static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s, bool fused) {
+  // Uses the primitives and <nu> that pre_div left for this state and q = F(f);
+  // with fused, the stage kernels already took the three maxima.
   const bool v4 = F.cells4 && aligned16(f, 8);
-  if (F.zs) {
+  if (fused) {
+  } else if (F.zs) {
     if (v4) courant_part<Nb4Z>(F, f, s); else courant_part<NbZ>(F, f, s);
   } else {
     if (v4) courant_part<Nb4>(F, f, s); else courant_part<Nb>(F, f, s);
@@ -453,14 +464,15 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
   float* const* st_in[3] = {A, B, C};
   float* const* st_out[3] = {B, C, A};
   for (int stg = 0; stg < 3; ++stg) {
-    int rc = pre_div(F, st_in[stg], s);
+    const bool cfl = stg == 0 && dt <= 0 && cfl_fused(F);
+    int rc = pre_div(F, st_in[stg], s, cfl);
     if (rc) return rc;
     float alpha = (float)RK_ALPHA[stg], beta = (float)RK_BETA[stg];
     if (stg == 0 && dt <= 0) {
       // Courant step from the state and its stage-1 derivative, then update.
-      rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0.f, 0, s);
+      rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0.f, 0, s, cfl);
       if (rc) return rc;
-      courant_to_dev(F, st_in[0], s);
+      courant_to_dev(F, st_in[0], s, cfl);
       Upd8 u;
       int vec = (F.geo.n % 4) == 0;
       for (int c = 0; c < 8; ++c) {
@@ -486,11 +498,12 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
 }
 
 int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s) {
-  int rc = pre_div(F, f, s);
+  const bool cfl = cfl_fused(F);
+  int rc = pre_div(F, f, s, cfl);
   if (rc) return rc;
-  rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s);
+  rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s, cfl);
   if (rc) return rc;
-  courant_to_dev(F, f, s);
+  courant_to_dev(F, f, s, cfl);
   double h[4];
   STG_CUDA_OK(cudaMemcpyAsync(h, F.dt_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
   STG_CUDA_OK(cudaStreamSynchronize(s));

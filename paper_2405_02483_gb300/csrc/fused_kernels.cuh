@@ -407,39 +407,74 @@ __global__ void STG_LB(N, STG_MINB) k_strain2(
   n.st(szx2, szx * szx);
 }
 
+// -------------------------------------------------------------- Courant ----
+// Non-negative maxima kept as the bits of a float: for x >= 0 (and +inf) the
+// unsigned order of the bit patterns is the numeric order.  NaN maps to +inf
+// (it must win the maximum) and anything below +0, -0 included, to +0.
+__device__ __forceinline__ unsigned max_bits(float v) {
+  if (!(v == v)) v = INFINITY;
+  return __float_as_uint(v > 0.f ? v : 0.f);
+}
+__device__ __forceinline__ unsigned max_bits(const F4& v) {
+  return max(max(max_bits(v.v[0]), max_bits(v.v[1])), max(max_bits(v.v[2]), max_bits(v.v[3])));
+}
+// |u_perp|^2 = u^2 - (u.B)^2 / B^2, and u^2 where B = 0.
+__device__ __forceinline__ float uperp2(float u2, float ub, float B2) {
+  return B2 > 0.f ? u2 - ub * ub / B2 : u2;
+}
+__device__ __forceinline__ F4 uperp2(const F4& u2, const F4& ub, const F4& B2) {
+  return F4(uperp2(u2.v[0], ub.v[0], B2.v[0]), uperp2(u2.v[1], ub.v[1], B2.v[1]),
+            uperp2(u2.v[2], ub.v[2], B2.v[2]), uperp2(u2.v[3], ub.v[3], B2.v[3]));
+}
+
+// Maximum of v over the thread block into *dst (atomic on the float bits of
+// max_bits).  Every thread of the block calls it once, at the same point.
+__device__ __forceinline__ void block_max_to(unsigned v, unsigned* dst) {
+  __shared__ unsigned sm[BX * BY * BZ / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) sm[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned m = 0u;
+    for (int w = 0; w < BX * BY * BZ / 32; ++w) m = max(m, sm[w]);
+    atomicMax(dst, m);
+  }
+}
+
 // eq. (RMnu): nu1 |u| + nu3 (c_s + c_A) + nu2 dl_min max(0, -div u), centred.
-template <bool SMAG, class N>
-__global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : STG_MINB)
-                                                          : (SMAG ? STG_MINB : STG_MINB_HI)) k_nu_raw(
-    const float* __restrict__ ux,
-                                                const float* __restrict__ uy,
-                                                const float* __restrict__ uz,
-                                                const float* __restrict__ rd,
-                                                const float* __restrict__ Ed,
-                                                const float* __restrict__ bx,
-                                                const float* __restrict__ by,
-                                                const float* __restrict__ bz,
-                                                const float* __restrict__ sqxy,
-                                                const float* __restrict__ sqyz,
-                                                const float* __restrict__ sqzx,
-                                                float* __restrict__ nv, KPar k, Geo g) {
-  N n;
-  if (!n.init(g, k)) return;
+// With CW (the stage whose derivative sets the Courant step) it also reduces
+// the wave speed c_s + c_A + |u_perp| of the same centred u and B into *cw.
+template <bool SMAG, bool CW, class N>
+__device__ __forceinline__ unsigned nu_raw_cell(
+    const N& n, const float* __restrict__ ux, const float* __restrict__ uy,
+    const float* __restrict__ uz, const float* __restrict__ rd, const float* __restrict__ Ed,
+    const float* __restrict__ bx, const float* __restrict__ by, const float* __restrict__ bz,
+    const float* __restrict__ sqxy, const float* __restrict__ sqyz,
+    const float* __restrict__ sqzx, float* __restrict__ nv, const KPar& k) {
   using T = typename N::T;
   T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
   const T sxx = s_du(AX(ux, 0), n.ju(0, k)), syy = s_du(AX(uy, 1), n.ju(1, k)),
               szz = s_du(AX(uz, 2), n.ju(2, k));
   T divu = sxx + syy + szz;
   T nu = 0.f;
-  if (k.nu1 > 0.f) nu = k.nu1 * sqrtf(ucx * ucx + ucy * ucy + ucz * ucz);
-  if (k.nu3 > 0.f) {
+  const T u2 = ucx * ucx + ucy * ucy + ucz * ucz;
+  if (k.nu1 > 0.f) nu = k.nu1 * sqrtf(u2);
+  unsigned wbits = 0u;
+  if (CW || k.nu3 > 0.f) {
     T bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
           bcz = s_up(AX(bz, 2)) + k.Bref[2];
     T r = n.ld(rd) + k.r0;
     T P = k.gm1 * (n.ld(Ed) + k.E0);
     T cs = sqrtf(k.gamma * P / r);
-    T ca = sqrtf((bcx * bcx + bcy * bcy + bcz * bcz) / r);
-    nu += k.nu3 * (cs + ca);
+    T B2 = bcx * bcx + bcy * bcy + bcz * bcz;
+    T ca = sqrtf(B2 / r);
+    if (k.nu3 > 0.f) nu += k.nu3 * (cs + ca);
+    if (CW) {
+      const T ub = ucx * bcx + ucy * bcy + ucz * bcz;
+      wbits = max_bits(cs + ca + sqrtf(fmaxf(uperp2(u2, ub, B2), T(0.f))));
+    }
   }
   // dl_min: of the mesh, or of the cell on a stretched z (R19).
   const float nu2dl = N::ZS ? k.nu2 * n.dlc(k) : k.nu2dl;
@@ -451,6 +486,27 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : 
     nu += (N::ZS ? k.csmag * n.dlc(k) : k.csmag_dl) * sqrtf(2.f * fmaxf(s2, 0.f));
   }
   n.st(nv, nu);
+  return wbits;
+}
+
+template <bool SMAG, bool CW, class N>
+__global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : STG_MINB)
+                                                          : (SMAG ? STG_MINB : STG_MINB_HI)) k_nu_raw(
+    const float* __restrict__ ux, const float* __restrict__ uy, const float* __restrict__ uz,
+    const float* __restrict__ rd, const float* __restrict__ Ed, const float* __restrict__ bx,
+    const float* __restrict__ by, const float* __restrict__ bz, const float* __restrict__ sqxy,
+    const float* __restrict__ sqyz, const float* __restrict__ sqzx, float* __restrict__ nv,
+    unsigned* cw, KPar k, Geo g) {
+  N n;
+  const bool in = n.init(g, k);
+  if constexpr (!CW) {
+    if (in) nu_raw_cell<SMAG, false>(n, ux, uy, uz, rd, Ed, bx, by, bz, sqxy, sqyz, sqzx, nv, k);
+  } else {
+    const unsigned m =
+        in ? nu_raw_cell<SMAG, true>(n, ux, uy, uz, rd, Ed, bx, by, bz, sqxy, sqyz, sqzx, nv, k)
+           : 0u;
+    block_max_to(m, cw);
+  }
 }
 
 // 3-cell max along x, y and z: the maximum over the 3x3x3 neighbourhood.
@@ -471,27 +527,36 @@ __global__ void STG_LB(N, STG_MINB) k_nu_max(const float* __restrict__ a,
 }
 
 // 3-cell mean along x, y and z (the 3x3x3 mean) and its logarithm.
-template <class N>
+// With CW (the stage whose derivative sets the Courant step) also the
+// maximum of <nu> into *cnu.
+template <class N, bool CW>
 __global__ void STG_LB(N, STG_MINB_HI) k_nu_smooth(const float* __restrict__ a,
                                                    float* __restrict__ nu,
-                                                   float* __restrict__ lnu, Geo g) {
+                                                   float* __restrict__ lnu, unsigned* cnu,
+                                                   Geo g) {
   N n;
-  if (!n.init(g)) return;
-  using T = typename N::T;
-  T sz = 0.f;
+  const bool in = n.init(g);
+  if (!CW && !in) return;
+  unsigned m = 0u;
+  if (in) {
+    using T = typename N::T;
+    T sz = 0.f;
 #pragma unroll
-  for (int dz = -1; dz <= 1; ++dz) {
-    T sy = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      T sy = 0.f;
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      T sx = n.ldat(a, -1, dy, dz) + n.ldat(a, 0, dy, dz) + n.ldat(a, 1, dy, dz);
-      sy += sx;
+      for (int dy = -1; dy <= 1; ++dy) {
+        T sx = n.ldat(a, -1, dy, dz) + n.ldat(a, 0, dy, dz) + n.ldat(a, 1, dy, dz);
+        sy += sx;
+      }
+      sz += sy;
     }
-    sz += sy;
+    T v = sz * (1.f / 27.f);
+    n.st(nu, v);
+    n.st(lnu, logf(fmaxf(v, 1e-30f)));
+    if (CW) m = max_bits(v);
   }
-  T v = sz * (1.f / 27.f);
-  n.st(nu, v);
-  n.st(lnu, logf(fmaxf(v, 1e-30f)));
+  if constexpr (CW) block_max_to(m, cnu);
 }
 
 // ln<nu> interpolated to the three faces (first half of the edge values).
@@ -903,20 +968,18 @@ struct DivIn {
 // formed.  mode 0: write F to q only; 1: also update with dt from *dtp.
 // Launched as three kernels (momentum; mass and energy; induction), whose
 // inputs are disjoint, at 4 blocks per SM: fewer live registers per launch.
-template <class N, int M>
-__global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
-                                          float* q4, float* q5, float* q6, float* q7,
-                                          float* o0, float* o1, float* o2, float* o3,
-                                          float* o4, float* o5, float* o6, float* o7,
-                                          float alpha, float beta, const double* dtp,
-                                          int mode, KPar k, Geo g) {
-  N n;
-  if (!n.init(g, k)) return;
+// With CR (mass and energy, the stage whose derivative sets the Courant step)
+// the launch also reduces max(|dr/dt| / r, |dE/dt| / E) into *cr.
+template <class N, int M, bool CR>
+__device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float* const* qs,
+                                             float* const* os, float alpha, float beta,
+                                             const double* dtp, int mode, const KPar& k) {
   using T = typename N::T;
-  float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
-  float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
   const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
+  T F0 = 0.f, F4 = 0.f;
   auto fin = [&](int c, const T& F) {
+    if (CR && c == 0) F0 = F;
+    if (CR && c == 4) F4 = F;
     const T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F : F;
     n.st(qs[c], qq);
     if (mode) n.st(os[c], n.ld(in.f[c]) + bdt * qq);
@@ -957,6 +1020,28 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
   if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k))));
   if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), n.ju(2, k)) - s_du(AX(in.Ez, 0), n.ju(0, k))));
   if (M & 128) fin(7, -(s_du(AX(in.Ey, 0), n.ju(0, k)) - s_du(AX(in.Ex, 1), n.ju(1, k))));
+  if (!CR) return 0u;
+  const T r = n.ld(in.f[0]) + k.r0, E = n.ld(in.f[4]) + k.E0;
+  return max_bits(fmaxf(fabsf(F0) / r, fabsf(F4) / E));
+}
+
+template <class N, int M, bool CR>
+__global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
+                                          float* q4, float* q5, float* q6, float* q7,
+                                          float* o0, float* o1, float* o2, float* o3,
+                                          float* o4, float* o5, float* o6, float* o7,
+                                          float alpha, float beta, const double* dtp,
+                                          int mode, unsigned* cr, KPar k, Geo g) {
+  N n;
+  const bool inside = n.init(g, k);
+  float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
+  float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
+  if constexpr (!CR) {
+    if (inside) div_cell<N, M, false>(n, in, qs, os, alpha, beta, dtp, mode, k);
+  } else {
+    const unsigned m = inside ? div_cell<N, M, true>(n, in, qs, os, alpha, beta, dtp, mode, k) : 0u;
+    block_max_to(m, cr);
+  }
 }
 
 __global__ void k_set_dt(double* dtp, double dt) { dtp[0] = dt; }
@@ -1020,25 +1105,6 @@ __global__ void k_plane_final(const double* part, int nb, double* mean, Geo g) {
 }
 
 // -------------------------------------------------------------- Courant ----
-// Non-negative maxima kept as the bits of a float: for x >= 0 (and +inf) the
-// unsigned order of the bit patterns is the numeric order.  NaN maps to +inf
-// (it must win the maximum) and anything below +0, -0 included, to +0.
-__device__ __forceinline__ unsigned max_bits(float v) {
-  if (!(v == v)) v = INFINITY;
-  return __float_as_uint(v > 0.f ? v : 0.f);
-}
-__device__ __forceinline__ unsigned max_bits(const F4& v) {
-  return max(max(max_bits(v.v[0]), max_bits(v.v[1])), max(max_bits(v.v[2]), max_bits(v.v[3])));
-}
-// |u_perp|^2 = u^2 - (u.B)^2 / B^2, and u^2 where B = 0.
-__device__ __forceinline__ float uperp2(float u2, float ub, float B2) {
-  return B2 > 0.f ? u2 - ub * ub / B2 : u2;
-}
-__device__ __forceinline__ F4 uperp2(const F4& u2, const F4& ub, const F4& B2) {
-  return F4(uperp2(u2.v[0], ub.v[0], B2.v[0]), uperp2(u2.v[1], ub.v[1], B2.v[1]),
-            uperp2(u2.v[2], ub.v[2], B2.v[2]), uperp2(u2.v[3], ub.v[3], B2.v[3]));
-}
-
 // Per-cell wave speed c_s + c_A + |u_perp|, rate max(|dr/dt|/r, |dE/dt|/E)
 // and <nu>; their maxima over the mesh into cmax[0..2] (float bits, atomic).
 template <class N>
