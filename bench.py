@@ -48,6 +48,7 @@ REF_N = 96                      # per-step sample grid of the reference (oracle)
 # dfdt) and write 16; k_update is the stage-1 update of all 8 fields (f, dfdt
 # in; f out).
 KERNEL_ARRAYS = {"k_lr_ed": 4, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
+                 "k_nu_maxsmooth": 3,
                  "k_nu_faces": 4, "k_tau": 26, "k_edge": 28, "k_flux": 40, "k_flux_e": 17,
                  "k_div": (33 + 54 + 54) / 3.0, "k_update": 24}
 # DRAM bytes (read + write) per cell per launch from one ncu capture of each

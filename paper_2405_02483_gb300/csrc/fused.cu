@@ -25,7 +25,7 @@ namespace stg {
 const char* const KNAMES[K_COUNT] = {"k_lr_ed", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
-                                     "k_d2flag", "k_cool2", "k_flux_e"};
+                                     "k_d2flag", "k_cool2", "k_flux_e", "k_nu_maxsmooth"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -321,9 +321,17 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
     TIMED(K_NU_RAW, (knu<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6], f[7],
                                            d[F_SQXY], d[F_SQYZ], d[F_SQZX], d[F_NV],
                                            cfl ? F.cmax : nullptr, k, g)));
-    TIMED(K_NU_MAX, (k_nu_max<NB><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
-    auto ksm = cfl ? k_nu_smooth<NB, true> : k_nu_smooth<NB, false>;
-    TIMED(K_NU_SMOOTH, (ksm<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], F.cmax + 2, g)));
+    if (N::W == 4) {
+      // One z-marching pass for the 3x3x3 max and mean (four-cell layout).
+      const dim3 gm((unsigned)((g.nx + 127) / 128), (unsigned)((g.ny + NUZ_TY - 1) / NUZ_TY),
+                    (unsigned)((g.nz + NUZ_ZC - 1) / NUZ_ZC));
+      auto kms = cfl ? k_nu_maxsmooth<true> : k_nu_maxsmooth<false>;
+      TIMED(K_NU_MS, (kms<<<gm, dim3(32, NUZ_TY), 0, s>>>(d[F_NV], d[F_NU], d[F_LNU], F.cmax + 2, g)));
+    } else {
+      TIMED(K_NU_MAX, (k_nu_max<NB><<<gg, bb, 0, s>>>(d[F_NV], d[F_NM], g)));
+      auto ksm = cfl ? k_nu_smooth<NB, true> : k_nu_smooth<NB, false>;
+      TIMED(K_NU_SMOOTH, (ksm<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], F.cmax + 2, g)));
+    }
     TIMED(K_NU_FACES, (k_nu_faces<NB><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
   if (k.inv_tchromo > 0.f) {

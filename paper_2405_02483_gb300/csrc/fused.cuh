@@ -60,7 +60,7 @@ enum Fld {
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
-           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_COUNT };
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_NU_MS, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {

@@ -427,10 +427,12 @@ __device__ __forceinline__ F4 uperp2(const F4& u2, const F4& ub, const F4& B2) {
             uperp2(u2.v[2], ub.v[2], B2.v[2]), uperp2(u2.v[3], ub.v[3], B2.v[3]));
 }
 
-// Maximum of v over the thread block into *dst (atomic on the float bits of
-// max_bits).  Every thread of the block calls it once, at the same point.
+// Maximum of v over the thread block (NT threads) into *dst (atomic on the
+// float bits of max_bits).  Every thread of the block calls it once, at the
+// same point.
+template <int NT = BX * BY * BZ>
 __device__ __forceinline__ void block_max_to(unsigned v, unsigned* dst) {
-  __shared__ unsigned sm[BX * BY * BZ / 32];
+  __shared__ unsigned sm[NT / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
@@ -438,7 +440,7 @@ __device__ __forceinline__ void block_max_to(unsigned v, unsigned* dst) {
   __syncthreads();
   if (tid == 0) {
     unsigned m = 0u;
-    for (int w = 0; w < BX * BY * BZ / 32; ++w) m = max(m, sm[w]);
+    for (int w = 0; w < NT / 32; ++w) m = max(m, sm[w]);
     atomicMax(dst, m);
   }
 }
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? (SMAG ? STG_MINB4 : 
     const unsigned m =
         in ? nu_raw_cell<SMAG, true>(n, ux, uy, uz, rd, Ed, bx, by, bz, sqxy, sqyz, sqzx, nv, k)
            : 0u;
-    block_max_to(m, cw);
+    block_max_to<>(m, cw);
   }
 }
 
@@ -556,7 +558,102 @@ __global__ void STG_LB(N, STG_MINB_HI) k_nu_smooth(const float* __restrict__ a,
     n.st(lnu, logf(fmaxf(v, 1e-30f)));
     if (CW) m = max_bits(v);
   }
-  if constexpr (CW) block_max_to(m, cnu);
+  if constexpr (CW) block_max_to<>(m, cnu);
+}
+
+// <nu> = smooth3(max3(nu_raw)) and ln<nu> in one pass that marches along z
+// (four-cell threads, nx % 4 == 0, 16-byte aligned arrays).  A thread owns
+// the four x-cells i0..i0+3 of row j over NUZ_ZC consecutive planes.  Per raw
+// plane it reads rows j-2..j+2 (three 16-byte chunks each) once, and keeps in
+// registers the in-plane maxima of the last three planes and the in-plane
+// sums of the last three, so each output plane costs one raw plane of loads.
+// The maxima are exact and the sums keep k_nu_smooth's order (x, then y,
+// then z), so the result equals k_nu_max followed by k_nu_smooth bit for bit.
+// With CW also the maximum of <nu> into *cnu (the Courant diffusion limit).
+#ifndef NUZ_TY
+#define NUZ_TY 4
+#endif
+#ifndef NUZ_ZC
+#define NUZ_ZC 32
+#endif
+template <bool CW>
+__global__ void __launch_bounds__(32 * NUZ_TY) k_nu_maxsmooth(const float* __restrict__ nv,
+                                                              float* __restrict__ nu,
+                                                              float* __restrict__ lnu,
+                                                              unsigned* cnu, Geo g) {
+  const int i0 = (blockIdx.x * 32 + threadIdx.x) * 4;
+  const int j = blockIdx.y * NUZ_TY + threadIdx.y;
+  const int z0 = blockIdx.z * NUZ_ZC;
+  const int z1 = min(z0 + NUZ_ZC, g.nz);
+  unsigned mb = 0u;
+  if (i0 < g.nx && j < g.ny) {
+    const int xl = wrap(i0 - 4, g.nx), xr = wrap(i0 + 4, g.nx);
+    long long yo[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) yo[r] = (long long)wrap(j + r - 2, g.ny) * g.sy;
+    // m[t][r][x]: in-plane 3x3 maxima at planes p-2, p-1, p (t = 0, 1, 2),
+    // rows j-1..j+1, x positions i0-1..i0+4.  s[t][l]: in-plane sums of the
+    // 3x3 maxima at planes p-3, p-2, p-1 for the four cells.
+    float m[3][3][6] = {}, s[3][4] = {};
+    for (int p = z0 - 2; p <= z1 + 1; ++p) {
+      const long long po = (long long)wrap(p, g.nz) * g.sz;
+      float mx[5][6];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const float* row = nv + po + yo[r];
+        const float4 a = *reinterpret_cast<const float4*>(row + xl);
+        const float4 b = *reinterpret_cast<const float4*>(row + i0);
+        const float4 c = *reinterpret_cast<const float4*>(row + xr);
+        // positions i0-2 .. i0+5
+        const float v[8] = {a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+#pragma unroll
+        for (int x = 0; x < 6; ++x) mx[r][x] = fmaxf(fmaxf(v[x], v[x + 1]), v[x + 2]);
+      }
+#pragma unroll
+      for (int x = 0; x < 6; ++x) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          m[0][r][x] = m[1][r][x];
+          m[1][r][x] = m[2][r][x];
+          m[2][r][x] = fmaxf(fmaxf(mx[r][x], mx[r + 1][x]), mx[r + 2][x]);
+        }
+      }
+      if (p < z0) continue;
+      // Plane p-1: the 3x3x3 maxima, then their sum over x and y.
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        s[0][l] = s[1][l];
+        s[1][l] = s[2][l];
+        float sy = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          float M[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            M[d] = fmaxf(fmaxf(m[0][r][l + d], m[1][r][l + d]), m[2][r][l + d]);
+          sy += (M[0] + M[1]) + M[2];
+        }
+        s[2][l] = sy;
+      }
+      if (p < z0 + 2) continue;
+      // Output plane p-2.
+      const long long o = (long long)(p - 2) * g.sz + (long long)j * g.sy + i0;
+      float4 vv, lv;
+      float* vp = &vv.x;
+      float* lp = &lv.x;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float sz = (s[0][l] + s[1][l]) + s[2][l];
+        const float v = sz * (1.f / 27.f);
+        vp[l] = v;
+        lp[l] = logf(fmaxf(v, 1e-30f));
+        if (CW) mb = max(mb, max_bits(v));
+      }
+      *reinterpret_cast<float4*>(nu + o) = vv;
+      *reinterpret_cast<float4*>(lnu + o) = lv;
+    }
+  }
+  if constexpr (CW) block_max_to<32 * NUZ_TY>(mb, cnu);
 }
 
 // ln<nu> interpolated to the three faces (first half of the edge values).
@@ -1040,7 +1137,7 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
     if (inside) div_cell<N, M, false>(n, in, qs, os, alpha, beta, dtp, mode, k);
   } else {
     const unsigned m = inside ? div_cell<N, M, true>(n, in, qs, os, alpha, beta, dtp, mode, k) : 0u;
-    block_max_to(m, cr);
+    block_max_to<>(m, cr);
   }
 }
 
