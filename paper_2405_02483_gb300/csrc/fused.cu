@@ -82,6 +82,18 @@ template <class N> static dim3 grid_cells(const Geo& g) {
               (unsigned)((g.nz + BZ - 1) / BZ));
 }
 
+// Thread-block shapes of BX * BY * BZ threads, chosen per kernel by A/B runs
+// on GB300 at 512^3: long in z (32 x 1 x 8) for k_tau, k_edge, k_flux and the
+// divergences, long in y (32 x 8 x 1) for the energy fluxes, k_vel, k_nu_raw
+// and k_nu_faces; the default 32 x 2 x 4 for the rest.
+static_assert(BY * BZ == 8, "the per-kernel shapes keep the launch bounds' thread count");
+static const dim3 BB_Z8(BX, 1, 8);
+static const dim3 BB_Y8(BX, 8, 1);
+template <class N> static dim3 grid_for(const Geo& g, dim3 b) {
+  return dim3((unsigned)((g.nx + b.x * N::W - 1) / (b.x * N::W)), (unsigned)((g.ny + b.y - 1) / b.y),
+              (unsigned)((g.nz + b.z - 1) / b.z));
+}
+
 // Four-cell threads need 16-byte aligned arrays (the workspace always is).
 static bool aligned16(float* const* a, int n) {
   uintptr_t u = 0;
@@ -304,11 +316,12 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   const KPar& k = F.kp;
   float** d = F.fld;
   const dim3 gg = grid_cells<N>(g), bb(BX, BY, BZ);
+  const dim3 gz8 = grid_for<N>(g, BB_Z8), gy8 = grid_for<N>(g, BB_Y8);
   using NB = typename N::Base;   // kernels without derivatives or lengths
   const float* ls = k.log_interp ? d[F_LR] : f[0];
   TIMED(K_LR, (k_lr_ed<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], f[4], k.log_interp ? d[F_LR] : nullptr,
                                                        d[F_ED], k, g.n)));
-  TIMED(K_VEL, (k_vel<NB><<<gg, bb, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
+  TIMED(K_VEL, (k_vel<NB><<<gy8, BB_Y8, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
     if (k.csmag_dl > 0.f)
@@ -318,7 +331,7 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
     // and <nu> maxima are taken here (cmax[0], cmax[2]).
     auto knu = k.csmag_dl > 0.f ? (cfl ? k_nu_raw<true, true, N> : k_nu_raw<true, false, N>)
                                 : (cfl ? k_nu_raw<false, true, N> : k_nu_raw<false, false, N>);
-    TIMED(K_NU_RAW, (knu<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6], f[7],
+    TIMED(K_NU_RAW, (knu<<<gy8, BB_Y8, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], f[4], f[5], f[6], f[7],
                                            d[F_SQXY], d[F_SQYZ], d[F_SQZX], d[F_NV],
                                            cfl ? F.cmax : nullptr, k, g)));
     if (N::W == 4) {
@@ -332,7 +345,7 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
       auto ksm = cfl ? k_nu_smooth<NB, true> : k_nu_smooth<NB, false>;
       TIMED(K_NU_SMOOTH, (ksm<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], F.cmax + 2, g)));
     }
-    TIMED(K_NU_FACES, (k_nu_faces<NB><<<gg, bb, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
+    TIMED(K_NU_FACES, (k_nu_faces<NB><<<gy8, BB_Y8, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
   }
   if (k.inv_tchromo > 0.f) {
     TIMED(K_COOL2, (k_plane_part<<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
@@ -343,14 +356,14 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   if (k.d2div)
     TIMED(K_D2FLAG, (k_d2flag<NB><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
   auto ktau = k.d2div ? k_tau<N, true> : k_tau<N, false>;
-  TIMED(K_TAU, (ktau<<<gg, bb, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
+  TIMED(K_TAU, (ktau<<<gz8, BB_Z8, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
                                        d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
                                        f[6], f[7], d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY],
                                        d[F_TYZ], d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
                                        d[F_JY], d[F_JZ], F.d2flag, k, g)));
   auto kedge = k.d2div ? k_edge<N, true> : k_edge<N, false>;
   if (k.visc)
-    TIMED(K_EDGE, (kedge<<<gg, bb, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
+    TIMED(K_EDGE, (kedge<<<gz8, BB_Z8, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
                                            d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
                                            d[F_JY], d[F_JZ], d[F_UX], d[F_UY], d[F_UZ],
                                            d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
@@ -365,8 +378,8 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
                 d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
-  TIMED(K_FLUX, (k_flux<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
-  TIMED(K_FLUX_E, (k_flux_e<N><<<gg, bb, 0, s>>>(fi, fo, k, g)));
+  TIMED(K_FLUX, (k_flux<N><<<gz8, BB_Z8, 0, s>>>(fi, fo, k, g)));
+  TIMED(K_FLUX_E, (k_flux_e<N><<<gy8, BB_Y8, 0, s>>>(fi, fo, k, g)));
   if (k.inv_tchromo > 0.f || k.corL0 > 0.f)
     TIMED(K_COOL2, (k_cool2<NB><<<gg, bb, 0, s>>>(f[0], f[4], d[F_QT], k, g)));
   STG_CUDA_OK(cudaGetLastError());
@@ -405,7 +418,7 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   float* oo[8];
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
   const bool v4 = F.cells4 && aligned16(f, 8) && aligned16(q, 8) && aligned16(oo, 8);
-  const dim3 gg = v4 ? grid_cells<Nb4>(F.geo) : grid_cells<Nb>(F.geo), bb(BX, BY, BZ);
+  const dim3 bb = BB_Z8, gg = v4 ? grid_for<Nb4>(F.geo, bb) : grid_for<Nb>(F.geo, bb);
   // Momentum; mass and energy; induction (disjoint inputs, one kernel each).
   const int nk = 3;
   typedef void (*DivK)(DivIn, float*, float*, float*, float*, float*, float*, float*, float*,
