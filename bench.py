@@ -54,8 +54,10 @@ KERNEL_ARRAYS = {"k_lr_ed": 4, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_
 # DRAM bytes (read + write) per cell per launch from one ncu capture of each
 # kernel on the same workload at 192^3 (traffic grows with the cells).  Only
 # kernels unchanged since their capture.
-NCU_TRAFFIC_PER_CELL = {"k_flux": 1105.0e6 / 192 ** 3, "k_flux_e": 499.5e6 / 192 ** 3,
-                        "k_edge": 762.2e6 / 192 ** 3, "k_tau": 707.4e6 / 192 ** 3}
+NCU_TRAFFIC_PER_CELL = {"k_flux": 1112.1e6 / 192 ** 3, "k_flux_e": 500.6e6 / 192 ** 3,
+                        "k_edge": 762.6e6 / 192 ** 3, "k_tau": 710.2e6 / 192 ** 3,
+                        # per unit of three launches, the mean over the three stages
+                        "k_div": (941.4e6 + 2 * 1539.8e6) / 3 / 192 ** 3}
 # Launches that together form one unit of KERNEL_ARRAYS.
 LAUNCHES_PER_UNIT = {"k_div": 3}
 
