@@ -57,7 +57,7 @@ KERNEL_ARRAYS = {"k_lr_ed": 4, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_
 NCU_TRAFFIC_PER_CELL = {"k_flux": 1112.1e6 / 192 ** 3, "k_flux_e": 500.6e6 / 192 ** 3,
                         "k_edge": 762.6e6 / 192 ** 3, "k_tau": 710.2e6 / 192 ** 3,
                         # per unit of three launches, the mean over the three stages
-                        "k_div": (941.4e6 + 2 * 1539.8e6) / 3 / 192 ** 3}
+                        "k_div": (940.6e6 + 2 * 1539.8e6) / 3 / 192 ** 3}
 # Launches that together form one unit of KERNEL_ARRAYS.
 LAUNCHES_PER_UNIT = {"k_div": 3}
 
