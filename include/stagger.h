@@ -49,7 +49,8 @@ enum {
 typedef struct stagger_ctx stagger_ctx;  /* opaque, library-owned */
 
 typedef struct {
-  int nx, ny, nz;          /* cells per axis, each >= 1; all axes periodic     */
+  int nx, ny, nz;          /* cells per axis, each >= 1; all axes periodic;
+                            * ny, nz <= 65535 and nx*ny*nz < 2^31 (EINVAL)    */
   double dx, dy, dz;       /* uniform spacings, > 0 (dz is that of a uniform z;
                             * stagger_params.zc/zf give a stretched one)      */
 } stagger_grid;

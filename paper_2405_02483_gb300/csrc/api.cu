@@ -70,6 +70,8 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return STAGGER_EINVAL;
   long long n = (long long)g->nx * g->ny * g->nz;
   if (n >= (1LL << 31)) return STAGGER_EINVAL;  // 32-bit cell offsets in the kernels
+  // Launch grids put y and z (over 1 to 8 cells a block) on the 65535-block axes.
+  if (g->ny > 65535 || g->nz > 65535) return STAGGER_EINVAL;
   if (!(p->gamma > 1.0)) return STAGGER_EINVAL;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu3 < 0 || p->nu_const < 0 || p->nuE < 0 || p->nuB < 0 ||
       p->csmag < 0)

@@ -387,8 +387,8 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
 }
 
 // The Courant maxima are taken inside the stage kernels (wave speed in
-// k_nu_raw, <nu> in k_nu_smooth, rate in the mass and energy k_div) when RM
-// viscosity runs on a uniform mesh; otherwise by k_courant_part.
+// k_nu_raw, <nu> in k_nu_maxsmooth or k_nu_smooth, rate in the mass and energy
+// k_div) when RM viscosity runs on a uniform mesh; otherwise by k_courant_part.
 static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs; }
 
 static int pre_div(Fused& F, float* const f[8], cudaStream_t s, bool cfl = false) {

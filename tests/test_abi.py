@@ -44,7 +44,8 @@ def test_create_rejects_bad_arguments_without_gpu(S):
     h = ctypes.c_void_p()
     p = S.default_params()
     bad_grids = [S.Grid(0, 8, 8, 1, 1, 1), S.Grid(8, 8, 8, 0, 1, 1), S.Grid(8, -1, 8, 1, 1, 1),
-                 S.Grid(2048, 2048, 1024, 1, 1, 1)]
+                 S.Grid(2048, 2048, 1024, 1, 1, 1), S.Grid(4, 65536, 1, 1, 1, 1),
+                 S.Grid(4, 1, 65536, 1, 1, 1)]
     for g in bad_grids:
         assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)) == S.EINVAL
     g = S.Grid(8, 8, 8, 0.1, 0.1, 0.1)
