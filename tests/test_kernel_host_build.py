@@ -5,7 +5,10 @@ bit for bit on the CPU, beyond the GPU tests' FP32 tolerance:
   the two gather kernels it replaces (the march's windows and halo planes);
 - the Courant maxima taken inside the stage-1 kernels (k_nu_raw, k_nu_maxsmooth,
   the mass and energy k_div) equal those of the separate pass k_courant_part
-  (the block reductions and the per-cell formulas)."""
+  (the block reductions and the per-cell formulas);
+- the right-hand side formed with one cell per thread equals the one formed
+  with four x-cells per thread, for the benchmark's physics and for every
+  option at once."""
 import os
 import shutil
 import subprocess
@@ -38,3 +41,8 @@ def test_nu_maxsmooth_equals_max_then_smooth(tmp_path):
 def test_courant_maxima_in_stage_kernels_equal_separate_pass(tmp_path):
     out = _build_and_run(tmp_path, "courant_fused")
     assert out.count(", 0 differing") == 5, out
+
+
+def test_one_cell_and_four_cell_threads_give_the_same_rhs(tmp_path):
+    out = _build_and_run(tmp_path, "rhs_mappings")
+    assert out.count(" 0 differing values, 0 non-finite") == 8, out
