@@ -168,6 +168,7 @@ int main() {
   };
   const int shapes[][3] = {{16, 8, 6}, {20, 4, 5}, {8, 3, 7}, {132, 2, 3}};
   int bad = 0;
+  for (int stretched = 0; stretched < 2; ++stretched)
   for (int ci = 0; ci < 2; ++ci) {
     const Case& C = cases[ci];
     for (const auto& sh : shapes) {
@@ -208,8 +209,37 @@ int main() {
       float* out1[8];
       float* out4[8];
       for (int c = 0; c < 8; ++c) { out1[c] = o1[c].data(); out4[c] = o4[c].data(); }
-      rhs<Nb>(g, k, f, d1, fl1, out1);
-      rhs<Nb4>(g, k, f, d4, fl4, out4);
+      // Each set runs on a uniform mesh and (ZCell types) on a stretched z,
+      // dz varying by +-40 %.
+      std::vector<float> mesh(4 * nz);
+      for (int kz = 0; kz < nz; ++kz) {
+        const double th = 2.0 * M_PI / nz;
+        const double zc = h[2] * (1.0 + 0.4 * cos(th * (kz + 0.5))), zf = h[2] * (1.0 + 0.4 * cos(th * kz));
+        mesh[kz] = (float)zc; mesh[nz + kz] = (float)zf;
+        mesh[2 * nz + kz] = (float)(1.0 / zc); mesh[3 * nz + kz] = (float)(1.0 / zf);
+      }
+      if (stretched) {
+        k.hzc = mesh.data(); k.hzf = mesh.data() + nz; k.jzc = mesh.data() + 2 * nz; k.jzf = mesh.data() + 3 * nz;
+        rhs<NbZ>(g, k, f, d1, fl1, out1);
+        rhs<Nb4Z>(g, k, f, d4, fl4, out4);
+        // the mesh must matter: the uniform-mesh right-hand side differs
+        std::vector<std::vector<float>> ou(8, std::vector<float>(g.n));
+        float* outu[8];
+        for (int c = 0; c < 8; ++c) outu[c] = ou[c].data();
+        std::vector<std::vector<float>> du(F_COUNT, std::vector<float>(g.n));
+        std::vector<unsigned char> flu(g.n + 16);
+        rhs<Nb>(g, k, f, du, flu, outu);
+        long long changed = 0;
+        for (int c = 0; c < 8; ++c)
+          for (long long i = 0; i < g.n; ++i) changed += ou[c][i] != o1[c][i];
+        if (changed < g.n) {
+          printf("stretched mesh left the right-hand side unchanged (%lld values)\n", changed);
+          ++bad;
+        }
+      } else {
+        rhs<Nb>(g, k, f, d1, fl1, out1);
+        rhs<Nb4>(g, k, f, d4, fl4, out4);
+      }
       long long diff = 0, nonfinite = 0;
       for (int c = 0; c < 8; ++c)
         for (long long i = 0; i < g.n; ++i) {
@@ -218,8 +248,8 @@ int main() {
         }
       long long flagged = 0;
       for (long long i = 0; i < g.n; ++i) flagged += fl1[i] != 0;
-      printf("case %d %dx%dx%d: %lld differing values, %lld non-finite, %lld flagged cells\n", ci, nx, ny, nz,
-             diff, nonfinite, flagged);
+      printf("case %d%s %dx%dx%d: %lld differing values, %lld non-finite, %lld flagged cells\n", ci,
+             stretched ? " stretched" : "", nx, ny, nz, diff, nonfinite, flagged);
       // the second-order switch must take both branches
       bad += diff != 0 || nonfinite != 0 || (C.d2div && (flagged == 0 || flagged == g.n));
     }
