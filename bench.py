@@ -9,10 +9,18 @@ arithmetic, Courant time step computed on the device every step.  A "step" is
 one full low-storage RK3 step (three right-hand-side evaluations).
 
 Prints one JSON line.  `value` is zone-updates/s over the whole job with the
-state resident in HBM; `e2e` repeats the measurement through the host-memory
-entry point (copies included); `roofline` reports the dominant kernel's
-algorithmic HBM bytes per launch over its CUDA-event time; `cpu_baseline`
-times the FP64 CPU oracle on a bounded sample of the same workload.
+state resident in HBM, timed with per-kernel instrumentation off; `e2e`
+repeats the measurement through the host-memory entry point (copies
+included).  `roofline` is the step's HBM roofline: the minimal algorithmic
+traffic of a full RK3 step (288 B per zone: the eight FP32 state arrays read
+per stage, the time-derivative arrays read and written, the state written)
+times the zone-updates/s, over the measured copy bandwidth.  `alu_roofline`
+sets the oracle's operation count per zone per step against the FP32 issue
+peak of the GPU (SMs x 128 lanes x 2 flops per multiply-add x the SM clock
+sampled under load).  `kernels` reports each kernel's share of a step and
+the bytes of the arrays it reads and writes, from a separate instrumented
+pass.  `cpu_baseline` times the FP64 CPU oracle on a bounded sample of the
+same workload.
 
 --impl reference times that CPU oracle alone (the comparison arm).
 """
@@ -40,13 +48,13 @@ CPU_SAMPLE_SECONDS = 12.0       # run oracle steps until this much host time is 
 CPU_SAMPLE_MAX_STEPS = 30
 REF_N = 96                      # per-step sample grid of the reference (oracle) arm
 
-# Distinct FP32 arrays each fused kernel reads + writes per launch (its
-# algorithmic HBM traffic: every array touched once), for the viscous,
-# quenched workload.  k_div: per stage, over its three launches (momentum;
-# mass and energy; induction; their arrays are disjoint): stage 1 (Courant)
-# reads 25 and writes 8; stages 2 and 3 read 38 (fluxes, state, previous
-# dfdt) and write 16; k_update is the stage-1 update of all 8 fields (f, dfdt
-# in; f out).
+# Distinct FP32 arrays each kernel reads + writes per launch (every array
+# touched once), for the viscous, quenched workload: the traffic of the
+# arrays the design materialises, not the method's algorithmic minimum.
+# k_div: per stage, over its three launches (momentum; mass and energy;
+# induction; their arrays are disjoint): stage 1 (Courant) reads 25 and
+# writes 8; stages 2 and 3 read 38 (fluxes, state, previous dfdt) and write
+# 16; k_update is the stage-1 update of all 8 fields (f, dfdt in; f out).
 KERNEL_ARRAYS = {"k_lr_ed": 4, "k_vel": 10, "k_nu_raw": 9, "k_nu_max": 2, "k_nu_smooth": 3,
                  "k_nu_maxsmooth": 3,
                  "k_nu_faces": 4, "k_tau": 26, "k_edge": 28, "k_flux": 40, "k_flux_e": 17,
@@ -58,8 +66,20 @@ NCU_TRAFFIC_PER_CELL = {"k_flux": 1112.1e6 / 192 ** 3, "k_flux_e": 500.6e6 / 192
                         "k_edge": 762.6e6 / 192 ** 3, "k_tau": 710.2e6 / 192 ** 3,
                         # per unit of three launches, the mean over the three stages
                         "k_div": (940.6e6 + 2 * 1539.8e6) / 3 / 192 ** 3}
+# DRAM bytes per zone of one whole step (sum over its launches), from an ncu
+# launch list with DRAM counters of the same step at 192^3; None until taken
+# for the current kernels.
+STEP_TRAFFIC_PER_ZONE = None
 # Launches that together form one unit of KERNEL_ARRAYS.
 LAUNCHES_PER_UNIT = {"k_div": 3}
+FP32_LANES_PER_SM = 128         # FP32 multiply-add lanes per SM (4 partitions x 32)
+
+
+def flops_per_zone(workload="turbulence"):
+    """Operations per zone per RK3 step counted from the oracle's operator
+    list (tests/golden/count_flops.py writes the file; this only reads it)."""
+    p = os.path.join(ROOT, "tests", "golden", "flops_per_zone.json")
+    return json.load(open(p))[workload]
 
 
 def peaks():
@@ -154,7 +174,7 @@ def cpu_baseline(n=CPU_SAMPLE_N, seconds=CPU_SAMPLE_SECONDS, max_steps=CPU_SAMPL
     import torch
 
     import oracle
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
     w = inputs.turbulence(n)
     g = oracle.Grid(*w.shape, *w.spacing)
     p = oracle.Params(**{k: (bool(v) if k == "do_quench" else v) for k, v in PHYS.items()})
@@ -181,7 +201,7 @@ def run_reference(args):
     n = REF_N
     steps_per = 1
     import oracle
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
     w = inputs.turbulence(n)
     g = oracle.Grid(*w.shape, *w.spacing)
     p = oracle.Params(**{k: (bool(v) if k == "do_quench" else v) for k, v in PHYS.items()})
@@ -230,7 +250,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2405_02483_gb300 as S
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -254,7 +274,6 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    sim.timing(True)
     l0 = sim.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -266,31 +285,56 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = sim.launches() - l0
-    ktimes = sim.kernel_times()
-    sim.timing(False)
     clk = clocks.stop()
     ms = max_over_ranks(ms, device="cuda")
     ms_step = ms / args.steps
     value = job_value(n ** 3, args.steps, ms, ws)
 
-    # Dominant kernel roofline (algorithmic bytes per launch / mean launch time).
+    # Per-kernel CUDA-event times, in a separate instrumented pass (events on
+    # the launch stream around every launch) after the headline timing.
+    sim.timing(True)
+    ksteps = max(2, min(args.steps, 5))
+    for _ in range(ksteps):
+        sim.step(dev, None)
+    ktimes = sim.kernel_times()
+    sim.timing(False)
+
+    # The step's HBM roofline (algorithmic bytes per zone per step) and its
+    # FP32 ALU roofline (oracle operation count per zone per step).
     peak, peak_kind = peaks()
-    top = max(ktimes.items(), key=lambda kv: kv[1][0])
-    kname, (kms, kcnt) = top
-    kbytes = KERNEL_ARRAYS.get(kname, 0) * 4.0 * n ** 3
-    kavg = kms / kcnt * LAUNCHES_PER_UNIT.get(kname, 1)
-    achieved = kbytes / (kavg * 1e-3) / 1e9
-    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind,
-            "bytes_per_launch": kbytes, "ms_per_launch": kavg,
-            "traffic": (NCU_TRAFFIC_PER_CELL[kname] * n ** 3
-                        if kname in NCU_TRAFFIC_PER_CELL else None)}
     step_gbs = STEP_BYTES_PER_ZONE * (value / ws) / 1e9
-    step_roof = {"bytes_per_zone": STEP_BYTES_PER_ZONE, "achieved": step_gbs, "peak": peak,
-                 "unit": "GB/s", "frac": step_gbs / peak}
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / args.steps,
-                   "share": v[0] / sum(x[0] for x in ktimes.values())}
-               for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])}
+    roof = {"kernel": "whole RK3 step (every launch of the three stages)", "bound": "hbm",
+            "achieved": step_gbs, "peak": peak, "unit": "GB/s", "frac": step_gbs / peak,
+            "peak_kind": peak_kind, "bytes_per_zone": STEP_BYTES_PER_ZONE,
+            "traffic": (STEP_TRAFFIC_PER_ZONE * n ** 3 if STEP_TRAFFIC_PER_ZONE else None),
+            "traffic_unit": "DRAM bytes per step"}
+    props = torch.cuda.get_device_properties(local)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fz = flops_per_zone("turbulence")
+    alu_ach = fz["flops"] * (value / ws) / 1e12
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": alu_ach / alu_peak, "flops_per_zone": fz["flops"],
+           "transcendentals_per_zone": fz["transc"],
+           "peak_derivation": "%d SMs x %d FP32 lanes x 2 flops per multiply-add x %.0f MHz "
+                              "(median SM clock sampled during the timed steps)"
+                              % (props.multi_processor_count, FP32_LANES_PER_SM, sm_mhz),
+           "ms_per_step_at_peak": fz["flops"] * n ** 3 / (alu_peak * 1e12) * 1e3,
+           "hbm_ms_per_step_at_peak": STEP_BYTES_PER_ZONE * n ** 3 / (peak * 1e9) * 1e3}
+    tot = sum(x[0] for x in ktimes.values()) or 1.0
+    kernels = {}
+    for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0]):
+        per = v[0] / v[1] * LAUNCHES_PER_UNIT.get(k, 1)
+        d = {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / ksteps,
+             "share": v[0] / tot}
+        if k in KERNEL_ARRAYS:
+            b = KERNEL_ARRAYS[k] * 4.0 * n ** 3
+            d["array_bytes_per_unit"] = b
+            d["array_gbs"] = b / (per * 1e-3) / 1e9
+            d["array_frac"] = d["array_gbs"] / peak
+        if k in NCU_TRAFFIC_PER_CELL:
+            d["ncu_dram_bytes_per_unit"] = NCU_TRAFFIC_PER_CELL[k] * n ** 3
+        kernels[k] = d
 
     # End to end through the host-memory entry point (copies inside).
     e2e = None
@@ -305,7 +349,7 @@ def main():
                       "grid": [n, n, n], "l2": "inputs larger than L2 (state %.1f GiB)"
                       % (8 * 4 * n ** 3 / 2 ** 30),
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
-           "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+           "roofline": roof, "alu_roofline": alu, "kernels": kernels,
            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
 
     if rank == 0 and not args.no_adjoint:
@@ -341,7 +385,7 @@ def adjoint_cost(S, torch, n=128, reps=3):
     """Adjoint step cost: the FP32 adjoint of one fixed-dt step (stage
     recompute and reverse sweep included) over one forward step, on the
     Orszag-Tang 128^3 workload with the same physics."""
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
     w = inputs.orszag_tang_3d(n)
     refs, dev = S.split_state(w.fields)
     sim = S.Sim((n, n, n), (1.0 / n,) * 3, S.default_params(ref=refs, **PHYS))

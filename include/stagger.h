@@ -225,9 +225,14 @@ int stagger_kernel_times(stagger_ctx* ctx, int max, const char** names, double* 
  * Limit: at most 65536 thread blocks of 32 x 2 x 4 cells, i.e.
  * ceil(nx/32) * ceil(ny/2) * ceil(nz/4) <= 65536 (for example 256^3); larger
  * grids return STAGGER_EINVAL.  A stretched z (params->zc, zf) needs its mesh
- * on the device and returns STAGGER_EUNSUPPORTED.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array:
+ * on the device and returns STAGGER_EUNSUPPORTED.  The grid and parameters
+ * pass the same checks as stagger_create (STAGGER_EINVAL).  Every call that is
+ * not being captured looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, so a context torn down and
+ * rebuilt (cudaDeviceReset) is safe; a call made during stream capture reuses
+ * the address of the last uncaptured call on that device, and returns
+ * STAGGER_EUNSUPPORTED if there was none: make the first call on each device
+ * before any stream capture, and again after a device reset.  All calls share the one array:
  * calls that overlap on the GPU (two streams, two host threads) race, so
  * serialise them.  Each call overwrites every scratch entry it reads. */
 int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagger_params* params,

@@ -30,41 +30,10 @@ struct stagger_ctx {
   double* dtp = nullptr;   // the step dt on the device (read by the captured graph)
 };
 
-extern "C" {
+namespace stg {
 
-int stagger_params_default(stagger_params* p) {
-  if (!p) return STAGGER_EINVAL;
-  memset(p, 0, sizeof(*p));
-  p->gamma = 5.0 / 3.0;
-  p->nuE = 1.0;
-  p->nuB = 1.0;
-  p->qmax = 8.0;
-  p->qlim = 2.0;
-  p->log_interp = 1;
-  p->Cdt = 0.4;
-  p->Cdtr = 0.1;
-  p->Cdtd = 0.7;
-  p->rho_cool = 1.0;
-  p->d2lnr_lim = 0.3;
-  p->rho_bot = 1.0;
-  p->cor_Tunit = 1.0;
-  return STAGGER_OK;
-}
-
-const char* stagger_strerror(int s) {
-  switch (s) {
-    case STAGGER_OK: return "ok";
-    case STAGGER_EINVAL: return "invalid argument";
-    case STAGGER_ECUDA: return "CUDA runtime error";
-    case STAGGER_ENONFINITE: return "non-finite value in the state";
-    case STAGGER_EOOM: return "device memory allocation failed";
-    case STAGGER_ETIMEOUT: return "bounded device wait timed out";
-    case STAGGER_EUNSUPPORTED: return "unsupported feature";
-    default: return "unknown status";
-  }
-}
-
-static int validate(const stagger_grid* g, const stagger_params* p) {
+// Argument checks shared by stagger_create and stagger_diagnostics_noalloc.
+int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (!g || !p) return STAGGER_EINVAL;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1) return STAGGER_EINVAL;
   if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return STAGGER_EINVAL;
@@ -100,10 +69,46 @@ static int validate(const stagger_grid* g, const stagger_params* p) {
   return STAGGER_OK;
 }
 
+}  // namespace stg
+
+extern "C" {
+
+int stagger_params_default(stagger_params* p) {
+  if (!p) return STAGGER_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->gamma = 5.0 / 3.0;
+  p->nuE = 1.0;
+  p->nuB = 1.0;
+  p->qmax = 8.0;
+  p->qlim = 2.0;
+  p->log_interp = 1;
+  p->Cdt = 0.4;
+  p->Cdtr = 0.1;
+  p->Cdtd = 0.7;
+  p->rho_cool = 1.0;
+  p->d2lnr_lim = 0.3;
+  p->rho_bot = 1.0;
+  p->cor_Tunit = 1.0;
+  return STAGGER_OK;
+}
+
+const char* stagger_strerror(int s) {
+  switch (s) {
+    case STAGGER_OK: return "ok";
+    case STAGGER_EINVAL: return "invalid argument";
+    case STAGGER_ECUDA: return "CUDA runtime error";
+    case STAGGER_ENONFINITE: return "non-finite value in the state";
+    case STAGGER_EOOM: return "device memory allocation failed";
+    case STAGGER_ETIMEOUT: return "bounded device wait timed out";
+    case STAGGER_EUNSUPPORTED: return "unsupported feature";
+    default: return "unknown status";
+  }
+}
+
 int stagger_create(const stagger_grid* grid, const stagger_params* params, stagger_ctx** out) {
   if (!out) return STAGGER_EINVAL;
   *out = nullptr;
-  int rc = validate(grid, params);
+  int rc = validate_inputs(grid, params);
   if (rc) return rc;
   stagger_ctx* c = new (std::nothrow) stagger_ctx();
   if (!c) return STAGGER_EOOM;

@@ -50,6 +50,9 @@ __host__ __device__ __forceinline__ long long lin(const Geo& g, int i, int j, in
   return (long long)k * g.sz + (long long)j * g.sy + i;
 }
 
+// Grid and parameter checks of stagger_create (STAGGER_OK or STAGGER_EINVAL).
+int validate_inputs(const stagger_grid* g, const stagger_params* p);
+
 }  // namespace stg
 
 #define STG_CUDA_OK(call)                                   \

@@ -570,7 +570,7 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
 // array instead of memory from cudaMalloc.  The array is part of this
 // library's device image, so every GPU that loads the library holds it until
 // the process exits.  Limit: grids of at most NOALLOC_MAX_BLOCKS thread blocks
-// of 32 x 8 cells (16,777,216 cells, e.g. 256^3).
+// of BX x BY x BZ = 32 x 2 x 4 cells (16,777,216 cells, e.g. 256^3).
 
 namespace stg {
 
@@ -578,9 +578,11 @@ namespace stg {
 #define NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 10 + 16];
 
-// Device address of g_noalloc_scratch per device, taken once per device by
+// Device address of g_noalloc_scratch per device, as last looked up by
 // cudaGetSymbolAddress (in host code the symbol names a host-side stand-in,
-// not device memory).
+// not device memory).  It is looked up again on every call that is not being
+// captured, so a context that was torn down and rebuilt (cudaDeviceReset)
+// never sees a stale address; a captured call uses the stored one.
 static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
 // Sum (max for entry 7) of the nb per-block partials into out[0..9], in a
@@ -612,21 +614,30 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
   if (!grid || !p || !state || !out) return STAGGER_EINVAL;
   for (int c = 0; c < 8; ++c)
     if (!state[c]) return STAGGER_EINVAL;
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return STAGGER_EINVAL;
-  if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || p->ref[0] < 0) return STAGGER_EINVAL;
+  // The same grid and parameter checks as stagger_create (sizes, launch-grid
+  // limits, finiteness).  Every check, the stretched-z rejection included,
+  // stays before the first launch: nothing below may run on arguments that a
+  // check would have refused.
+  int rc = validate_inputs(grid, p);
+  if (rc) return rc;
   // A stretched z needs its mesh on the device, which this entry cannot allocate.
   if (p->zc || p->zf) return STAGGER_EUNSUPPORTED;
-  const long long nb = (long long)((grid->nx + BX - 1) / BX) * ((grid->ny + BY - 1) / BY) *
-                       ((grid->nz + BZ - 1) / BZ);
+  const long long nb = (((long long)grid->nx + BX - 1) / BX) * (((long long)grid->ny + BY - 1) / BY) *
+                       (((long long)grid->nz + BZ - 1) / BZ);
   if (nb > NOALLOC_MAX_BLOCKS) return STAGGER_EINVAL;  // grid larger than the fixed scratch
 
   int dev = 0;
   STG_CUDA_OK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return STAGGER_EUNSUPPORTED;
-  if (!g_noalloc_ptr[dev]) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  STG_CUDA_OK(cudaStreamIsCapturing(s, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     STG_CUDA_OK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     g_noalloc_ptr[dev] = (double*)ptr;
+  } else if (!g_noalloc_ptr[dev]) {
+    return STAGGER_EUNSUPPORTED;  // the first call on a device must not be captured
   }
   double* part = g_noalloc_ptr[dev];
   double* fin = part + (size_t)NOALLOC_MAX_BLOCKS * 10;
@@ -646,7 +657,6 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
   }
   k.log_interp = p->log_interp ? 1 : 0;
   Geo g = make_geo(grid->nx, grid->ny, grid->nz);
-  cudaStream_t s = (cudaStream_t)stream;
   dim3 gg = grid3(g), bb(BX, BY, BZ);
   // Each block writes all ten of its partials, so nothing carries over from
   // an earlier call.

@@ -73,13 +73,33 @@ def test_mesh_and_switch_parameters_are_validated_without_gpu(S):
     g1 = S.Grid(8, 8, 1, 0.1, 0.1, 0.1)                      # a stretched z needs nz > 1
     q = S.default_params(zc=[0.1], zf=[0.1])
     assert S.lib.stagger_create(ctypes.byref(g1), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL
-    # The allocation-free diagnostics cannot hold a mesh on the device.
+    # The allocation-free diagnostics cannot hold a mesh on the device.  The
+    # rejection comes before any launch; where a GPU is present the state
+    # still points at real device arrays of the grid's size, so that no
+    # reordering of the checks could make a kernel read outside them.
     q = S.default_params(zc=good, zf=good)
-    fake = S.P8F(*[ctypes.cast(ctypes.c_void_p(16 * (i + 1)), ctypes.POINTER(ctypes.c_float))
-                   for i in range(8)])
+    keep = None
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        keep = [torch.zeros(6, 8, 8, device="cuda") for _ in range(8)]
+        state = S._dev(keep)
+    else:
+        state = S.P8F(*[ctypes.cast(ctypes.c_void_p(16 * (i + 1)), ctypes.POINTER(ctypes.c_float))
+                        for i in range(8)])
     out = (ctypes.c_double * 10)()
-    assert S.lib.stagger_diagnostics_noalloc(ctypes.byref(g), ctypes.byref(q), fake, out,
+    assert S.lib.stagger_diagnostics_noalloc(ctypes.byref(g), ctypes.byref(q), state, out,
                                              None) == S.EUNSUPPORTED
+    # Invalid grids and parameters take the same checks as stagger_create.
+    for gg, qq in [(S.Grid(8, 8, 0, 0.1, 0.1, 0.1), S.default_params()),
+                   (S.Grid(4, 65536, 1, 0.1, 0.1, 0.1), S.default_params()),
+                   (g, S.default_params(gamma=1.0))]:
+        assert S.lib.stagger_diagnostics_noalloc(ctypes.byref(gg), ctypes.byref(qq), state, out,
+                                                 None) == S.EINVAL
+    del keep
 
 
 def test_null_context_calls_are_rejected(S):

@@ -40,7 +40,7 @@ import torch
 
 import bench
 import oracle
-from paper_2405_02483_gb300 import inputs
+import workloads as inputs
 from test_gpu_parity import oracle_params
 from test_oracle_physics import RHS_REACH
 

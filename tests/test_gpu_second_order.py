@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from oracle import stagger as OS
-from paper_2405_02483_gb300 import inputs
+import workloads as inputs
 
 from test_gpu_parity import (VISC_KW, err_group, err_max, err_scale, make, oracle_params,
                              ragged_state)

@@ -16,7 +16,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2405_02483_gb300 import inputs
+import workloads as inputs
 
 pytestmark = pytest.mark.gpu
 

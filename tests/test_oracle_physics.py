@@ -923,7 +923,7 @@ def test_rhs_and_courant_fields_reach(seed):
     reaches cells -3..+2 of the face, the centring faces -2..+3 of the
     cell).  The full-size parity
     tests rely on this to evaluate the oracle on a patch of a larger box."""
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
     n = 2 * RHS_REACH + 6
     w = inputs.turbulence(n, seed=seed)
     gen = torch.Generator().manual_seed(seed)

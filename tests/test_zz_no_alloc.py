@@ -41,7 +41,7 @@ def _close(a, b):
 
 
 def test_noalloc_diagnostics_match_twice(S):
-    from paper_2405_02483_gb300 import inputs
+    import workloads as inputs
     w = inputs.orszag_tang_3d(48)
     refs, dev = S.split_state(w.fields)
     sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, nu1=0.04, nu2=1.0, nu3=0.04,
