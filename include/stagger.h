@@ -118,10 +118,26 @@ typedef struct {
    * code units) and cor_Tunit (kelvin per code unit) come from the caller's
    * unit system.  cor_L0 = 0: off. */
   double cor_L0, cor_Tunit;
+  /* Kernel layout of the fluxes and divergences of one stage (no effect on
+   * the results beyond rounding order).  0 (default): the fluxes are stored
+   * to device arrays by one set of launches and differentiated, with the RK
+   * update, by another; 1: one z-marching kernel forms every flux on chip
+   * and applies the divergences and the update (uniform z only; a stretched z
+   * keeps the default).  Other values: STAGGER_EINVAL. */
+  int fuse_flux_div;
+  /* The ratio of eq. (quench), q = |D2 T| / (M + |D2 T| / qmax), along each
+   * axis the component is differentiated along.  quench_max3 0 (default): M =
+   * |T| + quench_eps * max3|T|, the paper's point value, with the 3-cell max
+   * of |T| along the axis weighted by quench_eps (default 1e-4) so that the
+   * ratio is not 0/0 where T vanishes by symmetry on a grid point;
+   * quench_max3 1: M = max3|T| alone.  quench_max3 outside {0, 1} or a
+   * negative or non-finite quench_eps: STAGGER_EINVAL. */
+  int quench_max3;
+  double quench_eps;
 } stagger_params;
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
- * nuE = nuB = 1, qmax 8, qlim 2, log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
+ * nuE = nuB = 1, qmax 8, qlim 2 (quench_eps 1e-4), log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,
  * no gravity, zero references, no cooling (rho_cool 1, rho_bot 1, cor_Tunit 1),
  * no second-order switch (d2lnr_lim 0.3), uniform z.  Returns STAGGER_EINVAL if p is NULL. */
 int stagger_params_default(stagger_params* p);

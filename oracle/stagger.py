@@ -22,8 +22,11 @@ path by specification only, never by code):
   R6  energy diffusion flux nuE * dn(rho nu_ii) * dd_dn(e);
   R7  resistivity eta on an edge = nuB * nu of that edge;
   R8  quench: one quenched value per stress / eta J component, the factor
-      taken over the directions in which that component is differentiated,
-      the ratio's |T| taken as the 3-cell max of |T| along each direction;
+      taken over the directions in which that component is differentiated;
+      the ratio's denominator holds the point value |T| of the paper plus
+      quench_eps times the 3-cell max of |T| along the direction, which
+      only matters where |T| is at roundoff (quench_max3: the 3-cell max of
+      |T| alone, an alternative reading);
   R9  Courant step from the stage-1 right-hand side, held for all stages;
   R10 RK constants exactly as printed;
   R13 axes with n = 1 are skipped in dl_min, dl_max, and take dl_min as their
@@ -197,6 +200,8 @@ class Params:
     csmag: float = 0.0       # Smagorinsky constant, eq. (nusmag) (0: off)
     do_2nddiv: bool = False  # second-order stress derivatives where ln rho, ln e kink (R18)
     d2lnr_lim: float = 0.3
+    quench_max3: bool = False   # R8: the 3-cell max of |T| in the quench ratio instead of |T|
+    quench_eps: float = 1e-4    # R8: weight of the 3-cell max of |T| added to |T|
     t_chromo: float = 0.0    # chromospheric cooling time, eq. (ChromoCool) (0: off), R20
     rho_bot: float = 1.0
     cor_L0: float = 0.0      # coronal thin cooling prefactor in code units (0: off), R21
@@ -296,15 +301,21 @@ def smooth3(f, ax):
 
 def quench(T, dirs, p: Params):
     """Quenching of a stress-like component, eq. (quench), reading R8:
-    q = |d2 T| / (M + |d2 T|/qmax) with M the 3-cell max of |T| along the
-    same axis, T <- T * min(max_d max3_d(q_d), qlim).  (With the point value
-    |T| the ratio is 0/0 where T vanishes by symmetry on a grid point, and the
-    quenched stress of the neighbours then depends on roundoff.)"""
+    q = |d2 T| / (M + |d2 T|/qmax), T <- T * min(max_d max3_d(q_d), qlim),
+    with d2 the second difference along each axis d the component is
+    differentiated along.  M is the paper's point value |T| plus quench_eps
+    times the 3-cell max of |T| along d: the added term only matters where
+    |T| is at roundoff, where the literal ratio is 0/0 (T vanishing by
+    symmetry on a grid point) and would carry roundoff to the neighbours
+    through the 3-cell max of q.  With quench_max3, M is that 3-cell max
+    alone."""
     fac = None
     for ax in dirs:
         d2 = _s(T, ax, 1) - 2.0 * T + _s(T, ax, -1)
         a2 = torch.abs(d2)
-        q = a2 / (max3(torch.abs(T), ax) + a2 / p.qmax + Q_EPS)
+        aT = torch.abs(T)
+        M = max3(aT, ax) if p.quench_max3 else aT + p.quench_eps * max3(aT, ax)
+        q = a2 / (M + a2 / p.qmax + Q_EPS)
         m = max3(q, ax)
         fac = m if fac is None else torch.maximum(fac, m)
     return T * torch.clamp(fac, max=p.qlim)

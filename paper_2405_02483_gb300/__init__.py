@@ -45,7 +45,9 @@ class Params(ctypes.Structure):
                 ("do_2nddiv", ctypes.c_int), ("d2lnr_lim", ctypes.c_double),
                 ("zc", ctypes.POINTER(ctypes.c_double)), ("zf", ctypes.POINTER(ctypes.c_double)),
                 ("t_chromo", ctypes.c_double), ("rho_bot", ctypes.c_double),
-                ("cor_L0", ctypes.c_double), ("cor_Tunit", ctypes.c_double)]
+                ("cor_L0", ctypes.c_double), ("cor_Tunit", ctypes.c_double),
+                ("fuse_flux_div", ctypes.c_int),
+                ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double)]
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

@@ -51,6 +51,9 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (!(p->t_cool >= 0) || !isfinite(p->e_cool)) return STAGGER_EINVAL;
   if (p->cool_cut < 0 || p->cool_cut > 2 || (p->cool_cut && !(p->rho_cool > 0))) return STAGGER_EINVAL;
   if (p->scalar_cells < 0 || p->scalar_cells > 1) return STAGGER_EINVAL;
+  if (p->fuse_flux_div < 0 || p->fuse_flux_div > 1) return STAGGER_EINVAL;
+  if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
+    return STAGGER_EINVAL;
   if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
@@ -81,6 +84,7 @@ int stagger_params_default(stagger_params* p) {
   p->nuB = 1.0;
   p->qmax = 8.0;
   p->qlim = 2.0;
+  p->quench_eps = 1e-4;
   p->log_interp = 1;
   p->Cdt = 0.4;
   p->Cdtr = 0.1;

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "fused_kernels.cuh"
+#include "stage_kernels.cuh"
 
 namespace stg {
 
@@ -25,7 +26,8 @@ namespace stg {
 const char* const KNAMES[K_COUNT] = {"k_lr_ed", "k_vel", "k_strain2", "k_nu_raw", "k_nu_max",
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
-                                     "k_d2flag", "k_cool2", "k_flux_e", "k_nu_maxsmooth"};
+                                     "k_d2flag", "k_cool2", "k_flux_e", "k_nu_maxsmooth",
+                                     "k_fdiv"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -104,6 +106,8 @@ static bool aligned16(float* const* a, int n) {
 int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.geo = make_geo(gr.nx, gr.ny, gr.nz);
   F.cells4 = (gr.nx % 4) == 0 && !p.scalar_cells;
+  // One z-marching flux-divergence kernel per stage (on request; uniform z only).
+  F.fdiv = p.fuse_flux_div && p.zc == nullptr;
   F.launches = 0;
   F.timing = 0;
   for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
@@ -165,6 +169,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.c1 = (float)p.c1;
   k.inv_qmax = (float)(1.0 / p.qmax);
   k.qlim = (float)p.qlim;
+  k.qmax3 = p.quench_max3 ? 1 : 0;
+  k.qeps = (float)p.quench_eps;
   k.log_interp = p.log_interp ? 1 : 0;
   k.do_quench = p.do_quench ? 1 : 0;
   k.inv_tcool = p.t_cool > 0 ? (float)(1.0 / p.t_cool) : 0.f;
@@ -240,9 +246,14 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
     k.jzf = F.mesh + 3 * gr.nz;
   }
   // Which intermediate fields this parameter set needs.
-  std::vector<int> need = {F_UX, F_UY, F_UZ, F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ,
-                           F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY,
-                           F_LX1, F_LX2, F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT};
+  std::vector<int> need = {F_UX, F_UY, F_UZ};
+  // The fused flux-divergence kernel keeps every flux on chip and forms J
+  // itself; k_tau still writes J and eta J for k_edge in viscous runs.
+  if (!F.fdiv || k.visc) for (int f : {F_JX, F_JY, F_JZ, F_EX, F_EY, F_EZ}) need.push_back(f);
+  if (!F.fdiv)
+    for (int f : {F_MXX, F_MYY, F_MZZ, F_MXY, F_MYX, F_MXZ, F_MZX, F_MYZ, F_MZY, F_LX1, F_LX2,
+                  F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT})
+      need.push_back(f);
   need.push_back(F_ED);
   if (k.log_interp) need.push_back(F_LR);
   if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
@@ -355,13 +366,16 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   }
   if (k.d2div)
     TIMED(K_D2FLAG, (k_d2flag<NB><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
+  // The fused flux-divergence kernel forms J itself: k_tau only for viscous runs.
   auto ktau = k.d2div ? k_tau<N, true> : k_tau<N, false>;
+  if (!F.fdiv || k.visc)
   TIMED(K_TAU, (ktau<<<gz8, BB_Z8, 0, s>>>(d[F_UX], d[F_UY], d[F_UZ], f[0], d[F_LFX], d[F_LFY],
                                        d[F_LFZ], d[F_NU], d[F_LNX], d[F_LNY], d[F_LNZ], f[5],
                                        f[6], f[7], d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY],
                                        d[F_TYZ], d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
                                        d[F_JY], d[F_JZ], F.d2flag, k, g)));
-  auto kedge = k.d2div ? k_edge<N, true> : k_edge<N, false>;
+  auto kedge = k.qmax3 ? (k.d2div ? k_edge<N, true, true> : k_edge<N, false, true>)
+                       : (k.d2div ? k_edge<N, true, false> : k_edge<N, false, false>);
   if (k.visc)
     TIMED(K_EDGE, (kedge<<<gz8, BB_Z8, 0, s>>>(d[F_TXX], d[F_TYY], d[F_TZZ], d[F_TXY], d[F_TYZ],
                                            d[F_TZX], d[F_RX], d[F_RY], d[F_RZ], d[F_JX],
@@ -369,6 +383,10 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
                                            d[F_QXX], d[F_QYY], d[F_QZZ], d[F_QXY], d[F_QYZ],
                                            d[F_QZX], d[F_EX], d[F_EY], d[F_EZ], d[F_WC],
                                            d[F_WX], d[F_WY], d[F_WZ], F.d2flag, k, g)));
+  if (F.fdiv) {   // fluxes, divergences and update in k_fdiv (launch_div)
+    STG_CUDA_OK(cudaGetLastError());
+    return STAGGER_OK;
+  }
   const bool qn = k.visc && k.do_quench;
   FluxIn fi = {f[1], f[2], f[3], f[0], f[4], f[5], f[6], f[7], ls, d[F_UX], d[F_UY], d[F_UZ],
                qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],
@@ -412,8 +430,62 @@ static DivIn div_in(Fused& F, float* const f[8]) {
   return di;
 }
 
+// Stage inputs of k_fdiv: the state, the primitives of k_lr_ed and k_vel, and
+// the viscous fields of k_tau, k_nu_* and k_edge.
+static FdIn fdiv_in(Fused& F, float* const f[8]) {
+  float** d = F.fld;
+  const KPar& k = F.kp;
+  const bool qn = k.visc && k.do_quench;
+  FdIn in;
+  for (int c = 0; c < 8; ++c) in.f[c] = f[c];
+  in.ux = d[F_UX]; in.uy = d[F_UY]; in.uz = d[F_UZ];
+  in.ed = d[F_ED];
+  in.ls = k.log_interp ? d[F_LR] : f[0];
+  in.txx = qn ? d[F_QXX] : d[F_TXX]; in.tyy = qn ? d[F_QYY] : d[F_TYY];
+  in.tzz = qn ? d[F_QZZ] : d[F_TZZ]; in.txy = qn ? d[F_QXY] : d[F_TXY];
+  in.tyz = qn ? d[F_QYZ] : d[F_TYZ]; in.tzx = qn ? d[F_QZX] : d[F_TZX];
+  in.rx = d[F_EX]; in.ry = d[F_EY]; in.rz = d[F_EZ];   // eta J left by k_edge
+  in.nu = d[F_NU];
+  in.wc = d[F_WC]; in.wx = d[F_WX]; in.wy = d[F_WY]; in.wz = d[F_WZ];
+  return in;
+}
+
+#ifndef FD_TY
+#define FD_TY 8
+#endif
+
+static int launch_fdiv(Fused& F, float* const f[8], float* q[8], float* const* oo, float alpha,
+                       float beta, int mode, cudaStream_t s, bool cfl) {
+  const Geo& g = F.geo;
+  const FdIn in = fdiv_in(F, f);
+  const dim3 bb(FD_TX, FD_TY),
+      gg((unsigned)((g.nx + FD_TX - 1) / FD_TX), (unsigned)((g.ny + FD_TY - 1) / FD_TY),
+         (unsigned)((g.nz + FD_ZC - 1) / FD_ZC));
+  typedef void (*FdK)(FdIn, float*, float*, float*, float*, float*, float*, float*, float*,
+                      float*, float*, float*, float*, float*, float*, float*, float*, float,
+                      float, const double*, int, unsigned*, KPar, Geo);
+  FdK kern;
+  if (F.kp.visc)
+    kern = cfl ? k_fdiv<FD_TY, true, true> : k_fdiv<FD_TY, true, false>;
+  else
+    kern = cfl ? k_fdiv<FD_TY, false, true> : k_fdiv<FD_TY, false, false>;
+  const size_t smem = fd_smem_bytes(FD_TY);
+  if (smem > 48 * 1024)
+    STG_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TIMED(K_FDIV, (kern<<<gg, bb, smem, s>>>(in, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
+                                        oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6], oo[7],
+                                        alpha, beta, F.dt_dev, mode, F.cmax + 1, F.kp, g)));
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
 static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
                       float beta, int mode, cudaStream_t s, bool cfl = false) {
+  if (F.fdiv) {
+    float* oo[8];
+    for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
+    return launch_fdiv(F, f, q, oo, alpha, beta, mode, s, cfl);
+  }
   DivIn di = div_in(F, f);
   float* oo[8];
   for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];

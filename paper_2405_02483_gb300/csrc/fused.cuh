@@ -20,6 +20,8 @@ struct KPar {
   float sp[3];          // diffusion length per axis
   float spp[3];         // max(sp) of edge pairs: [yz (Ex), zx (Ey), xy (Ez)]
   float nuE, nuB, c1, inv_qmax, qlim;
+  int qmax3;            // quench ratio over the 3-cell max of |T| (else |T| + qeps max3|T|)
+  float qeps;
   int log_interp, do_quench, r0pos;
   float g[3];
   float inv_tcool, e_cool, inv_rho_cool;   // Newtonian cooling (inv_tcool 0: off)
@@ -60,7 +62,8 @@ enum Fld {
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
-           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_NU_MS, K_COUNT };
+           K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_NU_MS,
+           K_FDIV, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {
@@ -82,6 +85,7 @@ struct Fused {
   int plane_nb;
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
+  int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)
   long long launches;
   // Optional per-kernel timing with CUDA events on the launch stream.
   int timing;

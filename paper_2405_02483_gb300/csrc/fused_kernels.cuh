@@ -798,8 +798,9 @@ __global__ void STG_LB_HI(N, STG_MINB) k_tau(
 }
 
 // eq. (quench): T <- T min(max over the axes a0, a1 of max3(q), qlim),
-// q = |d2 T| / (M + |d2 T| / qmax), M the 3-cell max of |T| along the axis.
-template <class N>
+// q = |d2 T| / (M + |d2 T| / qmax), M = |T| + qeps max3|T| along the axis (the
+// paper's point value, regularised where it is at roundoff), or max3|T|.
+template <bool QM3, class N>
 __device__ __forceinline__ typename N::T quench1(const float* __restrict__ f, const N& n, int a0,
                                                  int a1, const KPar& k) {
   using T = typename N::T;
@@ -808,15 +809,19 @@ __device__ __forceinline__ typename N::T quench1(const float* __restrict__ f, co
   for (int t = 0; t < 2; ++t) {
     int a = t == 0 ? a0 : a1;
     if (a < 0) continue;
-    T v[5];
+    T v[5], av[5];
 #pragma unroll
-    for (int o = -2; o <= 2; ++o) v[o + 2] = n.lda(f, a, o);
+    for (int o = -2; o <= 2; ++o) {
+      v[o + 2] = n.lda(f, a, o);
+      av[o + 2] = fabsf(v[o + 2]);
+    }
     T m = -1.f;
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       T d2 = (v[o + 2] - 2.f * v[o + 1]) + v[o];
       T a2 = fabsf(d2);
-      T M = fmaxf(fmaxf(fabsf(v[o]), fabsf(v[o + 1])), fabsf(v[o + 2]));
+      const T M3 = fmaxf(fmaxf(av[o], av[o + 1]), av[o + 2]);
+      const T M = QM3 ? M3 : av[o + 1] + k.qeps * M3;
       T q = fdiv(a2, (M + a2 * k.inv_qmax) + 1e-30f);
       m = fmaxf(m, q);
     }
@@ -829,7 +834,7 @@ __device__ __forceinline__ typename N::T quench1(const float* __restrict__ f, co
 // where k_flux adds -u x B) and the heating densities
 // w_c = sum tau_ii S_ii (centre), w_edge = 2 tau_ij S_ij + eta J . J (edge).
 // Viscous runs only.
-template <class N, bool D2>
+template <class N, bool D2, bool QM3 = false>
 __global__ void STG_LB(N, STG_MINB_HI) k_edge(
     const float* __restrict__ txx, const float* __restrict__ tyy, const float* __restrict__ tzz,
     const float* __restrict__ txy, const float* __restrict__ tyz, const float* __restrict__ tzx,
@@ -846,15 +851,15 @@ __global__ void STG_LB(N, STG_MINB_HI) k_edge(
   using T = typename N::T;
   T txx_, tyy_, tzz_, txy_, tyz_, tzx_, rx_, ry_, rz_;
   if (k.do_quench) {
-    txx_ = quench1(txx, n, 0, -1, k);
-    tyy_ = quench1(tyy, n, 1, -1, k);
-    tzz_ = quench1(tzz, n, 2, -1, k);
-    txy_ = quench1(txy, n, 0, 1, k);
-    tyz_ = quench1(tyz, n, 1, 2, k);
-    tzx_ = quench1(tzx, n, 2, 0, k);
-    rx_ = quench1(Rx, n, 1, 2, k);
-    ry_ = quench1(Ry, n, 2, 0, k);
-    rz_ = quench1(Rz, n, 0, 1, k);
+    txx_ = quench1<QM3>(txx, n, 0, -1, k);
+    tyy_ = quench1<QM3>(tyy, n, 1, -1, k);
+    tzz_ = quench1<QM3>(tzz, n, 2, -1, k);
+    txy_ = quench1<QM3>(txy, n, 0, 1, k);
+    tyz_ = quench1<QM3>(tyz, n, 1, 2, k);
+    tzx_ = quench1<QM3>(tzx, n, 2, 0, k);
+    rx_ = quench1<QM3>(Rx, n, 1, 2, k);
+    ry_ = quench1<QM3>(Ry, n, 2, 0, k);
+    rz_ = quench1<QM3>(Rz, n, 0, 1, k);
     n.st(qxx, txx_);
     n.st(qyy, tyy_);
     n.st(qzz, tzz_);

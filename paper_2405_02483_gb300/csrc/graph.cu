@@ -79,7 +79,7 @@ __device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, in
 // Quench, eq. (quench) with reading R8, as one node: out = T min(fac, qlim),
 // fac = the max over the node's axes of max3 along the axis of
 // q = |D2 T| / ((M + |D2 T| / qmax) + 1e-30), D2 T = T(+1) - 2 T + T(-1) and
-// M = max3 |T|.  Its transpose follows the rules of the primitive nodes it
+// M = |T| + eps max3 |T| (eps = c2 >= 0), or M = max3 |T| (c2 < 0).  Its transpose follows the rules of the primitive nodes it
 // stands for: a max splits the gradient evenly on a tie (pairwise, the inner
 // pair first), |x|' = sign x with sign 0 = 0, the clamp passes the gradient
 // where fac <= qlim.
@@ -97,13 +97,16 @@ __device__ __forceinline__ T sgn(T a) {
 // q at z = c + s e_ax, and (dq) its derivatives with respect to T at z-1, z,
 // z+1 (through D2 T and through M).
 template <typename T>
-__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, const Geo& g,
-                                  T* dq) {
+__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, T eps,
+                                  const Geo& g, T* dq) {
   const T vm = A[nbr(c, ax, s - 1, g)], v0 = A[nbr(c, ax, s, g)], vp = A[nbr(c, ax, s + 1, g)];
   const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
   const T am = fabs(vm), a0 = fabs(v0), ap = fabs(vp);
   const T inner = am >= a0 ? am : a0;
-  const T M = inner >= ap ? inner : ap;
+  const T M3 = inner >= ap ? inner : ap;
+  // M = cM max3|T| + cP |T|.
+  const T cM = eps < (T)0 ? (T)1 : eps, cP = eps < (T)0 ? (T)0 : (T)1;
+  const T M = eps < (T)0 ? M3 : a0 + eps * M3;
   const T den = (M + a2 * iq) + (T)1e-30;
   const T q = a2 / den;
   if (dq) {
@@ -113,9 +116,9 @@ __device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T i
     const T dq_da2 = (T)1 / den + iq * (-a2 / (den * den));
     const T dq_dM = -a2 / (den * den);
     const T sd = sgn(d2);
-    dq[0] = dq_da2 * sd + dq_dM * (woi * wim) * sgn(vm);
-    dq[1] = dq_da2 * sd * (T)-2 + dq_dM * (woi * wi0) * sgn(v0);
-    dq[2] = dq_da2 * sd + dq_dM * wop * sgn(vp);
+    dq[0] = dq_da2 * sd + dq_dM * (cM * (woi * wim)) * sgn(vm);
+    dq[1] = dq_da2 * sd * (T)-2 + dq_dM * (cM * (woi * wi0) + cP) * sgn(v0);
+    dq[2] = dq_da2 * sd + dq_dM * (cM * wop) * sgn(vp);
   }
   return q;
 }
@@ -123,14 +126,15 @@ __device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T i
 // fac at c, and (when wq) the weights of the three q of each axis in fac:
 // wq[3 t + p + 1] for axis t and position p.
 template <typename T>
-__device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int a1, T iq,
+__device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int a1, T iq, T eps,
                                         const Geo& g, T* wq) {
   T m[2] = {0, 0}, w[2][3];
   for (int t = 0; t < 2; ++t) {
     const int ax = t == 0 ? a0 : a1;
     if (ax < 0) continue;
-    const T qm = q_at(A, c, ax, -1, iq, g, (T*)nullptr), q0 = q_at(A, c, ax, 0, iq, g, (T*)nullptr),
-            qp = q_at(A, c, ax, 1, iq, g, (T*)nullptr);
+    const T qm = q_at(A, c, ax, -1, iq, eps, g, (T*)nullptr),
+            q0 = q_at(A, c, ax, 0, iq, eps, g, (T*)nullptr),
+            qp = q_at(A, c, ax, 1, iq, eps, g, (T*)nullptr);
     const T inner = qm >= q0 ? qm : q0;
     m[t] = inner >= qp ? inner : qp;
     T wim, wi0, woi, wop;
@@ -165,7 +169,7 @@ __global__ void g_quench_b1(GNode nd, const T* A, const T* gout, T* S, Geo g) {
     const GCell c = gcell_at(c0, u, g);
     if (c.k >= g.nz) break;
     T wq[6];
-    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, g, wq);
+    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, (T)nd.c2, g, wq);
     const T gg = gout[c.idx];
     const T C = fac > qlim ? qlim : fac;
     const T dC = fac <= qlim ? (T)1 : (T)0;
@@ -195,7 +199,7 @@ __global__ void g_quench_b3(GNode nd, const T* A, const T* S, T* gA, int wA, Geo
         for (int p = -1; p <= 1; ++p)
           qbar += S[(long long)(1 + 3 * t + p + 1) * g.n + nbr(c, ax, r - p, g)];
         T dq[3];
-        q_at(A, c, ax, r, iq, g, dq);
+        q_at(A, c, ax, r, iq, (T)nd.c2, g, dq);
         acc += qbar * dq[1 - r];
       }
     }
@@ -211,7 +215,7 @@ __global__ void g_quench_f(GNode nd, const T* A, T* out, Geo g) {
   for (int u = 0; u < GZU; ++u) {
     const GCell c = gcell_at(c0, u, g);
     if (c.k >= g.nz) break;
-    const T fac = quench_fac(A, c, nd.axis, nd.sk, (T)1 / (T)nd.c0, g, (T*)nullptr);
+    const T fac = quench_fac(A, c, nd.axis, nd.sk, (T)1 / (T)nd.c0, (T)nd.c2, g, (T*)nullptr);
     out[c.idx] = A[c.idx] * (fac > (T)nd.c1 ? (T)nd.c1 : fac);
   }
 }
@@ -592,7 +596,8 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     if (p.do_quench) {
       // eq. (quench): one factor per component, over its differentiation axes;
       // |T| in the ratio is the 3-cell max of |T| along the axis.
-      auto quench = [&](int T, int a0, int a1) { return G.quench(T, a0, a1, p.qmax, p.qlim); };
+      const double qe = p.quench_max3 ? -1.0 : p.quench_eps;
+      auto quench = [&](int T, int a0, int a1) { return G.quench(T, a0, a1, p.qmax, p.qlim, qe); };
       txx = quench(txx, X, -1);
       tyy = quench(tyy, Y, -1);
       tzz = quench(tzz, Z, -1);

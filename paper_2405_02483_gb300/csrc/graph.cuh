@@ -17,7 +17,7 @@ enum GOp {
   G_STEP,  // 1 where a > c0, else 0 (a switch: no gradient)
   G_ZFIELD, // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
   G_PMEAN,  // mean of a over the horizontal plane (constant z) of each cell
-  G_QUENCH  // eq. (quench) of a over axes axis and sk (-1: one axis); c0 qmax, c1 qlim
+  G_QUENCH  // eq. (quench) of a over axes axis and sk (-1: one axis); c0 qmax, c1 qlim, c2 eps
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -27,6 +27,7 @@ struct GNode {
   int axis;     // 0 = x, 1 = y, 2 = z (stencil / shift)
   int sk;       // GStencil kind, or shift distance
   double c0, c1;  // scalars: spacing h (derivative), a*x+b, clamp bound, const
+  double c2 = 0;  // G_QUENCH: weight of max3|T| added to |T| (< 0: max3|T| alone)
 };
 
 // Precision-independent description of the graph.
@@ -62,8 +63,10 @@ struct GraphDef {
   int stepf(int a, double c) { return push(G_STEP, a, -1, 0, 0, c, 0); }
   int zfield(int which) { return push(G_ZFIELD, -1, -1, 2, which, 0, 0); }
   int pmean(int a) { return push(G_PMEAN, a, -1, 0, 0, 0, 0); }
-  int quench(int a, int a0, int a1, double qmax, double qlim) {
-    return push(G_QUENCH, a, -1, a0, a1, qmax, qlim);
+  int quench(int a, int a0, int a1, double qmax, double qlim, double eps) {
+    const int id = push(G_QUENCH, a, -1, a0, a1, qmax, qlim);
+    nodes[id].c2 = eps;
+    return id;
   }
   // Stretched z mesh: the five arrays of G_ZFIELD, nz values each (empty when uniform).
   std::vector<double> mesh;

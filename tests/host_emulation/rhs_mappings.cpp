@@ -196,7 +196,7 @@ int main() {
       k.nu1 = C.nu1; k.nu2 = C.nu2; k.nu2dl = (float)(C.nu2 * dlmin); k.nu3 = C.nu3; k.dlmin = (float)dlmin;
       k.dlxy = (float)std::min(h[0], h[1]);
       k.csmag = C.csmag; k.csmag_dl = (float)(C.csmag * dlmin);
-      k.nuE = C.nuE; k.nuB = C.nuB; k.c1 = C.c1; k.do_quench = C.quench; k.inv_qmax = 1.f / 8.f; k.qlim = 2.f;
+      k.nuE = C.nuE; k.nuB = C.nuB; k.c1 = C.c1; k.do_quench = C.quench; k.inv_qmax = 1.f / 8.f; k.qlim = 2.f; k.qeps = 1e-4f;
       k.log_interp = C.log_interp;
       k.inv_tcool = C.tcool > 0 ? 1.f / C.tcool : 0.f; k.e_cool = C.ecool; k.cool_cut = C.cool_cut;
       k.inv_rho_cool = C.cool_cut ? 1.f / C.rhocool : 0.f;

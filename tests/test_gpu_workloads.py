@@ -42,16 +42,28 @@ def _group_err(got, ora):
     return out
 
 
-@pytest.mark.parametrize("quench", [1, 0], ids=["quench", "no_quench"])
+# Bounds per reading of eq. (quench): FP32 group error at step 25, FP64 group
+# error at step 200.  The FP64 oracle itself (CPU, same step sequence) grows an
+# input perturbation of FP32 size (2^-24 of each stored deviation) to 7e-5
+# (max3|T| in the ratio) and 1e-4 (the point value |T|) of the group scale by
+# step 25, and a 1e-15 relative perturbation to 1.9e-8 and 5.3e-8 by step 200;
+# without the quench the dynamics do not amplify.  The GPU rounds at every
+# step, so the FP32 bounds leave a factor of about 3 to 5 over these.
+OT_BOUNDS = {"point": (5e-4, 3e-7), "max3": (1e-4, 1e-7), "off": (1e-5, 1e-7)}
+
+
+@pytest.mark.parametrize("quench", ["point", "max3", "off"])
 def test_orszag_tang_128_200_steps(S, quench):
     """FP32 fused and FP64 unfused GPU paths against the oracle on the same
     Courant step sequence.  With the quench on, the discrete dynamics amplify
-    any perturbation (measured: the two FP64 implementations drift from 1e-16
-    to 5e-9 over 200 steps, about x10 per 25 steps), so FP32 rounding grows to
-    1e-2 by step 200; the FP32 bound there is checked over the first 25 steps
-    and the FP64 path carries the 200-step comparison."""
-    kw = dict(VISC_KW, do_quench=quench)
-    po = oracle.Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=bool(quench))
+    any perturbation (about x10 per 25 steps), so FP32 rounding grows to 1e-2
+    by step 200; the FP32 bound there is checked over the first 25 steps and
+    the FP64 path carries the 200-step comparison."""
+    on = quench != "off"
+    kw = dict(VISC_KW, do_quench=int(on), quench_max3=int(quench == "max3"))
+    po = oracle.Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=on,
+                       quench_max3=quench == "max3")
+    b32, b64 = OT_BOUNDS[quench]
     w = inputs.orszag_tang(128, 128, 1)
     refs, dev = S.split_state(w.fields)
     sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **kw))
@@ -67,12 +79,13 @@ def test_orszag_tang_128_200_steps(S, quench):
         if n % 10 == 0:
             log.append(sim.diagnostics(dev))
         if n == 25:
-            assert _group_err(S.join_state(dev, refs), [t.numpy() for t in fo]) < 1e-4
+            e25 = _group_err(S.join_state(dev, refs), [t.numpy() for t in fo])
+            assert e25 < b32, e25
     ora = [t.numpy() for t in fo]
     e64 = _group_err([t.cpu().numpy() + r for t, r in zip(d64, refs)], ora)
     e32 = _group_err(S.join_state(dev, refs), ora)
-    assert e64 < 1e-7, e64
-    if not quench:
+    assert e64 < b64, e64
+    if not on:
         assert e32 < 1e-5, e32
     else:
         assert e32 < 5e-2, e32

@@ -278,20 +278,75 @@ def test_energy_diffusion_rate():
 
 # ---------------------------------------------- quench, max3, smooth3 --------
 
-def test_quench_closed_forms():
-    p = Params(qmax=8.0, qlim=2.0)
+@pytest.mark.parametrize("max3", [False, True])
+def test_quench_closed_forms(max3):
+    p = Params(qmax=8.0, qlim=2.0, quench_max3=max3)
+    eps = 0.0 if max3 else p.quench_eps
     x = torch.arange(16, dtype=DT).reshape(1, 1, 16)
     lin = 0.3 + 0.0 * x                      # constant: d2 = 0 -> quenched to 0
     assert float(S.quench(lin, "x", p).abs().max()) == 0.0
     alt = torch.where(x % 2 == 0, 1.0, -1.0).to(DT)
-    # |d2| = 4, |T| = 1: q = 4 / (1 + 4/8) = 8/3, factor min(8/3, 2) = 2.
+    # |d2| = 4, |T| = max3|T| = 1: q = 4 / (1 (+ eps) + 4/8), factor min(q, qlim).
     assert torch.allclose(S.quench(alt, "x", p), 2.0 * alt)
-    p2 = Params(qmax=8.0, qlim=5.0)
-    assert torch.allclose(S.quench(alt, "x", p2), (8.0 / 3.0) * alt)
+    p2 = Params(qmax=8.0, qlim=5.0, quench_max3=max3)
+    assert torch.allclose(S.quench(alt, "x", p2), (4.0 / (1.5 + eps)) * alt, rtol=1e-14)
     # Along an axis where T is constant the factor is 0 unless another axis wiggles.
     t2 = alt.expand(1, 4, 16).contiguous()
     assert torch.allclose(S.quench(t2, "y", p), torch.zeros_like(t2))
     assert torch.allclose(S.quench(t2, "xy", p), 2.0 * t2)
+
+
+def test_quench_point_value_and_three_cell_max_differ():
+    """T = (1, -2, 1, -2, ...) along x: |d2 T| = 6 in every cell.  With the
+    paper's point value the denominators are 1 + 2 eps + 6/8 (cells with |T| =
+    1) and 2 + 2 eps + 6/8 (|T| = 2), and the 3-cell max of q always holds a
+    |T| = 1 cell: T <- T 6 / (1.75 + 2 eps).  With the 3-cell max of |T| the
+    denominator is 2 + 6/8 everywhere: T <- T 6 / 2.75.  Along y (constant) q
+    is 0, so quenching over x and y gives the x factor."""
+    x = torch.arange(16, dtype=DT).reshape(1, 1, 16)
+    T = torch.where(x % 2 == 0, 1.0, -2.0).to(DT).expand(1, 3, 16).contiguous()
+    pp = Params(qmax=8.0, qlim=10.0)
+    pm = Params(qmax=8.0, qlim=10.0, quench_max3=True)
+    e = pp.quench_eps
+    assert torch.allclose(S.quench(T, "x", pp), T * (6.0 / (1.75 + 2 * e)), rtol=1e-14)
+    assert torch.allclose(S.quench(T, "x", pm), T * (6.0 / 2.75), rtol=1e-14)
+    assert torch.allclose(S.quench(T, "xy", pp), T * (6.0 / (1.75 + 2 * e)), rtol=1e-14)
+    assert torch.allclose(S.quench(T, "y", pm), torch.zeros_like(T))
+
+
+def test_quench_regularisation_where_T_vanishes_by_symmetry():
+    """T = sin(theta i), odd about i = 0, where T and d2 T vanish.  A
+    roundoff-sized value d there makes the literal ratio (eps = 0)
+    2d / (d + 2d/8) = 1.6 (up to the rounding of the 2d it is formed from:
+    the 0/0 is pure roundoff), which the 3-cell max carries to the neighbour at
+    i = 1 (whose own q is 4 s / (1 + s/2), s = sin^2(theta/2)).  With the
+    weight eps of max3|T| the ratio at i = 0 is 2d / (eps max3|T|), far below,
+    and the neighbour keeps its own factor: the quenched value there is
+    T(1) max(q(1), q(2)) whatever d is."""
+    n, th = 16, 2 * math.pi / 16
+    i = torch.arange(n, dtype=DT)
+    base = torch.sin(th * i)
+    base[0] = 0.0
+    base[n // 2] = 0.0
+    base[n // 2 + 1:] = -torch.flip(base[1:n // 2], [0])   # exactly odd
+    s2 = math.sin(th / 2) ** 2
+    d = 1e-15
+    for eps, moved in ((0.0, True), (1e-4, False)):
+        p = Params(qmax=8.0, qlim=10.0, quench_eps=eps)
+        a = S.quench(base.reshape(1, 1, n), "x", p)[0, 0]
+        bp = base.clone()
+        bp[0] = d
+        b = S.quench(bp.reshape(1, 1, n), "x", p)[0, 0]
+        if moved:
+            # the literal 0/0 (about 1.6, its rounding included) reaches i = 1
+            assert float(b[1] / base[1]) > 1.5 and float(b[1] / base[1] - a[1] / base[1]) > 0.5
+        else:
+            # the neighbour's factor is the larger own q of cells 1 and 2
+            q = [4 * s2 * abs(float(base[k])) / (abs(float(base[k])) + eps * max(
+                abs(float(base[k - 1])), abs(float(base[k])), abs(float(base[k + 1])))
+                + 4 * s2 * abs(float(base[k])) / 8) for k in (1, 2)]
+            assert float(b[1] / base[1]) == pytest.approx(max(q), rel=1e-12)
+            assert float(a[1] / base[1]) == pytest.approx(max(q), rel=1e-12)
 
 
 def test_max3_smooth3_delta():
@@ -353,6 +408,34 @@ def test_diagnostics_uniform():
     assert d[5] == pytest.approx(64 * 0.5 * (0.2 ** 2 + 0.4 ** 2) / 2.0)
     assert d[6] == pytest.approx(64 * 0.5 * (0.09 + 0.16))
     assert d[7] == 0.0 and d[9] == 0.0
+
+
+def test_diagnostics_sinusoidal_fields():
+    """Non-solenoidal B_x = A sin(2 pi m x) and p_x = P sin(2 pi m x) on the x
+    faces x_i = i h, uniform rho0: the discrete div B at the centres is
+    A (D(theta)/h) cos(2 pi m (i + 1/2) h) (the symbol of eq. (deriv), theta =
+    2 pi m h, D = 2 [a sin(theta/2) + b sin(3 theta/2) + c sin(5 theta/2)]), so
+    rms div B = A D / (h sqrt 2) and max |div B| = A (D/h) cos(pi/n) for m = 1
+    (the centre nearest a crest sits h/2 from it).  The sums of sin^2 over a
+    period give the kinetic energy P^2 N / (4 rho0) and the magnetic energy
+    A^2 N / 4, N cells."""
+    n, m, A, P, r0 = 16, 1, 0.7, 0.3, 1.3
+    h = 1.0 / n
+    g = Grid(n, n, n, h, h, h)
+    xf = (torch.arange(n, dtype=DT) * h).reshape(1, 1, n).expand(n, n, n)
+    sx = torch.sin(2 * math.pi * m * xf)
+    z = torch.zeros(n, n, n, dtype=DT)
+    f = [z + r0, P * sx, z.clone(), z.clone(), z + 1.0, A * sx, z.clone(), z.clone()]
+    d = S.diagnostics(f, g, Params())
+    a, b, c = 225.0 / 192.0, -25.0 / 384.0, 3.0 / 640.0
+    th = 2 * math.pi * m * h
+    D = 2 * (a * math.sin(th / 2) + b * math.sin(3 * th / 2) + c * math.sin(5 * th / 2))
+    N = n ** 3
+    assert d[8] == pytest.approx(A * D / h / math.sqrt(2.0), rel=1e-12)
+    assert d[7] == pytest.approx(A * D / h * math.cos(math.pi / n), rel=1e-12)
+    assert d[5] == pytest.approx(P * P * N / (4 * r0), rel=1e-12)
+    assert d[6] == pytest.approx(A * A * N / 4, rel=1e-12)
+    assert d[0] == pytest.approx(r0 * N, rel=1e-14) and abs(d[1]) < 1e-12 and d[9] == 0.0
 
 
 # ----------------------------------------------------------- adjoint ---------
