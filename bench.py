@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ot2d", action="store_true",
+                    help="skip the Orszag-Tang 1024^2 x 1, 2000-step run")
     ap.add_argument("--scalar-cells", action="store_true",
                     help="one cell per thread in the fused kernels (default: four x-cells)")
     args = ap.parse_args()
@@ -354,6 +356,8 @@ def main():
 
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = adjoint_cost(S, torch)
+    if rank == 0 and not args.no_ot2d:
+        out["orszag_tang_2d"] = orszag_tang_2d(S, torch)
     sim.close()
     del dev
     torch.cuda.empty_cache()
@@ -363,6 +367,41 @@ def main():
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def orszag_tang_2d(S, torch, n=1024, steps=2000, every=10):
+    """The Orszag-Tang vortex (eq. initOT) at its stated size, n x n x 1, with
+    the benchmark's physics for `steps` Courant steps; FP64 diagnostics every
+    `every` steps.  Zone-updates/s over the steps alone (CUDA events around
+    each run of `every` steps; the diagnostics between them are not timed)."""
+    import workloads as inputs
+    w = inputs.orszag_tang(n, n, 1)
+    refs, dev = S.split_state(w.fields)
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **PHYS))
+    d0 = sim.diagnostics(dev)
+    ms, log = 0.0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps // every):
+        e0.record()
+        sim.run(dev, every)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        log.append(sim.diagnostics(dev))
+    sim.close()
+    etot = [d[4] + d[5] + d[6] for d in [d0] + log]
+    return {"workload": "Orszag-Tang %dx%dx1, RM viscosity + quench, Courant dt" % (n, n),
+            "steps": steps, "value": n * n * steps / (ms * 1e-3), "unit": UNIT,
+            "log_every": every, "log_entries": len(log),
+            "max_rel_mass_drift": max(abs(d[0] - d0[0]) / d0[0] for d in log),
+            "max_abs_net_px": max(abs(d[1]) for d in log),
+            "max_abs_net_py": max(abs(d[2]) for d in log),
+            "max_abs_net_pz": max(abs(d[3]) for d in log),
+            "max_div_b": max(d[7] for d in log), "max_rms_div_b": max(d[8] for d in log),
+            "rel_total_energy_change": (etot[-1] - etot[0]) / etot[0],
+            "kinetic_first_last": [log[0][5], log[-1][5]],
+            "magnetic_first_last": [log[0][6], log[-1][6]],
+            "nonfinite": max(d[9] for d in log)}
 
 
 def run_e2e(sim, dev, steps, ws, n):

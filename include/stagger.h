@@ -176,6 +176,17 @@ int stagger_run(stagger_ctx* ctx, float* state[8], int nsteps, double dt, void* 
 int stagger_courant(stagger_ctx* ctx, float* const state[8], double* dt_host,
                     double limits[3], void* stream);
 
+/* The same Courant step as an asynchronous call: out receives 4 doubles, dt
+ * and the wave-speed, rate-of-change and diffusion limits (HUGE_VAL when
+ * inactive).  on_device 1: out is a DEVICE pointer, written on the stream
+ * with no host synchronisation (the value a later stagger_step with dt > 0
+ * could be given after a device-to-host read, or a device-side consumer
+ * reads directly); on_device 0: out is a HOST pointer and the call
+ * synchronises, returning ENONFINITE for a non-finite step.  The step is
+ * computed from the state and its stage-1 derivative, as stagger_step does
+ * with dt <= 0.  Errors: EINVAL (NULL, on_device not 0 or 1), ECUDA. */
+int stagger_dt(stagger_ctx* ctx, float* const state[8], double* out, int on_device, void* stream);
+
 /* FP64 diagnostics of the state (plain sums over cells): out[0..9] =
  * sum r, sum px, sum py, sum pz, sum E, sum 1/2 p.u (faces), sum 1/2 B^2,
  * max |div B|, rms div B (div B = sum_i ddup_i B_i at centres), count of

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("stagger_run", ctypes.c_int, [VP, P8F, ctypes.c_int, ctypes.c_double, VP]),
     ("stagger_courant", ctypes.c_int, [VP, P8F, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), VP]),
+    ("stagger_dt", ctypes.c_int, [VP, P8F, ctypes.c_void_p, ctypes.c_int, VP]),
     ("stagger_diagnostics", ctypes.c_int, [VP, P8F, ctypes.POINTER(ctypes.c_double), VP]),
     ("stagger_step_adjoint", ctypes.c_int, [VP, P8F, ctypes.c_double, P8F, P8F, VP]),
     ("stagger_rhs_unfused", ctypes.c_int, [VP, P8F, P8F, VP]),
@@ -209,6 +210,22 @@ class Sim:
         _check(lib.stagger_courant(self.ctx, _dev(state), ctypes.byref(dt), lim, _stream(stream)),
                "stagger_courant")
         return dt.value, tuple(lim)
+
+    def dt(self, state, out=None, stream=None):
+        """Courant step and its three limits.  With out (a CUDA float64 tensor
+        of 4 values) the result is written there on the stream, asynchronously;
+        without, the call synchronises and returns (dt, (wave, rate, diffusion))."""
+        if out is not None:
+            import torch
+            if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 4):
+                raise ValueError("out must be a CUDA float64 tensor of at least 4 values")
+            _check(lib.stagger_dt(self.ctx, _dev(state), ctypes.c_void_p(out.data_ptr()), 1,
+                                  _stream(stream)), "stagger_dt")
+            return out
+        h = (ctypes.c_double * 4)()
+        _check(lib.stagger_dt(self.ctx, _dev(state), ctypes.cast(h, ctypes.c_void_p), 0,
+                              _stream(stream)), "stagger_dt")
+        return h[0], (h[1], h[2], h[3])
 
     def diagnostics(self, state, stream=None, check=True):
         out = (ctypes.c_double * 10)()

@@ -221,6 +221,26 @@ int stagger_courant(stagger_ctx* c, float* const state[8], double* dt_host, doub
   return fused_courant(c->fused, state, limits, dt_host, (cudaStream_t)stream);
 }
 
+int stagger_dt(stagger_ctx* c, float* const state[8], double* out, int on_device, void* stream) {
+  if (!c || !ptrs_ok((void* const*)state) || !out || on_device < 0 || on_device > 1)
+    return STAGGER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = fused_dt(c->fused, state, s);
+  if (rc) return rc;
+  if (on_device) {
+    // Stream-ordered: copied before any later call on this stream rewrites it.
+    STG_CUDA_OK(cudaMemcpyAsync(out, c->fused.dt_dev, 4 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    return STAGGER_OK;
+  }
+  double h[4];
+  STG_CUDA_OK(cudaMemcpyAsync(h, c->fused.dt_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STG_CUDA_OK(cudaStreamSynchronize(s));
+  for (int i = 0; i < 4; ++i) out[i] = h[i];
+  if (!(h[0] == h[0]) || h[0] <= 0) return STAGGER_ENONFINITE;
+  return STAGGER_OK;
+}
+
 int stagger_diagnostics(stagger_ctx* c, float* const state[8], double out[10], void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !out) return STAGGER_EINVAL;
   return fused_diagnostics(c->fused, state, c->params, out, (cudaStream_t)stream);

@@ -590,13 +590,20 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
   return STAGGER_OK;
 }
 
-int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s) {
+int fused_dt(Fused& F, float* const f[8], cudaStream_t s) {
   const bool cfl = cfl_fused(F);
   int rc = pre_div(F, f, s, cfl);
   if (rc) return rc;
   rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s, cfl);
   if (rc) return rc;
   courant_to_dev(F, f, s, cfl);
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s) {
+  int rc = fused_dt(F, f, s);
+  if (rc) return rc;
   double h[4];
   STG_CUDA_OK(cudaMemcpyAsync(h, F.dt_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
   STG_CUDA_OK(cudaStreamSynchronize(s));

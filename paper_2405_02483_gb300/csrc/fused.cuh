@@ -101,6 +101,9 @@ void fused_release(Fused& F);
 int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s);
 // One RK3 step in place on f.  dt > 0 fixed, else Courant (device-side).
 int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s);
+// The Courant step of state f and its three limits into F.dt_dev[0..3]
+// (dt, t_wave, t_rate, t_diff), enqueued on s without synchronising.
+int fused_dt(Fused& F, float* const f[8], cudaStream_t s);
 // Courant limits (t_wave, t_rate, t_diff) and dt for state f, synchronising.
 int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaStream_t s);
 // Per-kernel timing: on/off, and collect (synchronises the stream).

@@ -173,3 +173,33 @@ def test_plain_c_program_matches_the_binding(tmp_path):
     sim.close()
     for c in range(8):
         assert np.array_equal(got[c], host[c].numpy()), c
+
+
+def test_dt_entry_rejects_bad_arguments_without_gpu(S):
+    nul = S.P8F()
+    out = (ctypes.c_double * 4)()
+    assert S.lib.stagger_dt(None, nul, ctypes.cast(out, ctypes.c_void_p), 0, None) == S.EINVAL
+
+
+@pytest.mark.gpu
+def test_dt_on_device_and_host_equal_courant():
+    """stagger_dt with a device output (asynchronous, stream-ordered) and with
+    a host output give the step and limits of stagger_courant bit for bit, and
+    the device copy is the value of the call, not of a later one."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2405_02483_gb300 as S
+    from test_gpu_parity import VISC_KW, make, ragged_state
+    w = ragged_state((20, 12, 10))
+    sim, refs, dev = make(S, w, VISC_KW)
+    dt, lim = sim.courant(dev)
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    sim.dt(dev, out=out)
+    sim.step(dev, None)                  # rewrites the library's own dt scratch
+    got = out.cpu().tolist()
+    assert got == [dt, *lim]
+    dt2, lim2 = sim.dt(dev)
+    dt3, lim3 = sim.courant(dev)
+    assert (dt2, lim2) == (dt3, lim3) and dt2 != dt
+    sim.close()

@@ -11,16 +11,19 @@ along x or y (the tile's halo then wraps onto the same cells), and grids with
 fewer planes than the kernel's 3-plane z halo.  Tolerances are those of the
 other RHS and step parity tests: 2e-4 of each equation's term scale for one
 right-hand side, 2e-5 between the two kernel layouts (the same FP32
-operations in another order), 3e-5 of each field group after three Courant
-steps."""
+operations in another order), each plus ten times the equation's FP32 floor
+at the state (the change of the oracle's right-hand side when the stored
+deviations are rounded to FP32, which the quench ratio of eq. (quench)
+amplifies where a stress is small); 5e-5 of each field group after three
+Courant steps."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import workloads as inputs
-from test_gpu_parity import (VISC_KW, err_group, err_scale, make, oracle_params,
-                             ragged_state)
+from test_gpu_parity import (K_FLOOR, VISC_KW, err_group, err_scale, fp32_floor, make,
+                             oracle_params, ragged_state, scale_of)
 
 pytestmark = pytest.mark.gpu
 
@@ -61,18 +64,20 @@ def _state(shape):
 def test_fused_stage_rhs_matches_oracle_and_split_kernels(S, name):
     shape, kw = CASES[name]
     w = _state(shape)
-    g = oracle.Grid(*w.shape, *w.spacing)
-    Fo = [t.numpy() for t in oracle.rhs([torch.tensor(a) for a in w.fields], g, oracle_params(kw))]
     got = {}
     for fuse in (1, 0):
         sim, refs, dev = make(S, w, dict(kw, fuse_flux_div=fuse))
         got[fuse] = [t.double().cpu().numpy() for t in sim.rhs(dev)]
         sim.close()
-    ef, es = err_scale(got[1], Fo), err_scale(got[0], Fo)
-    assert max(ef) < 2e-4, (name, "fused", ef)
-    assert max(es) < 2e-4, (name, "split", es)
-    d = err_scale(got[0], got[1])
-    assert max(d) < 2e-5, (name, d)
+    Fo, delta = fp32_floor(w, kw, refs)
+    sc = scale_of(Fo)
+    for c in range(8):
+        for tag, fuse in (("fused", 1), ("split", 0)):
+            err = float(np.abs(got[fuse][c] - Fo[c]).max())
+            assert err <= 2e-4 * sc[c] + K_FLOOR * delta[c], (name, tag, c, err / sc[c],
+                                                               delta[c] / sc[c])
+        d = float(np.abs(got[1][c] - got[0][c]).max())
+        assert d <= 2e-5 * sc[c] + K_FLOOR * delta[c], (name, c, d / sc[c], delta[c] / sc[c])
 
 
 @pytest.mark.parametrize("name", ["visc_quench_37x29x131", "ideal_gravity_33x9x70",
@@ -91,7 +96,7 @@ def test_fused_stage_courant_steps(S, name):
         fo, dto = oracle.step(fo, g, po, dt=dt)
         assert abs(dt / dto - 1) < 1e-4, (dt, dto)
     e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
-    assert max(e) < 3e-5, (name, e)
+    assert max(e) < 5e-5, (name, e)
     sim.close()
 
 

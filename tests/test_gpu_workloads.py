@@ -100,6 +100,33 @@ def test_orszag_tang_128_200_steps(S, quench):
     sim.close()
 
 
+def test_orszag_tang_1024_2000_steps_conservation(S):
+    """The Orszag-Tang workload at its stated size: 1024^2 x 1 cells, 2000
+    Courant steps with the viscous physics and the quench, FP64 diagnostics
+    every 10 steps.  Mass is conserved to the FP32 random walk of the stored
+    deviations (each cell update rounds at ulp(rho') ~ 4e-9; sqrt(3 x 2000 x
+    2^20) ~ 8e4 such roundings sum to ~3e-4 absolute, 1.5e-9 of the total
+    mass; bound 1e-8); the net momentum of the symmetric vortex stays at
+    rounding level (bound 1e-6 of the cells times the largest momentum, 1e-3);
+    div B stays at the FP32 rounding of the curl (bound 1e-3 / h); nothing
+    becomes non-finite."""
+    n, steps = 1024, 2000
+    w = inputs.orszag_tang(n, n, 1)
+    refs, dev = S.split_state(w.fields)
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **VISC_KW))
+    d0 = sim.diagnostics(dev)
+    pmax = max(float(t.abs().max()) for t in dev[1:3])
+    for k in range(steps // 10):
+        sim.run(dev, 10)
+        d = sim.diagnostics(dev)
+        assert d[9] == 0, k
+        assert abs(d[0] - d0[0]) < 1e-8 * d0[0], (k, d[0], d0[0])
+        assert abs(d[1]) < 1e-6 * n * n * pmax and abs(d[2]) < 1e-6 * n * n * pmax, (k, d[1], d[2])
+        assert d[3] == 0.0                           # pz stays exactly 0 on one plane
+        assert d[7] < 1e-3 * n, (k, d[7])
+    sim.close()
+
+
 def _ke_box(f, g, lo=12, hi=20):
     """1/2 sum p_d^2 / rho_face over the sub-box (FP64, oracle operators)."""
     r = f[0]
@@ -162,8 +189,8 @@ def test_differentiation_workload_fp32_rollout_32(S):
 
 
 def test_differentiation_workload_fp64_32(S):
-    """FP64 GPU reverse sweep over 40 steps: (1) quenched physics, against the
-    oracle's independent reverse sweep; (2) quench off, against FP64 central
+    """FP64 GPU reverse sweep over 40 steps: (1) quenched physics, both readings
+    of eq. (quench), against the oracle's independent reverse sweep; (2) quench off, against FP64 central
     differences of the GPU's own FP64 step along 20 seeded directions of the
     initial momenta.  The 40-step map is only piecewise smooth (3-cell maxima,
     max(0, -div u), and with the quench its ratio maxima), so central
@@ -176,8 +203,8 @@ def test_differentiation_workload_fp64_32(S):
     g = oracle.Grid(*w.shape, *w.spacing)
     refs, dev = S.split_state(w.fields)
     base = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
-    for quench in (1, 0):
-        kw = dict(VISC_KW, do_quench=quench)
+    for quench in ("max3", "point", "off"):
+        kw = dict(VISC_KW, do_quench=int(quench != "off"), quench_max3=int(quench == "max3"))
         sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **kw))
         dts = [0.8 * sim.courant(dev)[0]] * nsteps
 
@@ -198,9 +225,17 @@ def test_differentiation_workload_fp64_32(S):
         lam64 = [l.cuda() for l in lam64]
         for i in range(nsteps - 1, -1, -1):
             lam64 = sim.step_adjoint_f64(traj[i], dts[i], lam64)
-        if quench:
-            e = _rel_l2([t.cpu() for t in lam64], _oracle_grad(w, g, VISC_O, dts))
-            assert e < 1e-8, e
+        if quench != "off":
+            po = oracle.Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=True,
+                               quench_max3=quench == "max3")
+            e = _rel_l2([t.cpu() for t in lam64], _oracle_grad(w, g, po, dts))
+            # The 40-step map switches branch (3-cell maxima, |T| at zero) on
+            # roundoff: the oracle's own adjoint moves by 9.5e-3 (max3|T|)
+            # and 1.9e-1 (point |T|) in relative L2 when the initial state is
+            # perturbed by 1e-15.  The GPU's FP64 graph repeats the oracle's
+            # arithmetic closely enough to follow the same branches: 1e-8 with
+            # max3|T|; with the point value the two agree to 1.2e-4.
+            assert e < (1e-8 if quench == "max3" else 1e-3), (quench, e)
             sim.close()
             continue
         gen = torch.Generator(device="cuda").manual_seed(40)
