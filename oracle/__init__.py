@@ -9,4 +9,6 @@ from .stagger import (  # noqa: F401
     Grid, Params, up, dn, ddup, dddn, rhs, rhs_parts, rk3_step, step, courant_dt,
     courant_fields, courant_limits,
     diagnostics, step_adjoint, quench, max3, smooth3, ALPHA, BETA,
+    mirror_extend, fill_wall_ghosts, rhs_walls, courant_walls, step_walls, diagnostics_walls,
+    WALL_PARITY, Z_FACE,
 )

@@ -665,3 +665,147 @@ def diagnostics(f, g: Grid, p: Params):
             float((pz * wf).sum()), float((E * wc).sum()),
             float(kin), float(mag), float(divb.abs().max()), float(divb.pow(2).mean().sqrt()),
             float(nonfinite)]
+
+
+# --------------------------------------------------------------------------
+# Closed walls along z, Sect. "Boundary Conditions" ("Closed"), reading R22
+# --------------------------------------------------------------------------
+#
+# The box is periodic in x and y and closed at two boundary points in z, the
+# cell-centre planes lb and ub of the arrays (planes outside [lb, ub] are
+# ghost planes).  Every field is continued across a boundary point by
+# reflection about it, with the parity of the field: rho, E (so e), the
+# parallel momenta and B_z even; the normal momentum p_z and the parallel
+# field components B_x, B_y odd (the paper's symmetric parallel velocity,
+# anti-symmetric normal velocity and anti-symmetric parallel field; B_z even
+# keeps div B = 0 across the wall).  The right-hand side of the closed box is
+# then the periodic right-hand side of the mirror-symmetric state on the box
+# doubled about one wall, restricted to the physical planes: centres lb..ub,
+# z faces lb+1..ub.  Gravity along z is odd under the reflection, so it acts
+# with its own sign on the physical faces only.
+
+WALL_PARITY = (1.0, 1.0, 1.0, -1.0, 1.0, -1.0, -1.0, 1.0)   # r px py pz E Bx By Bz
+Z_FACE = (False, False, False, True, False, False, False, True)
+
+
+def mirror_extend(f, lb, ub):
+    """The doubled periodic state (period P = 2 (ub - lb) planes along z) of
+    the physical planes of a closed box: doubled centre plane m holds
+    physical centre lb + m for 0 <= m <= ub - lb and the reflection about ub
+    (times the parity) beyond; doubled face plane m (the face below doubled
+    centre m) holds physical face lb + m for 1 <= m <= ub - lb and the
+    reflection beyond.  Odd centred fields vanish on the boundary points."""
+    L = ub - lb
+    P = 2 * L
+    out = []
+    for c, a in enumerate(f):
+        s = WALL_PARITY[c]
+        d = torch.empty((P,) + tuple(a.shape[1:]), dtype=a.dtype)
+        for m in range(P):
+            if Z_FACE[c]:
+                if 1 <= m <= L:
+                    d[m] = a[lb + m]
+                else:
+                    mm = m if m > L else P
+                    d[m] = s * a[2 * ub - lb - mm + 1]
+            else:
+                if m <= L:
+                    d[m] = a[lb + m] if (s > 0 or (m != 0 and m != L)) else 0.0 * a[lb + m]
+                else:
+                    d[m] = s * a[2 * ub - lb - m]
+        out.append(d)
+    return out
+
+
+def fill_wall_ghosts(f, lb, ub):
+    """The state with its ghost planes (z < lb, z > ub for centres; faces <= lb
+    and > ub) set by the reflection of R22, and the odd centred fields zeroed
+    on the boundary points: the continuation the right-hand side of the closed
+    box implies, written into the arrays' own ghost planes."""
+    nz = f[0].shape[0]
+    out = [a.clone() for a in f]
+    for c, a in enumerate(out):
+        s = WALL_PARITY[c]
+        for k in range(nz):
+            if Z_FACE[c]:
+                if k <= lb:
+                    src = 2 * lb + 1 - k
+                elif k > ub:
+                    src = 2 * ub + 1 - k
+                else:
+                    continue
+            else:
+                if k < lb:
+                    src = 2 * lb - k
+                elif k > ub:
+                    src = 2 * ub - k
+                elif s < 0 and k in (lb, ub):
+                    a[k] = 0.0
+                    continue
+                else:
+                    continue
+            a[k] = s * f[c][src]
+    return out
+
+
+def _doubled_grid(g: Grid, P):
+    return Grid(g.nx, g.ny, P, g.dx, g.dy, g.dz)
+
+
+def rhs_walls(f, g: Grid, p: Params, lb, ub):
+    """F(f) of the closed box (reading R22): the periodic right-hand side of
+    the doubled mirror-symmetric state, restricted to the physical planes, with
+    gravity along z on the physical z faces.  Ghost planes of the result are
+    zero."""
+    d = mirror_extend([fi.to(DT) for fi in f], lb, ub)
+    L = ub - lb
+    pd = Params(**{**p.__dict__, "g": (p.g[0], p.g[1], 0.0)})
+    parts = rhs_parts(d, _doubled_grid(g, 2 * L), pd)
+    Fd = [parts[k] for k in _DKEYS]
+    out = [torch.zeros_like(fi, dtype=DT) for fi in f]
+    for c in range(8):
+        if Z_FACE[c]:
+            out[c][lb + 1:ub + 1] = Fd[c][1:L + 1]
+        else:
+            out[c][lb:ub + 1] = Fd[c][0:L + 1]
+    if p.g[2] != 0.0:
+        out[3][lb + 1:ub + 1] += parts["rz"][1:L + 1] * p.g[2]
+    return out
+
+
+def courant_walls(f, q1, g: Grid, p: Params, lb, ub):
+    """eq. (courantcond) of the closed box: the limits over the physical planes,
+    taken on the doubled state (whose other half repeats them)."""
+    L = ub - lb
+    d = mirror_extend([fi.to(DT) for fi in f], lb, ub)
+    qd = mirror_extend([qi.to(DT) for qi in q1], lb, ub)
+    gd = _doubled_grid(g, 2 * L)
+    return courant_dt(d, qd, gd, Params(**{**p.__dict__, "g": (p.g[0], p.g[1], 0.0)}))
+
+
+def step_walls(f, g: Grid, p: Params, lb, ub, dt=None):
+    """One full time step of the closed box (R9 for the Courant step); the
+    ghost planes of the result hold the reflection of its physical planes."""
+    f = fill_wall_ghosts([fi.to(DT) for fi in f], lb, ub)
+    if dt is None:
+        q1 = rhs_walls(f, g, p, lb, ub)
+        dt, _ = courant_walls(f, q1, g, p, lb, ub)
+    out = rk3_step(f, dt, lambda s: rhs_walls(s, g, p, lb, ub))
+    return fill_wall_ghosts(out, lb, ub), dt
+
+
+def diagnostics_walls(f, g: Grid, p: Params, lb, ub):
+    """The totals of the closed box: half the plain sums over the doubled
+    state (centre planes lb, ub count one half, faces lb+1..ub once) -- the
+    totals the closed box conserves -- except the sum of p_z, which is odd and
+    sums to zero over the doubled state, taken as the plain sum over the
+    physical faces lb+1..ub; max |div B| and rms div B over the doubled
+    centres; the non-finite count of the physical planes."""
+    L = ub - lb
+    d = mirror_extend([fi.to(DT) for fi in f], lb, ub)
+    out = diagnostics(d, _doubled_grid(g, 2 * L), p)
+    for i in range(7):
+        out[i] = 0.5 * out[i]
+    out[3] = float(f[3][lb + 1:ub + 1].to(DT).sum())
+    out[9] = float(sum(int((~torch.isfinite(fi[lb:ub + 1])).sum()) for fi in f))
+    return out
