@@ -134,7 +134,39 @@ typedef struct {
    * negative or non-finite quench_eps: STAGGER_EINVAL. */
   int quench_max3;
   double quench_eps;
+  /* Closed walls along z (Sect. "Boundary Conditions", "Closed"), x and y
+   * staying periodic.  zwalls 0 (default): z periodic.  zwalls 1: the
+   * boundary points are the centre planes zghost and nz - 1 - zghost of the
+   * arrays; the zghost planes beyond each are ghost planes, and the physical
+   * fields are the centre planes zghost .. nz-1-zghost and the z faces
+   * zghost+1 .. nz-1-zghost (p_z, B_z).  Every field is continued across a
+   * boundary point by reflection about it with its parity: rho, E (so e),
+   * p_x, p_y and B_z even, p_z, B_x and B_y odd (the paper's symmetric
+   * parallel and anti-symmetric normal velocity, anti-symmetric parallel
+   * field; B_z even keeps div B = 0); the odd centred fields are zero on the
+   * boundary planes.  The library writes the ghost planes of the state it is
+   * given (stagger_rhs, stagger_step, stagger_dt, stagger_courant,
+   * stagger_diagnostics refill them before use, and a step leaves them
+   * filled), zeroes those of a time derivative, takes the Courant step over
+   * the physical planes only, and reports the totals the closed box
+   * conserves (half weight on the boundary planes; sum p_z over the physical
+   * faces).  zghost >= STAGGER_ZGHOST_MIN (the reach of the right-hand side)
+   * and nz >= 2 zghost + 2, a uniform z, no Smagorinsky term (whose
+   * strain-rate centring reaches three cells further) and zero ref[] of the
+   * odd fields p_z, B_x, B_y (the reflection acts on the stored deviations),
+   * else STAGGER_EINVAL.  The op-graph
+   * entries (stagger_rhs_unfused*, stagger_step_unfused_f64,
+   * stagger_step_adjoint*) and stagger_diagnostics_noalloc return
+   * STAGGER_EUNSUPPORTED with walls.  Gravity along z acts on the physical
+   * faces; a stratified atmosphere is not in balance at a wall under this
+   * continuation (the density is reflected, not extrapolated). */
+  int zwalls;
+  int zghost;
 } stagger_params;
+
+/* Ghost planes needed at each closed z wall: the reach of the right-hand
+ * side along an axis (14 cells with viscosity and the quench). */
+#define STAGGER_ZGHOST_MIN 14
 
 /* Fill *p with the defaults of the paper's namelists: gamma 5/3, ideal MHD,
  * nuE = nuB = 1, qmax 8, qlim 2 (quench_eps 1e-4), log_interp 1, Cdt 0.4, Cdtr 0.1, Cdtd 0.7,

@@ -718,33 +718,22 @@ def mirror_extend(f, lb, ub):
 
 
 def fill_wall_ghosts(f, lb, ub):
-    """The state with its ghost planes (z < lb, z > ub for centres; faces <= lb
-    and > ub) set by the reflection of R22, and the odd centred fields zeroed
-    on the boundary points: the continuation the right-hand side of the closed
-    box implies, written into the arrays' own ghost planes."""
+    """The state with its ghost planes set to the doubled periodic extension
+    of its physical planes (reading R22): plane k of a centred field is plane
+    m = (k - lb) mod P of the doubled state (P = 2 (ub - lb)), and likewise for
+    the z faces; the odd centred fields are zeroed on the boundary points.
+    This is the continuation the right-hand side of the closed box implies,
+    written into the arrays' own ghost planes (repeated reflections when the
+    box is thinner than the ghost layers)."""
     nz = f[0].shape[0]
+    L = ub - lb
+    P = 2 * L
+    d = mirror_extend(f, lb, ub)
     out = [a.clone() for a in f]
-    for c, a in enumerate(out):
-        s = WALL_PARITY[c]
+    for c in range(8):
         for k in range(nz):
-            if Z_FACE[c]:
-                if k <= lb:
-                    src = 2 * lb + 1 - k
-                elif k > ub:
-                    src = 2 * ub + 1 - k
-                else:
-                    continue
-            else:
-                if k < lb:
-                    src = 2 * lb - k
-                elif k > ub:
-                    src = 2 * ub - k
-                elif s < 0 and k in (lb, ub):
-                    a[k] = 0.0
-                    continue
-                else:
-                    continue
-            a[k] = s * f[c][src]
+            m = (k - lb) % P
+            out[c][k] = d[c][m]
     return out
 
 

@@ -47,7 +47,10 @@ class Params(ctypes.Structure):
                 ("t_chromo", ctypes.c_double), ("rho_bot", ctypes.c_double),
                 ("cor_L0", ctypes.c_double), ("cor_Tunit", ctypes.c_double),
                 ("fuse_flux_div", ctypes.c_int),
-                ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double)]
+                ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double),
+                ("zwalls", ctypes.c_int), ("zghost", ctypes.c_int)]
+
+ZGHOST_MIN = 14   # STAGGER_ZGHOST_MIN of include/stagger.h
 
 
 P8F = ctypes.POINTER(ctypes.c_float) * 8

@@ -54,6 +54,14 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (p->fuse_flux_div < 0 || p->fuse_flux_div > 1) return STAGGER_EINVAL;
   if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
     return STAGGER_EINVAL;
+  if (p->zwalls < 0 || p->zwalls > 1) return STAGGER_EINVAL;
+  // Closed z walls: at least the reach of the right-hand side in ghost planes
+  // at each end, one physical spacing between the boundary planes, uniform z.
+  if (p->zwalls && (p->zghost < STAGGER_ZGHOST_MIN || g->nz < 2 * p->zghost + 2 || p->zc ||
+                    p->csmag > 0))
+    return STAGGER_EINVAL;
+  // The reflection acts on the stored deviations: the odd fields need a zero background.
+  if (p->zwalls && (p->ref[3] != 0 || p->ref[5] != 0 || p->ref[6] != 0)) return STAGGER_EINVAL;
   if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;
@@ -491,22 +499,26 @@ int stagger_step_adjoint(stagger_ctx* c, float* const state_n[8], double dt,
   if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
       !ptrs_ok((void* const*)lam_n) || !(dt > 0))
     return STAGGER_EINVAL;
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
   return graph_step_adjoint<float>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
 }
 
 int stagger_rhs_unfused(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
   return graph_rhs<float>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_rhs_unfused_f64(stagger_ctx* c, double* const state[8], double* dfdt[8],
                             void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
   return graph_rhs<double>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_step_unfused_f64(stagger_ctx* c, double* state[8], double dt, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !(dt > 0)) return STAGGER_EINVAL;
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
   return graph_step<double>(c, state, dt, (cudaStream_t)stream);
 }
 
@@ -515,6 +527,7 @@ int stagger_step_adjoint_f64(stagger_ctx* c, double* const state_n[8], double dt
   if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
       !ptrs_ok((void* const*)lam_n) || !(dt > 0))
     return STAGGER_EINVAL;
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
   return graph_step_adjoint<double>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
 }
 

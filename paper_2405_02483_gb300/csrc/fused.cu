@@ -27,7 +27,7 @@ const char* const KNAMES[K_COUNT] = {"k_lr_ed", "k_vel", "k_strain2", "k_nu_raw"
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
                                      "k_d2flag", "k_cool2", "k_flux_e", "k_nu_maxsmooth",
-                                     "k_fdiv"};
+                                     "k_fdiv", "k_wall"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -108,6 +108,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.cells4 = (gr.nx % 4) == 0 && !p.scalar_cells;
   // One z-marching flux-divergence kernel per stage (on request; uniform z only).
   F.fdiv = p.fuse_flux_div && p.zc == nullptr;
+  // Closed z walls (R22): boundary centre planes zghost and nz - 1 - zghost.
+  F.wall = p.zwalls ? 1 : 0;
   F.launches = 0;
   F.timing = 0;
   for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
@@ -191,6 +193,9 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.emean = nullptr;
   k.corL0 = (float)p.cor_L0;
   k.corTu = (float)p.cor_Tunit;
+  k.wall = p.zwalls ? 1 : 0;
+  k.klo = p.zwalls ? p.zghost : 0;
+  k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
   F.zs = zs ? 1 : 0;
   F.wsum_f = zs ? (double)gr.nx * gr.ny * zfsum * k.izbar : (double)F.geo.n;
   F.cdt = p.Cdt;
@@ -407,7 +412,22 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
 // The Courant maxima are taken inside the stage kernels (wave speed in
 // k_nu_raw, <nu> in k_nu_maxsmooth or k_nu_smooth, rate in the mass and energy
 // k_div) when RM viscosity runs on a uniform mesh; otherwise by k_courant_part.
-static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs; }
+static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs && !F.wall; }
+
+// Closed z walls: fill the ghost planes of the eight state arrays f (and
+// zero the odd centred fields on the boundary planes), or zero the ghost
+// planes of a time derivative.
+static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) {
+  const Geo& g = F.geo;
+  Wall8 w;
+  for (int c = 0; c < 8; ++c) w.f[c] = f[c];
+  const int lb = F.kp.klo, ub = F.kp.khi;
+  const dim3 gg((unsigned)((g.sz + 255) / 256), (unsigned)(lb + 1 + (g.nz - ub)), 8);
+  if (zero)
+    TIMED(K_WALL, (k_wall_zero<<<gg, 256, 0, s>>>(w, lb, ub, g)));
+  else
+    TIMED(K_WALL, (k_wall_fill<<<gg, 256, 0, s>>>(w, lb, ub, g)));
+}
 
 static int pre_div(Fused& F, float* const f[8], cudaStream_t s, bool cfl = false) {
   const bool v4 = F.cells4 && aligned16(f, 8);
@@ -519,9 +539,14 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
 }
 
 int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s) {
+  if (F.wall) wall_launch(F, f, false, s);
   int st = pre_div(F, f, s);
   if (st) return st;
-  return launch_div(F, f, out, nullptr, 0.f, 0.f, 0, s);
+  st = launch_div(F, f, out, nullptr, 0.f, 0.f, 0, s);
+  if (st) return st;
+  if (F.wall) wall_launch(F, out, true, s);
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
 }
 
 template <class N>
@@ -558,6 +583,8 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
   float* const* st_out[3] = {B, C, A};
   for (int stg = 0; stg < 3; ++stg) {
     const bool cfl = stg == 0 && dt <= 0 && cfl_fused(F);
+    // Closed z walls: the stage input's ghost planes from its physical planes.
+    if (F.wall) wall_launch(F, st_in[stg], false, s);
     int rc = pre_div(F, st_in[stg], s, cfl);
     if (rc) return rc;
     float alpha = (float)RK_ALPHA[stg], beta = (float)RK_BETA[stg];
@@ -587,11 +614,14 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
     rc = launch_div(F, st_in[stg], F.q, const_cast<float**>(st_out[stg]), alpha, beta, 1, s);
     if (rc) return rc;
   }
+  if (F.wall) wall_launch(F, f, false, s);
+  STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
 
 int fused_dt(Fused& F, float* const f[8], cudaStream_t s) {
   const bool cfl = cfl_fused(F);
+  if (F.wall) wall_launch(F, f, false, s);
   int rc = pre_div(F, f, s, cfl);
   if (rc) return rc;
   rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s, cfl);
@@ -615,6 +645,7 @@ int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaSt
 
 int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
                       cudaStream_t s) {
+  if (F.wall) wall_launch(F, f, false, s);
   dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
   auto kdiag = F.zs ? k_diag_part<NbZ> : k_diag_part<Nb>;
   TIMED(K_DIAG, (kdiag<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], F.red,
@@ -627,11 +658,13 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
   for (int b = 0; b < F.red_blocks; ++b)
     for (int c = 0; c < 10; ++c)
       acc[c] = c == 7 ? fmax(acc[c], h[10 * b + c]) : acc[c] + h[10 * b + c];
-  const double N = (double)F.geo.n;
+  // Sums of the weights: every cell, or with closed z walls the physical
+  // centre planes (half weight on the two boundary planes) and faces.
+  const double N = F.wall ? (double)F.geo.sz * (F.kp.khi - F.kp.klo) : (double)F.geo.n;
   out[0] = acc[0] + p.ref[0] * N;
   out[1] = acc[1] + p.ref[1] * N;
   out[2] = acc[2] + p.ref[2] * N;
-  out[3] = acc[3] + p.ref[3] * F.wsum_f;   // z-face weights on a stretched z
+  out[3] = acc[3] + p.ref[3] * (F.wall ? N : F.wsum_f);   // z-face weights on a stretched z
   out[4] = acc[4] + p.ref[4] * N;
   out[5] = acc[5];
   out[6] = acc[6];
@@ -699,8 +732,10 @@ extern "C" int stagger_diagnostics_noalloc(const stagger_grid* grid, const stagg
   // check would have refused.
   int rc = validate_inputs(grid, p);
   if (rc) return rc;
-  // A stretched z needs its mesh on the device, which this entry cannot allocate.
-  if (p->zc || p->zf) return STAGGER_EUNSUPPORTED;
+  // A stretched z needs its mesh on the device, which this entry cannot
+  // allocate; closed z walls need their ghost planes refilled (a launch on
+  // the caller's state) and weighted sums: neither is offered here.
+  if (p->zc || p->zf || p->zwalls) return STAGGER_EUNSUPPORTED;
   const long long nb = (((long long)grid->nx + BX - 1) / BX) * (((long long)grid->ny + BY - 1) / BY) *
                        (((long long)grid->nz + BZ - 1) / BZ);
   if (nb > NOALLOC_MAX_BLOCKS) return STAGGER_EINVAL;  // grid larger than the fixed scratch

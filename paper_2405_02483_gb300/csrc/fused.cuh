@@ -39,6 +39,9 @@ struct KPar {
   float inv_tchromo, inv_rhobot;   // chromospheric cooling (0: off)
   const double* emean;  // plane means of e - e0, one per z (chromospheric cooling)
   float corL0, corTu;   // coronal thin cooling (corL0 0: off)
+  // Closed z walls (reading R22): the physical centre planes are klo..khi,
+  // the planes outside are ghost planes filled by reflection.
+  int wall, klo, khi;
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -63,7 +66,7 @@ enum Fld {
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
            K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_NU_MS,
-           K_FDIV, K_COUNT };
+           K_FDIV, K_WALL, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {
@@ -86,6 +89,7 @@ struct Fused {
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)
+  int wall;             // closed z walls: ghost planes refilled before every stage
   long long launches;
   // Optional per-kernel timing with CUDA events on the launch stream.
   int timing;

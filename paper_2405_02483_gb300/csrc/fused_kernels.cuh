@@ -1219,7 +1219,8 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? STG_MINB : STG_MINB_
   __shared__ unsigned sm[3][BX * BY * BZ / 32];
   N n;
   unsigned m[3] = {0u, 0u, 0u};
-  if (n.init(g, k)) {
+  // With closed z walls only the physical centre planes count.
+  if (n.init(g, k) && (!k.wall || (n.kz >= k.klo && n.kz <= k.khi))) {
     T ucx = s_up(AX(ux, 0)), ucy = s_up(AX(uy, 1)), ucz = s_up(AX(uz, 2));
     T bcx = s_up(AX(bx, 0)) + k.Bref[0], bcy = s_up(AX(by, 1)) + k.Bref[1],
       bcz = s_up(AX(bz, 2)) + k.Bref[2];
@@ -1297,14 +1298,22 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
   double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   if (n.init(g, k)) {
-    const double wc = N::ZS ? (double)n.hzc(k) * k.izbar : 1.0;
-    const double wf = N::ZS ? (double)n.hzf(k) * k.izbar : 1.0;
+    double wc = N::ZS ? (double)n.hzc(k) * k.izbar : 1.0;
+    double wf = N::ZS ? (double)n.hzf(k) * k.izbar : 1.0;
+    // Closed z walls (R22): the totals the closed box conserves weight the
+    // boundary centre planes by one half and count the faces klo+1..khi.
+    if (k.wall) {
+      const int kz = n.kz;
+      wc = (kz < k.klo || kz > k.khi) ? 0.0 : (kz == k.klo || kz == k.khi) ? 0.5 : 1.0;
+      wf = (kz > k.klo && kz <= k.khi) ? 1.0 : 0.0;
+    }
     const float* pr[3] = {px, py, pz};
     const float* bb[3] = {bx, by, bz};
     float vals[8] = {LDG(rd, n.c), LDG(px, n.c), LDG(py, n.c), LDG(pz, n.c),
                      LDG(Ed, n.c), LDG(bx, n.c), LDG(by, n.c), LDG(bz, n.c)};
     int bad = 0;
-    for (int c = 0; c < 8; ++c) bad += isfinite(vals[c]) ? 0 : 1;
+    if (!k.wall || wc > 0.0)
+      for (int c = 0; c < 8; ++c) bad += isfinite(vals[c]) ? 0 : 1;
     v[0] = vals[0] * wc;
     v[1] = vals[1] * wc;
     v[2] = vals[2] * wc;
@@ -1328,8 +1337,8 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
     }
     v[5] = kin;
     v[6] = mag;
-    v[7] = fabs(divb);
-    v[8] = divb * divb;
+    v[7] = (!k.wall || wc > 0.0) ? fabs(divb) : 0.0;
+    v[8] = divb * divb * (k.wall ? wc : 1.0);
     v[9] = bad;
   }
   for (int c = 0; c < 10; ++c) sm[c][tid] = v[c];
@@ -1346,5 +1355,60 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
   }
 }
 
+// ------------------------------------------------------- closed z walls ----
+// Ghost planes of a box closed at the centre planes lb and ub (reading R22):
+// every field is continued across a boundary plane by reflection about it,
+// times its parity (r, px, py, E, Bz even; pz, Bx, By odd).  Plane index m =
+// k - lb is folded into the doubled period P = 2 (ub - lb); centre fields map
+// mm in (L, P) to plane lb + P - mm, z-face fields (pz, Bz: the face below
+// centre k) map mm = 0 or mm > L to face lb + P - mm + 1.  The odd centred
+// fields are set to zero on the boundary planes themselves.  Every source is
+// a physical plane, never one this launch writes.
+struct Wall8 {
+  float* f[8];
+};
+__global__ void k_wall_fill(Wall8 w, int lb, int ub, Geo g) {
+  const int c = blockIdx.z;
+  const int nlo = lb + 1;                      // planes 0..lb, then ub..nz-1
+  const int pl = blockIdx.y;
+  const int k = pl < nlo ? pl : ub + (pl - nlo);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || k >= g.nz) return;
+  const bool face = c == 3 || c == 7;
+  const bool odd = c == 3 || c == 5 || c == 6;
+  const int L = ub - lb, P = 2 * L;
+  const int mm = ((k - lb) % P + P) % P;
+  float* a = w.f[c];
+  if (face) {
+    if (mm >= 1 && mm <= L) return;            // a physical face
+    const int src = lb + P - (mm == 0 ? P : mm) + 1;
+    const float v = a[(long long)src * m2 + i];
+    a[(long long)k * m2 + i] = odd ? -v : v;
+  } else {
+    if (mm <= L) {                             // a physical centre plane
+      if (odd && (k == lb || k == ub)) a[(long long)k * m2 + i] = 0.f;
+      return;
+    }
+    const int src = lb + P - mm;
+    const float v = a[(long long)src * m2 + i];
+    a[(long long)k * m2 + i] = odd ? -v : v;
+  }
+}
+
+// Zero the ghost planes of a time derivative (centres outside lb..ub, faces
+// outside lb+1..ub).
+__global__ void k_wall_zero(Wall8 w, int lb, int ub, Geo g) {
+  const int c = blockIdx.z;
+  const int nlo = lb + 1;
+  const int pl = blockIdx.y;
+  const int k = pl < nlo ? pl : ub + (pl - nlo);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || k >= g.nz) return;
+  const bool face = c == 3 || c == 7;
+  const bool ghost = face ? (k <= lb || k > ub) : (k < lb || k > ub);
+  if (ghost) w.f[c][(long long)k * m2 + i] = 0.f;
+}
 
 }  // namespace stg

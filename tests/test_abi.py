@@ -203,3 +203,19 @@ def test_dt_on_device_and_host_equal_courant():
     dt3, lim3 = sim.courant(dev)
     assert (dt2, lim2) == (dt3, lim3) and dt2 != dt
     sim.close()
+
+
+def test_wall_parameters_are_validated_without_gpu(S):
+    h = ctypes.c_void_p()
+    ok_nz = 2 * S.ZGHOST_MIN + 2
+    cases = [(S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=2, zghost=S.ZGHOST_MIN)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN - 1)),
+             (S.Grid(8, 8, ok_nz - 1, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN, csmag=0.1)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1),
+              dict(zwalls=1, zghost=S.ZGHOST_MIN, zc=[0.1] * ok_nz, zf=[0.1] * ok_nz)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1),
+              dict(zwalls=1, zghost=S.ZGHOST_MIN, ref=[1, 0, 0, 0, 1, 0.2, 0, 0.3]))]
+    for g, kw in cases:
+        q = S.default_params(**kw)
+        assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL, kw

@@ -132,6 +132,8 @@ def test_conservation_between_walls(p):
 
 
 def test_ghost_fill_is_the_reflection():
+    """Reflection about each boundary point, repeated where the box is thinner
+    than the ghost layers (6 physical spacings, 14 ghost planes)."""
     f, g, lb, ub = wall_state(4, 3, 6)
     fp = oracle.fill_wall_ghosts(f, lb, ub)
     for c in range(8):
@@ -143,3 +145,8 @@ def test_ghost_fill_is_the_reflection():
             else:
                 assert torch.equal(fp[c][lb - d], s * fp[c][lb + d])
                 assert torch.equal(fp[c][ub + d], s * fp[c][ub - d])
+        # every plane: reflection about lb of the reflection about ub, i.e. the
+        # shift by the doubled period 2 (ub - lb)
+        P = 2 * (ub - lb)
+        for k in range(P, fp[c].shape[0]):
+            assert torch.equal(fp[c][k], fp[c][k - P])
