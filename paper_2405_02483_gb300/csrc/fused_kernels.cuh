@@ -1358,12 +1358,15 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
 // ------------------------------------------------------- closed z walls ----
 // Ghost planes of a box closed at the centre planes lb and ub (reading R22):
 // every field is continued across a boundary plane by reflection about it,
-// times its parity (r, px, py, E, Bz even; pz, Bx, By odd).  Plane index m =
-// k - lb is folded into the doubled period P = 2 (ub - lb); centre fields map
-// mm in (L, P) to plane lb + P - mm, z-face fields (pz, Bz: the face below
-// centre k) map mm = 0 or mm > L to face lb + P - mm + 1.  The odd centred
-// fields are set to zero on the boundary planes themselves.  Every source is
-// a physical plane, never one this launch writes.
+// times its parity (r, px, py, E, Bz even; pz, Bx, By odd), repeatedly where
+// the box is thinner than the ghost layers.  The plane index m = k - lb of a
+// ghost plane is folded into the doubled period P = 2 L, L = ub - lb, as mm:
+// centre fields take plane lb + mm (mm <= L) or the reflection lb + P - mm,
+// z-face fields (pz, Bz: the face below centre k) face lb + mm (1 <= mm <= L)
+// or the reflection lb + P - mm + 1 (mm = 0 read as P).  The odd centred
+// fields are zero on the boundary planes themselves.  Every source is a
+// physical plane; none is written by this launch except those zeroed odd
+// boundary values, which are read as zero.
 struct Wall8 {
   float* f[8];
 };
@@ -1381,18 +1384,23 @@ __global__ void k_wall_fill(Wall8 w, int lb, int ub, Geo g) {
   const int mm = ((k - lb) % P + P) % P;
   float* a = w.f[c];
   if (face) {
-    if (mm >= 1 && mm <= L) return;            // a physical face
-    const int src = lb + P - (mm == 0 ? P : mm) + 1;
+    if (k > lb && k <= ub) return;             // a physical face
+    // doubled face mm: face lb + mm for 1 <= mm <= L, else the reflection
+    const bool dir = mm >= 1 && mm <= L;
+    const int src = dir ? lb + mm : lb + P - (mm == 0 ? P : mm) + 1;
     const float v = a[(long long)src * m2 + i];
-    a[(long long)k * m2 + i] = odd ? -v : v;
+    a[(long long)k * m2 + i] = (dir || !odd) ? v : -v;
   } else {
-    if (mm <= L) {                             // a physical centre plane
+    if (k >= lb && k <= ub) {                  // a physical centre plane
       if (odd && (k == lb || k == ub)) a[(long long)k * m2 + i] = 0.f;
       return;
     }
-    const int src = lb + P - mm;
-    const float v = a[(long long)src * m2 + i];
-    a[(long long)k * m2 + i] = odd ? -v : v;
+    // doubled centre mm: plane lb + mm for mm <= L, else the reflection
+    const bool dir = mm <= L;
+    const int src = dir ? lb + mm : lb + P - mm;
+    // an odd field is zero on the boundary planes (zeroed by this launch)
+    const float v = (odd && (src == lb || src == ub)) ? 0.f : a[(long long)src * m2 + i];
+    a[(long long)k * m2 + i] = (dir || !odd) ? v : -v;
   }
 }
 
