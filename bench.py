@@ -66,10 +66,10 @@ NCU_TRAFFIC_PER_CELL = {"k_flux": 1112.1e6 / 192 ** 3, "k_flux_e": 500.6e6 / 192
                         "k_edge": 762.6e6 / 192 ** 3, "k_tau": 710.2e6 / 192 ** 3,
                         # per unit of three launches, the mean over the three stages
                         "k_div": (940.6e6 + 2 * 1539.8e6) / 3 / 192 ** 3}
-# DRAM bytes per zone of one whole step (sum over its launches), from an ncu
-# launch list with DRAM counters of the same step at 192^3; None until taken
-# for the current kernels.
-STEP_TRAFFIC_PER_ZONE = None
+# DRAM bytes per zone of one whole step (read + write summed over its 38
+# launches), from an ncu launch list with DRAM counters of the same step at
+# 192^3 (traffic grows with the cells): 10.537 GB + 5.189 GB over 192^3 zones.
+STEP_TRAFFIC_PER_ZONE = (10537.0e6 + 5189.3e6) / 192 ** 3
 # Launches that together form one unit of KERNEL_ARRAYS.
 LAUNCHES_PER_UNIT = {"k_div": 3}
 FP32_LANES_PER_SM = 128         # FP32 multiply-add lanes per SM (4 partitions x 32)
