@@ -358,6 +358,7 @@ def main():
         out["adjoint"] = adjoint_cost(S, torch)
     if rank == 0 and not args.no_ot2d:
         out["orszag_tang_2d"] = orszag_tang_2d(S, torch)
+        out["ideal_mhd"] = ideal_mhd(S, torch, peak, n=n)
     sim.close()
     del dev
     torch.cuda.empty_cache()
@@ -367,6 +368,36 @@ def main():
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def ideal_mhd(S, torch, peak, n=512, steps=5):
+    """The same 512^3 turbulence state and Courant steps with every diffusion
+    term off (ideal MHD, the physics of the linear-wave workload): its step
+    time and both rooflines, for context beside the viscous headline."""
+    import workloads as inputs
+    w = inputs.turbulence(n, device="cuda")
+    refs, dev = S.split_state(w.fields)
+    del w
+    sim = S.Sim((n, n, n), (1.0 / n,) * 3, S.default_params(ref=refs))
+    for _ in range(3):
+        sim.step(dev, None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        sim.step(dev, None)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.close()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070.0e6
+    zps = n ** 3 / (ms * 1e-3)
+    fz = flops_per_zone("ideal")["flops"]
+    return {"workload": "MHD turbulence %d^3, ideal MHD (no diffusion), Courant dt" % n,
+            "ms_per_step": ms, "value": zps, "unit": UNIT,
+            "hbm_frac": STEP_BYTES_PER_ZONE * zps / (peak * 1e9),
+            "alu_frac": fz * zps / alu_peak, "flops_per_zone": fz}
 
 
 def orszag_tang_2d(S, torch, n=1024, steps=2000, every=10):
