@@ -461,7 +461,8 @@ def test_rollout_gradient_matches_oracle(S):
     lo = 0.5 * sum((t * t).sum() for t in cur[1:4])
     go = torch.autograd.grad(lo, xo)
     e = err_l2([t.grad.double().cpu().numpy() for t in x], [t.numpy() for t in go])
-    assert max(e) < 1e-3, e
+    # measured on GB300: 1.2e-6 (point-value quench), 6.5e-7 (max3), 7.5e-7 (no quench)
+    assert max(e) < 1e-5, e
     sim.close()
 
 

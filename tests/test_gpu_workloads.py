@@ -184,7 +184,11 @@ def test_differentiation_workload_fp32_rollout_32(S):
     torch.autograd.backward(list(y), [l.float().cuda() for l in lam])
     g32 = [t.grad.double().cpu() for t in x]
     e = _rel_l2(g32, _oracle_grad(w, g, po, dts))
-    assert e < 1e-3, e
+    # measured on GB300: 1.6e-4.  The 1e-4 the survey proposed is not met: FP32
+    # rounding over 40 steps passes through the kinks of max(0, -div u) and of
+    # the 3-cell maxima of nu, whose branches FP32 and FP64 take differently in
+    # a few cells.
+    assert e < 5e-4, e
     sim.close()
 
 
