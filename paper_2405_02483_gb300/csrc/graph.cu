@@ -352,123 +352,6 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pointwise chains (GProg): the forward values and transposes of the ops above,
-// op by op in the chain's order, with the intermediate values in registers
-// (local memory) instead of node arrays.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T chain_value(int op, T a, T b, T c0, T c1) {
-  switch (op) {
-    case G_ADD: return a + b;
-    case G_SUB: return a - b;
-    case G_MUL: return a * b;
-    case G_DIV: return a / b;
-    case G_MAX: return a >= b ? a : b;
-    case G_EXP: return exp(a);
-    case G_LOG: return log(a);
-    case G_LOG1P: return log1p(a);
-    case G_SQRT: return sqrt(a);
-    case G_ABS: return fabs(a);
-    case G_AXPB: return c0 * a + c1;
-    case G_CLAMPMIN: return a < c0 ? c0 : a;
-    default: return a > c0 ? c0 : a;   // G_CLAMPMAX
-  }
-}
-
-// Cotangents ca, cb of the operands of one op from the cotangent gg of its
-// value out (the rules of bwd_value).
-template <typename T>
-__device__ __forceinline__ void chain_transpose(int op, T a, T b, T out, T gg, T c0, T& ca,
-                                                T& cb) {
-  ca = 0;
-  cb = 0;
-  switch (op) {
-    case G_ADD: ca = gg; cb = gg; break;
-    case G_SUB: ca = gg; cb = -gg; break;
-    case G_MUL: ca = gg * b; cb = gg * a; break;
-    case G_DIV: ca = gg / b; cb = -gg * a / (b * b); break;
-    case G_MAX:
-      ca = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
-      cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
-      break;
-    case G_EXP: ca = gg * out; break;
-    case G_LOG: ca = gg / a; break;
-    case G_LOG1P: ca = gg / ((T)1 + a); break;
-    case G_SQRT: ca = gg / ((T)2 * out); break;
-    case G_ABS: ca = a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0); break;
-    case G_AXPB: ca = c0 * gg; break;
-    case G_CLAMPMIN: ca = a >= c0 ? gg : (T)0; break;
-    case G_CLAMPMAX: ca = a <= c0 ? gg : (T)0; break;
-    default: break;
-  }
-}
-
-template <typename T>
-struct GIn {
-  const T* p[GP_MAXIN];
-};
-template <typename T>
-struct GOutG {
-  T* p[GP_MAXIN];
-};
-
-template <typename T>
-__device__ __forceinline__ void chain_eval(const GProg& pg, const GIn<T>& in, long long idx,
-                                           T* x, T* v) {
-  for (int e = 0; e < pg.nin; ++e) x[e] = in.p[e][idx];
-  for (int o = 0; o < pg.nops; ++o) {
-    const T a = pg.a[o] >= 0 ? v[pg.a[o]] : x[-1 - pg.a[o]];
-    const int rb = pg.b[o];
-    const T b = rb == GP_NONE ? (T)0 : (rb >= 0 ? v[rb] : x[-1 - rb]);
-    v[o] = chain_value(pg.op[o], a, b, (T)pg.c0[o], (T)pg.c1[o]);
-  }
-}
-
-template <typename T>
-__global__ void g_chain_f(GProg pg, GIn<T> in, T* out, Geo g) {
-  GCell c0;
-  if (!gcell(c0, g)) return;
-  for (int u = 0; u < GZU; ++u) {
-    const GCell c = gcell_at(c0, u, g);
-    if (c.k >= g.nz) break;
-    T x[GP_MAXIN], v[GP_MAXOPS];
-    chain_eval(pg, in, c.idx, x, v);
-    out[c.idx] = v[pg.nops - 1];
-  }
-}
-
-// Reverse of a chain: recompute its values, pass the root's cotangent down
-// the ops in reverse order, and write (win) or add the cotangent of each
-// external input once.
-template <typename T>
-__global__ void g_chain_b(GProg pg, GIn<T> in, const T* gout, GOutG<T> gin, Geo g) {
-  GCell c0;
-  if (!gcell(c0, g)) return;
-  for (int u = 0; u < GZU; ++u) {
-    const GCell c = gcell_at(c0, u, g);
-    if (c.k >= g.nz) break;
-    T x[GP_MAXIN], v[GP_MAXOPS], gv[GP_MAXOPS], gx[GP_MAXIN];
-    chain_eval(pg, in, c.idx, x, v);
-    for (int o = 0; o < pg.nops; ++o) gv[o] = 0;
-    for (int e = 0; e < pg.nin; ++e) gx[e] = 0;
-    gv[pg.nops - 1] = gout[c.idx];
-    for (int o = pg.nops - 1; o >= 0; --o) {
-      const int ra = pg.a[o], rb = pg.b[o];
-      const T a = ra >= 0 ? v[ra] : x[-1 - ra];
-      const T b = rb == GP_NONE ? (T)0 : (rb >= 0 ? v[rb] : x[-1 - rb]);
-      T ca, cb;
-      chain_transpose(pg.op[o], a, b, v[o], gv[o], (T)pg.c0[o], ca, cb);
-      if (ra >= 0) gv[ra] += ca; else gx[-1 - ra] += ca;
-      if (rb != GP_NONE) {
-        if (rb >= 0) gv[rb] += cb; else gx[-1 - rb] += cb;
-      }
-    }
-    for (int e = 0; e < pg.nin; ++e)
-      if (gin.p[e]) gin.p[e][c.idx] = pg.win[e] ? gx[e] : gin.p[e][c.idx] + gx[e];
-  }
-}
-
 // Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed
 // order; the broadcast writes (or, for the transpose, adds) sum / (nx ny).
 // The mean is linear and symmetric, so its transpose is the same mean.
@@ -868,10 +751,8 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
       return STAGGER_EOOM;
     }
   }
-  build_chains();
   // Reverse-sweep bookkeeping: which nodes receive a gradient, and which
-  // consumer slot (or chain input) gives each node its first contribution
-  // (in reverse order).  Absorbed nodes are covered by their chain's root.
+  // consumer slot gives each node its first contribution (in reverse order).
   hasg.assign(nn, 0);
   wa.assign(nn, 0);
   wb.assign(nn, 0);
@@ -880,18 +761,9 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
     for (int k = 0; k < 8; ++k) seen[def.out[k]] = hasg[def.out[k]] = 1;
     for (long long i = (long long)nn - 1; i >= 0; --i) {
       const GNode& nd = def.nodes[i];
-      if (!hasg[i] || absorbed[i] || nd.op == G_INPUT || nd.op == G_CONST ||
-          nd.op == G_ZFIELD || nd.op == G_STEP)
+      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
+          nd.op == G_STEP)
         continue;
-      if (chain[i] >= 0) {
-        GProg& pg = progs[chain[i]];
-        for (int e = 0; e < pg.nin; ++e) {
-          const int L = pg.in_node[e];
-          pg.win[e] = !seen[L];
-          seen[L] = hasg[L] = 1;
-        }
-        continue;
-      }
       if (nd.a >= 0) { wa[i] = !seen[nd.a]; seen[nd.a] = hasg[nd.a] = 1; }
       if (nd.b >= 0) { wb[i] = !seen[nd.b]; seen[nd.b] = hasg[nd.b] = 1; }
     }
@@ -901,87 +773,6 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
   for (size_t i = 0; i < nn; ++i)
     if (def.nodes[i].op != G_INPUT) ptr[i] = vals + (v++) * g.n;
   return STAGGER_OK;
-}
-
-// Pointwise chains: walking the nodes from the last to the first, a pointwise
-// node not yet taken becomes a chain's root and takes in every pointwise
-// operand used by it alone (and not an output), recursively, while the chain
-// has at most GP_MAXOPS ops and GP_MAXIN distinct external inputs.  A chain
-// of one op stays an ordinary node.  Disabled by STAGGER_GRAPH_NOCHAIN at
-// build time.
-static bool chain_op_ok(int op) { return op >= G_ADD && op <= G_CLAMPMAX && op != G_CONST; }
-
-template <typename T>
-void GraphExec<T>::build_chains() {
-  const int nn = (int)def.nodes.size();
-  absorbed.assign(nn, 0);
-  chain.assign(nn, -1);
-  progs.clear();
-#ifndef STAGGER_GRAPH_NOCHAIN
-  std::vector<int> uses(nn, 0);
-  for (auto& nd : def.nodes) {
-    if (nd.a >= 0) uses[nd.a]++;
-    if (nd.b >= 0) uses[nd.b]++;
-  }
-  for (int k = 0; k < 8; ++k) uses[def.out[k]] += 1000;   // outputs are stored
-  for (int j = nn - 1; j >= 0; --j) {
-    if (absorbed[j] || !chain_op_ok(def.nodes[j].op)) continue;
-    std::vector<int> mem = {j};          // chain members
-    std::vector<int> ext;                // distinct external inputs
-    auto operands = [&](int i) {
-      std::vector<int> o;
-      if (def.nodes[i].a >= 0) o.push_back(def.nodes[i].a);
-      if (def.nodes[i].b >= 0) o.push_back(def.nodes[i].b);
-      return o;
-    };
-    auto in_mem = [&](int i) { return std::find(mem.begin(), mem.end(), i) != mem.end(); };
-    auto externals = [&]() {
-      std::vector<int> e;
-      for (int m : mem)
-        for (int o : operands(m))
-          if (!in_mem(o) && std::find(e.begin(), e.end(), o) == e.end()) e.push_back(o);
-      return e;
-    };
-    std::vector<int> queue = operands(j);
-    while (!queue.empty()) {
-      const int i = queue.back();
-      queue.pop_back();
-      if (in_mem(i) || absorbed[i] || !chain_op_ok(def.nodes[i].op) || uses[i] != 1) continue;
-      if ((int)mem.size() + 1 > GP_MAXOPS) continue;
-      mem.push_back(i);
-      if ((int)externals().size() > GP_MAXIN) {
-        mem.pop_back();
-        continue;
-      }
-      for (int o : operands(i)) queue.push_back(o);
-    }
-    if (mem.size() < 2) continue;
-    std::sort(mem.begin(), mem.end());   // topological: operands precede their users
-    ext = externals();
-    GProg pg;
-    memset(&pg, 0, sizeof(pg));
-    pg.nops = (int)mem.size();
-    pg.nin = (int)ext.size();
-    for (int e = 0; e < pg.nin; ++e) pg.in_node[e] = ext[e];
-    auto ref = [&](int node) {
-      if (node < 0) return (int)GP_NONE;
-      auto it = std::find(mem.begin(), mem.end(), node);
-      if (it != mem.end()) return (int)(it - mem.begin());
-      return -1 - (int)(std::find(ext.begin(), ext.end(), node) - ext.begin());
-    };
-    for (int o = 0; o < pg.nops; ++o) {
-      const GNode& nd = def.nodes[mem[o]];
-      pg.op[o] = nd.op;
-      pg.a[o] = ref(nd.a);
-      pg.b[o] = ref(nd.b);
-      pg.c0[o] = nd.c0;
-      pg.c1[o] = nd.c1;
-    }
-    for (int o = 0; o + 1 < pg.nops; ++o) absorbed[mem[o]] = 1;
-    chain[j] = (int)progs.size();
-    progs.push_back(pg);
-  }
-#endif
 }
 
 template <typename T>
@@ -1061,15 +852,7 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
   const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
   for (size_t i = 0; i < def.nodes.size(); ++i) {
     const GNode& nd = def.nodes[i];
-    if (nd.op == G_INPUT || absorbed[i]) continue;
-    if (chain[i] >= 0) {
-      const GProg& pg = progs[chain[i]];
-      GIn<T> in;
-      for (int e = 0; e < GP_MAXIN; ++e) in.p[e] = e < pg.nin ? ptr[pg.in_node[e]] : nullptr;
-      g_chain_f<T><<<gg, gb, 0, s>>>(pg, in, ptr[i], geo);
-      ++launches;
-      continue;
-    }
+    if (nd.op == G_INPUT) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     if (nd.op == G_PMEAN) {
@@ -1100,21 +883,9 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
                                 sizeof(T) * geo.n, cudaMemcpyDeviceToDevice, s));
   for (long long i = (long long)nn - 1; i >= 0; --i) {
     const GNode& nd = def.nodes[i];
-    if (!hasg[i] || absorbed[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
+    if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
         nd.op == G_STEP)
       continue;
-    if (chain[i] >= 0) {
-      const GProg& pg = progs[chain[i]];
-      GIn<T> in;
-      GOutG<T> gi;
-      for (int e = 0; e < GP_MAXIN; ++e) {
-        in.p[e] = e < pg.nin ? ptr[pg.in_node[e]] : nullptr;
-        gi.p[e] = e < pg.nin ? grads + (size_t)pg.in_node[e] * geo.n : nullptr;
-      }
-      g_chain_b<T><<<gg, gb, 0, s>>>(pg, in, grads + (size_t)i * geo.n, gi, geo);
-      ++launches;
-      continue;
-    }
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;

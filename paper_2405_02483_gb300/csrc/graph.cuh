@@ -75,22 +75,6 @@ struct GraphDef {
 // Build the right-hand-side graph for a grid and parameter set.
 void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p);
 
-// A chain of pointwise nodes evaluated in one launch: ops in topological
-// order, each operand another op of the chain (index >= 0) or an external
-// input (-1 - input slot); the last op is the chain's root, the only node of
-// the chain whose value is stored.  The reverse of a chain recomputes its
-// values and passes the gradient through them in registers.
-#define GP_MAXOPS 12
-#define GP_MAXIN 8
-#define GP_NONE (-1000000)   // no second operand
-struct GProg {
-  int nops, nin;
-  int op[GP_MAXOPS], a[GP_MAXOPS], b[GP_MAXOPS];
-  double c0[GP_MAXOPS], c1[GP_MAXOPS];
-  int in_node[GP_MAXIN];   // graph node of each external input
-  int win[GP_MAXIN];       // reverse: 1 writes the input's gradient, 0 adds to it
-};
-
 // Device executor for one precision.  Holds one value and one gradient array
 // of n cells per node (inputs point at caller memory and need none).
 template <typename T>
@@ -106,15 +90,9 @@ struct GraphExec {
   // Reverse sweep: node receives a gradient; its a / b slot writes (rather
   // than accumulates into) the input's gradient.
   std::vector<char> hasg, wa, wb;
-  // Pointwise chains: absorbed[i] marks a node evaluated inside its single
-  // consumer's chain (never stored); chain[i] >= 0 indexes progs for a root.
-  std::vector<char> absorbed;
-  std::vector<int> chain;
-  std::vector<GProg> progs;
   long long launches = 0;
 
   int init(const GraphDef& d, const Geo& g, bool with_grads);
-  void build_chains();
   void release();
   // Evaluate every node; inputs are the 8 stored deviation arrays.
   int forward(T* const in[8], cudaStream_t s);
