@@ -65,6 +65,9 @@ CASES = {
                                  dict(nu_const=0.003, c1=-1 / 3, nuE=0.5, nuB=0.7,
                                       g=(0.1, 0.0, -1.0)), True),
     "viscous_quench_gravity_32x16x6": ((32, 16, 6), dict(VISC_KW, g=(0.0, 0.0, -1.0)), True),
+    "second_order_cooling_chromo_24x10x9": (
+        (24, 10, 9), dict(VISC_KW, do_2nddiv=1, d2lnr_lim=-1.0, t_cool=0.05, e_cool=0.7,
+                          rho_cool=1.02, cool_cut=1, t_chromo=0.2, rho_bot=1.1), True),
 }
 
 
