@@ -198,7 +198,11 @@ int stagger_rhs(stagger_ctx* ctx, float* const state[8], float* dfdt[8], void* s
  * then synchronises the stream and stores the step used.  Async otherwise. */
 int stagger_step(stagger_ctx* ctx, float* state[8], double dt, double* dt_used, void* stream);
 
-/* Run nsteps steps as stagger_step does, with dt <= 0 meaning Courant. */
+/* Run nsteps steps as stagger_step does, with dt <= 0 meaning Courant.
+ * A Courant-mode step (dt <= 0) with per-kernel timing off is replayed from a
+ * CUDA graph of its launches, captured on the first such call for the given
+ * state arrays (on a private stream; launched on `stream`) and captured again
+ * when the arrays change; stagger_step and stagger_step_host do the same. */
 int stagger_run(stagger_ctx* ctx, float* state[8], int nsteps, double dt, void* stream);
 
 /* The Courant step of eq. (courantcond) for this state (FP64 reduction on the

@@ -182,7 +182,7 @@ int stagger_rhs(stagger_ctx* c, float* const state[8], float* dfdt[8], void* str
 int stagger_step(stagger_ctx* c, float* state[8], double dt, double* dt_used, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !(dt == dt)) return STAGGER_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = fused_step(c->fused, state, dt, s);
+  int rc = fused_step_graphed(c->fused, state, dt, s);
   if (rc) return rc;
   if (dt_used) {
     double h;
@@ -196,7 +196,7 @@ int stagger_step(stagger_ctx* c, float* state[8], double dt, double* dt_used, vo
 int stagger_run(stagger_ctx* c, float* state[8], int nsteps, double dt, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || nsteps < 0 || !(dt == dt)) return STAGGER_EINVAL;
   for (int i = 0; i < nsteps; ++i) {
-    int rc = fused_step(c->fused, state, dt, (cudaStream_t)stream);
+    int rc = fused_step_graphed(c->fused, state, dt, (cudaStream_t)stream);
     if (rc) return rc;
   }
   return STAGGER_OK;
@@ -547,7 +547,7 @@ int stagger_step_host(stagger_ctx* c, float* state_host[8], int nsteps, double d
     STG_CUDA_OK(cudaMemcpyAsync(d[k], state_host[k], sizeof(float) * n, cudaMemcpyHostToDevice, s));
   }
   for (int i = 0; i < nsteps; ++i) {
-    int rc = fused_step(c->fused, d, dt, s);
+    int rc = fused_step_graphed(c->fused, d, dt, s);
     if (rc) return rc;
   }
   for (int k = 0; k < 8; ++k)

@@ -105,6 +105,11 @@ static bool aligned16(float* const* a, int n) {
 
 int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.geo = make_geo(gr.nx, gr.ny, gr.nz);
+  F.step_state = 0;
+  F.step_exec = nullptr;
+  F.cap = nullptr;
+  F.step_launches = 0;
+  for (int c = 0; c < 8; ++c) F.step_key[c] = nullptr;
   F.cells4 = (gr.nx % 4) == 0 && !p.scalar_cells;
   // One z-marching flux-divergence kernel per stage (on request; uniform z only).
   F.fdiv = p.fuse_flux_div && p.zc == nullptr;
@@ -299,6 +304,10 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
 }
 
 void fused_release(Fused& F) {
+  if (F.step_exec) cudaGraphExecDestroy(F.step_exec);
+  F.step_exec = nullptr;
+  if (F.cap) cudaStreamDestroy(F.cap);
+  F.cap = nullptr;
   for (auto& pe : F.pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   F.pending.clear();
   for (auto e : F.pool) cudaEventDestroy(e);
@@ -628,6 +637,50 @@ int fused_dt(Fused& F, float* const f[8], cudaStream_t s) {
   if (rc) return rc;
   courant_to_dev(F, f, s, cfl);
   STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+
+// A Courant-mode step is 38 to 50 launches whose arguments depend only on the
+// state arrays and the context (the step dt lives on the device), so it is
+// captured once, on a private stream, into a CUDA graph and replayed on the
+// caller's stream: on small grids the launches, not the kernels, set the time.
+// The capture is redone when the state arrays change, and not used while
+// per-kernel timing is on; a failed capture falls back to direct launches.
+int fused_step_graphed(Fused& F, float* f[8], double dt, cudaStream_t s) {
+  if (dt > 0 || F.timing || F.step_state < 0) return fused_step(F, f, dt, s);
+  bool same = F.step_state == 1;
+  for (int c = 0; c < 8 && same; ++c) same = F.step_key[c] == f[c];
+  if (!same) {
+    if (!F.cap && cudaStreamCreateWithFlags(&F.cap, cudaStreamNonBlocking) != cudaSuccess) {
+      F.cap = nullptr;
+      F.step_state = -1;
+      return fused_step(F, f, dt, s);
+    }
+    const long long l0 = F.launches;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamBeginCapture(F.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int rc = fused_step(F, f, dt, F.cap);
+      ok = cudaStreamEndCapture(F.cap, &graph) == cudaSuccess && rc == STAGGER_OK && graph;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    const long long nl = F.launches - l0;
+    F.launches = l0;
+    if (!ok) {
+      cudaGetLastError();   // clear a capture error; run the step directly from now on
+      F.step_state = -1;
+      return fused_step(F, f, dt, s);
+    }
+    if (F.step_exec) cudaGraphExecDestroy(F.step_exec);
+    F.step_exec = exec;
+    F.step_launches = nl;
+    for (int c = 0; c < 8; ++c) F.step_key[c] = f[c];
+    F.step_state = 1;
+  }
+  STG_CUDA_OK(cudaGraphLaunch(F.step_exec, s));
+  F.launches += F.step_launches;
   return STAGGER_OK;
 }
 

@@ -91,6 +91,13 @@ struct Fused {
   int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)
   int wall;             // closed z walls: ghost planes refilled before every stage
   long long launches;
+  // Courant-mode step captured as a CUDA graph for the state arrays step_key
+  // (step_state 0: not tried, 1: captured, -1: capture unavailable).
+  int step_state;
+  cudaGraphExec_t step_exec;
+  cudaStream_t cap;
+  float* step_key[8];
+  long long step_launches;
   // Optional per-kernel timing with CUDA events on the launch stream.
   int timing;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -105,6 +112,9 @@ void fused_release(Fused& F);
 int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s);
 // One RK3 step in place on f.  dt > 0 fixed, else Courant (device-side).
 int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s);
+// The same step; a Courant-mode step (dt <= 0) with timing off replays a CUDA
+// graph of its launches, captured once for these state arrays.
+int fused_step_graphed(Fused& F, float* f[8], double dt, cudaStream_t s);
 // The Courant step of state f and its three limits into F.dt_dev[0..3]
 // (dt, t_wave, t_rate, t_diff), enqueued on s without synchronising.
 int fused_dt(Fused& F, float* const f[8], cudaStream_t s);
