@@ -533,3 +533,31 @@ def test_zero_density_reference_with_energy_reference(S, sc):
     e = err_group(S.join_state(dev, refs), [t.numpy() for t in fo])
     sim.close()
     assert max(e) < 3e-5, e
+
+
+def test_graph_replayed_steps_equal_direct_launches(S):
+    """Courant-mode steps replayed from the captured CUDA graph equal the same
+    steps launched one kernel at a time (per-kernel timing on), bit for bit,
+    and the capture follows a change of state arrays; the launch count grows
+    by the captured launches on every replay."""
+    w, kw = _case("ragged37x29x11_visc_quench")
+    sim, refs, dev = make(S, w, kw)
+    a = [t.clone() for t in dev]
+    b = [t.clone() for t in dev]
+    c = [t.clone() for t in dev]
+    sim.timing(True)
+    for _ in range(3):
+        sim.step(a)
+    sim.kernel_times()
+    sim.timing(False)
+    l0 = sim.launches()
+    for _ in range(3):
+        sim.step(b)              # captured on the first call, replayed after
+    per_step = (sim.launches() - l0) / 3
+    sim.run(c, 2)                # other arrays: captured again
+    sim.step(c)
+    torch.cuda.synchronize()
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
+    assert all(torch.equal(x, y) for x, y in zip(a, c))
+    assert per_step == int(per_step) and per_step >= 36, per_step
+    sim.close()
