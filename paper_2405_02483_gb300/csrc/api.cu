@@ -440,6 +440,10 @@ static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* cons
                               T* lam_out[8], cudaStream_t s) {
   int rc = ensure_graph<T>(c, true);
   if (rc) return rc;
+  // The graph's sweeps on several streams: captured below as a DAG whose
+  // independent node kernels overlap.
+  rc = graph_of<T>(c)->enable_concurrency();
+  if (rc) return rc;
   rc = ensure_work<T>(c);
   if (rc) return rc;
   if (!c->dtp && cudaMalloc(&c->dtp, sizeof(double)) != cudaSuccess) {

@@ -776,7 +776,34 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
 }
 
 template <typename T>
+int GraphExec<T>::enable_concurrency() {
+  if (nconc) return STAGGER_OK;
+  for (int k = 0; k < GRAPH_NSTREAMS; ++k)
+    if (cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evjoin[k], cudaEventDisableTiming) != cudaSuccess)
+      return STAGGER_ECUDA;
+  if (cudaEventCreateWithFlags(&evfork, cudaEventDisableTiming) != cudaSuccess) return STAGGER_ECUDA;
+  evn.assign(def.nodes.size(), nullptr);
+  for (auto& e : evn)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return STAGGER_ECUDA;
+  nconc = GRAPH_NSTREAMS;
+  return STAGGER_OK;
+}
+
+template <typename T>
 void GraphExec<T>::release() {
+  for (auto e : evn)
+    if (e) cudaEventDestroy(e);
+  evn.clear();
+  for (int k = 0; k < GRAPH_NSTREAMS; ++k) {
+    if (aux[k]) cudaStreamDestroy(aux[k]);
+    if (evjoin[k]) cudaEventDestroy(evjoin[k]);
+    aux[k] = nullptr;
+    evjoin[k] = nullptr;
+  }
+  if (evfork) cudaEventDestroy(evfork);
+  evfork = nullptr;
+  nconc = 0;
   if (vals) cudaFree(vals);
   if (grads) cudaFree(grads);
   if (mesh) cudaFree(mesh);
@@ -845,28 +872,66 @@ static BwdK<T> bwd_kernel(int op) {
   }
 }
 
+// Fork the auxiliary streams from s (they then follow everything enqueued on
+// s so far), and join them back into s.
+template <typename T>
+static int fork_streams(GraphExec<T>& G, cudaStream_t s) {
+  STG_CUDA_OK(cudaEventRecord(G.evfork, s));
+  for (int k = 0; k < G.nconc; ++k) STG_CUDA_OK(cudaStreamWaitEvent(G.aux[k], G.evfork, 0));
+  return STAGGER_OK;
+}
+template <typename T>
+static int join_streams(GraphExec<T>& G, cudaStream_t s) {
+  for (int k = 0; k < G.nconc; ++k) {
+    STG_CUDA_OK(cudaEventRecord(G.evjoin[k], G.aux[k]));
+    STG_CUDA_OK(cudaStreamWaitEvent(s, G.evjoin[k], 0));
+  }
+  return STAGGER_OK;
+}
+
 template <typename T>
 int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
-  for (size_t i = 0; i < def.nodes.size(); ++i)
+  const size_t nn = def.nodes.size();
+  for (size_t i = 0; i < nn; ++i)
     if (def.nodes[i].op == G_INPUT) ptr[i] = in[def.nodes[i].sk];
   const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
-  for (size_t i = 0; i < def.nodes.size(); ++i) {
+  // Concurrent form: the stream of each node (-1: an input, ready at the fork).
+  std::vector<int> sto(nconc ? nn : 0, -1);
+  int rr = 0, prev_scr = -1;
+  if (nconc && fork_streams(*this, s)) return STAGGER_ECUDA;
+  for (size_t i = 0; i < nn; ++i) {
     const GNode& nd = def.nodes[i];
     if (nd.op == G_INPUT) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
-    if (nd.op == G_PMEAN) {
-      g_plane_sum<T><<<geo.nz, 256, 0, s>>>(A, psum, geo);
-      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, ptr[i], 0, geo);
-      launches += 2;
-      continue;
+    cudaStream_t st = s;
+    if (nconc) {
+      // Follow the first operand's stream (chains stay on one stream); a node
+      // without a computed operand starts the next stream in turn.
+      int k = (nd.a >= 0 && sto[nd.a] >= 0) ? sto[nd.a]
+            : (nd.b >= 0 && sto[nd.b] >= 0) ? sto[nd.b] : (rr++ % nconc);
+      st = aux[k];
+      for (int o : {nd.a, nd.b})
+        if (o >= 0 && sto[o] >= 0 && sto[o] != k) STG_CUDA_OK(cudaStreamWaitEvent(st, evn[o], 0));
+      if (nd.op == G_PMEAN && prev_scr >= 0 && sto[prev_scr] != k)
+        STG_CUDA_OK(cudaStreamWaitEvent(st, evn[prev_scr], 0));   // psum is shared
+      sto[i] = k;
     }
-    if (nd.op == G_QUENCH)
-      g_quench_f<T><<<gg, gb, 0, s>>>(nd, A, ptr[i], geo);
-    else
-      fwd_kernel<T>(nd.op)<<<gg, gb, 0, s>>>(nd, A, B, ptr[i], mesh, geo);
-    ++launches;
+    if (nd.op == G_PMEAN) {
+      g_plane_sum<T><<<geo.nz, 256, 0, st>>>(A, psum, geo);
+      g_plane_bcast<T><<<gg, gb, 0, st>>>(psum, ptr[i], 0, geo);
+      launches += 2;
+      prev_scr = (int)i;
+    } else if (nd.op == G_QUENCH) {
+      g_quench_f<T><<<gg, gb, 0, st>>>(nd, A, ptr[i], geo);
+      ++launches;
+    } else {
+      fwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, ptr[i], mesh, geo);
+      ++launches;
+    }
+    if (nconc) STG_CUDA_OK(cudaEventRecord(evn[i], st));
   }
+  if (nconc && join_streams(*this, s)) return STAGGER_ECUDA;
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -881,6 +946,11 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   for (int k = 0; k < 8; ++k)
     STG_CUDA_OK(cudaMemcpyAsync(grads + (size_t)def.out[k] * geo.n, seed[k],
                                 sizeof(T) * geo.n, cudaMemcpyDeviceToDevice, s));
+  // Concurrent form: the last launch that wrote each gradient array (-1: none
+  // since the fork), and its stream.
+  std::vector<int> lastw(nconc ? nn : 0, -1), sto(nconc ? nn : 0, -1);
+  int rr = 0, prev_scr = -1;
+  if (nconc && fork_streams(*this, s)) return STAGGER_ECUDA;
   for (long long i = (long long)nn - 1; i >= 0; --i) {
     const GNode& nd = def.nodes[i];
     if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
@@ -890,22 +960,41 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
     T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
     T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
+    cudaStream_t st = s;
+    if (nconc) {
+      // Wait for the complete gradient of this node, for the previous writer
+      // of each gradient it adds to, and for the previous user of the shared
+      // scratch (quench, plane mean).
+      const int own = lastw[i];
+      int k = own >= 0 ? sto[own] : (rr++ % nconc);
+      st = aux[k];
+      const bool scr = nd.op == G_QUENCH || nd.op == G_PMEAN;
+      for (int w : {own, nd.a >= 0 ? lastw[nd.a] : -1, nd.b >= 0 ? lastw[nd.b] : -1,
+                    scr ? prev_scr : -1})
+        if (w >= 0 && sto[w] != k) STG_CUDA_OK(cudaStreamWaitEvent(st, evn[w], 0));
+      sto[i] = k;
+      if (scr) prev_scr = (int)i;
+    }
     if (nd.op == G_PMEAN) {
-      g_plane_sum<T><<<geo.nz, 256, 0, s>>>(grads + (size_t)i * geo.n, psum, geo);
-      g_plane_bcast<T><<<gg, gb, 0, s>>>(psum, gA, wa[i] ? 0 : 1, geo);
+      g_plane_sum<T><<<geo.nz, 256, 0, st>>>(grads + (size_t)i * geo.n, psum, geo);
+      g_plane_bcast<T><<<gg, gb, 0, st>>>(psum, gA, wa[i] ? 0 : 1, geo);
       launches += 2;
-      continue;
-    }
-    if (nd.op == G_QUENCH) {
-      g_quench_b1<T><<<gg, gb, 0, s>>>(nd, A, grads + (size_t)i * geo.n, qscr, geo);
-      g_quench_b3<T><<<gg, gb, 0, s>>>(nd, A, qscr, gA, wa[i], geo);
+    } else if (nd.op == G_QUENCH) {
+      g_quench_b1<T><<<gg, gb, 0, st>>>(nd, A, grads + (size_t)i * geo.n, qscr, geo);
+      g_quench_b3<T><<<gg, gb, 0, st>>>(nd, A, qscr, gA, wa[i], geo);
       launches += 2;
-      continue;
+    } else {
+      bwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA,
+                                              gB, wa[i], wb[i], geo);
+      ++launches;
     }
-    bwd_kernel<T>(nd.op)<<<gg, gb, 0, s>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA, gB,
-                                           wa[i], wb[i], geo);
-    ++launches;
+    if (nconc) {
+      STG_CUDA_OK(cudaEventRecord(evn[i], st));
+      if (nd.a >= 0) lastw[nd.a] = (int)i;
+      if (nd.b >= 0) lastw[nd.b] = (int)i;
+    }
   }
+  if (nconc && join_streams(*this, s)) return STAGGER_ECUDA;
   for (int k = 0; k < 8; ++k) {
     if (!hasg[def.in[k]]) continue;   // the outputs do not depend on this input
     g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(gin[k], grads + (size_t)def.in[k] * geo.n, geo.n);

@@ -75,6 +75,8 @@ struct GraphDef {
 // Build the right-hand-side graph for a grid and parameter set.
 void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p);
 
+#define GRAPH_NSTREAMS 4
+
 // Device executor for one precision.  Holds one value and one gradient array
 // of n cells per node (inputs point at caller memory and need none).
 template <typename T>
@@ -91,6 +93,17 @@ struct GraphExec {
   // than accumulates into) the input's gradient.
   std::vector<char> hasg, wa, wb;
   long long launches = 0;
+  // Concurrent sweeps: with nconc auxiliary streams each node's launch waits
+  // only on the launches it depends on (its operands' values in the forward;
+  // its own gradient and the previous writer of each gradient it adds to in
+  // the reverse; the previous user of the shared quench and plane-mean
+  // scratch), so a sweep captured into a CUDA graph becomes a DAG whose
+  // independent kernels overlap.  0: one stream, in node order.
+  int nconc = 0;
+  cudaStream_t aux[GRAPH_NSTREAMS] = {};
+  std::vector<cudaEvent_t> evn;
+  cudaEvent_t evfork = nullptr, evjoin[GRAPH_NSTREAMS] = {};
+  int enable_concurrency();
 
   int init(const GraphDef& d, const Geo& g, bool with_grads);
   void release();
