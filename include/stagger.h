@@ -162,6 +162,12 @@ typedef struct {
    * continuation (the density is reflected, not extrapolated). */
   int zwalls;
   int zghost;
+  /* Energy diffusion of the fluctuations only, eq. (ediffav): with ediffav 1
+   * (and a viscosity on) the diffusion flux of eq. (ediffuse) becomes
+   * nuE dn(rho nu_ii) e dddn(ln e - ln <e>_h), <e>_h the mean of e = E/rho over
+   * the horizontal plane (constant z) of the cell, e at the face by
+   * interpolation.  0 (default): eq. (ediffuse).  Other values: EINVAL. */
+  int ediffav;
 } stagger_params;
 
 /* Ghost planes needed at each closed z wall: the reach of the right-hand

@@ -20,6 +20,9 @@ path by specification only, never by code):
   R4  log interpolation of rho to faces and edges (do_loginterp);
   R5  max over 3 cells then a 3-cell mean, along x, y, z in turn;
   R6  energy diffusion flux nuE * dn(rho nu_ii) * dd_dn(e);
+  R23 eq. (ediffav), with ediffav: the flux nuE * dn(rho nu_ii) * dn(e) *
+      dd_dn(ln e - ln <e>_h), <e>_h the mean of e = E/rho over the horizontal
+      plane (constant z) of the cell, of the state the RHS is evaluated on;
   R7  resistivity eta on an edge = nuB * nu of that edge;
   R8  quench: one quenched value per stress / eta J component, the factor
       taken over the directions in which that component is differentiated;
@@ -202,6 +205,7 @@ class Params:
     d2lnr_lim: float = 0.3
     quench_max3: bool = False   # R8: the 3-cell max of |T| in the quench ratio instead of |T|
     quench_eps: float = 1e-4    # R8: weight of the 3-cell max of |T| added to |T|
+    ediffav: bool = False    # energy diffusion of the fluctuations about <e>_h, eq. (ediffav), R23
     t_chromo: float = 0.0    # chromospheric cooling time, eq. (ChromoCool) (0: off), R20
     rho_bot: float = 1.0
     cor_L0: float = 0.0      # coronal thin cooling prefactor in code units (0: off), R21
@@ -464,9 +468,18 @@ def rhs_parts(f, g: Grid, p: Params):
         Q = Qv + Qj
         out.update(Qv=Qv, Qj=Qj)
         # Energy diffusion, eq. (ediffuse) with reading R6.
-        ediff = [p.nuE * ddup(dn(r * nxx, "x") * dddn(e, "x", hx), "x", hx),
-                 p.nuE * ddup(dn(r * nyy, "y") * dddn(e, "y", hy), "y", hy),
-                 p.nuE * ddup(dn(r * nzz, "z") * dddn(e, "z", hz), "z", hz)]
+        if p.ediffav:
+            # eq. (ediffav), reading R23: only the fluctuations about the
+            # horizontal-plane mean of e diffuse.
+            le = torch.log(e) - torch.log(e.mean(dim=(1, 2), keepdim=True))
+            ediff = [p.nuE * ddup(dn(r * nxx, "x") * dn(e, "x") * dddn(le, "x", hx), "x", hx),
+                     p.nuE * ddup(dn(r * nyy, "y") * dn(e, "y") * dddn(le, "y", hy), "y", hy),
+                     p.nuE * ddup(dn(r * nzz, "z") * dn(e, "z") * dddn(le, "z", hz), "z", hz)]
+        else:
+            ediff = [p.nuE * ddup(dn(r * nxx, "x") * dddn(e, "x", hx), "x", hx),
+                     p.nuE * ddup(dn(r * nyy, "y") * dddn(e, "y", hy), "y", hy),
+                     p.nuE * ddup(dn(r * nzz, "z") * dddn(e, "z", hz), "z", hz)]
+        out["ediff"] = ediff
     out.update(txx=txx, tyy=tyy, tzz=tzz, txy=txy, tyz=tyz, tzx=tzx, Ex=Ex, Ey=Ey, Ez=Ez)
 
     # eq. (mass)

@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
                 ("cor_L0", ctypes.c_double), ("cor_Tunit", ctypes.c_double),
                 ("fuse_flux_div", ctypes.c_int),
                 ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double),
-                ("zwalls", ctypes.c_int), ("zghost", ctypes.c_int)]
+                ("zwalls", ctypes.c_int), ("zghost", ctypes.c_int),
+                ("ediffav", ctypes.c_int)]
 
 ZGHOST_MIN = 14   # STAGGER_ZGHOST_MIN of include/stagger.h
 

@@ -55,6 +55,7 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
     return STAGGER_EINVAL;
   if (p->zwalls < 0 || p->zwalls > 1) return STAGGER_EINVAL;
+  if (p->ediffav < 0 || p->ediffav > 1) return STAGGER_EINVAL;
   // Closed z walls: at least the reach of the right-hand side in ghost planes
   // at each end, one physical spacing between the boundary planes, uniform z.
   if (p->zwalls && (p->zghost < STAGGER_ZGHOST_MIN || g->nz < 2 * p->zghost + 2 || p->zc ||

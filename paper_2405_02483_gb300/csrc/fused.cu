@@ -198,6 +198,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.emean = nullptr;
   k.corL0 = (float)p.cor_L0;
   k.corTu = (float)p.cor_Tunit;
+  k.ediffav = p.ediffav && k.visc ? 1 : 0;
   k.wall = p.zwalls ? 1 : 0;
   k.klo = p.zwalls ? p.zghost : 0;
   k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
@@ -219,9 +220,10 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.mesh = nullptr;
   F.plane = nullptr;
   F.plane_nb = 0;
-  if (p.t_chromo > 0) {
-    // Plane means of e for the chromospheric cooling: nz means, then the
-    // per-block parts of the fixed-order reduction.
+  if (p.t_chromo > 0 || k.ediffav) {
+    // Plane means of e for the chromospheric cooling and the energy diffusion
+    // of eq. (ediffav): nz means, then the per-block parts of the fixed-order
+    // reduction.
     const long long m = (long long)gr.nx * gr.ny;
     F.plane_nb = (int)std::max(1LL, std::min(64LL, (m + 1023) / 1024));
     if (cudaMalloc(&F.plane, sizeof(double) * (size_t)gr.nz * (1 + F.plane_nb)) != cudaSuccess) {
@@ -265,6 +267,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
                   F_LY1, F_LY2, F_LZ1, F_LZ2, F_GX, F_GY, F_GZ, F_QT})
       need.push_back(f);
   need.push_back(F_ED);
+  if (k.ediffav) need.push_back(F_LER);
   if (k.log_interp) need.push_back(F_LR);
   if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
   if (k.csmag_dl > 0.f) for (int f : {F_SQXY, F_SQYZ, F_SQZX}) need.push_back(f);
@@ -344,8 +347,17 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   const dim3 gz8 = grid_for<N>(g, BB_Z8), gy8 = grid_for<N>(g, BB_Y8);
   using NB = typename N::Base;   // kernels without derivatives or lengths
   const float* ls = k.log_interp ? d[F_LR] : f[0];
+  // Plane means of e - e0 (chromospheric cooling, eq. (ediffav)), before the
+  // kernels that read them.
+  if (k.inv_tchromo > 0.f || k.ediffav) {
+    TIMED(K_COOL2, (k_plane_part<<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
+                       f[0], f[4], F.plane + g.nz, k, g)));
+    TIMED(K_COOL2, (k_plane_final<<<(g.nz + 63) / 64, 64, 0, s>>>(F.plane + g.nz, F.plane_nb,
+                                                                   F.plane, g)));
+  }
   TIMED(K_LR, (k_lr_ed<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], f[4], k.log_interp ? d[F_LR] : nullptr,
-                                                       d[F_ED], k, g.n)));
+                                                       d[F_ED], k.ediffav ? d[F_LER] : nullptr,
+                                                       k, g.n, g.sz)));
   TIMED(K_VEL, (k_vel<NB><<<gy8, BB_Y8, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
@@ -371,12 +383,6 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
       TIMED(K_NU_SMOOTH, (ksm<<<gg, bb, 0, s>>>(d[F_NM], d[F_NU], d[F_LNU], F.cmax + 2, g)));
     }
     TIMED(K_NU_FACES, (k_nu_faces<NB><<<gy8, BB_Y8, 0, s>>>(d[F_LNU], d[F_LNX], d[F_LNY], d[F_LNZ], g)));
-  }
-  if (k.inv_tchromo > 0.f) {
-    TIMED(K_COOL2, (k_plane_part<<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
-                       f[0], f[4], F.plane + g.nz, k, g)));
-    TIMED(K_COOL2, (k_plane_final<<<(g.nz + 63) / 64, 64, 0, s>>>(F.plane + g.nz, F.plane_nb,
-                                                                   F.plane, g)));
   }
   if (k.d2div)
     TIMED(K_D2FLAG, (k_d2flag<NB><<<gg, bb, 0, s>>>(f[0], f[4], F.d2flag, k, g)));
@@ -406,7 +412,7 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
                qn ? d[F_QXX] : d[F_TXX], qn ? d[F_QYY] : d[F_TYY], qn ? d[F_QZZ] : d[F_TZZ],
                qn ? d[F_QXY] : d[F_TXY], qn ? d[F_QYZ] : d[F_TYZ], qn ? d[F_QZX] : d[F_TZX],
                d[F_JX], d[F_JY], d[F_JZ], d[F_NU], d[F_WC], d[F_WX], d[F_WY], d[F_WZ],
-               d[F_ED]};
+               d[F_ED], d[F_LER]};
   FluxOut fo = {d[F_MXX], d[F_MYY], d[F_MZZ], d[F_MXY], d[F_MYX], d[F_MXZ], d[F_MZX],
                 d[F_MYZ], d[F_MZY], d[F_LX1], d[F_LX2], d[F_LY1], d[F_LY2], d[F_LZ1],
                 d[F_LZ2], d[F_GX], d[F_GY], d[F_GZ], d[F_QT], d[F_EX], d[F_EY], d[F_EZ]};
@@ -469,6 +475,7 @@ static FdIn fdiv_in(Fused& F, float* const f[8]) {
   for (int c = 0; c < 8; ++c) in.f[c] = f[c];
   in.ux = d[F_UX]; in.uy = d[F_UY]; in.uz = d[F_UZ];
   in.ed = d[F_ED];
+  in.ler = d[F_LER];
   in.ls = k.log_interp ? d[F_LR] : f[0];
   in.txx = qn ? d[F_QXX] : d[F_TXX]; in.tyy = qn ? d[F_QYY] : d[F_TYY];
   in.tzz = qn ? d[F_QZZ] : d[F_TZZ]; in.txy = qn ? d[F_QXY] : d[F_TXY];

@@ -42,6 +42,7 @@ struct KPar {
   // Closed z walls (reading R22): the physical centre planes are klo..khi,
   // the planes outside are ghost planes filled by reflection.
   int wall, klo, khi;
+  int ediffav;          // energy diffusion of ln e - ln <e>_h, eq. (ediffav), R23
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -60,6 +61,7 @@ enum Fld {
   F_LNX, F_LNY, F_LNZ,                              // ln<nu> interpolated to the faces
   F_SQXY, F_SQYZ, F_SQZX,                           // squared off-diagonal strain (edges)
   F_ED,                                             // e - e0 at centres
+  F_LER,                                            // ln e - ln <e>_h (ediffav)
   F_COUNT
 };
 

@@ -340,15 +340,23 @@ template <class T> __device__ __forceinline__ T dens(T t, const KPar& k) {
 // Also the specific internal energy's deviation e - e0 = (E' + Ec - e0 r') /
 // (r' + r0) (Ec = E0 - e0 r0), whose taps the energy fluxes interpolate and
 // differentiate; ln rho only when lr is not null (log interpolation).
+// With ler (eq. (ediffav)) also ln e - ln <e>_h = log1p((ed - m) / (e0 + m)),
+// m = <e - e0>_h the plane mean of the cell's plane (k.emean, sz cells a plane).
 template <class N>
 __global__ void k_lr_ed(const float* __restrict__ rd, const float* __restrict__ Ed,
-                        float* __restrict__ lr, float* __restrict__ ed, KPar k, long long n) {
+                        float* __restrict__ lr, float* __restrict__ ed,
+                        float* __restrict__ ler, KPar k, long long n, long long sz) {
   using T = typename N::T;
   const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * N::W;
   if (i >= n) return;
   const T r = N::ldp(rd + i);
   if (lr) N::stp(lr + i, k.r0pos ? log1pf(r / k.r0) : logf(r));
-  N::stp(ed + i, fdiv((N::ldp(Ed + i) + k.Ec) - k.e0 * r, r + k.r0));
+  const T e = fdiv((N::ldp(Ed + i) + k.Ec) - k.e0 * r, r + k.r0);
+  N::stp(ed + i, e);
+  if (ler) {
+    const float m = (float)k.emean[i / sz];
+    N::stp(ler + i, log1pf((e - m) / (k.e0 + m)));
+  }
 }
 
 // ------------------------------------------------------------- velocity ----
@@ -889,6 +897,7 @@ struct FluxIn {
   const float *px, *py, *pz, *rd, *Ed, *bx, *by, *bz, *ls, *ux, *uy, *uz;
   const float *qxx, *qyy, *qzz, *qxy, *qyz, *qzx, *Jx, *Jy, *Jz, *nu, *wc, *wx, *wy, *wz;
   const float* ed;   // e - e0 at centres
+  const float* ler;  // ln e - ln <e>_h (ediffav)
 };
 struct FluxOut {
   float *mxx, *myy, *mzz, *mxy, *myx, *mxz, *mzx, *myz, *mzy;
@@ -978,14 +987,20 @@ __device__ __forceinline__ void flux_energy_cell(const N& n, const FluxIn& in,
   for (int d = 0; d < 3; ++d) {
     // e = e0 + (e - e0): the interpolation weights sum to one.
     auto ed_at = [&](int o) { return n.lda(in.ed, d, o); };
-    T v = (n.ld(pr[d]) + k.pref[d]) * (s_dn(ed_at) + k.e0);
+    const T ef = s_dn(ed_at) + k.e0;   // e at the face
+    T v = (n.ld(pr[d]) + k.pref[d]) * ef;
     if (k.visc) {
       auto rn_at = [&](int o) {
         const T r = n.lda(rd, d, o) + k.r0;
         const float sp = (N::ZS && d == 2) ? n.hzc_at(o, k) : k.sp[d];
         return r * (k.rm ? sp * n.lda(in.nu, d, o) : T(k.nu_const));
       };
-      v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, n.jd(d, k)));
+      if (k.ediffav) {   // eq. (ediffav): e dddn(ln e - ln <e>_h)
+        auto le_at = [&](int o) { return n.lda(in.ler, d, o); };
+        v -= k.nuE * (s_dn(rn_at) * (ef * s_dd(le_at, n.jd(d, k))));
+      } else {
+        v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, n.jd(d, k)));
+      }
     }
     n.st(go[d], v);
   }

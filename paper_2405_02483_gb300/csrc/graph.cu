@@ -619,10 +619,20 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
     int Qj = G.add(G.add(up(up(G.mul(Rx, Jx), Y), Z), up(up(G.mul(Ry, Jy), Z), X)),
                    up(up(G.mul(Rz, Jz), X), Y));
     Q = G.add(Qv, Qj);
-    // eq. (ediffuse): nuE ddup(dn(rho nu_ii) dddn e).
+    // eq. (ediffuse): nuE ddup(dn(rho nu_ii) dddn e); with eq. (ediffav) (R23)
+    // nuE ddup(dn(rho nu_ii) dn(e) dddn(ln e - ln <e>_h)), the log ratio as
+    // log1p((ed - <ed>_h) / (e0 + <ed>_h)).
     int nii[3] = {nxx, nyy, nzz};
+    int lrat = -1;
+    if (p.ediffav) {
+      const double e0 = r0 > 0 ? E0 / r0 : 0.0;
+      const int pm = G.pmean(ed);
+      lrat = G.lg1p(G.div(G.sub(ed, pm), G.axpb(pm, 1.0, e0)));
+    }
     for (int d = 0; d < 3; ++d)
-      ediff[d] = G.axpb(ddup(G.mul(dn(G.mul(r, nii[d]), d), dddn(ed, d)), d), p.nuE, 0.0);
+      ediff[d] = p.ediffav
+          ? G.axpb(ddup(G.mul(dn(G.mul(r, nii[d]), d), G.mul(dn(e, d), dddn(lrat, d))), d), p.nuE, 0.0)
+          : G.axpb(ddup(G.mul(dn(G.mul(r, nii[d]), d), dddn(ed, d)), d), p.nuE, 0.0);
   }
 
   // eq. (mass)

@@ -48,6 +48,7 @@ struct FdIn {
   const float* f[8];              // stage input state (deviations), r px py pz E Bx By Bz
   const float *ux, *uy, *uz;      // face velocities
   const float* ed;                // e - e0 at centres
+  const float* ler;               // ln e - ln <e>_h (ediffav)
   const float* ls;                // ln(rho/r0) (log interpolation) or rho' (gravity)
   const float *txx, *tyy, *tzz, *txy, *tyz, *tzx;   // stresses (viscous)
   const float *rx, *ry, *rz;      // eta J on the edges (viscous)
@@ -178,13 +179,19 @@ __device__ __forceinline__ void fd_fluxes(const Nb& n, const FdIn& in, const KPa
   // (e - e0), the interpolation weights summing to one.
   auto gflux = [&](int d, const float* pd) {
     auto ed_at = [&](int oo) { return n.lda(in.ed, d, oo); };
-    float v = (n.ld(pd) + k.pref[d]) * (s_dn(ed_at) + k.e0);
+    const float ef = s_dn(ed_at) + k.e0;
+    float v = (n.ld(pd) + k.pref[d]) * ef;
     if (VISC) {
       auto rn_at = [&](int oo) {
         const float r = n.lda(in.f[0], d, oo) + k.r0;
         return r * (k.rm ? k.sp[d] * n.lda(in.nu, d, oo) : k.nu_const);
       };
-      v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, k.ih[d]));
+      if (k.ediffav) {   // eq. (ediffav)
+        auto le_at = [&](int oo) { return n.lda(in.ler, d, oo); };
+        v -= k.nuE * (s_dn(rn_at) * (ef * s_dd(le_at, k.ih[d])));
+      } else {
+        v -= k.nuE * (s_dn(rn_at) * s_dd(ed_at, k.ih[d]));
+      }
     }
     return v;
   };

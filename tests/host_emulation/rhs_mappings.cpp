@@ -91,7 +91,7 @@ static void rhs(const Geo& g, const KPar& kin, float* const* f, std::vector<std:
   const float* ls = k.log_interp ? D[F_LR] : f[0];
   using NB = typename N::Base;
   run(dim3((unsigned)((g.n / N::W + 255) / 256)), dim3(256), [&] {
-    k_lr_ed<NB>(f[0], f[4], k.log_interp ? D[F_LR] : nullptr, D[F_ED], k, g.n);
+    k_lr_ed<NB>(f[0], f[4], k.log_interp ? D[F_LR] : nullptr, D[F_ED], nullptr, k, g.n, g.sz);
   });
   launch<N>(g, [&] { k_vel<NB>(ls, f[1], f[2], f[3], D[F_UX], D[F_UY], D[F_UZ], D[F_LFX], D[F_LFY], D[F_LFZ], k, g); });
   if (k.rm) {

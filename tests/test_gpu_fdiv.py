@@ -44,7 +44,7 @@ CASES = {
     "visc_cooling_all_1x17x9": (
         (1, 17, 9), dict(VISC_KW, t_cool=0.05, e_cool=0.7, rho_cool=1.02, cool_cut=1,
                          t_chromo=0.2, rho_bot=1.1, cor_L0=0.01, cor_Tunit=1e4)),
-    "smagorinsky_rm_64x8x66": ((64, 8, 66), dict(VISC_KW, csmag=0.15)),
+    "smagorinsky_rm_ediffav_64x8x66": ((64, 8, 66), dict(VISC_KW, csmag=0.15, ediffav=1)),
     "ideal_2planes_40x24x2": ((40, 24, 2), {}),
 }
 

@@ -132,6 +132,9 @@ CASES = {
         lambda: ragged_state((19, 23, 12)), dict(csmag=0.2, nuE=0.8, nuB=0.9)),
     "ragged_ideal_cooling_highcut": (
         lambda: ragged_state((21, 16, 12)), dict(t_cool=0.1, e_cool=0.8, rho_cool=0.98, cool_cut=2)),
+    # eq. (ediffav): only the fluctuations about the horizontal mean of e diffuse.
+    "ragged27x22x13_visc_quench_ediffav": (lambda: ragged_state((27, 22, 13)),
+                                           dict(VISC_KW, ediffav=1)),
     # The other reading of eq. (quench): the 3-cell max of |T| in the ratio.
     "ot3d24_visc_quench_max3": (lambda: inputs.orszag_tang_3d(24), dict(VISC_KW, quench_max3=1)),
     "ot2d_64x64x1_visc_quench_max3": (lambda: inputs.orszag_tang(64, 64, 1),
@@ -230,6 +233,7 @@ VEC_CASES = {
         dict(nu_const=0.002, c1=-1.0 / 3.0, nuE=0.5, nuB=0.7, g=(0.0, 0.0, -1.0), log_interp=0)),
     "vec8_ideal_cooling_highcut": (
         (8, 16, 12), dict(t_cool=0.1, e_cool=0.8, rho_cool=0.98, cool_cut=2)),
+    "vec24_ediffav_chromo": ((24, 14, 11), dict(VISC_KW, ediffav=1, t_chromo=0.2, rho_bot=1.1)),
 }
 
 

@@ -1039,3 +1039,45 @@ def test_rhs_and_courant_fields_reach(seed):
     assert seen <= RHS_REACH, seen
     assert seen >= RHS_REACH - 2, seen            # the perturbation did travel
     assert seen_w <= 5, seen_w
+
+
+# ------------------------------------------------ energy diffusion about the mean ---
+
+def _ediff_state(g, e_of):
+    """rho, E from a given specific energy e(z, y, x) on a random smooth density."""
+    torch.manual_seed(0)
+    z, y, x = torch.meshgrid(*[(torch.arange(n, dtype=DT) + 0.5) / n for n in (g.nz, g.ny, g.nx)],
+                             indexing="ij")
+    r = 1.0 + 0.1 * torch.sin(2 * math.pi * x) * torch.cos(2 * math.pi * (y + z))
+    e = e_of(z, y, x)
+    f = [r, 0.05 * torch.cos(2 * math.pi * z) + 0 * x, 0.0 * x, 0.02 * torch.sin(2 * math.pi * x) + 0 * z,
+         r * e, 0.0 * x, 0.0 * x, 0.3 + 0.0 * x]
+    return f
+
+
+def test_ediffav_vanishes_for_a_horizontally_uniform_energy():
+    """eq. (ediffav): with e a function of z alone, ln e - ln <e>_h = 0 and the
+    diffusion of the fluctuations is zero (to the rounding of the plane mean),
+    while the plain form (eq. ediffuse) diffuses the vertical gradient."""
+    g = Grid(8, 6, 10, 1 / 8, 1 / 6, 1 / 10)
+    f = _ediff_state(g, lambda z, y, x: 0.9 + 0.2 * torch.sin(2 * math.pi * z) + 0 * x)
+    p0 = Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0)
+    plain = S.rhs_parts(f, g, p0)["ediff"]
+    av = S.rhs_parts(f, g, Params(**{**p0.__dict__, "ediffav": True}))["ediff"]
+    scale = float(plain[2].abs().max())
+    assert scale > 1e-3
+    assert max(float(t.abs().max()) for t in av) <= 1e-13 * scale
+
+
+def test_ediffav_vertical_part_vanishes_for_a_separable_energy():
+    """e = A(z) B(x, y): ln e - ln <e>_h = ln B - ln <B>_h does not depend on z,
+    so the vertical diffusion of the fluctuations vanishes while the
+    horizontal diffusion does not."""
+    g = Grid(8, 6, 10, 1 / 8, 1 / 6, 1 / 10)
+    f = _ediff_state(g, lambda z, y, x: (0.9 + 0.2 * torch.sin(2 * math.pi * z))
+                     * (1.0 + 0.1 * torch.cos(2 * math.pi * x) * torch.sin(2 * math.pi * y)))
+    p = Params(nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, ediffav=True)
+    av = S.rhs_parts(f, g, p)["ediff"]
+    hx = float(av[0].abs().max())
+    assert hx > 1e-4
+    assert float(av[2].abs().max()) <= 1e-12 * hx
