@@ -20,6 +20,11 @@ path by specification only, never by code):
   R4  log interpolation of rho to faces and edges (do_loginterp);
   R5  max over 3 cells then a 3-cell mean, along x, y, z in turn;
   R6  energy diffusion flux nuE * dn(rho nu_ii) * dd_dn(e);
+  R24 eq. (pressure), with lnp_aver: the pressure leaves the diagonal momentum
+      flux and its gradient along d at the d face becomes
+      exp(dn_d(ln P_aver) + dn_d(ln(P/P_aver))) *
+      (dddn_d(ln(P/P_aver)) + dddn_d(ln P_aver)), P_aver the horizontal-plane
+      mean of P (the second derivative term vanishes for d = x, y);
   R23 eq. (ediffav), with ediffav: the flux nuE * dn(rho nu_ii) * dn(e) *
       dd_dn(ln e - ln <e>_h), <e>_h the mean of e = E/rho over the horizontal
       plane (constant z) of the cell, of the state the RHS is evaluated on;
@@ -206,6 +211,7 @@ class Params:
     quench_max3: bool = False   # R8: the 3-cell max of |T| in the quench ratio instead of |T|
     quench_eps: float = 1e-4    # R8: weight of the 3-cell max of |T| added to |T|
     ediffav: bool = False    # energy diffusion of the fluctuations about <e>_h, eq. (ediffav), R23
+    lnp_aver: bool = False   # pressure gradient through ln(P/P_aver), eq. (pressure), R24
     t_chromo: float = 0.0    # chromospheric cooling time, eq. (ChromoCool) (0: off), R20
     rho_bot: float = 1.0
     cor_L0: float = 0.0      # coronal thin cooling prefactor in code units (0: off), R21
@@ -486,21 +492,35 @@ def rhs_parts(f, g: Grid, p: Params):
     d_r = -(ddup(px, "x", hx) + ddup(py, "y", hy) + ddup(pz, "z", hz))
 
     # eq. (mom): -div(rho u u) - grad P + J x B + div tau + rho g (R2).
-    d_px = (-dddn(up(px, "x") * up(ux, "x") + P - txx, "x", hx)
+    if p.lnp_aver:
+        # eq. (pressure), reading R24: the gradient through ln(P/P_aver).
+        lpa = torch.log(P.mean(dim=(1, 2), keepdim=True)).expand_as(P)
+        lq = torch.log(P) - lpa
+        gradP = [torch.exp(dn(lpa, "x") + dn(lq, "x")) * dddn(lq, "x", hx),
+                 torch.exp(dn(lpa, "y") + dn(lq, "y")) * dddn(lq, "y", hy),
+                 torch.exp(dn(lpa, "z") + dn(lq, "z")) * (dddn(lq, "z", hz) + dddn(lpa, "z", hz))]
+        out["gradP"] = gradP
+        Pf = torch.zeros_like(P)
+    else:
+        gradP = [0.0, 0.0, 0.0]
+        Pf = P
+    d_px = (-dddn(up(px, "x") * up(ux, "x") + Pf - txx, "x", hx)
             - ddup(dn(px, "y") * dn(uy, "x") - txy, "y", hy)
             - ddup(dn(px, "z") * dn(uz, "x") - tzx, "z", hz)
             + up(Jy * dn(Bz, "x"), "z") - up(Jz * dn(By, "x"), "y")
             + rx * p.g[0])
     d_py = (-ddup(dn(py, "x") * dn(ux, "y") - txy, "x", hx)
-            - dddn(up(py, "y") * up(uy, "y") + P - tyy, "y", hy)
+            - dddn(up(py, "y") * up(uy, "y") + Pf - tyy, "y", hy)
             - ddup(dn(py, "z") * dn(uz, "y") - tyz, "z", hz)
             + up(Jz * dn(Bx, "y"), "x") - up(Jx * dn(Bz, "y"), "z")
             + ry * p.g[1])
     d_pz = (-ddup(dn(pz, "x") * dn(ux, "z") - tzx, "x", hx)
             - ddup(dn(pz, "y") * dn(uy, "z") - tyz, "y", hy)
-            - dddn(up(pz, "z") * up(uz, "z") + P - tzz, "z", hz)
+            - dddn(up(pz, "z") * up(uz, "z") + Pf - tzz, "z", hz)
             + up(Jx * dn(By, "z"), "y") - up(Jy * dn(Bx, "z"), "x")
             + rz * p.g[2])
+    if p.lnp_aver:
+        d_px, d_py, d_pz = d_px - gradP[0], d_py - gradP[1], d_pz - gradP[2]
 
     # eq. (ien): -div(rho e u) - P div u + Q_visc + eta J^2 (+ energy diffusion).
     d_E = (-(ddup(px * dn(e, "x"), "x", hx) + ddup(py * dn(e, "y"), "y", hy)

@@ -1081,3 +1081,32 @@ def test_ediffav_vertical_part_vanishes_for_a_separable_energy():
     hx = float(av[0].abs().max())
     assert hx > 1e-4
     assert float(av[2].abs().max()) <= 1e-12 * hx
+
+
+# ------------------------------------------------ pressure through ln(P/P_aver) ---
+
+def test_lnp_aver_pressure_gradient_is_exact_for_an_exponential_atmosphere():
+    """eq. (pressure) with P = P0 exp(-z/H), uniform in x and y: ln(P/P_aver)
+    = 0, so the horizontal gradients vanish, and ln P_aver is linear in z, so
+    its 6th-order derivative (-1/H) and its 5th-order interpolation are exact:
+    the vertical gradient at a face is -P(z_face)/H to roundoff.  The plain
+    derivative of P itself has the stencil's truncation error."""
+    n, H, P0, gam = 16, 0.3, 1.7, 5.0 / 3.0
+    g = Grid(6, 5, n, 1 / 6, 1 / 5, 1.0 / n)
+    z = ((torch.arange(n, dtype=DT) + 0.5) / n).reshape(n, 1, 1).expand(n, 5, 6)
+    P = P0 * torch.exp(-z / H)
+    z0 = torch.zeros(n, 5, 6, dtype=DT)
+    f = [z0 + 1.0, z0.clone(), z0.clone(), z0.clone(), P / (gam - 1.0), z0.clone(), z0.clone(), z0.clone()]
+    # a periodic box cannot hold an exponential: check the interior faces
+    # whose stencils do not wrap (z faces 3 .. n-3)
+    parts = S.rhs_parts(f, g, Params(lnp_aver=True))
+    gp = parts["gradP"]
+    zf = (torch.arange(n, dtype=DT) / n).reshape(n, 1, 1)
+    want = -P0 * torch.exp(-zf / H) / H
+    inner = slice(3, n - 2)
+    err = float((gp[2][inner] - want[inner].expand_as(gp[2][inner])).abs().max())
+    assert err <= 1e-12 * float(want.abs().max()), err
+    assert float(gp[0].abs().max()) <= 1e-14 and float(gp[1].abs().max()) <= 1e-14
+    plain = S.dddn(P, "z", g.dz)
+    perr = float((plain[inner] - want[inner].expand_as(plain[inner])).abs().max())
+    assert perr > 1e3 * err + 1e-9, (perr, err)
