@@ -168,6 +168,16 @@ typedef struct {
    * the horizontal plane (constant z) of the cell, e at the face by
    * interpolation.  0 (default): eq. (ediffuse).  Other values: EINVAL. */
   int ediffav;
+  /* Pressure gradient of eq. (mom) through ln(P/P_aver), eq. (pressure) (Sect.
+   * "Equations"): with lnp_aver 1 the pressure leaves the diagonal momentum
+   * fluxes and the gradient along d at the d face is
+   *   exp(dn_d ln P_aver + dn_d ln(P/P_aver)) (dddn_d ln(P/P_aver) + dddn_d ln P_aver),
+   * P_aver the mean of P = (gamma - 1) E over the horizontal plane (constant z)
+   * of the cell, of the state the right-hand side is evaluated on; the
+   * derivative of ln P_aver vanishes for d = x, y.  0 (default): P in the
+   * diagonal fluxes.  Other values, or lnp_aver 1 with fuse_flux_div 1:
+   * STAGGER_EINVAL. */
+  int lnp_aver;
 } stagger_params;
 
 /* Ghost planes needed at each closed z wall: the reach of the right-hand

@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("fuse_flux_div", ctypes.c_int),
                 ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double),
                 ("zwalls", ctypes.c_int), ("zghost", ctypes.c_int),
-                ("ediffav", ctypes.c_int)]
+                ("ediffav", ctypes.c_int),
+                ("lnp_aver", ctypes.c_int)]
 
 ZGHOST_MIN = 14   # STAGGER_ZGHOST_MIN of include/stagger.h
 

@@ -56,6 +56,8 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
     return STAGGER_EINVAL;
   if (p->zwalls < 0 || p->zwalls > 1) return STAGGER_EINVAL;
   if (p->ediffav < 0 || p->ediffav > 1) return STAGGER_EINVAL;
+  if (p->lnp_aver < 0 || p->lnp_aver > 1) return STAGGER_EINVAL;
+  if (p->lnp_aver && p->fuse_flux_div) return STAGGER_EINVAL;
   // Closed z walls: at least the reach of the right-hand side in ghost planes
   // at each end, one physical spacing between the boundary planes, uniform z.
   if (p->zwalls && (p->zghost < STAGGER_ZGHOST_MIN || g->nz < 2 * p->zghost + 2 || p->zc ||

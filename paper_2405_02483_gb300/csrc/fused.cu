@@ -27,7 +27,7 @@ const char* const KNAMES[K_COUNT] = {"k_lr_ed", "k_vel", "k_strain2", "k_nu_raw"
                                      "k_nu_smooth", "k_nu_faces", "k_tau", "k_edge", "k_flux",
                                      "k_div", "k_update", "k_courant", "k_diag", "k_misc",
                                      "k_d2flag", "k_cool2", "k_flux_e", "k_nu_maxsmooth",
-                                     "k_fdiv", "k_wall"};
+                                     "k_fdiv", "k_wall", "k_plane"};
 
 static cudaEvent_t ev_get(Fused& F) {
   if (!F.pool.empty()) {
@@ -199,6 +199,9 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.corL0 = (float)p.cor_L0;
   k.corTu = (float)p.cor_Tunit;
   k.ediffav = p.ediffav && k.visc ? 1 : 0;
+  k.lnpa = p.lnp_aver ? 1 : 0;
+  k.Emean = nullptr;
+  k.pa = k.paz = k.dpaz = nullptr;
   k.wall = p.zwalls ? 1 : 0;
   k.klo = p.zwalls ? p.zghost : 0;
   k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
@@ -219,13 +222,27 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.d2flag = nullptr;
   F.mesh = nullptr;
   F.plane = nullptr;
-  F.plane_nb = 0;
+  F.pplane = nullptr;
+  F.plane_nb = (int)std::max(1LL, std::min(64LL, ((long long)gr.nx * gr.ny + 1023) / 1024));
+  if (k.lnpa) {
+    // ln(P/P_aver): the plane means of E - E0 and their per-block parts, then
+    // P_aver, exp(dn_z ln P_aver) and dddn_z ln P_aver as 3 nz floats.
+    const size_t nd = (size_t)gr.nz * (1 + F.plane_nb);
+    if (cudaMalloc(&F.pplane, sizeof(double) * nd + sizeof(float) * 3 * (size_t)gr.nz) !=
+        cudaSuccess) {
+      F.pplane = nullptr;
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+    k.Emean = F.pplane;
+    k.pa = reinterpret_cast<const float*>(F.pplane + nd);
+    k.paz = k.pa + gr.nz;
+    k.dpaz = k.pa + 2 * gr.nz;
+  }
   if (p.t_chromo > 0 || k.ediffav) {
     // Plane means of e for the chromospheric cooling and the energy diffusion
     // of eq. (ediffav): nz means, then the per-block parts of the fixed-order
     // reduction.
-    const long long m = (long long)gr.nx * gr.ny;
-    F.plane_nb = (int)std::max(1LL, std::min(64LL, (m + 1023) / 1024));
     if (cudaMalloc(&F.plane, sizeof(double) * (size_t)gr.nz * (1 + F.plane_nb)) != cudaSuccess) {
       F.plane = nullptr;
       fused_release(F);
@@ -268,6 +285,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
       need.push_back(f);
   need.push_back(F_ED);
   if (k.ediffav) need.push_back(F_LER);
+  if (k.lnpa) need.push_back(F_LQ);
   if (k.log_interp) need.push_back(F_LR);
   if (k.rm) for (int f : {F_NV, F_NM, F_NU, F_LNU, F_LNX, F_LNY, F_LNZ}) need.push_back(f);
   if (k.csmag_dl > 0.f) for (int f : {F_SQXY, F_SQYZ, F_SQZX}) need.push_back(f);
@@ -332,6 +350,8 @@ void fused_release(Fused& F) {
   F.mesh = nullptr;
   if (F.plane) cudaFree(F.plane);
   F.plane = nullptr;
+  if (F.pplane) cudaFree(F.pplane);
+  F.pplane = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -350,14 +370,22 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
   // Plane means of e - e0 (chromospheric cooling, eq. (ediffav)), before the
   // kernels that read them.
   if (k.inv_tchromo > 0.f || k.ediffav) {
-    TIMED(K_COOL2, (k_plane_part<<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
+    TIMED(K_PLANE, (k_plane_part<false><<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
                        f[0], f[4], F.plane + g.nz, k, g)));
-    TIMED(K_COOL2, (k_plane_final<<<(g.nz + 63) / 64, 64, 0, s>>>(F.plane + g.nz, F.plane_nb,
+    TIMED(K_PLANE, (k_plane_final<<<(g.nz + 63) / 64, 64, 0, s>>>(F.plane + g.nz, F.plane_nb,
                                                                    F.plane, g)));
+  }
+  if (k.lnpa) {   // ln(P/P_aver), eq. (pressure): plane means of E - E0, P_aver factors
+    TIMED(K_PLANE, (k_plane_part<true><<<dim3(F.plane_nb, g.nz), 256, 0, s>>>(
+                       f[0], f[4], F.pplane + g.nz, k, g)));
+    TIMED(K_PLANE, (k_lnpa_tab<<<1, 256, 0, s>>>(F.pplane + g.nz, F.plane_nb, F.pplane,
+                                                 const_cast<float*>(k.pa),
+                                                 const_cast<float*>(k.paz),
+                                                 const_cast<float*>(k.dpaz), k, g)));
   }
   TIMED(K_LR, (k_lr_ed<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], f[4], k.log_interp ? d[F_LR] : nullptr,
                                                        d[F_ED], k.ediffav ? d[F_LER] : nullptr,
-                                                       k, g.n, g.sz)));
+                                                       k.lnpa ? d[F_LQ] : nullptr, k, g.n, g.sz)));
   TIMED(K_VEL, (k_vel<NB><<<gy8, BB_Y8, 0, s>>>(ls, f[1], f[2], f[3], d[F_UX], d[F_UY], d[F_UZ],
                                         d[F_LFX], d[F_LFY], d[F_LFZ], k, g)));
   if (k.rm) {
@@ -462,6 +490,7 @@ static DivIn div_in(Fused& F, float* const f[8]) {
   di.Ex = d[F_EX]; di.Ey = d[F_EY]; di.Ez = d[F_EZ];
   di.ls = F.kp.log_interp ? d[F_LR] : f[0];
   for (int c = 0; c < 8; ++c) di.f[c] = f[c];
+  di.lq = d[F_LQ];
   return di;
 }
 

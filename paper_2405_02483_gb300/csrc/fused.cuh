@@ -43,6 +43,12 @@ struct KPar {
   // the planes outside are ghost planes filled by reflection.
   int wall, klo, khi;
   int ediffav;          // energy diffusion of ln e - ln <e>_h, eq. (ediffav), R23
+  // Pressure gradient through ln(P/P_aver), eq. (pressure), R24: the plane
+  // means of E - E0 (nz), P_aver per centre plane, exp(dn_z ln P_aver) and
+  // dddn_z ln P_aver per lower z face (nz floats each).
+  int lnpa;
+  const double* Emean;
+  const float *pa, *paz, *dpaz;
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -62,13 +68,14 @@ enum Fld {
   F_SQXY, F_SQYZ, F_SQZX,                           // squared off-diagonal strain (edges)
   F_ED,                                             // e - e0 at centres
   F_LER,                                            // ln e - ln <e>_h (ediffav)
+  F_LQ,                                             // ln(P / P_aver) (lnp_aver)
   F_COUNT
 };
 
 // Kernel identities for per-kernel timing.
 enum KId { K_LR = 0, K_VEL, K_STRAIN2, K_NU_RAW, K_NU_MAX, K_NU_SMOOTH, K_NU_FACES, K_TAU, K_EDGE,
            K_FLUX, K_DIV, K_UPDATE, K_COURANT, K_DIAG, K_MISC, K_D2FLAG, K_COOL2, K_FLUX_E, K_NU_MS,
-           K_FDIV, K_WALL, K_COUNT };
+           K_FDIV, K_WALL, K_PLANE, K_COUNT };
 extern const char* const KNAMES[K_COUNT];
 
 struct Fused {
@@ -88,6 +95,8 @@ struct Fused {
   double wsum_f;        // sum of the z-face weights of the diagnostics (n when uniform)
   double* plane;        // plane means (nz) then per-block parts (nz * plane_nb), or null
   int plane_nb;
+  double* pplane;       // the same for E - E0 (ln(P/P_aver)), then its 3 nz floats of
+                        // per-plane pressure factors, or null
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)

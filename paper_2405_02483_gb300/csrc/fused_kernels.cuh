@@ -345,17 +345,23 @@ template <class T> __device__ __forceinline__ T dens(T t, const KPar& k) {
 template <class N>
 __global__ void k_lr_ed(const float* __restrict__ rd, const float* __restrict__ Ed,
                         float* __restrict__ lr, float* __restrict__ ed,
-                        float* __restrict__ ler, KPar k, long long n, long long sz) {
+                        float* __restrict__ ler, float* __restrict__ lq, KPar k, long long n,
+                        long long sz) {
   using T = typename N::T;
   const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * N::W;
   if (i >= n) return;
   const T r = N::ldp(rd + i);
   if (lr) N::stp(lr + i, k.r0pos ? log1pf(r / k.r0) : logf(r));
-  const T e = fdiv((N::ldp(Ed + i) + k.Ec) - k.e0 * r, r + k.r0);
+  const T Ev = N::ldp(Ed + i);
+  const T e = fdiv((Ev + k.Ec) - k.e0 * r, r + k.r0);
   N::stp(ed + i, e);
   if (ler) {
     const float m = (float)k.emean[i / sz];
     N::stp(ler + i, log1pf((e - m) / (k.e0 + m)));
+  }
+  if (lq) {   // ln(P / P_aver) = ln(E / <E>_h) = log1p((E' - <E'>_h) / (E0 + <E'>_h))
+    const double m = k.Emean[i / sz];
+    N::stp(lq + i, log1pf((Ev - (float)m) / (float)((double)k.E0 + m)));
   }
 }
 
@@ -916,7 +922,8 @@ __device__ __forceinline__ void flux_mom_cell(const N& n, const FluxIn& in, cons
   const float* uu[3] = {in.ux, in.uy, in.uz};
   const float* qd[3] = {in.qxx, in.qyy, in.qzz};
   float* md[3] = {out.mxx, out.myy, out.mzz};
-  const T Pd = k.gm1 * n.ld(in.Ed);
+  // With ln(P/P_aver) the pressure gradient is added by k_div instead.
+  const T Pd = k.lnpa ? T(0.f) : k.gm1 * n.ld(in.Ed);
   // Diagonal momentum flux at centres: up(p_d) up(u_d) + P - tau_dd.
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -1078,7 +1085,20 @@ struct DivIn {
   const float *mxx, *myy, *mzz, *mxy, *myx, *mxz, *mzx, *myz, *mzy;
   const float *lx1, *lx2, *ly1, *ly2, *lz1, *lz2, *gx, *gy, *gz, *qt, *Ex, *Ey, *Ez, *ls;
   const float* f[8];   // stage input (deviations), for the update
+  const float* lq;     // ln(P / P_aver) (lnp_aver), else null
 };
+
+// Pressure gradient along D at the D face through ln(P/P_aver), eq. (pressure):
+// exp(dn ln P_aver + dn lq) (dddn lq + dddn ln P_aver), the P_aver factors per
+// plane from k_lnpa_tab (the x and y derivatives of ln P_aver vanish).
+template <int D, class N>
+__device__ __forceinline__ typename N::T lnp_grad(const N& n, const float* lq, const KPar& k) {
+  using T = typename N::T;
+  auto q = [&](int o) { return n.lda(lq, D, o); };
+  const T d = s_dd(q, n.jd(D, k));
+  if (D == 2) return (__ldg(k.paz + n.kz) * expf(s_dn(q))) * (d + __ldg(k.dpaz + n.kz));
+  return (__ldg(k.pa + n.kz) * expf(s_dn(q))) * d;
+}
 
 // F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q, for the
 // fields in the bit mask M (bit c: field c), each stored as soon as it is
@@ -1110,6 +1130,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     t += s_up(AX(in.lx1, 2));
     t -= s_up(AX(in.lx2, 1));
     if (k.g[0] != 0.f) t += dens(s_dn(AX(in.ls, 0)), k) * k.g[0];
+    if (k.lnpa) t -= lnp_grad<0>(n, in.lq, k);
     fin(1, t);
   }
   if (M & 4) {   // eq. (mom), y
@@ -1119,6 +1140,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     t += s_up(AX(in.ly1, 0));
     t -= s_up(AX(in.ly2, 2));
     if (k.g[1] != 0.f) t += dens(s_dn(AX(in.ls, 1)), k) * k.g[1];
+    if (k.lnpa) t -= lnp_grad<1>(n, in.lq, k);
     fin(2, t);
   }
   if (M & 8) {   // eq. (mom), z
@@ -1128,6 +1150,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     t += s_up(AX(in.lz1, 1));
     t -= s_up(AX(in.lz2, 0));
     if (k.g[2] != 0.f) t += dens(s_dn(AX(in.ls, 2)), k) * k.g[2];
+    if (k.lnpa) t -= lnp_grad<2>(n, in.lq, k);
     fin(3, t);
   }
   if (M & 16)   // eq. (ien)
@@ -1193,6 +1216,8 @@ __global__ void k_update8(Upd8 u, float beta, const double* dtp, long long n, in
 // Mean over each horizontal plane (constant z) of e - e0 = (E' + Ec - e0 r')/r, in
 // FP64 with a fixed summation order: part[k * nb + b] is block b's sum over
 // its strided share of plane k; k_plane_final sums the nb parts of a plane.
+// PE: the plane sums of E - E0 instead (ln(P/P_aver)).
+template <bool PE>
 __global__ void k_plane_part(const float* __restrict__ rd, const float* __restrict__ Ed,
                              double* part, KPar k, Geo g) {
   __shared__ double sm[256];
@@ -1203,7 +1228,7 @@ __global__ void k_plane_part(const float* __restrict__ rd, const float* __restri
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)nb * blockDim.x)
-    acc += (double)(((E[i] + k.Ec) - k.e0 * r[i]) / (r[i] + k.r0));
+    acc += PE ? (double)E[i] : (double)(((E[i] + k.Ec) - k.e0 * r[i]) / (r[i] + k.r0));
   sm[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -1219,6 +1244,32 @@ __global__ void k_plane_final(const double* part, int nb, double* mean, Geo g) {
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += part[(long long)kz * nb + b];
   mean[kz] = s / ((double)g.nx * g.ny);
+}
+
+// ln(P/P_aver), eq. (pressure): one block.  The plane means of E - E0 from
+// their nb parts, then per plane k (z periodic over the arrays) P_aver(k) =
+// (gamma - 1)(E0 + <E'>_k), and at its lower z face exp(dn_z ln P_aver) and
+// dddn_z ln P_aver (eqs. (interp), (deriv) on the nz values of ln P_aver).
+__global__ void k_lnpa_tab(const double* part, int nb, double* mean, float* pa, float* paz,
+                           float* dpaz, KPar k, Geo g) {
+  const int nz = g.nz;
+  for (int kz = threadIdx.x; kz < nz; kz += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(long long)kz * nb + b];
+    mean[kz] = s / ((double)g.nx * g.ny);
+  }
+  __syncthreads();
+  const double a1 = 75.0 / 128.0, b1 = -25.0 / 256.0, c1 = 3.0 / 256.0;   // eq. (interp)
+  const double a2 = 75.0 / 64.0, b2 = -25.0 / 384.0, c2 = 3.0 / 640.0;    // eq. (deriv)
+  const double gm1 = (double)k.gm1, E0 = (double)k.E0;
+  auto lpa = [&](int kz) { return log(gm1 * (E0 + mean[wrap(kz, nz)])); };
+  for (int kz = threadIdx.x; kz < nz; kz += blockDim.x) {
+    const double l[6] = {lpa(kz - 3), lpa(kz - 2), lpa(kz - 1), lpa(kz), lpa(kz + 1), lpa(kz + 2)};
+    pa[kz] = (float)exp(l[3]);
+    paz[kz] = (float)exp(a1 * (l[2] + l[3]) + b1 * (l[1] + l[4]) + c1 * (l[0] + l[5]));
+    const double jf = k.jzf ? (double)k.jzf[kz] : (double)k.ih[2];
+    dpaz[kz] = (float)((a2 * (l[3] - l[2]) + b2 * (l[4] - l[1]) + c2 * (l[5] - l[0])) * jf);
+  }
 }
 
 // -------------------------------------------------------------- Courant ----

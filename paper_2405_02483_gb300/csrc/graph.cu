@@ -641,7 +641,8 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   // eq. (mom): momentum flux components minus the (quenched) stress.
   auto minus_tau = [&](int flux, int tau) { return tau >= 0 ? G.sub(flux, tau) : flux; };
   auto Tdiag = [&](int d, int tau) {
-    return minus_tau(G.add(G.mul(up(pf[d], d), up(u[d], d)), Pd), tau);
+    const int adv = G.mul(up(pf[d], d), up(u[d], d));
+    return minus_tau(p.lnp_aver ? adv : G.add(adv, Pd), tau);
   };
   auto Toff = [&](int d, int a, int tau) {  // p_d carried along axis a
     return minus_tau(G.mul(dn(pf[d], a), dn(u[a], d)), tau);
@@ -649,6 +650,20 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   auto grav = [&](int t, int d) {
     return p.g[d] != 0.0 ? G.add(t, G.axpb(rf[d], p.g[d], 0.0)) : t;
   };
+  // eq. (pressure), lnp_aver (R24): P leaves the diagonal fluxes; its gradient
+  // at the d face is exp(dn ln P_aver + dn lq) (dddn lq + dddn ln P_aver), lq =
+  // ln(P/P_aver) = log1p((E' - <E'>_h) / (E0 + <E'>_h)); x and y derivatives of
+  // the plane function ln P_aver vanish.
+  int gradP[3] = {-1, -1, -1};
+  if (p.lnp_aver) {
+    const int pm = G.pmean(Ed);
+    const int lpa = G.lg(G.axpb(pm, gm1, gm1 * E0));
+    const int lq = G.lg1p(G.div(G.sub(Ed, pm), G.axpb(pm, 1.0, E0)));
+    for (int d = 0; d < 3; ++d) {
+      const int pface = G.ex(G.add(d == Z ? dn(lpa, Z) : lpa, dn(lq, d)));
+      gradP[d] = G.mul(pface, d == Z ? G.add(dddn(lq, Z), dddn(lpa, Z)) : dddn(lq, d));
+    }
+  }
   int d_px = neg(dddn(Tdiag(X, txx), X));
   d_px = G.sub(d_px, ddup(Toff(X, Y, txy), Y));
   d_px = G.sub(d_px, ddup(Toff(X, Z, tzx), Z));
@@ -666,6 +681,11 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   d_pz = G.sub(d_pz, dddn(Tdiag(Z, tzz), Z));
   d_pz = G.add(d_pz, up(G.mul(Jx, dn(B[Y], Z)), Y));
   d_pz = grav(G.sub(d_pz, up(G.mul(Jy, dn(B[X], Z)), X)), Z);
+  if (p.lnp_aver) {
+    d_px = G.sub(d_px, gradP[X]);
+    d_py = G.sub(d_py, gradP[Y]);
+    d_pz = G.sub(d_pz, gradP[Z]);
+  }
 
   // eq. (ien)
   int adv = G.add(G.add(ddup(G.mul(pf[X], dn(e, X)), X), ddup(G.mul(pf[Y], dn(e, Y)), Y)),

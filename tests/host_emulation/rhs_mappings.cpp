@@ -91,7 +91,8 @@ static void rhs(const Geo& g, const KPar& kin, float* const* f, std::vector<std:
   const float* ls = k.log_interp ? D[F_LR] : f[0];
   using NB = typename N::Base;
   run(dim3((unsigned)((g.n / N::W + 255) / 256)), dim3(256), [&] {
-    k_lr_ed<NB>(f[0], f[4], k.log_interp ? D[F_LR] : nullptr, D[F_ED], nullptr, k, g.n, g.sz);
+    k_lr_ed<NB>(f[0], f[4], k.log_interp ? D[F_LR] : nullptr, D[F_ED], nullptr, nullptr, k, g.n,
+                g.sz);
   });
   launch<N>(g, [&] { k_vel<NB>(ls, f[1], f[2], f[3], D[F_UX], D[F_UY], D[F_UZ], D[F_LFX], D[F_LFY], D[F_LFZ], k, g); });
   if (k.rm) {
@@ -150,6 +151,7 @@ static void rhs(const Geo& g, const KPar& kin, float* const* f, std::vector<std:
   di.lz1 = D[F_LZ1]; di.lz2 = D[F_LZ2];
   di.gx = D[F_GX]; di.gy = D[F_GY]; di.gz = D[F_GZ]; di.qt = D[F_QT];
   di.Ex = D[F_EX]; di.Ey = D[F_EY]; di.Ez = D[F_EZ]; di.ls = ls;
+  di.lq = D[F_LQ];
   for (int c = 0; c < 8; ++c) di.f[c] = f[c];
   double dtv = 0;
   launch<N>(g, [&] {

@@ -66,7 +66,8 @@ def test_mesh_and_switch_parameters_are_validated_without_gpu(S):
              dict(zc=good, zf=good[:5] + [0.0]),             # a non-positive spacing
              dict(zc=good[:5] + [float("nan")], zf=good),    # not finite
              dict(do_2nddiv=2), dict(do_2nddiv=1, d2lnr_lim=float("inf")),
-             dict(scalar_cells=2)]
+             dict(scalar_cells=2), dict(ediffav=2), dict(lnp_aver=2), dict(lnp_aver=-1),
+             dict(lnp_aver=1, fuse_flux_div=1)]   # k_fdiv does not take ln(P/P_aver)
     for kw in cases:
         q = S.default_params(**kw)
         assert S.lib.stagger_create(ctypes.byref(g), ctypes.byref(q), ctypes.byref(h)) == S.EINVAL, kw

@@ -95,6 +95,19 @@ def ragged_state(shape, seed=7):
     return inputs.Workload("ragged", shape, (1.0 / nx, 1.1 / ny, 0.9 / nz), f)
 
 
+def stratified_state(shape, seed=7, depth=0.8):
+    """ragged_state with rho and E scaled along z by exp(depth cos(2 pi z))
+    (periodic): a horizontal-mean pressure that varies by a factor e^(2 depth)
+    over the box, the fluctuations about it a few per cent."""
+    w = ragged_state(shape, seed)
+    nz = shape[2]
+    prof = np.exp(depth * np.cos(2 * np.pi * (np.arange(nz) + 0.5) / nz))[:, None, None]
+    f = list(w.fields)
+    f[0] = f[0] * prof
+    f[4] = f[4] * prof ** 1.3
+    return inputs.Workload("stratified", shape, w.spacing, f)
+
+
 def make(S, w, kw, refs=None):
     refs, dev = S.split_state(w.fields, refs)
     sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **kw))
@@ -135,6 +148,13 @@ CASES = {
     # eq. (ediffav): only the fluctuations about the horizontal mean of e diffuse.
     "ragged27x22x13_visc_quench_ediffav": (lambda: ragged_state((27, 22, 13)),
                                            dict(VISC_KW, ediffav=1)),
+    # eq. (pressure): the pressure gradient through ln(P/P_aver).
+    "ragged26x20x12_visc_quench_lnp_aver": (lambda: ragged_state((26, 20, 12)),
+                                            dict(VISC_KW, lnp_aver=1)),
+    "strat24x18x20_visc_gravity_lnp_aver": (lambda: stratified_state((24, 18, 20)),
+                                            dict(VISC_KW, g=(0.0, 0.0, -1.0), lnp_aver=1)),
+    "strat17x13x16_ideal_lnp_aver": (lambda: stratified_state((17, 13, 16), depth=1.2),
+                                     dict(lnp_aver=1)),
     # The other reading of eq. (quench): the 3-cell max of |T| in the ratio.
     "ot3d24_visc_quench_max3": (lambda: inputs.orszag_tang_3d(24), dict(VISC_KW, quench_max3=1)),
     "ot2d_64x64x1_visc_quench_max3": (lambda: inputs.orszag_tang(64, 64, 1),
@@ -234,6 +254,7 @@ VEC_CASES = {
     "vec8_ideal_cooling_highcut": (
         (8, 16, 12), dict(t_cool=0.1, e_cool=0.8, rho_cool=0.98, cool_cut=2)),
     "vec24_ediffav_chromo": ((24, 14, 11), dict(VISC_KW, ediffav=1, t_chromo=0.2, rho_bot=1.1)),
+    "vec20_lnp_aver_gravity": ((20, 12, 10), dict(VISC_KW, lnp_aver=1, g=(0.0, 0.0, -1.0))),
 }
 
 
@@ -313,7 +334,8 @@ def test_linear_waves_one_and_fifty_steps(S):
                                          ("ragged37x29x11_visc_quench", 3),
                                          ("ragged_const_nu_c1_gravity_nolog", 3),
                                          ("ragged_visc_cooling_lowcut", 3),
-                                         ("ragged_smagorinsky_rm_quench", 3)])
+                                         ("ragged_smagorinsky_rm_quench", 3),
+                                         ("strat24x18x20_visc_gravity_lnp_aver", 3)])
 def test_viscous_steps(S, name, nsteps):
     w, kw = _case(name)
     sim, refs, dev = make(S, w, kw)
@@ -391,7 +413,8 @@ def test_step_host_equals_device_step(S):
     sim.close()
 
 
-@pytest.mark.parametrize("name", ["waves16_ideal", "ragged13x11x9_visc_quench", "ot3d12_visc_quench"])
+@pytest.mark.parametrize("name", ["waves16_ideal", "ragged13x11x9_visc_quench", "ot3d12_visc_quench",
+                                  "ragged13x11x9_visc_quench_lnp_aver"])
 def test_adjoint_matches_oracle(S, name):
     """FP64 GPU adjoint vs the oracle's reverse sweep to 1e-10 on every state.
     FP32 to 1e-4 relative L2 on states without exact ties; the Orszag-Tang
@@ -401,6 +424,8 @@ def test_adjoint_matches_oracle(S, name):
         w, kw = inputs.linear_waves(16), {}
     elif name.startswith("ragged"):
         w, kw = ragged_state((13, 11, 9)), VISC_KW
+        if name.endswith("lnp_aver"):
+            kw = dict(VISC_KW, lnp_aver=1)
     else:
         w, kw = inputs.orszag_tang_3d(12), VISC_KW
     sim, refs, dev = make(S, w, kw)

@@ -42,6 +42,8 @@ CASES = {
     "zs16x8x9_const_nu_cooling": ((16, 8, 9), dict(nu_const=0.002, nuE=0.5, nuB=0.7, t_cool=0.1,
                                                    e_cool=0.8, rho_cool=0.98, cool_cut=2,
                                                    log_interp=0)),
+    # eq. (pressure) through ln(P/P_aver): dddn_z ln P_aver on the stretched faces
+    "zs20x12x8_visc_lnp_aver": ((20, 12, 8), dict(VISC_KW, lnp_aver=1)),
 }
 
 
