@@ -159,7 +159,19 @@ typedef struct {
    * stagger_step_adjoint*) and stagger_diagnostics_noalloc return
    * STAGGER_EUNSUPPORTED with walls.  Gravity along z acts on the physical
    * faces; a stratified atmosphere is not in balance at a wall under this
-   * continuation (the density is reflected, not extrapolated). */
+   * continuation (the density is reflected, not extrapolated).
+   * zwalls 2: rigid walls (Sect. "Boundary Conditions", "Rigid") at the same
+   * planes.  Every plane outside zghost .. nz-1-zghost is a ghost plane, for
+   * the z-face fields too (so the faces zghost and nz-1-zghost are physical).
+   * The ghost values of rho, E and B are the caller's and never change (their
+   * time derivatives are zero); before every use of a state the library sets
+   * its ghost momenta to p_d = rho_d u_d(b): the density at the p_d position
+   * times the velocity p_d / rho_d of the boundary plane b at the same (x, y)
+   * (b = zghost below, nz-1-zghost above).  The Courant step and the
+   * diagnostics (plain sums) cover the physical planes.  The same zghost, nz,
+   * uniform-z and no-Smagorinsky conditions hold; ref[] is unrestricted.
+   * Ghost planes holding a hydrostatic atmosphere keep it in balance at the
+   * wall. */
   int zwalls;
   int zghost;
   /* Energy diffusion of the fluctuations only, eq. (ediffav): with ediffav 1

@@ -11,4 +11,5 @@ from .stagger import (  # noqa: F401
     diagnostics, step_adjoint, quench, max3, smooth3, ALPHA, BETA,
     mirror_extend, fill_wall_ghosts, rhs_walls, courant_walls, step_walls, diagnostics_walls,
     WALL_PARITY, Z_FACE,
+    face_densities, fill_rigid_ghosts, rhs_rigid, courant_rigid, step_rigid, diagnostics_rigid,
 )

@@ -20,14 +20,14 @@ path by specification only, never by code):
   R4  log interpolation of rho to faces and edges (do_loginterp);
   R5  max over 3 cells then a 3-cell mean, along x, y, z in turn;
   R6  energy diffusion flux nuE * dn(rho nu_ii) * dd_dn(e);
+  R23 eq. (ediffav), with ediffav: the flux nuE * dn(rho nu_ii) * dn(e) *
+      dd_dn(ln e - ln <e>_h), <e>_h the mean of e = E/rho over the horizontal
+      plane (constant z) of the cell, of the state the RHS is evaluated on;
   R24 eq. (pressure), with lnp_aver: the pressure leaves the diagonal momentum
       flux and its gradient along d at the d face becomes
       exp(dn_d(ln P_aver) + dn_d(ln(P/P_aver))) *
       (dddn_d(ln(P/P_aver)) + dddn_d(ln P_aver)), P_aver the horizontal-plane
       mean of P (the second derivative term vanishes for d = x, y);
-  R23 eq. (ediffav), with ediffav: the flux nuE * dn(rho nu_ii) * dn(e) *
-      dd_dn(ln e - ln <e>_h), <e>_h the mean of e = E/rho over the horizontal
-      plane (constant z) of the cell, of the state the RHS is evaluated on;
   R7  resistivity eta on an edge = nuB * nu of that edge;
   R8  quench: one quenched value per stress / eta J component, the factor
       taken over the directions in which that component is differentiated;
@@ -831,3 +831,96 @@ def diagnostics_walls(f, g: Grid, p: Params, lb, ub):
     out[3] = float(f[3][lb + 1:ub + 1].to(DT).sum())
     out[9] = float(sum(int((~torch.isfinite(fi[lb:ub + 1])).sum()) for fi in f))
     return out
+
+
+# --------------------------------------------------------------------------
+# Rigid walls along z, Sect. "Boundary Conditions" ("Rigid"), reading R25
+# --------------------------------------------------------------------------
+#
+# The arrays hold ghost planes below the boundary plane lb and above the
+# boundary plane ub; a ghost plane is one whose index lies outside lb..ub,
+# for every field whatever its staggering (so the z faces lb and ub are
+# physical).  The ghost values of rho, E and B are the caller's and never
+# change: their time derivatives are zero.  The ghost momenta are set, before
+# every evaluation of the right-hand side, so that the velocity of each ghost
+# point is the velocity of the boundary plane at the same (x, y):
+# p_d(k) = rho_d(k) u_d(b), u_d = p_d / rho_d, rho_d the density at the
+# position of p_d (the same face density as the right-hand side's), b = lb
+# below and ub above.  The right-hand side of the physical planes is then the
+# right-hand side of the padded arrays, whose ghost layers cover the reach of
+# the operators (at least 14 planes), so that the periodic wrap of the padded
+# arrays never reaches a physical plane.
+
+
+def face_densities(f, p: Params):
+    """rho at the x, y and z faces as the right-hand side forms it (R4)."""
+    r = f[0].to(DT)
+    if p.log_interp:
+        lr = torch.log(r)
+        return [torch.exp(dn(lr, a)) for a in "xyz"]
+    return [dn(r, a) for a in "xyz"]
+
+
+def fill_rigid_ghosts(f, p: Params, lb, ub):
+    """The state with the momenta of its ghost planes (indices outside lb..ub)
+    set to the face density there times the velocity of the boundary plane
+    (lb below, ub above) at the same (x, y), reading R25; rho, E and B are
+    returned unchanged."""
+    out = [fi.to(DT).clone() for fi in f]
+    rf = face_densities(out, p)
+    for d in range(3):
+        c = 1 + d
+        u = out[c] / rf[d]
+        out[c][:lb] = rf[d][:lb] * u[lb]
+        out[c][ub + 1:] = rf[d][ub + 1:] * u[ub]
+    return out
+
+
+def rhs_rigid(f, g: Grid, p: Params, lb, ub):
+    """F(f) of the box with rigid z walls (reading R25): the right-hand side of
+    the state with its ghost momenta filled, on the physical planes lb..ub of
+    every field; zero on the ghost planes."""
+    fr = fill_rigid_ghosts(f, p, lb, ub)
+    F = rhs(fr, g, p)
+    for c in range(8):
+        F[c][:lb] = 0.0
+        F[c][ub + 1:] = 0.0
+    return F
+
+
+def courant_rigid(f, q1, g: Grid, p: Params, lb, ub):
+    """eq. (courantcond) of the box with rigid z walls: the limits over the
+    physical centre planes lb..ub of the filled state."""
+    fr = fill_rigid_ghosts(f, p, lb, ub)
+    w, rate, nu = courant_fields(fr, q1, g, p)
+    sl = slice(lb, ub + 1)
+    return courant_limits(w[sl], rate[sl], None if nu is None else nu[sl], g, p)
+
+
+def step_rigid(f, g: Grid, p: Params, lb, ub, dt=None):
+    """One full time step with rigid z walls (R9 for the Courant step); the
+    ghost momenta of the result are filled from its own boundary planes."""
+    f = fill_rigid_ghosts(f, p, lb, ub)
+    if dt is None:
+        q1 = rhs_rigid(f, g, p, lb, ub)
+        dt, _ = courant_rigid(f, q1, g, p, lb, ub)
+    out = rk3_step(f, dt, lambda s: rhs_rigid(s, g, p, lb, ub))
+    return fill_rigid_ghosts(out, p, lb, ub), dt
+
+
+def diagnostics_rigid(f, g: Grid, p: Params, lb, ub):
+    """The totals of the physical planes lb..ub (every field, centres and z
+    faces alike) of the filled state: plain sums, kinetic and magnetic energy,
+    max |div B| and rms div B over the centres lb..ub, the non-finite count of
+    the physical planes."""
+    fr = fill_rigid_ghosts(f, p, lb, ub)
+    r, px, py, pz, E, Bx, By, Bz = fr
+    rx, ry, rz = face_densities(fr, p)
+    sl = slice(lb, ub + 1)
+    kin = 0.5 * (px * px / rx + py * py / ry + pz * pz / rz)[sl].sum()
+    mag = 0.5 * (Bx * Bx + By * By + Bz * Bz)[sl].sum()
+    divb = (ddup(Bx, "x", g.hc("x")) + ddup(By, "y", g.hc("y")) + ddup(Bz, "z", g.hc("z")))[sl]
+    nonfinite = sum(int((~torch.isfinite(fi[sl])).sum()) for fi in f)
+    return [float(r[sl].sum()), float(px[sl].sum()), float(py[sl].sum()), float(pz[sl].sum()),
+            float(E[sl].sum()), float(kin), float(mag), float(divb.abs().max()),
+            float(divb.pow(2).mean().sqrt()), float(nonfinite)]

@@ -54,17 +54,18 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (p->fuse_flux_div < 0 || p->fuse_flux_div > 1) return STAGGER_EINVAL;
   if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
     return STAGGER_EINVAL;
-  if (p->zwalls < 0 || p->zwalls > 1) return STAGGER_EINVAL;
+  if (p->zwalls < 0 || p->zwalls > 2) return STAGGER_EINVAL;
   if (p->ediffav < 0 || p->ediffav > 1) return STAGGER_EINVAL;
   if (p->lnp_aver < 0 || p->lnp_aver > 1) return STAGGER_EINVAL;
   if (p->lnp_aver && p->fuse_flux_div) return STAGGER_EINVAL;
-  // Closed z walls: at least the reach of the right-hand side in ghost planes
+  // z walls (closed or rigid): at least the reach of the right-hand side in ghost planes
   // at each end, one physical spacing between the boundary planes, uniform z.
   if (p->zwalls && (p->zghost < STAGGER_ZGHOST_MIN || g->nz < 2 * p->zghost + 2 || p->zc ||
                     p->csmag > 0))
     return STAGGER_EINVAL;
   // The reflection acts on the stored deviations: the odd fields need a zero background.
-  if (p->zwalls && (p->ref[3] != 0 || p->ref[5] != 0 || p->ref[6] != 0)) return STAGGER_EINVAL;
+  if (p->zwalls == 1 && (p->ref[3] != 0 || p->ref[5] != 0 || p->ref[6] != 0))
+    return STAGGER_EINVAL;
   if (p->do_2nddiv < 0 || p->do_2nddiv > 1 || !isfinite(p->d2lnr_lim)) return STAGGER_EINVAL;
   for (int k = 0; k < 8; ++k)
     if (!isfinite(p->ref[k])) return STAGGER_EINVAL;

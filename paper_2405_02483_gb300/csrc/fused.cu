@@ -113,8 +113,9 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.cells4 = (gr.nx % 4) == 0 && !p.scalar_cells;
   // One z-marching flux-divergence kernel per stage (on request; uniform z only).
   F.fdiv = p.fuse_flux_div && p.zc == nullptr;
-  // Closed z walls (R22): boundary centre planes zghost and nz - 1 - zghost.
-  F.wall = p.zwalls ? 1 : 0;
+  // z walls at the planes zghost and nz - 1 - zghost: 0 periodic, 1 closed
+  // (R22), 2 rigid (R25).
+  F.wall = p.zwalls;
   F.launches = 0;
   F.timing = 0;
   for (int i = 0; i < K_COUNT; ++i) { F.kt_ms[i] = 0; F.kt_n[i] = 0; }
@@ -202,7 +203,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.lnpa = p.lnp_aver ? 1 : 0;
   k.Emean = nullptr;
   k.pa = k.paz = k.dpaz = nullptr;
-  k.wall = p.zwalls ? 1 : 0;
+  k.wall = p.zwalls;
   k.klo = p.zwalls ? p.zghost : 0;
   k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
   F.zs = zs ? 1 : 0;
@@ -459,9 +460,19 @@ static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs && !F.wall; }
 
 // Closed z walls: fill the ghost planes of the eight state arrays f (and
 // zero the odd centred fields on the boundary planes), or zero the ghost
-// planes of a time derivative.
+// planes of a time derivative.  Rigid z walls: the ghost momenta of f.
 static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) {
   const Geo& g = F.geo;
+  if (F.wall == 2) {
+    // Rigid walls: the divergence kernels write zero derivatives on the ghost
+    // planes; a state gets the ghost momenta of its boundary velocity.
+    if (zero) return;
+    Mom3 m = {{f[1], f[2], f[3]}};
+    const int lb = F.kp.klo, ub = F.kp.khi;
+    const dim3 gr((unsigned)((g.sz + 255) / 256), (unsigned)(lb + (g.nz - 1 - ub)), 3);
+    TIMED(K_WALL, (k_rigid_fill<<<gr, 256, 0, s>>>(m, f[0], F.kp, lb, ub, g)));
+    return;
+  }
   Wall8 w;
   for (int c = 0; c < 8; ++c) w.f[c] = f[c];
   const int lb = F.kp.klo, ub = F.kp.khi;
@@ -628,7 +639,7 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
   float* const* st_out[3] = {B, C, A};
   for (int stg = 0; stg < 3; ++stg) {
     const bool cfl = stg == 0 && dt <= 0 && cfl_fused(F);
-    // Closed z walls: the stage input's ghost planes from its physical planes.
+    // z walls: the stage input's ghost planes from its physical planes.
     if (F.wall) wall_launch(F, st_in[stg], false, s);
     int rc = pre_div(F, st_in[stg], s, cfl);
     if (rc) return rc;
@@ -749,7 +760,10 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
       acc[c] = c == 7 ? fmax(acc[c], h[10 * b + c]) : acc[c] + h[10 * b + c];
   // Sums of the weights: every cell, or with closed z walls the physical
   // centre planes (half weight on the two boundary planes) and faces.
-  const double N = F.wall ? (double)F.geo.sz * (F.kp.khi - F.kp.klo) : (double)F.geo.n;
+  // Rigid walls: every physical plane klo..khi once.
+  const double N = F.wall == 1   ? (double)F.geo.sz * (F.kp.khi - F.kp.klo)
+                   : F.wall == 2 ? (double)F.geo.sz * (F.kp.khi - F.kp.klo + 1)
+                                 : (double)F.geo.n;
   out[0] = acc[0] + p.ref[0] * N;
   out[1] = acc[1] + p.ref[1] * N;
   out[2] = acc[2] + p.ref[2] * N;

@@ -1113,8 +1113,11 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
                                              const double* dtp, int mode, const KPar& k) {
   using T = typename N::T;
   const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
+  // Rigid z walls (R25): the time derivatives of the ghost planes are zero.
+  const bool frozen = k.wall == 2 && (n.kz < k.klo || n.kz > k.khi);
   T F0 = 0.f, F4 = 0.f;
-  auto fin = [&](int c, const T& F) {
+  auto fin = [&](int c, const T& Fc) {
+    const T F = frozen ? T(0.f) : Fc;
     if (CR && c == 0) F0 = F;
     if (CR && c == 4) F4 = F;
     const T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F : F;
@@ -1368,10 +1371,13 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
     double wf = N::ZS ? (double)n.hzf(k) * k.izbar : 1.0;
     // Closed z walls (R22): the totals the closed box conserves weight the
     // boundary centre planes by one half and count the faces klo+1..khi.
-    if (k.wall) {
+    // Rigid z walls (R25): every plane klo..khi counts once, centres and faces.
+    if (k.wall == 1) {
       const int kz = n.kz;
       wc = (kz < k.klo || kz > k.khi) ? 0.0 : (kz == k.klo || kz == k.khi) ? 0.5 : 1.0;
       wf = (kz > k.klo && kz <= k.khi) ? 1.0 : 0.0;
+    } else if (k.wall == 2) {
+      wc = wf = (n.kz < k.klo || n.kz > k.khi) ? 0.0 : 1.0;
     }
     const float* pr[3] = {px, py, pz};
     const float* bb[3] = {bx, by, bz};
@@ -1483,6 +1489,40 @@ __global__ void k_wall_zero(Wall8 w, int lb, int ub, Geo g) {
   const bool face = c == 3 || c == 7;
   const bool ghost = face ? (k <= lb || k > ub) : (k < lb || k > ub);
   if (ghost) w.f[c][(long long)k * m2 + i] = 0.f;
+}
+
+// ------------------------------------------------------- rigid z walls ----
+// Ghost momenta of a box with rigid walls at the planes lb and ub (reading
+// R25): every plane outside lb..ub is a ghost plane, for the face fields too;
+// its momentum p_d is set to rho_d u_d(b), the density at the p_d position
+// (as k_lr_ed and k_vel form it) times the velocity of the boundary plane b
+// (lb below, ub above) at the same (x, y).  The launch reads rho anywhere and
+// p_d on the boundary planes, and writes p_d on the ghost planes only.
+struct Mom3 {
+  float* p[3];
+};
+__global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int lb, int ub,
+                             Geo g) {
+  const int d = blockIdx.z;
+  const int pl = blockIdx.y;                   // planes 0..lb-1, then ub+1..nz-1
+  const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
+  const int b = kz < lb ? lb : ub;
+  auto rho_face = [&](int z) {
+    auto ls = [&](int o) {
+      const float r = rd[lin(g, wrap(ix + (d == 0 ? o : 0), g.nx), wrap(jy + (d == 1 ? o : 0), g.ny),
+                             wrap(z + (d == 2 ? o : 0), g.nz))];
+      if (!k.log_interp) return r;
+      return k.r0pos ? log1pf(r / k.r0) : logf(r);
+    };
+    return dens(s_dn(ls), k);
+  };
+  float* p = m.p[d];
+  const float u = fdiv(p[lin(g, ix, jy, b)] + k.pref[d], rho_face(b));
+  p[lin(g, ix, jy, kz)] = rho_face(kz) * u - k.pref[d];
 }
 
 }  // namespace stg

@@ -395,7 +395,11 @@ __global__ void __launch_bounds__(FD_TX * TY, TY <= 8 ? FD_MINB : 1) k_fdiv(
     const int ko = m - 3;
     if (own && ko >= z0) {
       const long long c = (long long)ko * g.sz + (long long)j * g.sy + i;
-      const float F[8] = {ar[0], apx[0], apy[0], apz[0], aE[0], aBx[0], aBy[0], aBz[0]};
+      // Rigid z walls (R25): the time derivatives of the ghost planes are zero.
+      const bool fz = k.wall == 2 && (ko < k.klo || ko > k.khi);
+      const float F[8] = {fz ? 0.f : ar[0], fz ? 0.f : apx[0], fz ? 0.f : apy[0],
+                          fz ? 0.f : apz[0], fz ? 0.f : aE[0], fz ? 0.f : aBx[0],
+                          fz ? 0.f : aBy[0], fz ? 0.f : aBz[0]};
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float qq = alpha != 0.f ? alpha * qs[e][c] + F[e] : F[e];

@@ -209,7 +209,10 @@ def test_dt_on_device_and_host_equal_courant():
 def test_wall_parameters_are_validated_without_gpu(S):
     h = ctypes.c_void_p()
     ok_nz = 2 * S.ZGHOST_MIN + 2
-    cases = [(S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=2, zghost=S.ZGHOST_MIN)),
+    cases = [(S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=3, zghost=S.ZGHOST_MIN)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=2, zghost=S.ZGHOST_MIN - 1)),
+             (S.Grid(8, 8, ok_nz - 1, 0.1, 0.1, 0.1), dict(zwalls=2, zghost=S.ZGHOST_MIN)),
+             (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=2, zghost=S.ZGHOST_MIN, csmag=0.1)),
              (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN - 1)),
              (S.Grid(8, 8, ok_nz - 1, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN)),
              (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN, csmag=0.1)),
