@@ -240,6 +240,11 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ot2d", action="store_true",
                     help="skip the Orszag-Tang 1024^2 x 1, 2000-step run")
+    ap.add_argument("--stratified", action="store_true",
+                    help="also run the stratified atmosphere with rigid z walls: 768^2 x 384 "
+                         "for 200 FP32 steps, and 384^2 x 192 FP32 against the FP64 op graph")
+    ap.add_argument("--stratified-size", type=int, nargs=3, default=[768, 768, 384],
+                    metavar=("NX", "NY", "NZ"))
     ap.add_argument("--scalar-cells", action="store_true",
                     help="one cell per thread in the fused kernels (default: four x-cells)")
     args = ap.parse_args()
@@ -362,6 +367,8 @@ def main():
     sim.close()
     del dev
     torch.cuda.empty_cache()
+    if rank == 0 and args.stratified:
+        out["stratified_atmosphere"] = stratified_atmosphere(S, torch, tuple(args.stratified_size))
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -433,6 +440,121 @@ def orszag_tang_2d(S, torch, n=1024, steps=2000, every=10):
             "kinetic_first_last": [log[0][5], log[-1][5]],
             "magnetic_first_last": [log[0][6], log[-1][6]],
             "nonfinite": max(d[9] for d in log)}
+
+
+def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
+    """The isothermal atmosphere of 8 scale heights (rho = exp(-8 z), g = 8
+    along -z, velocity noise 1e-3, B = (0, 0, 0.1)) in a (2, 2, 1) box with
+    rigid z walls (reading R25; 14 ghost planes at each end continue the
+    atmosphere) and the benchmark's physics, for `steps` Courant steps:
+    (1) FP32 at `size`, zone-updates/s of the physical cells over the steps
+    alone and FP64 totals every `every` steps, with rigid walls and (1b) with
+    the stellar-atmosphere boundaries (reading R26); (2) FP32 against the FP64
+    op graph at half the resolution with rigid walls, the same dt every step,
+    the error of each field on the physical planes after the steps."""
+    import numpy as np
+    import workloads as inputs
+    G = S.ZGHOST_MIN
+    phys = dict(PHYS, zwalls=2, zghost=G)
+    res = {"workload": "stratified atmosphere %dx%dx%d (+%d ghost planes each end), rigid z "
+                       "walls, RM viscosity + quench, gravity 8, Courant dt" % (size + (G,)),
+           "steps": steps}
+    # (1) full size, FP32
+    w = inputs.stratified_atmosphere(*size, zghost=G)
+    refs, dev = S.split_state(w.fields)
+    shape, spacing = w.shape, w.spacing
+    del w
+    sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **phys))
+    d0 = sim.diagnostics(dev)
+    ms, log = 0.0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps // every):
+        e0.record()
+        sim.run(dev, every)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        log.append(sim.diagnostics(dev))
+    sim.close()
+    ncell = size[0] * size[1] * size[2]
+    lb, ub = G, G + size[2] - 1
+    umax = max(float((dev[c][lb:ub + 1].double() + refs[c]).abs().max()) for c in (1, 2, 3))
+    res.update({"value": ncell * steps / (ms * 1e-3), "unit": UNIT + " (physical cells)",
+                "ms_per_step": ms / steps, "cells_with_ghosts": shape[0] * shape[1] * shape[2],
+                "mass_first_last": [d0[0], log[-1][0]],
+                "kinetic_first_last": [d0[5], log[-1][5]],
+                "max_abs_momentum_last": umax,
+                "max_div_b": max(d[7] for d in log), "nonfinite": max(d[9] for d in log)})
+    del dev
+    torch.cuda.empty_cache()
+    # (1b) the same atmosphere with the stellar-atmosphere boundaries (R26):
+    # the bottom relaxes to its initial plane values on t = 0.1, the inflow
+    # switch on the noise speed, the top limits at their defaults.
+    w = inputs.stratified_atmosphere(*size, zghost=G)
+    rb, Eb = float(w.fields[0][G, 0, 0]), float(w.fields[4][G, 0, 0])
+    refs, dev = S.split_state(w.fields)
+    shape, spacing = w.shape, w.spacing
+    del w
+    popen = dict(PHYS, zwalls=3, zghost=G, bdry_t=0.1, bdry_rho=rb, bdry_E=Eb, bdry_u=1e-3)
+    sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **popen))
+    o0 = sim.diagnostics(dev)
+    ms, olog = 0.0, []
+    for _ in range(steps // every):
+        e0.record()
+        sim.run(dev, every)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        olog.append(sim.diagnostics(dev))
+    sim.close()
+    lb, ub = G, G + size[2] - 1
+    umax = max(float((dev[c][lb:ub + 1].double() + refs[c]).abs().max()) for c in (1, 2, 3))
+    res["open_boundaries"] = {
+        "value": ncell * steps / (ms * 1e-3), "unit": UNIT + " (physical cells)",
+        "ms_per_step": ms / steps, "mass_first_last": [o0[0], olog[-1][0]],
+        "kinetic_first_last": [o0[5], olog[-1][5]], "max_abs_momentum_last": umax,
+        "max_div_b": max(d[7] for d in olog), "nonfinite": max(d[9] for d in olog)}
+    del dev
+    torch.cuda.empty_cache()
+    # (2) half resolution: FP32 fused path against the FP64 op graph
+    half = (size[0] // 2, size[1] // 2, size[2] // 2)
+    w = inputs.stratified_atmosphere(*half, zghost=G)
+    refs, d32 = S.split_state(w.fields)
+    d64 = [torch.tensor(a - r, dtype=torch.float64).cuda() for a, r in zip(w.fields, refs)]
+    shape, spacing = w.shape, w.spacing
+    del w
+    sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **phys))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dt = sim.step(d32, None, want_dt=True)
+        sim.step_unfused_f64(d64, dt)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    sim.close()
+    lb, ub = G, G + half[2] - 1
+    names = ("r", "px", "py", "pz", "E", "Bx", "By", "Bz")
+    err = {}
+    # natural scales: rho and E their own maxima, the momenta rho c_s (c_s = 1
+    # isothermal, times the largest density), the field its largest magnitude
+    rmax = float((d64[0][lb:ub + 1] + refs[0]).max())
+    bmax = max(float((d64[c][lb:ub + 1] + refs[c]).abs().max()) for c in (5, 6, 7))
+    for c in range(8):
+        a = d32[c][lb:ub + 1].double() + refs[c]
+        b = d64[c][lb:ub + 1] + refs[c]
+        rng_ = float(b.max() - b.min())
+        e = float((a - b).abs().max())
+        scale = (float(b.abs().max()) if c in (0, 4) else rmax if c in (1, 2, 3) else bmax)
+        err[names[c]] = {"err_over_range": e / rng_ if rng_ > 0 else e, "range": rng_,
+                         "err_over_scale": e / scale}
+    r32 = d32[0][lb:ub + 1].double() + refs[0]
+    r64 = d64[0][lb:ub + 1] + refs[0]
+    rel = ((r32 - r64).abs() / r64).amax(dim=(1, 2)).cpu().numpy()
+    q = max(1, len(rel) // 4)
+    res["fp32_vs_fp64"] = {"size": list(half), "steps": steps, "per_field": err,
+                           "rho_rel_err_bottom_quarter": float(np.max(rel[:q])),
+                           "rho_rel_err_top_quarter": float(np.max(rel[-q:])),
+                           "wall_seconds_both_paths": t64}
+    return res
 
 
 def run_e2e(sim, dev, steps, ws, n):

@@ -157,7 +157,7 @@ typedef struct {
    * else STAGGER_EINVAL.  The op-graph
    * entries (stagger_rhs_unfused*, stagger_step_unfused_f64,
    * stagger_step_adjoint*) and stagger_diagnostics_noalloc return
-   * STAGGER_EUNSUPPORTED with walls.  Gravity along z acts on the physical
+   * STAGGER_EUNSUPPORTED with closed walls.  Gravity along z acts on the physical
    * faces; a stratified atmosphere is not in balance at a wall under this
    * continuation (the density is reflected, not extrapolated).
    * zwalls 2: rigid walls (Sect. "Boundary Conditions", "Rigid") at the same
@@ -171,7 +171,10 @@ typedef struct {
    * diagnostics (plain sums) cover the physical planes.  The same zghost, nz,
    * uniform-z and no-Smagorinsky conditions hold; ref[] is unrestricted.
    * Ghost planes holding a hydrostatic atmosphere keep it in balance at the
-   * wall. */
+   * wall.  With rigid walls stagger_rhs_unfused, stagger_rhs_unfused_f64 and
+   * stagger_step_unfused_f64 apply the same fill and zero ghost derivatives;
+   * the adjoint entries and stagger_diagnostics_noalloc return
+   * STAGGER_EUNSUPPORTED. */
   int zwalls;
   int zghost;
   /* Energy diffusion of the fluctuations only, eq. (ediffav): with ediffav 1
@@ -190,6 +193,37 @@ typedef struct {
    * diagonal fluxes.  Other values, or lnp_aver 1 with fuse_flux_div 1:
    * STAGGER_EINVAL. */
   int lnp_aver;
+  /* Stellar-atmosphere z boundaries (Sect. "Boundary Conditions", "Stellar
+   * Atmosphere"), zwalls 3, at the planes of the closed walls: physical
+   * centres zghost .. nz-1-zghost and z faces zghost+1 .. nz-1-zghost, every
+   * other plane a ghost plane with zero time derivative.  The bottom (the
+   * interior boundary) is the end gravity points to (g[2] < 0: the low
+   * index end; g[2] == 0: STAGGER_EINVAL), the other end is the top.  Before
+   * every use of a state its ghost planes are filled: ln rho and e = E/rho
+   * extrapolated linearly from the boundary plane and its inner neighbour
+   * (at the top the ghost density limited to [top_rho_lo, top_rho_hi] times
+   * its plane mean, e to [e_b / top_e_fac, e_b top_e_fac] about the boundary
+   * value); bottom momenta symmetric about the boundary point; top momenta
+   * rho_d times the boundary velocity limited to |u| <= top_umax; B
+   * extrapolated linearly and, at the bottom, its horizontal components
+   * blended toward bdry_B (eq. bin) by f = 1/(1 + exp(U/bdry_u)) (eq.
+   * smooth), U the outward velocity at the boundary (f -> 1 in inflows).
+   * On the bottom plane dE/dt = (bdry_E - E)/bdry_t; d rho/dt = f (bdry_rho -
+   * rho)/bdry_t + (1 - f)(F_rho + ((bdry_E - E)/bdry_t - F_E)/(gamma e)) (eqs.
+   * rein, constS to addderiv for the ideal gas); the horizontal momenta
+   * lose f (p_h - <p_h>)/bdry_t.  On the top plane the vertical mass-flux
+   * divergence is replaced by the outward-signed flux over the pressure
+   * scale height (gamma - 1) e / |g_z| (eq. rbdrylo).  bdry_E is internal
+   * energy per volume.  The potential-field relaxation of the top field is
+   * not built.  Needs bdry_t, bdry_rho, bdry_E, bdry_u, top_umax > 0, 0 <
+   * top_rho_lo <= 1 <= top_rho_hi, top_e_fac >= 1, nz >= 3 zghost + 2 (the
+   * mirrored bottom momenta come from physical planes), fuse_flux_div 0 and
+   * the conditions of the closed walls but the ref[] one, else
+   * STAGGER_EINVAL.  The op-graph entries and stagger_diagnostics_noalloc
+   * return STAGGER_EUNSUPPORTED. */
+  double bdry_t, bdry_rho, bdry_E, bdry_u;
+  double bdry_B[3];
+  double top_rho_lo, top_rho_hi, top_e_fac, top_umax;
 } stagger_params;
 
 /* Ghost planes needed at each closed z wall: the reach of the right-hand

@@ -216,6 +216,16 @@ class Params:
     rho_bot: float = 1.0
     cor_L0: float = 0.0      # coronal thin cooling prefactor in code units (0: off), R21
     cor_Tunit: float = 1.0   # kelvin per code unit of (gamma - 1) e
+    # Stellar-atmosphere z boundaries, Sect. "Stellar Atmosphere", reading R26
+    bdry_t: float = 1.0      # relaxation time t_bdry of eq. (rein)
+    bdry_rho: float = 1.0    # density the bottom inflow relaxes to, eq. (rein)
+    bdry_E: float = 1.0      # internal energy per volume the bottom relaxes to
+    bdry_u: float = 1.0      # U_bdry of eq. (smooth)
+    bdry_B: tuple = (0.0, 0.0, 0.0)   # B_bdry of eq. (bin) (horizontal components used)
+    top_rho_lo: float = 0.5  # top ghost density limits, multiples of its plane mean
+    top_rho_hi: float = 2.0
+    top_e_fac: float = 2.0   # top ghost e within [e_b / fac, e_b * fac]
+    top_umax: float = 1.0    # top ghost |u| limit
 
     def visc_on(self):
         return (self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
@@ -923,4 +933,206 @@ def diagnostics_rigid(f, g: Grid, p: Params, lb, ub):
     nonfinite = sum(int((~torch.isfinite(fi[sl])).sum()) for fi in f)
     return [float(r[sl].sum()), float(px[sl].sum()), float(py[sl].sum()), float(pz[sl].sum()),
             float(E[sl].sum()), float(kin), float(mag), float(divb.abs().max()),
+            float(divb.pow(2).mean().sqrt()), float(nonfinite)]
+
+
+# --------------------------------------------------------------------------
+# Stellar-atmosphere z boundaries, Sect. "Boundary Conditions" ("Stellar
+# Atmosphere"), reading R26
+# --------------------------------------------------------------------------
+#
+# The arrays carry ghost planes beyond the boundary planes lb and ub as for
+# the closed walls: physical centres lb..ub and z faces lb+1..ub, every other
+# plane a ghost plane whose time derivative is zero.  The bottom boundary
+# (the interior one, inside the convection zone) is the end gravity points to:
+# lb when g_z < 0, ub when g_z > 0; the other end is the top (the exterior
+# boundary, in the atmosphere).  s is the outward index direction at an end
+# (-1 at lb, +1 at ub); the outward velocity there is U = s u_z, u_z taken on
+# the z face nearest the boundary plane inside the box (lb+1 or ub).
+#
+# Before every evaluation of the right-hand side the ghost planes are filled:
+#  - ln rho and e = E/rho: linear extrapolation from the boundary plane b and
+#    its inner neighbour, x(b + s j) = x(b) + j (x(b) - x(b - s)); at the top
+#    the ghost density is then limited to [lo, hi] times the mean of the
+#    extrapolated ghost density over its plane, and e to [e_b/fac, e_b fac]
+#    about the boundary value at the same (x, y); E = rho e;
+#  - bottom momenta symmetric about the boundary point: p_x, p_y of plane
+#    b + s j from plane b - s j, p_z of face m from face 2b + 1 - m;
+#  - top momenta p_d = rho_d u_d, the ghost velocity the boundary velocity at
+#    the same (x, y) limited to |u| <= top_umax (p_x, p_y from plane b, p_z
+#    from the nearest inside face), rho_d the face density of the filled rho;
+#  - B: every component extrapolated linearly (B_x, B_y from the plane b and
+#    its inner neighbour, B_z from the two nearest inside faces); at the
+#    bottom the horizontal components are then blended toward B_bdry, eq.
+#    (bin), B_h = (1 - f) B_h + f B_bdry, f = 1 / (1 + exp(U / U_bdry)), eq.
+#    (smooth), U the outward velocity of the column (f -> 1 in inflows).
+# After the right-hand side F of the filled state:
+#  - bottom plane b, per column, with the same f: the inflow part relaxes rho
+#    and E (per volume) to bdry_rho, bdry_E on bdry_t, eq. (rein), and damps
+#    the horizontal momenta toward their plane mean on bdry_t; the outflow
+#    part relaxes E the same way and adds to d rho/dt the change that keeps
+#    the entropy, eqs. (constS) to (addderiv) for the ideal gas, where
+#    (d ln P/d ln rho)_e = 1 and (d ln P/d e)_rho = 1/e give a = 0 and
+#    b = 1/(gamma e): d rho/dt += ((bdry_E - E)/t - dE/dt) / (gamma e);
+#    mixed: dE/dt = (bdry_E - E)/t, d rho/dt = f (bdry_rho - rho)/t +
+#    (1 - f)(F_rho + ((bdry_E - E)/t - F_E)/(gamma e)), dp_h/dt = F_ph -
+#    f (p_h - <p_h>_b)/t;
+#  - top plane b, eq. (rbdrylo): the vertical divergence of the mass flux is
+#    replaced by the inward mass flux over the pressure scale height,
+#    d rho/dt += ddup_z(p_z) + s up_z(p_z) / H_P, H_P = (gamma - 1) e / |g_z|.
+# The potential-field relaxation of the top magnetic field (which needs a
+# horizontal Fourier transform) is not built.
+
+
+def _open_ends(p: Params, lb, ub):
+    """(bottom plane, its outward sign), (top plane, its outward sign)."""
+    if p.g[2] < 0:
+        return (lb, -1), (ub, 1)
+    if p.g[2] > 0:
+        return (ub, 1), (lb, -1)
+    raise ValueError("stellar-atmosphere boundaries need gravity along z")
+
+
+def _inside_face(b, s):
+    """The z face nearest the boundary plane b inside the box."""
+    return b + 1 if s < 0 else b
+
+
+def _outward_u(f, p: Params, b, s):
+    """Outward velocity s u_z of each column at the boundary plane b."""
+    rz = face_densities(f, p)[2]
+    m = _inside_face(b, s)
+    return s * f[3][m] / rz[m]
+
+
+def fill_open_ghosts(f, p: Params, lb, ub):
+    """The state with the ghost planes of the stellar-atmosphere boundaries
+    filled (reading R26)."""
+    out = [fi.to(DT).clone() for fi in f]
+    nz = out[0].shape[0]
+    G = min(lb, nz - 1 - ub)
+    (bb, sb), (bt, st) = _open_ends(p, lb, ub)
+    lr = torch.log(out[0])
+    e = out[4] / out[0]
+    for b, s, top in ((bb, sb, False), (bt, st, True)):
+        dl = lr[b] - lr[b - s]
+        de = e[b] - e[b - s]
+        for j in range(1, G + 1):
+            k = b + s * j
+            rj = torch.exp(lr[b] + j * dl)
+            ej = e[b] + j * de
+            if top:
+                m = rj.mean()
+                rj = torch.clamp(rj, min=p.top_rho_lo * m, max=p.top_rho_hi * m)
+                ej = torch.minimum(torch.maximum(ej, e[b] / p.top_e_fac), e[b] * p.top_e_fac)
+            out[0][k] = rj
+            out[4][k] = rj * ej
+    # momenta: symmetric about the bottom boundary point
+    for j in range(1, G + 1):
+        k = bb + sb * j
+        for c in (1, 2):
+            out[c][k] = out[c][bb - sb * j]
+    for m in range(nz):
+        if (sb < 0 and m <= lb) or (sb > 0 and m >= ub + 1):
+            out[3][m] = out[3][2 * bb + 1 - m]
+    rf = face_densities(out, p)
+    mt = _inside_face(bt, st)
+    ub_top = [out[1][bt] / rf[0][bt], out[2][bt] / rf[1][bt], out[3][mt] / rf[2][mt]]
+    ub_top = [torch.clamp(u, min=-p.top_umax, max=p.top_umax) for u in ub_top]
+    for j in range(1, G + 1):
+        k = bt + st * j
+        out[1][k] = rf[0][k] * ub_top[0]
+        out[2][k] = rf[1][k] * ub_top[1]
+    for m in range(nz):
+        top_ghost = (m <= lb) if st < 0 else (m >= ub + 1)
+        if top_ghost:
+            out[3][m] = rf[2][m] * ub_top[2]
+    # magnetic field: linear extrapolation, then the bottom blending with the
+    # outward velocity of the filled state
+    f_bot = 1.0 / (1.0 + torch.exp(_outward_u(out, p, bb, sb) / p.bdry_u))
+    for b, s, top in ((bb, sb, False), (bt, st, True)):
+        mi = _inside_face(b, s)
+        for j in range(1, G + 1):
+            k = b + s * j
+            for c in (5, 6):
+                v = out[c][b] + j * (out[c][b] - out[c][b - s])
+                if not top:
+                    v = (1.0 - f_bot) * v + f_bot * p.bdry_B[c - 5]
+                out[c][k] = v
+        for m in range(nz):
+            d = (mi - m) if s < 0 else (m - mi)     # faces beyond the inside face
+            ghost = (m <= lb) if s < 0 else (m >= ub + 1)
+            if ghost:
+                out[7][m] = out[7][mi] + d * (out[7][mi] - out[7][mi - s])
+    return out
+
+
+def rhs_open(f, g: Grid, p: Params, lb, ub):
+    """F(f) with the stellar-atmosphere z boundaries (reading R26): the
+    right-hand side of the filled state with the bottom and top corrections
+    on the boundary planes, zero on the ghost planes."""
+    fo = fill_open_ghosts(f, p, lb, ub)
+    F = rhs(fo, g, p)
+    (bb, sb), (bt, st) = _open_ends(p, lb, ub)
+    r, E = fo[0], fo[4]
+    t = p.bdry_t
+    # bottom, eqs. (rein), (constS) to (addderiv)
+    fb = 1.0 / (1.0 + torch.exp(_outward_u(fo, p, bb, sb) / p.bdry_u))
+    eb = E[bb] / r[bb]
+    dE = (p.bdry_E - E[bb]) / t
+    Fr_out = F[0][bb] + (dE - F[4][bb]) / (p.gamma * eb)
+    F[0][bb] = fb * (p.bdry_rho - r[bb]) / t + (1.0 - fb) * Fr_out
+    F[4][bb] = dE.clone()
+    for c in (1, 2):
+        F[c][bb] = F[c][bb] - fb * (fo[c][bb] - fo[c][bb].mean()) / t
+    # top, eq. (rbdrylo)
+    hz = Spacing(g.hc("z"), g.hf("z"))
+    HP = (p.gamma - 1.0) * E[bt] / r[bt] / abs(p.g[2])
+    F[0][bt] = F[0][bt] + ddup(fo[3], "z", hz)[bt] + st * up(fo[3], "z")[bt] / HP
+    for c in range(8):
+        if Z_FACE[c]:
+            F[c][:lb + 1] = 0.0
+            F[c][ub + 1:] = 0.0
+        else:
+            F[c][:lb] = 0.0
+            F[c][ub + 1:] = 0.0
+    return F
+
+
+def courant_open(f, q1, g: Grid, p: Params, lb, ub):
+    """eq. (courantcond) with the stellar-atmosphere boundaries: the limits
+    over the physical centre planes lb..ub of the filled state."""
+    fo = fill_open_ghosts(f, p, lb, ub)
+    w, rate, nu = courant_fields(fo, q1, g, p)
+    sl = slice(lb, ub + 1)
+    return courant_limits(w[sl], rate[sl], None if nu is None else nu[sl], g, p)
+
+
+def step_open(f, g: Grid, p: Params, lb, ub, dt=None):
+    """One full time step with the stellar-atmosphere boundaries (R9 for the
+    Courant step); the ghost planes of the result are filled from it."""
+    f = fill_open_ghosts(f, p, lb, ub)
+    if dt is None:
+        q1 = rhs_open(f, g, p, lb, ub)
+        dt, _ = courant_open(f, q1, g, p, lb, ub)
+    out = rk3_step(f, dt, lambda s: rhs_open(s, g, p, lb, ub))
+    return fill_open_ghosts(out, p, lb, ub), dt
+
+
+def diagnostics_open(f, g: Grid, p: Params, lb, ub):
+    """The totals of the physical planes (centres lb..ub, z faces lb+1..ub) of
+    the filled state: plain sums, kinetic and magnetic energy, max |div B| and
+    rms div B over the centres lb..ub, the non-finite count of the physical
+    planes."""
+    fo = fill_open_ghosts(f, p, lb, ub)
+    r, px, py, pz, E, Bx, By, Bz = fo
+    rx, ry, rz = face_densities(fo, p)
+    c = slice(lb, ub + 1)
+    fz = slice(lb + 1, ub + 1)
+    kin = 0.5 * ((px * px / rx + py * py / ry)[c].sum() + (pz * pz / rz)[fz].sum())
+    mag = 0.5 * ((Bx * Bx + By * By)[c].sum() + (Bz * Bz)[fz].sum())
+    divb = (ddup(Bx, "x", g.hc("x")) + ddup(By, "y", g.hc("y")) + ddup(Bz, "z", g.hc("z")))[c]
+    nonfinite = sum(int((~torch.isfinite(fi[c])).sum()) for fi in f)
+    return [float(r[c].sum()), float(px[c].sum()), float(py[c].sum()), float(pz[fz].sum()),
+            float(E[c].sum()), float(kin), float(mag), float(divb.abs().max()),
             float(divb.pow(2).mean().sqrt()), float(nonfinite)]

@@ -50,7 +50,12 @@ class Params(ctypes.Structure):
                 ("quench_max3", ctypes.c_int), ("quench_eps", ctypes.c_double),
                 ("zwalls", ctypes.c_int), ("zghost", ctypes.c_int),
                 ("ediffav", ctypes.c_int),
-                ("lnp_aver", ctypes.c_int)]
+                ("lnp_aver", ctypes.c_int),
+                ("bdry_t", ctypes.c_double), ("bdry_rho", ctypes.c_double),
+                ("bdry_E", ctypes.c_double), ("bdry_u", ctypes.c_double),
+                ("bdry_B", ctypes.c_double * 3),
+                ("top_rho_lo", ctypes.c_double), ("top_rho_hi", ctypes.c_double),
+                ("top_e_fac", ctypes.c_double), ("top_umax", ctypes.c_double)]
 
 ZGHOST_MIN = 14   # STAGGER_ZGHOST_MIN of include/stagger.h
 
@@ -122,6 +127,8 @@ def default_params(**kw) -> Params:
             p.g = (ctypes.c_double * 3)(*v)
         elif k == "ref":
             p.ref = (ctypes.c_double * 8)(*v)
+        elif k == "bdry_B":
+            p.bdry_B = (ctypes.c_double * 3)(*v)
         elif k in ("zc", "zf"):
             # Stretched z mesh: dz/dk at centres / lower faces (nz values each);
             # the array lives as long as the Params object.

@@ -54,7 +54,19 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (p->fuse_flux_div < 0 || p->fuse_flux_div > 1) return STAGGER_EINVAL;
   if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
     return STAGGER_EINVAL;
-  if (p->zwalls < 0 || p->zwalls > 2) return STAGGER_EINVAL;
+  if (p->zwalls < 0 || p->zwalls > 3) return STAGGER_EINVAL;
+  if (p->zwalls == 3) {   // stellar-atmosphere boundaries
+    const double v[] = {p->bdry_t, p->bdry_rho, p->bdry_E, p->bdry_u, p->bdry_B[0],
+                        p->bdry_B[1], p->bdry_B[2], p->top_rho_lo, p->top_rho_hi,
+                        p->top_e_fac, p->top_umax};
+    for (double x : v)
+      if (!isfinite(x)) return STAGGER_EINVAL;
+    if (!(p->bdry_t > 0) || !(p->bdry_rho > 0) || !(p->bdry_E > 0) || !(p->bdry_u > 0) ||
+        !(p->top_umax > 0) || !(p->top_rho_lo > 0) || p->top_rho_lo > 1 ||
+        p->top_rho_hi < 1 || p->top_e_fac < 1 || p->g[2] == 0 || p->fuse_flux_div ||
+        g->nz < 3 * p->zghost + 2)
+      return STAGGER_EINVAL;
+  }
   if (p->ediffav < 0 || p->ediffav > 1) return STAGGER_EINVAL;
   if (p->lnp_aver < 0 || p->lnp_aver > 1) return STAGGER_EINVAL;
   if (p->lnp_aver && p->fuse_flux_div) return STAGGER_EINVAL;
@@ -105,6 +117,11 @@ int stagger_params_default(stagger_params* p) {
   p->d2lnr_lim = 0.3;
   p->rho_bot = 1.0;
   p->cor_Tunit = 1.0;
+  p->bdry_t = p->bdry_rho = p->bdry_E = p->bdry_u = 1.0;
+  p->top_rho_lo = 0.5;
+  p->top_rho_hi = 2.0;
+  p->top_e_fac = 2.0;
+  p->top_umax = 1.0;
   return STAGGER_OK;
 }
 
@@ -283,6 +300,82 @@ __global__ void k_copy(T* o, const T* x, long long n) {
   if (i < n) o[i] = x[i];
 }
 
+// Rigid z walls (reading R25) around the op graph: the ghost momenta of a
+// state from its boundary planes' velocity, p_d(k) = rho_d(k) u_d(b), rho_d
+// formed as the graph forms it (eq. (interp) on ln(rho/r0), or on rho without
+// log interpolation), and the ghost planes of a derivative zeroed.  Planes
+// outside lb..ub are ghost planes for every field.
+template <typename T>
+struct RigidG {
+  T* p[3];
+  const T* rd;
+  double r0, pref[3];
+  int log_interp;
+};
+template <typename T>
+__global__ void k_rigid_fill_g(RigidG<T> a, int lb, int ub, Geo g) {
+  const int d = blockIdx.z;
+  const int pl = blockIdx.y;                   // planes 0..lb-1, then ub+1..nz-1
+  const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
+  const int b = kz < lb ? lb : ub;
+  auto rho_face = [&](int z) {
+    auto ls = [&](int o) {
+      const double r = (double)a.rd[lin(g, wrap(ix + (d == 0 ? o : 0), g.nx),
+                                        wrap(jy + (d == 1 ? o : 0), g.ny),
+                                        wrap(z + (d == 2 ? o : 0), g.nz))];
+      if (!a.log_interp) return r;
+      return a.r0 > 0 ? log1p(r / a.r0) : log(r + a.r0);
+    };
+    // eq. (interp) to the lower face: weights 75/128, -25/256, 3/256
+    const double v = (75.0 / 128.0) * (ls(-1) + ls(0)) + (-25.0 / 256.0) * (ls(-2) + ls(1)) +
+                     (3.0 / 256.0) * (ls(-3) + ls(2));
+    if (!a.log_interp) return v + a.r0;
+    return a.r0 > 0 ? a.r0 * exp(v) : exp(v);
+  };
+  T* p = a.p[d];
+  const double u = ((double)p[lin(g, ix, jy, b)] + a.pref[d]) / rho_face(b);
+  p[lin(g, ix, jy, kz)] = (T)(rho_face(kz) * u - a.pref[d]);
+}
+template <typename T>
+__global__ void k_zero_ghost_planes(T* o, int lb, int ub, Geo g) {
+  const int pl = blockIdx.y;
+  const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  o[(long long)kz * m2 + i] = T(0);
+}
+
+template <typename T>
+static void rigid_fill_g(stagger_ctx* c, T* const f[8], cudaStream_t s) {
+  const stagger_params& p = c->params;
+  const Geo& g = c->geo;
+  const int lb = p.zghost, ub = g.nz - 1 - p.zghost;
+  RigidG<T> a;
+  for (int d = 0; d < 3; ++d) {
+    a.p[d] = f[1 + d];
+    a.pref[d] = p.ref[1 + d];
+  }
+  a.rd = f[0];
+  a.r0 = p.ref[0];
+  a.log_interp = p.log_interp;
+  const dim3 gr((unsigned)((g.sz + 255) / 256), (unsigned)(lb + (g.nz - 1 - ub)), 3);
+  k_rigid_fill_g<T><<<gr, 256, 0, s>>>(a, lb, ub, g);
+  ++c->extra_launches;
+}
+template <typename T>
+static void rigid_zero_g(stagger_ctx* c, T* o, cudaStream_t s) {
+  const Geo& g = c->geo;
+  const int lb = c->params.zghost, ub = g.nz - 1 - c->params.zghost;
+  const dim3 gr((unsigned)((g.sz + 255) / 256), (unsigned)(lb + (g.nz - 1 - ub)));
+  k_zero_ghost_planes<T><<<gr, 256, 0, s>>>(o, lb, ub, g);
+  ++c->extra_launches;
+}
+
 template <typename T> GraphExec<T>*& graph_of(stagger_ctx* c);
 template <> GraphExec<float>*& graph_of<float>(stagger_ctx* c) { return c->g32; }
 template <> GraphExec<double>*& graph_of<double>(stagger_ctx* c) { return c->g64; }
@@ -333,12 +426,15 @@ static int graph_rhs(stagger_ctx* c, T* const f[8], T* out[8], cudaStream_t s) {
   int rc = ensure_graph<T>(c, false);
   if (rc) return rc;
   GraphExec<T>* G = graph_of<T>(c);
+  const bool rigid = c->params.zwalls == 2;
+  if (rigid) rigid_fill_g<T>(c, f, s);
   rc = G->forward(f, s);
   if (rc) return rc;
   long long n = c->geo.n;
   for (int k = 0; k < 8; ++k) {
     k_copy<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out[k], G->output(k), n);
     ++c->extra_launches;
+    if (rigid) rigid_zero_g<T>(c, out[k], s);
   }
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
@@ -356,15 +452,19 @@ static int graph_step(stagger_ctx* c, T* f[8], double dt, cudaStream_t s) {
   const long long n = c->geo.n;
   T* q[8];
   for (int k = 0; k < 8; ++k) q[k] = w + (size_t)k * n;
+  const bool rigid = c->params.zwalls == 2;
   for (int st = 0; st < 3; ++st) {
+    if (rigid) rigid_fill_g<T>(c, f, s);
     rc = G->forward(f, s);
     if (rc) return rc;
     for (int k = 0; k < 8; ++k) {
+      if (rigid) rigid_zero_g<T>(c, G->output(k), s);
       if (st == 0) lin2<T>(c, q[k], G->output(k), 1.0, G->output(k), 0.0, s);
       else lin2<T>(c, q[k], q[k], RK_ALPHA[st], G->output(k), 1.0, s);
       lin2<T>(c, f[k], f[k], 1.0, q[k], RK_BETA[st] * dt, s);
     }
   }
+  if (rigid) rigid_fill_g<T>(c, f, s);
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -507,26 +607,27 @@ int stagger_step_adjoint(stagger_ctx* c, float* const state_n[8], double dt,
   if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
       !ptrs_ok((void* const*)lam_n) || !(dt > 0))
     return STAGGER_EINVAL;
-  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
+  // the op graph has no transpose of the wall fills
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;
   return graph_step_adjoint<float>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
 }
 
 int stagger_rhs_unfused(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
-  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
+  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
   return graph_rhs<float>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_rhs_unfused_f64(stagger_ctx* c, double* const state[8], double* dfdt[8],
                             void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
-  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
+  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
   return graph_rhs<double>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_step_unfused_f64(stagger_ctx* c, double* state[8], double dt, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !(dt > 0)) return STAGGER_EINVAL;
-  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
+  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
   return graph_step<double>(c, state, dt, (cudaStream_t)stream);
 }
 
@@ -535,7 +636,8 @@ int stagger_step_adjoint_f64(stagger_ctx* c, double* const state_n[8], double dt
   if (!c || !ptrs_ok((void* const*)state_n) || !ptrs_ok((void* const*)lam_np1) ||
       !ptrs_ok((void* const*)lam_n) || !(dt > 0))
     return STAGGER_EINVAL;
-  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;   // the op graph is periodic only
+  // the op graph has no transpose of the wall fills
+  if (c->params.zwalls) return STAGGER_EUNSUPPORTED;
   return graph_step_adjoint<double>(c, state_n, dt, lam_np1, lam_n, (cudaStream_t)stream);
 }
 

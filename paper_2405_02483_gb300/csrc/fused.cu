@@ -206,6 +206,23 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.wall = p.zwalls;
   k.klo = p.zwalls ? p.zghost : 0;
   k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
+  // Stellar-atmosphere boundaries (R26): the bottom is the end gravity points to.
+  k.obot = p.g[2] < 0 ? k.klo : k.khi;
+  k.otop = p.g[2] < 0 ? k.khi : k.klo;
+  k.osb = p.g[2] < 0 ? -1 : 1;
+  k.ost = -k.osb;
+  k.oinv_t = (float)(1.0 / p.bdry_t);
+  k.orho = (float)p.bdry_rho;
+  k.oE = (float)p.bdry_E;
+  k.oinv_u = (float)(1.0 / p.bdry_u);
+  k.oBx = (float)p.bdry_B[0];
+  k.oBy = (float)p.bdry_B[1];
+  k.orlo = (float)p.top_rho_lo;
+  k.orhi = (float)p.top_rho_hi;
+  k.oefac = (float)p.top_e_fac;
+  k.oumax = (float)p.top_umax;
+  k.ogabs = (float)fabs(p.g[2]);
+  k.omean = nullptr;
   F.zs = zs ? 1 : 0;
   F.wsum_f = zs ? (double)gr.nx * gr.ny * zfsum * k.izbar : (double)F.geo.n;
   F.cdt = p.Cdt;
@@ -224,6 +241,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.mesh = nullptr;
   F.plane = nullptr;
   F.pplane = nullptr;
+  F.oplane = nullptr;
   F.plane_nb = (int)std::max(1LL, std::min(64LL, ((long long)gr.nx * gr.ny + 1023) / 1024));
   if (k.lnpa) {
     // ln(P/P_aver): the plane means of E - E0 and their per-block parts, then
@@ -239,6 +257,16 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
     k.pa = reinterpret_cast<const float*>(F.pplane + nd);
     k.paz = k.pa + gr.nz;
     k.dpaz = k.pa + 2 * gr.nz;
+  }
+  if (F.wall == 3) {
+    // Stellar-atmosphere boundaries: zghost + 2 plane means, then their parts.
+    const size_t rows = (size_t)p.zghost + 2;
+    if (cudaMalloc(&F.oplane, sizeof(double) * rows * (1 + F.plane_nb)) != cudaSuccess) {
+      F.oplane = nullptr;
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+    k.omean = F.oplane;
   }
   if (p.t_chromo > 0 || k.ediffav) {
     // Plane means of e for the chromospheric cooling and the energy diffusion
@@ -353,6 +381,8 @@ void fused_release(Fused& F) {
   F.plane = nullptr;
   if (F.pplane) cudaFree(F.pplane);
   F.pplane = nullptr;
+  if (F.oplane) cudaFree(F.oplane);
+  F.oplane = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -463,6 +493,23 @@ static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs && !F.wall; }
 // planes of a time derivative.  Rigid z walls: the ghost momenta of f.
 static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) {
   const Geo& g = F.geo;
+  if (F.wall == 3) {
+    // Stellar-atmosphere boundaries (R26): the divergence kernels write zero
+    // derivatives on the ghost planes; a state gets its ghost planes from the
+    // plane means, the rho and E extrapolation, then momenta and field.
+    if (zero) return;
+    const KPar& k = F.kp;
+    const int G = k.klo, rows = G + 2;
+    TIMED(K_WALL, (k_open_part<<<dim3(F.plane_nb, rows), 256, 0, s>>>(
+                      f[0], f[1], f[2], F.oplane + rows, k, g)));
+    TIMED(K_WALL, (k_open_final<<<(rows + 63) / 64, 64, 0, s>>>(F.oplane + rows, F.plane_nb,
+                                                                  rows, F.oplane, g)));
+    const unsigned bx = (unsigned)((g.sz + 255) / 256);
+    TIMED(K_WALL, (k_open_fill_c<<<dim3(bx, 2 * G), 256, 0, s>>>(f[0], f[4], k, g)));
+    TIMED(K_WALL, (k_open_fill_m<<<dim3(bx, 2 * G + 1), 256, 0, s>>>(f[1], f[2], f[3], f[5],
+                                                                      f[6], f[7], f[0], k, g)));
+    return;
+  }
   if (F.wall == 2) {
     // Rigid walls: the divergence kernels write zero derivatives on the ghost
     // planes; a state gets the ghost momenta of its boundary velocity.
@@ -502,6 +549,7 @@ static DivIn div_in(Fused& F, float* const f[8]) {
   di.ls = F.kp.log_interp ? d[F_LR] : f[0];
   for (int c = 0; c < 8; ++c) di.f[c] = f[c];
   di.lq = d[F_LQ];
+  di.uz = d[F_UZ];
   return di;
 }
 
@@ -762,12 +810,14 @@ int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, doub
   // centre planes (half weight on the two boundary planes) and faces.
   // Rigid walls: every physical plane klo..khi once.
   const double N = F.wall == 1   ? (double)F.geo.sz * (F.kp.khi - F.kp.klo)
-                   : F.wall == 2 ? (double)F.geo.sz * (F.kp.khi - F.kp.klo + 1)
+                   : F.wall >= 2 ? (double)F.geo.sz * (F.kp.khi - F.kp.klo + 1)
                                  : (double)F.geo.n;
+  // Stellar-atmosphere boundaries: the z faces klo+1..khi.
+  const double Nf = F.wall == 3 ? (double)F.geo.sz * (F.kp.khi - F.kp.klo) : N;
   out[0] = acc[0] + p.ref[0] * N;
   out[1] = acc[1] + p.ref[1] * N;
   out[2] = acc[2] + p.ref[2] * N;
-  out[3] = acc[3] + p.ref[3] * (F.wall ? N : F.wsum_f);   // z-face weights on a stretched z
+  out[3] = acc[3] + p.ref[3] * (F.wall ? Nf : F.wsum_f);   // z-face weights on a stretched z
   out[4] = acc[4] + p.ref[4] * N;
   out[5] = acc[5];
   out[6] = acc[6];

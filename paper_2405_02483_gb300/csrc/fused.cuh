@@ -49,6 +49,14 @@ struct KPar {
   int lnpa;
   const double* Emean;
   const float *pa, *paz, *dpaz;
+  // Stellar-atmosphere z boundaries (R26, wall 3): the bottom and top boundary
+  // planes and their outward index directions, 1/bdry_t, the bottom targets,
+  // 1/bdry_u, B_bdry (x, y), the top limits, |g_z|, and the plane means: the
+  // extrapolated density of the top ghost planes 1..zghost (zghost doubles),
+  // then the p_x and p_y deviations of the bottom plane.
+  int obot, otop, osb, ost;
+  float oinv_t, orho, oE, oinv_u, oBx, oBy, orlo, orhi, oefac, oumax, ogabs;
+  const double* omean;
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -97,6 +105,7 @@ struct Fused {
   int plane_nb;
   double* pplane;       // the same for E - E0 (ln(P/P_aver)), then its 3 nz floats of
                         // per-plane pressure factors, or null
+  double* oplane;       // stellar-atmosphere means (zghost + 2), then their per-block parts
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)

@@ -1086,6 +1086,7 @@ struct DivIn {
   const float *lx1, *lx2, *ly1, *ly2, *lz1, *lz2, *gx, *gy, *gz, *qt, *Ex, *Ey, *Ez, *ls;
   const float* f[8];   // stage input (deviations), for the update
   const float* lq;     // ln(P / P_aver) (lnp_aver), else null
+  const float* uz;     // face velocity u_z (stellar-atmosphere boundaries)
 };
 
 // Pressure gradient along D at the D face through ln(P/P_aver), eq. (pressure):
@@ -1113,19 +1114,53 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
                                              const double* dtp, int mode, const KPar& k) {
   using T = typename N::T;
   const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
-  // Rigid z walls (R25): the time derivatives of the ghost planes are zero.
-  const bool frozen = k.wall == 2 && (n.kz < k.klo || n.kz > k.khi);
+  // Rigid (R25) and stellar-atmosphere (R26) z walls: the time derivatives of
+  // the ghost planes are zero (z faces klo and below are ghosts with R26).
+  const bool ghostC = k.wall >= 2 && (n.kz < k.klo || n.kz > k.khi);
+  const bool ghostF = k.wall == 3 ? (n.kz <= k.klo || n.kz > k.khi) : ghostC;
   T F0 = 0.f, F4 = 0.f;
   auto fin = [&](int c, const T& Fc) {
-    const T F = frozen ? T(0.f) : Fc;
+    const T F = ((c == 3 || c == 7) ? ghostF : ghostC) ? T(0.f) : Fc;
     if (CR && c == 0) F0 = F;
     if (CR && c == 4) F4 = F;
     const T qq = alpha != 0.f ? alpha * n.ldw(qs[c]) + F : F;
     n.st(qs[c], qq);
     if (mode) n.st(os[c], n.ld(in.f[c]) + bdt * qq);
   };
-  if (M & 1)   // eq. (mass)
-    fin(0, -((s_du(AX(in.px, 0), n.ju(0, k)) + s_du(AX(in.py, 1), n.ju(1, k))) + s_du(AX(in.pz, 2), n.ju(2, k))));
+  // Stellar-atmosphere boundaries (R26): the inflow weight f of the bottom
+  // plane's column, from the outward velocity on its inside z face.
+  const bool obot = k.wall == 3 && n.kz == k.obot;
+  auto open_f = [&]() {
+    const T ui = n.lda(in.uz, 2, k.osb < 0 ? 1 : 0);
+    return 1.f / (1.f + expf(ui * ((float)k.osb * k.oinv_u)));
+  };
+  T Fm = 0.f, Fe = 0.f;
+  if (M & 1) {   // eq. (mass)
+    const T dxy = s_du(AX(in.px, 0), n.ju(0, k)) + s_du(AX(in.py, 1), n.ju(1, k));
+    Fm = -(dxy + s_du(AX(in.pz, 2), n.ju(2, k)));
+    if (k.wall == 3 && n.kz == k.otop) {
+      // eq. (rbdrylo): the vertical divergence becomes the outward-signed
+      // mass flux over the pressure scale height (gamma - 1) e / |g_z|.
+      const T r = n.ld(in.f[0]) + k.r0, E = n.ld(in.f[4]) + k.E0;
+      const T HP = fdiv(k.gm1 * E, r * k.ogabs);
+      Fm = (float)k.ost * fdiv(s_up(AX(in.pz, 2)) + k.pref[2], HP) - dxy;
+    }
+  }
+  if (M & 16)   // eq. (ien)
+    Fe = -((s_du(AX(in.gx, 0), n.ju(0, k)) + s_du(AX(in.gy, 1), n.ju(1, k))) + s_du(AX(in.gz, 2), n.ju(2, k))) +
+         n.ld(in.qt);
+  if ((M & 17) == 17 && obot) {
+    // eqs. (rein), (constS) to (addderiv), ideal gas: E relaxes to oE; rho
+    // relaxes to orho in inflows (weight f) and takes the isentropic change
+    // in outflows.
+    const T r = n.ld(in.f[0]) + k.r0, E = n.ld(in.f[4]) + k.E0;
+    const T f = open_f();
+    const T dE = (k.oE - E) * k.oinv_t;
+    Fm = f * ((k.orho - r) * k.oinv_t) +
+         (1.f - f) * (Fm + fdiv((dE - Fe) * r, k.gamma * E));
+    Fe = dE;
+  }
+  if (M & 1) fin(0, Fm);
   if (M & 2) {   // eq. (mom), x
     T t = -s_dd(AX(in.mxx, 0), n.jd(0, k));
     t -= s_du(AX(in.mxy, 1), n.ju(1, k));
@@ -1134,6 +1169,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     t -= s_up(AX(in.lx2, 1));
     if (k.g[0] != 0.f) t += dens(s_dn(AX(in.ls, 0)), k) * k.g[0];
     if (k.lnpa) t -= lnp_grad<0>(n, in.lq, k);
+    if (obot) t -= open_f() * ((n.ld(in.px) - (float)k.omean[k.klo]) * k.oinv_t);
     fin(1, t);
   }
   if (M & 4) {   // eq. (mom), y
@@ -1144,6 +1180,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     t -= s_up(AX(in.ly2, 2));
     if (k.g[1] != 0.f) t += dens(s_dn(AX(in.ls, 1)), k) * k.g[1];
     if (k.lnpa) t -= lnp_grad<1>(n, in.lq, k);
+    if (obot) t -= open_f() * ((n.ld(in.py) - (float)k.omean[k.klo + 1]) * k.oinv_t);
     fin(2, t);
   }
   if (M & 8) {   // eq. (mom), z
@@ -1156,9 +1193,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
     if (k.lnpa) t -= lnp_grad<2>(n, in.lq, k);
     fin(3, t);
   }
-  if (M & 16)   // eq. (ien)
-    fin(4, -((s_du(AX(in.gx, 0), n.ju(0, k)) + s_du(AX(in.gy, 1), n.ju(1, k))) + s_du(AX(in.gz, 2), n.ju(2, k))) +
-               n.ld(in.qt));
+  if (M & 16) fin(4, Fe);
   // eq. (indu): dB/dt = -curl E
   if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k))));
   if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), n.ju(2, k)) - s_du(AX(in.Ez, 0), n.ju(0, k))));
@@ -1378,6 +1413,9 @@ __global__ void __launch_bounds__(BX * BY * BZ, STG_MINB) k_diag_part(
       wf = (kz > k.klo && kz <= k.khi) ? 1.0 : 0.0;
     } else if (k.wall == 2) {
       wc = wf = (n.kz < k.klo || n.kz > k.khi) ? 0.0 : 1.0;
+    } else if (k.wall == 3) {   // R26: centres klo..khi, faces klo+1..khi
+      wc = (n.kz < k.klo || n.kz > k.khi) ? 0.0 : 1.0;
+      wf = (n.kz <= k.klo || n.kz > k.khi) ? 0.0 : 1.0;
     }
     const float* pr[3] = {px, py, pz};
     const float* bb[3] = {bx, by, bz};
@@ -1501,6 +1539,17 @@ __global__ void k_wall_zero(Wall8 w, int lb, int ub, Geo g) {
 struct Mom3 {
   float* p[3];
 };
+// rho at the lower d face of cell (ix, jy, z), formed as k_lr_ed and k_vel form it.
+__device__ __forceinline__ float rho_face_at(const float* __restrict__ rd, const KPar& k,
+                                             const Geo& g, int d, int ix, int jy, int z) {
+  auto ls = [&](int o) {
+    const float r = rd[lin(g, wrap(ix + (d == 0 ? o : 0), g.nx), wrap(jy + (d == 1 ? o : 0), g.ny),
+                           wrap(z + (d == 2 ? o : 0), g.nz))];
+    if (!k.log_interp) return r;
+    return k.r0pos ? log1pf(r / k.r0) : logf(r);
+  };
+  return dens(s_dn(ls), k);
+}
 __global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int lb, int ub,
                              Geo g) {
   const int d = blockIdx.z;
@@ -1511,18 +1560,141 @@ __global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int l
   if (i >= m2 || kz >= g.nz) return;
   const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
   const int b = kz < lb ? lb : ub;
-  auto rho_face = [&](int z) {
-    auto ls = [&](int o) {
-      const float r = rd[lin(g, wrap(ix + (d == 0 ? o : 0), g.nx), wrap(jy + (d == 1 ? o : 0), g.ny),
-                             wrap(z + (d == 2 ? o : 0), g.nz))];
-      if (!k.log_interp) return r;
-      return k.r0pos ? log1pf(r / k.r0) : logf(r);
-    };
-    return dens(s_dn(ls), k);
-  };
   float* p = m.p[d];
-  const float u = fdiv(p[lin(g, ix, jy, b)] + k.pref[d], rho_face(b));
-  p[lin(g, ix, jy, kz)] = rho_face(kz) * u - k.pref[d];
+  const float u = fdiv(p[lin(g, ix, jy, b)] + k.pref[d], rho_face_at(rd, k, g, d, ix, jy, b));
+  p[lin(g, ix, jy, kz)] = rho_face_at(rd, k, g, d, ix, jy, kz) * u - k.pref[d];
 }
+
+// ------------------------------------- stellar-atmosphere z boundaries ----
+// Reading R26 (wall 3).  Physical centres klo..khi, z faces klo+1..khi; the
+// bottom plane obot (outward direction osb) is the end gravity points to,
+// the top otop (ost) the other.  G = klo ghost planes at each end.
+//
+// k_open_part: row j < G sums, over its plane, the density of the top ghost
+// plane otop + ost (j + 1) extrapolated linearly in ln rho from the top plane
+// and its inner neighbour; rows G and G + 1 sum the p_x and p_y deviations of
+// the bottom plane.  k_open_final divides by the plane size.
+__global__ void k_open_part(const float* __restrict__ rd, const float* __restrict__ px,
+                            const float* __restrict__ py, double* part, KPar k, Geo g) {
+  __shared__ double sm[256];
+  const int row = blockIdx.y, nb = gridDim.x, G = k.klo;
+  const long long m = (long long)g.nx * g.ny;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)nb * blockDim.x) {
+    if (row < G) {
+      const double lb_ = log((double)rd[(long long)k.otop * m + i] + k.r0);
+      const double li = log((double)rd[(long long)(k.otop - k.ost) * m + i] + k.r0);
+      acc += exp(lb_ + (row + 1) * (lb_ - li));
+    } else {
+      acc += (double)(row == G ? px : py)[(long long)k.obot * m + i];
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)row * nb + blockIdx.x] = sm[0];
+}
+__global__ void k_open_final(const double* part, int nb, int rows, double* mean, Geo g) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(long long)r * nb + b];
+  mean[r] = s / ((double)g.nx * g.ny);
+}
+
+// Ghost centre planes of rho and E: ln rho and e = E/rho extrapolated
+// linearly from the boundary plane b and its inner neighbour; at the top the
+// density limited to [orlo, orhi] times its plane mean (omean[j - 1]) and
+// e to [e_b / oefac, e_b oefac].  Planes 0..klo-1, then khi+1..nz-1.
+__global__ void k_open_fill_c(float* rd, float* Ed, KPar k, Geo g) {
+  const int lb = k.klo, ub = k.khi;
+  const int pl = blockIdx.y;
+  const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const bool low = kz < lb;
+  const int b = low ? lb : ub, s = low ? -1 : 1, j = low ? lb - kz : kz - ub;
+  const double rb = (double)rd[(long long)b * m2 + i] + k.r0;
+  const double ri = (double)rd[(long long)(b - s) * m2 + i] + k.r0;
+  const double eb = ((double)Ed[(long long)b * m2 + i] + k.E0) / rb;
+  const double ei = ((double)Ed[(long long)(b - s) * m2 + i] + k.E0) / ri;
+  const double lrb = log(rb);
+  double r = exp(lrb + j * (lrb - log(ri)));
+  double e = eb + j * (eb - ei);
+  if (b == k.otop) {
+    const double mj = k.omean[j - 1];
+    r = fmin(fmax(r, (double)k.orlo * mj), (double)k.orhi * mj);
+    e = fmin(fmax(e, eb / (double)k.oefac), eb * (double)k.oefac);
+  }
+  rd[(long long)kz * m2 + i] = (float)(r - k.r0);
+  Ed[(long long)kz * m2 + i] = (float)(r * e - k.E0);
+}
+
+// Ghost momenta and magnetic field, after k_open_fill_c: planes 0..klo (the
+// face klo is a ghost face, the centre klo physical), then khi+1..nz-1.
+// Bottom: p_x, p_y of centre 2b - kz, p_z of face 2b + 1 - kz (symmetric about
+// the boundary point).  Top: rho_d of the filled rho times the boundary
+// velocity limited to |u| <= oumax (p_x, p_y from plane b, p_z from the inside
+// face).  B_x, B_y extrapolated linearly from b and b - s, B_z from the two
+// inside faces; at the bottom B_x, B_y blended toward (oBx, oBy) by f =
+// 1/(1 + exp(U oinv_u)), U the outward velocity on the inside face.  Every
+// source is a physical plane (nz >= 3 klo + 2); rho is read only.
+__global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float* by,
+                              float* bz, const float* __restrict__ rd, KPar k, Geo g) {
+  const int lb = k.klo, ub = k.khi;
+  const int pl = blockIdx.y;
+  const int kz = pl <= lb ? pl : ub + 1 + (pl - lb - 1);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
+  const bool low = kz <= lb;
+  const int b = low ? lb : ub, s = low ? -1 : 1;
+  const int mi = low ? lb + 1 : ub;            // the inside face
+  const bool centre = low ? kz < lb : true;     // the face kz is a ghost in every case
+  const int j = low ? lb - kz : kz - ub;
+  const bool top = b == k.otop;
+  auto at = [&](int z) { return (long long)z * m2 + i; };
+  // outward velocity on the inside face
+  const float uzi = fdiv(pz[at(mi)] + k.pref[2], rho_face_at(rd, k, g, 2, ix, jy, mi));
+  if (!top) {
+    if (centre) {
+      px[at(kz)] = px[at(2 * b - kz)];
+      py[at(kz)] = py[at(2 * b - kz)];
+    }
+    pz[at(kz)] = pz[at(2 * b + 1 - kz)];
+  } else {
+    const float um = k.oumax;
+    if (centre) {
+      const float ux = fminf(fmaxf(fdiv(px[at(b)] + k.pref[0], rho_face_at(rd, k, g, 0, ix, jy, b)), -um), um);
+      const float uy = fminf(fmaxf(fdiv(py[at(b)] + k.pref[1], rho_face_at(rd, k, g, 1, ix, jy, b)), -um), um);
+      px[at(kz)] = rho_face_at(rd, k, g, 0, ix, jy, kz) * ux - k.pref[0];
+      py[at(kz)] = rho_face_at(rd, k, g, 1, ix, jy, kz) * uy - k.pref[1];
+    }
+    const float uz = fminf(fmaxf(uzi, -um), um);
+    pz[at(kz)] = rho_face_at(rd, k, g, 2, ix, jy, kz) * uz - k.pref[2];
+  }
+  // magnetic field (stored deviations; the reference cancels in the
+  // extrapolation, not in the blend)
+  const int d = low ? mi - kz : kz - mi;
+  bz[at(kz)] = bz[at(mi)] + (float)d * (bz[at(mi)] - bz[at(mi - s)]);
+  if (centre) {
+    float vx = bx[at(b)] + (float)j * (bx[at(b)] - bx[at(b - s)]);
+    float vy = by[at(b)] + (float)j * (by[at(b)] - by[at(b - s)]);
+    if (!top) {
+      const float f = 1.f / (1.f + expf((float)s * uzi * k.oinv_u));
+      vx = (1.f - f) * vx + f * (k.oBx - k.Bref[0]);
+      vy = (1.f - f) * vy + f * (k.oBy - k.Bref[1]);
+    }
+    bx[at(kz)] = vx;
+    by[at(kz)] = vy;
+  }
+}
+
 
 }  // namespace stg

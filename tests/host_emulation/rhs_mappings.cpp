@@ -152,6 +152,7 @@ static void rhs(const Geo& g, const KPar& kin, float* const* f, std::vector<std:
   di.gx = D[F_GX]; di.gy = D[F_GY]; di.gz = D[F_GZ]; di.qt = D[F_QT];
   di.Ex = D[F_EX]; di.Ey = D[F_EY]; di.Ez = D[F_EZ]; di.ls = ls;
   di.lq = D[F_LQ];
+  di.uz = D[F_UZ];
   for (int c = 0; c < 8; ++c) di.f[c] = f[c];
   double dtv = 0;
   launch<N>(g, [&] {

@@ -166,10 +166,75 @@ def test_rigid_box_keeps_a_balanced_atmosphere_at_rest(S, lnp):
     sim.close()
 
 
-def test_rigid_walls_refuse_the_op_graph(S):
+def test_rigid_walls_refuse_the_adjoint(S):
     fields, g, lb, ub = _state(S, (8, 8, 4))
     sim, refs, dev = _make(S, fields, g, {})
     with pytest.raises(S.StaggerError) as ei:
-        sim.rhs_unfused(dev)
+        sim.step_adjoint(dev, 1e-3, [torch.zeros_like(t) for t in dev])
     assert ei.value.status == S.EUNSUPPORTED
     sim.close()
+
+
+def test_rigid_op_graph_matches_oracle(S):
+    """stagger_rhs_unfused(_f64) and stagger_step_unfused_f64 with rigid walls:
+    the same ghost fill and zero ghost derivatives around the op graph; FP64
+    to 1e-10 of the term scale against the oracle, FP32 to the RHS tolerance."""
+    shape, kw = CASES["viscous_quench_gravity_36x9x12"]
+    fields, g, lb, ub = _state(S, shape, seed=6)
+    sim, refs, dev = _make(S, fields, g, kw)
+    po = oracle_params(kw)
+    f64 = [torch.tensor(a) for a in fields]
+    Fo = [t.numpy() for t in oracle.rhs_rigid(f64, g, po, lb, ub)]
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(fields, refs)]
+    F64 = [t.cpu().numpy() for t in sim.rhs_unfused_f64(d64)]
+    sc = scale_of(Fo)
+    for c in range(8):
+        assert float(np.abs(F64[c] - Fo[c]).max()) <= 1e-10 * sc[c], c
+        assert not F64[c][:lb].any() and not F64[c][ub + 1:].any(), c
+    Fo_, delta = _floor(fields, g, kw, refs, lb, ub)
+    F32 = [t.double().cpu().numpy() for t in sim.rhs_unfused(dev)]
+    for c in range(8):
+        assert float(np.abs(F32[c] - Fo[c]).max()) <= 2e-4 * sc[c] + K_FLOOR * delta[c], c
+    dt = 2e-3
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(fields, refs)]
+    sim.step_unfused_f64(d64, dt)
+    fo, _ = oracle.step_rigid(f64, g, po, lb, ub, dt=dt)
+    got = [t.cpu().numpy() + r for t, r in zip(d64, refs)]
+    for c in range(8):
+        ref = fo[c].numpy()
+        assert float(np.abs(got[c] - ref).max()) <= 1e-12 * max(1.0, float(np.abs(ref).max())), c
+    sim.close()
+
+
+def test_stratified_atmosphere_fp32_against_fp64_op_graph(S):
+    """The stratified atmosphere of the rigid-wall workload (two scale heights
+    here, 24^3 physical cells, velocity noise 1e-3), 20 Courant steps of the
+    FP32 fused path and of the FP64 op graph with the same dt, RM viscosity
+    and the quench.  The momentum derivative is the small residual of the
+    pressure gradient and gravity, each of size rho |g|, so FP32 rounding of
+    those terms sets the momentum error: judged on the sound-speed momentum
+    scale max(rho) c_s, the density and energy on their ranges, the field on
+    its largest magnitude; each within 1e-6."""
+    G = S.ZGHOST_MIN
+    w = inputs.stratified_atmosphere(24, 24, 24, zghost=G, lengths=(1.0, 1.0, 1.0), H=0.5)
+    kw = dict(VISC_KW, g=(0.0, 0.0, -2.0))
+    refs, d32 = S.split_state(w.fields)
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(w.fields, refs)]
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, zwalls=2, zghost=G, **kw))
+    for _ in range(20):
+        dt = sim.step(d32, None, want_dt=True)
+        sim.step_unfused_f64(d64, dt)
+    sim.close()
+    lb, ub = G, G + 23
+    a = [d32[c][lb:ub + 1].double().cpu().numpy() + refs[c] for c in range(8)]
+    b = [d64[c][lb:ub + 1].cpu().numpy() + refs[c] for c in range(8)]
+    rmax = float(b[0].max())
+    bmax = max(float(np.abs(b[c]).max()) for c in (5, 6, 7))
+    errs = []
+    for c in range(8):
+        e = float(np.abs(a[c] - b[c]).max())
+        sc = (float(b[c].max() - b[c].min()) if c in (0, 4) else rmax * 1.0 if c in (1, 2, 3)
+              else bmax)
+        errs.append(e / sc)
+    print("stratified 24^3 FP32 vs FP64 graph, 20 steps, err/scale:", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-6, errs

@@ -220,3 +220,34 @@ def orszag_tang_3d(n: int = 128, seed: int = 4, pert: float = 1e-3,
         w.fields[1 + d] = w.fields[1 + d] + rho0 * du[d]
     w.name = "orszag_tang_3d"
     return w
+
+
+def stratified_atmosphere(nx: int = 768, ny: int = 768, nz: int = 384, zghost: int = 14,
+                          lengths=(2.0, 2.0, 1.0), H: float = 0.125, noise: float = 1e-3,
+                          seed: int = 5, b0: float = 0.1, gamma: float = 5.0 / 3.0) -> Workload:
+    """Isothermal hydrostatic atmosphere for a box walled in z: P = rho (c_iso =
+    1), rho = exp(-z/H), which gravity g = 1/H along -z holds in balance,
+    E = P/(gamma - 1), B = (0, 0, b0), and Gaussian velocity noise of rms
+    ``noise`` per component (``numpy.random.default_rng(seed)``, independent
+    at every point).  The arrays hold the nz physical centre planes
+    z = (k + 1/2) h, k = 0..nz-1, and ``zghost`` planes beyond each end that
+    continue the atmosphere (at rest), so that the walls sit on the first and
+    last physical planes (indices zghost and zghost + nz - 1).  Each momentum
+    is rho at its own position times the velocity there.  ``physics`` carries
+    the gravity and the wall planes."""
+    Lx, Ly, Lz = lengths
+    h = (Lx / nx, Ly / ny, Lz / nz)
+    nzt = nz + 2 * zghost
+    kc = np.arange(nzt, dtype=np.float64) - zghost
+    zc = ((kc + 0.5) * h[2]).reshape(nzt, 1, 1)     # centres
+    zf = (kc * h[2]).reshape(nzt, 1, 1)              # lower z faces
+    ones = np.ones((nzt, ny, nx))
+    rc = np.exp(-zc / H) * ones
+    rf = np.exp(-zf / H) * ones
+    rng = np.random.default_rng(seed)
+    phys = ((kc >= 0) & (kc < nz)).reshape(nzt, 1, 1)
+    u = [noise * rng.standard_normal((nzt, ny, nx)) * phys for _ in range(3)]
+    fields = [rc, rc * u[0], rc * u[1], rf * u[2], rc / (gamma - 1.0),
+              np.zeros((nzt, ny, nx)), np.zeros((nzt, ny, nx)), np.full((nzt, ny, nx), b0)]
+    return Workload("stratified_atmosphere", (nx, ny, nzt), h, fields,
+                    dict(gamma=gamma, g=(0.0, 0.0, -1.0 / H), zghost=zghost))
