@@ -450,8 +450,9 @@ def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
     (1) FP32 at `size`, zone-updates/s of the physical cells over the steps
     alone and FP64 totals every `every` steps, with rigid walls and (1b) with
     the stellar-atmosphere boundaries (reading R26); (2) FP32 against the FP64
-    op graph at half the resolution with rigid walls, the same dt every step,
-    the error of each field on the physical planes after the steps."""
+    op graph at half the resolution with the stellar-atmosphere boundaries,
+    the same dt every step, the error of each field on the physical planes
+    after the steps."""
     import numpy as np
     import workloads as inputs
     G = S.ZGHOST_MIN
@@ -516,14 +517,17 @@ def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
         "max_div_b": max(d[7] for d in olog), "nonfinite": max(d[9] for d in olog)}
     del dev
     torch.cuda.empty_cache()
-    # (2) half resolution: FP32 fused path against the FP64 op graph
+    # (2) half resolution, stellar-atmosphere boundaries: FP32 fused path
+    # against the FP64 op graph
     half = (size[0] // 2, size[1] // 2, size[2] // 2)
     w = inputs.stratified_atmosphere(*half, zghost=G)
+    rb, Eb = float(w.fields[0][G, 0, 0]), float(w.fields[4][G, 0, 0])
     refs, d32 = S.split_state(w.fields)
     d64 = [torch.tensor(a - r, dtype=torch.float64).cuda() for a, r in zip(w.fields, refs)]
     shape, spacing = w.shape, w.spacing
     del w
-    sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **phys))
+    popen = dict(PHYS, zwalls=3, zghost=G, bdry_t=0.1, bdry_rho=rb, bdry_E=Eb, bdry_u=1e-3)
+    sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **popen))
     t0 = time.perf_counter()
     for _ in range(steps):
         dt = sim.step(d32, None, want_dt=True)

@@ -219,8 +219,10 @@ typedef struct {
    * top_rho_lo <= 1 <= top_rho_hi, top_e_fac >= 1, nz >= 3 zghost + 2 (the
    * mirrored bottom momenta come from physical planes), fuse_flux_div 0 and
    * the conditions of the closed walls but the ref[] one, else
-   * STAGGER_EINVAL.  The op-graph entries and stagger_diagnostics_noalloc
-   * return STAGGER_EUNSUPPORTED. */
+   * STAGGER_EINVAL.  stagger_rhs_unfused, stagger_rhs_unfused_f64 and
+   * stagger_step_unfused_f64 apply the same fill and rates around the op
+   * graph; the adjoint entries and stagger_diagnostics_noalloc return
+   * STAGGER_EUNSUPPORTED. */
   double bdry_t, bdry_rho, bdry_E, bdry_u;
   double bdry_B[3];
   double top_rho_lo, top_rho_hi, top_e_fac, top_umax;

@@ -28,6 +28,7 @@ struct stagger_ctx {
   long long adj_launches[2] = {0, 0};
   cudaStream_t cap = nullptr;
   double* dtp = nullptr;   // the step dt on the device (read by the captured graph)
+  double* omean_g = nullptr;  // plane means and parts of the op graph's open boundaries
 };
 
 namespace stg {
@@ -174,6 +175,7 @@ int stagger_destroy(stagger_ctx* c) {
     if (c->adj_exec[i]) cudaGraphExecDestroy(c->adj_exec[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->dtp) cudaFree(c->dtp);
+  if (c->omean_g) cudaFree(c->omean_g);
   delete c;
   return e == cudaSuccess ? STAGGER_OK : STAGGER_ECUDA;
 }
@@ -376,6 +378,249 @@ static void rigid_zero_g(stagger_ctx* c, T* o, cudaStream_t s) {
   ++c->extra_launches;
 }
 
+// Stellar-atmosphere z boundaries (reading R26) around the op graph: the same
+// ghost fill and boundary-plane rates as the fused path, in the graph's
+// precision (see stagger_params.zwalls).
+template <typename T>
+struct OpenG {
+  T* f[8];                       // the state (deviations)
+  double ref[8];
+  int lb, ub, bot, top, sb, st, log_interp;
+  double inv_t, rho_b, E_b, inv_u, Bb[2], rlo, rhi, efac, umax, gabs, gamma, gm1, ihz;
+  const double* mean;            // G top-ghost densities, then the p_x, p_y plane means
+};
+template <typename T>
+__device__ double open_rho_face(const OpenG<T>& a, const Geo& g, int d, int ix, int jy, int z) {
+  auto ls = [&](int o) {
+    const double r = (double)a.f[0][lin(g, wrap(ix + (d == 0 ? o : 0), g.nx),
+                                       wrap(jy + (d == 1 ? o : 0), g.ny),
+                                       wrap(z + (d == 2 ? o : 0), g.nz))];
+    if (!a.log_interp) return r;
+    return a.ref[0] > 0 ? log1p(r / a.ref[0]) : log(r + a.ref[0]);
+  };
+  const double v = (75.0 / 128.0) * (ls(-1) + ls(0)) + (-25.0 / 256.0) * (ls(-2) + ls(1)) +
+                   (3.0 / 256.0) * (ls(-3) + ls(2));
+  if (!a.log_interp) return v + a.ref[0];
+  return a.ref[0] > 0 ? a.ref[0] * exp(v) : exp(v);
+}
+template <typename T>
+__global__ void k_open_part_g(OpenG<T> a, double* part, Geo g) {
+  __shared__ double sm[256];
+  const int row = blockIdx.y, nb = gridDim.x, G = a.lb;
+  const long long m = (long long)g.nx * g.ny;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)nb * blockDim.x) {
+    if (row < G) {
+      const double lb_ = log((double)a.f[0][(long long)a.top * m + i] + a.ref[0]);
+      const double li = log((double)a.f[0][(long long)(a.top - a.st) * m + i] + a.ref[0]);
+      acc += exp(lb_ + (row + 1) * (lb_ - li));
+    } else {
+      acc += (double)a.f[row == G ? 1 : 2][(long long)a.bot * m + i];
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)row * nb + blockIdx.x] = sm[0];
+}
+__global__ void k_open_final_g(const double* part, int nb, int rows, double* mean, Geo g) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(long long)r * nb + b];
+  mean[r] = s / ((double)g.nx * g.ny);
+}
+// rho and E of the ghost centre planes (0..lb-1, then ub+1..nz-1).
+template <typename T>
+__global__ void k_open_fill_c_g(OpenG<T> a, Geo g) {
+  const int lb = a.lb, ub = a.ub, pl = blockIdx.y;
+  const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const bool low = kz < lb;
+  const int b = low ? lb : ub, s = low ? -1 : 1, j = low ? lb - kz : kz - ub;
+  T* rd = a.f[0];
+  T* Ed = a.f[4];
+  const double rb = (double)rd[(long long)b * m2 + i] + a.ref[0];
+  const double ri = (double)rd[(long long)(b - s) * m2 + i] + a.ref[0];
+  const double eb = ((double)Ed[(long long)b * m2 + i] + a.ref[4]) / rb;
+  const double ei = ((double)Ed[(long long)(b - s) * m2 + i] + a.ref[4]) / ri;
+  const double lrb = log(rb);
+  double r = exp(lrb + j * (lrb - log(ri)));
+  double e = eb + j * (eb - ei);
+  if (b == a.top) {
+    const double mj = a.mean[j - 1];
+    r = fmin(fmax(r, a.rlo * mj), a.rhi * mj);
+    e = fmin(fmax(e, eb / a.efac), eb * a.efac);
+  }
+  rd[(long long)kz * m2 + i] = (T)(r - a.ref[0]);
+  Ed[(long long)kz * m2 + i] = (T)(r * e - a.ref[4]);
+}
+// Momenta and field of the ghost planes (0..lb, then ub+1..nz-1).
+template <typename T>
+__global__ void k_open_fill_m_g(OpenG<T> a, Geo g) {
+  const int lb = a.lb, ub = a.ub, pl = blockIdx.y;
+  const int kz = pl <= lb ? pl : ub + 1 + (pl - lb - 1);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
+  const bool low = kz <= lb;
+  const int b = low ? lb : ub, s = low ? -1 : 1, mi = low ? lb + 1 : ub;
+  const bool centre = low ? kz < lb : true;
+  const int j = low ? lb - kz : kz - ub;
+  const bool top = b == a.top;
+  auto at = [&](int z) { return (long long)z * m2 + i; };
+  T *px = a.f[1], *py = a.f[2], *pz = a.f[3], *bx = a.f[5], *by = a.f[6], *bz = a.f[7];
+  const double uzi = ((double)pz[at(mi)] + a.ref[3]) / open_rho_face(a, g, 2, ix, jy, mi);
+  if (!top) {
+    if (centre) {
+      px[at(kz)] = px[at(2 * b - kz)];
+      py[at(kz)] = py[at(2 * b - kz)];
+    }
+    pz[at(kz)] = pz[at(2 * b + 1 - kz)];
+  } else {
+    const double um = a.umax;
+    if (centre) {
+      const double ux = fmin(fmax(((double)px[at(b)] + a.ref[1]) / open_rho_face(a, g, 0, ix, jy, b), -um), um);
+      const double uy = fmin(fmax(((double)py[at(b)] + a.ref[2]) / open_rho_face(a, g, 1, ix, jy, b), -um), um);
+      px[at(kz)] = (T)(open_rho_face(a, g, 0, ix, jy, kz) * ux - a.ref[1]);
+      py[at(kz)] = (T)(open_rho_face(a, g, 1, ix, jy, kz) * uy - a.ref[2]);
+    }
+    const double uz = fmin(fmax(uzi, -um), um);
+    pz[at(kz)] = (T)(open_rho_face(a, g, 2, ix, jy, kz) * uz - a.ref[3]);
+  }
+  const int d = low ? mi - kz : kz - mi;
+  bz[at(kz)] = (T)((double)bz[at(mi)] + d * ((double)bz[at(mi)] - (double)bz[at(mi - s)]));
+  if (centre) {
+    double vx = (double)bx[at(b)] + j * ((double)bx[at(b)] - (double)bx[at(b - s)]);
+    double vy = (double)by[at(b)] + j * ((double)by[at(b)] - (double)by[at(b - s)]);
+    if (!top) {
+      const double f = 1.0 / (1.0 + exp(s * uzi * a.inv_u));
+      vx = (1.0 - f) * vx + f * (a.Bb[0] - a.ref[5]);
+      vy = (1.0 - f) * vy + f * (a.Bb[1] - a.ref[6]);
+    }
+    bx[at(kz)] = (T)vx;
+    by[at(kz)] = (T)vy;
+  }
+}
+// The boundary-plane rates on the graph's derivatives F (state filled), and
+// zero derivatives on the ghost planes (centres outside lb..ub, z faces
+// outside lb+1..ub).
+template <typename T>
+__global__ void k_open_rates_g(OpenG<T> a, T* F0, T* F1, T* F2, T* F4, Geo g) {
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2) return;
+  const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
+  auto at = [&](int z) { return (long long)z * m2 + i; };
+  const T *rd = a.f[0], *Ed = a.f[4], *pz = a.f[3];
+  {  // bottom, eqs. (rein), (constS) to (addderiv)
+    const int b = a.bot, mi = a.sb < 0 ? b + 1 : b;
+    const double r = (double)rd[at(b)] + a.ref[0], E = (double)Ed[at(b)] + a.ref[4];
+    const double ui = ((double)pz[at(mi)] + a.ref[3]) / open_rho_face(a, g, 2, ix, jy, mi);
+    const double f = 1.0 / (1.0 + exp(a.sb * ui * a.inv_u));
+    const double dE = (a.E_b - E) * a.inv_t;
+    const double Fm = (double)F0[at(b)], Fe = (double)F4[at(b)];
+    F0[at(b)] = (T)(f * (a.rho_b - r) * a.inv_t + (1.0 - f) * (Fm + (dE - Fe) * r / (a.gamma * E)));
+    F4[at(b)] = (T)dE;
+    F1[at(b)] = (T)((double)F1[at(b)] - f * ((double)a.f[1][at(b)] - a.mean[a.lb]) * a.inv_t);
+    F2[at(b)] = (T)((double)F2[at(b)] - f * ((double)a.f[2][at(b)] - a.mean[a.lb + 1]) * a.inv_t);
+  }
+  {  // top, eq. (rbdrylo)
+    const int t = a.top;
+    const double r = (double)rd[at(t)] + a.ref[0], E = (double)Ed[at(t)] + a.ref[4];
+    const double HP = a.gm1 * (E / r) / a.gabs;
+    auto p = [&](int o) { return (double)pz[lin(g, ix, jy, wrap(t + o, g.nz))] + a.ref[3]; };
+    const double du = ((225.0 / 192.0) * (p(1) - p(0)) + (-25.0 / 384.0) * (p(2) - p(-1)) +
+                       (3.0 / 640.0) * (p(3) - p(-2))) * a.ihz;
+    const double upz = (75.0 / 128.0) * (p(0) + p(1)) + (-25.0 / 256.0) * (p(-1) + p(2)) +
+                       (3.0 / 256.0) * (p(-2) + p(3));
+    F0[at(t)] = (T)((double)F0[at(t)] + du + a.st * upz / HP);
+  }
+}
+template <typename T>
+__global__ void k_open_zero_g(T* o, int face, int lb, int ub, Geo g) {
+  const int pl = blockIdx.y;                   // planes 0..lb, then ub+1..nz-1
+  const int kz = pl <= lb ? pl : ub + 1 + (pl - lb - 1);
+  const long long m2 = (long long)g.nx * g.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2 || kz >= g.nz) return;
+  if (kz == lb && !face) return;               // the centre plane lb is physical
+  o[(long long)kz * m2 + i] = T(0);
+}
+
+template <typename T>
+static OpenG<T> open_args(stagger_ctx* c, T* const f[8]) {
+  const stagger_params& p = c->params;
+  const Geo& g = c->geo;
+  OpenG<T> a;
+  for (int k = 0; k < 8; ++k) {
+    a.f[k] = f[k];
+    a.ref[k] = p.ref[k];
+  }
+  a.lb = p.zghost;
+  a.ub = g.nz - 1 - p.zghost;
+  a.bot = p.g[2] < 0 ? a.lb : a.ub;
+  a.top = p.g[2] < 0 ? a.ub : a.lb;
+  a.sb = p.g[2] < 0 ? -1 : 1;
+  a.st = -a.sb;
+  a.log_interp = p.log_interp;
+  a.inv_t = 1.0 / p.bdry_t;
+  a.rho_b = p.bdry_rho;
+  a.E_b = p.bdry_E;
+  a.inv_u = 1.0 / p.bdry_u;
+  a.Bb[0] = p.bdry_B[0];
+  a.Bb[1] = p.bdry_B[1];
+  a.rlo = p.top_rho_lo;
+  a.rhi = p.top_rho_hi;
+  a.efac = p.top_e_fac;
+  a.umax = p.top_umax;
+  a.gabs = fabs(p.g[2]);
+  a.gamma = p.gamma;
+  a.gm1 = p.gamma - 1.0;
+  a.ihz = 1.0 / c->grid.dz;
+  a.mean = c->omean_g;
+  return a;
+}
+template <typename T>
+static int open_fill_g(stagger_ctx* c, T* const f[8], cudaStream_t s) {
+  const Geo& g = c->geo;
+  const int G = c->params.zghost, rows = G + 2;
+  const int nb = (int)std::max(1LL, std::min(64LL, ((long long)g.nx * g.ny + 1023) / 1024));
+  if (!c->omean_g &&
+      cudaMalloc(&c->omean_g, sizeof(double) * (size_t)rows * (1 + nb)) != cudaSuccess) {
+    c->omean_g = nullptr;
+    return STAGGER_EOOM;
+  }
+  OpenG<T> a = open_args<T>(c, f);
+  const unsigned bx = (unsigned)((g.sz + 255) / 256);
+  k_open_part_g<T><<<dim3(nb, rows), 256, 0, s>>>(a, c->omean_g + rows, g);
+  k_open_final_g<<<(rows + 63) / 64, 64, 0, s>>>(c->omean_g + rows, nb, rows, c->omean_g, g);
+  k_open_fill_c_g<T><<<dim3(bx, 2 * G), 256, 0, s>>>(a, g);
+  k_open_fill_m_g<T><<<dim3(bx, 2 * G + 1), 256, 0, s>>>(a, g);
+  c->extra_launches += 4;
+  STG_CUDA_OK(cudaGetLastError());
+  return STAGGER_OK;
+}
+// After the graph's forward on the filled state f: the boundary-plane rates
+// on its outputs and zero ghost derivatives.
+template <typename T>
+static void open_rates_g(stagger_ctx* c, T* const f[8], T* const F[8], cudaStream_t s) {
+  const Geo& g = c->geo;
+  OpenG<T> a = open_args<T>(c, f);
+  k_open_rates_g<T><<<(unsigned)((g.sz + 255) / 256), 256, 0, s>>>(a, F[0], F[1], F[2], F[4], g);
+  const dim3 gr((unsigned)((g.sz + 255) / 256), (unsigned)(2 * c->params.zghost + 1));
+  for (int k = 0; k < 8; ++k)
+    k_open_zero_g<T><<<gr, 256, 0, s>>>(F[k], k == 3 || k == 7, a.lb, a.ub, g);
+  c->extra_launches += 9;
+}
+
 template <typename T> GraphExec<T>*& graph_of(stagger_ctx* c);
 template <> GraphExec<float>*& graph_of<float>(stagger_ctx* c) { return c->g32; }
 template <> GraphExec<double>*& graph_of<double>(stagger_ctx* c) { return c->g64; }
@@ -426,8 +671,9 @@ static int graph_rhs(stagger_ctx* c, T* const f[8], T* out[8], cudaStream_t s) {
   int rc = ensure_graph<T>(c, false);
   if (rc) return rc;
   GraphExec<T>* G = graph_of<T>(c);
-  const bool rigid = c->params.zwalls == 2;
+  const bool rigid = c->params.zwalls == 2, open = c->params.zwalls == 3;
   if (rigid) rigid_fill_g<T>(c, f, s);
+  if (open && (rc = open_fill_g<T>(c, f, s))) return rc;
   rc = G->forward(f, s);
   if (rc) return rc;
   long long n = c->geo.n;
@@ -436,6 +682,7 @@ static int graph_rhs(stagger_ctx* c, T* const f[8], T* out[8], cudaStream_t s) {
     ++c->extra_launches;
     if (rigid) rigid_zero_g<T>(c, out[k], s);
   }
+  if (open) open_rates_g<T>(c, f, out, s);
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -452,11 +699,17 @@ static int graph_step(stagger_ctx* c, T* f[8], double dt, cudaStream_t s) {
   const long long n = c->geo.n;
   T* q[8];
   for (int k = 0; k < 8; ++k) q[k] = w + (size_t)k * n;
-  const bool rigid = c->params.zwalls == 2;
+  const bool rigid = c->params.zwalls == 2, open = c->params.zwalls == 3;
   for (int st = 0; st < 3; ++st) {
     if (rigid) rigid_fill_g<T>(c, f, s);
+    if (open && (rc = open_fill_g<T>(c, f, s))) return rc;
     rc = G->forward(f, s);
     if (rc) return rc;
+    if (open) {
+      T* Fo[8];
+      for (int k = 0; k < 8; ++k) Fo[k] = G->output(k);
+      open_rates_g<T>(c, f, Fo, s);
+    }
     for (int k = 0; k < 8; ++k) {
       if (rigid) rigid_zero_g<T>(c, G->output(k), s);
       if (st == 0) lin2<T>(c, q[k], G->output(k), 1.0, G->output(k), 0.0, s);
@@ -465,6 +718,7 @@ static int graph_step(stagger_ctx* c, T* f[8], double dt, cudaStream_t s) {
     }
   }
   if (rigid) rigid_fill_g<T>(c, f, s);
+  if (open && (rc = open_fill_g<T>(c, f, s))) return rc;
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -614,20 +868,20 @@ int stagger_step_adjoint(stagger_ctx* c, float* const state_n[8], double dt,
 
 int stagger_rhs_unfused(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
-  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
+  if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
   return graph_rhs<float>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_rhs_unfused_f64(stagger_ctx* c, double* const state[8], double* dfdt[8],
                             void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
-  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
+  if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
   return graph_rhs<double>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_step_unfused_f64(stagger_ctx* c, double* state[8], double dt, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !(dt > 0)) return STAGGER_EINVAL;
-  if (c->params.zwalls == 1 || c->params.zwalls == 3) return STAGGER_EUNSUPPORTED;
+  if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
   return graph_step<double>(c, state, dt, (cudaStream_t)stream);
 }
 

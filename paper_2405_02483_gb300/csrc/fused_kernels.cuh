@@ -1131,7 +1131,8 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   // plane's column, from the outward velocity on its inside z face.
   const bool obot = k.wall == 3 && n.kz == k.obot;
   auto open_f = [&]() {
-    const T ui = n.lda(in.uz, 2, k.osb < 0 ? 1 : 0);
+    // constant offsets: a run-time one would put the cell's index tables in local memory
+    const T ui = k.osb < 0 ? n.lda(in.uz, 2, 1) : n.lda(in.uz, 2, 0);
     return 1.f / (1.f + expf(ui * ((float)k.osb * k.oinv_u)));
   };
   T Fm = 0.f, Fe = 0.f;

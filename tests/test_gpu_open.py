@@ -178,10 +178,42 @@ def test_open_boundaries_keep_a_balanced_atmosphere_at_rest(S):
     sim.close()
 
 
-def test_open_refuses_the_op_graph(S):
+@pytest.mark.parametrize("name", ["viscous_quench_gravity_down_24x9x18", "const_nu_gravity_up_13x8x16"])
+def test_open_op_graph_matches_oracle(S, name):
+    """stagger_rhs_unfused(_f64) and stagger_step_unfused_f64 with the
+    stellar-atmosphere boundaries (the same fill and rates around the op
+    graph): FP64 to 1e-10 of the term scale and one FP64 step to 1e-12
+    against the oracle; FP32 to the RHS tolerance."""
+    shape, kw = CASES[name]
+    fields, g, lb, ub = _state(shape, seed=6)
+    sim, refs, dev = _make(S, fields, g, kw)
+    po = oracle_params(_kw(kw))
+    f64 = [torch.tensor(a) for a in fields]
+    Fo, delta = _floor(fields, g, kw, refs, lb, ub)
+    sc = scale_of(Fo)
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(fields, refs)]
+    F64 = [t.cpu().numpy() for t in sim.rhs_unfused_f64(d64)]
+    for c in range(8):
+        assert float(np.abs(F64[c] - Fo[c]).max()) <= 1e-10 * sc[c], (c, float(np.abs(F64[c] - Fo[c]).max()) / sc[c])
+    F32 = [t.double().cpu().numpy() for t in sim.rhs_unfused(dev)]
+    for c in range(8):
+        assert float(np.abs(F32[c] - Fo[c]).max()) <= 2e-4 * sc[c] + K_FLOOR * delta[c], c
+    dt = 2e-3
+    d64 = [torch.tensor(a - r).cuda() for a, r in zip(fields, refs)]
+    sim.step_unfused_f64(d64, dt)
+    fo, _ = oracle.step_open(f64, g, po, lb, ub, dt=dt)
+    got = [t.cpu().numpy() + r for t, r in zip(d64, refs)]
+    for c in range(8):
+        ref = fo[c].numpy()
+        err = float(np.abs(got[c] - ref).max())
+        assert err <= 1e-12 * max(1.0, float(np.abs(ref).max())), (c, err)
+    sim.close()
+
+
+def test_open_refuses_the_adjoint(S):
     fields, g, lb, ub = _state((8, 8, 16))
     sim, refs, dev = _make(S, fields, g, dict(g=(0.0, 0.0, -1.0)))
     with pytest.raises(S.StaggerError) as ei:
-        sim.rhs_unfused(dev)
+        sim.step_adjoint(dev, 1e-3, [torch.zeros_like(t) for t in dev])
     assert ei.value.status == S.EUNSUPPORTED
     sim.close()
