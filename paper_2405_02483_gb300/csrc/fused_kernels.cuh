@@ -1575,6 +1575,18 @@ __global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int l
 // plane otop + ost (j + 1) extrapolated linearly in ln rho from the top plane
 // and its inner neighbour; rows G and G + 1 sum the p_x and p_y deviations of
 // the bottom plane.  k_open_final divides by the plane size.
+// ln(rho/r0) (ln rho when r0 = 0) and e - e0 of a cell as k_lr_ed forms them,
+// and the density deviation of an extrapolated ln(rho/r0).  FP32 throughout:
+// FP64 transcendentals run at a small fraction of the FP32 rate.
+__device__ __forceinline__ float open_lnr(float rdv, const KPar& k) {
+  return k.r0pos ? log1pf(rdv / k.r0) : logf(rdv);
+}
+__device__ __forceinline__ float open_ed(float rdv, float Edv, const KPar& k) {
+  return fdiv((Edv + k.Ec) - k.e0 * rdv, rdv + k.r0);
+}
+__device__ __forceinline__ float open_rdev(float l, const KPar& k) {
+  return k.r0pos ? k.r0 * expm1f(l) : expf(l);
+}
 __global__ void k_open_part(const float* __restrict__ rd, const float* __restrict__ px,
                             const float* __restrict__ py, double* part, KPar k, Geo g) {
   __shared__ double sm[256];
@@ -1584,9 +1596,9 @@ __global__ void k_open_part(const float* __restrict__ rd, const float* __restric
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)nb * blockDim.x) {
     if (row < G) {
-      const double lb_ = log((double)rd[(long long)k.otop * m + i] + k.r0);
-      const double li = log((double)rd[(long long)(k.otop - k.ost) * m + i] + k.r0);
-      acc += exp(lb_ + (row + 1) * (lb_ - li));
+      const float lb_ = open_lnr(rd[(long long)k.otop * m + i], k);
+      const float li = open_lnr(rd[(long long)(k.otop - k.ost) * m + i], k);
+      acc += (double)(open_rdev(lb_ + (float)(row + 1) * (lb_ - li), k) + k.r0);
     } else {
       acc += (double)(row == G ? px : py)[(long long)k.obot * m + i];
     }
@@ -1620,20 +1632,24 @@ __global__ void k_open_fill_c(float* rd, float* Ed, KPar k, Geo g) {
   if (i >= m2 || kz >= g.nz) return;
   const bool low = kz < lb;
   const int b = low ? lb : ub, s = low ? -1 : 1, j = low ? lb - kz : kz - ub;
-  const double rb = (double)rd[(long long)b * m2 + i] + k.r0;
-  const double ri = (double)rd[(long long)(b - s) * m2 + i] + k.r0;
-  const double eb = ((double)Ed[(long long)b * m2 + i] + k.E0) / rb;
-  const double ei = ((double)Ed[(long long)(b - s) * m2 + i] + k.E0) / ri;
-  const double lrb = log(rb);
-  double r = exp(lrb + j * (lrb - log(ri)));
-  double e = eb + j * (eb - ei);
+  const float rb = rd[(long long)b * m2 + i], ri = rd[(long long)(b - s) * m2 + i];
+  const float eb = open_ed(rb, Ed[(long long)b * m2 + i], k);
+  const float ei = open_ed(ri, Ed[(long long)(b - s) * m2 + i], k);
+  const float lb_ = open_lnr(rb, k);
+  float r = open_rdev(lb_ + (float)j * (lb_ - open_lnr(ri, k)), k);   // deviation
+  float e = eb + (float)j * (eb - ei);                                  // e - e0
   if (b == k.otop) {
-    const double mj = k.omean[j - 1];
-    r = fmin(fmax(r, (double)k.orlo * mj), (double)k.orhi * mj);
-    e = fmin(fmax(e, eb / (double)k.oefac), eb * (double)k.oefac);
+    const float mj = (float)k.omean[j - 1];
+    const float rf = r + k.r0;
+    if (rf < k.orlo * mj) r = k.orlo * mj - k.r0;
+    if (rf > k.orhi * mj) r = k.orhi * mj - k.r0;
+    const float ef = e + k.e0, ebf = eb + k.e0;
+    if (ef < ebf / k.oefac) e = ebf / k.oefac - k.e0;
+    if (ef > ebf * k.oefac) e = ebf * k.oefac - k.e0;
   }
-  rd[(long long)kz * m2 + i] = (float)(r - k.r0);
-  Ed[(long long)kz * m2 + i] = (float)(r * e - k.E0);
+  rd[(long long)kz * m2 + i] = r;
+  // E' = rho (e0 + e') + ... = r' (e0 + e') + r0 e' - Ec
+  Ed[(long long)kz * m2 + i] = r * (k.e0 + e) + k.r0 * e - k.Ec;
 }
 
 // Ghost momenta and magnetic field, after k_open_fill_c: planes 0..klo (the
