@@ -202,7 +202,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.ediffav = p.ediffav && k.visc ? 1 : 0;
   k.lnpa = p.lnp_aver ? 1 : 0;
   k.Emean = nullptr;
-  k.pa = k.paz = k.dpaz = nullptr;
+  k.pa = k.paz = k.dpaz = k.qm = k.qden = nullptr;
   k.wall = p.zwalls;
   k.klo = p.zwalls ? p.zghost : 0;
   k.khi = p.zwalls ? gr.nz - 1 - p.zghost : gr.nz - 1;
@@ -245,9 +245,9 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.plane_nb = (int)std::max(1LL, std::min(64LL, ((long long)gr.nx * gr.ny + 1023) / 1024));
   if (k.lnpa) {
     // ln(P/P_aver): the plane means of E - E0 and their per-block parts, then
-    // P_aver, exp(dn_z ln P_aver) and dddn_z ln P_aver as 3 nz floats.
+    // P_aver, exp(dn_z ln P_aver), dddn_z ln P_aver, <E'> and E0 + <E'> as 5 nz floats.
     const size_t nd = (size_t)gr.nz * (1 + F.plane_nb);
-    if (cudaMalloc(&F.pplane, sizeof(double) * nd + sizeof(float) * 3 * (size_t)gr.nz) !=
+    if (cudaMalloc(&F.pplane, sizeof(double) * nd + sizeof(float) * 5 * (size_t)gr.nz) !=
         cudaSuccess) {
       F.pplane = nullptr;
       fused_release(F);
@@ -257,6 +257,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
     k.pa = reinterpret_cast<const float*>(F.pplane + nd);
     k.paz = k.pa + gr.nz;
     k.dpaz = k.pa + 2 * gr.nz;
+    k.qm = k.pa + 3 * gr.nz;
+    k.qden = k.pa + 4 * gr.nz;
   }
   if (F.wall == 3) {
     // Stellar-atmosphere boundaries: zghost + 2 plane means, then their parts.
@@ -412,7 +414,9 @@ static int pre_div_t(Fused& F, float* const f[8], cudaStream_t s, bool cfl) {
     TIMED(K_PLANE, (k_lnpa_tab<<<1, 256, 0, s>>>(F.pplane + g.nz, F.plane_nb, F.pplane,
                                                  const_cast<float*>(k.pa),
                                                  const_cast<float*>(k.paz),
-                                                 const_cast<float*>(k.dpaz), k, g)));
+                                                 const_cast<float*>(k.dpaz),
+                                                 const_cast<float*>(k.qm),
+                                                 const_cast<float*>(k.qden), k, g)));
   }
   TIMED(K_LR, (k_lr_ed<NB><<<nb1(g.n / N::W), 256, 0, s>>>(f[0], f[4], k.log_interp ? d[F_LR] : nullptr,
                                                        d[F_ED], k.ediffav ? d[F_LER] : nullptr,

@@ -49,6 +49,7 @@ struct KPar {
   int lnpa;
   const double* Emean;
   const float *pa, *paz, *dpaz;
+  const float *qm, *qden;   // <E'> and E0 + <E'> per plane, for ln(P/P_aver) in k_lr_ed
   // Stellar-atmosphere z boundaries (R26, wall 3): the bottom and top boundary
   // planes and their outward index directions, 1/bdry_t, the bottom targets,
   // 1/bdry_u, B_bdry (x, y), the top limits, |g_z|, and the plane means: the

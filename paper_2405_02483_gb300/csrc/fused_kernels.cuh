@@ -360,8 +360,8 @@ __global__ void k_lr_ed(const float* __restrict__ rd, const float* __restrict__ 
     N::stp(ler + i, log1pf((e - m) / (k.e0 + m)));
   }
   if (lq) {   // ln(P / P_aver) = ln(E / <E>_h) = log1p((E' - <E'>_h) / (E0 + <E'>_h))
-    const double m = k.Emean[i / sz];
-    N::stp(lq + i, log1pf((Ev - (float)m) / (float)((double)k.E0 + m)));
+    const long long kz = i / sz;
+    N::stp(lq + i, log1pf((Ev - __ldg(k.qm + kz)) / __ldg(k.qden + kz)));
   }
 }
 
@@ -1288,9 +1288,10 @@ __global__ void k_plane_final(const double* part, int nb, double* mean, Geo g) {
 // ln(P/P_aver), eq. (pressure): one block.  The plane means of E - E0 from
 // their nb parts, then per plane k (z periodic over the arrays) P_aver(k) =
 // (gamma - 1)(E0 + <E'>_k), and at its lower z face exp(dn_z ln P_aver) and
-// dddn_z ln P_aver (eqs. (interp), (deriv) on the nz values of ln P_aver).
+// dddn_z ln P_aver (eqs. (interp), (deriv) on the nz values of ln P_aver);
+// <E'>_k and E0 + <E'>_k as floats for the log ratio of k_lr_ed.
 __global__ void k_lnpa_tab(const double* part, int nb, double* mean, float* pa, float* paz,
-                           float* dpaz, KPar k, Geo g) {
+                           float* dpaz, float* qm, float* qden, KPar k, Geo g) {
   const int nz = g.nz;
   for (int kz = threadIdx.x; kz < nz; kz += blockDim.x) {
     double s = 0.0;
@@ -1305,6 +1306,8 @@ __global__ void k_lnpa_tab(const double* part, int nb, double* mean, float* pa, 
   for (int kz = threadIdx.x; kz < nz; kz += blockDim.x) {
     const double l[6] = {lpa(kz - 3), lpa(kz - 2), lpa(kz - 1), lpa(kz), lpa(kz + 1), lpa(kz + 2)};
     pa[kz] = (float)exp(l[3]);
+    qm[kz] = (float)mean[kz];
+    qden[kz] = (float)(E0 + mean[kz]);
     paz[kz] = (float)exp(a1 * (l[2] + l[3]) + b1 * (l[1] + l[4]) + c1 * (l[0] + l[5]));
     const double jf = k.jzf ? (double)k.jzf[kz] : (double)k.ih[2];
     dpaz[kz] = (float)((a2 * (l[3] - l[2]) + b2 * (l[4] - l[1]) + c2 * (l[5] - l[0])) * jf);
