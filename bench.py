@@ -245,6 +245,7 @@ def main():
                          "for 200 FP32 steps, and 384^2 x 192 FP32 against the FP64 op graph")
     ap.add_argument("--stratified-size", type=int, nargs=3, default=[768, 768, 384],
                     metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--stratified-steps", type=int, default=200)
     ap.add_argument("--scalar-cells", action="store_true",
                     help="one cell per thread in the fused kernels (default: four x-cells)")
     args = ap.parse_args()
@@ -368,7 +369,9 @@ def main():
     del dev
     torch.cuda.empty_cache()
     if rank == 0 and args.stratified:
-        out["stratified_atmosphere"] = stratified_atmosphere(S, torch, tuple(args.stratified_size))
+        out["stratified_atmosphere"] = stratified_atmosphere(S, torch, tuple(args.stratified_size),
+                                                             steps=args.stratified_steps,
+                                                             every=min(20, args.stratified_steps))
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -507,10 +510,20 @@ def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
         olog.append(sim.diagnostics(dev))
+    # per-kernel CUDA-event times of two more steps (boundary kernels included)
+    sim.timing(True)
+    for _ in range(2):
+        sim.step(dev, None)
+    kt = sim.kernel_times()
+    sim.timing(False)
     sim.close()
+    ktot = sum(v[0] for v in kt.values()) or 1.0
+    kshare = {k: {"ms_per_step": v[0] / 2, "share": v[0] / ktot}
+              for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
     lb, ub = G, G + size[2] - 1
     umax = max(float((dev[c][lb:ub + 1].double() + refs[c]).abs().max()) for c in (1, 2, 3))
     res["open_boundaries"] = {
+        "kernels": kshare,
         "value": ncell * steps / (ms * 1e-3), "unit": UNIT + " (physical cells)",
         "ms_per_step": ms / steps, "mass_first_last": [o0[0], olog[-1][0]],
         "kinetic_first_last": [o0[5], olog[-1][5]], "max_abs_momentum_last": umax,
