@@ -45,6 +45,9 @@ CASES = {
                                                       g=(0.0, 0.0, 1.0))),
     "lnp_aver_gravity_down_16x10x16": ((16, 10, 16), dict(VISC_KW, lnp_aver=1,
                                                          g=(0.0, 0.0, -1.0))),
+    # the thinnest box allowed (nz = 3 zghost + 2): the mirrored bottom momenta
+    # reach the last physical face
+    "thinnest_viscous_gravity_down_12x8x15": ((12, 8, 15), dict(VISC_KW, g=(0.0, 0.0, -1.0))),
 }
 
 

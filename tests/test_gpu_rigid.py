@@ -45,6 +45,8 @@ CASES = {
                                                           g=(0.0, 0.0, -1.0))),
     "second_order_ediffav_16x8x11": ((16, 8, 11), dict(VISC_KW, do_2nddiv=1, d2lnr_lim=-1.0,
                                                       ediffav=1)),
+    # the thinnest box allowed: two physical planes between the ghost layers
+    "thinnest_viscous_gravity_12x8x1": ((12, 8, 1), dict(VISC_KW, g=(0.0, 0.0, -1.0))),
 }
 RHS_PARAMS = [(name, fuse) for name in CASES for fuse in (0, 1)
               if not (fuse and CASES[name][1].get("lnp_aver"))]
