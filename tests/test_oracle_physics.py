@@ -119,6 +119,23 @@ def test_conservation_and_divb(p):
     assert float((divb1 - divb0).abs().max()) < 1e-11
 
 
+def test_linear_waves_start_with_exactly_zero_discrete_divb():
+    """The 32^3 linear-wave workload (seed 1) draws the Alfven wave vector
+    2 pi (0, 0, 2): its field perturbation lies along x and depends on z
+    alone, so every term of the discrete div B vanishes exactly, and three
+    steps keep it at roundoff."""
+    import workloads
+    w = workloads.linear_waves(32)
+    assert w.physics["m_alfven"][:2] == [0.0, 0.0]
+    g = Grid(32, 32, 32, 1 / 32, 1 / 32, 1 / 32)
+    f = [torch.tensor(a) for a in w.fields]
+    d = S.diagnostics(f, g, Params())
+    assert d[7] == 0.0 and d[8] == 0.0
+    for _ in range(3):
+        f, _ = S.step(f, g, Params())
+    assert S.diagnostics(f, g, Params())[7] < 1e-12
+
+
 def test_divb_change_zero_for_any_b():
     # Even for a B that is not solenoidal, the curl update leaves div B unchanged.
     g = Grid(10, 9, 8, 0.1, 0.11, 0.12)
