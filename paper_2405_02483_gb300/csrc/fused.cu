@@ -495,6 +495,26 @@ static bool cfl_fused(const Fused& F) { return F.kp.rm && !F.zs && !F.wall; }
 // Closed z walls: fill the ghost planes of the eight state arrays f (and
 // zero the odd centred fields on the boundary planes), or zero the ghost
 // planes of a time derivative.  Rigid z walls: the ghost momenta of f.
+// ln(rho/r0) of the planes the ghost-momentum fills read (with log
+// interpolation): 0..klo+3 and khi-3..nz-1, into F_LR, after the density of the
+// ghost planes is final.  Returns F_LR, or null without log interpolation.
+static const float* wall_lr(Fused& F, float* const f[8], cudaStream_t s) {
+  const KPar& k = F.kp;
+  const Geo& g = F.geo;
+  if (!k.log_interp) return nullptr;
+  float** d = F.fld;
+  const int lo = std::min(k.klo + 4, g.nz), hi0 = std::max(k.khi - 3, lo);
+  const long long r[2][2] = {{0, lo}, {hi0, g.nz}};
+  for (int i = 0; i < 2; ++i) {
+    const long long off = r[i][0] * g.sz, n = (r[i][1] - r[i][0]) * g.sz;
+    if (n <= 0) continue;
+    TIMED(K_WALL, (k_lr_ed<Nb><<<nb1(n), 256, 0, s>>>(f[0] + off, f[4] + off, d[F_LR] + off,
+                                                       d[F_ED] + off, nullptr, nullptr, k, n,
+                                                       g.sz)));
+  }
+  return d[F_LR];
+}
+
 static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) {
   const Geo& g = F.geo;
   if (F.wall == 3) {
@@ -510,8 +530,9 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
                                                                   rows, F.oplane, g)));
     const unsigned bx = (unsigned)((g.sz + 255) / 256);
     TIMED(K_WALL, (k_open_fill_c<<<dim3(bx, 2 * G), 256, 0, s>>>(f[0], f[4], k, g)));
+    const float* lr = wall_lr(F, f, s);
     TIMED(K_WALL, (k_open_fill_m<<<dim3(bx, 2 * G + 1), 256, 0, s>>>(f[1], f[2], f[3], f[5],
-                                                                      f[6], f[7], f[0], k, g)));
+                                                                      f[6], f[7], f[0], lr, k, g)));
     return;
   }
   if (F.wall == 2) {
@@ -521,7 +542,8 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
     Mom3 m = {{f[1], f[2], f[3]}};
     const int lb = F.kp.klo, ub = F.kp.khi;
     const dim3 gr((unsigned)((g.sz + 255) / 256), (unsigned)(lb + (g.nz - 1 - ub)), 3);
-    TIMED(K_WALL, (k_rigid_fill<<<gr, 256, 0, s>>>(m, f[0], F.kp, lb, ub, g)));
+    const float* lr = wall_lr(F, f, s);
+    TIMED(K_WALL, (k_rigid_fill<<<gr, 256, 0, s>>>(m, f[0], lr, F.kp, lb, ub, g)));
     return;
   }
   Wall8 w;

@@ -1543,19 +1543,23 @@ __global__ void k_wall_zero(Wall8 w, int lb, int ub, Geo g) {
 struct Mom3 {
   float* p[3];
 };
-// rho at the lower d face of cell (ix, jy, z), formed as k_lr_ed and k_vel form it.
-__device__ __forceinline__ float rho_face_at(const float* __restrict__ rd, const KPar& k,
+// rho at the lower d face of cell (ix, jy, z), formed as k_lr_ed and k_vel form it;
+// with log interpolation the logarithms are read from lr (k_lr_ed's output for the
+// planes the stencil reaches) when it is given.
+__device__ __forceinline__ float rho_face_at(const float* __restrict__ rd,
+                                             const float* __restrict__ lr, const KPar& k,
                                              const Geo& g, int d, int ix, int jy, int z) {
   auto ls = [&](int o) {
-    const float r = rd[lin(g, wrap(ix + (d == 0 ? o : 0), g.nx), wrap(jy + (d == 1 ? o : 0), g.ny),
-                           wrap(z + (d == 2 ? o : 0), g.nz))];
-    if (!k.log_interp) return r;
-    return k.r0pos ? log1pf(r / k.r0) : logf(r);
+    const long long c = lin(g, wrap(ix + (d == 0 ? o : 0), g.nx), wrap(jy + (d == 1 ? o : 0), g.ny),
+                            wrap(z + (d == 2 ? o : 0), g.nz));
+    if (!k.log_interp) return rd[c];
+    if (lr) return lr[c];
+    return k.r0pos ? log1pf(rd[c] / k.r0) : logf(rd[c]);
   };
   return dens(s_dn(ls), k);
 }
-__global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int lb, int ub,
-                             Geo g) {
+__global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, const float* __restrict__ lr,
+                             KPar k, int lb, int ub, Geo g) {
   const int d = blockIdx.z;
   const int pl = blockIdx.y;                   // planes 0..lb-1, then ub+1..nz-1
   const int kz = pl < lb ? pl : ub + 1 + (pl - lb);
@@ -1565,8 +1569,8 @@ __global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, KPar k, int l
   const int ix = (int)(i % g.nx), jy = (int)(i / g.nx);
   const int b = kz < lb ? lb : ub;
   float* p = m.p[d];
-  const float u = fdiv(p[lin(g, ix, jy, b)] + k.pref[d], rho_face_at(rd, k, g, d, ix, jy, b));
-  p[lin(g, ix, jy, kz)] = rho_face_at(rd, k, g, d, ix, jy, kz) * u - k.pref[d];
+  const float u = fdiv(p[lin(g, ix, jy, b)] + k.pref[d], rho_face_at(rd, lr, k, g, d, ix, jy, b));
+  p[lin(g, ix, jy, kz)] = rho_face_at(rd, lr, k, g, d, ix, jy, kz) * u - k.pref[d];
 }
 
 // ------------------------------------- stellar-atmosphere z boundaries ----
@@ -1665,7 +1669,8 @@ __global__ void k_open_fill_c(float* rd, float* Ed, KPar k, Geo g) {
 // 1/(1 + exp(U oinv_u)), U the outward velocity on the inside face.  Every
 // source is a physical plane (nz >= 3 klo + 2); rho is read only.
 __global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float* by,
-                              float* bz, const float* __restrict__ rd, KPar k, Geo g) {
+                              float* bz, const float* __restrict__ rd,
+                              const float* __restrict__ lr, KPar k, Geo g) {
   const int lb = k.klo, ub = k.khi;
   const int pl = blockIdx.y;
   const int kz = pl <= lb ? pl : ub + 1 + (pl - lb - 1);
@@ -1681,7 +1686,7 @@ __global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float*
   const bool top = b == k.otop;
   auto at = [&](int z) { return (long long)z * m2 + i; };
   // outward velocity on the inside face
-  const float uzi = fdiv(pz[at(mi)] + k.pref[2], rho_face_at(rd, k, g, 2, ix, jy, mi));
+  const float uzi = fdiv(pz[at(mi)] + k.pref[2], rho_face_at(rd, lr, k, g, 2, ix, jy, mi));
   if (!top) {
     if (centre) {
       px[at(kz)] = px[at(2 * b - kz)];
@@ -1691,13 +1696,13 @@ __global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float*
   } else {
     const float um = k.oumax;
     if (centre) {
-      const float ux = fminf(fmaxf(fdiv(px[at(b)] + k.pref[0], rho_face_at(rd, k, g, 0, ix, jy, b)), -um), um);
-      const float uy = fminf(fmaxf(fdiv(py[at(b)] + k.pref[1], rho_face_at(rd, k, g, 1, ix, jy, b)), -um), um);
-      px[at(kz)] = rho_face_at(rd, k, g, 0, ix, jy, kz) * ux - k.pref[0];
-      py[at(kz)] = rho_face_at(rd, k, g, 1, ix, jy, kz) * uy - k.pref[1];
+      const float ux = fminf(fmaxf(fdiv(px[at(b)] + k.pref[0], rho_face_at(rd, lr, k, g, 0, ix, jy, b)), -um), um);
+      const float uy = fminf(fmaxf(fdiv(py[at(b)] + k.pref[1], rho_face_at(rd, lr, k, g, 1, ix, jy, b)), -um), um);
+      px[at(kz)] = rho_face_at(rd, lr, k, g, 0, ix, jy, kz) * ux - k.pref[0];
+      py[at(kz)] = rho_face_at(rd, lr, k, g, 1, ix, jy, kz) * uy - k.pref[1];
     }
     const float uz = fminf(fmaxf(uzi, -um), um);
-    pz[at(kz)] = rho_face_at(rd, k, g, 2, ix, jy, kz) * uz - k.pref[2];
+    pz[at(kz)] = rho_face_at(rd, lr, k, g, 2, ix, jy, kz) * uz - k.pref[2];
   }
   // magnetic field (stored deviations; the reference cancels in the
   // extrapolation, not in the blend)
