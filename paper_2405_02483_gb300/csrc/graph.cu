@@ -395,6 +395,7 @@ __global__ void g_add_into(T* dst, const T* src, long long n) {
 // ---------------------------------------------------------------------------
 void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& p) {
   G.nodes.clear();
+  G.memo.clear();
   const int X = 0, Y = 1, Z = 2;
   const double h[3] = {gr.dx, gr.dy, gr.dz};
   const int nn[3] = {gr.nx, gr.ny, gr.nz};

@@ -5,6 +5,9 @@
 // graph gives an unfused forward and, swept in reverse, the adjoint.
 #pragma once
 
+#include <map>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -36,11 +39,23 @@ struct GraphDef {
   int in[8];    // input node per state field (stored deviation)
   int out[8];   // output node per time derivative
 
+  // Every node is a pure function of its inputs and constants, so a node
+  // identical to an earlier one (commutative inputs in either order) is that
+  // node: the graph holds each distinct value once.  The quench node takes its
+  // eps after the push and is never shared.
   int push(int op, int a, int b, int axis, int sk, double c0, double c1) {
+    if (op != G_INPUT && op != G_QUENCH) {
+      if ((op == G_ADD || op == G_MUL || op == G_MAX) && a > b) std::swap(a, b);
+      const auto key = std::make_tuple(op, a, b, axis, sk, c0, c1);
+      const auto it = memo.find(key);
+      if (it != memo.end()) return it->second;
+      memo[key] = (int)nodes.size();
+    }
     GNode n{op, a, b, axis, sk, c0, c1};
     nodes.push_back(n);
     return (int)nodes.size() - 1;
   }
+  std::map<std::tuple<int, int, int, int, int, double, double>, int> memo;
   int input(int k) { return in[k] = push(G_INPUT, -1, -1, 0, k, 0, 0); }
   int st(int kind, int a, int axis, double h) { return push(G_STENCIL, a, -1, axis, kind, h, 0); }
   int up(int a, int ax) { return st(ST_UP, a, ax, 1.0); }
