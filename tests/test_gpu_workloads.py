@@ -4,6 +4,8 @@
   on and off, 200 Courant steps: FP32 fused and FP64 unfused GPU states vs the
   oracle run with the same step sequence, plus FP64 conservation and div B
   logged every 10 steps.
+- Brio-Wu shock tube (Sect. "Brio-Wu MHD Shock Tube"), 250 cells per unit
+  tube to t = 0.15, along x and along z.
 - Differentiation workload (Orszag-Tang 3D plus a compressive perturbation),
   scaled to 32^3: loss = kinetic energy 1/2 p^2 / rho_face in the sub-box
   [12, 20)^3 after 40 steps.  FP32 checkpointed rollout (every 8 steps) vs the
@@ -255,3 +257,50 @@ def test_differentiation_workload_fp64_32(S):
             errs.append(abs(fd - an) / abs(an))
         assert float(np.median(errs)) < 1e-4 and max(errs) < 1e-3, errs
         sim.close()
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_brio_wu_shock_tube_to_t015(S, axis):
+    """The Brio-Wu shock tube of the paper (Sect. "Brio-Wu MHD Shock Tube",
+    Table 2; gamma = 2), 250 cells per unit tube (two mirror tubes on a
+    periodic line of 500 cells), the viscous physics with the quench, Courant
+    steps to t = 0.15 (about 490), along x (four-cell threads) and along z
+    (one cell in x: one-cell threads).  FP32 against the FP64 oracle
+    stepped with the device's dt: every field group within 1e-4 of its
+    magnitude plus three times the FP32 floor of the run (the oracle's own
+    change when the initial deviations are perturbed by 2^-24, one seed);
+    mass and momentum conserved in FP64 sums of the device state."""
+    from test_gpu_parity import U32, err_group
+    w = inputs.brio_wu(axis=axis)
+    kw = dict(VISC_KW, gamma=2.0)
+    refs, dev = S.split_state(w.fields)
+    sim = S.Sim(w.shape, w.spacing, S.default_params(ref=refs, **kw))
+    g = oracle.Grid(*w.shape, *w.spacing)
+    po = oracle.Params(gamma=2.0, nu1=0.04, nu2=1.0, nu3=0.04, nuE=1.0, nuB=1.0, do_quench=True)
+    f0 = [torch.tensor(a) for a in w.fields]
+    d0 = sim.diagnostics(dev)
+    dts, t = [], 0.0
+    while t < 0.15:
+        dts.append(sim.step(dev, None, want_dt=True))
+        t += dts[-1]
+    d1 = sim.diagnostics(dev)
+    sim.close()
+    assert 300 < len(dts) < 800, len(dts)
+    fo = f0
+    for dt in dts:
+        fo, _ = oracle.step(fo, g, po, dt=dt)
+    ref = [x.numpy() for x in fo]
+    e = err_group(S.join_state(dev, refs), ref)
+    gen = torch.Generator().manual_seed(1)
+    fp = [a + (a - r) * U32 * (2.0 * torch.rand(a.shape, generator=gen, dtype=a.dtype) - 1.0)
+          for a, r in zip(f0, refs)]
+    for dt in dts:
+        fp, _ = oracle.step(fp, g, po, dt=dt)
+    floor = err_group([x.numpy() for x in fp], ref)
+    print("Brio-Wu axis %d, %d steps: err %s floor %s" % (axis, len(dts), ["%.1e" % x for x in e],
+                                                         ["%.1e" % x for x in floor]))
+    for c in range(8):
+        assert e[c] <= 1e-4 + 3 * floor[c], (c, e[c], floor[c])
+    assert abs(d1[0] - d0[0]) <= 1e-6 * d0[0]
+    for c in (1, 2, 3):
+        assert abs(d1[c] - d0[c]) <= 1e-5, (c, d1[c], d0[c])

@@ -251,3 +251,41 @@ def stratified_atmosphere(nx: int = 768, ny: int = 768, nz: int = 384, zghost: i
               np.zeros((nzt, ny, nx)), np.zeros((nzt, ny, nx)), np.full((nzt, ny, nx), b0)]
     return Workload("stratified_atmosphere", (nx, ny, nzt), h, fields,
                     dict(gamma=gamma, g=(0.0, 0.0, -1.0 / H), zghost=zghost))
+
+
+def brio_wu(n: int = 500, L: float = 2.0, gamma: float = 2.0, bn: float = 0.75,
+            axis: int = 0) -> Workload:
+    """The Brio-Wu MHD shock tube (Sect. "Brio-Wu MHD Shock Tube", Table 2):
+    left state rho = 1, P = 1, transverse B = 1; right state rho = 0.125,
+    P = 0.1, transverse B = -1; gamma = 2; at rest; the field component along
+    the tube ``bn`` (0.75, the usual value for this problem; the paper's table
+    does not list it).  On a periodic line of ``n`` cells and length ``L`` along
+    ``axis`` (the other two axes one cell), the left state fills the middle
+    half [L/4, 3L/4): two mirror-image tubes whose waves do not meet before
+    t = 0.15 when L = 2 (each half then matches the paper's 250 cells on a unit
+    tube).  The transverse field lies along the next axis."""
+    shape = [1, 1, 1]
+    shape[axis] = n
+    shape = tuple(shape)
+    lengths = [1.0, 1.0, 1.0]
+    lengths[axis] = L
+    h = tuple(lengths[a] / shape[a] for a in range(3))
+    tr = (axis + 1) % 3
+    nx, ny, nz = shape
+
+    def coord(face_axis):
+        X, Y, Z = _mesh(shape, lengths, face_axis)
+        return (X, Y, Z)[axis]
+
+    def left(s):
+        return (s >= 0.25 * L) & (s < 0.75 * L)
+
+    sc = coord(None)
+    r = np.where(left(sc), 1.0, 0.125)
+    P = np.where(left(sc), 1.0, 0.1)
+    zero = np.zeros((nz, ny, nx))
+    B = [zero.copy(), zero.copy(), zero.copy()]
+    B[axis] = np.full((nz, ny, nx), bn)
+    B[tr] = np.where(left(coord(tr)), 1.0, -1.0)
+    fields = [r, zero.copy(), zero.copy(), zero.copy(), P / (gamma - 1.0), B[0], B[1], B[2]]
+    return Workload("brio_wu", shape, h, fields, dict(gamma=gamma))
