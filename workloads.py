@@ -289,3 +289,28 @@ def brio_wu(n: int = 500, L: float = 2.0, gamma: float = 2.0, bn: float = 0.75,
     B[tr] = np.where(left(coord(tr)), 1.0, -1.0)
     fields = [r, zero.copy(), zero.copy(), zero.copy(), P / (gamma - 1.0), B[0], B[1], B[2]]
     return Workload("brio_wu", shape, h, fields, dict(gamma=gamma))
+
+
+def advection(n: int = 64, sharp: bool = False, u0: float = 1.0, P0: float = 0.01,
+              amp: float = 0.5, gamma: float = 5.0 / 3.0) -> Workload:
+    """The density advection test (Sect. "Advection"): a density profile
+    1 + amp g(x) in a uniform flow u0 along x at uniform pressure P0, on a
+    periodic unit line of ``n`` cells; g is a Gaussian of width 6 cells
+    (smooth) or a hat 16 cells wide (sharp), centred at x = 1/4.  The exact
+    solution is the profile carried at u0; the momentum is the density at the
+    x faces times u0."""
+    h = 1.0 / n
+
+    def rho(x):
+        d = ((x - 0.25 + 0.5) % 1.0) - 0.5
+        if sharp:
+            return 1.0 + amp * (np.abs(d) < 8 * h)
+        return 1.0 + amp * np.exp(-(d / (6 * h)) ** 2)
+
+    xc = ((np.arange(n) + 0.5) * h).reshape(1, 1, n)
+    xf = (np.arange(n) * h).reshape(1, 1, n)
+    zero = np.zeros((1, 1, n))
+    fields = [rho(xc), rho(xf) * u0, zero.copy(), zero.copy(),
+              np.full((1, 1, n), P0 / (gamma - 1.0)), zero.copy(), zero.copy(), zero.copy()]
+    return Workload("advection", (n, 1, 1), (h, 1.0, 1.0), fields,
+                    dict(gamma=gamma, u0=u0, exact=rho))
