@@ -226,6 +226,16 @@ typedef struct {
   double bdry_t, bdry_rho, bdry_E, bdry_u;
   double bdry_B[3];
   double top_rho_lo, top_rho_hi, top_e_fac, top_umax;
+  /* With zwalls 3 and top_tpot > 0: the horizontal field of the top plane also
+   * relaxes toward the potential field of its normal field (Sect. "Exterior
+   * Boundary In the Atmosphere"): dB_h/dt += (B_pot,h - (B_h - <B_h>)) /
+   * top_tpot, B_pot,h the horizontal components on the plane of the
+   * current-free field that decays outward from B_z on the nearest inside z
+   * face, by horizontal Fourier modes (B_h = -i s (k_h/|k|) B_z, s the outward
+   * direction; no mean or Nyquist part).  0 (default): off.  Negative or not
+   * finite: STAGGER_EINVAL.  The op-graph entries return STAGGER_EUNSUPPORTED
+   * with it. */
+  double top_tpot;
 } stagger_params;
 
 /* Ghost planes needed at each closed z wall: the reach of the right-hand

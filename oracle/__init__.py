@@ -12,5 +12,5 @@ from .stagger import (  # noqa: F401
     mirror_extend, fill_wall_ghosts, rhs_walls, courant_walls, step_walls, diagnostics_walls,
     WALL_PARITY, Z_FACE,
     face_densities, fill_rigid_ghosts, rhs_rigid, courant_rigid, step_rigid, diagnostics_rigid,
-    fill_open_ghosts, rhs_open, courant_open, step_open, diagnostics_open,
+    fill_open_ghosts, rhs_open, courant_open, step_open, diagnostics_open, potential_horizontal,
 )

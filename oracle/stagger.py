@@ -226,6 +226,8 @@ class Params:
     top_rho_hi: float = 2.0
     top_e_fac: float = 2.0   # top ghost e within [e_b / fac, e_b * fac]
     top_umax: float = 1.0    # top ghost |u| limit
+    top_tpot: float = 0.0    # relaxation time of the top horizontal field toward the
+                             # potential field, R27 (0: off)
 
     def visc_on(self):
         return (self.nu_const > 0 or self.nu1 > 0 or self.nu2 > 0 or self.nu3 > 0
@@ -980,8 +982,11 @@ def diagnostics_rigid(f, g: Grid, p: Params, lb, ub):
 #  - top plane b, eq. (rbdrylo): the vertical divergence of the mass flux is
 #    replaced by the inward mass flux over the pressure scale height,
 #    d rho/dt += ddup_z(p_z) + s up_z(p_z) / H_P, H_P = (gamma - 1) e / |g_z|.
-# The potential-field relaxation of the top magnetic field (which needs a
-# horizontal Fourier transform) is not built.
+# With top_tpot > 0 (reading R27), the horizontal field of the top plane also
+# relaxes toward the potential field of its normal field: dB_h/dt +=
+# (B_pot,h - (B_h - <B_h>))/top_tpot, B_pot,h the horizontal components, on
+# the plane, of the current-free field that decays outward from the normal
+# field B_z of the inside face nearest the plane (zero horizontal mean).
 
 
 def _open_ends(p: Params, lb, ub):
@@ -1067,6 +1072,35 @@ def fill_open_ghosts(f, p: Params, lb, ub):
     return out
 
 
+def potential_horizontal(bz, g: Grid, s):
+    """The horizontal components, at the x faces and the y faces of a plane,
+    of the potential (current-free) field above a plane whose normal field is
+    bz (cell centres in x and y, shape (ny, nx)), decaying in the outward
+    direction s along z (reading R27): per horizontal Fourier mode k,
+    B_h = -i s (k_h / |k|) B_z, B = -grad Phi with Phi ~ exp(-|k| zeta).  The
+    mean and the Nyquist modes carry no potential part.  The faces sit half a
+    cell below the centres along their axis, which is a phase factor."""
+    ny, nx = bz.shape
+    Lx, Ly = g.nx * g.dx, g.ny * g.dy
+    mx = torch.fft.fftfreq(nx, d=1.0 / nx, dtype=DT)          # integer mode numbers
+    my = torch.fft.fftfreq(ny, d=1.0 / ny, dtype=DT)
+    MY, MX = torch.meshgrid(my, mx, indexing="ij")
+    kx, ky = 2 * math.pi * MX / Lx, 2 * math.pi * MY / Ly
+    kk = torch.sqrt(kx ** 2 + ky ** 2)
+    keep = (kk > 0)
+    if nx % 2 == 0:
+        keep = keep & (MX != -nx // 2)
+    if ny % 2 == 0:
+        keep = keep & (MY != -ny // 2)
+    bh = torch.fft.fft2(bz.to(DT))
+    safe = torch.where(keep, kk, torch.ones_like(kk))
+    px = torch.where(keep, -1j * s * (kx / safe) * bh, torch.zeros_like(bh))
+    py = torch.where(keep, -1j * s * (ky / safe) * bh, torch.zeros_like(bh))
+    px = px * torch.exp(-1j * math.pi * MX / nx)              # x faces: x_c - h/2
+    py = py * torch.exp(-1j * math.pi * MY / ny)
+    return torch.fft.ifft2(px).real, torch.fft.ifft2(py).real
+
+
 def rhs_open(f, g: Grid, p: Params, lb, ub):
     """F(f) with the stellar-atmosphere z boundaries (reading R26): the
     right-hand side of the filled state with the bottom and top corrections
@@ -1089,6 +1123,12 @@ def rhs_open(f, g: Grid, p: Params, lb, ub):
     hz = Spacing(g.hc("z"), g.hf("z"))
     HP = (p.gamma - 1.0) * E[bt] / r[bt] / abs(p.g[2])
     F[0][bt] = F[0][bt] + ddup(fo[3], "z", hz)[bt] + st * up(fo[3], "z")[bt] / HP
+    if p.top_tpot > 0:
+        # R27: the top horizontal field relaxes toward the potential field.
+        bxp, byp = potential_horizontal(fo[7][_inside_face(bt, st)], g, st)
+        for c, target in ((5, bxp), (6, byp)):
+            fluct = fo[c][bt] - fo[c][bt].mean()
+            F[c][bt] = F[c][bt] + (target - fluct) / p.top_tpot
     for c in range(8):
         if Z_FACE[c]:
             F[c][:lb + 1] = 0.0

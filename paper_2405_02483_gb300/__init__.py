@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
                 ("bdry_E", ctypes.c_double), ("bdry_u", ctypes.c_double),
                 ("bdry_B", ctypes.c_double * 3),
                 ("top_rho_lo", ctypes.c_double), ("top_rho_hi", ctypes.c_double),
-                ("top_e_fac", ctypes.c_double), ("top_umax", ctypes.c_double)]
+                ("top_e_fac", ctypes.c_double), ("top_umax", ctypes.c_double),
+                ("top_tpot", ctypes.c_double)]
 
 ZGHOST_MIN = 14   # STAGGER_ZGHOST_MIN of include/stagger.h
 

@@ -56,14 +56,15 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
   if (p->quench_max3 < 0 || p->quench_max3 > 1 || !(p->quench_eps >= 0) || !isfinite(p->quench_eps))
     return STAGGER_EINVAL;
   if (p->zwalls < 0 || p->zwalls > 3) return STAGGER_EINVAL;
+  if (!(p->top_tpot >= 0) || !isfinite(p->top_tpot)) return STAGGER_EINVAL;
   if (p->zwalls == 3) {   // stellar-atmosphere boundaries
     const double v[] = {p->bdry_t, p->bdry_rho, p->bdry_E, p->bdry_u, p->bdry_B[0],
                         p->bdry_B[1], p->bdry_B[2], p->top_rho_lo, p->top_rho_hi,
-                        p->top_e_fac, p->top_umax};
+                        p->top_e_fac, p->top_umax, p->top_tpot};
     for (double x : v)
       if (!isfinite(x)) return STAGGER_EINVAL;
     if (!(p->bdry_t > 0) || !(p->bdry_rho > 0) || !(p->bdry_E > 0) || !(p->bdry_u > 0) ||
-        !(p->top_umax > 0) || !(p->top_rho_lo > 0) || p->top_rho_lo > 1 ||
+        !(p->top_umax > 0) || !(p->top_tpot >= 0) || !(p->top_rho_lo > 0) || p->top_rho_lo > 1 ||
         p->top_rho_hi < 1 || p->top_e_fac < 1 || p->g[2] == 0 || p->fuse_flux_div ||
         g->nz < 3 * p->zghost + 2)
       return STAGGER_EINVAL;
@@ -869,6 +870,7 @@ int stagger_step_adjoint(stagger_ctx* c, float* const state_n[8], double dt,
 int stagger_rhs_unfused(stagger_ctx* c, float* const state[8], float* dfdt[8], void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
   if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
+  if (c->params.zwalls == 3 && c->params.top_tpot > 0) return STAGGER_EUNSUPPORTED;
   return graph_rhs<float>(c, state, dfdt, (cudaStream_t)stream);
 }
 
@@ -876,12 +878,14 @@ int stagger_rhs_unfused_f64(stagger_ctx* c, double* const state[8], double* dfdt
                             void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !ptrs_ok((void* const*)dfdt)) return STAGGER_EINVAL;
   if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
+  if (c->params.zwalls == 3 && c->params.top_tpot > 0) return STAGGER_EUNSUPPORTED;
   return graph_rhs<double>(c, state, dfdt, (cudaStream_t)stream);
 }
 
 int stagger_step_unfused_f64(stagger_ctx* c, double* state[8], double dt, void* stream) {
   if (!c || !ptrs_ok((void* const*)state) || !(dt > 0)) return STAGGER_EINVAL;
   if (c->params.zwalls == 1) return STAGGER_EUNSUPPORTED;   // the graph does not reflect
+  if (c->params.zwalls == 3 && c->params.top_tpot > 0) return STAGGER_EUNSUPPORTED;
   return graph_step<double>(c, state, dt, (cudaStream_t)stream);
 }
 

@@ -223,6 +223,8 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   k.oumax = (float)p.top_umax;
   k.ogabs = (float)fabs(p.g[2]);
   k.omean = nullptr;
+  k.oinv_tpot = (p.zwalls == 3 && p.top_tpot > 0) ? (float)(1.0 / p.top_tpot) : 0.f;
+  k.bpx = k.bpy = nullptr;
   F.zs = zs ? 1 : 0;
   F.wsum_f = zs ? (double)gr.nx * gr.ny * zfsum * k.izbar : (double)F.geo.n;
   F.cdt = p.Cdt;
@@ -242,6 +244,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   F.plane = nullptr;
   F.pplane = nullptr;
   F.oplane = nullptr;
+  F.pot = nullptr;
   F.plane_nb = (int)std::max(1LL, std::min(64LL, ((long long)gr.nx * gr.ny + 1023) / 1024));
   if (k.lnpa) {
     // ln(P/P_aver): the plane means of E - E0 and their per-block parts, then
@@ -262,13 +265,40 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   }
   if (F.wall == 3) {
     // Stellar-atmosphere boundaries: zghost + 2 plane means, then their parts.
-    const size_t rows = (size_t)p.zghost + 2;
+    const size_t rows = (size_t)p.zghost + 4;
     if (cudaMalloc(&F.oplane, sizeof(double) * rows * (1 + F.plane_nb)) != cudaSuccess) {
       F.oplane = nullptr;
       fused_release(F);
       return STAGGER_EOOM;
     }
     k.omean = F.oplane;
+  }
+  if (k.oinv_tpot > 0.f) {
+    // R27 scratch: the two target planes, the roots of unity along x and y,
+    // and six complex planes of the transforms.
+    const size_t m2 = (size_t)gr.nx * gr.ny;
+    const size_t nfl = 14 * m2 + 2 * ((size_t)gr.nx + gr.ny);
+    if (cudaMalloc(&F.pot, sizeof(float) * nfl) != cudaSuccess) {
+      F.pot = nullptr;
+      fused_release(F);
+      return STAGGER_EOOM;
+    }
+    std::vector<float> w(2 * ((size_t)gr.nx + gr.ny));
+    for (int r = 0; r < gr.nx; ++r) {
+      w[2 * r] = (float)cos(2.0 * M_PI * r / gr.nx);
+      w[2 * r + 1] = (float)-sin(2.0 * M_PI * r / gr.nx);
+    }
+    for (int r = 0; r < gr.ny; ++r) {
+      w[2 * (gr.nx + r)] = (float)cos(2.0 * M_PI * r / gr.ny);
+      w[2 * (gr.nx + r) + 1] = (float)-sin(2.0 * M_PI * r / gr.ny);
+    }
+    if (cudaMemcpy(F.pot + 2 * m2, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      fused_release(F);
+      return STAGGER_ECUDA;
+    }
+    k.bpx = F.pot;
+    k.bpy = F.pot + m2;
   }
   if (p.t_chromo > 0 || k.ediffav) {
     // Plane means of e for the chromospheric cooling and the energy diffusion
@@ -385,6 +415,8 @@ void fused_release(Fused& F) {
   F.pplane = nullptr;
   if (F.oplane) cudaFree(F.oplane);
   F.oplane = nullptr;
+  if (F.pot) cudaFree(F.pot);
+  F.pot = nullptr;
   F.dt_dev = nullptr;
   F.red = nullptr;
 }
@@ -523,9 +555,9 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
     // plane means, the rho and E extrapolation, then momenta and field.
     if (zero) return;
     const KPar& k = F.kp;
-    const int G = k.klo, rows = G + 2;
+    const int G = k.klo, rows = G + 4;
     TIMED(K_WALL, (k_open_part<<<dim3(F.plane_nb, rows), 256, 0, s>>>(
-                      f[0], f[1], f[2], F.oplane + rows, k, g)));
+                      f[0], f[1], f[2], f[5], f[6], F.oplane + rows, k, g)));
     TIMED(K_WALL, (k_open_final<<<(rows + 63) / 64, 64, 0, s>>>(F.oplane + rows, F.plane_nb,
                                                                   rows, F.oplane, g)));
     const unsigned bx = (unsigned)((g.sz + 255) / 256);
@@ -533,6 +565,28 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
     const float* lr = wall_lr(F, f, s);
     TIMED(K_WALL, (k_open_fill_m<<<dim3(bx, 2 * G + 1), 256, 0, s>>>(f[1], f[2], f[3], f[5],
                                                                       f[6], f[7], f[0], lr, k, g)));
+    if (k.oinv_tpot > 0.f) {
+      // R27: the potential-field targets of the top plane from B_z on its
+      // inside face, by horizontal Fourier modes.
+      const int nx = g.nx, ny = g.ny;
+      const size_t m2 = (size_t)nx * ny;
+      float* bpx = F.pot;
+      float* bpy = F.pot + m2;
+      const float2* wx = reinterpret_cast<const float2*>(F.pot + 2 * m2);
+      const float2* wy = wx + nx;
+      float2* X = reinterpret_cast<float2*>(F.pot + 2 * m2 + 2 * ((size_t)nx + ny));
+      float2 *Y = X + m2, *Px = Y + m2, *Py = Px + m2, *Zx = Py + m2, *Zy = Zx + m2;
+      const int mi = k.ost > 0 ? k.khi : k.klo + 1;
+      const dim3 gp((unsigned)((nx + 127) / 128), (unsigned)ny);
+      const float Lx = (float)(nx / (double)k.ih[0]), Ly = (float)(ny / (double)k.ih[1]);
+      TIMED(K_WALL, (k_dft_rows<<<gp, 128, 0, s>>>(f[7] + (long long)mi * g.sz, X, wx, nx, ny)));
+      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(X, Y, wy, nx, ny, 0, 1.f)));
+      TIMED(K_WALL, (k_pot_sym<<<gp, 128, 0, s>>>(Y, Px, Py, nx, ny, Lx, Ly, (float)k.ost)));
+      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(Px, Zx, wy, nx, ny, 1, 1.f / ny)));
+      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(Py, Zy, wy, nx, ny, 1, 1.f / ny)));
+      TIMED(K_WALL, (k_idft_rows<<<gp, 128, 0, s>>>(Zx, bpx, wx, nx, ny, 1.f / nx)));
+      TIMED(K_WALL, (k_idft_rows<<<gp, 128, 0, s>>>(Zy, bpy, wx, nx, ny, 1.f / nx)));
+    }
     return;
   }
   if (F.wall == 2) {

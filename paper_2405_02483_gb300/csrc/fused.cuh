@@ -54,10 +54,15 @@ struct KPar {
   // planes and their outward index directions, 1/bdry_t, the bottom targets,
   // 1/bdry_u, B_bdry (x, y), the top limits, |g_z|, and the plane means: the
   // extrapolated density of the top ghost planes 1..zghost (zghost doubles),
-  // then the p_x and p_y deviations of the bottom plane.
+  // the p_x and p_y deviations of the bottom plane, the B_x and B_y deviations
+  // of the top plane.
   int obot, otop, osb, ost;
   float oinv_t, orho, oE, oinv_u, oBx, oBy, orlo, orhi, oefac, oumax, ogabs;
   const double* omean;
+  // R27: 1/top_tpot (0: off) and the potential-field targets of the top
+  // plane's B_x, B_y fluctuations (one plane each).
+  float oinv_tpot;
+  const float *bpx, *bpy;
 };
 
 // Fields of the fused path, one contiguous device array each.
@@ -106,7 +111,8 @@ struct Fused {
   int plane_nb;
   double* pplane;       // the same for E - E0 (ln(P/P_aver)), then its 3 nz floats of
                         // per-plane pressure factors, or null
-  double* oplane;       // stellar-atmosphere means (zghost + 2), then their per-block parts
+  double* oplane;       // stellar-atmosphere means (zghost + 4), then their per-block parts
+  float* pot;           // R27 scratch: roots (nx + ny), 6 complex and 2 real planes, or null
   int red_blocks;
   int cells4;           // nx % 4 == 0 and four-cell threads not switched off
   int fdiv;             // fluxes, divergences and update in one kernel (k_fdiv)

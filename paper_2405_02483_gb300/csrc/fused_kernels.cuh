@@ -158,6 +158,10 @@ struct Nb {
   }
   // Plain load of the cell's own element of an array the launch rewrites.
   __device__ __forceinline__ float ldw(const float* p) const { return p[c]; }
+  // The cell's element of an array of one horizontal plane (nx ny values).
+  __device__ __forceinline__ float ldpl(const float* __restrict__ p) const {
+    return __ldg(p + (c - z[3]));
+  }
   __device__ __forceinline__ void st(float* p, float v) const { p[c] = v; }
   // W consecutive elements at p (element-wise kernels).
   static __device__ __forceinline__ float ldp(const float* __restrict__ p) { return __ldg(p); }
@@ -258,6 +262,7 @@ struct Nb4 {
   __device__ __forceinline__ F4 ldw(const float* p) const {
     return v4(*reinterpret_cast<const float4*>(p + c));
   }
+  __device__ __forceinline__ F4 ldpl(const float* __restrict__ p) const { return row(p, c - z[3]); }
   __device__ __forceinline__ void st(float* p, const F4& v) const { stp(p + c, v); }
   static __device__ __forceinline__ F4 ldp(const float* __restrict__ p) { return row(p, 0); }
   static __device__ __forceinline__ void stp(float* p, const F4& v) {
@@ -1196,8 +1201,19 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   }
   if (M & 16) fin(4, Fe);
   // eq. (indu): dB/dt = -curl E
-  if (M & 32) fin(5, -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k))));
-  if (M & 64) fin(6, -(s_du(AX(in.Ex, 2), n.ju(2, k)) - s_du(AX(in.Ez, 0), n.ju(0, k))));
+  // R27: the top plane's horizontal field relaxes toward the potential field
+  // (targets and plane means from the boundary fill).
+  const bool opot = k.wall == 3 && n.kz == k.otop && k.oinv_tpot > 0.f;
+  if (M & 32) {
+    T t = -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k)));
+    if (opot) t += (n.ldpl(k.bpx) - (n.ld(in.f[5]) - (float)k.omean[k.klo + 2])) * k.oinv_tpot;
+    fin(5, t);
+  }
+  if (M & 64) {
+    T t = -(s_du(AX(in.Ex, 2), n.ju(2, k)) - s_du(AX(in.Ez, 0), n.ju(0, k)));
+    if (opot) t += (n.ldpl(k.bpy) - (n.ld(in.f[6]) - (float)k.omean[k.klo + 3])) * k.oinv_tpot;
+    fin(6, t);
+  }
   if (M & 128) fin(7, -(s_du(AX(in.Ey, 0), n.ju(0, k)) - s_du(AX(in.Ex, 1), n.ju(1, k))));
   if (!CR) return 0u;
   const T r = n.ld(in.f[0]) + k.r0, E = n.ld(in.f[4]) + k.E0;
@@ -1581,7 +1597,8 @@ __global__ void k_rigid_fill(Mom3 m, const float* __restrict__ rd, const float* 
 // k_open_part: row j < G sums, over its plane, the density of the top ghost
 // plane otop + ost (j + 1) extrapolated linearly in ln rho from the top plane
 // and its inner neighbour; rows G and G + 1 sum the p_x and p_y deviations of
-// the bottom plane.  k_open_final divides by the plane size.
+// the bottom plane, rows G + 2 and G + 3 the B_x and B_y deviations of the top
+// plane.  k_open_final divides by the plane size.
 // ln(rho/r0) (ln rho when r0 = 0) and e - e0 of a cell as k_lr_ed forms them,
 // and the density deviation of an extrapolated ln(rho/r0).  FP32 throughout:
 // FP64 transcendentals run at a small fraction of the FP32 rate.
@@ -1595,7 +1612,8 @@ __device__ __forceinline__ float open_rdev(float l, const KPar& k) {
   return k.r0pos ? k.r0 * expm1f(l) : expf(l);
 }
 __global__ void k_open_part(const float* __restrict__ rd, const float* __restrict__ px,
-                            const float* __restrict__ py, double* part, KPar k, Geo g) {
+                            const float* __restrict__ py, const float* __restrict__ bx,
+                            const float* __restrict__ by, double* part, KPar k, Geo g) {
   __shared__ double sm[256];
   const int row = blockIdx.y, nb = gridDim.x, G = k.klo;
   const long long m = (long long)g.nx * g.ny;
@@ -1606,8 +1624,10 @@ __global__ void k_open_part(const float* __restrict__ rd, const float* __restric
       const float lb_ = open_lnr(rd[(long long)k.otop * m + i], k);
       const float li = open_lnr(rd[(long long)(k.otop - k.ost) * m + i], k);
       acc += (double)(open_rdev(lb_ + (float)(row + 1) * (lb_ - li), k) + k.r0);
-    } else {
+    } else if (row < G + 2) {
       acc += (double)(row == G ? px : py)[(long long)k.obot * m + i];
+    } else {
+      acc += (double)(row == G + 2 ? bx : by)[(long long)k.otop * m + i];
     }
   }
   sm[threadIdx.x] = acc;
@@ -1721,5 +1741,90 @@ __global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float*
   }
 }
 
+
+// ------------------------------------------- top potential field (R27) ----
+// Horizontal discrete Fourier transforms of one plane by direct sums along
+// one axis at a time (one thread per output element), with twiddles from a
+// table of the n roots e^(-2 pi i r / n), the index r = m j advanced modulo n.
+// k_dft_rows: X[j][m] = sum_i B[j][i] w^(m i); k_dft_cols: Y[q][m] = scale
+// sum_j X[j][m] w^(+-q j); k_idft_rows: b[j][i] = scale Re sum_m Z[j][m]
+// w^(-m i).  FP32 sums of at most a few thousand terms.
+__global__ void k_dft_rows(const float* __restrict__ B, float2* X, const float2* __restrict__ w,
+                           int nx, int ny) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (m >= nx || j >= ny) return;
+  const float* b = B + (long long)j * nx;
+  float re = 0.f, im = 0.f;
+  int r = 0;
+  for (int i = 0; i < nx; ++i) {
+    const float2 t = __ldg(w + r);
+    const float v = __ldg(b + i);
+    re += v * t.x;
+    im += v * t.y;
+    r += m;
+    if (r >= nx) r -= nx;
+  }
+  X[(long long)j * nx + m] = make_float2(re, im);
+}
+__global__ void k_dft_cols(const float2* __restrict__ X, float2* Y, const float2* __restrict__ w,
+                           int nx, int ny, int inverse, float scale) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+  if (m >= nx || q >= ny) return;
+  float re = 0.f, im = 0.f;
+  int r = 0;
+  for (int j = 0; j < ny; ++j) {
+    float2 t = __ldg(w + r);
+    if (inverse) t.y = -t.y;
+    const float2 v = __ldg(X + (long long)j * nx + m);
+    re += v.x * t.x - v.y * t.y;
+    im += v.x * t.y + v.y * t.x;
+    r += q;
+    if (r >= ny) r -= ny;
+  }
+  Y[(long long)q * nx + m] = make_float2(re * scale, im * scale);
+}
+__global__ void k_idft_rows(const float2* __restrict__ Z, float* b, const float2* __restrict__ w,
+                            int nx, int ny, float scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= nx || j >= ny) return;
+  const float2* z = Z + (long long)j * nx;
+  float re = 0.f;
+  int r = 0;
+  for (int m = 0; m < nx; ++m) {
+    const float2 t = __ldg(w + r);        // e^(+2 pi i m i / nx): the conjugate root
+    const float2 v = __ldg(z + m);
+    re += v.x * t.x + v.y * t.y;
+    r += i;
+    if (r >= nx) r -= nx;
+  }
+  b[(long long)j * nx + i] = re * scale;
+}
+// The horizontal potential field's spectrum from that of B_z (reading R27):
+// P_x = -i s (k_x/|k|) B^_z e^(-i pi m_x/nx) (the x faces half a cell below
+// the centres), P_y likewise; no mean or Nyquist part.
+__global__ void k_pot_sym(const float2* __restrict__ Y, float2* Px, float2* Py, int nx, int ny,
+                          float Lx, float Ly, float s) {
+  const int mx = blockIdx.x * blockDim.x + threadIdx.x, my = blockIdx.y;
+  if (mx >= nx || my >= ny) return;
+  const long long o = (long long)my * nx + mx;
+  const int sx = mx < (nx + 1) / 2 ? mx : mx - nx, sy = my < (ny + 1) / 2 ? my : my - ny;
+  const bool nyq = ((nx % 2 == 0) && mx == nx / 2) || ((ny % 2 == 0) && my == ny / 2);
+  const float kx = 2.f * 3.14159265358979f * (float)sx / Lx, ky = 2.f * 3.14159265358979f * (float)sy / Ly;
+  const float kk = sqrtf(kx * kx + ky * ky);
+  if (nyq || kk == 0.f) {
+    Px[o] = make_float2(0.f, 0.f);
+    Py[o] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float2 b = Y[o];
+  // -i s c b = s c (b.y, -b.x), then the face phase e^(-i pi m / n)
+  float cx, snx, cy, sny;
+  sincosf(3.14159265358979f * (float)sx / (float)nx, &snx, &cx);
+  sincosf(3.14159265358979f * (float)sy / (float)ny, &sny, &cy);
+  const float ax = s * kx / kk, ay = s * ky / kk;
+  const float2 qx = make_float2(ax * b.y, -ax * b.x), qy = make_float2(ay * b.y, -ay * b.x);
+  Px[o] = make_float2(qx.x * cx + qx.y * snx, qx.y * cx - qx.x * snx);
+  Py[o] = make_float2(qy.x * cy + qy.y * sny, qy.y * cy - qy.x * sny);
+}
 
 }  // namespace stg

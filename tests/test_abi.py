@@ -226,6 +226,8 @@ def test_wall_parameters_are_validated_without_gpu(S):
               dict(zwalls=3, zghost=S.ZGHOST_MIN, g=(0, 0, -1.0), fuse_flux_div=1)),
              (S.Grid(8, 8, 3 * S.ZGHOST_MIN + 2, 0.1, 0.1, 0.1),
               dict(zwalls=3, zghost=S.ZGHOST_MIN, g=(0, 0, -1.0), bdry_B=(float("nan"), 0, 0))),
+             (S.Grid(8, 8, 3 * S.ZGHOST_MIN + 2, 0.1, 0.1, 0.1),
+              dict(zwalls=3, zghost=S.ZGHOST_MIN, g=(0, 0, -1.0), top_tpot=-1.0)),
              (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN - 1)),
              (S.Grid(8, 8, ok_nz - 1, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN)),
              (S.Grid(8, 8, ok_nz, 0.1, 0.1, 0.1), dict(zwalls=1, zghost=S.ZGHOST_MIN, csmag=0.1)),

@@ -48,6 +48,13 @@ CASES = {
     # the thinnest box allowed (nz = 3 zghost + 2): the mirrored bottom momenta
     # reach the last physical face
     "thinnest_viscous_gravity_down_12x8x15": ((12, 8, 15), dict(VISC_KW, g=(0.0, 0.0, -1.0))),
+    # the top's relaxation toward the potential field (R27), even and odd
+    # horizontal sizes, the top at either end
+    "potential_top_viscous_gravity_down_24x9x18": ((24, 9, 18), dict(VISC_KW, g=(0.0, 0.0, -1.0),
+                                                                     top_tpot=0.05)),
+    "potential_top_const_nu_gravity_up_13x8x16": ((13, 8, 16), dict(nu_const=0.003, nuE=0.5,
+                                                                    nuB=0.7, g=(0.0, 0.0, 1.0),
+                                                                    top_tpot=0.1)),
 }
 
 
@@ -97,7 +104,8 @@ def test_open_rhs_matches_oracle(S, name, sc):
         assert err <= 2e-4 * sc_[c] + K_FLOOR * delta[c], (name, c, err / sc_[c], delta[c] / sc_[c])
 
 
-@pytest.mark.parametrize("name", ["viscous_quench_gravity_down_24x9x18", "const_nu_gravity_up_13x8x16"])
+@pytest.mark.parametrize("name", ["viscous_quench_gravity_down_24x9x18", "const_nu_gravity_up_13x8x16",
+                                  "potential_top_viscous_gravity_down_24x9x18"])
 def test_open_steps_courant_and_ghosts(S, name):
     shape, kw = CASES[name]
     fields, g, lb, ub = _state(shape, seed=8)
@@ -210,6 +218,15 @@ def test_open_op_graph_matches_oracle(S, name):
         ref = fo[c].numpy()
         err = float(np.abs(got[c] - ref).max())
         assert err <= 1e-12 * max(1.0, float(np.abs(ref).max())), (c, err)
+    sim.close()
+
+
+def test_open_potential_top_refuses_the_op_graph(S):
+    fields, g, lb, ub = _state((8, 8, 16))
+    sim, refs, dev = _make(S, fields, g, dict(g=(0.0, 0.0, -1.0), top_tpot=0.1))
+    with pytest.raises(S.StaggerError) as ei:
+        sim.rhs_unfused(dev)
+    assert ei.value.status == S.EUNSUPPORTED
     sim.close()
 
 

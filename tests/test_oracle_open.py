@@ -209,3 +209,65 @@ def test_open_boundaries_hold_a_balanced_atmosphere_at_rest():
     for c in range(8):
         err = float(F[c].abs().max())
         assert err <= 1e-12 * scale, (c, err / scale)
+
+
+# ------------------------------------------ top potential field (reading R27) ---
+
+@pytest.mark.parametrize("s", [1, -1])
+def test_potential_field_of_a_single_mode_in_closed_form(s):
+    """B_z = cos(kx x + ky y) on the plane: the potential field decaying in the
+    outward direction s has B_x = s (kx/|k|) sin(kx x + ky y) and
+    B_y = s (ky/|k|) sin(kx x + ky y), each at its own face position (B = -grad
+    Phi, Phi ~ cos(.) exp(-|k| zeta); div B = 0 and curl B = 0)."""
+    nx, ny = 12, 10
+    g = Grid(nx, ny, 40, 1.0 / nx, 1.3 / ny, 0.1)
+    mx, my = 2, 1
+    kx, ky = 2 * math.pi * mx / 1.0, 2 * math.pi * my / 1.3
+    kk = math.hypot(kx, ky)
+    xc = (torch.arange(nx, dtype=DT) + 0.5) / nx
+    yc = (torch.arange(ny, dtype=DT) + 0.5) * 1.3 / ny
+    xf = torch.arange(nx, dtype=DT) / nx
+    yf = torch.arange(ny, dtype=DT) * 1.3 / ny
+    Y, X = torch.meshgrid(yc, xc, indexing="ij")
+    bz = torch.cos(kx * X + ky * Y)
+    bx, by = oracle.potential_horizontal(bz, g, s)
+    Yx, Xx = torch.meshgrid(yc, xf, indexing="ij")
+    Yy, Xy = torch.meshgrid(yf, xc, indexing="ij")
+    wx = s * kx / kk * torch.sin(kx * Xx + ky * Yx)
+    wy = s * ky / kk * torch.sin(kx * Xy + ky * Yy)
+    assert float((bx - wx).abs().max()) <= 1e-13
+    assert float((by - wy).abs().max()) <= 1e-13
+    # a uniform normal field has no horizontal potential part
+    bx0, by0 = oracle.potential_horizontal(torch.full((ny, nx), 0.3, dtype=DT), g, s)
+    assert float(bx0.abs().max()) <= 1e-15 and float(by0.abs().max()) <= 1e-15
+
+
+def test_top_relaxes_toward_the_potential_field_and_leaves_it_alone():
+    """With top_tpot, the top plane's horizontal field gains (B_pot - (B_h -
+    <B_h>)) / top_tpot: zero when the plane already holds the potential field
+    of its normal field plus any uniform part, B_pot / top_tpot when its
+    horizontal field is uniform; no other plane changes."""
+    f, g, lb, ub = random_state(8, 6, 16, seed=4)
+    p0 = Params(g=(0.0, 0.0, -1.0), top_umax=10.0)
+    pt = Params(**{**p0.__dict__, "top_tpot": 0.05})
+    fo = oracle.fill_open_ghosts(f, p0, lb, ub)
+    bxp, byp = oracle.potential_horizontal(fo[7][ub], g, 1)
+    # top plane: the potential field plus a uniform part
+    f = [a.clone() for a in f]
+    f[5][ub] = bxp + 0.07
+    f[6][ub] = byp - 0.02
+    d = [a - b for a, b in zip(oracle.rhs_open(f, g, pt, lb, ub), oracle.rhs_open(f, g, p0, lb, ub))]
+    for c in range(8):
+        assert float(d[c].abs().max()) <= 1e-12, c
+    # uniform horizontal field on the top plane: the rate is B_pot / top_tpot
+    f[5][ub] = 0.0 * bxp + 0.07
+    f[6][ub] = 0.0 * byp - 0.02
+    fo = oracle.fill_open_ghosts(f, p0, lb, ub)
+    bxp, byp = oracle.potential_horizontal(fo[7][ub], g, 1)
+    d = [a - b for a, b in zip(oracle.rhs_open(f, g, pt, lb, ub), oracle.rhs_open(f, g, p0, lb, ub))]
+    assert float((d[5][ub] - bxp / 0.05).abs().max()) <= 1e-11
+    assert float((d[6][ub] - byp / 0.05).abs().max()) <= 1e-11
+    assert float(bxp.abs().max()) > 1e-3
+    for c in range(8):
+        rest = torch.cat([d[c][:ub], d[c][ub + 1:]])
+        assert float(rest.abs().max()) == 0.0, c
