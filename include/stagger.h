@@ -214,8 +214,8 @@ typedef struct {
    * lose f (p_h - <p_h>)/bdry_t.  On the top plane the vertical mass-flux
    * divergence is replaced by the outward-signed flux over the pressure
    * scale height (gamma - 1) e / |g_z| (eq. rbdrylo).  bdry_E is internal
-   * energy per volume.  The potential-field relaxation of the top field is
-   * not built.  Needs bdry_t, bdry_rho, bdry_E, bdry_u, top_umax > 0, 0 <
+   * energy per volume.  The top field's relaxation toward the potential
+   * field is top_tpot below.  Needs bdry_t, bdry_rho, bdry_E, bdry_u, top_umax > 0, 0 <
    * top_rho_lo <= 1 <= top_rho_hi, top_e_fac >= 1, nz >= 3 zghost + 2 (the
    * mirrored bottom momenta come from physical planes), fuse_flux_div 0 and
    * the conditions of the closed walls but the ref[] one, else
