@@ -452,8 +452,9 @@ def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
     atmosphere) and the benchmark's physics, for `steps` Courant steps:
     (1) FP32 at `size`, zone-updates/s of the physical cells over the steps
     alone and FP64 totals every `every` steps, with rigid walls and (1b) with
-    the stellar-atmosphere boundaries (reading R26); (2) FP32 against the FP64
-    op graph at half the resolution with the stellar-atmosphere boundaries,
+    the stellar-atmosphere boundaries (readings R26, R27); (2) FP32 against the
+    FP64 op graph at half the resolution with the stellar-atmosphere boundaries
+    but no potential-field relaxation (the op graph does not take it),
     the same dt every step, the error of each field on the physical planes
     after the steps."""
     import numpy as np
@@ -493,13 +494,16 @@ def stratified_atmosphere(S, torch, size=(768, 768, 384), steps=200, every=20):
     torch.cuda.empty_cache()
     # (1b) the same atmosphere with the stellar-atmosphere boundaries (R26):
     # the bottom relaxes to its initial plane values on t = 0.1, the inflow
-    # switch on the noise speed, the top limits at their defaults.
+    # switch on the noise speed, the top limits at their defaults, and the
+    # top's horizontal field relaxes toward the potential field on t = 2e-3,
+    # about ten Courant steps (R27).
     w = inputs.stratified_atmosphere(*size, zghost=G)
     rb, Eb = float(w.fields[0][G, 0, 0]), float(w.fields[4][G, 0, 0])
     refs, dev = S.split_state(w.fields)
     shape, spacing = w.shape, w.spacing
     del w
-    popen = dict(PHYS, zwalls=3, zghost=G, bdry_t=0.1, bdry_rho=rb, bdry_E=Eb, bdry_u=1e-3)
+    popen = dict(PHYS, zwalls=3, zghost=G, bdry_t=0.1, bdry_rho=rb, bdry_E=Eb, bdry_u=1e-3,
+                 top_tpot=2e-3)
     sim = S.Sim(shape, spacing, S.default_params(ref=refs, g=(0.0, 0.0, -8.0), **popen))
     o0 = sim.diagnostics(dev)
     ms, olog = 0.0, []

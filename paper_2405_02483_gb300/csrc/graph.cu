@@ -13,9 +13,15 @@ namespace stg {
 // cell's (i, j, k) come from the launch and a periodic neighbour needs no
 // division.
 // ---------------------------------------------------------------------------
+#ifndef GBX
 #define GBX 32
+#endif
+#ifndef GBY
 #define GBY 2
+#endif
+#ifndef GBZ
 #define GBZ 4
+#endif
 
 struct GCell {
   int i, j, k;

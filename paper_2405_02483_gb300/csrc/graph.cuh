@@ -90,7 +90,9 @@ struct GraphDef {
 // Build the right-hand-side graph for a grid and parameter set.
 void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p);
 
+#ifndef GRAPH_NSTREAMS
 #define GRAPH_NSTREAMS 4
+#endif
 
 // Device executor for one precision.  Holds one value and one gradient array
 // of n cells per node (inputs point at caller memory and need none).
