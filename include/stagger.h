@@ -233,7 +233,7 @@ typedef struct {
    * current-free field that decays outward from B_z on the nearest inside z
    * face, by horizontal Fourier modes (B_h = -i s (k_h/|k|) B_z, s the outward
    * direction; no mean or Nyquist part).  0 (default): off.  Negative or not
-   * finite: STAGGER_EINVAL.  The op-graph entries return STAGGER_EUNSUPPORTED
+   * finite, or nx > 24576 with it: STAGGER_EINVAL.  The op-graph entries return STAGGER_EUNSUPPORTED
    * with it. */
   double top_tpot;
 } stagger_params;

@@ -57,6 +57,8 @@ int validate_inputs(const stagger_grid* g, const stagger_params* p) {
     return STAGGER_EINVAL;
   if (p->zwalls < 0 || p->zwalls > 3) return STAGGER_EINVAL;
   if (!(p->top_tpot >= 0) || !isfinite(p->top_tpot)) return STAGGER_EINVAL;
+  // The potential-field transforms keep nx complex roots in shared memory.
+  if (p->zwalls == 3 && p->top_tpot > 0 && g->nx > 24576) return STAGGER_EINVAL;
   if (p->zwalls == 3) {   // stellar-atmosphere boundaries
     const double v[] = {p->bdry_t, p->bdry_rho, p->bdry_E, p->bdry_u, p->bdry_B[0],
                         p->bdry_B[1], p->bdry_B[2], p->top_rho_lo, p->top_rho_hi,

@@ -299,6 +299,16 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
     }
     k.bpx = F.pot;
     k.bpy = F.pot + m2;
+    // The row transforms keep the nx roots in shared memory.
+    const int sm = (int)(sizeof(float2) * (size_t)gr.nx);
+    if (sm > 48 * 1024 &&
+        (cudaFuncSetAttribute(k_dft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
+             cudaSuccess ||
+         cudaFuncSetAttribute(k_idft_rows2, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
+             cudaSuccess)) {
+      fused_release(F);
+      return STAGGER_ECUDA;
+    }
   }
   if (p.t_chromo > 0 || k.ediffav) {
     // Plane means of e for the chromospheric cooling and the energy diffusion
@@ -547,7 +557,8 @@ static const float* wall_lr(Fused& F, float* const f[8], cudaStream_t s) {
   return d[F_LR];
 }
 
-static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) {
+// rhs: a right-hand side of f follows (the R27 targets are formed only then).
+static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s, bool rhs = true) {
   const Geo& g = F.geo;
   if (F.wall == 3) {
     // Stellar-atmosphere boundaries (R26): the divergence kernels write zero
@@ -565,7 +576,7 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
     const float* lr = wall_lr(F, f, s);
     TIMED(K_WALL, (k_open_fill_m<<<dim3(bx, 2 * G + 1), 256, 0, s>>>(f[1], f[2], f[3], f[5],
                                                                       f[6], f[7], f[0], lr, k, g)));
-    if (k.oinv_tpot > 0.f) {
+    if (k.oinv_tpot > 0.f && rhs) {
       // R27: the potential-field targets of the top plane from B_z on its
       // inside face, by horizontal Fourier modes.
       const int nx = g.nx, ny = g.ny;
@@ -579,13 +590,12 @@ static void wall_launch(Fused& F, float* const f[8], bool zero, cudaStream_t s) 
       const int mi = k.ost > 0 ? k.khi : k.klo + 1;
       const dim3 gp((unsigned)((nx + 127) / 128), (unsigned)ny);
       const float Lx = (float)(nx / (double)k.ih[0]), Ly = (float)(ny / (double)k.ih[1]);
-      TIMED(K_WALL, (k_dft_rows<<<gp, 128, 0, s>>>(f[7] + (long long)mi * g.sz, X, wx, nx, ny)));
-      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(X, Y, wy, nx, ny, 0, 1.f)));
+      const size_t sm = sizeof(float2) * (size_t)nx;   // the x roots in shared memory
+      TIMED(K_WALL, (k_dft_rows<<<gp, 128, sm, s>>>(f[7] + (long long)mi * g.sz, X, wx, nx, ny)));
+      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(X, Y, wy, nx, ny)));
       TIMED(K_WALL, (k_pot_sym<<<gp, 128, 0, s>>>(Y, Px, Py, nx, ny, Lx, Ly, (float)k.ost)));
-      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(Px, Zx, wy, nx, ny, 1, 1.f / ny)));
-      TIMED(K_WALL, (k_dft_cols<<<gp, 128, 0, s>>>(Py, Zy, wy, nx, ny, 1, 1.f / ny)));
-      TIMED(K_WALL, (k_idft_rows<<<gp, 128, 0, s>>>(Zx, bpx, wx, nx, ny, 1.f / nx)));
-      TIMED(K_WALL, (k_idft_rows<<<gp, 128, 0, s>>>(Zy, bpy, wx, nx, ny, 1.f / nx)));
+      TIMED(K_WALL, (k_idft_cols2<<<gp, 128, 0, s>>>(Px, Py, Zx, Zy, wy, nx, ny)));
+      TIMED(K_WALL, (k_idft_rows2<<<gp, 128, sm, s>>>(Zx, Zy, bpx, bpy, wx, nx, ny)));
     }
     return;
   }
@@ -798,7 +808,7 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
     rc = launch_div(F, st_in[stg], F.q, const_cast<float**>(st_out[stg]), alpha, beta, 1, s);
     if (rc) return rc;
   }
-  if (F.wall) wall_launch(F, f, false, s);
+  if (F.wall) wall_launch(F, f, false, s, false);
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
@@ -873,7 +883,7 @@ int fused_courant(Fused& F, float* const f[8], double lim[3], double* dt, cudaSt
 
 int fused_diagnostics(Fused& F, float* const f[8], const stagger_params& p, double out[10],
                       cudaStream_t s) {
-  if (F.wall) wall_launch(F, f, false, s);
+  if (F.wall) wall_launch(F, f, false, s, false);
   dim3 gg = grid3(F.geo), bb(BX, BY, BZ);
   auto kdiag = F.zs ? k_diag_part<NbZ> : k_diag_part<Nb>;
   TIMED(K_DIAG, (kdiag<<<gg, bb, 0, s>>>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], F.red,

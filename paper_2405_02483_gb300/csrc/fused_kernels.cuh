@@ -1742,22 +1742,28 @@ __global__ void k_open_fill_m(float* px, float* py, float* pz, float* bx, float*
 }
 
 
+#ifdef __CUDACC__   // device-only (dynamic shared memory); not in the host build of the kernels
 // ------------------------------------------- top potential field (R27) ----
 // Horizontal discrete Fourier transforms of one plane by direct sums along
 // one axis at a time (one thread per output element), with twiddles from a
-// table of the n roots e^(-2 pi i r / n), the index r = m j advanced modulo n.
-// k_dft_rows: X[j][m] = sum_i B[j][i] w^(m i); k_dft_cols: Y[q][m] = scale
-// sum_j X[j][m] w^(+-q j); k_idft_rows: b[j][i] = scale Re sum_m Z[j][m]
-// w^(-m i).  FP32 sums of at most a few thousand terms.
+// table of the n roots e^(-2 pi i r / n), the index r = m j advanced modulo n
+// (the row kernels keep the table in shared memory: their threads read it at
+// scattered places).  k_dft_rows: X[j][m] = sum_i B[j][i] w^(m i);
+// k_dft_cols: Y[q][m] = sum_j X[j][m] w^(q j); k_idft_cols2 and k_idft_rows2
+// invert two spectra at once, with 1/ny and 1/nx, keeping the real part at the
+// end.  FP32 sums of at most a few thousand terms.
 __global__ void k_dft_rows(const float* __restrict__ B, float2* X, const float2* __restrict__ w,
                            int nx, int ny) {
+  extern __shared__ float2 ws[];
+  for (int r = threadIdx.x; r < nx; r += blockDim.x) ws[r] = w[r];
+  __syncthreads();
   const int m = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (m >= nx || j >= ny) return;
   const float* b = B + (long long)j * nx;
   float re = 0.f, im = 0.f;
   int r = 0;
   for (int i = 0; i < nx; ++i) {
-    const float2 t = __ldg(w + r);
+    const float2 t = ws[r];
     const float v = __ldg(b + i);
     re += v * t.x;
     im += v * t.y;
@@ -1767,37 +1773,64 @@ __global__ void k_dft_rows(const float* __restrict__ B, float2* X, const float2*
   X[(long long)j * nx + m] = make_float2(re, im);
 }
 __global__ void k_dft_cols(const float2* __restrict__ X, float2* Y, const float2* __restrict__ w,
-                           int nx, int ny, int inverse, float scale) {
+                           int nx, int ny) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
   if (m >= nx || q >= ny) return;
   float re = 0.f, im = 0.f;
   int r = 0;
   for (int j = 0; j < ny; ++j) {
-    float2 t = __ldg(w + r);
-    if (inverse) t.y = -t.y;
+    const float2 t = __ldg(w + r);
     const float2 v = __ldg(X + (long long)j * nx + m);
     re += v.x * t.x - v.y * t.y;
     im += v.x * t.y + v.y * t.x;
     r += q;
     if (r >= ny) r -= ny;
   }
-  Y[(long long)q * nx + m] = make_float2(re * scale, im * scale);
+  Y[(long long)q * nx + m] = make_float2(re, im);
 }
-__global__ void k_idft_rows(const float2* __restrict__ Z, float* b, const float2* __restrict__ w,
-                            int nx, int ny, float scale) {
+__global__ void k_idft_cols2(const float2* __restrict__ P, const float2* __restrict__ Q,
+                             float2* ZP, float2* ZQ, const float2* __restrict__ w, int nx,
+                             int ny) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (m >= nx || j >= ny) return;
+  float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
+  int r = 0;
+  for (int q = 0; q < ny; ++q) {
+    float2 t = __ldg(w + r);
+    t.y = -t.y;                            // e^(+2 pi i q j / ny)
+    const float2 a = __ldg(P + (long long)q * nx + m), b = __ldg(Q + (long long)q * nx + m);
+    pr += a.x * t.x - a.y * t.y;
+    pi += a.x * t.y + a.y * t.x;
+    qr += b.x * t.x - b.y * t.y;
+    qi += b.x * t.y + b.y * t.x;
+    r += j;
+    if (r >= ny) r -= ny;
+  }
+  const float sc = 1.f / (float)ny;
+  ZP[(long long)j * nx + m] = make_float2(pr * sc, pi * sc);
+  ZQ[(long long)j * nx + m] = make_float2(qr * sc, qi * sc);
+}
+__global__ void k_idft_rows2(const float2* __restrict__ ZP, const float2* __restrict__ ZQ,
+                             float* bp, float* bq, const float2* __restrict__ w, int nx, int ny) {
+  extern __shared__ float2 ws[];
+  for (int r = threadIdx.x; r < nx; r += blockDim.x) ws[r] = w[r];
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= nx || j >= ny) return;
-  const float2* z = Z + (long long)j * nx;
-  float re = 0.f;
+  const float2* zp = ZP + (long long)j * nx;
+  const float2* zq = ZQ + (long long)j * nx;
+  float p = 0.f, q = 0.f;
   int r = 0;
   for (int m = 0; m < nx; ++m) {
-    const float2 t = __ldg(w + r);        // e^(+2 pi i m i / nx): the conjugate root
-    const float2 v = __ldg(z + m);
-    re += v.x * t.x + v.y * t.y;
+    const float2 t = ws[r];                // Re(z e^(+2 pi i m i / nx)) = z.x t.x + z.y t.y
+    const float2 a = __ldg(zp + m), b = __ldg(zq + m);
+    p += a.x * t.x + a.y * t.y;
+    q += b.x * t.x + b.y * t.y;
     r += i;
     if (r >= nx) r -= nx;
   }
-  b[(long long)j * nx + i] = re * scale;
+  bp[(long long)j * nx + i] = p / (float)nx;
+  bq[(long long)j * nx + i] = q / (float)nx;
 }
 // The horizontal potential field's spectrum from that of B_z (reading R27):
 // P_x = -i s (k_x/|k|) B^_z e^(-i pi m_x/nx) (the x faces half a cell below
@@ -1826,5 +1859,7 @@ __global__ void k_pot_sym(const float2* __restrict__ Y, float2* Px, float2* Py, 
   Px[o] = make_float2(qx.x * cx + qx.y * snx, qx.y * cx - qx.x * snx);
   Py[o] = make_float2(qy.x * cy + qy.y * sny, qy.y * cy - qy.x * sny);
 }
+
+#endif  // __CUDACC__
 
 }  // namespace stg
