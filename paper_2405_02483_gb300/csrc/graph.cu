@@ -81,6 +81,29 @@ __device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, in
   }
 }
 
+// The same stencil of the values v(idx) of a functor at the taps.
+template <typename T, class V>
+__device__ __forceinline__ T stencil_fn(V v, const GCell& c, int axis, int kind, T h,
+                                        const Geo& g) {
+  const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
+  const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
+  T m3 = v(nbr(c, axis, -3, g)), m2 = v(nbr(c, axis, -2, g)), m1 = v(nbr(c, axis, -1, g));
+  T z0 = v(c.idx), p1 = v(nbr(c, axis, 1, g)), p2 = v(nbr(c, axis, 2, g)),
+    p3 = v(nbr(c, axis, 3, g));
+  switch (kind) {
+    case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
+    case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
+    case ST_DDUP: return (DA * (p1 - z0) + DB * (p2 - m1) + DC * (p3 - m2)) / h;
+    default: return (DA * (z0 - m1) + DB * (p1 - m2) + DC * (p2 - m3)) / h;
+  }
+}
+// Transposed kind and sign of a stencil: up^T = dn, dn^T = up, ddup^T =
+// -dddn, dddn^T = -ddup (periodic summation by parts).
+__device__ __forceinline__ int st_transpose(int kind) {
+  return kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
+}
+__device__ __forceinline__ bool st_negates(int kind) { return kind == ST_DDUP || kind == ST_DDDN; }
+
 // ---------------------------------------------------------------------------
 // Quench, eq. (quench) with reading R8, as one node: out = T min(fac, qlim),
 // fac = the max over the node's axes of max3 along the axis of
@@ -232,6 +255,15 @@ __device__ __forceinline__ T fwd_value(int op, const GNode& nd, const T* A, cons
   const long long idx = c.idx;
   switch (op) {
     case G_STENCIL: return stencil_at(A, c, nd.axis, nd.sk, (T)nd.c0, g);
+    case G_STBIN: {
+      const T st = stencil_at(A, c, nd.axis, nd.sk, (T)nd.c0, g), b = B[idx];
+      if (nd.iop == G_MUL) return st * b;
+      if (nd.iop == G_ADD) return nd.side ? b + st : st + b;
+      return nd.side ? b - st : st - b;     // G_SUB
+    }
+    case G_STMUL:
+      return stencil_fn<T>([&](long long j) { return A[j] * B[j]; }, c, nd.axis, nd.sk,
+                           (T)nd.c0, g);
     case G_SHIFT: return A[nbr(c, nd.axis, nd.sk, g)];
     case G_ADD: return A[idx] + B[idx];
     case G_SUB: return A[idx] - B[idx];
@@ -284,9 +316,31 @@ __device__ __forceinline__ void bwd_value(int op, const GNode& nd, const T* A, c
     // Gather form of the transpose: up^T = dn, dn^T = up, ddup^T = -dddn,
     // dddn^T = -ddup (periodic summation by parts).
     int kind = nd.sk;
-    int tk = kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
-    T v = stencil_at(gout, c, nd.axis, tk, (T)nd.c0, g);
-    ca = (kind == ST_DDUP || kind == ST_DDDN) ? -v : v;
+    T v = stencil_at(gout, c, nd.axis, st_transpose(kind), (T)nd.c0, g);
+    ca = st_negates(kind) ? -v : v;
+  } else if (op == G_STBIN) {
+    // y = st(a) (op) b: the stencil's transpose of the cotangent of st(a),
+    // which is g (add), -+g (sub) or g b (mul) at each tap.
+    const int tk = st_transpose(nd.sk);
+    const T sg = st_negates(nd.sk) ? (T)-1 : (T)1;
+    const T gg = gout[idx];
+    if (nd.iop == G_MUL) {
+      ca = sg * stencil_fn<T>([&](long long j) { return gout[j] * B[j]; }, c, nd.axis, tk,
+                              (T)nd.c0, g);
+      cb = gg * stencil_at(A, c, nd.axis, nd.sk, (T)nd.c0, g);
+    } else {
+      const T v = sg * stencil_at(gout, c, nd.axis, tk, (T)nd.c0, g);
+      const bool neg_st = nd.iop == G_SUB && nd.side;    // b - st
+      const bool neg_b = nd.iop == G_SUB && !nd.side;    // st - b
+      ca = neg_st ? -v : v;
+      cb = neg_b ? -gg : gg;
+    }
+  } else if (op == G_STMUL) {
+    // y = st(a b): the transposed stencil of g, times the other factor.
+    T v = stencil_at(gout, c, nd.axis, st_transpose(nd.sk), (T)nd.c0, g);
+    if (st_negates(nd.sk)) v = -v;
+    ca = v * B[idx];
+    cb = v * A[idx];
   } else if (op == G_SHIFT) {
     ca = gout[nbr(c, nd.axis, -nd.sk, g)];
   } else {
@@ -399,6 +453,72 @@ __global__ void g_add_into(T* dst, const T* src, long long n) {
 // The right-hand side, eqs. (mass), (mom), (itv), (ien), (vdiss), (indu),
 // (ohm), written on the stored deviations f' (full value ref + f').
 // ---------------------------------------------------------------------------
+// Every node is a whole-array pass whose launch, ramp and tail cost as much as
+// its bytes, so a stencil that feeds one sum, difference or product, and a
+// product that feeds one stencil, are merged into one node (G_STBIN, G_STMUL):
+// the pair's intermediate array and launches go away, and the fused node's
+// transpose is the pair's (the stencil's gather-form transpose of the
+// cotangent, times the other factor where there is one).  A node used twice,
+// or as an output, keeps its array.  The graph is then compacted.
+static void fuse_stencil_pairs(GraphDef& G) {
+  const int nn = (int)G.nodes.size();
+  std::vector<int> uses(nn, 0);
+  for (const GNode& nd : G.nodes) {
+    if (nd.a >= 0) ++uses[nd.a];
+    if (nd.b >= 0) ++uses[nd.b];
+  }
+  for (int k = 0; k < 8; ++k) uses[G.out[k]] += 2;   // outputs keep their arrays
+  std::vector<char> dead(nn, 0);
+  for (int i = 0; i < nn; ++i) {
+    GNode& nd = G.nodes[i];
+    if (nd.op == G_ADD || nd.op == G_SUB || nd.op == G_MUL) {
+      for (int side = 0; side < 2; ++side) {
+        const int src = side == 0 ? nd.a : nd.b;
+        if (src < 0 || dead[src] || G.nodes[src].op != G_STENCIL || uses[src] != 1) continue;
+        const GNode st = G.nodes[src];
+        GNode f = nd;
+        f.op = G_STBIN;
+        f.iop = nd.op;
+        f.side = side;
+        f.a = st.a;
+        f.b = side == 0 ? nd.b : nd.a;
+        f.axis = st.axis;
+        f.sk = st.sk;
+        f.c0 = st.c0;
+        f.c1 = 0;
+        nd = f;
+        dead[src] = 1;
+        break;
+      }
+    } else if (nd.op == G_STENCIL && nd.a >= 0 && !dead[nd.a] && G.nodes[nd.a].op == G_MUL &&
+               uses[nd.a] == 1) {
+      const GNode m = G.nodes[nd.a];
+      dead[nd.a] = 1;
+      nd.op = G_STMUL;
+      nd.a = m.a;
+      nd.b = m.b;
+    }
+  }
+  // Compact: drop the absorbed nodes and renumber every reference.
+  std::vector<int> id(nn, -1);
+  std::vector<GNode> kept;
+  for (int i = 0; i < nn; ++i)
+    if (!dead[i]) {
+      id[i] = (int)kept.size();
+      kept.push_back(G.nodes[i]);
+    }
+  for (GNode& nd : kept) {
+    if (nd.a >= 0) nd.a = id[nd.a];
+    if (nd.b >= 0) nd.b = id[nd.b];
+  }
+  for (int k = 0; k < 8; ++k) {
+    G.in[k] = id[G.in[k]];
+    G.out[k] = id[G.out[k]];
+  }
+  G.nodes.swap(kept);
+  G.memo.clear();
+}
+
 void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& p) {
   G.nodes.clear();
   G.memo.clear();
@@ -738,6 +858,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
 
   int outs[8] = {d_r, d_px, d_py, d_pz, d_E, d_Bx, d_By, d_Bz};
   for (int k = 0; k < 8; ++k) G.out[k] = outs[k];
+  fuse_stencil_pairs(G);
 }
 
 // ---------------------------------------------------------------------------
@@ -868,6 +989,8 @@ static FwdK<T> fwd_kernel(int op) {
   switch (op) {
     case G_STENCIL: return g_forward<T, G_STENCIL>;
     case G_SHIFT: return g_forward<T, G_SHIFT>;
+    case G_STBIN: return g_forward<T, G_STBIN>;
+    case G_STMUL: return g_forward<T, G_STMUL>;
     case G_ADD: return g_forward<T, G_ADD>;
     case G_SUB: return g_forward<T, G_SUB>;
     case G_MUL: return g_forward<T, G_MUL>;
@@ -892,6 +1015,8 @@ static BwdK<T> bwd_kernel(int op) {
   switch (op) {
     case G_STENCIL: return g_backward<T, G_STENCIL>;
     case G_SHIFT: return g_backward<T, G_SHIFT>;
+    case G_STBIN: return g_backward<T, G_STBIN>;
+    case G_STMUL: return g_backward<T, G_STMUL>;
     case G_ADD: return g_backward<T, G_ADD>;
     case G_SUB: return g_backward<T, G_SUB>;
     case G_MUL: return g_backward<T, G_MUL>;

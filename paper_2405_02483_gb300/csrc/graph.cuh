@@ -20,7 +20,12 @@ enum GOp {
   G_STEP,  // 1 where a > c0, else 0 (a switch: no gradient)
   G_ZFIELD, // a mesh array over z (sk: 0 1/dz_c, 1 1/dz_f, 2 dz_c, 3 dz_f, 4 local dl_min)
   G_PMEAN,  // mean of a over the horizontal plane (constant z) of each cell
-  G_QUENCH  // eq. (quench) of a over axes axis and sk (-1: one axis); c0 qmax, c1 qlim, c2 eps
+  G_QUENCH, // eq. (quench) of a over axes axis and sk (-1: one axis); c0 qmax, c1 qlim, c2 eps
+  // Fused pairs (formed after the build, see fuse_stencil_pairs): a stencil
+  // (kind sk, axis, spacing c0) of a combined with b by iop (G_ADD, G_SUB,
+  // G_MUL; side 1: b comes first), and a stencil of the product a b.
+  G_STBIN,
+  G_STMUL
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -31,6 +36,8 @@ struct GNode {
   int sk;       // GStencil kind, or shift distance
   double c0, c1;  // scalars: spacing h (derivative), a*x+b, clamp bound, const
   double c2 = 0;  // G_QUENCH: weight of max3|T| added to |T| (< 0: max3|T| alone)
+  int iop = 0;    // G_STBIN: the binary op
+  int side = 0;   // G_STBIN: 1 when the stencil is the second operand
 };
 
 // Precision-independent description of the graph.
