@@ -716,12 +716,18 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
     kern[1] = v4 ? k_div<Nb4Z, 0x11, false> : k_div<NbZ, 0x11, false>;
     kern[2] = v4 ? k_div<Nb4Z, 0xE0, false> : k_div<NbZ, 0xE0, false>;
   } else {
-    kern[0] = v4 ? k_div<Nb4, 0x0E, false> : k_div<Nb, 0x0E, false>;
-    if (cfl)   // and the rate maximum (cmax[1])
-      kern[1] = v4 ? k_div<Nb4, 0x11, true> : k_div<Nb, 0x11, true>;
-    else
-      kern[1] = v4 ? k_div<Nb4, 0x11, false> : k_div<Nb, 0x11, false>;
-    kern[2] = v4 ? k_div<Nb4, 0xE0, false> : k_div<Nb, 0xE0, false>;
+    if (F.wall >= 2) {   // rigid or stellar-atmosphere walls: the boundary branches
+      kern[0] = v4 ? k_div<Nb4, 0x0E, false, true> : k_div<Nb, 0x0E, false, true>;
+      kern[1] = v4 ? k_div<Nb4, 0x11, false, true> : k_div<Nb, 0x11, false, true>;
+      kern[2] = v4 ? k_div<Nb4, 0xE0, false, true> : k_div<Nb, 0xE0, false, true>;
+    } else {
+      kern[0] = v4 ? k_div<Nb4, 0x0E, false> : k_div<Nb, 0x0E, false>;
+      if (cfl)   // and the rate maximum (cmax[1])
+        kern[1] = v4 ? k_div<Nb4, 0x11, true> : k_div<Nb, 0x11, true>;
+      else
+        kern[1] = v4 ? k_div<Nb4, 0x11, false> : k_div<Nb, 0x11, false>;
+      kern[2] = v4 ? k_div<Nb4, 0xE0, false> : k_div<Nb, 0xE0, false>;
+    }
   }
   for (int i = 0; i < nk; ++i)
     TIMED(K_DIV, (kern[i]<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],

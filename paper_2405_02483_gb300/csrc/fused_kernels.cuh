@@ -1113,15 +1113,16 @@ __device__ __forceinline__ typename N::T lnp_grad(const N& n, const float* lq, c
 // inputs are disjoint, at 4 blocks per SM: fewer live registers per launch.
 // With CR (mass and energy, the stage whose derivative sets the Courant step)
 // the launch also reduces max(|dr/dt| / r, |dE/dt| / E) into *cr.
-template <class N, int M, bool CR>
+template <class N, int M, bool CR, bool WB = false>
 __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float* const* qs,
                                              float* const* os, float alpha, float beta,
                                              const double* dtp, int mode, const KPar& k) {
   using T = typename N::T;
   const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
-  // Rigid (R25) and stellar-atmosphere (R26) z walls: the time derivatives of
-  // the ghost planes are zero (z faces klo and below are ghosts with R26).
-  const bool ghostC = k.wall >= 2 && (n.kz < k.klo || n.kz > k.khi);
+  // Rigid (R25) and stellar-atmosphere (R26) z walls (compiled in with WB):
+  // the time derivatives of the ghost planes are zero (z faces klo and below
+  // are ghosts with R26).
+  const bool ghostC = WB && k.wall >= 2 && (n.kz < k.klo || n.kz > k.khi);
   const bool ghostF = k.wall == 3 ? (n.kz <= k.klo || n.kz > k.khi) : ghostC;
   T F0 = 0.f, F4 = 0.f;
   auto fin = [&](int c, const T& Fc) {
@@ -1134,7 +1135,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   };
   // Stellar-atmosphere boundaries (R26): the inflow weight f of the bottom
   // plane's column, from the outward velocity on its inside z face.
-  const bool obot = k.wall == 3 && n.kz == k.obot;
+  const bool obot = WB && k.wall == 3 && n.kz == k.obot;
   auto open_f = [&]() {
     // constant offsets: a run-time one would put the cell's index tables in local memory
     const T ui = k.osb < 0 ? n.lda(in.uz, 2, 1) : n.lda(in.uz, 2, 0);
@@ -1144,7 +1145,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   if (M & 1) {   // eq. (mass)
     const T dxy = s_du(AX(in.px, 0), n.ju(0, k)) + s_du(AX(in.py, 1), n.ju(1, k));
     Fm = -(dxy + s_du(AX(in.pz, 2), n.ju(2, k)));
-    if (k.wall == 3 && n.kz == k.otop) {
+    if (WB && k.wall == 3 && n.kz == k.otop) {
       // eq. (rbdrylo): the vertical divergence becomes the outward-signed
       // mass flux over the pressure scale height (gamma - 1) e / |g_z|.
       const T r = n.ld(in.f[0]) + k.r0, E = n.ld(in.f[4]) + k.E0;
@@ -1203,7 +1204,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   // eq. (indu): dB/dt = -curl E
   // R27: the top plane's horizontal field relaxes toward the potential field
   // (targets and plane means from the boundary fill).
-  const bool opot = k.wall == 3 && n.kz == k.otop && k.oinv_tpot > 0.f;
+  const bool opot = WB && k.wall == 3 && n.kz == k.otop && k.oinv_tpot > 0.f;
   if (M & 32) {
     T t = -(s_du(AX(in.Ez, 1), n.ju(1, k)) - s_du(AX(in.Ey, 2), n.ju(2, k)));
     if (opot) t += (n.ldpl(k.bpx) - (n.ld(in.f[5]) - (float)k.omean[k.klo + 2])) * k.oinv_tpot;
@@ -1220,7 +1221,7 @@ __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float*
   return max_bits(fmaxf(fabsf(F0) / r, fabsf(F4) / E));
 }
 
-template <class N, int M, bool CR>
+template <class N, int M, bool CR, bool WB = false>
 __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, float* q2, float* q3,
                                           float* q4, float* q5, float* q6, float* q7,
                                           float* o0, float* o1, float* o2, float* o3,
@@ -1232,7 +1233,7 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
   float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
   float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
   if constexpr (!CR) {
-    if (inside) div_cell<N, M, false>(n, in, qs, os, alpha, beta, dtp, mode, k);
+    if (inside) div_cell<N, M, false, WB>(n, in, qs, os, alpha, beta, dtp, mode, k);
   } else {
     const unsigned m = inside ? div_cell<N, M, true>(n, in, qs, os, alpha, beta, dtp, mode, k) : 0u;
     block_max_to<>(m, cr);
