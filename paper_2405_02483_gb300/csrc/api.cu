@@ -27,7 +27,9 @@ struct stagger_ctx {
   cudaGraphExec_t adj_exec[2] = {nullptr, nullptr};
   long long adj_launches[2] = {0, 0};
   cudaStream_t cap = nullptr;
-  double* dtp = nullptr;   // the step dt on the device (read by the captured graph)
+  double* dtp = nullptr;   // the step dt on the device (read by the captured graph),
+                           // then beta_s dt of the three RK stages
+  float* bdtf = nullptr;   // beta_s dt in FP32
   double* omean_g = nullptr;  // plane means and parts of the op graph's open boundaries
 };
 
@@ -178,6 +180,7 @@ int stagger_destroy(stagger_ctx* c) {
     if (c->adj_exec[i]) cudaGraphExecDestroy(c->adj_exec[i]);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->dtp) cudaFree(c->dtp);
+  if (c->bdtf) cudaFree(c->bdtf);
   if (c->omean_g) cudaFree(c->omean_g);
   delete c;
   return e == cudaSuccess ? STAGGER_OK : STAGGER_ECUDA;
@@ -285,20 +288,29 @@ int stagger_diagnostics(stagger_ctx* c, float* const state[8], double out[10], v
 // ---------------------------------------------------------------------------
 // Unfused graph path and the adjoint step.
 // ---------------------------------------------------------------------------
+// The scalars come in the sweep's precision (a conversion from double, or a
+// double product, runs on the narrow FP64 pipe: not once per thread).
 template <typename T>
-__global__ void k_lin2(T* o, const T* x, double a, const T* y, double b, long long n) {
+__global__ void k_lin2(T* o, const T* x, T a, const T* y, T b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = (T)a * x[i] + (T)b * y[i];
+  if (i < n) o[i] = a * x[i] + b * y[i];
 }
-// o = a x + (bB * dt) y with dt read on the device (the adjoint's graph
-// replays with any dt).
+// o = a x + (beta_s dt) y with beta_s dt read on the device (the adjoint's
+// graph replays with any dt).
 template <typename T>
-__global__ void k_lin2d(T* o, const T* x, double a, const T* y, double bB, const double* dtp,
-                        long long n) {
+__global__ void k_lin2d(T* o, const T* x, T a, const T* y, const T* bdt, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = (T)a * x[i] + (T)(bB * dtp[0]) * y[i];
+  if (i < n) o[i] = a * x[i] + bdt[0] * y[i];
 }
-__global__ void k_set_scalar(double* p, double v) { p[0] = v; }
+// dt, and beta_s dt of the three RK stages in FP64 and FP32.
+__global__ void k_set_dt3(double* dtp, float* bdtf, double dt, double b0, double b1, double b2) {
+  const double b[3] = {b0, b1, b2};
+  dtp[0] = dt;
+  for (int s = 0; s < 3; ++s) {
+    dtp[1 + s] = b[s] * dt;
+    bdtf[s] = (float)(b[s] * dt);
+  }
+}
 template <typename T>
 __global__ void k_copy(T* o, const T* x, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -658,14 +670,18 @@ static int ensure_work(stagger_ctx* c) {
 template <typename T>
 static void lin2(stagger_ctx* c, T* o, const T* x, double a, const T* y, double b, cudaStream_t s) {
   long long n = c->geo.n;
-  k_lin2<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, a, y, b, n);
+  k_lin2<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, (T)a, y, (T)b, n);
   ++c->extra_launches;
 }
+// o = a x + beta_st dt y (k_set_dt3 has written beta_st dt).
 template <typename T>
-static void lin2d(stagger_ctx* c, T* o, const T* x, double a, const T* y, double bB,
+static void lin2d(stagger_ctx* c, T* o, const T* x, double a, const T* y, int st,
                   cudaStream_t s) {
   long long n = c->geo.n;
-  k_lin2d<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, a, y, bB, c->dtp, n);
+  const T* bdt;
+  if constexpr (sizeof(T) == sizeof(float)) bdt = c->bdtf + st;
+  else bdt = c->dtp + 1 + st;
+  k_lin2d<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, (T)a, y, bdt, n);
   ++c->extra_launches;
 }
 
@@ -760,31 +776,31 @@ static int adjoint_body(stagger_ctx* c, T* const f0[8], T* const lam_in[8], T* l
     fb[k] = w + (size_t)(24 + k) * n;
     qb[k] = w + (size_t)(32 + k) * n;
   }
-  const double *A = RK_ALPHA, *B = RK_BETA;
+  const double* A = RK_ALPHA;
   int rc;
   // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)); the FP32
   // path takes F from the fused kernels, FP64 from the graph.
   if ((rc = stage_rhs<T>(c, G, f0, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, q[k], fb[k], 1.0, fb[k], 0.0, s);
-    lin2d<T>(c, f1[k], f0[k], 1.0, q[k], B[0], s);
+    lin2d<T>(c, f1[k], f0[k], 1.0, q[k], 0, s);
   }
   if ((rc = stage_rhs<T>(c, G, f1, fb, s))) return rc;
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, q[k], q[k], A[1], fb[k], 1.0, s);
-    lin2d<T>(c, f2[k], f1[k], 1.0, q[k], B[1], s);
+    lin2d<T>(c, f2[k], f1[k], 1.0, q[k], 1, s);
   }
   // Reverse sweep: fbar_3 = lam; qbar_3 = beta_3 dt fbar.
   for (int k = 0; k < 8; ++k) {
     lin2<T>(c, fb[k], lam_in[k], 1.0, lam_in[k], 0.0, s);
-    lin2d<T>(c, qb[k], fb[k], 0.0, fb[k], B[2], s);
+    lin2d<T>(c, qb[k], fb[k], 0.0, fb[k], 2, s);
   }
   T* const* stages[3] = {f0, f1, f2};
   for (int st = 2; st >= 0; --st) {
     if ((rc = G->forward(stages[st], s))) return rc;
     if ((rc = G->backward(qb, fb, s))) return rc;     // fbar += J(f_st)^T qbar
     if (st > 0)                                         // qbar_{st} = alpha qbar + beta dt fbar
-      for (int k = 0; k < 8; ++k) lin2d<T>(c, qb[k], qb[k], A[st], fb[k], B[st - 1], s);
+      for (int k = 0; k < 8; ++k) lin2d<T>(c, qb[k], qb[k], A[st], fb[k], st - 1, s);
   }
   for (int k = 0; k < 8; ++k) lin2<T>(c, lam_out[k], fb[k], 1.0, fb[k], 0.0, s);
   STG_CUDA_OK(cudaGetLastError());
@@ -807,11 +823,15 @@ static int graph_step_adjoint(stagger_ctx* c, T* const f0[8], double dt, T* cons
   if (rc) return rc;
   rc = ensure_work<T>(c);
   if (rc) return rc;
-  if (!c->dtp && cudaMalloc(&c->dtp, sizeof(double)) != cudaSuccess) {
+  if (!c->dtp && cudaMalloc(&c->dtp, sizeof(double) * 4) != cudaSuccess) {
     c->dtp = nullptr;
     return STAGGER_EOOM;
   }
-  k_set_scalar<<<1, 1, 0, s>>>(c->dtp, dt);
+  if (!c->bdtf && cudaMalloc(&c->bdtf, sizeof(float) * 4) != cudaSuccess) {
+    c->bdtf = nullptr;
+    return STAGGER_EOOM;
+  }
+  k_set_dt3<<<1, 1, 0, s>>>(c->dtp, c->bdtf, dt, RK_BETA[0], RK_BETA[1], RK_BETA[2]);
   ++c->extra_launches;
   const int pi = sizeof(T) == sizeof(float) ? 0 : 1;
   const long long n = c->geo.n;

@@ -237,6 +237,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
   for (int i = 0; i < F_COUNT; ++i) F.fld[i] = nullptr;
   for (int c = 0; c < 8; ++c) F.q[c] = F.ping[c] = F.pong[c] = nullptr;
   F.dt_dev = nullptr;
+  F.bdt_dev = nullptr;
   F.red = nullptr;
   F.cmax = nullptr;
   F.d2flag = nullptr;
@@ -388,6 +389,7 @@ int fused_init(Fused& F, const stagger_grid& gr, const stagger_params& p) {
     return STAGGER_EOOM;
   }
   if (cudaMalloc(&F.dt_dev, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc(&F.bdt_dev, sizeof(float) * 4) != cudaSuccess ||
       cudaMalloc(&F.red, sizeof(double) * 10 * (size_t)F.red_blocks) != cudaSuccess) {
     fused_release(F);
     return STAGGER_EOOM;
@@ -412,6 +414,7 @@ void fused_release(Fused& F) {
     F.q[c] = F.ping[c] = F.pong[c] = nullptr;
   }
   if (F.dt_dev) cudaFree(F.dt_dev);
+  if (F.bdt_dev) cudaFree(F.bdt_dev);
   if (F.red) cudaFree(F.red);
   if (F.cmax) cudaFree(F.cmax);
   F.cmax = nullptr;
@@ -428,6 +431,7 @@ void fused_release(Fused& F) {
   if (F.pot) cudaFree(F.pot);
   F.pot = nullptr;
   F.dt_dev = nullptr;
+  F.bdt_dev = nullptr;
   F.red = nullptr;
 }
 
@@ -669,7 +673,7 @@ static FdIn fdiv_in(Fused& F, float* const f[8]) {
 #endif
 
 static int launch_fdiv(Fused& F, float* const f[8], float* q[8], float* const* oo, float alpha,
-                       float beta, int mode, cudaStream_t s, bool cfl) {
+                       int stg, int mode, cudaStream_t s, bool cfl) {
   const Geo& g = F.geo;
   const FdIn in = fdiv_in(F, f);
   const dim3 bb(FD_TX, FD_TY),
@@ -677,7 +681,7 @@ static int launch_fdiv(Fused& F, float* const f[8], float* q[8], float* const* o
          (unsigned)((g.nz + FD_ZC - 1) / FD_ZC));
   typedef void (*FdK)(FdIn, float*, float*, float*, float*, float*, float*, float*, float*,
                       float*, float*, float*, float*, float*, float*, float*, float*, float,
-                      float, const double*, int, unsigned*, KPar, Geo);
+                      const float*, int, unsigned*, KPar, Geo);
   FdK kern;
   if (F.kp.visc)
     kern = cfl ? k_fdiv<FD_TY, true, true> : k_fdiv<FD_TY, true, false>;
@@ -688,17 +692,19 @@ static int launch_fdiv(Fused& F, float* const f[8], float* q[8], float* const* o
     STG_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TIMED(K_FDIV, (kern<<<gg, bb, smem, s>>>(in, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
                                         oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6], oo[7],
-                                        alpha, beta, F.dt_dev, mode, F.cmax + 1, F.kp, g)));
+                                        alpha, F.bdt_dev + stg, mode, F.cmax + 1, F.kp, g)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }
 
+// Stage stg's right-hand side into q (mode 0), or with the update by its
+// beta dt (mode 1: F.bdt_dev[stg]).
 static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], float alpha,
-                      float beta, int mode, cudaStream_t s, bool cfl = false) {
+                      int stg, int mode, cudaStream_t s, bool cfl = false) {
   if (F.fdiv) {
     float* oo[8];
     for (int c = 0; c < 8; ++c) oo[c] = o ? o[c] : q[c];
-    return launch_fdiv(F, f, q, oo, alpha, beta, mode, s, cfl);
+    return launch_fdiv(F, f, q, oo, alpha, stg, mode, s, cfl);
   }
   DivIn di = div_in(F, f);
   float* oo[8];
@@ -709,7 +715,7 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   const int nk = 3;
   typedef void (*DivK)(DivIn, float*, float*, float*, float*, float*, float*, float*, float*,
                        float*, float*, float*, float*, float*, float*, float*, float*, float,
-                       float, const double*, int, unsigned*, KPar, Geo);
+                       const float*, int, unsigned*, KPar, Geo);
   DivK kern[3];
   if (F.zs) {
     kern[0] = v4 ? k_div<Nb4Z, 0x0E, false> : k_div<NbZ, 0x0E, false>;
@@ -732,7 +738,7 @@ static int launch_div(Fused& F, float* const f[8], float* q[8], float* o[8], flo
   for (int i = 0; i < nk; ++i)
     TIMED(K_DIV, (kern[i]<<<gg, bb, 0, s>>>(di, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7],
                                             oo[0], oo[1], oo[2], oo[3], oo[4], oo[5], oo[6],
-                                            oo[7], alpha, beta, F.dt_dev, mode, F.cmax + 1,
+                                            oo[7], alpha, F.bdt_dev + stg, mode, F.cmax + 1,
                                             F.kp, F.geo)));
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
@@ -742,7 +748,7 @@ int fused_rhs(Fused& F, float* const f[8], float* out[8], cudaStream_t s) {
   if (F.wall) wall_launch(F, f, false, s);
   int st = pre_div(F, f, s);
   if (st) return st;
-  st = launch_div(F, f, out, nullptr, 0.f, 0.f, 0, s);
+  st = launch_div(F, f, out, nullptr, 0.f, 0, 0, s);
   if (st) return st;
   if (F.wall) wall_launch(F, out, true, s);
   STG_CUDA_OK(cudaGetLastError());
@@ -768,9 +774,10 @@ static int courant_to_dev(Fused& F, float* const f[8], cudaStream_t s, bool fuse
   }
   // A stretched z reduces w / dl and nu / dl per cell: the final pass then
   // takes dl = 1 and a velocity-like nu.
-  TIMED(K_COURANT, (k_courant_final<<<1, 32, 0, s>>>(F.cmax, F.dt_dev, F.cdt, F.cdtr, F.cdtd,
-                                                     F.zs ? 1.0 : F.dlmin, F.dfac,
-                                                     F.zs ? 1 : F.kp.rm)));
+  TIMED(K_COURANT, (k_courant_final<<<1, 32, 0, s>>>(
+                        F.cmax, F.dt_dev, F.bdt_dev, (float)RK_BETA[0], (float)RK_BETA[1],
+                        (float)RK_BETA[2], F.cdt, F.cdtr, F.cdtd, F.zs ? 1.0 : F.dlmin, F.dfac,
+                        F.zs ? 1 : F.kp.rm)));
   return STAGGER_OK;
 }
 
@@ -787,10 +794,10 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
     if (F.wall) wall_launch(F, st_in[stg], false, s);
     int rc = pre_div(F, st_in[stg], s, cfl);
     if (rc) return rc;
-    float alpha = (float)RK_ALPHA[stg], beta = (float)RK_BETA[stg];
+    const float alpha = (float)RK_ALPHA[stg];
     if (stg == 0 && dt <= 0) {
       // Courant step from the state and its stage-1 derivative, then update.
-      rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0.f, 0, s, cfl);
+      rc = launch_div(F, st_in[0], F.q, nullptr, 0.f, 0, 0, s, cfl);
       if (rc) return rc;
       courant_to_dev(F, st_in[0], s, cfl);
       Upd8 u;
@@ -804,14 +811,15 @@ int fused_step(Fused& F, float* f[8], double dt, cudaStream_t s) {
       const long long work = vec ? F.geo.n / 4 : F.geo.n;
       unsigned bx = (unsigned)((work + 255) / 256);
       if (bx > 2048) bx = 2048;
-      TIMED(K_UPDATE, (k_update8<<<dim3(bx, 8), 256, 0, s>>>(u, beta, F.dt_dev, F.geo.n, vec)));
+      TIMED(K_UPDATE, (k_update8<<<dim3(bx, 8), 256, 0, s>>>(u, F.bdt_dev, F.geo.n, vec)));
       STG_CUDA_OK(cudaGetLastError());
       continue;
     }
     if (stg == 0 && dt > 0) {
-      TIMED(K_MISC, (k_set_dt<<<1, 1, 0, s>>>(F.dt_dev, dt)));
+      TIMED(K_MISC, (k_set_dt<<<1, 1, 0, s>>>(F.dt_dev, F.bdt_dev, dt, (float)RK_BETA[0],
+                                              (float)RK_BETA[1], (float)RK_BETA[2])));
     }
-    rc = launch_div(F, st_in[stg], F.q, const_cast<float**>(st_out[stg]), alpha, beta, 1, s);
+    rc = launch_div(F, st_in[stg], F.q, const_cast<float**>(st_out[stg]), alpha, stg, 1, s);
     if (rc) return rc;
   }
   if (F.wall) wall_launch(F, f, false, s, false);
@@ -824,7 +832,7 @@ int fused_dt(Fused& F, float* const f[8], cudaStream_t s) {
   if (F.wall) wall_launch(F, f, false, s);
   int rc = pre_div(F, f, s, cfl);
   if (rc) return rc;
-  rc = launch_div(F, f, F.q, nullptr, 0.f, 0.f, 0, s, cfl);
+  rc = launch_div(F, f, F.q, nullptr, 0.f, 0, 0, s, cfl);
   if (rc) return rc;
   courant_to_dev(F, f, s, cfl);
   STG_CUDA_OK(cudaGetLastError());

@@ -101,6 +101,7 @@ struct Fused {
   float* pong[8];
   double cdt, cdtr, cdtd, dlmin, dfac;  // Courant factors, dl_min, diffusion factor
   double* dt_dev;       // device step and the three limits
+  float* bdt_dev;       // beta_s dt of the three RK stages, in FP32, written with dt_dev[0]
   double* red;          // reduction partials (diagnostics)
   unsigned* cmax;       // Courant maxima as float bits, cleared by each final pass
   unsigned char* d2flag;  // second-order switch flags per cell (bit = axis), or null

@@ -1108,17 +1108,17 @@ __device__ __forceinline__ typename N::T lnp_grad(const N& n, const float* lq, c
 
 // F(f) and the RK update: q <- alpha q + F, f_out <- f + beta dt q, for the
 // fields in the bit mask M (bit c: field c), each stored as soon as it is
-// formed.  mode 0: write F to q only; 1: also update with dt from *dtp.
+// formed.  mode 0: write F to q only; 1: also update with beta dt = *bdtp.
 // Launched as three kernels (momentum; mass and energy; induction), whose
 // inputs are disjoint, at 4 blocks per SM: fewer live registers per launch.
 // With CR (mass and energy, the stage whose derivative sets the Courant step)
 // the launch also reduces max(|dr/dt| / r, |dE/dt| / E) into *cr.
 template <class N, int M, bool CR, bool WB = false>
 __device__ __forceinline__ unsigned div_cell(const N& n, const DivIn& in, float* const* qs,
-                                             float* const* os, float alpha, float beta,
-                                             const double* dtp, int mode, const KPar& k) {
+                                             float* const* os, float alpha,
+                                             const float* bdtp, int mode, const KPar& k) {
   using T = typename N::T;
-  const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
+  const float bdt = mode ? bdtp[0] : 0.f;
   // Rigid (R25) and stellar-atmosphere (R26) z walls (compiled in with WB):
   // the time derivatives of the ghost planes are zero (z faces klo and below
   // are ghosts with R26).
@@ -1226,21 +1226,32 @@ __global__ void STG_LB_4(N, STG_MINB) k_div(DivIn in, float* q0, float* q1, floa
                                           float* q4, float* q5, float* q6, float* q7,
                                           float* o0, float* o1, float* o2, float* o3,
                                           float* o4, float* o5, float* o6, float* o7,
-                                          float alpha, float beta, const double* dtp,
+                                          float alpha, const float* bdtp,
                                           int mode, unsigned* cr, KPar k, Geo g) {
   N n;
   const bool inside = n.init(g, k);
   float* qs[8] = {q0, q1, q2, q3, q4, q5, q6, q7};
   float* os[8] = {o0, o1, o2, o3, o4, o5, o6, o7};
   if constexpr (!CR) {
-    if (inside) div_cell<N, M, false, WB>(n, in, qs, os, alpha, beta, dtp, mode, k);
+    if (inside) div_cell<N, M, false, WB>(n, in, qs, os, alpha, bdtp, mode, k);
   } else {
-    const unsigned m = inside ? div_cell<N, M, true>(n, in, qs, os, alpha, beta, dtp, mode, k) : 0u;
+    const unsigned m = inside ? div_cell<N, M, true>(n, in, qs, os, alpha, bdtp, mode, k) : 0u;
     block_max_to<>(m, cr);
   }
 }
 
-__global__ void k_set_dt(double* dtp, double dt) { dtp[0] = dt; }
+// The step dt, and beta_s dt of the three RK stages in FP32 (formed once
+// here: a conversion from double runs on the narrow FP64 pipe, so the update
+// kernels read the float product instead of forming it per thread).
+__device__ __forceinline__ void set_bdt(float* bdt, double dt, float b0, float b1, float b2) {
+  bdt[0] = (float)((double)b0 * dt);
+  bdt[1] = (float)((double)b1 * dt);
+  bdt[2] = (float)((double)b2 * dt);
+}
+__global__ void k_set_dt(double* dtp, float* bdt, double dt, float b0, float b1, float b2) {
+  dtp[0] = dt;
+  set_bdt(bdt, dt, b0, b1, b2);
+}
 
 // f_out = f + beta dt q for the 8 fields in one launch (blockIdx.y = field),
 // 16-byte vectors when every array is 16-byte aligned and n % 4 == 0.
@@ -1249,9 +1260,9 @@ struct Upd8 {
   const float* q[8];
   float* o[8];
 };
-__global__ void k_update8(Upd8 u, float beta, const double* dtp, long long n, int vec) {
+__global__ void k_update8(Upd8 u, const float* bdtp, long long n, int vec) {
   const int c = blockIdx.y;
-  const float bdt = (float)((double)beta * dtp[0]);
+  const float bdt = bdtp[0];
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (vec) {
@@ -1389,8 +1400,9 @@ __global__ void __launch_bounds__(BX * BY * BZ, N::W == 4 ? STG_MINB : STG_MINB_
 
 // dt = min(Cdt dl/wmax, Cdtr/ratemax, Cdtd dl/(numax f)) in FP64 from the
 // three maxima, which it then clears for the next reduction.
-__global__ void k_courant_final(unsigned* cmax, double* dt_out, double cdt, double cdtr,
-                                double cdtd, double dlmin, double dfac, int nu_is_velocity) {
+__global__ void k_courant_final(unsigned* cmax, double* dt_out, float* bdt, float b0, float b1,
+                                float b2, double cdt, double cdtr, double cdtd, double dlmin,
+                                double dfac, int nu_is_velocity) {
   if (threadIdx.x != 0) return;
   const double wmax = (double)__uint_as_float(cmax[0]);
   const double rmax = (double)__uint_as_float(cmax[1]);
@@ -1402,6 +1414,7 @@ __global__ void k_courant_final(unsigned* cmax, double* dt_out, double cdt, doub
   double td = nv > 0 ? cdtd * dlmin / (nv * dfac) : HUGE_VAL;
   double dt = fmin(tw, fmin(tr, td));
   dt_out[0] = dt;
+  set_bdt(bdt, dt, b0, b1, b2);
   dt_out[1] = tw;
   dt_out[2] = tr;
   dt_out[3] = td;

@@ -25,7 +25,10 @@ enum GOp {
   // (kind sk, axis, spacing c0) of a combined with b by iop (G_ADD, G_SUB,
   // G_MUL; side 1: b comes first), and a stencil of the product a b.
   G_STBIN,
-  G_STMUL
+  G_STMUL,
+  // The sum or difference (iop) of two stencils: (kind sk, axis, spacing c0)
+  // of a and (kind sk2, axis2, spacing h2) of b.
+  G_ST2
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 
@@ -38,6 +41,16 @@ struct GNode {
   double c2 = 0;  // G_QUENCH: weight of max3|T| added to |T| (< 0: max3|T| alone)
   int iop = 0;    // G_STBIN: the binary op
   int side = 0;   // G_STBIN: 1 when the stencil is the second operand
+  double ps = 1, pt = 0;  // epilogue: the node's value is ps v + pt (a folded G_AXPB)
+  int axis2 = 0, sk2 = 0;  // G_ST2: the second stencil
+  double h2 = 0;
+  // A folded sum: the node's value v becomes v + C (pop 1), v - C (2) or
+  // C - v (3), C the value of node c; the epilogue (ps, pt) applies after it.
+  int c = -1, pop = 0;
+  // Float copies of the constants, for the FP32 kernels, and whether the
+  // epilogue is other than the identity (set when the graph is complete).
+  float f0 = 0, f1 = 0, f2 = 0, fh2 = 0, fps = 1, fpt = 0;
+  int ep = 0;
 };
 
 // Precision-independent description of the graph.
@@ -94,8 +107,11 @@ struct GraphDef {
   std::vector<double> mesh;
 };
 
-// Build the right-hand-side graph for a grid and parameter set.
-void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p);
+// Build the right-hand-side graph for a grid and parameter set; with fuse,
+// merge single-use nodes into their consumers (the same values, fewer arrays
+// and launches), without it keep one node per primitive.
+void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p,
+                     bool fuse = true);
 
 #ifndef GRAPH_NSTREAMS
 #define GRAPH_NSTREAMS 4
@@ -113,9 +129,9 @@ struct GraphExec {
   T* qscr = nullptr;     // 7 arrays of scratch for the G_QUENCH transpose, or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
-  // Reverse sweep: node receives a gradient; its a / b slot writes (rather
-  // than accumulates into) the input's gradient.
-  std::vector<char> hasg, wa, wb;
+  // Reverse sweep: node receives a gradient; its a / b / c slot writes
+  // (rather than accumulates into) the input's gradient.
+  std::vector<char> hasg, wa, wb, wc;
   long long launches = 0;
   // Concurrent sweeps: with nconc auxiliary streams each node's launch waits
   // only on the launches it depends on (its operands' values in the forward;

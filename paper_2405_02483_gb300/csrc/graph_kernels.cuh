@@ -1,0 +1,498 @@
+// Op-graph kernels (see graph.cuh): the forward and the hand-written
+// transpose (vector-Jacobian) kernel of every primitive, as templates over the
+// sweep's precision.  Included by the executor (graph.cu); plain C++ apart
+// from the CUDA qualifiers, so that a host build can run them too.
+#pragma once
+
+#include <math.h>
+
+#include "graph.cuh"
+
+namespace stg {
+
+// ---------------------------------------------------------------------------
+// A cell of a graph launch: 3-D grid of GB x GBY x GBZ thread blocks, so the
+// cell's (i, j, k) come from the launch and a periodic neighbour needs no
+// division.
+// ---------------------------------------------------------------------------
+#ifndef GBX
+#define GBX 32
+#endif
+#ifndef GBY
+#define GBY 2
+#endif
+#ifndef GBZ
+#define GBZ 4
+#endif
+
+struct GCell {
+  int i, j, k;
+  long long idx;
+};
+
+__device__ __forceinline__ bool gcell(GCell& c, const Geo& g) {
+  c.i = blockIdx.x * blockDim.x + threadIdx.x;
+  c.j = blockIdx.y * blockDim.y + threadIdx.y;
+  c.k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (c.i >= g.nx || c.j >= g.ny || c.k >= g.nz) return false;
+  c.idx = (long long)c.k * g.sz + (long long)c.j * g.sy + c.i;
+  return true;
+}
+
+// A thread of a graph launch takes GZU cells along z: its first cell from the
+// launch, then steps of the launch's z extent (gridDim.z * GBZ).  The
+// pointwise and stencil kernels compute every value before they store any,
+// so that GZU loads of each operand are in flight together.  One cell per
+// thread measured fastest on GB300 (adjoint step at 128^3: 25.3 / 26.5 / 26.7
+// / 32.4 ms with 1 / 2 / 4 / 8): the per-op kernels are small enough that
+// occupancy, not loads per thread, sets their throughput.
+#ifndef GZU
+#define GZU 1
+#endif
+
+__device__ __forceinline__ GCell gcell_at(const GCell& c0, int u, const Geo& g) {
+  GCell c = c0;
+  const int dz = u * (int)(gridDim.z * blockDim.z);
+  c.k += dz;
+  c.idx += (long long)dz * g.sz;
+  return c;
+}
+
+// A node's constant in the sweep's precision: the FP32 kernels read the
+// float copies made when the graph was built (a conversion from double, or
+// a double comparison, runs on the FP64 pipe, which is narrow on this GPU).
+template <typename T>
+__device__ __forceinline__ T kc(double d, float f) {
+  if constexpr (sizeof(T) == sizeof(float)) return f;
+  else return d;
+}
+
+// Periodic neighbour of cell c along an axis (shifted by o).
+__device__ __forceinline__ long long nbr(const GCell& c, int axis, int o, const Geo& g) {
+  if (axis == 0) return c.idx + (wrap(c.i + o, g.nx) - c.i);
+  if (axis == 1) return c.idx + (long long)(wrap(c.j + o, g.ny) - c.j) * g.sy;
+  return c.idx + (long long)(wrap(c.k + o, g.nz) - c.k) * g.sz;
+}
+
+// Stencil value at c: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
+// are eq. (deriv) to i+1/2 and i-1/2, divided by the spacing h.
+template <typename T>
+__device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, int kind, T h,
+                                        const Geo& g) {
+  const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
+  const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
+  T m3 = f[nbr(c, axis, -3, g)], m2 = f[nbr(c, axis, -2, g)], m1 = f[nbr(c, axis, -1, g)];
+  T z0 = f[c.idx], p1 = f[nbr(c, axis, 1, g)], p2 = f[nbr(c, axis, 2, g)],
+    p3 = f[nbr(c, axis, 3, g)];
+  switch (kind) {
+    case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
+    case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
+    case ST_DDUP: return (DA * (p1 - z0) + DB * (p2 - m1) + DC * (p3 - m2)) / h;
+    default: return (DA * (z0 - m1) + DB * (p1 - m2) + DC * (p2 - m3)) / h;
+  }
+}
+
+// The same stencil of the values v(idx) of a functor at the taps.
+template <typename T, class V>
+__device__ __forceinline__ T stencil_fn(V v, const GCell& c, int axis, int kind, T h,
+                                        const Geo& g) {
+  const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
+  const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
+  T m3 = v(nbr(c, axis, -3, g)), m2 = v(nbr(c, axis, -2, g)), m1 = v(nbr(c, axis, -1, g));
+  T z0 = v(c.idx), p1 = v(nbr(c, axis, 1, g)), p2 = v(nbr(c, axis, 2, g)),
+    p3 = v(nbr(c, axis, 3, g));
+  switch (kind) {
+    case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
+    case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
+    case ST_DDUP: return (DA * (p1 - z0) + DB * (p2 - m1) + DC * (p3 - m2)) / h;
+    default: return (DA * (z0 - m1) + DB * (p1 - m2) + DC * (p2 - m3)) / h;
+  }
+}
+// Transposed kind and sign of a stencil: up^T = dn, dn^T = up, ddup^T =
+// -dddn, dddn^T = -ddup (periodic summation by parts).
+__device__ __forceinline__ int st_transpose(int kind) {
+  return kind == ST_UP ? ST_DN : kind == ST_DN ? ST_UP : kind == ST_DDUP ? ST_DDDN : ST_DDUP;
+}
+__device__ __forceinline__ bool st_negates(int kind) { return kind == ST_DDUP || kind == ST_DDDN; }
+
+// ---------------------------------------------------------------------------
+// Quench, eq. (quench) with reading R8, as one node: out = T min(fac, qlim),
+// fac = the max over the node's axes of max3 along the axis of
+// q = |D2 T| / ((M + |D2 T| / qmax) + 1e-30), D2 T = T(+1) - 2 T + T(-1) and
+// M = |T| + eps max3 |T| (eps = c2 >= 0), or M = max3 |T| (c2 < 0).  Its transpose follows the rules of the primitive nodes it
+// stands for: a max splits the gradient evenly on a tie (pairwise, the inner
+// pair first), |x|' = sign x with sign 0 = 0, the clamp passes the gradient
+// where fac <= qlim.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void max_w(T a, T b, T& wa, T& wb) {
+  wa = a > b ? (T)1 : (a == b ? (T)0.5 : (T)0);
+  wb = b > a ? (T)1 : (a == b ? (T)0.5 : (T)0);
+}
+template <typename T>
+__device__ __forceinline__ T sgn(T a) {
+  return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
+}
+
+// q at z = c + s e_ax, and (dq) its derivatives with respect to T at z-1, z,
+// z+1 (through D2 T and through M).
+template <typename T>
+__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, T eps,
+                                  const Geo& g, T* dq) {
+  const T vm = A[nbr(c, ax, s - 1, g)], v0 = A[nbr(c, ax, s, g)], vp = A[nbr(c, ax, s + 1, g)];
+  const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
+  const T am = fabs(vm), a0 = fabs(v0), ap = fabs(vp);
+  const T inner = am >= a0 ? am : a0;
+  const T M3 = inner >= ap ? inner : ap;
+  // M = cM max3|T| + cP |T|.
+  const T cM = eps < (T)0 ? (T)1 : eps, cP = eps < (T)0 ? (T)0 : (T)1;
+  const T M = eps < (T)0 ? M3 : a0 + eps * M3;
+  const T den = (M + a2 * iq) + (T)1e-30;
+  const T q = a2 / den;
+  if (dq) {
+    T wim, wi0, woi, wop;
+    max_w(am, a0, wim, wi0);
+    max_w(inner, ap, woi, wop);
+    const T dq_da2 = (T)1 / den + iq * (-a2 / (den * den));
+    const T dq_dM = -a2 / (den * den);
+    const T sd = sgn(d2);
+    dq[0] = dq_da2 * sd + dq_dM * (cM * (woi * wim)) * sgn(vm);
+    dq[1] = dq_da2 * sd * (T)-2 + dq_dM * (cM * (woi * wi0) + cP) * sgn(v0);
+    dq[2] = dq_da2 * sd + dq_dM * (cM * wop) * sgn(vp);
+  }
+  return q;
+}
+
+// fac at c, and (when wq) the weights of the three q of each axis in fac:
+// wq[3 t + p + 1] for axis t and position p.
+template <typename T>
+__device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int a1, T iq, T eps,
+                                        const Geo& g, T* wq) {
+  T m[2] = {0, 0}, w[2][3];
+  for (int t = 0; t < 2; ++t) {
+    const int ax = t == 0 ? a0 : a1;
+    if (ax < 0) continue;
+    const T qm = q_at(A, c, ax, -1, iq, eps, g, (T*)nullptr),
+            q0 = q_at(A, c, ax, 0, iq, eps, g, (T*)nullptr),
+            qp = q_at(A, c, ax, 1, iq, eps, g, (T*)nullptr);
+    const T inner = qm >= q0 ? qm : q0;
+    m[t] = inner >= qp ? inner : qp;
+    T wim, wi0, woi, wop;
+    max_w(qm, q0, wim, wi0);
+    max_w(inner, qp, woi, wop);
+    w[t][0] = woi * wim;
+    w[t][1] = woi * wi0;
+    w[t][2] = wop;
+  }
+  T fac = m[0], wf0 = 1, wf1 = 0;
+  if (a1 >= 0) {
+    fac = m[0] >= m[1] ? m[0] : m[1];
+    max_w(m[0], m[1], wf0, wf1);
+  }
+  if (wq)
+    for (int p = 0; p < 3; ++p) {
+      wq[p] = wf0 * w[0][p];
+      wq[3 + p] = a1 >= 0 ? wf1 * w[1][p] : (T)0;
+    }
+  return fac;
+}
+
+// Transpose, first pass (per output cell y): S0 = gbar C (the product's own
+// term) and S[1 + 3 t + p + 1] = gbar T dC/dfac dfac/dq, the cotangent each
+// q of axis t at position p receives from y.
+template <typename T>
+__global__ void g_quench_b1(GNode nd, const T* A, const T* gout, T* S, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  const T iq = (T)1 / kc<T>(nd.c0, nd.f0), qlim = kc<T>(nd.c1, nd.f1);
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k >= g.nz) break;
+    T wq[6];
+    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, kc<T>(nd.c2, nd.f2), g, wq);
+    const T gg = gout[c.idx];
+    const T C = fac > qlim ? qlim : fac;
+    const T dC = fac <= qlim ? (T)1 : (T)0;
+    const T base = gg * A[c.idx] * dC;
+    S[c.idx] = gg * C;
+    for (int j = 0; j < 6; ++j) S[(long long)(1 + j) * g.n + c.idx] = base * wq[j];
+  }
+}
+
+// Transpose, second pass (per input cell x): Tbar(x) = S0(x) + the sum over
+// the axes and the three q positions z = x + r e_a whose stencils hold x of
+// qbar(z) dq(z)/dT(x), qbar(z) = sum_p S[.. p](z - p e_a).
+template <typename T>
+__global__ void g_quench_b3(GNode nd, const T* A, const T* S, T* gA, int wA, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  const T iq = (T)1 / kc<T>(nd.c0, nd.f0);
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k >= g.nz) break;
+    T acc = S[c.idx];
+    for (int t = 0; t < 2; ++t) {
+      const int ax = t == 0 ? nd.axis : nd.sk;
+      if (ax < 0) continue;
+      for (int r = -1; r <= 1; ++r) {
+        T qbar = 0;
+        for (int p = -1; p <= 1; ++p)
+          qbar += S[(long long)(1 + 3 * t + p + 1) * g.n + nbr(c, ax, r - p, g)];
+        T dq[3];
+        q_at(A, c, ax, r, iq, kc<T>(nd.c2, nd.f2), g, dq);
+        acc += qbar * dq[1 - r];
+      }
+    }
+    gA[c.idx] = wA ? acc : gA[c.idx] + acc;
+  }
+}
+
+// Quench forward (G_QUENCH): out = T min(fac, qlim).
+template <typename T>
+__global__ void g_quench_f(GNode nd, const T* A, T* out, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k >= g.nz) break;
+    const T iq = (T)1 / kc<T>(nd.c0, nd.f0), qlim = kc<T>(nd.c1, nd.f1);
+    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, kc<T>(nd.c2, nd.f2), g, (T*)nullptr);
+    out[c.idx] = A[c.idx] * (fac > qlim ? qlim : fac);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T fwd_value(int op, const GNode& nd, const T* A, const T* B,
+                                       const T* mesh, const GCell& c, const Geo& g) {
+  const long long idx = c.idx;
+  switch (op) {
+    case G_STENCIL: return stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g);
+    case G_STBIN: {
+      const T st = stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g), b = B[idx];
+      if (nd.iop == G_MUL) return st * b;
+      if (nd.iop == G_ADD) return nd.side ? b + st : st + b;
+      return nd.side ? b - st : st - b;     // G_SUB
+    }
+    case G_STMUL:
+      return stencil_fn<T>([&](long long j) { return A[j] * B[j]; }, c, nd.axis, nd.sk,
+                           kc<T>(nd.c0, nd.f0), g);
+    case G_ST2: {
+      const T s1 = stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g);
+      const T s2 = stencil_at(B, c, nd.axis2, nd.sk2, kc<T>(nd.h2, nd.fh2), g);
+      return nd.iop == G_ADD ? s1 + s2 : s1 - s2;
+    }
+    case G_SHIFT: return A[nbr(c, nd.axis, nd.sk, g)];
+    case G_ADD: return A[idx] + B[idx];
+    case G_SUB: return A[idx] - B[idx];
+    case G_MUL: return A[idx] * B[idx];
+    case G_DIV: return A[idx] / B[idx];
+    case G_MAX: return A[idx] >= B[idx] ? A[idx] : B[idx];
+    case G_EXP: return exp(A[idx]);
+    case G_LOG: return log(A[idx]);
+    case G_LOG1P: return log1p(A[idx]);
+    case G_SQRT: return sqrt(A[idx]);
+    case G_ABS: return fabs(A[idx]);
+    case G_AXPB: return kc<T>(nd.c0, nd.f0) * A[idx] + kc<T>(nd.c1, nd.f1);
+    case G_CLAMPMIN: return A[idx] < kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : A[idx];
+    case G_CLAMPMAX: return A[idx] > kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : A[idx];
+    case G_STEP: return A[idx] > kc<T>(nd.c0, nd.f0) ? (T)1 : (T)0;
+    case G_ZFIELD: return mesh[(long long)nd.sk * g.nz + c.k];
+    default: return kc<T>(nd.c0, nd.f0);  // G_CONST
+  }
+}
+
+// Every node but G_QUENCH (g_quench_f) and G_PMEAN; one instance per op.
+template <typename T, int OP>
+__global__ void g_forward(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
+                          Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  T r[GZU];
+#pragma unroll
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k < g.nz) {
+      r[u] = fwd_value(OP, nd, A, B, mesh, c, g);
+      if (nd.pop) {
+        const T cv = C[c.idx];
+        r[u] = nd.pop == 1 ? r[u] + cv : nd.pop == 2 ? r[u] - cv : cv - r[u];
+      }
+    }
+  }
+  if (nd.ep) {
+#pragma unroll
+    for (int u = 0; u < GZU; ++u) r[u] = kc<T>(nd.ps, nd.fps) * r[u] + kc<T>(nd.pt, nd.fpt);
+  }
+#pragma unroll
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k < g.nz) out[c.idx] = r[u];
+  }
+}
+
+// Transpose kernels.  Pointwise rules follow the usual subgradient choices:
+// |x|' = sign(x) with sign(0) = 0; clamp passes the gradient where the bound
+// holds with equality; max(a, b) splits it evenly on ties.
+template <typename T>
+__device__ __forceinline__ void bwd_value(int op, const GNode& nd, const T* A, const T* B,
+                                          const T* out, const T* gout, const GCell& c,
+                                          const Geo& g, T& ca, T& cb) {
+  const long long idx = c.idx;
+  ca = 0;
+  cb = 0;
+  if (op == G_STENCIL) {
+    // Gather form of the transpose: up^T = dn, dn^T = up, ddup^T = -dddn,
+    // dddn^T = -ddup (periodic summation by parts).
+    int kind = nd.sk;
+    T v = stencil_at(gout, c, nd.axis, st_transpose(kind), kc<T>(nd.c0, nd.f0), g);
+    ca = st_negates(kind) ? -v : v;
+  } else if (op == G_STBIN) {
+    // y = st(a) (op) b: the stencil's transpose of the cotangent of st(a),
+    // which is g (add), -+g (sub) or g b (mul) at each tap.
+    const int tk = st_transpose(nd.sk);
+    const T sg = st_negates(nd.sk) ? (T)-1 : (T)1;
+    const T gg = gout[idx];
+    if (nd.iop == G_MUL) {
+      ca = sg * stencil_fn<T>([&](long long j) { return gout[j] * B[j]; }, c, nd.axis, tk,
+                              kc<T>(nd.c0, nd.f0), g);
+      cb = gg * stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g);
+    } else {
+      const T v = sg * stencil_at(gout, c, nd.axis, tk, kc<T>(nd.c0, nd.f0), g);
+      const bool neg_st = nd.iop == G_SUB && nd.side;    // b - st
+      const bool neg_b = nd.iop == G_SUB && !nd.side;    // st - b
+      ca = neg_st ? -v : v;
+      cb = neg_b ? -gg : gg;
+    }
+  } else if (op == G_STMUL) {
+    // y = st(a b): the transposed stencil of g, times the other factor.
+    T v = stencil_at(gout, c, nd.axis, st_transpose(nd.sk), kc<T>(nd.c0, nd.f0), g);
+    if (st_negates(nd.sk)) v = -v;
+    ca = v * B[idx];
+    cb = v * A[idx];
+  } else if (op == G_ST2) {
+    // y = st1(a) +- st2(b): each stencil's transpose of the cotangent.
+    const T v1 = stencil_at(gout, c, nd.axis, st_transpose(nd.sk), kc<T>(nd.c0, nd.f0), g);
+    const T v2 = stencil_at(gout, c, nd.axis2, st_transpose(nd.sk2), kc<T>(nd.h2, nd.fh2), g);
+    ca = st_negates(nd.sk) ? -v1 : v1;
+    cb = (st_negates(nd.sk2) != (nd.iop == G_SUB)) ? -v2 : v2;
+  } else if (op == G_SHIFT) {
+    ca = gout[nbr(c, nd.axis, -nd.sk, g)];
+  } else {
+    const T gg = gout[idx];
+    switch (op) {
+      case G_ADD: ca = gg; cb = gg; break;
+      case G_SUB: ca = gg; cb = -gg; break;
+      case G_MUL: ca = gg * B[idx]; cb = gg * A[idx]; break;
+      case G_DIV: {
+        T a = A[idx], b = B[idx];
+        ca = gg / b;
+        cb = -gg * a / (b * b);
+        break;
+      }
+      case G_MAX: {
+        T a = A[idx], b = B[idx];
+        ca = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
+        cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
+        break;
+      }
+      case G_EXP: ca = gg * out[idx]; break;
+      case G_LOG: ca = gg / A[idx]; break;
+      case G_LOG1P: ca = gg / ((T)1 + A[idx]); break;
+      case G_SQRT: ca = gg / ((T)2 * out[idx]); break;
+      case G_ABS: {
+        T a = A[idx];
+        ca = a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0);
+        break;
+      }
+      case G_AXPB: ca = kc<T>(nd.c0, nd.f0) * gg; break;
+      case G_CLAMPMIN: ca = A[idx] >= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
+      case G_CLAMPMAX: ca = A[idx] <= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
+      default: break;
+    }
+  }
+}
+
+// The first contribution a gradient receives in the reverse sweep writes it
+// (wA, wB); later ones accumulate.  a and b may be the same node: a's
+// contribution is applied first, as two sequential updates would.
+template <typename T, int OP>
+__global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+                           T* gA, T* gB, T* gC, int wA, int wB, int wC, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  const bool same = gA != nullptr && gA == gB;
+  // The factors of the epilogue and the folded sum: every transpose is linear
+  // in gout, and C's cotangent is +-ps gout at the cell (C is neither a nor b).
+  const T sv = kc<T>(nd.ps, nd.fps) * (nd.pop == 3 ? (T)-1 : (T)1);
+  const T sc = kc<T>(nd.ps, nd.fps) * (nd.pop == 2 ? (T)-1 : (T)1);
+  T ca[GZU], cb[GZU], oa[GZU], ob[GZU];
+#pragma unroll
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k < g.nz) {
+      bwd_value(OP, nd, A, B, out, gout, c, g, ca[u], cb[u]);
+      if (nd.ep || nd.pop == 3) {
+        ca[u] *= sv;
+        cb[u] *= sv;
+      }
+      oa[u] = (gA && !wA) ? gA[c.idx] : (T)0;
+      ob[u] = (gB && !wB && !same) ? gB[c.idx] : (T)0;
+      if (gC) {
+        const T v = sc * gout[c.idx];
+        gC[c.idx] = wC ? v : gC[c.idx] + v;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k < g.nz) {
+      if (same) {
+        T v = wA ? ca[u] : oa[u] + ca[u];
+        gA[c.idx] = wB ? cb[u] : v + cb[u];
+      } else {
+        if (gA) gA[c.idx] = wA ? ca[u] : oa[u] + ca[u];
+        if (gB) gB[c.idx] = wB ? cb[u] : ob[u] + cb[u];
+      }
+    }
+  }
+}
+
+// Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed
+// order; the broadcast writes (or, for the transpose, adds) sum / (nx ny).
+// The mean is linear and symmetric, so its transpose is the same mean.
+template <typename T>
+__global__ void g_plane_sum(const T* A, T* psum, Geo g) {
+  __shared__ T sm[256];
+  const int kz = blockIdx.x;
+  const long long m = (long long)g.nx * g.ny;
+  T acc = 0;
+  for (long long i = threadIdx.x; i < m; i += blockDim.x) acc += A[(long long)kz * g.sz + i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) psum[kz] = sm[0];
+}
+
+template <typename T>
+__global__ void g_plane_bcast(const T* psum, T* out, int add, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k >= g.nz) break;
+    const T v = psum[c.k] / (T)((double)g.nx * g.ny);
+    out[c.idx] = add ? out[c.idx] + v : v;
+  }
+}
+
+template <typename T>
+__global__ void g_add_into(T* dst, const T* src, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
+}  // namespace stg

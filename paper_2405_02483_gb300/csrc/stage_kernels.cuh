@@ -254,7 +254,7 @@ template <int TY, bool VISC, bool CR>
 __global__ void __launch_bounds__(FD_TX * TY, TY <= 8 ? FD_MINB : 1) k_fdiv(
     FdIn in, float* q0, float* q1, float* q2, float* q3, float* q4, float* q5, float* q6,
     float* q7, float* o0, float* o1, float* o2, float* o3, float* o4, float* o5, float* o6,
-    float* o7, float alpha, float beta, const double* dtp, int mode, unsigned* cr, KPar k,
+    float* o7, float alpha, const float* bdtp, int mode, unsigned* cr, KPar k,
     Geo g) {
   static_assert(6 * FD_TX + 6 * TY <= FD_TX * TY, "one halo task per thread");
   // S_COUNT flux planes of (TY + 6) x FD_W floats (dynamic shared memory).
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(FD_TX * TY, TY <= 8 ? FD_MINB : 1) k_fdiv(
   const int z1 = min(z0 + FD_ZC, g.nz);
   const int i = x0 + tx, j = y0 + ty;
   const bool own = i < g.nx && j < g.ny;   // an output cell (else only smem fluxes)
-  const float bdt = mode ? (float)((double)beta * dtp[0]) : 0.f;
+  const float bdt = mode ? bdtp[0] : 0.f;
   const float ihz = k.ih[2];
   // With a single plane every z-derivative and z-interpolation difference is
   // exactly zero (periodic wrap of size 1): the z parts are left out rather

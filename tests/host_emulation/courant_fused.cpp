@@ -112,10 +112,10 @@ int main() {
     di.f[0] = rd.data();
     di.f[4] = Ed.data();
     float* o = dummy.data();
-    double dtv = 0;
+    float bdtv = 0;
     run(gg, bb, [&] {
       k_div<Nb4, 0x11, true>(di, q0.data(), o, o, o, q4.data(), o, o, o, q0.data(), o, o, o, q4.data(), o,
-                             o, o, 0.f, 0.f, &dtv, 0, fused + 1, k, g);
+                             o, o, 0.f, &bdtv, 0, fused + 1, k, g);
     });
     run(gg, bb, [&] {
       k_courant_part<Nb4>(ux.data(), uy.data(), uz.data(), rd.data(), Ed.data(), bx.data(), by.data(),

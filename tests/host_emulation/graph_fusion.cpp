@@ -1,0 +1,256 @@
+// Host build of the op graph: the graph with its merged nodes (fused stencil
+// pairs and stencil sums, folded sums and scalings) against the graph of one
+// node per primitive, both swept by the same forward and transpose kernels run
+// over their launch grids one thread at a time.  The forward outputs must be
+// equal bit for bit; the reverse sweep's input gradients may differ only by
+// rounding (the merged transposes scale a gathered cotangent instead of
+// gathering a scaled one): within 1e-12 (FP64) or 1e-5 (FP32) of each
+// field's largest gradient.  Cases: the benchmark's viscosity and quench; with
+// chromospheric and coronal cooling (plane means, exp, sqrt); Smagorinsky
+// with the bulk term, gravity, ediffav, ln(P/P_aver), the second-order switch
+// and no log interpolation on a stretched z mesh.  Exit status: the number of
+// failing (case, precision) pairs.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+#undef __global__
+#undef __device__
+#undef __host__
+#undef __forceinline__
+#undef __launch_bounds__
+#undef __shared__
+#define __global__
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __launch_bounds__(...)
+#define __shared__ static
+#define __ldg(p) (*(p))
+#define __syncthreads()
+uint3 blockIdx, threadIdx;
+dim3 blockDim, gridDim;
+#include "../../paper_2405_02483_gb300/csrc/graph_kernels.cuh"
+#include "../../paper_2405_02483_gb300/csrc/graph_build.cu"
+using namespace stg;
+
+template <class K>
+static void run(const Geo& g, K kern) {
+  const dim3 bd(GBX, GBY, GBZ);
+  const dim3 gd((g.nx + GBX - 1) / GBX, (g.ny + GBY - 1) / GBY, (g.nz + GBZ * GZU - 1) / (GBZ * GZU));
+  gridDim = gd;
+  blockDim = bd;
+  for (unsigned bz = 0; bz < gd.z; ++bz)
+    for (unsigned by = 0; by < gd.y; ++by)
+      for (unsigned bx = 0; bx < gd.x; ++bx)
+        for (unsigned tz = 0; tz < bd.z; ++tz)
+          for (unsigned ty = 0; ty < bd.y; ++ty)
+            for (unsigned tx = 0; tx < bd.x; ++tx) {
+              blockIdx = make_uint3(bx, by, bz);
+              threadIdx = make_uint3(tx, ty, tz);
+              kern();
+            }
+}
+
+// The executor's sweeps (graph.cu) on the host, one node after another.
+template <typename T>
+struct HostExec {
+  GraphDef d;
+  Geo g;
+  std::vector<std::vector<T>> v, gr;
+  std::vector<T> mesh;
+  std::vector<char> hasg, wa, wb, wc;
+
+  void init() {
+    const size_t nn = d.nodes.size();
+    v.assign(nn, std::vector<T>(g.n, 0));
+    gr.assign(nn, std::vector<T>(g.n, 0));
+    mesh.assign(d.mesh.begin(), d.mesh.end());
+    hasg.assign(nn, 0);
+    wa.assign(nn, 0);
+    wb.assign(nn, 0);
+    wc.assign(nn, 0);
+    std::vector<char> seen(nn, 0);
+    for (int k = 0; k < 8; ++k) seen[d.out[k]] = hasg[d.out[k]] = 1;
+    for (long long i = (long long)nn - 1; i >= 0; --i) {
+      const GNode& nd = d.nodes[i];
+      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP)
+        continue;
+      if (nd.a >= 0) { wa[i] = !seen[nd.a]; seen[nd.a] = hasg[nd.a] = 1; }
+      if (nd.b >= 0) { wb[i] = !seen[nd.b]; seen[nd.b] = hasg[nd.b] = 1; }
+      if (nd.c >= 0) { wc[i] = !seen[nd.c]; seen[nd.c] = hasg[nd.c] = 1; }
+    }
+  }
+  // The horizontal-plane mean, written or added (G_PMEAN and its transpose).
+  void pmean(const T* a, T* o, bool add) const {
+    for (int k = 0; k < g.nz; ++k) {
+      T s = 0;
+      for (long long q = 0; q < g.sz; ++q) s += a[k * g.sz + q];
+      s /= (T)g.sz;
+      for (long long q = 0; q < g.sz; ++q) o[k * g.sz + q] = add ? o[k * g.sz + q] + s : s;
+    }
+  }
+  void forward(const std::vector<std::vector<T>>& in) {
+    const T* M = mesh.empty() ? nullptr : mesh.data();
+    for (size_t i = 0; i < d.nodes.size(); ++i) {
+      const GNode nd = d.nodes[i];
+      if (nd.op == G_INPUT) {
+        v[i] = in[nd.sk];
+        continue;
+      }
+      const T* A = nd.a >= 0 ? v[nd.a].data() : nullptr;
+      const T* B = nd.b >= 0 ? v[nd.b].data() : nullptr;
+      const T* C = nd.c >= 0 ? v[nd.c].data() : nullptr;
+      T* out = v[i].data();
+      const Geo& G = g;
+#define FW(OP) case OP: run(G, [&] { g_forward<T, OP>(nd, A, B, C, out, M, G); }); break;
+      switch (nd.op) {
+        case G_PMEAN: pmean(A, out, false); break;
+        case G_QUENCH: run(G, [&] { g_quench_f<T>(nd, A, out, G); }); break;
+        FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_ADD) FW(G_SUB)
+        FW(G_MUL) FW(G_DIV) FW(G_MAX) FW(G_EXP) FW(G_LOG) FW(G_LOG1P) FW(G_SQRT) FW(G_ABS)
+        FW(G_AXPB) FW(G_CLAMPMIN) FW(G_CLAMPMAX) FW(G_STEP) FW(G_ZFIELD) FW(G_CONST)
+        default: printf("no forward for op %d\n", nd.op); exit(100);
+      }
+#undef FW
+    }
+  }
+  void backward(const std::vector<std::vector<T>>& seed, std::vector<std::vector<T>>& gin) {
+    for (int k = 0; k < 8; ++k) gr[d.out[k]] = seed[k];
+    std::vector<T> S(7 * g.n);
+    for (long long i = (long long)d.nodes.size() - 1; i >= 0; --i) {
+      const GNode nd = d.nodes[i];
+      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP)
+        continue;
+      const T* A = nd.a >= 0 ? v[nd.a].data() : nullptr;
+      const T* B = nd.b >= 0 ? v[nd.b].data() : nullptr;
+      T* gA = nd.a >= 0 ? gr[nd.a].data() : nullptr;
+      T* gB = nd.b >= 0 ? gr[nd.b].data() : nullptr;
+      T* gC = nd.c >= 0 ? gr[nd.c].data() : nullptr;
+      const T* out = v[i].data();
+      const T* go = gr[i].data();
+      const int WA = wa[i], WB = wb[i], WC = wc[i];
+      const Geo& G = g;
+#define BW(OP) case OP: run(G, [&] { g_backward<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, G); }); break;
+      switch (nd.op) {
+        case G_PMEAN: pmean(go, gA, !WA); break;
+        case G_QUENCH:
+          run(G, [&] { g_quench_b1<T>(nd, A, go, S.data(), G); });
+          run(G, [&] { g_quench_b3<T>(nd, A, S.data(), gA, WA, G); });
+          break;
+        BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_ADD) BW(G_SUB)
+        BW(G_MUL) BW(G_DIV) BW(G_MAX) BW(G_EXP) BW(G_LOG) BW(G_LOG1P) BW(G_SQRT) BW(G_ABS)
+        BW(G_AXPB) BW(G_CLAMPMIN) BW(G_CLAMPMAX)
+        default: printf("no transpose for op %d\n", nd.op); exit(100);
+      }
+#undef BW
+    }
+    for (int k = 0; k < 8; ++k) gin[k] = gr[d.in[k]];
+  }
+};
+
+// The library's defaults (stagger_params_default), for the fields the graph reads.
+static stagger_params base_params() {
+  stagger_params p;
+  memset(&p, 0, sizeof(p));
+  p.gamma = 5.0 / 3.0;
+  p.nuE = p.nuB = 1.0;
+  p.qmax = 8.0;
+  p.qlim = 2.0;
+  p.quench_eps = 1e-4;
+  p.log_interp = 1;
+  p.rho_cool = 1.0;
+  p.d2lnr_lim = 0.3;
+  p.rho_bot = 1.0;
+  p.cor_Tunit = 1.0;
+  p.nu1 = 0.04;
+  p.nu2 = 1.0;
+  p.nu3 = 0.04;
+  p.do_quench = 1;
+  p.ref[0] = 1.0;
+  p.ref[4] = 1.5;
+  p.ref[7] = 0.5;
+  return p;
+}
+
+template <typename T>
+static int compare(const char* name, const stagger_grid& gg, const stagger_params& p, double tol) {
+  const Geo g = make_geo(gg.nx, gg.ny, gg.nz);
+  std::mt19937_64 rng(7);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  std::vector<std::vector<T>> in(8, std::vector<T>(g.n)), seed(8, std::vector<T>(g.n));
+  for (int k = 0; k < 8; ++k)
+    for (auto& x : in[k]) x = (T)((k == 0 || k == 4 ? 0.1 : 0.3) * U(rng));
+  for (int k = 0; k < 8; ++k)
+    for (auto& x : seed[k]) x = (T)U(rng);
+  std::vector<std::vector<T>> res[2], gin[2];
+  size_t nodes[2];
+  for (int t = 0; t < 2; ++t) {
+    HostExec<T> h;
+    h.g = g;
+    build_rhs_graph(h.d, gg, p, t == 1);
+    nodes[t] = h.d.nodes.size();
+    h.init();
+    h.forward(in);
+    for (int k = 0; k < 8; ++k) res[t].push_back(h.v[h.d.out[k]]);
+    gin[t].resize(8);
+    h.backward(seed, gin[t]);
+  }
+  long long diff = 0, bad = 0;
+  double worst = 0;
+  for (int k = 0; k < 8; ++k) {
+    double e = 0, s = 0;
+    for (long long q = 0; q < g.n; ++q) {
+      if (std::memcmp(&res[0][k][q], &res[1][k][q], sizeof(T)) != 0) ++diff;
+      if (!std::isfinite((double)res[1][k][q]) || !std::isfinite((double)gin[1][k][q])) ++bad;
+      e = std::max(e, std::fabs((double)gin[0][k][q] - (double)gin[1][k][q]));
+      s = std::max(s, std::fabs((double)gin[0][k][q]));
+    }
+    worst = std::max(worst, e / std::max(s, 1e-300));
+  }
+  const bool ok = diff == 0 && bad == 0 && worst <= tol;
+  printf("%s %s: %zu -> %zu nodes, forward %lld differing values, %lld non-finite, "
+         "reverse max rel err %.2e%s\n", name, sizeof(T) == 8 ? "FP64" : "FP32", nodes[0], nodes[1],
+         diff, bad, worst, ok ? "" : "  FAIL");
+  return ok ? 0 : 1;
+}
+
+int main() {
+  int fails = 0;
+  const stagger_grid g1 = {13, 11, 9, 1.0 / 13, 1.0 / 11, 1.0 / 9};
+  stagger_params visc = base_params();
+  stagger_params cool = base_params();
+  cool.t_chromo = 0.05;
+  cool.rho_bot = 0.9;
+  cool.cor_L0 = 0.3;
+  cool.cor_Tunit = 8e3;
+  cool.t_cool = 0.2;
+  cool.e_cool = 1.2;
+  // A stretched z mesh: centre and face spacings of a smooth mapping.
+  const stagger_grid g2 = {12, 10, 11, 1.0 / 12, 1.0 / 10, 1.0 / 11};
+  std::vector<double> zc(g2.nz), zf(g2.nz);
+  for (int k = 0; k < g2.nz; ++k) {
+    zc[k] = (1.0 + 0.3 * std::sin(2 * M_PI * (k + 0.5) / g2.nz)) / g2.nz;
+    zf[k] = (1.0 + 0.3 * std::sin(2 * M_PI * k / (double)g2.nz)) / g2.nz;
+  }
+  stagger_params opts = base_params();
+  opts.csmag = 0.2;
+  opts.c1 = -1.0 / 3.0;
+  opts.g[0] = 0.1;
+  opts.g[2] = -1.0;
+  opts.ediffav = 1;
+  opts.lnp_aver = 1;
+  opts.do_2nddiv = 1;
+  opts.log_interp = 0;
+  opts.zc = zc.data();
+  opts.zf = zf.data();
+  fails += compare<double>("viscosity+quench", g1, visc, 1e-12);
+  fails += compare<float>("viscosity+quench", g1, visc, 1e-5);
+  fails += compare<double>("cooling", g1, cool, 1e-12);
+  fails += compare<float>("cooling", g1, cool, 1e-5);
+  fails += compare<double>("options+stretched", g2, opts, 1e-12);
+  fails += compare<float>("options+stretched", g2, opts, 1e-5);
+  return fails;
+}

@@ -154,10 +154,10 @@ static void rhs(const Geo& g, const KPar& kin, float* const* f, std::vector<std:
   di.lq = D[F_LQ];
   di.uz = D[F_UZ];
   for (int c = 0; c < 8; ++c) di.f[c] = f[c];
-  double dtv = 0;
+  float bdtv = 0;
   launch<N>(g, [&] {
     k_div<N, 0xFF, false>(di, out[0], out[1], out[2], out[3], out[4], out[5], out[6], out[7], out[0], out[1],
-                          out[2], out[3], out[4], out[5], out[6], out[7], 0.f, 0.f, &dtv, 0, nullptr, k, g);
+                          out[2], out[3], out[4], out[5], out[6], out[7], 0.f, &bdtv, 0, nullptr, k, g);
   });
 }
 

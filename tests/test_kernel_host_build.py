@@ -8,7 +8,10 @@ bit for bit on the CPU, beyond the GPU tests' FP32 tolerance:
   (the block reductions and the per-cell formulas);
 - the right-hand side formed with one cell per thread equals the one formed
   with four x-cells per thread, for the benchmark's physics and for every
-  option at once, on a uniform and on a stretched z mesh."""
+  option at once, on a uniform and on a stretched z mesh;
+- the op graph with its merged nodes (stencil pairs and sums, folded sums and
+  scalings) gives the same forward values bit for bit as the graph of one node
+  per primitive, and a reverse sweep equal to rounding, in FP64 and FP32."""
 import os
 import shutil
 import subprocess
@@ -46,3 +49,8 @@ def test_courant_maxima_in_stage_kernels_equal_separate_pass(tmp_path):
 def test_one_cell_and_four_cell_threads_give_the_same_rhs(tmp_path):
     out = _build_and_run(tmp_path, "rhs_mappings")
     assert out.count(" 0 differing values, 0 non-finite") == 16, out
+
+
+def test_merged_op_graph_equals_one_node_per_primitive(tmp_path):
+    out = _build_and_run(tmp_path, "graph_fusion")
+    assert out.count("forward 0 differing values, 0 non-finite") == 6, out
