@@ -149,6 +149,8 @@ static FwdK<T> fwd_kernel(int op) {
     case G_DIV: return g_forward<T, G_DIV>;
     case G_MAX: return g_forward<T, G_MAX>;
     case G_EXP: return g_forward<T, G_EXP>;
+    case G_STEXP: return g_forward<T, G_STEXP>;
+    case G_NB3: return g_forward<T, G_NB3>;
     case G_LOG: return g_forward<T, G_LOG>;
     case G_LOG1P: return g_forward<T, G_LOG1P>;
     case G_SQRT: return g_forward<T, G_SQRT>;
@@ -176,6 +178,8 @@ static BwdK<T> bwd_kernel(int op) {
     case G_DIV: return g_backward<T, G_DIV>;
     case G_MAX: return g_backward<T, G_MAX>;
     case G_EXP: return g_backward<T, G_EXP>;
+    case G_STEXP: return g_backward<T, G_STEXP>;
+    case G_NB3: return g_backward<T, G_NB3>;
     case G_LOG: return g_backward<T, G_LOG>;
     case G_LOG1P: return g_backward<T, G_LOG1P>;
     case G_SQRT: return g_backward<T, G_SQRT>;

@@ -28,7 +28,12 @@ enum GOp {
   G_STMUL,
   // The sum or difference (iop) of two stencils: (kind sk, axis, spacing c0)
   // of a and (kind sk2, axis2, spacing h2) of b.
-  G_ST2
+  G_ST2,
+  // exp of a stencil (kind sk, axis, spacing c0) of a.
+  G_STEXP,
+  // Three neighbours along axis combined by iop (G_ADD or G_MAX) as the graph
+  // built them: (a(i + sk) op a(i)) op a(i - sk).
+  G_NB3
 };
 enum GStencil { ST_UP = 0, ST_DN, ST_DDUP, ST_DDDN };
 

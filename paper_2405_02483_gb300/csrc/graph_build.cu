@@ -14,12 +14,15 @@ namespace stg {
 // (ohm), written on the stored deviations f' (full value ref + f').
 // ---------------------------------------------------------------------------
 // Every node is a whole-array pass whose launch, ramp and tail cost as much as
-// its bytes, so a stencil that feeds one sum, difference or product, and a
-// product that feeds one stencil, are merged into one node (G_STBIN, G_STMUL):
-// the pair's intermediate array and launches go away, and the fused node's
+// its bytes, so a stencil that feeds one sum, difference, product or exp, two
+// stencils that feed one sum or difference, and a product that feeds one
+// stencil are merged into one node (G_STBIN, G_ST2, G_STEXP, G_STMUL): the
+// pair's intermediate array and launches go away, and the fused node's
 // transpose is the pair's (the stencil's gather-form transpose of the
 // cotangent, times the other factor where there is one).  A node used twice,
-// or as an output, keeps its array.  The graph is then compacted.
+// or as an output, keeps its array.  (A quench that reads the product forming
+// its T at every tap measured slower than the product's own node: its many
+// taps then load two arrays.)  The graph is then compacted.
 static void compact(GraphDef& G, const std::vector<char>& dead);
 static bool generic_op(int op);
 
@@ -72,6 +75,14 @@ static void fuse_stencil_pairs(GraphDef& G) {
         dead[src] = 1;
         break;
       }
+    } else if (nd.op == G_EXP && lone_st(nd.a)) {
+      const GNode st = G.nodes[nd.a];
+      dead[nd.a] = 1;
+      nd.op = G_STEXP;
+      nd.a = st.a;
+      nd.axis = st.axis;
+      nd.sk = st.sk;
+      nd.c0 = st.c0;
     } else if (nd.op == G_STENCIL && nd.a >= 0 && !dead[nd.a] && G.nodes[nd.a].op == G_MUL &&
                uses[nd.a] == 1) {
       const GNode m = G.nodes[nd.a];
@@ -103,7 +114,10 @@ static void fold_affine(GraphDef& G) {
     GNode& nd = G.nodes[i];
     if (nd.op != G_AXPB || nd.pop || nd.a < 0 || uses[nd.a] != 1 || dead[nd.a]) continue;
     const GNode& s = G.nodes[nd.a];
-    if (!generic_op(s.op) || s.ps != 1.0 || s.pt != 0.0) continue;
+    // exp takes an epilogue too (its transpose reads y - pt = ps exp), when it
+    // has no folded sum.
+    const bool ex = (s.op == G_EXP || s.op == G_STEXP) && !s.pop;
+    if (!(generic_op(s.op) || ex) || s.ps != 1.0 || s.pt != 0.0) continue;
     GNode f = s;
     f.ps = nd.c0;
     f.pt = nd.c1;
@@ -120,7 +134,8 @@ static void fold_affine(GraphDef& G) {
 // value), and so do the nodes with their own kernels or without a gradient,
 // and C may not be an operand of the node it joins.
 static bool generic_op(int op) {
-  return op == G_STENCIL || op == G_STBIN || op == G_STMUL || op == G_ST2 || op == G_SHIFT ||
+  return op == G_STENCIL || op == G_STBIN || op == G_STMUL || op == G_ST2 || op == G_NB3 ||
+         op == G_SHIFT ||
          op == G_ADD || op == G_SUB || op == G_MUL || op == G_DIV || op == G_MAX ||
          op == G_LOG || op == G_LOG1P || op == G_ABS || op == G_AXPB || op == G_CLAMPMIN ||
          op == G_CLAMPMAX;
@@ -149,6 +164,51 @@ static void fold_sums(GraphDef& G) {
       f.c = oth;
       f.pop = nd.op == G_ADD ? 1 : (side == 0 ? 2 : 3);
       dead[src] = 1;
+      nd = f;
+      break;
+    }
+  }
+  compact(G, dead);
+}
+
+// The 3-cell max and sum along an axis, built as (shift(a, s) op a) op
+// shift(a, -s) from single-use shifts and an inner node of the same op (max or
+// add), become one node (G_NB3) that reads the three neighbours itself.
+static void fuse_neighbour3(GraphDef& G) {
+  const int nn = (int)G.nodes.size();
+  std::vector<int> uses(nn, 0);
+  for (const GNode& nd : G.nodes) {
+    if (nd.a >= 0) ++uses[nd.a];
+    if (nd.b >= 0) ++uses[nd.b];
+  }
+  for (int k = 0; k < 8; ++k) uses[G.out[k]] += 2;
+  std::vector<char> dead(nn, 0);
+  auto lone = [&](int i, int op) {
+    return i >= 0 && !dead[i] && uses[i] == 1 && G.nodes[i].op == op;
+  };
+  for (int i = 0; i < nn; ++i) {
+    GNode& nd = G.nodes[i];
+    if (nd.op != G_MAX && nd.op != G_ADD) continue;
+    for (int side = 0; side < 2; ++side) {
+      const int in = side == 0 ? nd.a : nd.b, s2 = side == 0 ? nd.b : nd.a;
+      if (!lone(in, nd.op) || !lone(s2, G_SHIFT)) continue;
+      const GNode& I = G.nodes[in];
+      const GNode& S2 = G.nodes[s2];
+      const int base = S2.a;
+      const int s1 = I.a == base ? I.b : I.b == base ? I.a : -1;
+      if (!lone(s1, G_SHIFT)) continue;
+      const GNode& S1 = G.nodes[s1];
+      if (S1.a != base || S1.axis != S2.axis || S1.sk != -S2.sk || (S1.sk != 1 && S1.sk != -1))
+        continue;
+      GNode f = nd;
+      f.op = G_NB3;
+      f.iop = nd.op;
+      f.a = base;
+      f.b = -1;
+      f.axis = S1.axis;
+      f.sk = S1.sk;
+      f.c0 = f.c1 = 0;
+      dead[in] = dead[s1] = dead[s2] = 1;
       nd = f;
       break;
     }
@@ -519,6 +579,7 @@ void build_rhs_graph(GraphDef& G, const stagger_grid& gr, const stagger_params& 
   int outs[8] = {d_r, d_px, d_py, d_pz, d_E, d_Bx, d_By, d_Bz};
   for (int k = 0; k < 8; ++k) G.out[k] = outs[k];
   if (fuse) {
+    fuse_neighbour3(G);
     fuse_stencil_pairs(G);
     fold_sums(G);
     fold_affine(G);

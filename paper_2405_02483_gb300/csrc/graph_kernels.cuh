@@ -153,8 +153,11 @@ __device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T i
     T wim, wi0, woi, wop;
     max_w(am, a0, wim, wi0);
     max_w(inner, ap, woi, wop);
-    const T dq_da2 = (T)1 / den + iq * (-a2 / (den * den));
-    const T dq_dM = -a2 / (den * den);
+    // a2 / den^2 as q / den: den^2 underflows in FP32 where T and D2 T are
+    // both zero (den = 1e-30), and 0 / 0 would poison the cotangent.
+    const T qd = q / den;
+    const T dq_da2 = (T)1 / den - iq * qd;
+    const T dq_dM = -qd;
     const T sd = sgn(d2);
     dq[0] = dq_da2 * sd + dq_dM * (cM * (woi * wim)) * sgn(vm);
     dq[1] = dq_da2 * sd * (T)-2 + dq_dM * (cM * (woi * wi0) + cP) * sgn(v0);
@@ -276,6 +279,13 @@ __device__ __forceinline__ T fwd_value(int op, const GNode& nd, const T* A, cons
     case G_STMUL:
       return stencil_fn<T>([&](long long j) { return A[j] * B[j]; }, c, nd.axis, nd.sk,
                            kc<T>(nd.c0, nd.f0), g);
+    case G_STEXP: return exp(stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g));
+    case G_NB3: {
+      const T m = A[nbr(c, nd.axis, nd.sk, g)], z = A[idx], p = A[nbr(c, nd.axis, -nd.sk, g)];
+      if (nd.iop == G_ADD) return (m + z) + p;
+      const T in = m >= z ? m : z;
+      return in >= p ? in : p;
+    }
     case G_ST2: {
       const T s1 = stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g);
       const T s2 = stencil_at(B, c, nd.axis2, nd.sk2, kc<T>(nd.h2, nd.fh2), g);
@@ -369,6 +379,35 @@ __device__ __forceinline__ void bwd_value(int op, const GNode& nd, const T* A, c
     if (st_negates(nd.sk)) v = -v;
     ca = v * B[idx];
     cb = v * A[idx];
+  } else if (op == G_STEXP) {
+    // y = ps exp(st(a)) + pt: the stencil's transpose of g (y - pt), the
+    // epilogue's factor included (it is in y).
+    const T pt = kc<T>(nd.pt, nd.fpt);
+    T v = stencil_fn<T>([&](long long j) { return gout[j] * (out[j] - pt); }, c, nd.axis,
+                        st_transpose(nd.sk), kc<T>(nd.c0, nd.f0), g);
+    ca = st_negates(nd.sk) ? -v : v;
+  } else if (op == G_NB3) {
+    // Gather over the three outputs y = x - o, x, x + o (o = sk) that read x
+    // as their a(y + o), a(y), a(y - o); a max passes g by the primitive
+    // nodes' rule (an even split on a tie, the inner pair first).
+    const int ax = nd.axis, o = nd.sk;
+    const T gm = gout[nbr(c, ax, -o, g)], g0 = gout[idx], gp = gout[nbr(c, ax, o, g)];
+    if (nd.iop == G_ADD) {
+      ca = (gm + g0) + gp;
+    } else {
+      const T a0 = A[idx], am = A[nbr(c, ax, -o, g)], am2 = A[nbr(c, ax, -2 * o, g)];
+      const T ap = A[nbr(c, ax, o, g)], ap2 = A[nbr(c, ax, 2 * o, g)];
+      T wm, wz, wi, wp;
+      max_w(a0, am, wm, wz);   // y = x - o: (a0 op am) op am2, x in the inner first slot
+      max_w(a0 >= am ? a0 : am, am2, wi, wp);
+      T acc = gm * (wi * wm);
+      max_w(ap, a0, wm, wz);   // y = x: (ap op a0) op am, x in the inner second slot
+      max_w(ap >= a0 ? ap : a0, am, wi, wp);
+      acc += g0 * (wi * wz);
+      max_w(ap2, ap, wm, wz);  // y = x + o: (ap2 op ap) op a0, x the outer second slot
+      max_w(ap2 >= ap ? ap2 : ap, a0, wi, wp);
+      ca = acc + gp * wp;
+    }
   } else if (op == G_ST2) {
     // y = st1(a) +- st2(b): each stencil's transpose of the cotangent.
     const T v1 = stencil_at(gout, c, nd.axis, st_transpose(nd.sk), kc<T>(nd.c0, nd.f0), g);
@@ -395,7 +434,7 @@ __device__ __forceinline__ void bwd_value(int op, const GNode& nd, const T* A, c
         cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
         break;
       }
-      case G_EXP: ca = gg * out[idx]; break;
+      case G_EXP: ca = gg * (out[idx] - kc<T>(nd.pt, nd.fpt)); break;   // ps exp(a) = y - pt
       case G_LOG: ca = gg / A[idx]; break;
       case G_LOG1P: ca = gg / ((T)1 + A[idx]); break;
       case G_SQRT: ca = gg / ((T)2 * out[idx]); break;
@@ -431,7 +470,8 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
     const GCell c = gcell_at(c0, u, g);
     if (c.k < g.nz) {
       bwd_value(OP, nd, A, B, out, gout, c, g, ca[u], cb[u]);
-      if (nd.ep || nd.pop == 3) {
+      // exp's transposes take the epilogue's factor from their own value.
+      if ((nd.ep && OP != G_EXP && OP != G_STEXP) || nd.pop == 3) {
         ca[u] *= sv;
         cb[u] *= sv;
       }

@@ -1,15 +1,17 @@
 // Host build of the op graph: the graph with its merged nodes (fused stencil
-// pairs and stencil sums, folded sums and scalings) against the graph of one
-// node per primitive, both swept by the same forward and transpose kernels run
-// over their launch grids one thread at a time.  The forward outputs must be
-// equal bit for bit; the reverse sweep's input gradients may differ only by
-// rounding (the merged transposes scale a gathered cotangent instead of
-// gathering a scaled one): within 1e-12 (FP64) or 1e-5 (FP32) of each
-// field's largest gradient.  Cases: the benchmark's viscosity and quench; with
-// chromospheric and coronal cooling (plane means, exp, sqrt); Smagorinsky
-// with the bulk term, gravity, ediffav, ln(P/P_aver), the second-order switch
-// and no log interpolation on a stretched z mesh.  Exit status: the number of
-// failing (case, precision) pairs.
+// pairs, stencil sums and exps, 3-cell maxima and sums, folded sums and
+// scalings) against the graph of one node per primitive, both swept by the
+// same forward and transpose kernels run over their launch grids one thread
+// at a time.  The forward outputs must be equal bit for bit; the reverse
+// sweep's input gradients may differ only by rounding (the merged transposes
+// scale a gathered cotangent instead of gathering a scaled one): within 1e-12
+// (FP64) or 1e-5 (FP32) of each field's largest gradient.  Cases: the
+// benchmark's viscosity and quench (also on a state uniform along z, whose
+// maxima along z tie exactly); with chromospheric and coronal cooling (plane
+// means, exp, sqrt); Smagorinsky with the bulk term, gravity, ediffav,
+// ln(P/P_aver), the second-order switch and no log interpolation on a
+// stretched z mesh.  Exit status: the number of failing (case, precision)
+// pairs.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdio>
@@ -109,7 +111,7 @@ struct HostExec {
       switch (nd.op) {
         case G_PMEAN: pmean(A, out, false); break;
         case G_QUENCH: run(G, [&] { g_quench_f<T>(nd, A, out, G); }); break;
-        FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_ADD) FW(G_SUB)
+        FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_STEXP) FW(G_NB3) FW(G_ADD) FW(G_SUB)
         FW(G_MUL) FW(G_DIV) FW(G_MAX) FW(G_EXP) FW(G_LOG) FW(G_LOG1P) FW(G_SQRT) FW(G_ABS)
         FW(G_AXPB) FW(G_CLAMPMIN) FW(G_CLAMPMAX) FW(G_STEP) FW(G_ZFIELD) FW(G_CONST)
         default: printf("no forward for op %d\n", nd.op); exit(100);
@@ -140,7 +142,7 @@ struct HostExec {
           run(G, [&] { g_quench_b1<T>(nd, A, go, S.data(), G); });
           run(G, [&] { g_quench_b3<T>(nd, A, S.data(), gA, WA, G); });
           break;
-        BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_ADD) BW(G_SUB)
+        BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_STEXP) BW(G_NB3) BW(G_ADD) BW(G_SUB)
         BW(G_MUL) BW(G_DIV) BW(G_MAX) BW(G_EXP) BW(G_LOG) BW(G_LOG1P) BW(G_SQRT) BW(G_ABS)
         BW(G_AXPB) BW(G_CLAMPMIN) BW(G_CLAMPMAX)
         default: printf("no transpose for op %d\n", nd.op); exit(100);
@@ -175,14 +177,20 @@ static stagger_params base_params() {
   return p;
 }
 
+// zuni: every input field uniform along z, so that the 3-cell maxima along z
+// meet exact ties (split evenly by the transposes).
 template <typename T>
-static int compare(const char* name, const stagger_grid& gg, const stagger_params& p, double tol) {
+static int compare(const char* name, const stagger_grid& gg, const stagger_params& p, double tol,
+                   bool zuni = false) {
   const Geo g = make_geo(gg.nx, gg.ny, gg.nz);
   std::mt19937_64 rng(7);
   std::uniform_real_distribution<double> U(-1.0, 1.0);
   std::vector<std::vector<T>> in(8, std::vector<T>(g.n)), seed(8, std::vector<T>(g.n));
   for (int k = 0; k < 8; ++k)
     for (auto& x : in[k]) x = (T)((k == 0 || k == 4 ? 0.1 : 0.3) * U(rng));
+  if (zuni)
+    for (int k = 0; k < 8; ++k)
+      for (long long q = g.sz; q < g.n; ++q) in[k][q] = in[k][q % g.sz];
   for (int k = 0; k < 8; ++k)
     for (auto& x : seed[k]) x = (T)U(rng);
   std::vector<std::vector<T>> res[2], gin[2];
@@ -248,6 +256,8 @@ int main() {
   opts.zf = zf.data();
   fails += compare<double>("viscosity+quench", g1, visc, 1e-12);
   fails += compare<float>("viscosity+quench", g1, visc, 1e-5);
+  fails += compare<double>("viscosity+quench z-uniform", g1, visc, 1e-12, true);
+  fails += compare<float>("viscosity+quench z-uniform", g1, visc, 1e-5, true);
   fails += compare<double>("cooling", g1, cool, 1e-12);
   fails += compare<float>("cooling", g1, cool, 1e-5);
   fails += compare<double>("options+stretched", g2, opts, 1e-12);

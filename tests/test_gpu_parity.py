@@ -419,7 +419,11 @@ def test_adjoint_matches_oracle(S, name):
     """FP64 GPU adjoint vs the oracle's reverse sweep to 1e-10 on every state.
     FP32 to 1e-4 relative L2 on states without exact ties; the Orszag-Tang
     state puts exact ties of max and |T| on symmetry points, which FP32 and
-    FP64 break differently (measured 2e-3 there), so FP32 is not compared on it."""
+    FP64 break differently, so there FP32 is only checked to be finite (its
+    stresses with a z derivative are exactly zero, where the quench's
+    transpose once formed 0/0) and within a loose bound (measured 2.4e-2 on
+    GB300; the merged and the one-node-per-primitive graphs agree to rounding
+    on such states, tests/host_emulation/graph_fusion.cpp)."""
     if name == "waves16_ideal":
         w, kw = inputs.linear_waves(16), {}
     elif name.startswith("ragged"):
@@ -442,9 +446,10 @@ def test_adjoint_matches_oracle(S, name):
     torch.cuda.synchronize()
     e64 = err_max([t.cpu().numpy() for t in out64], ref)
     assert max(e64) < 1e-10, e64
-    if not name.startswith("ot3d"):
-        e32 = err_l2([t.double().cpu().numpy() for t in out32], ref)
-        assert max(e32) < 1e-4, e32
+    assert all(bool(torch.isfinite(t).all()) for t in out32)
+    e32 = err_l2([t.double().cpu().numpy() for t in out32], ref)
+    print(name, "FP32 adjoint rel L2", max(e32))
+    assert max(e32) < (5e-2 if name.startswith("ot3d") else 1e-4), e32
     sim.close()
 
 

@@ -53,4 +53,5 @@ def test_one_cell_and_four_cell_threads_give_the_same_rhs(tmp_path):
 
 def test_merged_op_graph_equals_one_node_per_primitive(tmp_path):
     out = _build_and_run(tmp_path, "graph_fusion")
-    assert out.count("forward 0 differing values, 0 non-finite") == 6, out
+    assert out.count("forward 0 differing values, 0 non-finite") == 8, out
+    assert "FAIL" not in out, out
