@@ -3,6 +3,8 @@
 // over several.
 #include <math.h>
 
+#include <stdint.h>
+
 #include <algorithm>
 
 #include "graph_kernels.cuh"
@@ -28,7 +30,7 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
     has_quench |= nd.op == G_QUENCH;
   }
   if (has_quench && with_grads &&
-      cudaMalloc(&qscr, sizeof(T) * 7 * (size_t)g.n) != cudaSuccess) {
+      cudaMalloc(&qscr, sizeof(T) * 15 * (size_t)g.n) != cudaSuccess) {
     qscr = nullptr;
     release();
     return STAGGER_EOOM;
@@ -128,12 +130,19 @@ static inline dim3 ggrid(const Geo& g) {
               (unsigned)((g.nz + GBZ * GZU - 1) / (GBZ * GZU)));
 }
 
-// The forward and transpose kernel of each op (the op a template constant).
+// The forward and transpose kernel of each op (the op a template constant):
+// the stencil-like ops on the 3-D launch grid, the pointwise ops as flat
+// kernels (pointwise_op).
 template <typename T>
 using FwdK = void (*)(GNode, const T*, const T*, const T*, T*, const T*, Geo);
 template <typename T>
 using BwdK = void (*)(GNode, const T*, const T*, const T*, const T*, T*, T*, T*, int, int, int,
                       Geo);
+template <typename T>
+using FwdPwK = void (*)(GNode, const T*, const T*, const T*, T*, long long, int);
+template <typename T>
+using BwdPwK = void (*)(GNode, const T*, const T*, const T*, const T*, T*, T*, T*, int, int, int,
+                        long long, int);
 
 template <typename T>
 static FwdK<T> fwd_kernel(int op) {
@@ -143,24 +152,9 @@ static FwdK<T> fwd_kernel(int op) {
     case G_STBIN: return g_forward<T, G_STBIN>;
     case G_STMUL: return g_forward<T, G_STMUL>;
     case G_ST2: return g_forward<T, G_ST2>;
-    case G_ADD: return g_forward<T, G_ADD>;
-    case G_SUB: return g_forward<T, G_SUB>;
-    case G_MUL: return g_forward<T, G_MUL>;
-    case G_DIV: return g_forward<T, G_DIV>;
-    case G_MAX: return g_forward<T, G_MAX>;
-    case G_EXP: return g_forward<T, G_EXP>;
     case G_STEXP: return g_forward<T, G_STEXP>;
     case G_NB3: return g_forward<T, G_NB3>;
-    case G_LOG: return g_forward<T, G_LOG>;
-    case G_LOG1P: return g_forward<T, G_LOG1P>;
-    case G_SQRT: return g_forward<T, G_SQRT>;
-    case G_ABS: return g_forward<T, G_ABS>;
-    case G_AXPB: return g_forward<T, G_AXPB>;
-    case G_CLAMPMIN: return g_forward<T, G_CLAMPMIN>;
-    case G_CLAMPMAX: return g_forward<T, G_CLAMPMAX>;
-    case G_STEP: return g_forward<T, G_STEP>;
-    case G_ZFIELD: return g_forward<T, G_ZFIELD>;
-    default: return g_forward<T, G_CONST>;
+    default: return g_forward<T, G_ZFIELD>;
   }
 }
 
@@ -168,27 +162,61 @@ template <typename T>
 static BwdK<T> bwd_kernel(int op) {
   switch (op) {
     case G_STENCIL: return g_backward<T, G_STENCIL>;
-    case G_SHIFT: return g_backward<T, G_SHIFT>;
     case G_STBIN: return g_backward<T, G_STBIN>;
     case G_STMUL: return g_backward<T, G_STMUL>;
     case G_ST2: return g_backward<T, G_ST2>;
-    case G_ADD: return g_backward<T, G_ADD>;
-    case G_SUB: return g_backward<T, G_SUB>;
-    case G_MUL: return g_backward<T, G_MUL>;
-    case G_DIV: return g_backward<T, G_DIV>;
-    case G_MAX: return g_backward<T, G_MAX>;
-    case G_EXP: return g_backward<T, G_EXP>;
     case G_STEXP: return g_backward<T, G_STEXP>;
     case G_NB3: return g_backward<T, G_NB3>;
-    case G_LOG: return g_backward<T, G_LOG>;
-    case G_LOG1P: return g_backward<T, G_LOG1P>;
-    case G_SQRT: return g_backward<T, G_SQRT>;
-    case G_ABS: return g_backward<T, G_ABS>;
-    case G_AXPB: return g_backward<T, G_AXPB>;
-    case G_CLAMPMIN: return g_backward<T, G_CLAMPMIN>;
-    case G_CLAMPMAX: return g_backward<T, G_CLAMPMAX>;
-    default: return g_backward<T, G_CONST>;   // no contribution
+    default: return g_backward<T, G_SHIFT>;
   }
+}
+
+template <typename T>
+static FwdPwK<T> fwd_kernel_pw(int op) {
+  switch (op) {
+    case G_ADD: return g_forward_pw<T, G_ADD>;
+    case G_SUB: return g_forward_pw<T, G_SUB>;
+    case G_MUL: return g_forward_pw<T, G_MUL>;
+    case G_DIV: return g_forward_pw<T, G_DIV>;
+    case G_MAX: return g_forward_pw<T, G_MAX>;
+    case G_EXP: return g_forward_pw<T, G_EXP>;
+    case G_LOG: return g_forward_pw<T, G_LOG>;
+    case G_LOG1P: return g_forward_pw<T, G_LOG1P>;
+    case G_SQRT: return g_forward_pw<T, G_SQRT>;
+    case G_ABS: return g_forward_pw<T, G_ABS>;
+    case G_AXPB: return g_forward_pw<T, G_AXPB>;
+    case G_CLAMPMIN: return g_forward_pw<T, G_CLAMPMIN>;
+    case G_CLAMPMAX: return g_forward_pw<T, G_CLAMPMAX>;
+    case G_STEP: return g_forward_pw<T, G_STEP>;
+    default: return g_forward_pw<T, G_CONST>;
+  }
+}
+
+template <typename T>
+static BwdPwK<T> bwd_kernel_pw(int op) {
+  switch (op) {
+    case G_ADD: return g_backward_pw<T, G_ADD>;
+    case G_SUB: return g_backward_pw<T, G_SUB>;
+    case G_MUL: return g_backward_pw<T, G_MUL>;
+    case G_DIV: return g_backward_pw<T, G_DIV>;
+    case G_MAX: return g_backward_pw<T, G_MAX>;
+    case G_EXP: return g_backward_pw<T, G_EXP>;
+    case G_LOG: return g_backward_pw<T, G_LOG>;
+    case G_LOG1P: return g_backward_pw<T, G_LOG1P>;
+    case G_SQRT: return g_backward_pw<T, G_SQRT>;
+    case G_ABS: return g_backward_pw<T, G_ABS>;
+    case G_AXPB: return g_backward_pw<T, G_AXPB>;
+    case G_CLAMPMIN: return g_backward_pw<T, G_CLAMPMIN>;
+    default: return g_backward_pw<T, G_CLAMPMAX>;
+  }
+}
+
+// Flat launch of a pointwise kernel: four cells a thread when every array is
+// 16-byte aligned and n a multiple of 4.
+static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+static inline unsigned pw_blocks(long long work) {
+  const long long b = (work + 255) / 256;
+  return (unsigned)(b < 8192 ? (b > 0 ? b : 1) : 8192);
 }
 
 // Fork the auxiliary streams from s (they then follow everything enqueued on
@@ -247,7 +275,13 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
       g_quench_f<T><<<gg, gb, 0, st>>>(nd, A, ptr[i], geo);
       ++launches;
     } else {
-      fwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
+      if (pointwise_op(nd.op)) {
+        const int vec = geo.n % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(ptr[i]);
+        fwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
+            nd, A, B, C, ptr[i], geo.n, vec);
+      } else {
+        fwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
+      }
       ++launches;
     }
     if (nconc) STG_CUDA_OK(cudaEventRecord(evn[i], st));
@@ -302,12 +336,22 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
       g_plane_bcast<T><<<gg, gb, 0, st>>>(psum, gA, wa[i] ? 0 : 1, geo);
       launches += 2;
     } else if (nd.op == G_QUENCH) {
-      g_quench_b1<T><<<gg, gb, 0, st>>>(nd, A, grads + (size_t)i * geo.n, qscr, geo);
-      g_quench_b3<T><<<gg, gb, 0, st>>>(nd, A, qscr, gA, wa[i], geo);
-      launches += 2;
+      T* Q = qscr + (size_t)7 * geo.n;   // q and its derivatives, 4 arrays per axis slot
+      g_quench_q<T><<<gg, gb, 0, st>>>(nd, A, Q, geo);
+      g_quench_b1<T><<<gg, gb, 0, st>>>(nd, A, Q, grads + (size_t)i * geo.n, qscr, geo);
+      g_quench_b3<T><<<gg, gb, 0, st>>>(nd, Q, qscr, gA, wa[i], geo);
+      launches += 3;
     } else {
-      bwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, ptr[i], grads + (size_t)i * geo.n, gA,
-                                              gB, gC, wa[i], wb[i], wc[i], geo);
+      T* gi = grads + (size_t)i * geo.n;
+      if (pointwise_op(nd.op)) {
+        const int vec = geo.n % 4 == 0 && al16(A) && al16(B) && al16(ptr[i]) && al16(gi) &&
+                        al16(gA) && al16(gB) && al16(gC);
+        bwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
+            nd, A, B, ptr[i], gi, gA, gB, gC, wa[i], wb[i], wc[i], geo.n, vec);
+      } else {
+        bwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, ptr[i], gi, gA, gB, gC, wa[i], wb[i],
+                                                wc[i], geo);
+      }
       ++launches;
     }
     if (nconc) {

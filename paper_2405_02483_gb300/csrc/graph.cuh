@@ -131,7 +131,7 @@ struct GraphExec {
   T* vals = nullptr;     // node values (non-input nodes)
   T* mesh = nullptr;     // the mesh arrays of G_ZFIELD on the device, or null
   T* psum = nullptr;     // per-plane sums of G_PMEAN (nz), or null
-  T* qscr = nullptr;     // 7 arrays of scratch for the G_QUENCH transpose, or null
+  T* qscr = nullptr;     // 15 arrays of scratch for the G_QUENCH transpose, or null
   T* grads = nullptr;    // node gradients (all nodes)
   std::vector<T*> ptr;   // value pointer per node
   // Reverse sweep: node receives a gradient; its a / b / c slot writes

@@ -74,6 +74,22 @@ __device__ __forceinline__ long long nbr(const GCell& c, int axis, int o, const 
   return c.idx + (long long)(wrap(c.k + o, g.nz) - c.k) * g.sz;
 }
 
+// The values v(j) at the seven taps c - 3 .. c + 3 along an axis: plain
+// strides away from the periodic seam, wrapped indices within 3 cells of it.
+template <typename T, class V>
+__device__ __forceinline__ void taps7(V v, const GCell& c, int axis, const Geo& g, T t[7]) {
+  const long long st = axis == 0 ? 1 : axis == 1 ? g.sy : g.sz;
+  const int pos = axis == 0 ? c.i : axis == 1 ? c.j : c.k;
+  const int n = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
+  if (pos >= 3 && pos + 3 < n) {
+#pragma unroll
+    for (int o = -3; o <= 3; ++o) t[o + 3] = v(c.idx + o * st);
+  } else {
+#pragma unroll
+    for (int o = -3; o <= 3; ++o) t[o + 3] = v(c.idx + (long long)(wrap(pos + o, n) - pos) * st);
+  }
+}
+
 // Stencil value at c: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
 // are eq. (deriv) to i+1/2 and i-1/2, divided by the spacing h.
 template <typename T>
@@ -81,9 +97,9 @@ __device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, in
                                         const Geo& g) {
   const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
   const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
-  T m3 = f[nbr(c, axis, -3, g)], m2 = f[nbr(c, axis, -2, g)], m1 = f[nbr(c, axis, -1, g)];
-  T z0 = f[c.idx], p1 = f[nbr(c, axis, 1, g)], p2 = f[nbr(c, axis, 2, g)],
-    p3 = f[nbr(c, axis, 3, g)];
+  T t[7];
+  taps7<T>([&](long long j) { return f[j]; }, c, axis, g, t);
+  const T m3 = t[0], m2 = t[1], m1 = t[2], z0 = t[3], p1 = t[4], p2 = t[5], p3 = t[6];
   switch (kind) {
     case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
     case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
@@ -98,9 +114,9 @@ __device__ __forceinline__ T stencil_fn(V v, const GCell& c, int axis, int kind,
                                         const Geo& g) {
   const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
   const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
-  T m3 = v(nbr(c, axis, -3, g)), m2 = v(nbr(c, axis, -2, g)), m1 = v(nbr(c, axis, -1, g));
-  T z0 = v(c.idx), p1 = v(nbr(c, axis, 1, g)), p2 = v(nbr(c, axis, 2, g)),
-    p3 = v(nbr(c, axis, 3, g));
+  T t[7];
+  taps7<T>(v, c, axis, g, t);
+  const T m3 = t[0], m2 = t[1], m1 = t[2], z0 = t[3], p1 = t[4], p2 = t[5], p3 = t[6];
   switch (kind) {
     case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
     case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
@@ -167,17 +183,16 @@ __device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T i
 }
 
 // fac at c, and (when wq) the weights of the three q of each axis in fac:
-// wq[3 t + p + 1] for axis t and position p.
-template <typename T>
-__device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int a1, T iq, T eps,
-                                        const Geo& g, T* wq) {
+// wq[3 t + p + 1] for axis t and position p.  qf(t, ax, s) is q at
+// c + s e_ax (axis slot t): formed from T, or read from the transpose's
+// per-cell q arrays.
+template <typename T, class QF>
+__device__ __forceinline__ T quench_fac(QF qf, int a0, int a1, T* wq) {
   T m[2] = {0, 0}, w[2][3];
   for (int t = 0; t < 2; ++t) {
     const int ax = t == 0 ? a0 : a1;
     if (ax < 0) continue;
-    const T qm = q_at(A, c, ax, -1, iq, eps, g, (T*)nullptr),
-            q0 = q_at(A, c, ax, 0, iq, eps, g, (T*)nullptr),
-            qp = q_at(A, c, ax, 1, iq, eps, g, (T*)nullptr);
+    const T qm = qf(t, ax, -1), q0 = qf(t, ax, 0), qp = qf(t, ax, 1);
     const T inner = qm >= q0 ? qm : q0;
     m[t] = inner >= qp ? inner : qp;
     T wim, wi0, woi, wop;
@@ -200,19 +215,43 @@ __device__ __forceinline__ T quench_fac(const T* A, const GCell& c, int a0, int 
   return fac;
 }
 
+// Transpose, q pass (per cell z, per axis slot t): q(z) and its derivatives
+// with respect to T at z - 1, z, z + 1, into Q[(4 t + 0 .. 3) n + z], formed
+// once here instead of at every tap of the two passes that follow.
+template <typename T>
+__global__ void g_quench_q(GNode nd, const T* A, T* Q, Geo g) {
+  GCell c0;
+  if (!gcell(c0, g)) return;
+  const T iq = (T)1 / kc<T>(nd.c0, nd.f0), eps = kc<T>(nd.c2, nd.f2);
+  for (int u = 0; u < GZU; ++u) {
+    const GCell c = gcell_at(c0, u, g);
+    if (c.k >= g.nz) break;
+    for (int t = 0; t < 2; ++t) {
+      const int ax = t == 0 ? nd.axis : nd.sk;
+      if (ax < 0) continue;
+      T dq[3];
+      const T q = q_at(A, c, ax, 0, iq, eps, g, dq);
+      Q[(long long)(4 * t) * g.n + c.idx] = q;
+      for (int k = 0; k < 3; ++k) Q[(long long)(4 * t + 1 + k) * g.n + c.idx] = dq[k];
+    }
+  }
+}
+
 // Transpose, first pass (per output cell y): S0 = gbar C (the product's own
 // term) and S[1 + 3 t + p + 1] = gbar T dC/dfac dfac/dq, the cotangent each
 // q of axis t at position p receives from y.
 template <typename T>
-__global__ void g_quench_b1(GNode nd, const T* A, const T* gout, T* S, Geo g) {
+__global__ void g_quench_b1(GNode nd, const T* A, const T* Q, const T* gout, T* S, Geo g) {
   GCell c0;
   if (!gcell(c0, g)) return;
-  const T iq = (T)1 / kc<T>(nd.c0, nd.f0), qlim = kc<T>(nd.c1, nd.f1);
+  const T qlim = kc<T>(nd.c1, nd.f1);
   for (int u = 0; u < GZU; ++u) {
     const GCell c = gcell_at(c0, u, g);
     if (c.k >= g.nz) break;
     T wq[6];
-    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, kc<T>(nd.c2, nd.f2), g, wq);
+    const T fac = quench_fac<T>(
+        [&](int t, int ax, int s) { return Q[(long long)(4 * t) * g.n + nbr(c, ax, s, g)]; },
+        nd.axis, nd.sk, wq);
     const T gg = gout[c.idx];
     const T C = fac > qlim ? qlim : fac;
     const T dC = fac <= qlim ? (T)1 : (T)0;
@@ -226,10 +265,9 @@ __global__ void g_quench_b1(GNode nd, const T* A, const T* gout, T* S, Geo g) {
 // the axes and the three q positions z = x + r e_a whose stencils hold x of
 // qbar(z) dq(z)/dT(x), qbar(z) = sum_p S[.. p](z - p e_a).
 template <typename T>
-__global__ void g_quench_b3(GNode nd, const T* A, const T* S, T* gA, int wA, Geo g) {
+__global__ void g_quench_b3(GNode nd, const T* Q, const T* S, T* gA, int wA, Geo g) {
   GCell c0;
   if (!gcell(c0, g)) return;
-  const T iq = (T)1 / kc<T>(nd.c0, nd.f0);
   for (int u = 0; u < GZU; ++u) {
     const GCell c = gcell_at(c0, u, g);
     if (c.k >= g.nz) break;
@@ -241,9 +279,8 @@ __global__ void g_quench_b3(GNode nd, const T* A, const T* S, T* gA, int wA, Geo
         T qbar = 0;
         for (int p = -1; p <= 1; ++p)
           qbar += S[(long long)(1 + 3 * t + p + 1) * g.n + nbr(c, ax, r - p, g)];
-        T dq[3];
-        q_at(A, c, ax, r, iq, kc<T>(nd.c2, nd.f2), g, dq);
-        acc += qbar * dq[1 - r];
+        // d q(z) / d T(x), z = x + r e_ax: the derivative at z's tap 1 - r.
+        acc += qbar * Q[(long long)(4 * t + 2 - r) * g.n + nbr(c, ax, r, g)];
       }
     }
     gA[c.idx] = wA ? acc : gA[c.idx] + acc;
@@ -259,7 +296,10 @@ __global__ void g_quench_f(GNode nd, const T* A, T* out, Geo g) {
     const GCell c = gcell_at(c0, u, g);
     if (c.k >= g.nz) break;
     const T iq = (T)1 / kc<T>(nd.c0, nd.f0), qlim = kc<T>(nd.c1, nd.f1);
-    const T fac = quench_fac(A, c, nd.axis, nd.sk, iq, kc<T>(nd.c2, nd.f2), g, (T*)nullptr);
+    const T eps = kc<T>(nd.c2, nd.f2);
+    const T fac = quench_fac<T>(
+        [&](int, int ax, int s) { return q_at(A, c, ax, s, iq, eps, g, (T*)nullptr); }, nd.axis,
+        nd.sk, (T*)nullptr);
     out[c.idx] = A[c.idx] * (fac > qlim ? qlim : fac);
   }
 }
@@ -292,26 +332,99 @@ __device__ __forceinline__ T fwd_value(int op, const GNode& nd, const T* A, cons
       return nd.iop == G_ADD ? s1 + s2 : s1 - s2;
     }
     case G_SHIFT: return A[nbr(c, nd.axis, nd.sk, g)];
-    case G_ADD: return A[idx] + B[idx];
-    case G_SUB: return A[idx] - B[idx];
-    case G_MUL: return A[idx] * B[idx];
-    case G_DIV: return A[idx] / B[idx];
-    case G_MAX: return A[idx] >= B[idx] ? A[idx] : B[idx];
-    case G_EXP: return exp(A[idx]);
-    case G_LOG: return log(A[idx]);
-    case G_LOG1P: return log1p(A[idx]);
-    case G_SQRT: return sqrt(A[idx]);
-    case G_ABS: return fabs(A[idx]);
-    case G_AXPB: return kc<T>(nd.c0, nd.f0) * A[idx] + kc<T>(nd.c1, nd.f1);
-    case G_CLAMPMIN: return A[idx] < kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : A[idx];
-    case G_CLAMPMAX: return A[idx] > kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : A[idx];
-    case G_STEP: return A[idx] > kc<T>(nd.c0, nd.f0) ? (T)1 : (T)0;
-    case G_ZFIELD: return mesh[(long long)nd.sk * g.nz + c.k];
+    default: return mesh[(long long)nd.sk * g.nz + c.k];   // G_ZFIELD
+  }
+}
+
+// The ops whose value at a cell reads only that cell of their operands: they
+// run as flat kernels over the arrays (g_forward_pw, g_backward_pw).
+__host__ __device__ __forceinline__ bool pointwise_op(int op) {
+  return op == G_ADD || op == G_SUB || op == G_MUL || op == G_DIV || op == G_MAX ||
+         op == G_EXP || op == G_LOG || op == G_LOG1P || op == G_SQRT || op == G_ABS ||
+         op == G_AXPB || op == G_CLAMPMIN || op == G_CLAMPMAX || op == G_STEP || op == G_CONST;
+}
+
+// A pointwise op's value from its operands' values a, b at the cell.
+template <typename T>
+__device__ __forceinline__ T pw_value(int op, const GNode& nd, T a, T b) {
+  switch (op) {
+    case G_ADD: return a + b;
+    case G_SUB: return a - b;
+    case G_MUL: return a * b;
+    case G_DIV: return a / b;
+    case G_MAX: return a >= b ? a : b;
+    case G_EXP: return exp(a);
+    case G_LOG: return log(a);
+    case G_LOG1P: return log1p(a);
+    case G_SQRT: return sqrt(a);
+    case G_ABS: return fabs(a);
+    case G_AXPB: return kc<T>(nd.c0, nd.f0) * a + kc<T>(nd.c1, nd.f1);
+    case G_CLAMPMIN: return a < kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : a;
+    case G_CLAMPMAX: return a > kc<T>(nd.c0, nd.f0) ? kc<T>(nd.c0, nd.f0) : a;
+    case G_STEP: return a > kc<T>(nd.c0, nd.f0) ? (T)1 : (T)0;
     default: return kc<T>(nd.c0, nd.f0);  // G_CONST
   }
 }
 
-// Every node but G_QUENCH (g_quench_f) and G_PMEAN; one instance per op.
+// The folded sum and the epilogue of a node's value v (C's value cv).
+template <typename T>
+__device__ __forceinline__ T finish(const GNode& nd, T v, T cv) {
+  if (nd.pop) v = nd.pop == 1 ? v + cv : nd.pop == 2 ? v - cv : cv - v;
+  return nd.ep ? kc<T>(nd.ps, nd.fps) * v + kc<T>(nd.pt, nd.fpt) : v;
+}
+
+// Four consecutive elements i .. i + 3 as 16-byte loads and stores (i a
+// multiple of 4, the array 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, long long i, T (&v)[4]) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const float4 x = *reinterpret_cast<const float4*>(p + i);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2*>(p + i);
+    const double2 y = *reinterpret_cast<const double2*>(p + i + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, long long i, const T (&v)[4]) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    *reinterpret_cast<float4*>(p + i) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p + i) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + i + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+// Pointwise forward over n cells: with vec (every array 16-byte aligned and n
+// a multiple of 4) four cells a thread through 16-byte accesses, which keeps
+// enough bytes in flight per SM; else one cell at a time.  Grid-stride.
+template <typename T, int OP>
+__global__ void g_forward_pw(GNode nd, const T* A, const T* B, const T* C, T* out, long long n,
+                             int vec) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    for (; t < n / 4; t += stride) {
+      const long long i = 4 * t;
+      T a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, cv[4] = {0, 0, 0, 0}, r[4];
+      if (A) ld4(A, i, a);
+      if (B) ld4(B, i, b);
+      if (nd.pop) ld4(C, i, cv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = finish(nd, pw_value(OP, nd, a[k], b[k]), cv[k]);
+      st4(out, i, r);
+    }
+  } else {
+    for (; t < n; t += stride) {
+      const T a = A ? A[t] : (T)0, b = B ? B[t] : (T)0, cv = nd.pop ? C[t] : (T)0;
+      out[t] = finish(nd, pw_value(OP, nd, a, b), cv);
+    }
+  }
+}
+
+// Every node but the pointwise ones, G_QUENCH (g_quench_f) and G_PMEAN; one
+// instance per op.
 template <typename T, int OP>
 __global__ void g_forward(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
                           Geo g) {
@@ -321,17 +434,8 @@ __global__ void g_forward(GNode nd, const T* A, const T* B, const T* C, T* out, 
 #pragma unroll
   for (int u = 0; u < GZU; ++u) {
     const GCell c = gcell_at(c0, u, g);
-    if (c.k < g.nz) {
-      r[u] = fwd_value(OP, nd, A, B, mesh, c, g);
-      if (nd.pop) {
-        const T cv = C[c.idx];
-        r[u] = nd.pop == 1 ? r[u] + cv : nd.pop == 2 ? r[u] - cv : cv - r[u];
-      }
-    }
-  }
-  if (nd.ep) {
-#pragma unroll
-    for (int u = 0; u < GZU; ++u) r[u] = kc<T>(nd.ps, nd.fps) * r[u] + kc<T>(nd.pt, nd.fpt);
+    if (c.k < g.nz)
+      r[u] = finish(nd, fwd_value(OP, nd, A, B, mesh, c, g), nd.pop ? C[c.idx] : (T)0);
   }
 #pragma unroll
   for (int u = 0; u < GZU; ++u) {
@@ -414,39 +518,106 @@ __device__ __forceinline__ void bwd_value(int op, const GNode& nd, const T* A, c
     const T v2 = stencil_at(gout, c, nd.axis2, st_transpose(nd.sk2), kc<T>(nd.h2, nd.fh2), g);
     ca = st_negates(nd.sk) ? -v1 : v1;
     cb = (st_negates(nd.sk2) != (nd.iop == G_SUB)) ? -v2 : v2;
-  } else if (op == G_SHIFT) {
+  } else {   // G_SHIFT
     ca = gout[nbr(c, nd.axis, -nd.sk, g)];
+  }
+}
+
+// A pointwise op's cotangents of a and b from y = its value and gg = y's
+// cotangent (before the folded sum's sign and the epilogue's factor, which
+// the kernel applies; exp reads ps exp(a) = y - pt itself).
+template <typename T>
+__device__ __forceinline__ void pw_grad(int op, const GNode& nd, T a, T b, T y, T gg, T& ca,
+                                        T& cb) {
+  ca = 0;
+  cb = 0;
+  switch (op) {
+    case G_ADD: ca = gg; cb = gg; break;
+    case G_SUB: ca = gg; cb = -gg; break;
+    case G_MUL: ca = gg * b; cb = gg * a; break;
+    case G_DIV:
+      ca = gg / b;
+      cb = -gg * a / (b * b);
+      break;
+    case G_MAX:
+      ca = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
+      cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
+      break;
+    case G_EXP: ca = gg * (y - kc<T>(nd.pt, nd.fpt)); break;   // ps exp(a) = y - pt
+    case G_LOG: ca = gg / a; break;
+    case G_LOG1P: ca = gg / ((T)1 + a); break;
+    case G_SQRT: ca = gg / ((T)2 * y); break;
+    case G_ABS: ca = a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0); break;
+    case G_AXPB: ca = kc<T>(nd.c0, nd.f0) * gg; break;
+    case G_CLAMPMIN: ca = a >= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
+    case G_CLAMPMAX: ca = a <= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
+    default: break;
+  }
+}
+
+// Pointwise transpose over n cells (the layout of g_forward_pw): the
+// cotangents, scaled by the folded sum's sign and the epilogue's factor, are
+// written (first contribution) or added into gA, gB, gC; a and b may be the
+// same node (a's contribution first).
+template <typename T, int OP>
+__device__ __forceinline__ void pw_back_cell(const GNode& nd, T a, T b, T y, T gg, T sv, T sc,
+                                             T& ca, T& cb, T& cc) {
+  pw_grad(OP, nd, a, b, y, gg, ca, cb);
+  if ((nd.ep && OP != G_EXP) || nd.pop == 3) {
+    ca *= sv;
+    cb *= sv;
+  }
+  cc = sc * gg;
+}
+
+template <typename T, int OP>
+__global__ void g_backward_pw(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+                              T* gA, T* gB, T* gC, int wA, int wB, int wC, long long n, int vec) {
+  const bool same = gA != nullptr && gA == gB;
+  const T sv = kc<T>(nd.ps, nd.fps) * (nd.pop == 3 ? (T)-1 : (T)1);
+  const T sc = kc<T>(nd.ps, nd.fps) * (nd.pop == 2 ? (T)-1 : (T)1);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  auto put = [](int w, T v, T old) { return w ? v : old + v; };   // first write, or add
+  if (vec) {
+    for (; t < n / 4; t += stride) {
+      const long long i = 4 * t;
+      T a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, y[4], gg[4], ca[4], cb[4], cc[4];
+      T oa[4] = {0, 0, 0, 0}, ob[4] = {0, 0, 0, 0}, oc[4] = {0, 0, 0, 0};
+      if (A) ld4(A, i, a);
+      if (B) ld4(B, i, b);
+      ld4(out, i, y);
+      ld4(gout, i, gg);
+      if (gA && !wA) ld4((const T*)gA, i, oa);
+      if (gB && !wB && !same) ld4((const T*)gB, i, ob);
+      if (gC && !wC) ld4((const T*)gC, i, oc);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        pw_back_cell<T, OP>(nd, a[k], b[k], y[k], gg[k], sv, sc, ca[k], cb[k], cc[k]);
+        if (same) {
+          oa[k] = put(wB, cb[k], put(wA, ca[k], oa[k]));
+        } else {
+          oa[k] = put(wA, ca[k], oa[k]);
+          ob[k] = put(wB, cb[k], ob[k]);
+        }
+        oc[k] = put(wC, cc[k], oc[k]);
+      }
+      if (gA) st4(gA, i, oa);
+      if (gB && !same) st4(gB, i, ob);
+      if (gC) st4(gC, i, oc);
+    }
   } else {
-    const T gg = gout[idx];
-    switch (op) {
-      case G_ADD: ca = gg; cb = gg; break;
-      case G_SUB: ca = gg; cb = -gg; break;
-      case G_MUL: ca = gg * B[idx]; cb = gg * A[idx]; break;
-      case G_DIV: {
-        T a = A[idx], b = B[idx];
-        ca = gg / b;
-        cb = -gg * a / (b * b);
-        break;
+    for (; t < n; t += stride) {
+      T ca, cb, cc;
+      pw_back_cell<T, OP>(nd, A ? A[t] : (T)0, B ? B[t] : (T)0, out[t], gout[t], sv, sc, ca, cb,
+                          cc);
+      if (same) {
+        gA[t] = put(wB, cb, put(wA, ca, wA ? (T)0 : gA[t]));
+      } else {
+        if (gA) gA[t] = put(wA, ca, wA ? (T)0 : gA[t]);
+        if (gB) gB[t] = put(wB, cb, wB ? (T)0 : gB[t]);
       }
-      case G_MAX: {
-        T a = A[idx], b = B[idx];
-        ca = a > b ? gg : (a == b ? gg / (T)2 : (T)0);
-        cb = b > a ? gg : (a == b ? gg / (T)2 : (T)0);
-        break;
-      }
-      case G_EXP: ca = gg * (out[idx] - kc<T>(nd.pt, nd.fpt)); break;   // ps exp(a) = y - pt
-      case G_LOG: ca = gg / A[idx]; break;
-      case G_LOG1P: ca = gg / ((T)1 + A[idx]); break;
-      case G_SQRT: ca = gg / ((T)2 * out[idx]); break;
-      case G_ABS: {
-        T a = A[idx];
-        ca = a > (T)0 ? gg : (a < (T)0 ? -gg : (T)0);
-        break;
-      }
-      case G_AXPB: ca = kc<T>(nd.c0, nd.f0) * gg; break;
-      case G_CLAMPMIN: ca = A[idx] >= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
-      case G_CLAMPMAX: ca = A[idx] <= kc<T>(nd.c0, nd.f0) ? gg : (T)0; break;
-      default: break;
+      if (gC) gC[t] = put(wC, cc, wC ? (T)0 : gC[t]);
     }
   }
 }

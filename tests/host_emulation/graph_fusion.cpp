@@ -13,6 +13,9 @@
 // stretched z mesh.  Exit status: the number of failing (case, precision)
 // pairs.
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +58,21 @@ static void run(const Geo& g, K kern) {
               kern();
             }
 }
+
+// A flat launch (the pointwise kernels): blocks of 256 threads, grid-stride.
+template <class K>
+static void run1d(long long work, K kern) {
+  const unsigned nb = (unsigned)std::min<long long>((work + 255) / 256, 8192);
+  gridDim = dim3(nb, 1, 1);
+  blockDim = dim3(256, 1, 1);
+  for (unsigned b = 0; b < nb; ++b)
+    for (unsigned t = 0; t < 256; ++t) {
+      blockIdx = make_uint3(b, 0, 0);
+      threadIdx = make_uint3(t, 0, 0);
+      kern();
+    }
+}
+static bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // The executor's sweeps (graph.cu) on the host, one node after another.
 template <typename T>
@@ -107,21 +125,26 @@ struct HostExec {
       const T* C = nd.c >= 0 ? v[nd.c].data() : nullptr;
       T* out = v[i].data();
       const Geo& G = g;
+      const int vec = g.n % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(out);
 #define FW(OP) case OP: run(G, [&] { g_forward<T, OP>(nd, A, B, C, out, M, G); }); break;
+#define FP(OP) \
+  case OP: run1d(vec ? g.n / 4 : g.n, [&] { g_forward_pw<T, OP>(nd, A, B, C, out, g.n, vec); }); break;
       switch (nd.op) {
         case G_PMEAN: pmean(A, out, false); break;
         case G_QUENCH: run(G, [&] { g_quench_f<T>(nd, A, out, G); }); break;
-        FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_STEXP) FW(G_NB3) FW(G_ADD) FW(G_SUB)
-        FW(G_MUL) FW(G_DIV) FW(G_MAX) FW(G_EXP) FW(G_LOG) FW(G_LOG1P) FW(G_SQRT) FW(G_ABS)
-        FW(G_AXPB) FW(G_CLAMPMIN) FW(G_CLAMPMAX) FW(G_STEP) FW(G_ZFIELD) FW(G_CONST)
+        FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_STEXP) FW(G_NB3)
+        FW(G_ZFIELD) FP(G_ADD) FP(G_SUB) FP(G_MUL) FP(G_DIV) FP(G_MAX) FP(G_EXP) FP(G_LOG)
+        FP(G_LOG1P) FP(G_SQRT) FP(G_ABS) FP(G_AXPB) FP(G_CLAMPMIN) FP(G_CLAMPMAX) FP(G_STEP)
+        FP(G_CONST)
         default: printf("no forward for op %d\n", nd.op); exit(100);
       }
 #undef FW
+#undef FP
     }
   }
   void backward(const std::vector<std::vector<T>>& seed, std::vector<std::vector<T>>& gin) {
     for (int k = 0; k < 8; ++k) gr[d.out[k]] = seed[k];
-    std::vector<T> S(7 * g.n);
+    std::vector<T> S(15 * g.n);
     for (long long i = (long long)d.nodes.size() - 1; i >= 0; --i) {
       const GNode nd = d.nodes[i];
       if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP)
@@ -135,19 +158,28 @@ struct HostExec {
       const T* go = gr[i].data();
       const int WA = wa[i], WB = wb[i], WC = wc[i];
       const Geo& G = g;
+      const int vec = g.n % 4 == 0 && al16(A) && al16(B) && al16(out) && al16(go) && al16(gA) &&
+                      al16(gB) && al16(gC);
 #define BW(OP) case OP: run(G, [&] { g_backward<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, G); }); break;
+#define BP(OP)                                                                                 \
+  case OP:                                                                                     \
+    run1d(vec ? g.n / 4 : g.n,                                                                 \
+          [&] { g_backward_pw<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, g.n, vec); }); \
+    break;
       switch (nd.op) {
         case G_PMEAN: pmean(go, gA, !WA); break;
         case G_QUENCH:
-          run(G, [&] { g_quench_b1<T>(nd, A, go, S.data(), G); });
-          run(G, [&] { g_quench_b3<T>(nd, A, S.data(), gA, WA, G); });
+          run(G, [&] { g_quench_q<T>(nd, A, S.data() + 7 * G.n, G); });
+          run(G, [&] { g_quench_b1<T>(nd, A, S.data() + 7 * G.n, go, S.data(), G); });
+          run(G, [&] { g_quench_b3<T>(nd, S.data() + 7 * G.n, S.data(), gA, WA, G); });
           break;
-        BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_STEXP) BW(G_NB3) BW(G_ADD) BW(G_SUB)
-        BW(G_MUL) BW(G_DIV) BW(G_MAX) BW(G_EXP) BW(G_LOG) BW(G_LOG1P) BW(G_SQRT) BW(G_ABS)
-        BW(G_AXPB) BW(G_CLAMPMIN) BW(G_CLAMPMAX)
+        BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_STEXP) BW(G_NB3)
+        BP(G_ADD) BP(G_SUB) BP(G_MUL) BP(G_DIV) BP(G_MAX) BP(G_EXP) BP(G_LOG) BP(G_LOG1P)
+        BP(G_SQRT) BP(G_ABS) BP(G_AXPB) BP(G_CLAMPMIN) BP(G_CLAMPMAX)
         default: printf("no transpose for op %d\n", nd.op); exit(100);
       }
 #undef BW
+#undef BP
     }
     for (int k = 0; k < 8; ++k) gin[k] = gr[d.in[k]];
   }
