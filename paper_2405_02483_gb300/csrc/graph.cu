@@ -172,6 +172,33 @@ static BwdK<T> bwd_kernel(int op) {
 }
 
 template <typename T>
+static FwdK<T> fwd_kernel4(int op) {
+  switch (op) {
+    case G_STENCIL: return g_forward4<T, G_STENCIL>;
+    case G_SHIFT: return g_forward4<T, G_SHIFT>;
+    case G_STBIN: return g_forward4<T, G_STBIN>;
+    case G_STMUL: return g_forward4<T, G_STMUL>;
+    case G_ST2: return g_forward4<T, G_ST2>;
+    case G_STEXP: return g_forward4<T, G_STEXP>;
+    case G_NB3: return g_forward4<T, G_NB3>;
+    default: return g_forward4<T, G_ZFIELD>;
+  }
+}
+
+template <typename T>
+static BwdK<T> bwd_kernel4(int op) {
+  switch (op) {
+    case G_STENCIL: return g_backward4<T, G_STENCIL>;
+    case G_STBIN: return g_backward4<T, G_STBIN>;
+    case G_STMUL: return g_backward4<T, G_STMUL>;
+    case G_ST2: return g_backward4<T, G_ST2>;
+    case G_STEXP: return g_backward4<T, G_STEXP>;
+    case G_NB3: return g_backward4<T, G_NB3>;
+    default: return g_backward4<T, G_SHIFT>;
+  }
+}
+
+template <typename T>
 static FwdPwK<T> fwd_kernel_pw(int op) {
   switch (op) {
     case G_ADD: return g_forward_pw<T, G_ADD>;
@@ -214,6 +241,15 @@ static BwdPwK<T> bwd_kernel_pw(int op) {
 // Flat launch of a pointwise kernel: four cells a thread when every array is
 // 16-byte aligned and n a multiple of 4.
 static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+// The four-x-cell stencil kernels: nx a multiple of 4 and shifts of one cell
+// (the arrays' alignment is checked per launch).
+static inline bool cells4(const GNode& nd, const Geo& g) {
+  return g.nx % 4 == 0 && ((nd.op != G_SHIFT && nd.op != G_NB3) || nd.sk == 1 || nd.sk == -1);
+}
+static inline dim3 ggrid4(const Geo& g) {
+  return dim3((unsigned)((g.nx / 4 + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),
+              (unsigned)((g.nz + GBZ - 1) / GBZ));
+}
 static inline unsigned pw_blocks(long long work) {
   const long long b = (work + 255) / 256;
   return (unsigned)(b < 8192 ? (b > 0 ? b : 1) : 8192);
@@ -279,6 +315,8 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
         const int vec = geo.n % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(ptr[i]);
         fwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
             nd, A, B, C, ptr[i], geo.n, vec);
+      } else if (cells4(nd, geo) && al16(A) && al16(B) && al16(C) && al16(ptr[i])) {
+        fwd_kernel4<T>(nd.op)<<<ggrid4(geo), gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
       } else {
         fwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
       }
@@ -348,6 +386,10 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
                         al16(gA) && al16(gB) && al16(gC);
         bwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
             nd, A, B, ptr[i], gi, gA, gB, gC, wa[i], wb[i], wc[i], geo.n, vec);
+      } else if (cells4(nd, geo) && al16(A) && al16(B) && al16(ptr[i]) && al16(gi) &&
+                 al16(gA) && al16(gB) && al16(gC)) {
+        bwd_kernel4<T>(nd.op)<<<ggrid4(geo), gb, 0, st>>>(nd, A, B, ptr[i], gi, gA, gB, gC,
+                                                          wa[i], wb[i], wc[i], geo);
       } else {
         bwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, ptr[i], gi, gA, gB, gC, wa[i], wb[i],
                                                 wc[i], geo);

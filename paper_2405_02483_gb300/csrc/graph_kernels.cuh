@@ -90,15 +90,13 @@ __device__ __forceinline__ void taps7(V v, const GCell& c, int axis, const Geo& 
   }
 }
 
-// Stencil value at c: up/dn are eq. (interp) to i+1/2 and i-1/2; ddup/dddn
-// are eq. (deriv) to i+1/2 and i-1/2, divided by the spacing h.
+// A stencil from the values at its seven taps t[0..6] = c - 3 .. c + 3: up/dn
+// are eq. (interp) to i+1/2 and i-1/2; ddup/dddn are eq. (deriv) to i+1/2 and
+// i-1/2, divided by the spacing h.
 template <typename T>
-__device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, int kind, T h,
-                                        const Geo& g) {
+__device__ __forceinline__ T st_comb(int kind, T h, const T t[7]) {
   const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
   const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
-  T t[7];
-  taps7<T>([&](long long j) { return f[j]; }, c, axis, g, t);
   const T m3 = t[0], m2 = t[1], m1 = t[2], z0 = t[3], p1 = t[4], p2 = t[5], p3 = t[6];
   switch (kind) {
     case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
@@ -108,21 +106,22 @@ __device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, in
   }
 }
 
+// Stencil value of f at c.
+template <typename T>
+__device__ __forceinline__ T stencil_at(const T* f, const GCell& c, int axis, int kind, T h,
+                                        const Geo& g) {
+  T t[7];
+  taps7<T>([&](long long j) { return f[j]; }, c, axis, g, t);
+  return st_comb(kind, h, t);
+}
+
 // The same stencil of the values v(idx) of a functor at the taps.
 template <typename T, class V>
 __device__ __forceinline__ T stencil_fn(V v, const GCell& c, int axis, int kind, T h,
                                         const Geo& g) {
-  const T IA = (T)STG_IA, IB = (T)STG_IB, IC = (T)STG_IC;
-  const T DA = (T)STG_DA, DB = (T)STG_DB, DC = (T)STG_DC;
   T t[7];
   taps7<T>(v, c, axis, g, t);
-  const T m3 = t[0], m2 = t[1], m1 = t[2], z0 = t[3], p1 = t[4], p2 = t[5], p3 = t[6];
-  switch (kind) {
-    case ST_UP: return IA * (z0 + p1) + IB * (m1 + p2) + IC * (m2 + p3);
-    case ST_DN: return IA * (m1 + z0) + IB * (m2 + p1) + IC * (m3 + p2);
-    case ST_DDUP: return (DA * (p1 - z0) + DB * (p2 - m1) + DC * (p3 - m2)) / h;
-    default: return (DA * (z0 - m1) + DB * (p1 - m2) + DC * (p2 - m3)) / h;
-  }
+  return st_comb(kind, h, t);
 }
 // Transposed kind and sign of a stencil: up^T = dn, dn^T = up, ddup^T =
 // -dddn, dddn^T = -ddup (periodic summation by parts).
@@ -304,18 +303,22 @@ __global__ void g_quench_f(GNode nd, const T* A, T* out, Geo g) {
   }
 }
 
+// y = st (op) b of a G_STBIN node (side 1: b first).
+template <typename T>
+__device__ __forceinline__ T stbin_val(const GNode& nd, T st, T b) {
+  if (nd.iop == G_MUL) return st * b;
+  if (nd.iop == G_ADD) return nd.side ? b + st : st + b;
+  return nd.side ? b - st : st - b;     // G_SUB
+}
+
 template <typename T>
 __device__ __forceinline__ T fwd_value(int op, const GNode& nd, const T* A, const T* B,
                                        const T* mesh, const GCell& c, const Geo& g) {
   const long long idx = c.idx;
   switch (op) {
     case G_STENCIL: return stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g);
-    case G_STBIN: {
-      const T st = stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g), b = B[idx];
-      if (nd.iop == G_MUL) return st * b;
-      if (nd.iop == G_ADD) return nd.side ? b + st : st + b;
-      return nd.side ? b - st : st - b;     // G_SUB
-    }
+    case G_STBIN:
+      return stbin_val(nd, stencil_at(A, c, nd.axis, nd.sk, kc<T>(nd.c0, nd.f0), g), B[idx]);
     case G_STMUL:
       return stencil_fn<T>([&](long long j) { return A[j] * B[j]; }, c, nd.axis, nd.sk,
                            kc<T>(nd.c0, nd.f0), g);
@@ -667,6 +670,265 @@ __global__ void g_backward(GNode nd, const T* A, const T* B, const T* out, const
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same stencil-type kernels with four consecutive x-cells a thread (nx a
+// multiple of 4, every array 16-byte aligned): each tap is one 16-byte load,
+// the x taps come from the aligned 4-cell chunks left of, at and right of the
+// thread's cells, and the per-thread index work is shared by four cells (the
+// one-cell kernels are bound by their instruction issue).  Every lane takes
+// the one-cell arithmetic, so the values are the same bit for bit.  SHIFT and
+// NB3 here take offsets of one cell.
+// ---------------------------------------------------------------------------
+struct GCell4 {
+  int i0, j, k;   // i0: the first of the four x-cells
+  long long idx;  // index of cell i0
+};
+
+__device__ __forceinline__ bool gcell4(GCell4& c, const Geo& g) {
+  c.i0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  c.j = blockIdx.y * blockDim.y + threadIdx.y;
+  c.k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (c.i0 >= g.nx || c.j >= g.ny || c.k >= g.nz) return false;
+  c.idx = (long long)c.k * g.sz + (long long)c.j * g.sy + c.i0;
+  return true;
+}
+
+// t[o + 3][l]: f at cell (i0 + l, j, k) + o e_axis, o = -3 .. 3.
+template <typename T>
+__device__ __forceinline__ void taps7x4(const T* f, const GCell4& c, int axis, const Geo& g,
+                                        T t[7][4]) {
+  if (axis == 0) {
+    const long long row = c.idx - c.i0;
+    T L[4], M[4], R[4];
+    ld4(f, row + wrap(c.i0 - 4, g.nx), L);
+    ld4(f, c.idx, M);
+    ld4(f, row + wrap(c.i0 + 4, g.nx), R);
+#pragma unroll
+    for (int o = -3; o <= 3; ++o)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int q = 4 + l + o;   // in the 12-cell window i0 - 4 .. i0 + 7
+        t[o + 3][l] = q < 4 ? L[q] : q < 8 ? M[q - 4] : R[q - 8];
+      }
+  } else {
+    const long long st = axis == 1 ? g.sy : g.sz;
+    const int pos = axis == 1 ? c.j : c.k, n = axis == 1 ? g.ny : g.nz;
+    const bool inner = pos >= 3 && pos + 3 < n;
+#pragma unroll
+    for (int o = -3; o <= 3; ++o)
+      ld4(f, c.idx + (inner ? o * st : (long long)(wrap(pos + o, n) - pos) * st), t[o + 3]);
+  }
+}
+
+// Lane l's seven taps as one array.
+template <typename T>
+__device__ __forceinline__ void lane7(const T t[7][4], int l, T u[7]) {
+#pragma unroll
+  for (int o = 0; o < 7; ++o) u[o] = t[o][l];
+}
+// The tap at offset s = +-1 (or +-2 with d2) of lane l.
+template <typename T>
+__device__ __forceinline__ T tap1(const T t[7][4], int s, int l) {
+  return s > 0 ? t[4][l] : t[2][l];
+}
+template <typename T>
+__device__ __forceinline__ T tap2(const T t[7][4], int s, int l) {
+  return s > 0 ? t[5][l] : t[1][l];
+}
+
+template <typename T, int OP>
+__global__ void g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
+                           Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  const T h = kc<T>(nd.c0, nd.f0);
+  T r[4];
+  if (OP == G_ZFIELD) {
+    const T z = mesh[(long long)nd.sk * g.nz + c.k];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) r[l] = z;
+  } else if (OP == G_STMUL) {
+    T ta[7][4], tb[7][4];
+    taps7x4(A, c, nd.axis, g, ta);
+    taps7x4(B, c, nd.axis, g, tb);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      T u[7];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) u[o] = ta[o][l] * tb[o][l];
+      r[l] = st_comb(nd.sk, h, u);
+    }
+  } else if (OP == G_ST2) {
+    T ta[7][4], tb[7][4];
+    taps7x4(A, c, nd.axis, g, ta);
+    taps7x4(B, c, nd.axis2, g, tb);
+    const T h2 = kc<T>(nd.h2, nd.fh2);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      T u[7], v[7];
+      lane7(ta, l, u);
+      lane7(tb, l, v);
+      const T s1 = st_comb(nd.sk, h, u), s2 = st_comb(nd.sk2, h2, v);
+      r[l] = nd.iop == G_ADD ? s1 + s2 : s1 - s2;
+    }
+  } else {
+    T t[7][4];
+    taps7x4(A, c, nd.axis, g, t);
+    T b[4] = {0, 0, 0, 0};
+    if (OP == G_STBIN) ld4(B, c.idx, b);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if (OP == G_SHIFT) {
+        r[l] = tap1(t, nd.sk, l);
+      } else if (OP == G_NB3) {
+        const T m = tap1(t, nd.sk, l), z = t[3][l], p = tap1(t, -nd.sk, l);
+        if (nd.iop == G_ADD) {
+          r[l] = (m + z) + p;
+        } else {
+          const T in = m >= z ? m : z;
+          r[l] = in >= p ? in : p;
+        }
+      } else {
+        T u[7];
+        lane7(t, l, u);
+        const T st = st_comb(nd.sk, h, u);
+        r[l] = OP == G_STEXP ? exp(st) : OP == G_STBIN ? stbin_val(nd, st, b[l]) : st;
+      }
+    }
+  }
+  T cv[4] = {0, 0, 0, 0};
+  if (nd.pop) ld4(C, c.idx, cv);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) r[l] = finish(nd, r[l], cv[l]);
+  st4(out, c.idx, r);
+}
+
+template <typename T, int OP>
+__global__ void g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+                            T* gA, T* gB, T* gC, int wA, int wB, int wC, Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  const T h = kc<T>(nd.c0, nd.f0);
+  const int tk = st_transpose(nd.sk);
+  const bool ng = st_negates(nd.sk);
+  T ca[4] = {0, 0, 0, 0}, cb[4] = {0, 0, 0, 0}, gg[4];
+  ld4(gout, c.idx, gg);
+  if (OP == G_ST2) {
+    T t1[7][4], t2[7][4];
+    taps7x4(gout, c, nd.axis, g, t1);
+    taps7x4(gout, c, nd.axis2, g, t2);
+    const T h2 = kc<T>(nd.h2, nd.fh2);
+    const bool n2 = st_negates(nd.sk2) != (nd.iop == G_SUB);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      T u[7], v[7];
+      lane7(t1, l, u);
+      lane7(t2, l, v);
+      const T v1 = st_comb(tk, h, u), v2 = st_comb(st_transpose(nd.sk2), h2, v);
+      ca[l] = ng ? -v1 : v1;
+      cb[l] = n2 ? -v2 : v2;
+    }
+  } else if (OP == G_NB3) {
+    T tg[7][4], ta[7][4];
+    taps7x4(gout, c, nd.axis, g, tg);
+    if (nd.iop != G_ADD) taps7x4(A, c, nd.axis, g, ta);
+    const int o = nd.sk;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const T gm = tap1(tg, -o, l), g0 = tg[3][l], gp = tap1(tg, o, l);
+      if (nd.iop == G_ADD) {
+        ca[l] = (gm + g0) + gp;
+      } else {
+        const T a0 = ta[3][l], am = tap1(ta, -o, l), am2 = tap2(ta, -o, l);
+        const T ap = tap1(ta, o, l), ap2 = tap2(ta, o, l);
+        T wm, wz, wi, wp;
+        max_w(a0, am, wm, wz);
+        max_w(a0 >= am ? a0 : am, am2, wi, wp);
+        T acc = gm * (wi * wm);
+        max_w(ap, a0, wm, wz);
+        max_w(ap >= a0 ? ap : a0, am, wi, wp);
+        acc += g0 * (wi * wz);
+        max_w(ap2, ap, wm, wz);
+        max_w(ap2 >= ap ? ap2 : ap, a0, wi, wp);
+        ca[l] = acc + gp * wp;
+      }
+    }
+  } else if (OP == G_SHIFT) {
+    T tg[7][4];
+    taps7x4(gout, c, nd.axis, g, tg);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) ca[l] = tap1(tg, -nd.sk, l);
+  } else {
+    // STENCIL, STBIN, STMUL, STEXP: the transposed stencil of gout, or of
+    // gout times B (STBIN with a product) or times y - pt (STEXP).
+    T tg[7][4], tb[7][4];
+    taps7x4(gout, c, nd.axis, g, tg);
+    const bool prod = (OP == G_STBIN && nd.iop == G_MUL) || OP == G_STEXP;
+    if (prod) taps7x4(OP == G_STEXP ? out : B, c, nd.axis, g, tb);
+    const T pt = kc<T>(nd.pt, nd.fpt);
+    T a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+    if (OP == G_STMUL) {
+      ld4(A, c.idx, a);
+      ld4(B, c.idx, b);
+    }
+    T ta[7][4];
+    if (OP == G_STBIN && nd.iop == G_MUL) taps7x4(A, c, nd.axis, g, ta);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      T u[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q)
+        u[q] = !prod ? tg[q][l] : OP == G_STEXP ? tg[q][l] * (tb[q][l] - pt) : tg[q][l] * tb[q][l];
+      T v = st_comb(tk, h, u);
+      if (ng) v = -v;
+      if (OP == G_STBIN) {
+        if (nd.iop == G_MUL) {
+          T w[7];
+          lane7(ta, l, w);
+          ca[l] = v;
+          cb[l] = gg[l] * st_comb(nd.sk, h, w);
+        } else {
+          ca[l] = (nd.iop == G_SUB && nd.side) ? -v : v;
+          cb[l] = (nd.iop == G_SUB && !nd.side) ? -gg[l] : gg[l];
+        }
+      } else if (OP == G_STMUL) {
+        ca[l] = v * b[l];
+        cb[l] = v * a[l];
+      } else {
+        ca[l] = v;
+      }
+    }
+  }
+  const bool same = gA != nullptr && gA == gB;
+  const T sv = kc<T>(nd.ps, nd.fps) * (nd.pop == 3 ? (T)-1 : (T)1);
+  const T sc = kc<T>(nd.ps, nd.fps) * (nd.pop == 2 ? (T)-1 : (T)1);
+  if ((nd.ep && OP != G_STEXP) || nd.pop == 3) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      ca[l] *= sv;
+      cb[l] *= sv;
+    }
+  }
+  auto put = [](int w, T v, T old) { return w ? v : old + v; };   // first write, or add
+  T oa[4] = {0, 0, 0, 0}, ob[4] = {0, 0, 0, 0}, oc[4] = {0, 0, 0, 0};
+  if (gA && !wA) ld4((const T*)gA, c.idx, oa);
+  if (gB && !wB && !same) ld4((const T*)gB, c.idx, ob);
+  if (gC && !wC) ld4((const T*)gC, c.idx, oc);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    if (same) {
+      oa[l] = put(wB, cb[l], put(wA, ca[l], oa[l]));
+    } else {
+      oa[l] = put(wA, ca[l], oa[l]);
+      ob[l] = put(wB, cb[l], ob[l]);
+    }
+    oc[l] = put(wC, sc * gg[l], oc[l]);
+  }
+  if (gA) st4(gA, c.idx, oa);
+  if (gB && !same) st4(gB, c.idx, ob);
+  if (gC) st4(gC, c.idx, oc);
 }
 
 // Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed

@@ -1,8 +1,8 @@
 // Host build of the op graph: the graph with its merged nodes (fused stencil
 // pairs, stencil sums and exps, 3-cell maxima and sums, folded sums and
-// scalings) against the graph of one node per primitive, both swept by the
-// same forward and transpose kernels run over their launch grids one thread
-// at a time.  The forward outputs must be equal bit for bit; the reverse
+// scalings), swept by the one-cell and by the four-x-cell kernels, against
+// the graph of one node per primitive, the kernels run over their launch
+// grids one thread at a time.  The forward outputs must be equal bit for bit; the reverse
 // sweep's input gradients may differ only by rounding (the merged transposes
 // scale a gathered cotangent instead of gathering a scaled one): within 1e-12
 // (FP64) or 1e-5 (FP32) of each field's largest gradient.  Cases: the
@@ -41,10 +41,14 @@ dim3 blockDim, gridDim;
 #include "../../paper_2405_02483_gb300/csrc/graph_build.cu"
 using namespace stg;
 
+static long long g_four = 0;   // four-x-cell launches run
+
 template <class K>
-static void run(const Geo& g, K kern) {
+static void run(const Geo& g, K kern, bool four = false) {
+  g_four += four;
   const dim3 bd(GBX, GBY, GBZ);
-  const dim3 gd((g.nx + GBX - 1) / GBX, (g.ny + GBY - 1) / GBY, (g.nz + GBZ * GZU - 1) / (GBZ * GZU));
+  const dim3 gd(four ? (g.nx / 4 + GBX - 1) / GBX : (g.nx + GBX - 1) / GBX, (g.ny + GBY - 1) / GBY,
+                four ? (g.nz + GBZ - 1) / GBZ : (g.nz + GBZ * GZU - 1) / (GBZ * GZU));
   gridDim = gd;
   blockDim = bd;
   for (unsigned bz = 0; bz < gd.z; ++bz)
@@ -79,6 +83,7 @@ template <typename T>
 struct HostExec {
   GraphDef d;
   Geo g;
+  bool allow4 = true;   // the four-x-cell kernels where the executor takes them
   std::vector<std::vector<T>> v, gr;
   std::vector<T> mesh;
   std::vector<char> hasg, wa, wb, wc;
@@ -126,7 +131,15 @@ struct HostExec {
       T* out = v[i].data();
       const Geo& G = g;
       const int vec = g.n % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(out);
-#define FW(OP) case OP: run(G, [&] { g_forward<T, OP>(nd, A, B, C, out, M, G); }); break;
+      const bool four = allow4 && g.nx % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(out) &&
+                        ((nd.op != G_SHIFT && nd.op != G_NB3) || nd.sk == 1 || nd.sk == -1);
+#define FW(OP)                                                                    \
+  case OP:                                                                        \
+    if (four)                                                                     \
+      run(G, [&] { g_forward4<T, OP>(nd, A, B, C, out, M, G); }, true);           \
+    else                                                                          \
+      run(G, [&] { g_forward<T, OP>(nd, A, B, C, out, M, G); });                  \
+    break;
 #define FP(OP) \
   case OP: run1d(vec ? g.n / 4 : g.n, [&] { g_forward_pw<T, OP>(nd, A, B, C, out, g.n, vec); }); break;
       switch (nd.op) {
@@ -160,7 +173,15 @@ struct HostExec {
       const Geo& G = g;
       const int vec = g.n % 4 == 0 && al16(A) && al16(B) && al16(out) && al16(go) && al16(gA) &&
                       al16(gB) && al16(gC);
-#define BW(OP) case OP: run(G, [&] { g_backward<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, G); }); break;
+      const bool four = allow4 && g.nx % 4 == 0 && vec &&
+                        ((nd.op != G_SHIFT && nd.op != G_NB3) || nd.sk == 1 || nd.sk == -1);
+#define BW(OP)                                                                                 \
+  case OP:                                                                                     \
+    if (four)                                                                                  \
+      run(G, [&] { g_backward4<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, G); }, true); \
+    else                                                                                       \
+      run(G, [&] { g_backward<T, OP>(nd, A, B, out, go, gA, gB, gC, WA, WB, WC, G); });        \
+    break;
 #define BP(OP)                                                                                 \
   case OP:                                                                                     \
     run1d(vec ? g.n / 4 : g.n,                                                                 \
@@ -211,6 +232,11 @@ static stagger_params base_params() {
 
 // zuni: every input field uniform along z, so that the 3-cell maxima along z
 // meet exact ties (split evenly by the transposes).
+// Three sweeps of the same state: one node per primitive with one-cell
+// kernels (the reference), the merged graph with one-cell kernels, and the
+// merged graph with the four-x-cell kernels where they apply.  zuni: every
+// input field uniform along z, so that the 3-cell maxima along z meet exact
+// ties (split evenly by the transposes).
 template <typename T>
 static int compare(const char* name, const stagger_grid& gg, const stagger_params& p, double tol,
                    bool zuni = false) {
@@ -225,41 +251,51 @@ static int compare(const char* name, const stagger_grid& gg, const stagger_param
       for (long long q = g.sz; q < g.n; ++q) in[k][q] = in[k][q % g.sz];
   for (int k = 0; k < 8; ++k)
     for (auto& x : seed[k]) x = (T)U(rng);
-  std::vector<std::vector<T>> res[2], gin[2];
-  size_t nodes[2];
-  for (int t = 0; t < 2; ++t) {
+  std::vector<std::vector<T>> res[3], gin[3];
+  size_t nodes[3];
+  long long four[3];
+  for (int t = 0; t < 3; ++t) {
+    g_four = 0;
     HostExec<T> h;
     h.g = g;
-    build_rhs_graph(h.d, gg, p, t == 1);
+    h.allow4 = t == 2;
+    build_rhs_graph(h.d, gg, p, t > 0);
     nodes[t] = h.d.nodes.size();
     h.init();
     h.forward(in);
     for (int k = 0; k < 8; ++k) res[t].push_back(h.v[h.d.out[k]]);
     gin[t].resize(8);
     h.backward(seed, gin[t]);
+    four[t] = g_four;
   }
-  long long diff = 0, bad = 0;
-  double worst = 0;
-  for (int k = 0; k < 8; ++k) {
-    double e = 0, s = 0;
-    for (long long q = 0; q < g.n; ++q) {
-      if (std::memcmp(&res[0][k][q], &res[1][k][q], sizeof(T)) != 0) ++diff;
-      if (!std::isfinite((double)res[1][k][q]) || !std::isfinite((double)gin[1][k][q])) ++bad;
-      e = std::max(e, std::fabs((double)gin[0][k][q] - (double)gin[1][k][q]));
-      s = std::max(s, std::fabs((double)gin[0][k][q]));
+  int fails = 0;
+  for (int t = 1; t < 3; ++t) {
+    long long diff = 0, bad = 0;
+    double worst = 0;
+    for (int k = 0; k < 8; ++k) {
+      double e = 0, s = 0;
+      for (long long q = 0; q < g.n; ++q) {
+        if (std::memcmp(&res[0][k][q], &res[t][k][q], sizeof(T)) != 0) ++diff;
+        if (!std::isfinite((double)res[t][k][q]) || !std::isfinite((double)gin[t][k][q])) ++bad;
+        e = std::max(e, std::fabs((double)gin[0][k][q] - (double)gin[t][k][q]));
+        s = std::max(s, std::fabs((double)gin[0][k][q]));
+      }
+      worst = std::max(worst, e / std::max(s, 1e-300));
     }
-    worst = std::max(worst, e / std::max(s, 1e-300));
+    const bool ok = diff == 0 && bad == 0 && worst <= tol;
+    printf("%s %s %s (%lld four-cell launches): %zu -> %zu nodes, forward %lld differing "
+           "values, %lld non-finite, reverse max rel err %.2e%s\n", name,
+           sizeof(T) == 8 ? "FP64" : "FP32", t == 1 ? "one-cell" : "four-cell", four[t],
+           nodes[0], nodes[t], diff, bad, worst, ok ? "" : "  FAIL");
+    fails += !ok;
   }
-  const bool ok = diff == 0 && bad == 0 && worst <= tol;
-  printf("%s %s: %zu -> %zu nodes, forward %lld differing values, %lld non-finite, "
-         "reverse max rel err %.2e%s\n", name, sizeof(T) == 8 ? "FP64" : "FP32", nodes[0], nodes[1],
-         diff, bad, worst, ok ? "" : "  FAIL");
-  return ok ? 0 : 1;
+  return fails;
 }
 
 int main() {
   int fails = 0;
-  const stagger_grid g1 = {13, 11, 9, 1.0 / 13, 1.0 / 11, 1.0 / 9};
+  const stagger_grid g1 = {16, 11, 9, 1.0 / 16, 1.0 / 11, 1.0 / 9};
+  const stagger_grid g3 = {13, 11, 9, 1.0 / 13, 1.0 / 11, 1.0 / 9};   // no four-cell kernels
   stagger_params visc = base_params();
   stagger_params cool = base_params();
   cool.t_chromo = 0.05;
@@ -290,8 +326,8 @@ int main() {
   fails += compare<float>("viscosity+quench", g1, visc, 1e-5);
   fails += compare<double>("viscosity+quench z-uniform", g1, visc, 1e-12, true);
   fails += compare<float>("viscosity+quench z-uniform", g1, visc, 1e-5, true);
-  fails += compare<double>("cooling", g1, cool, 1e-12);
-  fails += compare<float>("cooling", g1, cool, 1e-5);
+  fails += compare<double>("cooling", g3, cool, 1e-12);
+  fails += compare<float>("cooling", g3, cool, 1e-5);
   fails += compare<double>("options+stretched", g2, opts, 1e-12);
   fails += compare<float>("options+stretched", g2, opts, 1e-5);
   return fails;

@@ -10,8 +10,9 @@ bit for bit on the CPU, beyond the GPU tests' FP32 tolerance:
   with four x-cells per thread, for the benchmark's physics and for every
   option at once, on a uniform and on a stretched z mesh;
 - the op graph with its merged nodes (stencil pairs and sums, folded sums and
-  scalings) gives the same forward values bit for bit as the graph of one node
-  per primitive, and a reverse sweep equal to rounding, in FP64 and FP32."""
+  scalings), with one-cell and with four-x-cell kernels, gives the same
+  forward values bit for bit as the graph of one node per primitive, and a
+  reverse sweep equal to rounding, in FP64 and FP32."""
 import os
 import shutil
 import subprocess
@@ -53,5 +54,9 @@ def test_one_cell_and_four_cell_threads_give_the_same_rhs(tmp_path):
 
 def test_merged_op_graph_equals_one_node_per_primitive(tmp_path):
     out = _build_and_run(tmp_path, "graph_fusion")
-    assert out.count("forward 0 differing values, 0 non-finite") == 8, out
+    assert out.count("forward 0 differing values, 0 non-finite") == 16, out
     assert "FAIL" not in out, out
+    # the four-x-cell kernels ran on the boxes whose nx is a multiple of 4
+    import re
+    four = [int(m) for m in re.findall(r"four-cell \((\d+) four-cell launches\)", out)]
+    assert len(four) == 8 and sum(1 for f in four if f > 0) == 6, out
