@@ -242,9 +242,17 @@ static BwdPwK<T> bwd_kernel_pw(int op) {
 // 16-byte aligned and n a multiple of 4.
 static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // The four-x-cell stencil kernels: nx a multiple of 4 and shifts of one cell
-// (the arrays' alignment is checked per launch).
-static inline bool cells4(const GNode& nd, const Geo& g) {
-  return g.nx % 4 == 0 && ((nd.op != G_SHIFT && nd.op != G_NB3) || nd.sk == 1 || nd.sk == -1);
+// (the arrays' alignment is checked per launch), for the kernels they made
+// faster.  Those that gather two or three tap arrays per cell at high
+// register counts measured slower with four cells (FP32, 128^3, ncu launch
+// list: forward ST2 22.1 / STMUL 19.0 us against 19.3 / 15.9 with one cell,
+// transpose STEXP 22.8 and STBIN of a product among 30.6 us STBIN launches,
+// against 17.2 and 23.8) and keep one cell a thread.
+static inline bool cells4(const GNode& nd, const Geo& g, bool bwd) {
+  if (g.nx % 4 != 0) return false;
+  if ((nd.op == G_SHIFT || nd.op == G_NB3) && nd.sk != 1 && nd.sk != -1) return false;
+  if (!bwd) return nd.op != G_ST2 && nd.op != G_STMUL;
+  return nd.op != G_STEXP && !(nd.op == G_STBIN && nd.iop == G_MUL);
 }
 static inline dim3 ggrid4(const Geo& g) {
   return dim3((unsigned)((g.nx / 4 + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),
@@ -308,14 +316,17 @@ int GraphExec<T>::forward(T* const in[8], cudaStream_t s) {
       launches += 2;
       prev_scr = (int)i;
     } else if (nd.op == G_QUENCH) {
-      g_quench_f<T><<<gg, gb, 0, st>>>(nd, A, ptr[i], geo);
+      if (geo.nx % 4 == 0 && al16(A) && al16(ptr[i]))
+        g_quench_f4<T><<<ggrid4(geo), gb, 0, st>>>(nd, A, ptr[i], geo);
+      else
+        g_quench_f<T><<<gg, gb, 0, st>>>(nd, A, ptr[i], geo);
       ++launches;
     } else {
       if (pointwise_op(nd.op)) {
         const int vec = geo.n % 4 == 0 && al16(A) && al16(B) && al16(C) && al16(ptr[i]);
         fwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
             nd, A, B, C, ptr[i], geo.n, vec);
-      } else if (cells4(nd, geo) && al16(A) && al16(B) && al16(C) && al16(ptr[i])) {
+      } else if (cells4(nd, geo, false) && al16(A) && al16(B) && al16(C) && al16(ptr[i])) {
         fwd_kernel4<T>(nd.op)<<<ggrid4(geo), gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
       } else {
         fwd_kernel<T>(nd.op)<<<gg, gb, 0, st>>>(nd, A, B, C, ptr[i], mesh, geo);
@@ -375,9 +386,17 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
       launches += 2;
     } else if (nd.op == G_QUENCH) {
       T* Q = qscr + (size_t)7 * geo.n;   // q and its derivatives, 4 arrays per axis slot
-      g_quench_q<T><<<gg, gb, 0, st>>>(nd, A, Q, geo);
-      g_quench_b1<T><<<gg, gb, 0, st>>>(nd, A, Q, grads + (size_t)i * geo.n, qscr, geo);
-      g_quench_b3<T><<<gg, gb, 0, st>>>(nd, Q, qscr, gA, wa[i], geo);
+      T* gi = grads + (size_t)i * geo.n;
+      if (geo.nx % 4 == 0 && al16(A) && al16(gi) && al16(gA) && al16(qscr)) {
+        const dim3 g4 = ggrid4(geo);
+        g_quench_q4<T><<<g4, gb, 0, st>>>(nd, A, Q, geo);
+        g_quench_b1_4<T><<<g4, gb, 0, st>>>(nd, A, Q, gi, qscr, geo);
+        g_quench_b3_4<T><<<g4, gb, 0, st>>>(nd, Q, qscr, gA, wa[i], geo);
+      } else {
+        g_quench_q<T><<<gg, gb, 0, st>>>(nd, A, Q, geo);
+        g_quench_b1<T><<<gg, gb, 0, st>>>(nd, A, Q, gi, qscr, geo);
+        g_quench_b3<T><<<gg, gb, 0, st>>>(nd, Q, qscr, gA, wa[i], geo);
+      }
       launches += 3;
     } else {
       T* gi = grads + (size_t)i * geo.n;
@@ -386,7 +405,7 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
                         al16(gA) && al16(gB) && al16(gC);
         bwd_kernel_pw<T>(nd.op)<<<pw_blocks(vec ? geo.n / 4 : geo.n), 256, 0, st>>>(
             nd, A, B, ptr[i], gi, gA, gB, gC, wa[i], wb[i], wc[i], geo.n, vec);
-      } else if (cells4(nd, geo) && al16(A) && al16(B) && al16(ptr[i]) && al16(gi) &&
+      } else if (cells4(nd, geo, true) && al16(A) && al16(B) && al16(ptr[i]) && al16(gi) &&
                  al16(gA) && al16(gB) && al16(gC)) {
         bwd_kernel4<T>(nd.op)<<<ggrid4(geo), gb, 0, st>>>(nd, A, B, ptr[i], gi, gA, gB, gC,
                                                           wa[i], wb[i], wc[i], geo);

@@ -149,12 +149,10 @@ __device__ __forceinline__ T sgn(T a) {
   return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
 }
 
-// q at z = c + s e_ax, and (dq) its derivatives with respect to T at z-1, z,
-// z+1 (through D2 T and through M).
+// q at z = c + s e_ax from T at z - 1, z, z + 1 (vm, v0, vp), and (dq) its
+// derivatives with respect to those (through D2 T and through M).
 template <typename T>
-__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, T eps,
-                                  const Geo& g, T* dq) {
-  const T vm = A[nbr(c, ax, s - 1, g)], v0 = A[nbr(c, ax, s, g)], vp = A[nbr(c, ax, s + 1, g)];
+__device__ __forceinline__ T q_val(T vm, T v0, T vp, T iq, T eps, T* dq) {
   const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
   const T am = fabs(vm), a0 = fabs(v0), ap = fabs(vp);
   const T inner = am >= a0 ? am : a0;
@@ -179,6 +177,12 @@ __device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T i
     dq[2] = dq_da2 * sd + dq_dM * (cM * wop) * sgn(vp);
   }
   return q;
+}
+template <typename T>
+__device__ __forceinline__ T q_at(const T* A, const GCell& c, int ax, int s, T iq, T eps,
+                                  const Geo& g, T* dq) {
+  return q_val(A[nbr(c, ax, s - 1, g)], A[nbr(c, ax, s, g)], A[nbr(c, ax, s + 1, g)], iq, eps,
+               dq);
 }
 
 // fac at c, and (when wq) the weights of the three q of each axis in fac:
@@ -695,10 +699,10 @@ __device__ __forceinline__ bool gcell4(GCell4& c, const Geo& g) {
   return true;
 }
 
-// t[o + 3][l]: f at cell (i0 + l, j, k) + o e_axis, o = -3 .. 3.
-template <typename T>
-__device__ __forceinline__ void taps7x4(const T* f, const GCell4& c, int axis, const Geo& g,
-                                        T t[7][4]) {
+// t[o + K][l]: f at cell (i0 + l, j, k) + o e_axis, o = -K .. K (K <= 3).
+template <int K, typename T>
+__device__ __forceinline__ void tapsx4(const T* f, const GCell4& c, int axis, const Geo& g,
+                                       T t[2 * K + 1][4]) {
   if (axis == 0) {
     const long long row = c.idx - c.i0;
     T L[4], M[4], R[4];
@@ -706,20 +710,25 @@ __device__ __forceinline__ void taps7x4(const T* f, const GCell4& c, int axis, c
     ld4(f, c.idx, M);
     ld4(f, row + wrap(c.i0 + 4, g.nx), R);
 #pragma unroll
-    for (int o = -3; o <= 3; ++o)
+    for (int o = -K; o <= K; ++o)
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int q = 4 + l + o;   // in the 12-cell window i0 - 4 .. i0 + 7
-        t[o + 3][l] = q < 4 ? L[q] : q < 8 ? M[q - 4] : R[q - 8];
+        t[o + K][l] = q < 4 ? L[q] : q < 8 ? M[q - 4] : R[q - 8];
       }
   } else {
     const long long st = axis == 1 ? g.sy : g.sz;
     const int pos = axis == 1 ? c.j : c.k, n = axis == 1 ? g.ny : g.nz;
-    const bool inner = pos >= 3 && pos + 3 < n;
+    const bool inner = pos >= K && pos + K < n;
 #pragma unroll
-    for (int o = -3; o <= 3; ++o)
-      ld4(f, c.idx + (inner ? o * st : (long long)(wrap(pos + o, n) - pos) * st), t[o + 3]);
+    for (int o = -K; o <= K; ++o)
+      ld4(f, c.idx + (inner ? o * st : (long long)(wrap(pos + o, n) - pos) * st), t[o + K]);
   }
+}
+template <typename T>
+__device__ __forceinline__ void taps7x4(const T* f, const GCell4& c, int axis, const Geo& g,
+                                        T t[7][4]) {
+  tapsx4<3>(f, c, axis, g, t);
 }
 
 // Lane l's seven taps as one array.
@@ -929,6 +938,119 @@ __global__ void g_backward4(GNode nd, const T* A, const T* B, const T* out, cons
   if (gA) st4(gA, c.idx, oa);
   if (gB && !same) st4(gB, c.idx, ob);
   if (gC) st4(gC, c.idx, oc);
+}
+
+// The quench's kernels with four x-cells a thread (the same per-lane
+// arithmetic as g_quench_f, g_quench_q, g_quench_b1 and g_quench_b3).
+template <typename T>
+__global__ void g_quench_f4(GNode nd, const T* A, T* out, Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  const T iq = (T)1 / kc<T>(nd.c0, nd.f0), qlim = kc<T>(nd.c1, nd.f1);
+  const T eps = kc<T>(nd.c2, nd.f2);
+  T ta[2][5][4];   // T at offsets -2 .. 2 along each axis slot
+  tapsx4<2>(A, c, nd.axis, g, ta[0]);
+  if (nd.sk >= 0) tapsx4<2>(A, c, nd.sk, g, ta[1]);
+  T r[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const T fac = quench_fac<T>(
+        [&](int t, int, int s) {
+          return q_val(ta[t][s + 1][l], ta[t][s + 2][l], ta[t][s + 3][l], iq, eps, (T*)nullptr);
+        },
+        nd.axis, nd.sk, (T*)nullptr);
+    r[l] = ta[0][2][l] * (fac > qlim ? qlim : fac);
+  }
+  st4(out, c.idx, r);
+}
+
+template <typename T>
+__global__ void g_quench_q4(GNode nd, const T* A, T* Q, Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  const T iq = (T)1 / kc<T>(nd.c0, nd.f0), eps = kc<T>(nd.c2, nd.f2);
+  for (int t = 0; t < 2; ++t) {
+    const int ax = t == 0 ? nd.axis : nd.sk;
+    if (ax < 0) continue;
+    T ta[3][4];
+    tapsx4<1>(A, c, ax, g, ta);
+    T q[4], d0[4], d1[4], d2[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      T dq[3];
+      q[l] = q_val(ta[0][l], ta[1][l], ta[2][l], iq, eps, dq);
+      d0[l] = dq[0];
+      d1[l] = dq[1];
+      d2[l] = dq[2];
+    }
+    st4(Q + (long long)(4 * t) * g.n, c.idx, q);
+    st4(Q + (long long)(4 * t + 1) * g.n, c.idx, d0);
+    st4(Q + (long long)(4 * t + 2) * g.n, c.idx, d1);
+    st4(Q + (long long)(4 * t + 3) * g.n, c.idx, d2);
+  }
+}
+
+template <typename T>
+__global__ void g_quench_b1_4(GNode nd, const T* A, const T* Q, const T* gout, T* S, Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  const T qlim = kc<T>(nd.c1, nd.f1);
+  T tq[2][3][4];   // q at offsets -1 .. 1 along each axis slot
+  tapsx4<1>(Q, c, nd.axis, g, tq[0]);
+  if (nd.sk >= 0) tapsx4<1>(Q + 4 * g.n, c, nd.sk, g, tq[1]);
+  T a[4], gg[4];
+  ld4(A, c.idx, a);
+  ld4(gout, c.idx, gg);
+  T s0[4], sw[6][4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    T wq[6];
+    const T fac = quench_fac<T>([&](int t, int, int s) { return tq[t][s + 1][l]; }, nd.axis,
+                                nd.sk, wq);
+    const T C = fac > qlim ? qlim : fac;
+    const T dC = fac <= qlim ? (T)1 : (T)0;
+    const T base = gg[l] * a[l] * dC;
+    s0[l] = gg[l] * C;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sw[j][l] = base * wq[j];
+  }
+  st4(S, c.idx, s0);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) st4(S + (long long)(1 + j) * g.n, c.idx, sw[j]);
+}
+
+template <typename T>
+__global__ void g_quench_b3_4(GNode nd, const T* Q, const T* S, T* gA, int wA, Geo g) {
+  GCell4 c;
+  if (!gcell4(c, g)) return;
+  T acc[4];
+  ld4(S, c.idx, acc);
+  for (int t = 0; t < 2; ++t) {
+    const int ax = t == 0 ? nd.axis : nd.sk;
+    if (ax < 0) continue;
+    T ts[3][5][4];   // S of q position p = -1 .. 1 at offsets -2 .. 2
+#pragma unroll
+    for (int p = 0; p < 3; ++p) tapsx4<2>(S + (long long)(1 + 3 * t + p) * g.n, c, ax, g, ts[p]);
+    T td[3][3][4];   // d q(z) / d T at its tap 1 - r, z at offsets r = -1 .. 1
+#pragma unroll
+    for (int r = 0; r < 3; ++r) tapsx4<1>(Q + (long long)(4 * t + 3 - r) * g.n, c, ax, g, td[r]);
+#pragma unroll
+    for (int r = -1; r <= 1; ++r)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T qbar = 0;
+#pragma unroll
+        for (int p = -1; p <= 1; ++p) qbar += ts[p + 1][r - p + 2][l];
+        acc[l] += qbar * td[r + 1][r + 1][l];
+      }
+  }
+  if (!wA) {
+    T o[4];
+    ld4((const T*)gA, c.idx, o);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[l] = o[l] + acc[l];
+  }
+  st4(gA, c.idx, acc);
 }
 
 // Horizontal-plane mean (G_PMEAN): one block per z sums its plane in a fixed

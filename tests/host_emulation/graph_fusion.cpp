@@ -144,7 +144,12 @@ struct HostExec {
   case OP: run1d(vec ? g.n / 4 : g.n, [&] { g_forward_pw<T, OP>(nd, A, B, C, out, g.n, vec); }); break;
       switch (nd.op) {
         case G_PMEAN: pmean(A, out, false); break;
-        case G_QUENCH: run(G, [&] { g_quench_f<T>(nd, A, out, G); }); break;
+        case G_QUENCH:
+          if (allow4 && g.nx % 4 == 0 && al16(A) && al16(out))
+            run(G, [&] { g_quench_f4<T>(nd, A, out, G); }, true);
+          else
+            run(G, [&] { g_quench_f<T>(nd, A, out, G); });
+          break;
         FW(G_STENCIL) FW(G_SHIFT) FW(G_STBIN) FW(G_STMUL) FW(G_ST2) FW(G_STEXP) FW(G_NB3)
         FW(G_ZFIELD) FP(G_ADD) FP(G_SUB) FP(G_MUL) FP(G_DIV) FP(G_MAX) FP(G_EXP) FP(G_LOG)
         FP(G_LOG1P) FP(G_SQRT) FP(G_ABS) FP(G_AXPB) FP(G_CLAMPMIN) FP(G_CLAMPMAX) FP(G_STEP)
@@ -190,9 +195,15 @@ struct HostExec {
       switch (nd.op) {
         case G_PMEAN: pmean(go, gA, !WA); break;
         case G_QUENCH:
-          run(G, [&] { g_quench_q<T>(nd, A, S.data() + 7 * G.n, G); });
-          run(G, [&] { g_quench_b1<T>(nd, A, S.data() + 7 * G.n, go, S.data(), G); });
-          run(G, [&] { g_quench_b3<T>(nd, S.data() + 7 * G.n, S.data(), gA, WA, G); });
+          if (allow4 && g.nx % 4 == 0 && al16(A) && al16(go) && al16(gA) && al16(S.data())) {
+            run(G, [&] { g_quench_q4<T>(nd, A, S.data() + 7 * G.n, G); }, true);
+            run(G, [&] { g_quench_b1_4<T>(nd, A, S.data() + 7 * G.n, go, S.data(), G); }, true);
+            run(G, [&] { g_quench_b3_4<T>(nd, S.data() + 7 * G.n, S.data(), gA, WA, G); }, true);
+          } else {
+            run(G, [&] { g_quench_q<T>(nd, A, S.data() + 7 * G.n, G); });
+            run(G, [&] { g_quench_b1<T>(nd, A, S.data() + 7 * G.n, go, S.data(), G); });
+            run(G, [&] { g_quench_b3<T>(nd, S.data() + 7 * G.n, S.data(), gA, WA, G); });
+          }
           break;
         BW(G_STENCIL) BW(G_SHIFT) BW(G_STBIN) BW(G_STMUL) BW(G_ST2) BW(G_STEXP) BW(G_NB3)
         BP(G_ADD) BP(G_SUB) BP(G_MUL) BP(G_DIV) BP(G_MAX) BP(G_EXP) BP(G_LOG) BP(G_LOG1P)
