@@ -872,41 +872,56 @@ __global__ void g_backward4(GNode nd, const T* A, const T* B, const T* out, cons
   } else {
     // STENCIL, STBIN, STMUL, STEXP: the transposed stencil of gout, or of
     // gout times B (STBIN with a product) or times y - pt (STEXP).
-    T tg[7][4], tb[7][4];
-    taps7x4(gout, c, nd.axis, g, tg);
+    // One tap array live at a time (the product formed as its factor
+    // arrives), then, for STBIN of a product, the stencil of A for cb.
     const bool prod = (OP == G_STBIN && nd.iop == G_MUL) || OP == G_STEXP;
-    if (prod) taps7x4(OP == G_STEXP ? out : B, c, nd.axis, g, tb);
-    const T pt = kc<T>(nd.pt, nd.fpt);
-    T a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
-    if (OP == G_STMUL) {
-      ld4(A, c.idx, a);
-      ld4(B, c.idx, b);
-    }
-    T ta[7][4];
-    if (OP == G_STBIN && nd.iop == G_MUL) taps7x4(A, c, nd.axis, g, ta);
+    {
+      T tg[7][4];
+      taps7x4(gout, c, nd.axis, g, tg);
+      if (prod) {
+        T tb[7][4];
+        taps7x4(OP == G_STEXP ? out : B, c, nd.axis, g, tb);
+        const T pt = kc<T>(nd.pt, nd.fpt);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      T u[7];
+        for (int q = 0; q < 7; ++q)
 #pragma unroll
-      for (int q = 0; q < 7; ++q)
-        u[q] = !prod ? tg[q][l] : OP == G_STEXP ? tg[q][l] * (tb[q][l] - pt) : tg[q][l] * tb[q][l];
-      T v = st_comb(tk, h, u);
-      if (ng) v = -v;
-      if (OP == G_STBIN) {
-        if (nd.iop == G_MUL) {
-          T w[7];
-          lane7(ta, l, w);
-          ca[l] = v;
-          cb[l] = gg[l] * st_comb(nd.sk, h, w);
+          for (int l = 0; l < 4; ++l)
+            tg[q][l] = OP == G_STEXP ? tg[q][l] * (tb[q][l] - pt) : tg[q][l] * tb[q][l];
+      }
+      T a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+      if (OP == G_STMUL) {
+        ld4(A, c.idx, a);
+        ld4(B, c.idx, b);
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T u[7];
+        lane7(tg, l, u);
+        T v = st_comb(tk, h, u);
+        if (ng) v = -v;
+        if (OP == G_STBIN) {
+          if (nd.iop == G_MUL) {
+            ca[l] = v;
+          } else {
+            ca[l] = (nd.iop == G_SUB && nd.side) ? -v : v;
+            cb[l] = (nd.iop == G_SUB && !nd.side) ? -gg[l] : gg[l];
+          }
+        } else if (OP == G_STMUL) {
+          ca[l] = v * b[l];
+          cb[l] = v * a[l];
         } else {
-          ca[l] = (nd.iop == G_SUB && nd.side) ? -v : v;
-          cb[l] = (nd.iop == G_SUB && !nd.side) ? -gg[l] : gg[l];
+          ca[l] = v;
         }
-      } else if (OP == G_STMUL) {
-        ca[l] = v * b[l];
-        cb[l] = v * a[l];
-      } else {
-        ca[l] = v;
+      }
+    }
+    if (OP == G_STBIN && nd.iop == G_MUL) {
+      T ta[7][4];
+      taps7x4(A, c, nd.axis, g, ta);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T w[7];
+        lane7(ta, l, w);
+        cb[l] = gg[l] * st_comb(nd.sk, h, w);
       }
     }
   }
