@@ -2,10 +2,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdint.h>
+
+#include <algorithm>
 #include <new>
 
 #include "fused.cuh"
-#include "graph.cuh"
+#include "graph_kernels.cuh"
 
 using namespace stg;
 
@@ -295,13 +298,37 @@ __global__ void k_lin2(T* o, const T* x, T a, const T* y, T b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = a * x[i] + b * y[i];
 }
-// o = a x + (beta_s dt) y with beta_s dt read on the device (the adjoint's
-// graph replays with any dt).
+// o_k = a x_k + b_k y_k for the eight fields in one launch (blockIdx.y = k),
+// b_k = *bdt when bdt is given (beta_s dt on the device), else b; four
+// elements a thread through 16-byte accesses when vec.
 template <typename T>
-__global__ void k_lin2d(T* o, const T* x, T a, const T* y, const T* bdt, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) o[i] = a * x[i] + bdt[0] * y[i];
+struct Lin8 {
+  T* o[8];
+  const T* x[8];
+  const T* y[8];
+};
+template <typename T>
+__global__ void k_lin2x8(Lin8<T> p, T a, T b, const T* bdt, long long n, int vec) {
+  const int f = blockIdx.y;
+  const T bb = bdt ? bdt[0] : b;
+  T* o = p.o[f];
+  const T *x = p.x[f], *y = p.y[f];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    for (; t < n / 4; t += stride) {
+      T xv[4], yv[4], ov[4];
+      ld4(x, 4 * t, xv);
+      ld4(y, 4 * t, yv);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ov[l] = a * xv[l] + bb * yv[l];
+      st4(o, 4 * t, ov);
+    }
+  } else {
+    for (; t < n; t += stride) o[t] = a * x[t] + bb * y[t];
+  }
 }
+
 // dt, and beta_s dt of the three RK stages in FP64 and FP32.
 __global__ void k_set_dt3(double* dtp, float* bdtf, double dt, double b0, double b1, double b2) {
   const double b[3] = {b0, b1, b2};
@@ -673,17 +700,31 @@ static void lin2(stagger_ctx* c, T* o, const T* x, double a, const T* y, double 
   k_lin2<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, (T)a, y, (T)b, n);
   ++c->extra_launches;
 }
-// o = a x + beta_st dt y (k_set_dt3 has written beta_st dt).
+// The same over the eight fields in one launch: o[k] = a x[k] + b y[k], or
+// with st >= 0 the coefficient beta_st dt of y read on the device.
 template <typename T>
-static void lin2d(stagger_ctx* c, T* o, const T* x, double a, const T* y, int st,
-                  cudaStream_t s) {
-  long long n = c->geo.n;
-  const T* bdt;
-  if constexpr (sizeof(T) == sizeof(float)) bdt = c->bdtf + st;
-  else bdt = c->dtp + 1 + st;
-  k_lin2d<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o, x, (T)a, y, bdt, n);
+static void lin2x8(stagger_ctx* c, T* const o[8], T* const x[8], double a, T* const y[8],
+                   double b, int st, cudaStream_t s) {
+  const long long n = c->geo.n;
+  Lin8<T> p;
+  int vec = n % 4 == 0;
+  for (int k = 0; k < 8; ++k) {
+    p.o[k] = o[k];
+    p.x[k] = x[k];
+    p.y[k] = y[k];
+    vec &= (((uintptr_t)o[k] | (uintptr_t)x[k] | (uintptr_t)y[k]) & 15) == 0;
+  }
+  const T* bdt = nullptr;
+  if (st >= 0) {
+    if constexpr (sizeof(T) == sizeof(float)) bdt = c->bdtf + st;
+    else bdt = c->dtp + 1 + st;
+  }
+  const long long work = vec ? n / 4 : n;
+  const unsigned bx = (unsigned)std::min<long long>((work + 255) / 256, 4096);
+  k_lin2x8<T><<<dim3(bx, 8), 256, 0, s>>>(p, (T)a, (T)b, bdt, n, vec);
   ++c->extra_launches;
 }
+
 
 template <typename T>
 static int graph_rhs(stagger_ctx* c, T* const f[8], T* out[8], cudaStream_t s) {
@@ -781,28 +822,22 @@ static int adjoint_body(stagger_ctx* c, T* const f0[8], T* const lam_in[8], T* l
   // Recompute the stage states f1, f2 (eqs. (ddt), (tupdate)); the FP32
   // path takes F from the fused kernels, FP64 from the graph.
   if ((rc = stage_rhs<T>(c, G, f0, fb, s))) return rc;
-  for (int k = 0; k < 8; ++k) {
-    lin2<T>(c, q[k], fb[k], 1.0, fb[k], 0.0, s);
-    lin2d<T>(c, f1[k], f0[k], 1.0, q[k], 0, s);
-  }
+  lin2x8<T>(c, q, fb, 1.0, fb, 0.0, -1, s);
+  lin2x8<T>(c, f1, f0, 1.0, q, 0.0, 0, s);
   if ((rc = stage_rhs<T>(c, G, f1, fb, s))) return rc;
-  for (int k = 0; k < 8; ++k) {
-    lin2<T>(c, q[k], q[k], A[1], fb[k], 1.0, s);
-    lin2d<T>(c, f2[k], f1[k], 1.0, q[k], 1, s);
-  }
+  lin2x8<T>(c, q, q, A[1], fb, 1.0, -1, s);
+  lin2x8<T>(c, f2, f1, 1.0, q, 0.0, 1, s);
   // Reverse sweep: fbar_3 = lam; qbar_3 = beta_3 dt fbar.
-  for (int k = 0; k < 8; ++k) {
-    lin2<T>(c, fb[k], lam_in[k], 1.0, lam_in[k], 0.0, s);
-    lin2d<T>(c, qb[k], fb[k], 0.0, fb[k], 2, s);
-  }
+  lin2x8<T>(c, fb, lam_in, 1.0, lam_in, 0.0, -1, s);
+  lin2x8<T>(c, qb, fb, 0.0, fb, 0.0, 2, s);
   T* const* stages[3] = {f0, f1, f2};
   for (int st = 2; st >= 0; --st) {
     if ((rc = G->forward(stages[st], s))) return rc;
     if ((rc = G->backward(qb, fb, s))) return rc;     // fbar += J(f_st)^T qbar
     if (st > 0)                                         // qbar_{st} = alpha qbar + beta dt fbar
-      for (int k = 0; k < 8; ++k) lin2d<T>(c, qb[k], qb[k], A[st], fb[k], st - 1, s);
+      lin2x8<T>(c, qb, qb, A[st], fb, 0.0, st - 1, s);
   }
-  for (int k = 0; k < 8; ++k) lin2<T>(c, lam_out[k], fb[k], 1.0, fb[k], 0.0, s);
+  lin2x8<T>(c, lam_out, fb, 1.0, fb, 0.0, -1, s);
   STG_CUDA_OK(cudaGetLastError());
   return STAGGER_OK;
 }

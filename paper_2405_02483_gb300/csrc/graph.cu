@@ -423,9 +423,15 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
     }
   }
   if (nconc && join_streams(*this, s)) return STAGGER_ECUDA;
+  Add8<T> ad;
+  unsigned na = 0;
   for (int k = 0; k < 8; ++k) {
     if (!hasg[def.in[k]]) continue;   // the outputs do not depend on this input
-    g_add_into<T><<<nblocks(geo.n, bs), bs, 0, s>>>(gin[k], grads + (size_t)def.in[k] * geo.n, geo.n);
+    ad.dst[na] = gin[k];
+    ad.src[na++] = grads + (size_t)def.in[k] * geo.n;
+  }
+  if (na) {
+    g_add_into8<T><<<dim3(std::min(nblocks(geo.n, bs), 4096u), na), bs, 0, s>>>(ad, geo.n);
     ++launches;
   }
   STG_CUDA_OK(cudaGetLastError());

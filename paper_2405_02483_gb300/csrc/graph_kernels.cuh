@@ -1099,10 +1099,19 @@ __global__ void g_plane_bcast(const T* psum, T* out, int add, Geo g) {
   }
 }
 
+// dst[k] += src[k] for up to eight arrays in one launch (blockIdx.y = k).
 template <typename T>
-__global__ void g_add_into(T* dst, const T* src, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] += src[i];
+struct Add8 {
+  T* dst[8];
+  const T* src[8];
+};
+template <typename T>
+__global__ void g_add_into8(Add8<T> p, long long n) {
+  T* dst = p.dst[blockIdx.y];
+  const T* src = p.src[blockIdx.y];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    dst[i] += src[i];
 }
 
 }  // namespace stg
