@@ -1,7 +1,8 @@
 // Op-graph kernels (see graph.cuh): the forward and the hand-written
 // transpose (vector-Jacobian) kernel of every primitive, as templates over the
-// sweep's precision.  Included by the executor (graph.cu); plain C++ apart
-// from the CUDA qualifiers, so that a host build can run them too.
+// sweep's precision.  Included by the executor (graph.cu) and by the C ABI
+// (api.cu, for the 16-byte access helpers of its RK combinations); plain C++
+// apart from the CUDA qualifiers, so that a host build can run them too.
 #pragma once
 
 #include <math.h>
