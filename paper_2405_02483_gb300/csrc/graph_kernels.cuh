@@ -152,6 +152,14 @@ __device__ __forceinline__ T sgn(T a) {
 
 // q at z = c + s e_ax from T at z - 1, z, z + 1 (vm, v0, vp), and (dq) its
 // derivatives with respect to those (through D2 T and through M).
+// The quench's divisions: the fast intrinsic in FP32 (within 2 ulp; the
+// divisors are >= 1e-30 and far below 2^126), IEEE division in FP64.
+template <typename T>
+__device__ __forceinline__ T qdiv(T a, T b) {
+  if constexpr (sizeof(T) == sizeof(float)) return __fdividef(a, b);
+  else return a / b;
+}
+
 template <typename T>
 __device__ __forceinline__ T q_val(T vm, T v0, T vp, T iq, T eps, T* dq) {
   const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
@@ -162,15 +170,15 @@ __device__ __forceinline__ T q_val(T vm, T v0, T vp, T iq, T eps, T* dq) {
   const T cM = eps < (T)0 ? (T)1 : eps, cP = eps < (T)0 ? (T)0 : (T)1;
   const T M = eps < (T)0 ? M3 : a0 + eps * M3;
   const T den = (M + a2 * iq) + (T)1e-30;
-  const T q = a2 / den;
+  const T q = qdiv(a2, den);
   if (dq) {
     T wim, wi0, woi, wop;
     max_w(am, a0, wim, wi0);
     max_w(inner, ap, woi, wop);
     // a2 / den^2 as q / den: den^2 underflows in FP32 where T and D2 T are
     // both zero (den = 1e-30), and 0 / 0 would poison the cotangent.
-    const T qd = q / den;
-    const T dq_da2 = (T)1 / den - iq * qd;
+    const T qd = qdiv(q, den);
+    const T dq_da2 = qdiv((T)1, den) - iq * qd;
     const T dq_dM = -qd;
     const T sd = sgn(d2);
     dq[0] = dq_da2 * sd + dq_dM * (cM * (woi * wim)) * sgn(vm);
@@ -732,6 +740,22 @@ __device__ __forceinline__ void taps7x4(const T* f, const GCell4& c, int axis, c
   tapsx4<3>(f, c, axis, g, t);
 }
 
+// v[l]: f at cell (i0 + l, j, k) + o e_axis, one offset o in -1 .. 1.
+template <typename T>
+__device__ __forceinline__ void tap1x4(const T* f, const GCell4& c, int axis, int o,
+                                       const Geo& g, T (&v)[4]) {
+  if (axis == 0) {
+    T t[3][4];
+    tapsx4<1>(f, c, 0, g, t);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) v[l] = o < 0 ? t[0][l] : o > 0 ? t[2][l] : t[1][l];
+  } else {
+    const long long st = axis == 1 ? g.sy : g.sz;
+    const int pos = axis == 1 ? c.j : c.k, n = axis == 1 ? g.ny : g.nz;
+    ld4(f, c.idx + (long long)(wrap(pos + o, n) - pos) * st, v);
+  }
+}
+
 // Lane l's seven taps as one array.
 template <typename T>
 __device__ __forceinline__ void lane7(const T t[7][4], int l, T u[7]) {
@@ -1047,9 +1071,10 @@ __global__ void g_quench_b3_4(GNode nd, const T* Q, const T* S, T* gA, int wA, G
     T ts[3][5][4];   // S of q position p = -1 .. 1 at offsets -2 .. 2
 #pragma unroll
     for (int p = 0; p < 3; ++p) tapsx4<2>(S + (long long)(1 + 3 * t + p) * g.n, c, ax, g, ts[p]);
-    T td[3][3][4];   // d q(z) / d T at its tap 1 - r, z at offsets r = -1 .. 1
+    T td[3][4];   // d q(z) / d T at its tap 1 - r, z at offsets r = -1 .. 1
 #pragma unroll
-    for (int r = 0; r < 3; ++r) tapsx4<1>(Q + (long long)(4 * t + 3 - r) * g.n, c, ax, g, td[r]);
+    for (int r = -1; r <= 1; ++r)
+      tap1x4(Q + (long long)(4 * t + 2 - r) * g.n, c, ax, r, g, td[r + 1]);
 #pragma unroll
     for (int r = -1; r <= 1; ++r)
 #pragma unroll
@@ -1057,7 +1082,7 @@ __global__ void g_quench_b3_4(GNode nd, const T* Q, const T* S, T* gA, int wA, G
         T qbar = 0;
 #pragma unroll
         for (int p = -1; p <= 1; ++p) qbar += ts[p + 1][r - p + 2][l];
-        acc[l] += qbar * td[r + 1][r + 1][l];
+        acc[l] += qbar * td[r + 1][l];
       }
   }
   if (!wA) {

@@ -37,6 +37,7 @@
 #define __syncthreads()
 uint3 blockIdx, threadIdx;
 dim3 blockDim, gridDim;
+static inline float __fdividef(float a, float b) { return a / b; }
 #include "../../paper_2405_02483_gb300/csrc/graph_kernels.cuh"
 #include "../../paper_2405_02483_gb300/csrc/graph_build.cu"
 using namespace stg;
