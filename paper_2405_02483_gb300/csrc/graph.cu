@@ -243,16 +243,14 @@ static BwdPwK<T> bwd_kernel_pw(int op) {
 static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // The four-x-cell stencil kernels: nx a multiple of 4 and shifts of one cell
 // (the arrays' alignment is checked per launch), for the kernels they made
-// faster.  Those that gather two or three tap arrays per cell at high
-// register counts measured slower with four cells (FP32, 128^3, ncu launch
-// list: forward ST2 22.1 / STMUL 19.0 us against 19.3 / 15.9 with one cell,
-// transpose STEXP 22.8 and STBIN of a product among 30.6 us STBIN launches,
-// against 17.2 and 23.8) and keep one cell a thread.
+// faster.  The forward ST2 and STMUL, which gather two tap arrays, measured
+// slower with four cells (FP32, 128^3, ncu launch list: 20.5 / 17.4 us at 64
+// registers, 22.1 / 19.0 at 80, against 19.3 / 15.9 with one cell) and keep
+// one cell a thread; every transpose is faster with four.
 static inline bool cells4(const GNode& nd, const Geo& g, bool bwd) {
   if (g.nx % 4 != 0) return false;
   if ((nd.op == G_SHIFT || nd.op == G_NB3) && nd.sk != 1 && nd.sk != -1) return false;
-  if (!bwd) return nd.op != G_ST2 && nd.op != G_STMUL;
-  return nd.op != G_STEXP && !(nd.op == G_STBIN && nd.iop == G_MUL);
+  return bwd || (nd.op != G_ST2 && nd.op != G_STMUL);
 }
 static inline dim3 ggrid4(const Geo& g) {
   return dim3((unsigned)((g.nx / 4 + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),
@@ -425,13 +423,16 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   if (nconc && join_streams(*this, s)) return STAGGER_ECUDA;
   Add8<T> ad;
   unsigned na = 0;
+  int vec = geo.n % 4 == 0;
   for (int k = 0; k < 8; ++k) {
     if (!hasg[def.in[k]]) continue;   // the outputs do not depend on this input
     ad.dst[na] = gin[k];
-    ad.src[na++] = grads + (size_t)def.in[k] * geo.n;
+    ad.src[na] = grads + (size_t)def.in[k] * geo.n;
+    vec &= al16(ad.dst[na]) && al16(ad.src[na]);
+    ++na;
   }
   if (na) {
-    g_add_into8<T><<<dim3(std::min(nblocks(geo.n, bs), 4096u), na), bs, 0, s>>>(ad, geo.n);
+    g_add_into8<T><<<dim3(pw_blocks(vec ? geo.n / 4 : geo.n), na), bs, 0, s>>>(ad, geo.n, vec);
     ++launches;
   }
   STG_CUDA_OK(cudaGetLastError());

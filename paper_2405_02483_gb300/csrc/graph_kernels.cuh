@@ -772,8 +772,12 @@ __device__ __forceinline__ T tap2(const T t[7][4], int s, int l) {
   return s > 0 ? t[5][l] : t[1][l];
 }
 
+// At most 64 registers (4 blocks per SM): the transposes that gather two or
+// three tap arrays spill about 100 bytes then, yet run faster than at 76-84
+// registers and 3 blocks (STBIN of a product 38 -> 21 us, STEXP 23 -> 16 us at
+// 128^3); the forward kernels taken with four cells stay under 64 anyway.
 template <typename T, int OP>
-__global__ void g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
+__global__ void __launch_bounds__(GBX * GBY * GBZ, 4) g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
                            Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
@@ -840,7 +844,7 @@ __global__ void g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out,
 }
 
 template <typename T, int OP>
-__global__ void g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+__global__ void __launch_bounds__(GBX * GBY * GBZ, 4) g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
                             T* gA, T* gB, T* gC, int wA, int wB, int wC, Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
@@ -1132,12 +1136,23 @@ struct Add8 {
   const T* src[8];
 };
 template <typename T>
-__global__ void g_add_into8(Add8<T> p, long long n) {
+__global__ void g_add_into8(Add8<T> p, long long n, int vec) {
   T* dst = p.dst[blockIdx.y];
   const T* src = p.src[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    dst[i] += src[i];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {   // four elements a thread through 16-byte accesses
+    for (; t < n / 4; t += stride) {
+      T a[4], b[4];
+      ld4((const T*)dst, 4 * t, a);
+      ld4(src, 4 * t, b);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) a[l] += b[l];
+      st4(dst, 4 * t, a);
+    }
+  } else {
+    for (; t < n; t += stride) dst[t] += src[t];
+  }
 }
 
 }  // namespace stg
