@@ -123,7 +123,6 @@ void GraphExec<T>::release() {
   ptr.clear();
 }
 
-static inline unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 // z extent of the launch: GBZ * GZU cells per block along z (GZU per thread).
 static inline dim3 ggrid(const Geo& g) {
   return dim3((unsigned)((g.nx + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),
