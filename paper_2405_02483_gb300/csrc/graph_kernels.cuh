@@ -772,12 +772,13 @@ __device__ __forceinline__ T tap2(const T t[7][4], int s, int l) {
   return s > 0 ? t[5][l] : t[1][l];
 }
 
-// At most 64 registers (4 blocks per SM): the transposes that gather two or
-// three tap arrays spill about 100 bytes then, yet run faster than at 76-84
-// registers and 3 blocks (STBIN of a product 38 -> 21 us, STEXP 23 -> 16 us at
-// 128^3); the forward kernels taken with four cells stay under 64 anyway.
+// FP32: at most 64 registers (4 blocks per SM): the transposes that gather
+// two or three tap arrays spill about 100 bytes then, yet run faster than at
+// 76-84 registers and 3 blocks (STBIN of a product 38 -> 21 us, STEXP 23 -> 16
+// us at 128^3); the forward kernels taken with four cells stay under 64
+// anyway.  FP64 (twice the registers a value) keeps the compiler's choice.
 template <typename T, int OP>
-__global__ void __launch_bounds__(GBX * GBY * GBZ, 4) g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
+__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
                            Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
@@ -844,7 +845,7 @@ __global__ void __launch_bounds__(GBX * GBY * GBZ, 4) g_forward4(GNode nd, const
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(GBX * GBY * GBZ, 4) g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
+__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
                             T* gA, T* gB, T* gC, int wA, int wB, int wC, Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
