@@ -242,14 +242,15 @@ static BwdPwK<T> bwd_kernel_pw(int op) {
 static inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // The four-x-cell stencil kernels: nx a multiple of 4 and shifts of one cell
 // (the arrays' alignment is checked per launch), for the kernels they made
-// faster.  The forward ST2 and STMUL, which gather two tap arrays, measured
-// slower with four cells (FP32, 128^3, ncu launch list: 20.5 / 17.4 us at 64
-// registers, 22.1 / 19.0 at 80, against 19.3 / 15.9 with one cell) and keep
-// one cell a thread; every transpose is faster with four.
+// faster.  The forward STMUL, which gathers two tap arrays, measured slower
+// with four cells (FP32, 128^3, ncu launch list: 16.8 us at 64 registers
+// against 15.9 with one cell) and keeps one cell a thread; every other
+// forward (ST2 17.5 against 19.2 once its two stencils were formed one after
+// the other) and every transpose is faster with four.
 static inline bool cells4(const GNode& nd, const Geo& g, bool bwd) {
   if (g.nx % 4 != 0) return false;
   if ((nd.op == G_SHIFT || nd.op == G_NB3) && nd.sk != 1 && nd.sk != -1) return false;
-  return bwd || (nd.op != G_ST2 && nd.op != G_STMUL);
+  return bwd || nd.op != G_STMUL;
 }
 static inline dim3 ggrid4(const Geo& g) {
   return dim3((unsigned)((g.nx / 4 + GBX - 1) / GBX), (unsigned)((g.ny + GBY - 1) / GBY),

@@ -789,28 +789,45 @@ __global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_for
 #pragma unroll
     for (int l = 0; l < 4; ++l) r[l] = z;
   } else if (OP == G_STMUL) {
-    T ta[7][4], tb[7][4];
+    // The product formed as B's taps arrive: one tap array live.
+    T ta[7][4];
     taps7x4(A, c, nd.axis, g, ta);
-    taps7x4(B, c, nd.axis, g, tb);
+    {
+      T tb[7][4];
+      taps7x4(B, c, nd.axis, g, tb);
+#pragma unroll
+      for (int o = 0; o < 7; ++o)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) ta[o][l] = ta[o][l] * tb[o][l];
+    }
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       T u[7];
-#pragma unroll
-      for (int o = 0; o < 7; ++o) u[o] = ta[o][l] * tb[o][l];
+      lane7(ta, l, u);
       r[l] = st_comb(nd.sk, h, u);
     }
   } else if (OP == G_ST2) {
-    T ta[7][4], tb[7][4];
-    taps7x4(A, c, nd.axis, g, ta);
+    // The two stencils one after the other: one tap array live.
+    T s1[4];
+    {
+      T ta[7][4];
+      taps7x4(A, c, nd.axis, g, ta);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T u[7];
+        lane7(ta, l, u);
+        s1[l] = st_comb(nd.sk, h, u);
+      }
+    }
+    T tb[7][4];
     taps7x4(B, c, nd.axis2, g, tb);
     const T h2 = kc<T>(nd.h2, nd.fh2);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-      T u[7], v[7];
-      lane7(ta, l, u);
+      T v[7];
       lane7(tb, l, v);
-      const T s1 = st_comb(nd.sk, h, u), s2 = st_comb(nd.sk2, h2, v);
-      r[l] = nd.iop == G_ADD ? s1 + s2 : s1 - s2;
+      const T s2 = st_comb(nd.sk2, h2, v);
+      r[l] = nd.iop == G_ADD ? s1[l] + s2 : s1[l] - s2;
     }
   } else {
     T t[7][4];
