@@ -135,10 +135,11 @@ __device__ __forceinline__ bool st_negates(int kind) { return kind == ST_DDUP ||
 // Quench, eq. (quench) with reading R8, as one node: out = T min(fac, qlim),
 // fac = the max over the node's axes of max3 along the axis of
 // q = |D2 T| / ((M + |D2 T| / qmax) + 1e-30), D2 T = T(+1) - 2 T + T(-1) and
-// M = |T| + eps max3 |T| (eps = c2 >= 0), or M = max3 |T| (c2 < 0).  Its transpose follows the rules of the primitive nodes it
-// stands for: a max splits the gradient evenly on a tie (pairwise, the inner
-// pair first), |x|' = sign x with sign 0 = 0, the clamp passes the gradient
-// where fac <= qlim.
+// M = |T| + eps max3 |T| (eps = c2 >= 0), or M = max3 |T| (c2 < 0).  Its
+// transpose follows the rules of the primitive nodes it stands for: a max
+// splits the gradient evenly on a tie (pairwise, the inner pair first),
+// |x|' = sign x with sign 0 = 0, the clamp passes the gradient where
+// fac <= qlim.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void max_w(T a, T b, T& wa, T& wb) {
@@ -150,8 +151,6 @@ __device__ __forceinline__ T sgn(T a) {
   return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
 }
 
-// q at z = c + s e_ax from T at z - 1, z, z + 1 (vm, v0, vp), and (dq) its
-// derivatives with respect to those (through D2 T and through M).
 // The quench's divisions: the fast intrinsic in FP32 (within 2 ulp; the
 // divisors are >= 1e-30 and far below 2^126), IEEE division in FP64.
 template <typename T>
@@ -160,6 +159,8 @@ __device__ __forceinline__ T qdiv(T a, T b) {
   else return a / b;
 }
 
+// q at z = c + s e_ax from T at z - 1, z, z + 1 (vm, v0, vp), and (dq) its
+// derivatives with respect to those (through D2 T and through M).
 template <typename T>
 __device__ __forceinline__ T q_val(T vm, T v0, T vp, T iq, T eps, T* dq) {
   const T d2 = (vp - (T)2 * v0) + vm, a2 = fabs(d2);
@@ -778,8 +779,8 @@ __device__ __forceinline__ T tap2(const T t[7][4], int s, int l) {
 // us at 128^3); the forward kernels taken with four cells stay under 64
 // anyway.  FP64 (twice the registers a value) keeps the compiler's choice.
 template <typename T, int OP>
-__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh,
-                           Geo g) {
+__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1)
+    g_forward4(GNode nd, const T* A, const T* B, const T* C, T* out, const T* mesh, Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
   const T h = kc<T>(nd.c0, nd.f0);
@@ -862,8 +863,9 @@ __global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_for
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1) g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout,
-                            T* gA, T* gB, T* gC, int wA, int wB, int wC, Geo g) {
+__global__ void __launch_bounds__(GBX * GBY * GBZ, sizeof(T) == 4 ? 4 : 1)
+    g_backward4(GNode nd, const T* A, const T* B, const T* out, const T* gout, T* gA, T* gB,
+                T* gC, int wA, int wB, int wC, Geo g) {
   GCell4 c;
   if (!gcell4(c, g)) return;
   const T h = kc<T>(nd.c0, nd.f0);

@@ -141,8 +141,10 @@ struct HostExec {
     else                                                                          \
       run(G, [&] { g_forward<T, OP>(nd, A, B, C, out, M, G); });                  \
     break;
-#define FP(OP) \
-  case OP: run1d(vec ? g.n / 4 : g.n, [&] { g_forward_pw<T, OP>(nd, A, B, C, out, g.n, vec); }); break;
+#define FP(OP)                                                                         \
+  case OP:                                                                             \
+    run1d(vec ? g.n / 4 : g.n, [&] { g_forward_pw<T, OP>(nd, A, B, C, out, g.n, vec); }); \
+    break;
       switch (nd.op) {
         case G_PMEAN: pmean(A, out, false); break;
         case G_QUENCH:
