@@ -60,3 +60,7 @@ def test_merged_op_graph_equals_one_node_per_primitive(tmp_path):
     import re
     four = [int(m) for m in re.findall(r"four-cell \((\d+) four-cell launches\)", out)]
     assert len(four) == 8 and sum(1 for f in four if f > 0) == 6, out
+    # the merges keep taking out more than a third of the nodes (the
+    # adjoint's launches and arrays scale with them; 39-43% now)
+    for a, b in re.findall(r": (\d+) -> (\d+) nodes", out):
+        assert int(b) <= 0.65 * int(a), (a, b)
