@@ -52,30 +52,13 @@ int GraphExec<T>::init(const GraphDef& d, const Geo& g, bool with_grads) {
       return STAGGER_ECUDA;
     }
   }
+  // Reverse-sweep bookkeeping: gradient flags and the reused gradient arrays.
+  plan_reverse(def, rp);
   if (with_grads) {
-    if (cudaMalloc(&grads, sizeof(T) * nn * g.n) != cudaSuccess) {
+    if (cudaMalloc(&grads, sizeof(T) * (size_t)rp.nslots * g.n) != cudaSuccess) {
       grads = nullptr;
       release();
       return STAGGER_EOOM;
-    }
-  }
-  // Reverse-sweep bookkeeping: which nodes receive a gradient, and which
-  // consumer slot gives each node its first contribution (in reverse order).
-  hasg.assign(nn, 0);
-  wa.assign(nn, 0);
-  wb.assign(nn, 0);
-  wc.assign(nn, 0);
-  {
-    std::vector<char> seen(nn, 0);
-    for (int k = 0; k < 8; ++k) seen[def.out[k]] = hasg[def.out[k]] = 1;
-    for (long long i = (long long)nn - 1; i >= 0; --i) {
-      const GNode& nd = def.nodes[i];
-      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
-          nd.op == G_STEP)
-        continue;
-      if (nd.a >= 0) { wa[i] = !seen[nd.a]; seen[nd.a] = hasg[nd.a] = 1; }
-      if (nd.b >= 0) { wb[i] = !seen[nd.b]; seen[nd.b] = hasg[nd.b] = 1; }
-      if (nd.c >= 0) { wc[i] = !seen[nd.c]; seen[nd.c] = hasg[nd.c] = 1; }
     }
   }
   ptr.assign(nn, nullptr);
@@ -346,45 +329,47 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   const dim3 gg = ggrid(geo), gb(GBX, GBY, GBZ);
   // Seeds are the first contribution to the outputs' gradients: copy them.
   for (int k = 0; k < 8; ++k)
-    STG_CUDA_OK(cudaMemcpyAsync(grads + (size_t)def.out[k] * geo.n, seed[k],
+    STG_CUDA_OK(cudaMemcpyAsync(gptr(def.out[k]), seed[k],
                                 sizeof(T) * geo.n, cudaMemcpyDeviceToDevice, s));
   // Concurrent form: the last launch that wrote each gradient array (-1: none
   // since the fork), and its stream.
   std::vector<int> lastw(nconc ? nn : 0, -1), sto(nconc ? nn : 0, -1);
   int rr = 0, prev_scr = -1;
   if (nconc && fork_streams(*this, s)) return STAGGER_ECUDA;
+  const std::vector<char>&wa = rp.wa, &wb = rp.wb, &wc = rp.wc;
   for (long long i = (long long)nn - 1; i >= 0; --i) {
     const GNode& nd = def.nodes[i];
-    if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD ||
-        nd.op == G_STEP)
-      continue;
+    if (!rp.hasg[i] || !has_transpose(nd.op)) continue;
     const T* A = nd.a >= 0 ? ptr[nd.a] : nullptr;
     const T* B = nd.b >= 0 ? ptr[nd.b] : nullptr;
-    T* gA = nd.a >= 0 ? grads + (size_t)nd.a * geo.n : nullptr;
-    T* gB = nd.b >= 0 ? grads + (size_t)nd.b * geo.n : nullptr;
-    T* gC = nd.c >= 0 ? grads + (size_t)nd.c * geo.n : nullptr;
+    T* gA = nd.a >= 0 ? gptr(nd.a) : nullptr;
+    T* gB = nd.b >= 0 ? gptr(nd.b) : nullptr;
+    T* gC = nd.c >= 0 ? gptr(nd.c) : nullptr;
     cudaStream_t st = s;
     if (nconc) {
       // Wait for the complete gradient of this node, for the previous writer
-      // of each gradient it adds to, and for the previous user of the shared
-      // scratch (quench, plane mean).
+      // of each gradient it adds to, for the transpose that last read an
+      // array this launch writes first, and for the previous user of the
+      // shared scratch (quench, plane mean).
       const int own = lastw[i];
       int k = own >= 0 ? sto[own] : (rr++ % nconc);
       st = aux[k];
       const bool scr = nd.op == G_QUENCH || nd.op == G_PMEAN;
       for (int w : {own, nd.a >= 0 ? lastw[nd.a] : -1, nd.b >= 0 ? lastw[nd.b] : -1,
-                    nd.c >= 0 ? lastw[nd.c] : -1, scr ? prev_scr : -1})
+                    nd.c >= 0 ? lastw[nd.c] : -1, scr ? prev_scr : -1,
+                    wa[i] ? rp.gprev[nd.a] : -1, wb[i] ? rp.gprev[nd.b] : -1,
+                    wc[i] ? rp.gprev[nd.c] : -1})
         if (w >= 0 && sto[w] != k) STG_CUDA_OK(cudaStreamWaitEvent(st, evn[w], 0));
       sto[i] = k;
       if (scr) prev_scr = (int)i;
     }
     if (nd.op == G_PMEAN) {
-      g_plane_sum<T><<<geo.nz, 256, 0, st>>>(grads + (size_t)i * geo.n, psum, geo);
+      g_plane_sum<T><<<geo.nz, 256, 0, st>>>(gptr((int)i), psum, geo);
       g_plane_bcast<T><<<gg, gb, 0, st>>>(psum, gA, wa[i] ? 0 : 1, geo);
       launches += 2;
     } else if (nd.op == G_QUENCH) {
       T* Q = qscr + (size_t)7 * geo.n;   // q and its derivatives, 4 arrays per axis slot
-      T* gi = grads + (size_t)i * geo.n;
+      T* gi = gptr((int)i);
       if (geo.nx % 4 == 0 && al16(A) && al16(gi) && al16(gA) && al16(qscr)) {
         const dim3 g4 = ggrid4(geo);
         g_quench_q4<T><<<g4, gb, 0, st>>>(nd, A, Q, geo);
@@ -397,7 +382,7 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
       }
       launches += 3;
     } else {
-      T* gi = grads + (size_t)i * geo.n;
+      T* gi = gptr((int)i);
       if (pointwise_op(nd.op)) {
         const int vec = geo.n % 4 == 0 && al16(A) && al16(B) && al16(ptr[i]) && al16(gi) &&
                         al16(gA) && al16(gB) && al16(gC);
@@ -425,9 +410,9 @@ int GraphExec<T>::backward(T* const seed[8], T* gin[8], cudaStream_t s) {
   unsigned na = 0;
   int vec = geo.n % 4 == 0;
   for (int k = 0; k < 8; ++k) {
-    if (!hasg[def.in[k]]) continue;   // the outputs do not depend on this input
+    if (!rp.hasg[def.in[k]]) continue;   // the outputs do not depend on this input
     ad.dst[na] = gin[k];
-    ad.src[na] = grads + (size_t)def.in[k] * geo.n;
+    ad.src[na] = gptr(def.in[k]);
     vec &= al16(ad.dst[na]) && al16(ad.src[na]);
     ++na;
   }

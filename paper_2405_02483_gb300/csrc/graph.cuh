@@ -118,6 +118,25 @@ struct GraphDef {
 void build_rhs_graph(GraphDef& G, const stagger_grid& grid, const stagger_params& p,
                      bool fuse = true);
 
+// The reverse sweep's plan, from the graph alone: which nodes receive a
+// gradient (hasg), which operand slot of a node gives an input its first
+// contribution and so writes rather than adds (wa, wb, wc), and the gradient
+// array of each node.  A gradient is live from its first contribution (by its
+// highest-numbered consumer) to its own transpose; arrays are reused once the
+// transpose that read them has run: gslot[i] is node i's array (-1: none),
+// gprev[i] the node whose transpose last read that array before (-1: a fresh
+// array), which the first writer must wait for.  Returns the number of arrays.
+struct ReversePlan {
+  std::vector<char> hasg, wa, wb, wc;
+  std::vector<int> gslot, gprev;
+  int nslots = 0;
+};
+void plan_reverse(const GraphDef& G, ReversePlan& P);
+// Whether node op has a transpose kernel (the others pass no gradient on).
+inline bool has_transpose(int op) {
+  return op != G_INPUT && op != G_CONST && op != G_ZFIELD && op != G_STEP;
+}
+
 #ifndef GRAPH_NSTREAMS
 #define GRAPH_NSTREAMS 4
 #endif
@@ -132,11 +151,10 @@ struct GraphExec {
   T* mesh = nullptr;     // the mesh arrays of G_ZFIELD on the device, or null
   T* psum = nullptr;     // per-plane sums of G_PMEAN (nz), or null
   T* qscr = nullptr;     // 15 arrays of scratch for the G_QUENCH transpose, or null
-  T* grads = nullptr;    // node gradients (all nodes)
+  T* grads = nullptr;    // gradient arrays (rp.nslots, reused by liveness)
   std::vector<T*> ptr;   // value pointer per node
-  // Reverse sweep: node receives a gradient; its a / b / c slot writes
-  // (rather than accumulates into) the input's gradient.
-  std::vector<char> hasg, wa, wb, wc;
+  ReversePlan rp;        // the reverse sweep's gradient flags and arrays
+  T* gptr(int i) { return grads + (size_t)rp.gslot[i] * geo.n; }
   long long launches = 0;
   // Concurrent sweeps: with nconc auxiliary streams each node's launch waits
   // only on the launches it depends on (its operands' values in the forward;

@@ -216,6 +216,45 @@ static void fuse_neighbour3(GraphDef& G) {
   compact(G, dead);
 }
 
+void plan_reverse(const GraphDef& G, ReversePlan& P) {
+  const int nn = (int)G.nodes.size();
+  P.hasg.assign(nn, 0);
+  P.wa.assign(nn, 0);
+  P.wb.assign(nn, 0);
+  P.wc.assign(nn, 0);
+  P.gslot.assign(nn, -1);
+  P.gprev.assign(nn, -1);
+  P.nslots = 0;
+  std::vector<int> freel, last_reader;   // free arrays; per array, its last reader
+  auto take = [&](int x) {
+    if (P.gslot[x] >= 0) return;
+    if (!freel.empty()) {
+      P.gslot[x] = freel.back();
+      freel.pop_back();
+      P.gprev[x] = last_reader[P.gslot[x]];
+    } else {
+      P.gslot[x] = P.nslots++;
+      last_reader.push_back(-1);
+    }
+  };
+  std::vector<char> seen(nn, 0);
+  for (int k = 0; k < 8; ++k) {
+    seen[G.out[k]] = P.hasg[G.out[k]] = 1;
+    take(G.out[k]);   // the seeds
+  }
+  for (int i = nn - 1; i >= 0; --i) {
+    const GNode& nd = G.nodes[i];
+    if (!P.hasg[i] || !has_transpose(nd.op)) continue;
+    if (nd.a >= 0) { P.wa[i] = !seen[nd.a]; seen[nd.a] = P.hasg[nd.a] = 1; take(nd.a); }
+    if (nd.b >= 0) { P.wb[i] = !seen[nd.b]; seen[nd.b] = P.hasg[nd.b] = 1; take(nd.b); }
+    if (nd.c >= 0) { P.wc[i] = !seen[nd.c]; seen[nd.c] = P.hasg[nd.c] = 1; take(nd.c); }
+    // Node i's transpose has read its gradient: the array is free for the
+    // nodes after it in the sweep (not an input's, read at the end).
+    last_reader[P.gslot[i]] = i;
+    freel.push_back(P.gslot[i]);
+  }
+}
+
 // Drop the absorbed nodes and renumber every reference.
 static void compact(GraphDef& G, const std::vector<char>& dead) {
   const int nn = (int)G.nodes.size();

@@ -85,30 +85,21 @@ struct HostExec {
   GraphDef d;
   Geo g;
   bool allow4 = true;   // the four-x-cell kernels where the executor takes them
-  std::vector<std::vector<T>> v, gr;
+  std::vector<std::vector<T>> v, gr;   // node values; the plan's gradient arrays
   std::vector<T> mesh;
-  std::vector<char> hasg, wa, wb, wc;
+  ReversePlan rp;
+  int nslots = 0;
 
   void init() {
     const size_t nn = d.nodes.size();
     v.assign(nn, std::vector<T>(g.n, 0));
-    gr.assign(nn, std::vector<T>(g.n, 0));
     mesh.assign(d.mesh.begin(), d.mesh.end());
-    hasg.assign(nn, 0);
-    wa.assign(nn, 0);
-    wb.assign(nn, 0);
-    wc.assign(nn, 0);
-    std::vector<char> seen(nn, 0);
-    for (int k = 0; k < 8; ++k) seen[d.out[k]] = hasg[d.out[k]] = 1;
-    for (long long i = (long long)nn - 1; i >= 0; --i) {
-      const GNode& nd = d.nodes[i];
-      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP)
-        continue;
-      if (nd.a >= 0) { wa[i] = !seen[nd.a]; seen[nd.a] = hasg[nd.a] = 1; }
-      if (nd.b >= 0) { wb[i] = !seen[nd.b]; seen[nd.b] = hasg[nd.b] = 1; }
-      if (nd.c >= 0) { wc[i] = !seen[nd.c]; seen[nd.c] = hasg[nd.c] = 1; }
-    }
+    plan_reverse(d, rp);
+    // NaN-filled: a contribution added to an array that its first writer
+    // did not write (a fresh or a reused one) shows as non-finite.
+    gr.assign(rp.nslots, std::vector<T>(g.n, (T)NAN));
   }
+  T* gp(int x) { return gr[rp.gslot[x]].data(); }
   // The horizontal-plane mean, written or added (G_PMEAN and its transpose).
   void pmean(const T* a, T* o, bool add) const {
     for (int k = 0; k < g.nz; ++k) {
@@ -164,20 +155,19 @@ struct HostExec {
     }
   }
   void backward(const std::vector<std::vector<T>>& seed, std::vector<std::vector<T>>& gin) {
-    for (int k = 0; k < 8; ++k) gr[d.out[k]] = seed[k];
+    for (int k = 0; k < 8; ++k) gr[rp.gslot[d.out[k]]] = seed[k];
     std::vector<T> S(15 * g.n);
     for (long long i = (long long)d.nodes.size() - 1; i >= 0; --i) {
       const GNode nd = d.nodes[i];
-      if (!hasg[i] || nd.op == G_INPUT || nd.op == G_CONST || nd.op == G_ZFIELD || nd.op == G_STEP)
-        continue;
+      if (!rp.hasg[i] || !has_transpose(nd.op)) continue;
       const T* A = nd.a >= 0 ? v[nd.a].data() : nullptr;
       const T* B = nd.b >= 0 ? v[nd.b].data() : nullptr;
-      T* gA = nd.a >= 0 ? gr[nd.a].data() : nullptr;
-      T* gB = nd.b >= 0 ? gr[nd.b].data() : nullptr;
-      T* gC = nd.c >= 0 ? gr[nd.c].data() : nullptr;
+      T* gA = nd.a >= 0 ? gp(nd.a) : nullptr;
+      T* gB = nd.b >= 0 ? gp(nd.b) : nullptr;
+      T* gC = nd.c >= 0 ? gp(nd.c) : nullptr;
       const T* out = v[i].data();
-      const T* go = gr[i].data();
-      const int WA = wa[i], WB = wb[i], WC = wc[i];
+      const T* go = gp((int)i);
+      const int WA = rp.wa[i], WB = rp.wb[i], WC = rp.wc[i];
       const Geo& G = g;
       const int vec = g.n % 4 == 0 && al16(A) && al16(B) && al16(out) && al16(go) && al16(gA) &&
                       al16(gB) && al16(gC);
@@ -216,7 +206,9 @@ struct HostExec {
 #undef BW
 #undef BP
     }
-    for (int k = 0; k < 8; ++k) gin[k] = gr[d.in[k]];
+    for (int k = 0; k < 8; ++k)
+      gin[k] = rp.gslot[d.in[k]] >= 0 ? gr[rp.gslot[d.in[k]]] : std::vector<T>(g.n, (T)0);
+    nslots = rp.nslots;
   }
 };
 
@@ -268,6 +260,7 @@ static int compare(const char* name, const stagger_grid& gg, const stagger_param
   std::vector<std::vector<T>> res[3], gin[3];
   size_t nodes[3];
   long long four[3];
+  int arrays[3];
   for (int t = 0; t < 3; ++t) {
     g_four = 0;
     HostExec<T> h;
@@ -281,6 +274,7 @@ static int compare(const char* name, const stagger_grid& gg, const stagger_param
     gin[t].resize(8);
     h.backward(seed, gin[t]);
     four[t] = g_four;
+    arrays[t] = h.nslots;
   }
   int fails = 0;
   for (int t = 1; t < 3; ++t) {
@@ -297,10 +291,10 @@ static int compare(const char* name, const stagger_grid& gg, const stagger_param
       worst = std::max(worst, e / std::max(s, 1e-300));
     }
     const bool ok = diff == 0 && bad == 0 && worst <= tol;
-    printf("%s %s %s (%lld four-cell launches): %zu -> %zu nodes, forward %lld differing "
-           "values, %lld non-finite, reverse max rel err %.2e%s\n", name,
+    printf("%s %s %s (%lld four-cell launches): %zu -> %zu nodes, %d -> %d gradient arrays, "
+           "forward %lld differing values, %lld non-finite, reverse max rel err %.2e%s\n", name,
            sizeof(T) == 8 ? "FP64" : "FP32", t == 1 ? "one-cell" : "four-cell", four[t],
-           nodes[0], nodes[t], diff, bad, worst, ok ? "" : "  FAIL");
+           nodes[0], nodes[t], arrays[0], arrays[t], diff, bad, worst, ok ? "" : "  FAIL");
     fails += !ok;
   }
   return fails;
